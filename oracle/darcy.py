@@ -1,0 +1,310 @@
+"""One Darcy-flow sample of the layered model, plain FP64 (test infrastructure).
+
+Follows the paper section by section:
+
+* Sec. 2, random partition and Ex. 1 / Ex. 2: the unit square is split into
+  horizontal layers by random interface heights; layer t carries
+  k_t = exp(g_t) with g_t either the constant mu_t + sigma_t Z_t (Ex. 1) or a
+  stationary Gaussian field with the exponential covariance of Eq. 2.3.
+* Sec. 3.4 / 3.5: fields are drawn exactly on the cell-centre grid by
+  circulant embedding (CE) on an M x M torus.
+* Sec. 3.1, Eq. 3.3 with the harmonic face average of Sec. 3.1/3.4: the
+  cell-centred five-point system; Dirichlet faces use the one-sided
+  difference over half a cell (transmissibility 2k), Neumann faces carry no
+  flux.
+* Sec. 3.4, Model Problem 2: p = 1 at x1 = 0, p = 0 at x1 = 1, no flow on
+  x2 = 0 and x2 = 1; the quantity of interest M^(2) is the outflow at x1 = 1.
+
+Layout: a grid of m x m cells, cell (i, j) 0-based with centre
+((i + 1/2) h, (j + 1/2) h), h = 1/m; arrays are indexed [j, i] (x1 = flow
+direction along the fast axis).
+"""
+from dataclasses import dataclass, field
+from typing import List
+
+import numpy as np
+import scipy.linalg
+
+from . import philox
+
+# Padding rule of the circulant embedding: grow M = p*m (p = 2, 4, 8, ...)
+# until every eigenvalue of the embedding is >= -CE_NEG_TOL * max eigenvalue;
+# eigenvalues inside that band are clipped to zero.
+CE_NEG_TOL = 1e-13
+CE_MAX_PAD = 16
+
+
+@dataclass
+class Model:
+    """Parameters of the layered permeability model and the solver.
+
+    k_kind: 0 = piecewise constant (Ex. 1), 1 = piecewise log-normal field (Ex. 2)
+    if_lo, if_hi: the n_layers-1 interface heights are U(if_lo, if_hi) draws,
+        sorted ascending; layer 0 is the bottom layer.
+    mu, sigma2, lam: per-layer mean, variance and correlation length.
+    norm_r: the l_r norm of Eq. 2.3 (1 or 2).
+    m0, L: level l has m0 * 2^l cells per side, l = 0..L.
+    cgv: 0 plain MLMC coupling, 1 Coarse Grid Variates subsampling the
+        per-layer Gaussian fields, 2 CGV subsampling the composed k.
+    tol: relative residual tolerance of iterative solvers (unused by the
+        direct solve of the oracle).
+    """
+    n_layers: int = 2
+    k_kind: int = 0
+    if_lo: float = 0.3
+    if_hi: float = 0.7
+    mu: List[float] = field(default_factory=lambda: [0.0] * 8)
+    sigma2: List[float] = field(default_factory=lambda: [1.0] * 8)
+    lam: List[float] = field(default_factory=lambda: [0.3] * 8)
+    norm_r: int = 2
+    m0: int = 8
+    L: int = 2
+    cgv: int = 0
+    prec: int = 0
+    tol: float = 1e-12
+    max_it: int = 200
+
+    @classmethod
+    def from_dict(cls, d):
+        kw = {k: d[k] for k in cls.__dataclass_fields__ if k in d}
+        for key in ("mu", "sigma2", "lam"):
+            if key in kw:
+                v = list(kw[key]) + [kw[key][-1]] * (8 - len(kw[key]))
+                kw[key] = v[:8]
+        return cls(**kw)
+
+    def m(self, level):
+        return self.m0 << level
+
+
+# ---------------------------------------------------------------- layers ----
+def interfaces(model, seed, level, sample):
+    """Sorted interface heights eta_t ~ U(if_lo, if_hi) (Sec. 2, random partition).
+
+    eta = lo + (hi - lo) * u, each operation rounded once (no fused multiply-add)."""
+    n_if = model.n_layers - 1
+    if n_if == 0:
+        return np.zeros(0)
+    u = philox.interface_uniforms(seed, level, sample, n_if)
+    width = np.float64(model.if_hi) - np.float64(model.if_lo)
+    eta = np.float64(model.if_lo) + width * u
+    return np.sort(eta)
+
+
+def layer_of_rows(eta, m):
+    """Layer index of each cell row j: the number of interfaces at or below the
+    row's centre y_j = (j + 1/2)/m (a centre exactly on an interface belongs to
+    the upper layer)."""
+    y = (np.arange(m) + 0.5) / m
+    return np.array([int(np.sum(eta <= yj)) for yj in y], dtype=np.int64)
+
+
+# ------------------------------------------------------ circulant embedding --
+def covariance_torus(m, M, sigma2, lam, norm_r):
+    """c[b, a] = sigma2 * exp(-||(d_a h, d_b h)||_r / lam) on the M x M torus of
+    cell-centre offsets (Eq. 2.3), d_a = min(a, M - a), h = 1/m."""
+    a = np.arange(M)
+    d = np.minimum(a, M - a) / m
+    dx = d[None, :]
+    dy = d[:, None]
+    if norm_r == 1:
+        dist = np.abs(dx) + np.abs(dy)
+    else:
+        dist = np.sqrt(dx * dx + dy * dy)
+    return sigma2 * np.exp(-dist / lam)
+
+
+def ce_eigenvalues(m, M, sigma2, lam, norm_r):
+    """Eigenvalues of the block-circulant embedding: the unnormalised forward
+    2-D DFT of the torus covariance (real because c is even)."""
+    return np.fft.fft2(covariance_torus(m, M, sigma2, lam, norm_r)).real
+
+
+def ce_padding(m, sigma2, lam, norm_r):
+    """Smallest M = p*m, p in {2, 4, 8, 16}, whose embedding is non-negative up to
+    the clipping band; returns (M, eigenvalues clipped to >= 0)."""
+    p = 2
+    while True:
+        M = p * m
+        lam_q = ce_eigenvalues(m, M, sigma2, lam, norm_r)
+        if lam_q.min() >= -CE_NEG_TOL * lam_q.max() or p >= CE_MAX_PAD:
+            if lam_q.min() < -CE_NEG_TOL * lam_q.max():
+                raise ValueError("circulant embedding not non-negative at p=%d" % p)
+            return M, np.maximum(lam_q, 0.0)
+        p *= 2
+
+
+def ce_pair(lam_q, xi, m):
+    """Two independent fields on the m x m cell centres from one complex draw:
+    y[b, a] = sum_q sqrt(Lambda_q)/M xi_q exp(-2 pi i (a q1 + b q2)/M);
+    returns (Re y, Im y) cropped to the first m x m entries."""
+    M = lam_q.shape[0]
+    y = np.fft.fft2(np.sqrt(lam_q) / M * xi)
+    return y.real[:m, :m], y.imag[:m, :m]
+
+
+def layer_fields(model, seed, level, sample, m, ce_cache=None):
+    """Per-layer fields g_t on the m x m grid: Ex. 1 constants or Ex. 2 CE fields.
+
+    Returns an array g[t, j, i] (t < n_layers)."""
+    nl = model.n_layers
+    g = np.empty((nl, m, m))
+    if model.k_kind == 0:
+        z = philox.layer_normals(seed, level, sample, nl)
+        for t in range(nl):
+            g[t] = model.mu[t] + np.sqrt(model.sigma2[t]) * z[t]
+        return g
+    for f in range((nl + 1) // 2):
+        t0, t1 = 2 * f, min(2 * f + 1, nl - 1)
+        if (model.sigma2[t0], model.lam[t0]) != (model.sigma2[t1], model.lam[t1]):
+            raise ValueError("layers of one field pair must share sigma2 and lambda")
+        key = (m, model.sigma2[t0], model.lam[t0], model.norm_r)
+        if ce_cache is not None and key in ce_cache:
+            M, lam_q = ce_cache[key]
+        else:
+            M, lam_q = ce_padding(m, model.sigma2[t0], model.lam[t0], model.norm_r)
+            if ce_cache is not None:
+                ce_cache[key] = (M, lam_q)
+        xi = philox.field_normals(seed, level, sample, f, M)
+        re, im = ce_pair(lam_q, xi, m)
+        g[t0] = model.mu[t0] + re
+        if 2 * f + 1 < nl:
+            g[t1] = model.mu[t1] + im
+    return g
+
+
+def compose_k(g, rows_layer):
+    """k at the cell centres: k[j, i] = exp(g_{layer(j)}[j, i])."""
+    m = g.shape[1]
+    return np.exp(g[rows_layer[:, None], np.arange(m)[:, None], np.arange(m)[None, :]])
+
+
+# ----------------------------------------------------------------- TPFA -----
+def transmissibilities(k):
+    """Face coefficients of Eq. 3.3 with harmonic face averages.
+
+    tx[j, i'] for the m+1 faces x1 = i'/m of row j: interior faces
+    2 k_a k_b / (k_a + k_b); Dirichlet faces (i' = 0, m) 2 k_cell from the
+    one-sided difference over half a cell.
+    ty[j', i] for the m+1 faces x2 = j'/m of column i: interior faces harmonic;
+    the no-flow faces (j' = 0, m) carry 0."""
+    m = k.shape[0]
+    tx = np.zeros((m, m + 1))
+    ty = np.zeros((m + 1, m))
+    ka, kb = k[:, :-1], k[:, 1:]
+    tx[:, 1:m] = 2.0 * ka * kb / (ka + kb)
+    tx[:, 0] = 2.0 * k[:, 0]
+    tx[:, m] = 2.0 * k[:, m - 1]
+    ka, kb = k[:-1, :], k[1:, :]
+    ty[1:m, :] = 2.0 * ka * kb / (ka + kb)
+    return tx, ty
+
+
+def rhs(tx):
+    """Right-hand side: the Dirichlet value p = 1 at x1 = 0 enters through the
+    west boundary face of column i = 0 (f = 0 in Model Problem 2)."""
+    m = tx.shape[0]
+    b = np.zeros((m, m))
+    b[:, 0] = tx[:, 0] * 1.0
+    return b
+
+
+def banded_upper(tx, ty):
+    """The SPD five-point matrix in LAPACK upper banded storage (bandwidth m),
+    unknown n = j*m + i."""
+    m = tx.shape[0]
+    n = m * m
+    ab = np.zeros((m + 1, n))
+    diag = tx[:, :m] + tx[:, 1:] + ty[:m, :] + ty[1:, :]
+    ab[m, :] = diag.reshape(-1)
+    east = np.zeros((m, m))
+    east[:, :m - 1] = -tx[:, 1:m]           # coupling (i, j) -- (i+1, j)
+    ab[m - 1, 1:] = east.reshape(-1)[:-1]
+    if m > 1:
+        north = -ty[1:m, :]                 # coupling (i, j) -- (i, j+1)
+        ab[0, m:] = north.reshape(-1)
+    return ab
+
+
+def solve_direct(tx, ty, b):
+    """Direct banded Cholesky solve of the five-point system (LAPACK pbsv)."""
+    m = tx.shape[0]
+    if m == 1:
+        return (b / (tx[:, :1] + tx[:, 1:] + ty[:1, :] + ty[1:, :])).reshape(1, 1)
+    p = scipy.linalg.solveh_banded(banded_upper(tx, ty), b.reshape(-1), lower=False)
+    return p.reshape(m, m)
+
+
+def outflow(tx, p):
+    """M^(2): outflow through x1 = 1, sum_j tx[j, m] * (p[j, m-1] - 0)."""
+    return float(np.sum(tx[:, -1] * p[:, -1]))
+
+
+def inflow(tx, p):
+    """Inflow through x1 = 0, sum_j tx[j, 0] * (1 - p[j, 0])."""
+    return float(np.sum(tx[:, 0] * (1.0 - p[:, 0])))
+
+
+def solve_k(k):
+    """Assemble and solve for one permeability array; returns (p, Q)."""
+    tx, ty = transmissibilities(k)
+    p = solve_direct(tx, ty, rhs(tx))
+    return p, outflow(tx, p)
+
+
+# ------------------------------------------------------- one MLMC sample ----
+CGV_OFFSETS = ((0, 0), (1, 0), (0, 1), (1, 1))  # (ox, oy) in summation order
+
+
+def coarse_samples(model, g_fine, k_fine, eta, mode):
+    """Coarse permeability arrays on the level below, extracted from the fine
+    sample (Sec. 4.1, Eq. 4.1).
+
+    mode 0 (plain coupling): one coarse sample, offset (0, 0).
+    mode 1 (CGV): the 2^d = 4 strided sub-vectors of the fine per-layer fields
+        g_t at offsets (ox, oy), composed with the layer map of the coarse
+        centres.
+    mode 2 (CGV on k): the 4 strided sub-vectors of the composed fine k."""
+    m = g_fine.shape[1]
+    mc = m // 2
+    rows_c = layer_of_rows(eta, mc)
+    offsets = CGV_OFFSETS[:1] if mode == 0 else CGV_OFFSETS
+    out = []
+    for ox, oy in offsets:
+        if mode == 2:
+            out.append(k_fine[oy::2, ox::2].copy())
+        else:
+            gc = g_fine[:, oy::2, ox::2]
+            out.append(compose_k(gc, rows_c))
+    return out
+
+
+def sample(model, seed, level, i, ce_cache=None, want_fields=False):
+    """Q_l and the coarse Q's of sample i at level l (Eq. 3.6, Eq. 4.2).
+
+    Returns a dict with qf, qc (plain coupling, offset (0,0); 0 at l = 0),
+    qc_cgv (mean of the 4 CGV coarse Q's, in CGV_OFFSETS order; NaN if
+    cgv == 0), and diagnostics."""
+    m = model.m(level)
+    eta = interfaces(model, seed, level, i)
+    rows = layer_of_rows(eta, m)
+    g = layer_fields(model, seed, level, i, m, ce_cache)
+    k = compose_k(g, rows)
+    p, qf = solve_k(k)
+    out = {"qf": qf, "qc": 0.0, "qc_cgv": float("nan"), "eta": eta, "rows": rows,
+           "inflow": inflow(transmissibilities(k)[0], p)}
+    if want_fields:
+        out.update(g=g, k=k, p=p)
+    if level > 0:
+        if model.cgv == 0:
+            (kc,) = coarse_samples(model, g, k, eta, 0)
+            out["qc"] = solve_k(kc)[1]
+        else:
+            kcs = coarse_samples(model, g, k, eta, model.cgv)
+            qcs = [solve_k(kc)[1] for kc in kcs]
+            out["qc"] = qcs[0]
+            out["qc_cgv"] = 0.25 * (((qcs[0] + qcs[1]) + qcs[2]) + qcs[3])
+            out["qc_each"] = qcs
+    elif model.cgv != 0:
+        out["qc_cgv"] = 0.0
+    return out

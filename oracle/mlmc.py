@@ -1,0 +1,125 @@
+"""MLMC level batches and the estimator, plain FP64 (test infrastructure).
+
+* Eq. 3.6: the estimator sums, level by level, sample means of
+  Y_l = Q_l - Q_{l-1} where both terms use the same random sample and
+  Q_{-1} = 0.
+* Eq. 4.1 / 4.2: with Coarse Grid Variates the coarse term is the mean of the
+  2^d coarse quantities extracted from the fine sample.
+* Eq. 3.7 and Thm 3.1: the sampling error sum_l V_l / N_l is held below
+  eps^2 / 2 (the even split of eps^2); N_l follows the standard cost-optimal
+  rule N_l = ceil(2 eps^-2 sqrt(V_l / C_l) sum_k sqrt(V_k C_k)).
+
+Level sums are exactly rounded (math.fsum); variances use the unbiased
+(N - 1) sample estimator.
+"""
+import math
+
+import numpy as np
+
+from . import darcy
+
+SUM_KEYS = ("s_qf", "s_qf2", "s_qc", "s_qc2", "s_y", "s_y2",
+            "s_qcg", "s_qcg2", "s_yg", "s_yg2")
+
+
+def level_batch(model, level, first, n, seed, ce_cache=None):
+    """Samples first .. first+n-1 of level ``level``; returns per-sample arrays
+    qf, qc, qc_cgv and the exactly rounded level sums."""
+    if ce_cache is None:
+        ce_cache = {}
+    qf = np.empty(n)
+    qc = np.empty(n)
+    qg = np.empty(n)
+    for s in range(n):
+        r = darcy.sample(model, seed, level, first + s, ce_cache)
+        qf[s], qc[s], qg[s] = r["qf"], r["qc"], r["qc_cgv"]
+    return {"qf": qf, "qc": qc, "qc_cgv": qg, "sums": level_sums(qf, qc, qg, model.cgv != 0)}
+
+
+def level_sums(qf, qc, qg, cgv):
+    """Exactly rounded sums of Q_f, Q_c, Y = Q_f - Q_c and their squares, plus
+    the CGV versions (zero when CGV is off)."""
+    y = qf - qc
+    s = {"n": len(qf),
+         "s_qf": math.fsum(qf), "s_qf2": math.fsum(qf * qf),
+         "s_qc": math.fsum(qc), "s_qc2": math.fsum(qc * qc),
+         "s_y": math.fsum(y), "s_y2": math.fsum(y * y)}
+    if cgv:
+        yg = qf - qg
+        s.update(s_qcg=math.fsum(qg), s_qcg2=math.fsum(qg * qg),
+                 s_yg=math.fsum(yg), s_yg2=math.fsum(yg * yg))
+    else:
+        s.update(s_qcg=0.0, s_qcg2=0.0, s_yg=0.0, s_yg2=0.0)
+    return s
+
+
+def merge_sums(a, b):
+    """Sums of the union of two disjoint sample ranges."""
+    out = {"n": a["n"] + b["n"]}
+    for key in SUM_KEYS:
+        out[key] = math.fsum([a[key], b[key]])
+    return out
+
+
+def mean_var(n, s1, s2):
+    """Sample mean and unbiased sample variance from a count, a sum and a sum
+    of squares."""
+    mean = s1 / n
+    var = (s2 - s1 * s1 / n) / (n - 1) if n > 1 else float("inf")
+    return mean, max(var, 0.0)
+
+
+def level_stats(sums, use_cgv):
+    """(mean, variance) of the level correction used by the estimator:
+    Y^cgv when CGV is on, else Y."""
+    if use_cgv:
+        return mean_var(sums["n"], sums["s_yg"], sums["s_yg2"])
+    return mean_var(sums["n"], sums["s_y"], sums["s_y2"])
+
+
+def optimal_samples(eps, V, C):
+    """N_l = ceil(2 eps^-2 sqrt(V_l / C_l) sum_k sqrt(V_k C_k)): the cost-minimal
+    sample sizes with sum_l V_l / N_l = eps^2 / 2."""
+    total = sum(math.sqrt(v * c) for v, c in zip(V, C))
+    return [int(math.ceil(2.0 / (eps * eps) * math.sqrt(v / c) * total)) for v, c in zip(V, C)]
+
+
+def parity_cost(model, level):
+    """Deterministic cost model: fine cells plus coarse cells solved per sample."""
+    m2 = float(model.m(level) ** 2)
+    if level == 0:
+        return m2
+    nc = 4 if model.cgv else 1
+    return m2 * (1.0 + 0.25 * nc)
+
+
+def estimate(model, eps, seed, n_pilot=64, max_rounds=10, cost=None):
+    """Adaptive MLMC estimate of E[Q_L] with sampling error <= eps^2 / 2.
+
+    Runs n_pilot samples per level, then tops every level up to the optimal N_l
+    computed from the running variances, until no level needs more samples.
+    Returns dict(q_hat, N, V, mean, C, rounds)."""
+    cost = cost or (lambda lvl: parity_cost(model, lvl))
+    L = model.L
+    C = [cost(lvl) for lvl in range(L + 1)]
+    cache = {}
+    sums = []
+    for lvl in range(L + 1):
+        sums.append(level_batch(model, lvl, 0, n_pilot, seed, cache)["sums"])
+    rounds = 0
+    while True:
+        stats = [level_stats(sums[lvl], model.cgv != 0 and lvl > 0) for lvl in range(L + 1)]
+        V = [v for _, v in stats]
+        N_opt = optimal_samples(eps, V, C)
+        todo = [max(0, N_opt[lvl] - sums[lvl]["n"]) for lvl in range(L + 1)]
+        if not any(todo) or rounds >= max_rounds:
+            break
+        rounds += 1
+        for lvl in range(L + 1):
+            if todo[lvl]:
+                b = level_batch(model, lvl, sums[lvl]["n"], todo[lvl], seed, cache)
+                sums[lvl] = merge_sums(sums[lvl], b["sums"])
+    stats = [level_stats(sums[lvl], model.cgv != 0 and lvl > 0) for lvl in range(L + 1)]
+    q_hat = math.fsum(mu for mu, _ in stats)
+    return {"q_hat": q_hat, "N": [s["n"] for s in sums], "V": [v for _, v in stats],
+            "mean": [mu for mu, _ in stats], "C": C, "rounds": rounds, "sums": sums}

@@ -1,0 +1,165 @@
+"""Pins of the oracle's MLMC layer (Eq. 3.6, Eq. 3.7, Eq. 4.1, Eq. 4.2):
+exact per-sample closed form and exact moments of the piecewise-constant
+model, sum identities, the sample-size rule, CGV unbiasedness and its
+variance reduction."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import darcy, mlmc, philox
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def const_model(**kw):
+    return darcy.Model.from_dict(workloads.workload("const_2layer_8to32", **kw))
+
+
+def test_const_model_per_sample_closed_form():
+    # Horizontal constant layers: Q_l = k_2 + (k_1 - k_2) * n_l(eta) / m_l with
+    # n_l the number of row centres below eta, for the fine and the coarse grid.
+    model = const_model()
+    for lvl in (0, 1, 2):
+        m = model.m(lvl)
+        for i in range(20):
+            r = darcy.sample(model, 0, lvl, i)
+            u = philox.interface_uniforms(0, lvl, i, 1)[0]
+            eta = 0.3 + (0.7 - 0.3) * u
+            z = philox.layer_normals(0, lvl, i, 2)
+            k1, k2 = math.exp(z[0]), math.exp(z[1])
+            w = math.ceil(m * eta - 0.5) / m
+            assert abs(r["qf"] - (k2 + (k1 - k2) * w)) < 1e-11 * r["qf"]
+            if lvl:
+                wc = math.ceil(m // 2 * eta - 0.5) / (m // 2)
+                assert abs(r["qc"] - (k2 + (k1 - k2) * wc)) < 1e-11 * r["qc"]
+
+
+def test_const_model_exact_moments():
+    gold = json.load(open(os.path.join(GOLD, "const_2layer_moments.json")))
+    assert abs(gold["E_Q"] - math.exp(0.5)) < 1e-15
+    model = const_model()
+    n = 4000
+    for lvl, m in enumerate((8, 16, 32)):
+        b = mlmc.level_batch(model, lvl, 0, n, 1000 + lvl)
+        vq = gold["V_Q"][str(m)]
+        # sample mean within 4.5 standard errors of e^(1/2)
+        assert abs(b["qf"].mean() - gold["E_Q"]) < 4.5 * math.sqrt(vq / n)
+        # sample variance of a log-normal mixture: loose relative band
+        assert abs(b["qf"].var(ddof=1) / vq - 1.0) < 0.35
+        if lvl:
+            vy = gold["V_Y"]["%d_%d" % (m, m // 2)]
+            y = b["qf"] - b["qc"]
+            assert abs(y.mean()) < 5 * math.sqrt(vy / n)
+            assert abs(y.var(ddof=1) / vy - 1.0) < 0.35
+
+
+def test_const_model_cgv_equals_plain():
+    # Constant per-layer k: every strided sub-vector carries the same values,
+    # so the CGV average equals the plain coarse sample.
+    model = const_model(cgv=1)
+    for i in range(5):
+        r = darcy.sample(model, 0, 2, i)
+        for q in r["qc_each"]:
+            assert abs(q - r["qc"]) < 1e-12 * r["qc"]
+        assert abs(r["qc_cgv"] - r["qc"]) < 1e-12 * r["qc"]
+
+
+def test_level_sums_identities():
+    model = darcy.Model.from_dict(workloads.workload("lognormal_2layer_cgv_16to512", m0=8, L=1))
+    b = mlmc.level_batch(model, 1, 3, 40, 5)
+    s = b["sums"]
+    assert s["n"] == 40
+    assert abs(s["s_y"] - (s["s_qf"] - s["s_qc"])) < 1e-13 * abs(s["s_qf"])
+    assert abs(s["s_yg"] - (s["s_qf"] - s["s_qcg"])) < 1e-13 * abs(s["s_qf"])
+    assert s["s_qf2"] == math.fsum(b["qf"] ** 2)
+    # ranges merge: [3, 23) + [23, 43) == [3, 43)
+    b1 = mlmc.level_batch(model, 1, 3, 20, 5)
+    b2 = mlmc.level_batch(model, 1, 23, 20, 5)
+    assert np.array_equal(np.concatenate([b1["qf"], b2["qf"]]), b["qf"])
+    merged = mlmc.merge_sums(b1["sums"], b2["sums"])
+    for key in mlmc.SUM_KEYS:
+        assert abs(merged[key] - s[key]) <= 2e-16 * max(1.0, abs(s[key]))
+
+
+def test_level_zero_has_no_coarse_term():
+    model = darcy.Model.from_dict(workloads.workload("lognormal_2layer_16to256", m0=8))
+    b = mlmc.level_batch(model, 0, 0, 5, 0)
+    assert np.all(b["qc"] == 0.0)
+    assert b["sums"]["s_y"] == b["sums"]["s_qf"]
+
+
+def test_optimal_samples_rule():
+    # Lagrange optimum of sum N_l C_l subject to sum V_l/N_l = eps^2/2:
+    # N_l proportional to sqrt(V_l/C_l); the constraint holds after rounding up.
+    V = [0.27, 1.9e-3, 4.6e-4, 6.1e-5, 1.7e-5]
+    C = [256.0 * 4 ** l for l in range(5)]
+    eps = 1e-3
+    N = mlmc.optimal_samples(eps, V, C)
+    assert sum(v / n for v, n in zip(V, N)) <= eps * eps / 2
+    lam = math.sqrt(2) / eps * math.sqrt(sum(math.sqrt(v * c) for v, c in zip(V, C)))
+    cont = [lam ** 2 * math.sqrt(v / c) / 1.0 for v, c in zip(V, C)]
+    cont = [x * 1.0 for x in cont]
+    for n, x in zip(N, cont):
+        assert n == math.ceil(x) or abs(n - x) < 1e-6 * x + 1
+    # any feasible reallocation of the continuous optimum costs more
+    rng = np.random.default_rng(0)
+    base = sum(x * c for x, c in zip(cont, C))
+    for _ in range(50):
+        pert = np.array(cont) * np.exp(0.3 * rng.standard_normal(5))
+        scale = sum(v / n for v, n in zip(V, pert)) / (eps * eps / 2)
+        pert *= scale
+        assert sum(x * c for x, c in zip(pert, C)) >= base * (1 - 1e-12)
+
+
+def test_estimate_const_model():
+    model = const_model(L=1)
+    est = mlmc.estimate(model, eps=0.15, seed=3, n_pilot=32)
+    # sampling error <= eps^2 / 2 by construction, and the estimate agrees with
+    # the exact mean e^(1/2) (the bias of this model is zero: E[Q_l] is exact)
+    var = sum(v / n for v, n in zip(est["V"], est["N"]))
+    assert var <= 0.15 ** 2 / 2 * 1.0001
+    assert abs(est["q_hat"] - math.exp(0.5)) < 4.5 * math.sqrt(var)
+    assert est["N"][0] > est["N"][1]
+
+
+def stationary_model(**kw):
+    d = workloads.workload("lognormal_2layer_16to256", n_layers=1, norm_r=1, lam=[0.3],
+                           sigma2=[1.0], mu=[0.0], m0=4, L=2, cgv=1)
+    d.update(kw)
+    return darcy.Model.from_dict(d)
+
+
+@pytest.mark.parametrize("layered", [False, True])
+def test_cgv_coarse_term_unbiased(layered):
+    # Eq. 4.1: each strided sub-vector of a fine sample is a valid coarse
+    # sample, so E[Q^cgv_{l-1}] from level-l batches equals E[Q_{l-1}] from
+    # independent level-(l-1) batches (two-sample z-test at 4.5 sigma).
+    if layered:
+        model = darcy.Model.from_dict(workloads.workload(
+            "lognormal_2layer_cgv_16to512", m0=4, L=1, lam=[0.3, 0.3]))
+    else:
+        model = stationary_model(L=1)
+    n = 1200
+    fine = mlmc.level_batch(model, 1, 0, n, 2024)
+    coarse = mlmc.level_batch(model, 0, 0, n, 4048)
+    for key in ("qc_cgv", "qc"):
+        a = fine[key]
+        z = (a.mean() - coarse["qf"].mean()) / math.sqrt(a.var() / n + coarse["qf"].var() / n)
+        assert abs(z) < 4.5, (key, z)
+
+
+def test_cgv_variance_reduction():
+    # Sec. 4.2: CGV lowers V[Y_l] by a large factor already on coarse grids and
+    # the reduction grows with the level (faster decay).  The paper's figure is
+    # not reproduced; the check is on the order of magnitude and the trend.
+    model = stationary_model(L=3)
+    ratios = []
+    for lvl in (1, 2, 3):
+        b = mlmc.level_batch(model, lvl, 0, 300, 1)
+        ratios.append(np.var(b["qf"] - b["qc"], ddof=1) / np.var(b["qf"] - b["qc_cgv"], ddof=1))
+    assert ratios[0] > 10 and ratios[1] > 30 and ratios[2] > 100
+    assert ratios[0] < ratios[1] < ratios[2]
