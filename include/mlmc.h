@@ -1,0 +1,192 @@
+/*
+ * mlmc.h -- C ABI of the GB300 MLMC level-batch library (libmlmc.so).
+ *
+ * The library computes, on one GPU, the per-level sample batch of the
+ * multilevel Monte Carlo method of Park & Teckentrup (arXiv 1506.04694) for
+ * steady Darcy flow in randomly layered media, Model Problem 2 of Sec. 3.4:
+ *   -div(k grad p) = 0 on (0,1)^2, p = 1 at x1 = 0, p = 0 at x1 = 1,
+ *   no flow at x2 = 0 and x2 = 1, quantity of interest Q = outflow at x1 = 1.
+ * Each sample draws a layered permeability (Sec. 2, Ex. 1 piecewise constant
+ * or Ex. 2 piecewise log-normal with the exponential covariance of Eq. 2.3,
+ * sampled by circulant embedding), assembles the cell-centred five-point
+ * finite-volume system of Eq. 3.3 with harmonic face averages, solves it,
+ * and reduces Q into the level sums of the estimators of Eq. 3.6 (plain) and
+ * Eq. 4.2 (Coarse Grid Variates, coarse samples from Eq. 4.1).
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: 0 = success; MLMC_SOME_FAILED (+1) = completed but some
+ *    samples did not converge (their Q is NaN and they are left out of the
+ *    sums); a negative value is an error, described by mlmc_error_string().
+ *  - "device pointer" arguments must point to memory of the context's GPU;
+ *    they are owned by the caller.  "host pointer" arguments are owned by the
+ *    caller too.  The context owns every internal workspace and table.
+ *  - All GPU work is issued on the stream given to mlmc_create(); a call
+ *    returns after its host-visible results are complete.
+ *  - There is no CPU fallback: without a usable GPU, mlmc_create() fails.
+ *  - Grid layout: level l has m = m0 * 2^l cells per side; cell (i, j),
+ *    0-based, has centre ((i + 1/2)/m, (j + 1/2)/m); per-sample arrays are
+ *    stored row-major as [j][i] (x1, the flow direction, fastest).
+ *  - Random numbers: sample i of level l with seed s is a pure function of
+ *    (s, l, i), drawn from Philox4x64-10 (Salmon et al. 2011) with key (s, 0)
+ *    and counter (call index, i, l, stream); see mlmc_philox_words().
+ */
+#ifndef MLMC_H
+#define MLMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MLMC_MAX_LAYERS 8
+
+#if defined(__GNUC__)
+#define MLMC_API __attribute__((visibility("default")))
+#else
+#define MLMC_API
+#endif
+
+/* Error codes. */
+#define MLMC_OK 0
+#define MLMC_SOME_FAILED 1
+#define MLMC_ERR_ARG (-1)       /* invalid argument */
+#define MLMC_ERR_CUDA (-2)      /* a CUDA runtime call failed */
+#define MLMC_ERR_NOMEM (-3)     /* device allocation failed */
+#define MLMC_ERR_EMBED (-4)     /* circulant embedding not non-negative up to padding 16 */
+#define MLMC_ERR_NODEV (-5)     /* no usable CUDA device */
+#define MLMC_ERR_TOOBIG (-6)    /* size above a documented maximum */
+
+/* Model and solver parameters (Sec. 2 Ex. 1 / Ex. 2, Sec. 3.4, Sec. 3.5, Sec. 4.1). */
+typedef struct mlmc_model {
+  int32_t n_layers;            /* 1..8 horizontal layers; layer 0 is the bottom one */
+  int32_t k_kind;              /* 0: k_t = exp(mu_t + sqrt(sigma2_t) Z_t), Z_t ~ N(0,1) (Ex. 1)
+                                  1: k_t = exp(g_t), g_t Gaussian field, mean mu_t, covariance
+                                     sigma2_t exp(-||x - y||_r / lam_t) (Ex. 2, Eq. 2.3) */
+  double if_lo, if_hi;         /* the n_layers-1 interface heights are U(if_lo, if_hi) draws,
+                                  sorted ascending; a row whose centre lies at or above
+                                  interface t is above it */
+  double mu[MLMC_MAX_LAYERS], sigma2[MLMC_MAX_LAYERS], lam[MLMC_MAX_LAYERS];
+                               /* k_kind 1: one embedding table per level serves all layers
+                                  (layers 2f and 2f+1 share one complex draw), so every layer
+                                  must have the same sigma2 and lam */
+  int32_t norm_r;              /* 1 or 2: the l_r norm of Eq. 2.3 */
+  int32_t m0, L;               /* coarsest cells per side (power of two, 2..4096); finest level */
+  int32_t cgv;                 /* 0: plain coupling, coarse sample = fine fields at the even
+                                     cells (offset (0,0)) composed on the coarse layer map;
+                                  1: Coarse Grid Variates, Eq. 4.1 / 4.2, the four offsets
+                                     (0,0), (1,0), (0,1), (1,1) of the per-layer fields;
+                                  2: Coarse Grid Variates on the composed k */
+  int32_t prec;                /* 0: FP64 throughout;
+                                  1: FP32 multigrid-preconditioned CG inside FP64 iterative
+                                     refinement (FP64 residual, solution, QoI and sums),
+                                     FP32 circulant-embedding FFT */
+  double tol;                  /* stop when ||b - A x||_2 < tol ||b||_2 (Sec. 3.5 uses 1e-10) */
+  int32_t max_it;              /* cap on CG iterations per solve (sum over refinement sweeps) */
+} mlmc_model;
+
+/* Level sums over a range of samples (Eq. 3.6 and Eq. 4.2): Q_f is Q_l of the
+ * sample, Q_c the plain coarse Q_{l-1} (0 at level 0), Y = Q_f - Q_c;
+ * Q_cg = (1/4) sum of the four CGV coarse Q's, Y_g = Q_f - Q_cg (zero when
+ * cgv == 0).  Sums are FP64 with Neumaier compensation in a fixed order. */
+typedef struct mlmc_level_sums {
+  int64_t n;                   /* samples summed (converged ones) */
+  int64_t n_failed;            /* samples whose solve did not converge */
+  int64_t iters_total;         /* CG iterations over all solves of the range */
+  double s_qf, s_qf2, s_qc, s_qc2, s_y, s_y2;
+  double s_qcg, s_qcg2, s_yg, s_yg2;
+  double seconds;              /* wall time of the call */
+} mlmc_level_sums;
+
+#define MLMC_MAX_LEVELS 12
+
+/* Result of mlmc_estimate(). */
+typedef struct mlmc_estimate_out {
+  double q_hat;                        /* MLMC estimate of E[Q_L] (Eq. 3.6 / Eq. 4.2) */
+  double var_hat;                      /* sum_l V_l / N_l, held <= eps^2 / 2 */
+  int64_t N[MLMC_MAX_LEVELS];          /* samples per level */
+  double V[MLMC_MAX_LEVELS];           /* unbiased sample variance of the level correction */
+  double mean[MLMC_MAX_LEVELS];        /* sample mean of the level correction */
+  double C[MLMC_MAX_LEVELS];           /* cost per sample used in the sample-size rule */
+  mlmc_level_sums sums[MLMC_MAX_LEVELS];
+  int32_t rounds;                      /* top-up rounds after the pilot */
+  double seconds;                      /* wall time */
+} mlmc_estimate_out;
+
+typedef struct mlmc_ctx mlmc_ctx;
+
+/* Create a context on CUDA device `device` for `model`, issuing work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  Builds
+ * the circulant-embedding tables of every level (padding M = p m with the
+ * smallest p in {2, 4, 8, 16} whose embedding eigenvalues are all
+ * >= -1e-13 max; the remaining negative ones are set to 0).
+ * Errors: MLMC_ERR_ARG (bad model), MLMC_ERR_NODEV, MLMC_ERR_EMBED, MLMC_ERR_NOMEM,
+ * MLMC_ERR_CUDA.  On error *out is NULL. */
+MLMC_API int mlmc_create(int device, const mlmc_model* model, void* cuda_stream, mlmc_ctx** out);
+
+/* Release the context and all its device memory.  NULL is allowed. */
+MLMC_API void mlmc_destroy(mlmc_ctx* ctx);
+
+/* Samples first .. first+n-1 of level `level` (Eq. 3.6 / Eq. 4.2).
+ * qf, qc, qc_cgv: device pointers to n doubles each, or NULL; receive Q_l,
+ *   the plain coarse Q_{l-1} (0 at level 0) and the CGV coarse average (NaN
+ *   when cgv == 0).  Failed samples hold NaN.
+ * iters: device pointer to n int32 (CG iterations of the fine solve) or NULL.
+ * sums: host pointer, required; receives the level sums of the range.
+ * Returns MLMC_OK, MLMC_SOME_FAILED or a negative error. */
+MLMC_API int mlmc_level_batch(mlmc_ctx* ctx, int level, int64_t first, int64_t n, uint64_t seed,
+                     double* qf, double* qc, double* qc_cgv, int32_t* iters,
+                     mlmc_level_sums* sums);
+
+/* Same as mlmc_level_batch() but qf, qc, qc_cgv, iters are HOST pointers (or
+ * NULL); the library copies results back before returning. */
+MLMC_API int mlmc_level_batch_host(mlmc_ctx* ctx, int level, int64_t first, int64_t n, uint64_t seed,
+                          double* qf, double* qc, double* qc_cgv, int32_t* iters,
+                          mlmc_level_sums* sums);
+
+/* Adaptive MLMC estimate with sampling error sum_l V_l/N_l <= eps^2/2 (the
+ * even split of Eq. 3.7): n_pilot samples per level, then repeated top-ups
+ * to N_l = ceil(2 eps^-2 sqrt(V_l/C_l) sum_k sqrt(V_k C_k)) until no level
+ * needs more (at most 10 rounds).  cost_model 0: C_l = m_l^2 (1 + n_coarse/4)
+ * with n_coarse = 0 at level 0, 1 plain, 4 CGV (deterministic); 1: C_l =
+ * measured seconds per sample of the pilot.  out: host pointer, required. */
+MLMC_API int mlmc_estimate(mlmc_ctx* ctx, double eps, uint64_t seed, int32_t n_pilot,
+                  int32_t cost_model, mlmc_estimate_out* out);
+
+/* Padding of level `level`: *M_out = M, and the smallest / largest raw
+ * embedding eigenvalue before clipping (host pointers, any may be NULL). */
+MLMC_API int mlmc_ce_info(mlmc_ctx* ctx, int level, int32_t* M_out, double* lam_min, double* lam_max);
+
+/* Raw Philox4x64-10 words for calls first_call .. first_call+n_calls-1 of one
+ * (seed, level, sample, stream): out is a device pointer to 4*n_calls uint64,
+ * call-major.  Stream 0 holds interface uniforms, 1 the Ex. 1 layer normals,
+ * 2+f the complex normals of circulant-embedding field pair f. */
+MLMC_API int mlmc_philox_words(uint64_t seed, uint64_t level, uint64_t sample, uint64_t stream,
+                      uint64_t first_call, int64_t n_calls, uint64_t* out, void* cuda_stream);
+
+/* Stage output for parity checks: the per-layer fields g_t of the fine grid of
+ * samples first .. first+n-1 of `level` (Ex. 1 constants or Ex. 2 fields),
+ * g: device pointer to n * n_layers * m * m doubles ([sample][t][j][i]);
+ * eta: device pointer to n * (n_layers - 1) doubles (sorted interfaces) or NULL. */
+MLMC_API int mlmc_sample_fields(mlmc_ctx* ctx, int level, int64_t first, int64_t n, uint64_t seed,
+                       double* g, double* eta);
+
+/* Solve n independent systems of size m x m (m a power of two, 1..4096)
+ * for given cell permeabilities, with the context's solver settings.
+ * k: device pointer to n*m*m doubles ([s][j][i]), all > 0.
+ * p: device pointer to n*m*m doubles (pressure) or NULL.
+ * q: device pointer to n doubles (outflow Q; NaN if not converged), required.
+ * iters: device pointer to n int32 or NULL. */
+MLMC_API int mlmc_solve_k(mlmc_ctx* ctx, int32_t m, int64_t n, const double* k, double* p, double* q,
+                 int32_t* iters);
+
+/* Human-readable text of an error code (static storage). */
+MLMC_API const char* mlmc_error_string(int code);
+
+/* Description of the last error on this thread (static storage). */
+MLMC_API const char* mlmc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLMC_H */

@@ -1,0 +1,256 @@
+"""GB300 MLMC level batch for Darcy flow in randomly layered media.
+
+Thin ctypes binding of ``libmlmc.so`` (C ABI in ``include/mlmc.h``): argument
+marshalling only; every step of the level batch runs in the library's CUDA
+kernels.  PyTorch supplies device memory and the CUDA stream.
+
+Functions keep the C names: ``mlmc_create`` -> :class:`Context`,
+``mlmc_level_batch`` -> :meth:`Context.level_batch`, ``mlmc_estimate`` ->
+:meth:`Context.estimate`, and so on.  There is no CPU fallback: without the
+built library, or without a GPU, the calls raise.
+"""
+import ctypes
+import os
+
+from . import build as _build_mod
+
+MAX_LAYERS = 8
+MAX_LEVELS = 12
+LIB_PATH = _build_mod.LIB
+
+_lib = None
+
+
+class Model(ctypes.Structure):
+    _fields_ = [
+        ("n_layers", ctypes.c_int32), ("k_kind", ctypes.c_int32),
+        ("if_lo", ctypes.c_double), ("if_hi", ctypes.c_double),
+        ("mu", ctypes.c_double * MAX_LAYERS), ("sigma2", ctypes.c_double * MAX_LAYERS),
+        ("lam", ctypes.c_double * MAX_LAYERS),
+        ("norm_r", ctypes.c_int32), ("m0", ctypes.c_int32), ("L", ctypes.c_int32),
+        ("cgv", ctypes.c_int32), ("prec", ctypes.c_int32),
+        ("tol", ctypes.c_double), ("max_it", ctypes.c_int32),
+    ]
+
+
+SUM_FIELDS = ("s_qf", "s_qf2", "s_qc", "s_qc2", "s_y", "s_y2", "s_qcg", "s_qcg2", "s_yg", "s_yg2")
+
+
+class LevelSums(ctypes.Structure):
+    _fields_ = ([("n", ctypes.c_int64), ("n_failed", ctypes.c_int64), ("iters_total", ctypes.c_int64)]
+                + [(k, ctypes.c_double) for k in SUM_FIELDS] + [("seconds", ctypes.c_double)])
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class EstimateOut(ctypes.Structure):
+    _fields_ = [
+        ("q_hat", ctypes.c_double), ("var_hat", ctypes.c_double),
+        ("N", ctypes.c_int64 * MAX_LEVELS), ("V", ctypes.c_double * MAX_LEVELS),
+        ("mean", ctypes.c_double * MAX_LEVELS), ("C", ctypes.c_double * MAX_LEVELS),
+        ("sums", LevelSums * MAX_LEVELS), ("rounds", ctypes.c_int32), ("seconds", ctypes.c_double),
+    ]
+
+
+class MLMCError(RuntimeError):
+    pass
+
+
+EXPORTS = {
+    "mlmc_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(Model), ctypes.c_void_p,
+                                   ctypes.POINTER(ctypes.c_void_p)]),
+    "mlmc_destroy": (None, [ctypes.c_void_p]),
+    "mlmc_level_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                        ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(LevelSums)]),
+    "mlmc_level_batch_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                                             ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.POINTER(LevelSums)]),
+    "mlmc_estimate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_uint64, ctypes.c_int32,
+                                     ctypes.c_int32, ctypes.POINTER(EstimateOut)]),
+    "mlmc_ce_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "mlmc_philox_words": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                         ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                                         ctypes.c_void_p, ctypes.c_void_p]),
+    "mlmc_sample_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
+    "mlmc_solve_k": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "mlmc_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "mlmc_last_error": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise MLMCError("libmlmc.so is not built (run paper_1506_04694_gb300.build.build())")
+        h = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            fn = getattr(h, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = h
+    return _lib
+
+
+def _check(rc, allow_failed=True):
+    if rc < 0 or (rc > 0 and not allow_failed):
+        L = lib()
+        raise MLMCError("%s: %s" % (L.mlmc_error_string(rc).decode(), L.mlmc_last_error().decode()))
+    return rc
+
+
+def make_model(d):
+    """C model struct from a dict with the fields of ``Model``."""
+    m = Model()
+    for name, ctype in Model._fields_:
+        if name not in d:
+            continue
+        v = d[name]
+        if name in ("mu", "sigma2", "lam"):
+            arr = list(v) + [v[-1]] * (MAX_LAYERS - len(v))
+            setattr(m, name, (ctypes.c_double * MAX_LAYERS)(*arr[:MAX_LAYERS]))
+        else:
+            setattr(m, name, v)
+    return m
+
+
+def _ptr(t, dtype=None):
+    if t is None:
+        return None
+    import torch
+    if not t.is_cuda:
+        raise MLMCError("expected a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise MLMCError("expected dtype %s, got %s" % (dtype, t.dtype))
+    if not t.is_contiguous():
+        raise MLMCError("expected a contiguous tensor")
+    del torch
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """An ``mlmc_ctx``: model, per-level embedding tables and workspaces on one GPU."""
+
+    def __init__(self, model, device=0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise MLMCError("no CUDA device: the MLMC level batch has no CPU fallback")
+        self.model_dict = dict(model)
+        self.model = make_model(model)
+        self.device = device
+        with torch.cuda.device(device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        h = ctypes.c_void_p()
+        _check(lib().mlmc_create(device, ctypes.byref(self.model), _stream_handle(self.stream),
+                                 ctypes.byref(h)), allow_failed=False)
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mlmc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def m(self, level):
+        return self.model.m0 << level
+
+    def level_batch(self, level, n, seed, first=0, qf=None, qc=None, qc_cgv=None, iters=None):
+        """mlmc_level_batch: per-sample outputs in the given CUDA tensors (float64
+        / int32, length n, optional) and the level sums as a dict."""
+        import torch
+        s = LevelSums()
+        rc = _check(lib().mlmc_level_batch(self._h, level, first, n, seed, _ptr(qf, torch.float64),
+                                           _ptr(qc, torch.float64), _ptr(qc_cgv, torch.float64),
+                                           _ptr(iters, torch.int32), ctypes.byref(s)))
+        d = s.as_dict()
+        d["rc"] = rc
+        return d
+
+    def level_batch_host(self, level, n, seed, first=0, want_arrays=True):
+        """mlmc_level_batch_host: per-sample outputs copied to host numpy arrays."""
+        import numpy as np
+        s = LevelSums()
+        qf = np.empty(n) if want_arrays else None
+        qc = np.empty(n) if want_arrays else None
+        qg = np.empty(n) if want_arrays else None
+        it = np.empty(n, dtype=np.int32) if want_arrays else None
+        p = (lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p))
+        rc = _check(lib().mlmc_level_batch_host(self._h, level, first, n, seed, p(qf), p(qc), p(qg),
+                                                p(it), ctypes.byref(s)))
+        d = s.as_dict()
+        d["rc"] = rc
+        return d, qf, qc, qg, it
+
+    def estimate(self, eps, seed, n_pilot=64, cost_model=0):
+        """mlmc_estimate: adaptive MLMC estimate with sampling error <= eps^2/2."""
+        out = EstimateOut()
+        rc = _check(lib().mlmc_estimate(self._h, eps, seed, n_pilot, cost_model, ctypes.byref(out)))
+        L = self.model.L + 1
+        return {"q_hat": out.q_hat, "var_hat": out.var_hat, "N": list(out.N[:L]), "V": list(out.V[:L]),
+                "mean": list(out.mean[:L]), "C": list(out.C[:L]), "rounds": out.rounds,
+                "seconds": out.seconds, "sums": [out.sums[i].as_dict() for i in range(L)], "rc": rc}
+
+    def ce_info(self, level):
+        M = ctypes.c_int32()
+        lo = ctypes.c_double()
+        hi = ctypes.c_double()
+        _check(lib().mlmc_ce_info(self._h, level, ctypes.byref(M), ctypes.byref(lo), ctypes.byref(hi)))
+        return M.value, lo.value, hi.value
+
+    def sample_fields(self, level, n, seed, first=0):
+        """mlmc_sample_fields: fine per-layer fields g [n, n_layers, m, m] and
+        sorted interfaces [n, n_layers-1], as CUDA float64 tensors."""
+        import torch
+        m = self.m(level)
+        nl = self.model.n_layers
+        g = torch.empty((n, nl, m, m), dtype=torch.float64, device="cuda:%d" % self.device)
+        eta = torch.empty((n, max(nl - 1, 1)), dtype=torch.float64, device=g.device)
+        _check(lib().mlmc_sample_fields(self._h, level, first, n, seed, _ptr(g), _ptr(eta)),
+               allow_failed=False)
+        return g, eta[:, :nl - 1]
+
+    def solve_k(self, k, want_p=True):
+        """mlmc_solve_k: solve the systems of a CUDA float64 tensor k [n, m, m];
+        returns (p or None, Q, iterations)."""
+        import torch
+        n, m, _ = k.shape
+        q = torch.empty(n, dtype=torch.float64, device=k.device)
+        it = torch.empty(n, dtype=torch.int32, device=k.device)
+        p = torch.empty_like(k) if want_p else None
+        _check(lib().mlmc_solve_k(self._h, m, n, _ptr(k.contiguous(), torch.float64), _ptr(p), _ptr(q),
+                                  _ptr(it)), allow_failed=False)
+        return p, q, it
+
+
+def philox_words(seed, level, sample, stream_id, first_call, n_calls, device=0):
+    """mlmc_philox_words: raw Philox4x64-10 words [n_calls, 4] as a CUDA int64
+    tensor (bit patterns of the uint64 words)."""
+    import torch
+    out = torch.empty((n_calls, 4), dtype=torch.int64, device="cuda:%d" % device)
+    _check(lib().mlmc_philox_words(seed, level, sample, stream_id, first_call, n_calls, _ptr(out),
+                                   _stream_handle(None)), allow_failed=False)
+    return out

@@ -1,0 +1,281 @@
+// Circulant-embedding sampler of the per-layer Gaussian fields (Sec. 2 Ex. 2,
+// Eq. 2.3; circulant embedding as cited in Sec. 3.4), with a hand-written
+// batched radix-2 FFT.
+//
+// A level with m x m cells embeds the cell-centre grid in an M x M torus,
+// M = p m.  With s_q = sqrt(Lambda_q)/M (Lambda = unnormalised forward 2-D DFT
+// of the torus covariance) and complex normals xi_q = z_re + i z_im,
+//   y[b][a] = sum_{q2,q1} s[q2][q1] xi[q2][q1] exp(-2 pi i (a q1 + b q2)/M)
+// gives two independent fields on the m x m grid: layer 2f <- Re y, layer
+// 2f+1 <- Im y, for field pair f.  Only a < m and b < m are needed, so:
+//   pass 1 (rows):    W[q2][a] = sum_q1 s xi exp(-2 pi i a q1/M),  a < m,
+//                     normals generated on chip from Philox, never stored;
+//   pass 2 (columns): y[b][a] = sum_q2 W[q2][a] exp(-2 pi i b q2/M), b < m,
+//                     written as g_t = mu_t + Re/Im y.
+// Each FFT of length M runs in shared memory: bit-reversed load, then log2 M
+// radix-2 decimation-in-time stages.
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace mlmc {
+
+template <typename R>
+struct Cplx {
+  R x, y;
+};
+
+__device__ __forceinline__ unsigned brev_n(unsigned v, int logn) {
+  return logn ? (__brev(v) >> (32 - logn)) : 0u;
+}
+
+// In-place radix-2 DIT FFTs of `nrows` contiguous rows of length M (rows
+// already in bit-reversed order) in shared memory; tw[k] = exp(-2 pi i k/M).
+template <typename R>
+__device__ void block_fft_rows(Cplx<R>* s, int nrows, int M, int logM, const Cplx<R>* __restrict__ tw) {
+  const int half = M >> 1;
+  const int nb = nrows * half;
+  for (int st = 0; st < logM; ++st) {
+    const int hs = 1 << st;
+    const int tstride = half >> st;  // twiddle index step M / (2 hs)
+    for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+      const int row = t / half;
+      const int b = t - row * half;
+      const int grp = b >> st;
+      const int pos = b & (hs - 1);
+      Cplx<R>* base = s + row * M;
+      const int i0 = (grp << (st + 1)) + pos;
+      const int i1 = i0 + hs;
+      const Cplx<R> w = tw[pos * tstride];
+      const Cplx<R> u = base[i0];
+      const Cplx<R> v = base[i1];
+      const R tx = w.x * v.x - w.y * v.y;
+      const R ty = w.x * v.y + w.y * v.x;
+      base[i0] = Cplx<R>{u.x + tx, u.y + ty};
+      base[i1] = Cplx<R>{u.x - tx, u.y - ty};
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ set-up -------
+template <typename R>
+__global__ void twiddle_kernel(Cplx<R>* tw, int M) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < M / 2) {
+    double s, c;
+    sincospi(-2.0 * (double)k / (double)M, &s, &c);
+    tw[k] = Cplx<R>{(R)c, (R)s};
+  }
+}
+
+// Torus covariance c[b][a] = sigma2 exp(-||(d_a h, d_b h)||_r / lam),
+// d_a = min(a, M - a), h = 1/m (Eq. 2.3 at cell-centre offsets).
+__global__ void covariance_kernel(Cplx<double>* c, int m, int M, double sigma2, double lam,
+                                  int norm_r) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (int64_t)M * M) return;
+  const int b = (int)(id / M), a = (int)(id - (int64_t)b * M);
+  const double dx = (double)min(a, M - a) / (double)m;
+  const double dy = (double)min(b, M - b) / (double)m;
+  const double dist = norm_r == 1 ? fabs(dx) + fabs(dy) : sqrt(dx * dx + dy * dy);
+  c[id] = Cplx<double>{sigma2 * exp(-dist / lam), 0.0};
+}
+
+// Full in-place FFT of each row of a rows x M array (global), one row per block.
+__global__ void fft_rows_full_kernel(Cplx<double>* data, int M, int logM, const Cplx<double>* tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cplx<double>* s = reinterpret_cast<Cplx<double>*>(smem_raw);
+  Cplx<double>* row = data + (int64_t)blockIdx.x * M;
+  for (int t = threadIdx.x; t < M; t += blockDim.x) s[brev_n(t, logM)] = row[t];
+  __syncthreads();
+  block_fft_rows(s, 1, M, logM, tw);
+  for (int t = threadIdx.x; t < M; t += blockDim.x) row[t] = s[t];
+}
+
+__global__ void transpose_kernel(const Cplx<double>* in, Cplx<double>* out, int M) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (int64_t)M * M) return;
+  const int r = (int)(id / M), c = (int)(id - (int64_t)r * M);
+  out[(int64_t)c * M + r] = in[id];
+}
+
+// Min and max of Re(data) over n entries, one block, fixed order.
+__global__ void minmax_kernel(const Cplx<double>* data, int64_t n, double* out2) {
+  __shared__ double smin[1024], smax[1024];
+  double lo = 1e300, hi = -1e300;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    lo = fmin(lo, data[i].x);
+    hi = fmax(hi, data[i].x);
+  }
+  smin[threadIdx.x] = lo;
+  smax[threadIdx.x] = hi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + o]);
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out2[0] = smin[0];
+    out2[1] = smax[0];
+  }
+}
+
+// s = sqrt(max(Lambda, 0)) / M in FP64 and FP32.
+__global__ void scale_kernel(const Cplx<double>* lam, double* s64, float* s32, int M) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (int64_t)M * M) return;
+  const double v = sqrt(fmax(lam[id].x, 0.0)) / (double)M;
+  s64[id] = v;
+  s32[id] = (float)v;
+}
+
+// ------------------------------------------------------------ pass 1 -------
+// Block (row block rb, pair f, sample s): rows q2 in [rb*R, rb*R + R) of the
+// M x M draw of field pair f, FFT along q1, keep a < m.
+// W layout: [sample][pair][q2][a] complex.
+template <typename R>
+__global__ void ce_rows_kernel(CeRowsArgs args, const R* __restrict__ scale,
+                               const Cplx<R>* __restrict__ tw, Cplx<R>* __restrict__ W) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cplx<R>* s = reinterpret_cast<Cplx<R>*>(smem_raw);
+  const int M = args.M, logM = args.logM, m = args.m, rows = args.rows_per_block;
+  const int rb = blockIdx.x, f = blockIdx.y;
+  const int64_t sidx = blockIdx.z + args.z_offset;
+  const uint64_t sample = (uint64_t)(args.first + sidx);
+  const int q2_0 = rb * rows;
+  const int halfM = M >> 1;
+  // one Philox call per pair of consecutive q1 (two complex normals)
+  const int ncalls = rows * halfM;
+  for (int t = threadIdx.x; t < ncalls; t += blockDim.x) {
+    const int r = t / halfM;
+    const int q1 = (t - r * halfM) << 1;
+    const int q2 = q2_0 + r;
+    const uint64_t call = ((uint64_t)q2 * (uint64_t)M + (uint64_t)q1) >> 1;
+    const Words4 w = philox4x64_10(call, sample, (uint64_t)args.level, kStreamField0 + f, args.seed);
+    R re0, im0, re1, im1;
+    box_muller(uniform52(w.w0), uniform52(w.w1), re0, im0);
+    box_muller(uniform52(w.w2), uniform52(w.w3), re1, im1);
+    const R s0 = scale[(int64_t)q2 * M + q1];
+    const R s1 = scale[(int64_t)q2 * M + q1 + 1];
+    s[r * M + brev_n(q1, logM)] = Cplx<R>{s0 * re0, s0 * im0};
+    s[r * M + brev_n(q1 + 1, logM)] = Cplx<R>{s1 * re1, s1 * im1};
+  }
+  __syncthreads();
+  block_fft_rows(s, rows, M, logM, tw);
+  Cplx<R>* out = W + ((sidx * args.n_pairs + f) * (int64_t)M + q2_0) * m;
+  for (int t = threadIdx.x; t < rows * m; t += blockDim.x) {
+    const int r = t / m, a = t - r * m;
+    out[(int64_t)r * m + a] = s[r * M + a];
+  }
+}
+
+// ------------------------------------------------------------ pass 2 -------
+// Block (column block cb, pair f, sample s): columns a in [cb*C, cb*C + C),
+// FFT along q2, keep b < m; g layout [sample][layer][b][a].
+template <typename R, typename G>
+__global__ void ce_cols_kernel(CeColsArgs args, const Cplx<R>* __restrict__ tw,
+                               const Cplx<R>* __restrict__ W, G* __restrict__ g) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cplx<R>* s = reinterpret_cast<Cplx<R>*>(smem_raw);
+  const int M = args.M, logM = args.logM, m = args.m, C = args.cols_per_block;
+  const int cb = blockIdx.x, f = blockIdx.y;
+  const int64_t sidx = blockIdx.z + args.z_offset;
+  const int a0 = cb * C;
+  const Cplx<R>* in = W + ((sidx * args.n_pairs + f) * (int64_t)M) * m + a0;
+  for (int t = threadIdx.x; t < M * C; t += blockDim.x) {
+    const int q2 = t / C, cc = t - q2 * C;
+    s[cc * M + brev_n(q2, logM)] = in[(int64_t)q2 * m + cc];
+  }
+  __syncthreads();
+  block_fft_rows(s, C, M, logM, tw);
+  const int t0 = 2 * f, t1 = 2 * f + 1;
+  const double mu0 = args.mu[t0];
+  const double mu1 = t1 < args.n_layers ? args.mu[t1] : 0.0;
+  G* g0 = g + ((sidx * args.n_layers + t0) * (int64_t)m) * m;
+  G* g1 = g + ((sidx * args.n_layers + t1) * (int64_t)m) * m;
+  for (int t = threadIdx.x; t < m * C; t += blockDim.x) {
+    const int b = t / C, cc = t - b * C;
+    const Cplx<R> v = s[cc * M + b];
+    g0[(int64_t)b * m + a0 + cc] = (G)(mu0 + (double)v.x);
+    if (t1 < args.n_layers) g1[(int64_t)b * m + a0 + cc] = (G)(mu1 + (double)v.y);
+  }
+}
+
+// ----------------------------------------------------------- host side ----
+int ce_build_table(int m, int M, double sigma2, double lam, int norm_r, void* scratch,
+                   double* s64, float* s32, double* minmax_dev, void* tw64, void* tw32,
+                   cudaStream_t st) {
+  const int logM = ilog2(M);
+  Cplx<double>* a = reinterpret_cast<Cplx<double>*>(scratch);
+  Cplx<double>* b = a + (int64_t)M * M;
+  const int64_t n = (int64_t)M * M;
+  const int nt = 256;
+  const unsigned nblk = (unsigned)((n + nt - 1) / nt);
+  twiddle_kernel<double><<<(M / 2 + nt - 1) / nt, nt, 0, st>>>((Cplx<double>*)tw64, M);
+  twiddle_kernel<float><<<(M / 2 + nt - 1) / nt, nt, 0, st>>>((Cplx<float>*)tw32, M);
+  covariance_kernel<<<nblk, nt, 0, st>>>(a, m, M, sigma2, lam, norm_r);
+  const size_t sm = (size_t)M * sizeof(Cplx<double>);
+  cudaFuncSetAttribute(fft_rows_full_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  fft_rows_full_kernel<<<M, 256, sm, st>>>(a, M, logM, (const Cplx<double>*)tw64);
+  transpose_kernel<<<nblk, nt, 0, st>>>(a, b, M);
+  fft_rows_full_kernel<<<M, 256, sm, st>>>(b, M, logM, (const Cplx<double>*)tw64);
+  transpose_kernel<<<nblk, nt, 0, st>>>(b, a, M);
+  minmax_kernel<<<1, 1024, 0, st>>>(a, n, minmax_dev);
+  scale_kernel<<<nblk, nt, 0, st>>>(a, s64, s32, M);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename R, typename G>
+static int ce_sample_impl(const CeLaunch& L, const R* scale, const void* tw, void* W, G* g,
+                          cudaStream_t st) {
+  const size_t esz = sizeof(Cplx<R>);
+  // rows / columns per block: at most 64 KB of FP64 (128 KB of FP32) per block
+  const int budget = (int)(65536 / sizeof(Cplx<double>)) * (int)(sizeof(Cplx<double>) / esz);
+  int rows = budget / L.M;
+  if (rows < 1) rows = 1;
+  if (rows > L.M) rows = L.M;
+  int cols = budget / L.M;
+  if (cols < 1) cols = 1;
+  if (cols > L.m) cols = L.m;
+  CeRowsArgs ra;
+  ra.M = L.M; ra.logM = ilog2(L.M); ra.m = L.m; ra.rows_per_block = rows; ra.n_pairs = L.n_pairs;
+  ra.level = L.level; ra.seed = L.seed; ra.first = L.first;
+  CeColsArgs ca;
+  ca.M = L.M; ca.logM = ra.logM; ca.m = L.m; ca.cols_per_block = cols; ca.n_pairs = L.n_pairs;
+  ca.n_layers = L.n_layers;
+  for (int t = 0; t < MAX_LAYERS_DEV; ++t) ca.mu[t] = L.mu[t];
+  const size_t sm_r = (size_t)rows * L.M * esz;
+  const size_t sm_c = (size_t)cols * L.M * esz;
+  cudaFuncSetAttribute(ce_rows_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_r);
+  cudaFuncSetAttribute(ce_cols_kernel<R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c);
+  // grid.z is limited to 65535: launch in slices of samples
+  for (int64_t z0 = 0; z0 < L.n_samples; z0 += 65535) {
+    const unsigned nz = (unsigned)((L.n_samples - z0) < 65535 ? (L.n_samples - z0) : 65535);
+    ra.z_offset = z0;
+    ca.z_offset = z0;
+    dim3 gr((unsigned)(L.M / rows), (unsigned)L.n_pairs, nz);
+    ce_rows_kernel<R><<<gr, 256, sm_r, st>>>(ra, scale, (const Cplx<R>*)tw, (Cplx<R>*)W);
+    dim3 gc((unsigned)(L.m / cols), (unsigned)L.n_pairs, nz);
+    ce_cols_kernel<R, G><<<gc, 256, sm_c, st>>>(ca, (const Cplx<R>*)tw, (const Cplx<R>*)W, g);
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int ce_sample_fp64(const CeLaunch& L, const double* scale, const void* tw, void* W, double* g,
+                   cudaStream_t st) {
+  return ce_sample_impl<double, double>(L, scale, tw, W, g, st);
+}
+
+int ce_sample_fp32(const CeLaunch& L, const float* scale, const void* tw, void* W, float* g,
+                   cudaStream_t st) {
+  return ce_sample_impl<float, float>(L, scale, tw, W, g, st);
+}
+
+size_t ce_w_bytes_per_sample(int m, int M, int n_pairs, bool fp32) {
+  return (size_t)n_pairs * M * m * (fp32 ? sizeof(Cplx<float>) : sizeof(Cplx<double>));
+}
+
+}  // namespace mlmc

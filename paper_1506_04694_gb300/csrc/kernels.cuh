@@ -1,0 +1,100 @@
+// Launch descriptors and host entry points of the kernels (internal header).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mlmc {
+
+constexpr int MAX_LAYERS_DEV = 8;
+
+// ------------------------------------------------------------------- CE ---
+struct CeRowsArgs {
+  int M, logM, m, rows_per_block, n_pairs, level;
+  uint64_t seed;
+  int64_t first;     // sample index of chunk entry 0
+  int64_t z_offset;  // chunk entry of blockIdx.z == 0
+};
+
+struct CeColsArgs {
+  int M, logM, m, cols_per_block, n_pairs, n_layers;
+  int64_t z_offset;
+  double mu[MAX_LAYERS_DEV];
+};
+
+struct CeLaunch {
+  int M, m, n_pairs, n_layers, level;
+  uint64_t seed;
+  int64_t first, n_samples;
+  double mu[MAX_LAYERS_DEV];
+};
+
+int ce_build_table(int m, int M, double sigma2, double lam, int norm_r, void* scratch,
+                   double* s64, float* s32, double* minmax_dev, void* tw64, void* tw32,
+                   cudaStream_t st);
+int ce_sample_fp64(const CeLaunch& L, const double* scale, const void* tw, void* W, double* g,
+                   cudaStream_t st);
+int ce_sample_fp32(const CeLaunch& L, const float* scale, const void* tw, void* W, float* g,
+                   cudaStream_t st);
+size_t ce_w_bytes_per_sample(int m, int M, int n_pairs, bool fp32);
+
+// ---------------------------------------------------------------- solve ---
+// Where the permeability of a system comes from.
+enum KSource : int {
+  KSRC_FIELDS = 0,   // g fields of the chunk + layer map from the interfaces
+  KSRC_CONST = 1,    // Ex. 1: per-layer constants exp(mu + sigma Z) + layer map
+  KSRC_ARRAY = 2,    // a caller-given k array per system (fine systems only)
+};
+
+struct SolveArgs {
+  // systems: fine systems [0, n_samples), then n_coarse per sample
+  int64_t n_samples;
+  int n_coarse;        // 0, 1 (plain, offset (0,0)) or 4 (CGV offsets)
+  int m;               // fine cells per side
+  int ksrc;
+  int cgv_on_k;        // coarse k = strided fine k (CGV mode 2)
+  int level;
+  uint64_t seed;
+  int64_t first;       // sample index of chunk entry 0
+  int n_layers;
+  double if_lo, if_hi;
+  double mu[MAX_LAYERS_DEV];
+  double sigma[MAX_LAYERS_DEV];
+  const void* g;       // fields [sample][layer][j][i] (double or float by precision)
+  const double* k;     // KSRC_ARRAY: [system][j][i]
+  double tol;
+  int max_it;
+  double inner_tol;    // mixed: relative tolerance of each FP32 inner solve
+  // workspace
+  int use_smem;
+  size_t ws_stride;    // bytes per block slot (global workspace)
+  unsigned char* ws;   // global workspace base (n_blocks * ws_stride)
+  // outputs per system
+  double* q;           // outflow Q (NaN when not converged)
+  int32_t* iters;      // CG iterations
+  double* p_out;       // optional pressure of fine systems [sample][j][i]
+};
+
+size_t solve_ws_bytes(int m, int prec);
+int solve_launch(const SolveArgs& a, int prec, int n_blocks, size_t smem_bytes, cudaStream_t st);
+int solve_blocks_per_sm(int m, int prec, size_t* smem_bytes, int* use_smem);
+
+// --------------------------------------------------------------- reduce ---
+struct LevelSumsDev {
+  double s[10];  // qf, qf2, qc, qc2, y, y2, qcg, qcg2, yg, yg2
+  long long n, n_failed, iters;
+};
+
+// Gather system Q's of a chunk into the per-sample outputs.
+int gather_launch(const double* q_sys, const int32_t* it_sys, int64_t n_samples, int n_coarse,
+                  int cgv, double* qf, double* qc, double* qcg, int32_t* iters, int64_t* it_acc,
+                  cudaStream_t st);
+int reduce_launch(const double* qf, const double* qc, const double* qcg, int64_t n, int cgv,
+                  const int64_t* it_acc, LevelSumsDev* out, cudaStream_t st);
+int philox_launch(uint64_t seed, uint64_t level, uint64_t sample, uint64_t stream,
+                  uint64_t first_call, int64_t n_calls, uint64_t* out, cudaStream_t st);
+int interfaces_launch(const SolveArgs& a, int64_t n, double* eta, cudaStream_t st);
+int const_fields_launch(const SolveArgs& a, int64_t n, double* g, cudaStream_t st);
+int f32_to_f64_launch(const float* in, double* out, int64_t n, cudaStream_t st);
+
+}  // namespace mlmc

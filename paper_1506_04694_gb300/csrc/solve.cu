@@ -1,0 +1,601 @@
+// Fused assembly + multigrid-preconditioned CG + outflow QoI, one thread
+// block per linear system (many systems per launch, grid-stride over systems).
+//
+// System of one sample (Sec. 3.1 Eq. 3.3 with harmonic faces, Sec. 3.4 Model
+// Problem 2): unknown p on m x m cells,
+//   sum_faces T_f (p_c - p_nbr) = b_c,  T = 2 k_a k_b / (k_a + k_b) inside,
+//   T = 2 k_c on the Dirichlet faces x1 = 0, 1 (p_nbr = 1 at x1 = 0, 0 at
+//   x1 = 1, moved into b), T = 0 on the no-flow faces x2 = 0, 1.
+// Solver (Sec. 3.5 uses CG preconditioned by one multigrid cycle, stopping at
+// ||r|| / ||r0|| < tol, x0 = 0): the multigrid here is geometric and
+// matrix-free: cell-centred 2x2 aggregation, coarse faces T_c = (T_a + T_b)/2
+// over the two fine faces that make up a coarse face (the rediscretisation of
+// a constant k), restriction = sum of the four fine residuals, prolongation =
+// piecewise constant, red-black Gauss-Seidel smoothing (red-black before the
+// coarse correction, black-red after it, so the cycle is symmetric), exact
+// solve on the 1 x 1 grid.
+//
+// prec 0: CG and multigrid in FP64.
+// prec 1: FP64 iterative refinement (solution, residual b - A x, stopping test
+//         and QoI in FP64) around an FP32 CG with FP32 multigrid; the face
+//         coefficients are rounded to FP32 once and the FP64 residual uses
+//         exactly those values.
+// Outflow QoI M^(2) (Sec. 3.4): Q = sum_j T(m, j) p(m-1, j).
+#include <cmath>
+#include <type_traits>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace mlmc {
+
+constexpr int kMaxLevels = 14;
+
+__host__ __device__ __forceinline__ size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+// Workspace layout for an m x m system; element size ts of the solver
+// precision; mixed adds FP64 x and r.  Returns total bytes; fills offsets
+// when `off` is non-null: off[0..1] x64, r64; then per level l 5 offsets
+// (tx, ty, invd, e, f) at 2 + 5 l; level-0 extra PCG vectors x, p, q at
+// 2 + 5*kMaxLevels + {0, 1, 2}.
+__host__ __device__ inline size_t ws_layout(int m, int ts, bool mixed, size_t* off) {
+  size_t o = 0;
+  const size_t n = (size_t)m * m;
+  auto take = [&](size_t bytes) {
+    const size_t r = o;
+    o += align16(bytes);
+    return r;
+  };
+  size_t x64 = 0, r64 = 0;
+  if (mixed) {
+    x64 = take(n * 8);
+    r64 = take(n * 8);
+  }
+  if (off) {
+    off[0] = x64;
+    off[1] = r64;
+  }
+  int ml = m, l = 0;
+  while (true) {
+    const size_t nl = (size_t)ml * ml;
+    const size_t nf = (size_t)ml * (ml + 1);
+    const size_t a0 = take(nf * ts), a1 = take(nf * ts), a2 = take(nl * ts), a3 = take(nl * ts),
+                 a4 = take(nl * ts);
+    if (off) {
+      off[2 + 5 * l + 0] = a0;
+      off[2 + 5 * l + 1] = a1;
+      off[2 + 5 * l + 2] = a2;
+      off[2 + 5 * l + 3] = a3;
+      off[2 + 5 * l + 4] = a4;
+    }
+    if (l == 0) {
+      const size_t b0 = take(nl * ts), b1 = take(nl * ts), b2 = take(nl * ts);
+      if (off) {
+        off[2 + 5 * kMaxLevels + 0] = b0;
+        off[2 + 5 * kMaxLevels + 1] = b1;
+        off[2 + 5 * kMaxLevels + 2] = b2;
+      }
+    }
+    if (ml == 1) break;
+    ml >>= 1;
+    ++l;
+  }
+  return o;
+}
+
+template <typename T>
+struct Level {
+  int m;
+  T* tx;    // m rows x (m+1) faces
+  T* ty;    // (m+1) face rows x m
+  T* invd;  // 1 / diagonal
+  T* e;     // correction (level 0: CG z)
+  T* f;     // right-hand side (level 0: CG r)
+};
+
+// (A v)_c = sum over the 4 faces of T (v_c - v_nbr), v_nbr = 0 outside.
+template <typename T>
+__device__ __forceinline__ T apply_row(const T* __restrict__ tx, const T* __restrict__ ty,
+                                       const T* __restrict__ v, int m, int i, int j) {
+  const int c = j * m + i;
+  const int rf = j * (m + 1) + i;
+  const T vc = v[c];
+  const T vw = i > 0 ? v[c - 1] : T(0);
+  const T ve = i < m - 1 ? v[c + 1] : T(0);
+  const T vs = j > 0 ? v[c - m] : T(0);
+  const T vn = j < m - 1 ? v[c + m] : T(0);
+  return (tx[rf] * (vc - vw) + tx[rf + 1] * (vc - ve)) + (ty[c] * (vc - vs) + ty[c + m] * (vc - vn));
+}
+
+// One red (color 0) or black (color 1) Gauss-Seidel half sweep; `zero_guess`
+// treats the other color as zero (first sweep of a cycle).
+template <typename T>
+__device__ __forceinline__ void rb_sweep(const Level<T>& L, int color, bool zero_guess) {
+  const int m = L.m, hm = m >> 1;
+  const int nh = m * hm;
+  for (int h = threadIdx.x; h < nh; h += blockDim.x) {
+    const int j = h / hm;
+    const int i = ((h - j * hm) << 1) + ((j + color) & 1);
+    const int c = j * m + i;
+    T s = L.f[c];
+    if (!zero_guess) {
+      const int rf = j * (m + 1) + i;
+      if (i > 0) s += L.tx[rf] * L.e[c - 1];
+      if (i < m - 1) s += L.tx[rf + 1] * L.e[c + 1];
+      if (j > 0) s += L.ty[c] * L.e[c - m];
+      if (j < m - 1) s += L.ty[c + m] * L.e[c + m];
+    }
+    L.e[c] = s * L.invd[c];
+  }
+  __syncthreads();
+}
+
+// Coarse f = sum of the four fine residuals f - A e of each 2x2 aggregate.
+template <typename T>
+__device__ __forceinline__ void restrict_residual(const Level<T>& F, const Level<T>& C) {
+  const int mc = C.m, m = F.m;
+  for (int cc = threadIdx.x; cc < mc * mc; cc += blockDim.x) {
+    const int J = cc / mc, I = cc - J * mc;
+    T acc = T(0);
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const int i = 2 * I + a, j = 2 * J + b;
+        acc += F.f[j * m + i] - apply_row(F.tx, F.ty, F.e, m, i, j);
+      }
+    C.f[cc] = acc;
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void prolong_add(const Level<T>& C, const Level<T>& F) {
+  const int m = F.m, mc = C.m;
+  for (int c = threadIdx.x; c < m * m; c += blockDim.x) {
+    const int j = c / m, i = c - j * m;
+    F.e[c] += C.e[(j >> 1) * mc + (i >> 1)];
+  }
+  __syncthreads();
+}
+
+// Coarse faces: mean of the two fine faces forming each coarse face.
+template <typename T>
+__device__ __forceinline__ void build_coarse(const Level<T>& F, const Level<T>& C) {
+  const int m = F.m, mc = C.m;
+  const int nfx = mc * (mc + 1);
+  for (int t = threadIdx.x; t < 2 * nfx; t += blockDim.x) {
+    if (t < nfx) {
+      const int J = t / (mc + 1), Ip = t - J * (mc + 1);
+      C.tx[t] = T(0.5) * (F.tx[(2 * J) * (m + 1) + 2 * Ip] + F.tx[(2 * J + 1) * (m + 1) + 2 * Ip]);
+    } else {
+      const int u = t - nfx;
+      const int Jp = u / mc, I = u - Jp * mc;
+      C.ty[u] = T(0.5) * (F.ty[(2 * Jp) * m + 2 * I] + F.ty[(2 * Jp) * m + 2 * I + 1]);
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void build_invd(const Level<T>& L) {
+  const int m = L.m;
+  for (int c = threadIdx.x; c < m * m; c += blockDim.x) {
+    const int j = c / m, i = c - j * m;
+    const int rf = j * (m + 1) + i;
+    L.invd[c] = T(1) / ((L.tx[rf] + L.tx[rf + 1]) + (L.ty[c] + L.ty[c + m]));
+  }
+  __syncthreads();
+}
+
+// Symmetric V-cycle: level-0 e <- B f.
+template <typename T>
+__device__ void vcycle(Level<T>* lev, int nl) {
+  for (int l = 0; l < nl - 1; ++l) {
+    rb_sweep(lev[l], 0, true);
+    rb_sweep(lev[l], 1, false);
+    restrict_residual(lev[l], lev[l + 1]);
+  }
+  {
+    const Level<T>& Lc = lev[nl - 1];  // 1 x 1
+    if (threadIdx.x == 0) Lc.e[0] = Lc.f[0] * Lc.invd[0];
+    __syncthreads();
+  }
+  for (int l = nl - 2; l >= 0; --l) {
+    prolong_add(lev[l + 1], lev[l]);
+    rb_sweep(lev[l], 1, false);
+    rb_sweep(lev[l], 0, false);
+  }
+}
+
+// Preconditioned CG on level-0 operator: x = 0 on entry, r = rhs.
+// Stops when r.r <= thr; returns iterations, status 0 converged, 1 hit the
+// cap, 2 breakdown (p.Ap <= 0 or not finite).
+template <typename T>
+__device__ int pcg(Level<T>* lev, int nl, T* x, T* p, T* q, T thr, int max_it, T* red, int& par,
+                   int& status) {
+  const Level<T>& L0 = lev[0];
+  const int m = L0.m, n = m * m;
+  T* r = L0.f;
+  T* z = L0.e;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) x[c] = T(0);
+  T rr = T(0);
+  for (int c = threadIdx.x; c < n; c += blockDim.x) rr += r[c] * r[c];
+  rr = block_sum(rr, red, par);
+  status = 1;
+  if (rr <= thr) {
+    status = 0;
+    return 0;
+  }
+  vcycle(lev, nl);
+  T rz = T(0);
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    p[c] = z[c];
+    rz += r[c] * z[c];
+  }
+  rz = block_sum(rz, red, par);
+  int it = 0;
+  while (it < max_it) {
+    ++it;
+    T pq = T(0);
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      const int j = c / m, i = c - j * m;
+      const T v = apply_row(L0.tx, L0.ty, p, m, i, j);
+      q[c] = v;
+      pq += p[c] * v;
+    }
+    pq = block_sum(pq, red, par);
+    if (!(pq > T(0)) || !isfinite(pq) || !isfinite(rz)) {
+      status = 2;
+      break;
+    }
+    const T alpha = rz / pq;
+    rr = T(0);
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      x[c] += alpha * p[c];
+      const T rv = r[c] - alpha * q[c];
+      r[c] = rv;
+      rr += rv * rv;
+    }
+    rr = block_sum(rr, red, par);
+    if (rr <= thr) {
+      status = 0;
+      break;
+    }
+    vcycle(lev, nl);
+    T rzn = T(0);
+    for (int c = threadIdx.x; c < n; c += blockDim.x) rzn += r[c] * z[c];
+    rzn = block_sum(rzn, red, par);
+    const T beta = rzn / rz;
+    rz = rzn;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) p[c] = z[c] + beta * p[c];
+    __syncthreads();
+  }
+  return it;
+}
+
+__device__ __forceinline__ int layer_at(const double* eta, int n_if, double y) {
+  int t = 0;
+  for (int s = 0; s < n_if; ++s) t += (eta[s] <= y) ? 1 : 0;
+  return t;
+}
+
+// Interfaces of one sample (sorted) and, for Ex. 1, the layer constants.
+__device__ void sample_layers(const SolveArgs& a, uint64_t sample, double* eta, double* kc) {
+  const int n_if = a.n_layers - 1;
+  const double width = __dadd_rn(a.if_hi, -a.if_lo);
+  for (int t = 0; t < n_if; ++t) {
+    const Words4 w = philox4x64_10((uint64_t)(t >> 2), sample, (uint64_t)a.level, kStreamInterface,
+                                   a.seed);
+    const uint64_t wt = (t & 3) == 0 ? w.w0 : (t & 3) == 1 ? w.w1 : (t & 3) == 2 ? w.w2 : w.w3;
+    eta[t] = __dadd_rn(a.if_lo, __dmul_rn(width, uniform52(wt)));
+  }
+  for (int t = 1; t < n_if; ++t) {  // insertion sort, ascending
+    const double v = eta[t];
+    int s = t - 1;
+    while (s >= 0 && eta[s] > v) {
+      eta[s + 1] = eta[s];
+      --s;
+    }
+    eta[s + 1] = v;
+  }
+  if (a.ksrc == KSRC_CONST) {
+    for (int t = 0; t < a.n_layers; t += 4) {
+      const Words4 w = philox4x64_10((uint64_t)(t >> 2), sample, (uint64_t)a.level, kStreamLayerZ,
+                                     a.seed);
+      double z[4];
+      box_muller(uniform52(w.w0), uniform52(w.w1), z[0], z[1]);
+      box_muller(uniform52(w.w2), uniform52(w.w3), z[2], z[3]);
+      for (int u = 0; u < 4 && t + u < a.n_layers; ++u)
+        kc[t + u] = exp(a.mu[t + u] + a.sigma[t + u] * z[u]);
+    }
+  }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(256) solve_kernel(SolveArgs a) {
+  using T = typename std::conditional<MIXED, float, double>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T red[132];
+  __shared__ double red64[132];
+  __shared__ double eta_s[MAX_LAYERS_DEV], kc_s[MAX_LAYERS_DEV];
+  unsigned char* base = a.use_smem ? smem_raw : a.ws + (size_t)blockIdx.x * a.ws_stride;
+  const int64_t n_sys = a.n_samples * (int64_t)(1 + a.n_coarse);
+  int par = 0;
+  for (int64_t sys = blockIdx.x; sys < n_sys; sys += gridDim.x) {
+    int64_t sidx;
+    int coarse = 0, ox = 0, oy = 0;
+    if (sys < a.n_samples) {
+      sidx = sys;
+    } else {
+      const int64_t t = sys - a.n_samples;
+      sidx = t / a.n_coarse;
+      const int o = (int)(t - sidx * a.n_coarse);
+      coarse = 1;
+      ox = o & 1;
+      oy = o >> 1;
+    }
+    const int m = coarse ? a.m >> 1 : a.m;
+    const int n = m * m;
+    const uint64_t sample = (uint64_t)(a.first + sidx);
+    size_t off[2 + 5 * kMaxLevels + 3];
+    ws_layout(m, sizeof(T), MIXED, off);
+    Level<T> lev[kMaxLevels];
+    int nl = 0;
+    for (int ml = m; ; ml >>= 1) {
+      Level<T>& L = lev[nl];
+      L.m = ml;
+      L.tx = reinterpret_cast<T*>(base + off[2 + 5 * nl + 0]);
+      L.ty = reinterpret_cast<T*>(base + off[2 + 5 * nl + 1]);
+      L.invd = reinterpret_cast<T*>(base + off[2 + 5 * nl + 2]);
+      L.e = reinterpret_cast<T*>(base + off[2 + 5 * nl + 3]);
+      L.f = reinterpret_cast<T*>(base + off[2 + 5 * nl + 4]);
+      ++nl;
+      if (ml == 1) break;
+    }
+    T* xv = reinterpret_cast<T*>(base + off[2 + 5 * kMaxLevels + 0]);
+    T* pv = reinterpret_cast<T*>(base + off[2 + 5 * kMaxLevels + 1]);
+    T* qv = reinterpret_cast<T*>(base + off[2 + 5 * kMaxLevels + 2]);
+    double* x64 = MIXED ? reinterpret_cast<double*>(base + off[0]) : reinterpret_cast<double*>(xv);
+    double* r64 = MIXED ? reinterpret_cast<double*>(base + off[1]) : reinterpret_cast<double*>(lev[0].f);
+
+    // ---- layers and per-cell permeability (into r64 as scratch) ----
+    if (a.ksrc != KSRC_ARRAY) {
+      if (threadIdx.x == 0) sample_layers(a, sample, eta_s, kc_s);
+      __syncthreads();
+    }
+    const int n_if = a.n_layers - 1;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      const int j = c / m, i = c - j * m;
+      double kk;
+      if (a.ksrc == KSRC_ARRAY) {
+        kk = a.k[sys * (int64_t)n + c];
+      } else {
+        // fine row of the value, and the row whose centre decides the layer
+        const int jf = coarse ? 2 * j + oy : j;
+        const int iff = coarse ? 2 * i + ox : i;
+        const double yc = (coarse && !a.cgv_on_k) ? ((double)j + 0.5) / (double)m
+                                                  : ((double)jf + 0.5) / (double)a.m;
+        const int t = layer_at(eta_s, n_if, yc);
+        if (a.ksrc == KSRC_CONST) {
+          kk = kc_s[t];
+        } else if (MIXED) {
+          const float* g = reinterpret_cast<const float*>(a.g);
+          kk = (double)expf(g[((sidx * a.n_layers + t) * (int64_t)a.m + jf) * a.m + iff]);
+        } else {
+          const double* g = reinterpret_cast<const double*>(a.g);
+          kk = exp(g[((sidx * a.n_layers + t) * (int64_t)a.m + jf) * a.m + iff]);
+        }
+      }
+      r64[c] = kk;
+    }
+    __syncthreads();
+    // ---- faces (Eq. 3.3, harmonic averages; Dirichlet 2k; no-flow 0) ----
+    {
+      const Level<T>& L = lev[0];
+      const int nfx = m * (m + 1);
+      for (int t = threadIdx.x; t < 2 * nfx; t += blockDim.x) {
+        if (t < nfx) {
+          const int j = t / (m + 1), ip = t - j * (m + 1);
+          T v;
+          if (ip == 0) v = T(2) * (T)r64[j * m];
+          else if (ip == m) v = T(2) * (T)r64[j * m + m - 1];
+          else {
+            const T ka = (T)r64[j * m + ip - 1], kb = (T)r64[j * m + ip];
+            v = T(2) * ka * kb / (ka + kb);
+          }
+          L.tx[t] = v;
+        } else {
+          const int u = t - nfx;
+          const int jp = u / m, i = u - jp * m;
+          T v = T(0);
+          if (jp > 0 && jp < m) {
+            const T ka = (T)r64[(jp - 1) * m + i], kb = (T)r64[jp * m + i];
+            v = T(2) * ka * kb / (ka + kb);
+          }
+          L.ty[u] = v;
+        }
+      }
+      __syncthreads();
+      build_invd(L);
+    }
+    for (int l = 1; l < nl; ++l) {
+      build_coarse(lev[l - 1], lev[l]);
+      build_invd(lev[l]);
+    }
+    // ---- solve ----
+    int status = 1, iters = 0;
+    const Level<T>& L0 = lev[0];
+    if (!MIXED) {
+      // r = b, bb = b.b; stop at r.r <= tol^2 b.b
+      T bb = T(0);
+      for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        const int j = c / m, i = c - j * m;
+        const T bv = i == 0 ? L0.tx[j * (m + 1)] : T(0);
+        L0.f[c] = bv;
+        bb += bv * bv;
+      }
+      bb = block_sum(bb, red, par);
+      iters = pcg(lev, nl, xv, pv, qv, (T)(a.tol * a.tol) * bb, a.max_it, red, par, status);
+    } else {
+      // FP64 refinement: r64 = b - A64 x64 with A64 = the FP32 faces in FP64.
+      double bb = 0.0;
+      for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        const int j = c / m, i = c - j * m;
+        const double bv = i == 0 ? (double)L0.tx[j * (m + 1)] : 0.0;
+        x64[c] = 0.0;
+        r64[c] = bv;
+        bb += bv * bv;
+      }
+      bb = block_sum(bb, red64, par);
+      double rr = bb;
+      const double thr = a.tol * a.tol * bb;
+      int sweeps = 0;
+      while (true) {
+        if (rr <= thr) {
+          status = 0;
+          break;
+        }
+        if (iters >= a.max_it || sweeps >= 40) {
+          status = 1;
+          break;
+        }
+        ++sweeps;
+        const double scl = sqrt(rr);
+        const double inv = 1.0 / scl;
+        T r32 = T(0);
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+          const T v = (T)(r64[c] * inv);
+          L0.f[c] = v;
+          r32 += v * v;
+        }
+        r32 = block_sum(r32, red, par);
+        int st_in = 1;
+        const T thr_in = (T)(a.inner_tol * a.inner_tol) * r32;
+        const int it = pcg(lev, nl, xv, pv, qv, thr_in, a.max_it - iters, red, par, st_in);
+        iters += it;
+        // x64 += scl * d, then r64 = b - A64 x64 (FP64)
+        for (int c = threadIdx.x; c < n; c += blockDim.x) x64[c] += scl * (double)xv[c];
+        __syncthreads();
+        rr = 0.0;
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+          const int j = c / m, i = c - j * m;
+          const int rf = j * (m + 1) + i;
+          const double vc = x64[c];
+          const double vw = i > 0 ? x64[c - 1] : 0.0;
+          const double ve = i < m - 1 ? x64[c + 1] : 0.0;
+          const double vs = j > 0 ? x64[c - m] : 0.0;
+          const double vn = j < m - 1 ? x64[c + m] : 0.0;
+          const double ax = ((double)L0.tx[rf] * (vc - vw) + (double)L0.tx[rf + 1] * (vc - ve)) +
+                            ((double)L0.ty[c] * (vc - vs) + (double)L0.ty[c + m] * (vc - vn));
+          const double bv = i == 0 ? (double)L0.tx[rf] : 0.0;
+          const double rv = bv - ax;
+          r64[c] = rv;
+          rr += rv * rv;
+        }
+        rr = block_sum(rr, red64, par);
+        if (it == 0 && st_in != 0) {  // inner solver made no progress
+          status = 2;
+          break;
+        }
+      }
+    }
+    // ---- outflow QoI and outputs ----
+    double qsum = 0.0;
+    for (int j = threadIdx.x; j < m; j += blockDim.x)
+      qsum += (double)L0.tx[j * (m + 1) + m] * x64[j * m + m - 1];
+    qsum = block_sum(qsum, red64, par);
+    if (threadIdx.x == 0) {
+      a.q[sys] = status == 0 ? qsum : nan("");
+      if (a.iters) a.iters[sys] = iters;
+    }
+    if (a.p_out && !coarse)
+      for (int c = threadIdx.x; c < n; c += blockDim.x) a.p_out[sidx * (int64_t)n + c] = x64[c];
+    __syncthreads();
+  }
+}
+
+size_t solve_ws_bytes(int m, int prec) {
+  return ws_layout(m, prec ? 4 : 8, prec != 0, nullptr);
+}
+
+static const size_t kSmemCap = 110 * 1024;
+
+int solve_blocks_per_sm(int m, int prec, size_t* smem_bytes, int* use_smem) {
+  const size_t ws = solve_ws_bytes(m, prec);
+  *use_smem = ws <= kSmemCap;
+  *smem_bytes = *use_smem ? ws : 0;
+  int nb = 0;
+  cudaError_t e;
+  if (prec) {
+    cudaFuncSetAttribute(solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<true>, 256, *smem_bytes);
+  } else {
+    cudaFuncSetAttribute(solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<false>, 256, *smem_bytes);
+  }
+  if (e != cudaSuccess) return -1;
+  return nb < 1 ? 1 : nb;
+}
+
+int solve_launch(const SolveArgs& a, int prec, int n_blocks, size_t smem_bytes, cudaStream_t st) {
+  if (prec)
+    solve_kernel<true><<<n_blocks, 256, smem_bytes, st>>>(a);
+  else
+    solve_kernel<false><<<n_blocks, 256, smem_bytes, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace mlmc
+
+namespace mlmc {
+
+// Sorted interfaces of each sample (stage output for parity checks).
+__global__ void interfaces_kernel(SolveArgs a, int64_t n, double* eta) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  double e[MAX_LAYERS_DEV], kc[MAX_LAYERS_DEV];
+  SolveArgs b = a;
+  b.ksrc = KSRC_FIELDS;  // interfaces only
+  sample_layers(b, (uint64_t)(a.first + s), e, kc);
+  for (int t = 0; t < a.n_layers - 1; ++t) eta[s * (a.n_layers - 1) + t] = e[t];
+}
+
+int interfaces_launch(const SolveArgs& a, int64_t n, double* eta, cudaStream_t st) {
+  if (n <= 0 || a.n_layers < 2) return 0;
+  interfaces_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a, n, eta);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// Ex. 1 fields: g_t = mu_t + sigma_t Z_t on every cell (stage output).
+__global__ void const_fields_kernel(SolveArgs a, int64_t n, double* g) {
+  const int64_t s = blockIdx.x;
+  if (s >= n) return;
+  __shared__ double e[MAX_LAYERS_DEV], kc[MAX_LAYERS_DEV], gz[MAX_LAYERS_DEV];
+  if (threadIdx.x == 0) {
+    const uint64_t sample = (uint64_t)(a.first + s);
+    SolveArgs b = a;
+    b.ksrc = KSRC_FIELDS;
+    sample_layers(b, sample, e, kc);
+    for (int t = 0; t < a.n_layers; t += 4) {
+      const Words4 w = philox4x64_10((uint64_t)(t >> 2), sample, (uint64_t)a.level, kStreamLayerZ,
+                                     a.seed);
+      double z[4];
+      box_muller(uniform52(w.w0), uniform52(w.w1), z[0], z[1]);
+      box_muller(uniform52(w.w2), uniform52(w.w3), z[2], z[3]);
+      for (int u = 0; u < 4 && t + u < a.n_layers; ++u) gz[t + u] = a.mu[t + u] + a.sigma[t + u] * z[u];
+    }
+  }
+  __syncthreads();
+  const int64_t mm = (int64_t)a.m * a.m;
+  for (int64_t c = threadIdx.x; c < mm * a.n_layers; c += blockDim.x)
+    g[s * mm * a.n_layers + c] = gz[c / mm];
+}
+
+int const_fields_launch(const SolveArgs& a, int64_t n, double* g, cudaStream_t st) {
+  if (n <= 0) return 0;
+  const_fields_kernel<<<(unsigned)n, 256, 0, st>>>(a, n, g);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace mlmc

@@ -1,0 +1,122 @@
+"""GPU parity of the individual stages against the oracle, through the C ABI:
+Philox words and interfaces bit-exact, fields (Ex. 1 constants, Ex. 2
+circulant embedding), and the linear solve + outflow QoI on given k."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import darcy, philox
+from tests.gpu_util import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("seed,level,sample,stream,first,n", [
+    (0, 0, 0, 0, 0, 3), (12345, 3, 77, 2, 1000, 257), (2**63 + 5, 11, 2**40, 9, 2**33, 64)])
+def test_philox_words_bit_exact(seed, level, sample, stream, first, n):
+    torch, pk = need_gpu()
+    w = pk.philox_words(seed, level, sample, stream, first, n).cpu().numpy().view(np.uint64)
+    ref = philox.stream_words(seed, level, sample, stream, np.arange(first, first + n, dtype=np.uint64))
+    assert np.array_equal(w, ref)
+
+
+@pytest.mark.parametrize("name", ["const_2layer_8to32", "lognormal_4layer_cgv_16to1024"])
+def test_interfaces_bit_exact(name):
+    torch, pk = need_gpu()
+    d = workloads.workload(name, L=1)
+    model = darcy.Model.from_dict(d)
+    with pk.Context(d) as ctx:
+        for level in (0, 1):
+            g, eta = ctx.sample_fields(level, 37, seed=9, first=5)
+            eta = eta.cpu().numpy()
+            for s in range(37):
+                ref = darcy.interfaces(model, 9, level, 5 + s)
+                assert np.array_equal(eta[s], ref)
+
+
+def test_const_fields():
+    torch, pk = need_gpu()
+    d = workloads.workload("const_2layer_8to32", mu=[0.3, -0.2], sigma2=[1.5, 0.5])
+    model = darcy.Model.from_dict(d)
+    with pk.Context(d) as ctx:
+        g, _ = ctx.sample_fields(1, 20, seed=4)
+        g = g.cpu().numpy()
+    for s in range(20):
+        ref = darcy.layer_fields(model, 4, 1, s, 16)
+        np.testing.assert_allclose(g[s], ref, rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("name,levels", [("lognormal_2layer_16to256", (0, 1, 2)),
+                                         ("lognormal_4layer_cgv_16to1024", (0, 1))])
+def test_ce_fields_fp64(name, levels):
+    torch, pk = need_gpu()
+    d = workloads.workload(name, prec=0)
+    model = darcy.Model.from_dict(d)
+    cache = {}
+    with pk.Context(d) as ctx:
+        for level in levels:
+            m = model.m(level)
+            M, lo, hi = ctx.ce_info(level)
+            Mo, _ = darcy.ce_padding(m, model.sigma2[0], model.lam[0], model.norm_r)
+            assert M == Mo
+            n = 6
+            g, _ = ctx.sample_fields(level, n, seed=3, first=11)
+            g = g.cpu().numpy()
+            for s in range(n):
+                ref = darcy.layer_fields(model, 3, level, 11 + s, m, cache)
+                np.testing.assert_allclose(g[s], ref, rtol=0, atol=1e-12)
+
+
+def test_ce_fields_fp32_error_bound():
+    torch, pk = need_gpu()
+    d = workloads.workload("lognormal_2layer_cgv_16to512", L=2)
+    model = darcy.Model.from_dict(d)
+    with pk.Context(d) as ctx:
+        g, _ = ctx.sample_fields(2, 4, seed=1)
+        g = g.cpu().numpy()
+    for s in range(4):
+        ref = darcy.layer_fields(model, 1, 2, s, 64)
+        assert np.max(np.abs(g[s] - ref)) < 2e-5
+
+
+@pytest.mark.parametrize("m", [1, 2, 4, 8, 16, 32, 64, 128])
+def test_solve_k_fp64(m):
+    torch, pk = need_gpu()
+    n = 12 if m <= 32 else 4
+    k = workloads.random_k(m, seed=m, n=n, contrast=4.0)
+    d = workloads.workload("const_2layer_8to32", tol=1e-13, max_it=500)
+    with pk.Context(d) as ctx:
+        p, q, it = ctx.solve_k(torch.from_numpy(k).cuda())
+        p, q, it = p.cpu().numpy(), q.cpu().numpy(), it.cpu().numpy()
+    for s in range(n):
+        p_ref, q_ref = darcy.solve_k(k[s])
+        assert abs(q[s] - q_ref) <= 1e-10 * abs(q_ref), (s, q[s], q_ref, it[s])
+        assert np.max(np.abs(p[s] - p_ref)) < 1e-9
+    assert it.max() < 100
+
+
+@pytest.mark.parametrize("m", [16, 64, 256])
+def test_solve_k_mixed(m):
+    torch, pk = need_gpu()
+    n = 6
+    k = workloads.random_k(m, seed=100 + m, n=n, contrast=4.0)
+    d = workloads.workload("const_2layer_8to32", tol=1e-12, max_it=1000, prec=1)
+    with pk.Context(d) as ctx:
+        _, q, it = ctx.solve_k(torch.from_numpy(k).cuda(), want_p=False)
+        q = q.cpu().numpy()
+    for s in range(n):
+        _, q_ref = darcy.solve_k(k[s])
+        assert abs(q[s] - q_ref) <= 1e-6 * abs(q_ref), (s, q[s], q_ref)
+
+
+def test_constant_k_closed_form_gpu():
+    torch, pk = need_gpu()
+    for m in (1, 2, 8, 64, 512):
+        k = np.full((1, m, m), 2.5)
+        with pk.Context(workloads.workload("const_2layer_8to32", tol=1e-13)) as ctx:
+            p, q, _ = ctx.solve_k(torch.from_numpy(k).cuda())
+        assert abs(q.item() - 2.5) < 1e-10 * 2.5
+        x = (np.arange(m) + 0.5) / m
+        assert np.max(np.abs(p.cpu().numpy()[0] - (1 - x)[None, :])) < 1e-9
