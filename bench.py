@@ -1,0 +1,346 @@
+#!/usr/bin/env python
+"""Benchmark of the MLMC level batch on GB300.
+
+One step = one complete adaptive MLMC estimate to RMSE eps (pilot batches on
+every level, then top-ups to the cost-optimal N_l until the sampling error is
+<= eps^2/2), i.e. one pass of every stage of the hot path: Philox normals,
+circulant-embedding fields, TPFA assembly, multigrid-preconditioned CG, the
+outflow QoI, the level reduction and the estimator.  Default workload: two
+layers, piecewise log-normal fields (sigma^2 = 1, lambda = 0.3, 2-norm),
+levels m = 16 .. 256, eps = 1e-3, FP64.
+
+value = level samples solved per second (sum_l N_l over all ranks / time);
+ms_per_step = the time-to-eps of one estimate.
+
+--impl reference times the CPU FP64 oracle on the host cores on a bounded
+sample of the same workload and prints the same line with "impl": "reference".
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "lognormal_2layer_16to256"
+# Algorithmic FP64 flops of one CG iteration per fine cell of the FP64 solver:
+# operator apply 11 + p.q 2; x, r updates and r.r 6; symmetric V(1,1) cycle
+# ~29.5 per finest cell (half-sweep zero-guess 0.5, black sweep 5, fused
+# residual + restriction 13, prolongation 1, two post half-sweeps 10) times
+# 4/3 for the coarser grids; r.z 2; p update 2.
+FLOPS_PER_CELL_ITER = 13 + 6 + 29.5 * 4.0 / 3.0 + 4
+# FP64 vector peak of GB300 (nominal 1.25 TFLOP/s: 152 SMs x 2 FP64 FMA/clk x
+# 2 flop x ~2.06 GHz).
+FP64_PEAK_TFLOPS = 1.25
+# Sample of the oracle timed for the CPU baseline: samples per level.
+CPU_SAMPLE = {0: 512, 1: 128, 2: 48, 3: 16, 4: 8, 5: 2, 6: 1}
+
+
+def _worker_init():
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+
+
+def _oracle_worker(job):
+    """Runs in a spawned process: oracle samples of one level; returns
+    (level, seconds, per-sample (qf, qc, qc_cgv))."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import workloads
+    from oracle import darcy
+    name, overrides, level, first, n, seed = job
+    model = darcy.Model.from_dict(workloads.workload(name, **overrides))
+    cache = {}
+    darcy.layer_fields(model, seed, level, first, model.m(level), cache)  # embedding table
+    t = time.perf_counter()
+    out = []
+    for i in range(first, first + n):
+        r = darcy.sample(model, seed, level, i, cache)
+        out.append((r["qf"], r["qc"], r["qc_cgv"]))
+    return level, time.perf_counter() - t, out
+
+
+def oracle_rates(name, overrides, levels, seed, cores):
+    """Per-level oracle throughput (samples/s) on `cores` spawned processes,
+    plus the per-sample results."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    jobs = []
+    for lvl in levels:
+        n = CPU_SAMPLE.get(lvl, 1)
+        per = max(1, n // cores)
+        for c0 in range(0, n, per):
+            jobs.append((name, overrides, lvl, 10_000_000 + c0, min(per, n - c0), seed))
+    rates, results = {}, {}
+    with ctx.Pool(cores, initializer=_worker_init) as pool:
+        for lvl in levels:
+            lj = [j for j in jobs if j[2] == lvl]
+            t = time.perf_counter()
+            res = pool.map(_oracle_worker, lj)
+            wall = time.perf_counter() - t
+            n = sum(j[4] for j in lj)
+            rates[lvl] = n / wall
+            results[lvl] = [x for r in res for x in r[2]]
+    return rates, results
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 10:
+                rows.append(p)
+        if not rows:
+            return None
+        try:
+            busy = [r for r in rows if float(r[4]) >= 50] or rows
+            sm = sorted(float(r[1]) for r in busy)
+            reasons = set()
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for r in busy:
+                for k, name in enumerate(names):
+                    if r[6 + k].lower() == "active":
+                        reasons.add(name)
+            return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": float(busy[0][2]), "reasons": sorted(reasons),
+                    "samples": len(busy)}
+        except ValueError:
+            return None
+
+
+def run_reference(args, d):
+    """The CPU oracle on the host cores, bounded sample; same metric and unit."""
+    cores = min(host_cores(), 16)
+    L = d["L"]
+    levels = list(range(L + 1))
+    times, values = [], []
+    from oracle import mlmc
+    import numpy as np
+    for step in range(args.warmup + args.steps):
+        rates, results = oracle_rates(args.workload, {}, levels, args.seed, cores)
+        # sample sizes from the oracle's own pilot variances (deterministic cost model)
+        V = []
+        for lvl in levels:
+            arr = np.array(results[lvl])
+            y = arr[:, 0] - (arr[:, 2] if (d["cgv"] and lvl) else arr[:, 1])
+            V.append(float(np.var(y, ddof=1)) if len(y) > 1 else float(np.var(arr[:, 0])))
+        from oracle import darcy
+        model = darcy.Model.from_dict(d)
+        C = [mlmc.parity_cost(model, lvl) for lvl in levels]
+        N = mlmc.optimal_samples(d["eps"], V, C)
+        t_eps = sum(n / rates[lvl] for lvl, n in zip(levels, N))
+        if step >= args.warmup:
+            times.append(t_eps)
+            values.append(sum(N) / t_eps)
+    value = sum(values) / len(values)
+    ms = 1000 * sum(times) / len(times)
+    sample = ("oracle (numpy/scipy FP64, banded Cholesky) on %d spawned processes; per step %s samples "
+              "of levels %s timed, time-to-eps extrapolated as sum_l N_l / rate_l with N_l from the "
+              "oracle's pilot variances" % (cores, [CPU_SAMPLE.get(lv, 1) for lv in levels], levels))
+    return {"impl": "reference", "metric": metric_name(d, args), "value": value, "unit": "level-samples/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (Philox4x64-10 streams)", "config": config_block(args, d),
+            "cpu_baseline": {"value": value, "unit": "level-samples/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "level-samples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def metric_name(d, args):
+    return ("level solves/s: MLMC time-to-RMSE eps=%g, %d-layer piecewise log-normal, m=%d..%d, %s%s"
+            % (d["eps"], d["n_layers"], d["m0"], d["m0"] << d["L"], "FP64" if d["prec"] == 0 else "mixed FP32-MG",
+               ", CGV" if d["cgv"] else ""))
+
+
+def config_block(args, d):
+    return {"workload": args.workload, "m_levels": [d["m0"] << l for l in range(d["L"] + 1)],
+            "eps": d["eps"], "sigma2": d["sigma2"][0], "lambda": d["lam"][0], "layers": d["n_layers"],
+            "cgv": d["cgv"], "prec": "fp64" if d["prec"] == 0 else "fp32-mg/fp64-refinement",
+            "solver_tol": d["tol"], "seed": args.seed, "cost_model": "deterministic m_l^2 (1 + n_coarse/4)",
+            "l2": "flushed between steps (256 MB device write)", "parallelism": "replicas%d" % args.gpus}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    import workloads
+    d = workloads.workload(args.workload)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, d)), flush=True)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import paper_1506_04694_gb300 as pk
+
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = pk.Context(d, device=local, stream=stream)
+    eps = d["eps"]
+    seed = args.seed + 7919 * rank
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        ctx.estimate(eps, seed, n_pilot=64, cost_model=0)
+    torch.cuda.synchronize(dev)
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    phys = vis.split(",")[local] if vis else str(local)
+    clocks = ClockSampler(phys)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize(dev)
+    ctx.profile(True)
+    step_ms, n_total, est = [], 0, None
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        est = ctx.estimate(eps, seed, n_pilot=64, cost_model=0)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        n_total += sum(est["N"])
+    torch.cuda.synchronize(dev)
+    barrier()
+    ctx.profile(False)
+    clk = clocks.stop()
+    prof = ctx.profile_read()
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms, float(n_total)], dtype=torch.float64, device=dev)
+    if world > 1:
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        total_ms, n_all = float(tmax[0]), float(t[1])
+    else:
+        n_all = float(n_total)
+
+    # end to end through the host-buffer API: the estimate's per-level sample
+    # counts run with per-sample results copied back to host memory
+    e2e = None
+    if rank == 0:
+        N = est["N"]
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for lvl, n in enumerate(N):
+            ctx.level_batch_host(lvl, n, seed, first=0)
+        torch.cuda.synchronize(dev)
+        te = time.perf_counter() - t0
+        e2e = {"value": sum(N) / te, "unit": "level-samples/s", "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": int(sum(N) * (3 * 8 + 4) + (d["L"] + 1) * 128),
+               "note": "inputs are (seed, model) passed by value; per-sample Q_f, Q_c, Q_cgv and "
+                       "iterations copied to host inside the timed region"}
+
+    if rank != 0:
+        return
+    stage_ms = prof["ms"]
+    dom = max(stage_ms, key=lambda k: stage_ms[k])
+    launches = int(sum(prof["launches"].values()))
+    roof = None
+    if dom == "solve" and d["prec"] == 0:
+        flops = FLOPS_PER_CELL_ITER * prof["cell_iters"]
+        ach = flops / (stage_ms["solve"] / 1e3) / 1e12
+        roof = {"kernel": "solve_kernel<false> (assembly + MG-PCG + QoI, FP64)", "bound": "alu",
+                "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": None, "peak_source": "nominal FP64 vector rate (152 SMs x 2 DFMA/clk x 2.06 GHz)"}
+    elif dom == "fields" and d["prec"] == 0:
+        # radix-2 FFT: 5 N log2 N flops per length-N transform
+        pts_r, pts_c = prof["fft_row_points"], prof["fft_col_points"]
+        M = ctx.ce_info(d["L"])[0]
+        lg = math.log2(M)
+        flops = 5 * (pts_r + pts_c) * lg
+        ach = flops / (stage_ms["fields"] / 1e3) / 1e12
+        roof = {"kernel": "ce_rows/ce_cols (Philox + Box-Muller + FFT, FP64)", "bound": "alu", "achieved": ach,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None}
+    out = {
+        "metric": metric_name(d, args), "value": n_all / (total_ms / 1e3), "unit": "level-samples/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if d["prec"] == 0 else "f32+f64", "data": "synthetic (Philox4x64-10 streams)",
+        "config": config_block(args, d), "roofline": roof, "e2e": e2e, "gpu_launches": launches // 1,
+        "clocks": clk, "time_to_eps_s": total_ms / args.steps / 1e3, "N_per_level": est["N"],
+        "q_hat": est["q_hat"], "var_hat": est["var_hat"],
+        "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
+        "iters_per_cell_solve": prof["cell_iters"] / max(prof["cells"], 1.0),
+    }
+    if not args.no_cpu_baseline:
+        cores = min(host_cores(), 16)
+        rates, _ = oracle_rates(args.workload, {}, list(range(d["L"] + 1)), args.seed, cores)
+        N = est["N"]
+        t_cpu = sum(n / rates[lvl] for lvl, n in enumerate(N))
+        out["cpu_baseline"] = {
+            "value": sum(N) / t_cpu, "unit": "level-samples/s", "cores": cores, "kind": "oracle",
+            "sample": "oracle on %d spawned processes, %s samples of levels 0..%d timed; time-to-eps "
+                      "extrapolated with the GPU run's N_l (%.1f s)" % (
+                          cores, [CPU_SAMPLE.get(lv, 1) for lv in range(d["L"] + 1)], d["L"], t_cpu)}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -180,6 +180,25 @@ MLMC_API int mlmc_sample_fields(mlmc_ctx* ctx, int level, int64_t first, int64_t
 MLMC_API int mlmc_solve_k(mlmc_ctx* ctx, int32_t m, int64_t n, const double* k, double* p, double* q,
                  int32_t* iters);
 
+/* Per-stage device timing of a context, collected with CUDA events on the
+ * context's stream while enabled (used by the benchmark for the roofline). */
+typedef struct mlmc_profile_stats {
+  int64_t launches[3];     /* kernel launches: 0 field kernels (both FFT passes),
+                              1 fused assembly + solve + QoI, 2 gather + level reduction */
+  double ms[3];            /* summed event time of each stage */
+  double cell_iters;       /* sum over all solves of (cells x CG iterations) */
+  double cells;            /* sum over all solves of cells */
+  double fft_row_points;   /* sum of M*M complex points transformed by the row pass */
+  double fft_col_points;   /* sum of m*M complex points transformed by the column pass */
+  double samples;          /* samples processed */
+} mlmc_profile_stats;
+
+/* enable != 0: reset the counters and start collecting; 0: stop. */
+MLMC_API int mlmc_profile(mlmc_ctx* ctx, int enable);
+
+/* Copy the counters collected so far (host pointer, required). */
+MLMC_API int mlmc_profile_read(mlmc_ctx* ctx, mlmc_profile_stats* out);
+
 /* Human-readable text of an error code (static storage). */
 MLMC_API const char* mlmc_error_string(int code);
 

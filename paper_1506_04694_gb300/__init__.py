@@ -53,6 +53,16 @@ class EstimateOut(ctypes.Structure):
     ]
 
 
+class ProfileStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 3), ("ms", ctypes.c_double * 3),
+                ("cell_iters", ctypes.c_double), ("cells", ctypes.c_double),
+                ("fft_row_points", ctypes.c_double), ("fft_col_points", ctypes.c_double),
+                ("samples", ctypes.c_double)]
+
+
+STAGES = ("fields", "solve", "reduce")
+
+
 class MLMCError(RuntimeError):
     pass
 
@@ -79,6 +89,8 @@ EXPORTS = {
                                           ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
     "mlmc_solve_k": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "mlmc_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "mlmc_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ProfileStats)]),
     "mlmc_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mlmc_last_error": (ctypes.c_char_p, []),
 }
@@ -213,6 +225,18 @@ class Context:
         return {"q_hat": out.q_hat, "var_hat": out.var_hat, "N": list(out.N[:L]), "V": list(out.V[:L]),
                 "mean": list(out.mean[:L]), "C": list(out.C[:L]), "rounds": out.rounds,
                 "seconds": out.seconds, "sums": [out.sums[i].as_dict() for i in range(L)], "rc": rc}
+
+    def profile(self, enable=True):
+        """mlmc_profile: reset and start (or stop) per-stage event timing."""
+        _check(lib().mlmc_profile(self._h, 1 if enable else 0), allow_failed=False)
+
+    def profile_read(self):
+        """mlmc_profile_read: per-stage launches and milliseconds plus work counters."""
+        p = ProfileStats()
+        _check(lib().mlmc_profile_read(self._h, ctypes.byref(p)), allow_failed=False)
+        return {"launches": dict(zip(STAGES, p.launches)), "ms": dict(zip(STAGES, p.ms)),
+                "cell_iters": p.cell_iters, "cells": p.cells, "fft_row_points": p.fft_row_points,
+                "fft_col_points": p.fft_col_points, "samples": p.samples}
 
     def ce_info(self, level):
         M = ctypes.c_int32()

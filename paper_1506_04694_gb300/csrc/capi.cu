@@ -77,6 +77,8 @@ struct mlmc_ctx {
   int nsm = 0;
   std::vector<LevelTable> lev;
   Buf W, g, ws, qsys, itsys, oqf, oqc, oqg, oit, sums, itacc, g64;
+  bool prof_on = false;
+  mlmc_profile_stats prof{};
 };
 
 namespace {
@@ -195,6 +197,44 @@ int run_solves(mlmc_ctx* c, SolveArgs a, int64_t n_samples, int nc, int64_t max_
   return 0;
 }
 
+// CUDA-event timing of one stage on the context stream (profiling only).
+struct StageTimer {
+  mlmc_ctx* c;
+  int stage;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  StageTimer(mlmc_ctx* c_, int stage_) : c(c_), stage(stage_) {
+    if (!c->prof_on) return;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, c->st);
+  }
+  void stop(int launches) {
+    if (!c->prof_on) return;
+    cudaEventRecord(e1, c->st);
+    c->prof.launches[stage] += launches;
+    pending().push_back({stage, e0, e1});
+    e0 = e1 = nullptr;
+  }
+  struct Pend {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  static std::vector<Pend>& pending() {
+    static thread_local std::vector<Pend> v;
+    return v;
+  }
+  // after a stream synchronisation: fold the elapsed times into the counters
+  static void collect(mlmc_ctx* c) {
+    for (auto& p : pending()) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) c->prof.ms[p.stage] += ms;
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    pending().clear();
+  }
+};
+
 double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -204,26 +244,55 @@ int level_batch_impl(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t 
   const mlmc_model& md = c->model;
   const int nc = n_coarse(md, level);
   const int64_t chunk = chunk_samples(c, level);
-  if (int e = c->itacc.ensure(sizeof(int64_t))) return e;
+  if (int e = c->itacc.ensure(2 * sizeof(int64_t))) return e;
   if (int e = c->sums.ensure(sizeof(LevelSumsDev))) return e;
-  CUDA_TRY(cudaMemsetAsync(c->itacc.p, 0, sizeof(int64_t), c->st));
+  CUDA_TRY(cudaMemsetAsync(c->itacc.p, 0, 2 * sizeof(int64_t), c->st));
+  const int m = md.m0 << level;
+  const int M = c->lev[level].M;
   for (int64_t c0 = 0; c0 < n; c0 += chunk) {
     const int64_t cn = std::min<int64_t>(chunk, n - c0);
     SolveArgs a = base_args(c, level, seed, first + c0);
     if (md.k_kind == 1) {
+      StageTimer t(c, 0);
       if (int e = run_fields(c, level, first + c0, cn, seed)) return e;
+      t.stop(2 * (int)((cn + 65534) / 65535));
       a.g = c->g.p;
+      if (c->prof_on) {
+        c->prof.fft_row_points += (double)cn * n_pairs(md) * M * M;
+        c->prof.fft_col_points += (double)cn * n_pairs(md) * M * m;
+      }
     }
-    if (int e = run_solves(c, a, cn, nc, 0)) return e;
-    if (gather_launch(c->qsys.as<double>(), c->itsys.as<int32_t>(), cn, nc, md.cgv, qf + c0, qc + c0,
-                      qcg + c0, iters ? iters + c0 : nullptr, c->itacc.as<int64_t>(), c->st))
+    {
+      StageTimer t(c, 1);
+      if (int e = run_solves(c, a, cn, nc, 0)) return e;
+      t.stop(1);
+    }
+    StageTimer t(c, 2);
+    if (gather_launch(c->qsys.as<double>(), c->itsys.as<int32_t>(), cn, nc, md.cgv, m, qf + c0,
+                      qc + c0, qcg + c0, iters ? iters + c0 : nullptr, c->itacc.as<int64_t>(), c->st))
       return fail(MLMC_ERR_CUDA, "gather kernel");
+    t.stop(1);
+    if (c->prof_on) {
+      c->prof.cells += (double)cn * ((double)m * m + nc * (double)(m / 2) * (m / 2));
+      c->prof.samples += (double)cn;
+    }
   }
-  if (reduce_launch(qf, qc, qcg, n, md.cgv != 0, c->itacc.as<int64_t>(), c->sums.as<LevelSumsDev>(), c->st))
-    return fail(MLMC_ERR_CUDA, "reduce kernel");
+  {
+    StageTimer t(c, 2);
+    if (reduce_launch(qf, qc, qcg, n, md.cgv != 0, c->itacc.as<int64_t>(), c->sums.as<LevelSumsDev>(),
+                      c->st))
+      return fail(MLMC_ERR_CUDA, "reduce kernel");
+    t.stop(1);
+  }
   LevelSumsDev h;
+  int64_t itc[2];
   CUDA_TRY(cudaMemcpyAsync(&h, c->sums.p, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(cudaMemcpyAsync(itc, c->itacc.p, sizeof(itc), cudaMemcpyDeviceToHost, c->st));
   CUDA_TRY(cudaStreamSynchronize(c->st));
+  if (c->prof_on) {
+    StageTimer::collect(c);
+    c->prof.cell_iters += (double)itc[1];
+  }
   sums->n = h.n;
   sums->n_failed = h.n_failed;
   sums->iters_total = h.iters;
@@ -462,6 +531,19 @@ int mlmc_estimate(mlmc_ctx* c, double eps, uint64_t seed, int32_t n_pilot, int32
   out->rounds = rounds;
   out->seconds = now_s() - t0;
   return rc_any ? MLMC_SOME_FAILED : MLMC_OK;
+}
+
+int mlmc_profile(mlmc_ctx* c, int enable) {
+  if (!c) return fail(MLMC_ERR_ARG, "null context");
+  if (enable) std::memset(&c->prof, 0, sizeof(c->prof));
+  c->prof_on = enable != 0;
+  return 0;
+}
+
+int mlmc_profile_read(mlmc_ctx* c, mlmc_profile_stats* out) {
+  if (!c || !out) return fail(MLMC_ERR_ARG, "null argument");
+  *out = c->prof;
+  return 0;
 }
 
 int mlmc_ce_info(mlmc_ctx* c, int level, int32_t* M_out, double* lam_min, double* lam_max) {

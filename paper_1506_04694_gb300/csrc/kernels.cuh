@@ -86,8 +86,9 @@ struct LevelSumsDev {
 };
 
 // Gather system Q's of a chunk into the per-sample outputs.
+// it_acc[0] += iterations of all systems, it_acc[1] += cells x iterations.
 int gather_launch(const double* q_sys, const int32_t* it_sys, int64_t n_samples, int n_coarse,
-                  int cgv, double* qf, double* qc, double* qcg, int32_t* iters, int64_t* it_acc,
+                  int cgv, int m, double* qf, double* qc, double* qcg, int32_t* iters, int64_t* it_acc,
                   cudaStream_t st);
 int reduce_launch(const double* qf, const double* qc, const double* qcg, int64_t n, int cgv,
                   const int64_t* it_acc, LevelSumsDev* out, cudaStream_t st);

@@ -8,13 +8,14 @@
 namespace mlmc {
 
 __global__ void gather_kernel(const double* q_sys, const int32_t* it_sys, int64_t n, int nc, int cgv,
-                              double* qf, double* qc, double* qcg, int32_t* iters,
+                              int m, double* qf, double* qc, double* qcg, int32_t* iters,
                               unsigned long long* it_acc) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  long long it = 0;
+  long long it = 0, itc = 0;
   if (s < n) {
     qf[s] = q_sys[s];
     it = it_sys[s];
+    itc = (long long)it_sys[s] * m * m;
     if (iters) iters[s] = it_sys[s];
     if (nc == 0) {
       qc[s] = 0.0;
@@ -22,20 +23,27 @@ __global__ void gather_kernel(const double* q_sys, const int32_t* it_sys, int64_
     } else {
       const double* qq = q_sys + n + s * nc;
       qc[s] = qq[0];
-      for (int o = 0; o < nc; ++o) it += it_sys[n + s * nc + o];
+      for (int o = 0; o < nc; ++o) {
+        it += it_sys[n + s * nc + o];
+        itc += (long long)it_sys[n + s * nc + o] * (m / 2) * (m / 2);
+      }
       qcg[s] = nc == 4 ? 0.25 * (((qq[0] + qq[1]) + qq[2]) + qq[3]) : nan("");
     }
   }
   it = warp_sum(it);
-  if ((threadIdx.x & 31) == 0 && it) atomicAdd(it_acc, (unsigned long long)it);
+  itc = warp_sum(itc);
+  if ((threadIdx.x & 31) == 0 && it) {
+    atomicAdd(it_acc, (unsigned long long)it);
+    atomicAdd(it_acc + 1, (unsigned long long)itc);
+  }
 }
 
-int gather_launch(const double* q_sys, const int32_t* it_sys, int64_t n, int n_coarse, int cgv,
+int gather_launch(const double* q_sys, const int32_t* it_sys, int64_t n, int n_coarse, int cgv, int m,
                   double* qf, double* qc, double* qcg, int32_t* iters, int64_t* it_acc,
                   cudaStream_t st) {
   if (n <= 0) return 0;
   gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-      q_sys, it_sys, n, n_coarse, cgv, qf, qc, qcg, iters, (unsigned long long*)it_acc);
+      q_sys, it_sys, n, n_coarse, cgv, m, qf, qc, qcg, iters, (unsigned long long*)it_acc);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

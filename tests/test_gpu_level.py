@@ -81,11 +81,15 @@ def test_four_layers_mixed():
     check_against_oracle(d, 1, 8, seed=3, first=0, rtol=RTOL_MIX)
 
 
-def test_full_size_sampled_fp64():
+@pytest.mark.parametrize("tol,rtol", [(1e-12, RTOL64), (1e-10, 1e-7)])
+def test_full_size_sampled_fp64(tol, rtol):
     # the benchmark's finest level (m = 256, M = 1024) in the launch the
-    # benchmark uses (a large batch); sampled outputs checked one by one
+    # benchmark uses (a large batch); sampled outputs checked one by one.
+    # With the paper's stopping rule (||r||/||r0|| < 1e-10) the algebraic error
+    # of Q is ~1e-8; with 1e-12 the FP64 path agrees with the direct solve to
+    # 1e-10.
     torch, pk = need_gpu()
-    d = workloads.workload("lognormal_2layer_16to256")
+    d = workloads.workload("lognormal_2layer_16to256", tol=tol)
     model = darcy.Model.from_dict(d)
     n = 400
     s, qf, qc, qg, it = run_gpu(pk, torch, d, 4, n, seed=0)
@@ -93,9 +97,8 @@ def test_full_size_sampled_fp64():
     cache = {}
     for i in (0, 137, 399):
         r = darcy.sample(model, 0, 4, i, cache)
-        # tol 1e-10 (the paper's) on the benchmark settings: Q within 1e-8
-        assert abs(qf[i] - r["qf"]) <= 1e-8 * abs(r["qf"])
-        assert abs(qc[i] - r["qc"]) <= 1e-8 * abs(r["qc"])
+        assert abs(qf[i] - r["qf"]) <= rtol * abs(r["qf"])
+        assert abs(qc[i] - r["qc"]) <= rtol * abs(r["qc"])
 
 
 def test_full_size_sampled_mixed_cgv():
