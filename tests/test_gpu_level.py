@@ -81,12 +81,12 @@ def test_four_layers_mixed():
     check_against_oracle(d, 1, 8, seed=3, first=0, rtol=RTOL_MIX)
 
 
-@pytest.mark.parametrize("tol,rtol", [(1e-12, RTOL64), (1e-10, 1e-7)])
+@pytest.mark.parametrize("tol,rtol", [(1e-13, RTOL64), (1e-10, 1e-7)])
 def test_full_size_sampled_fp64(tol, rtol):
     # the benchmark's finest level (m = 256, M = 1024) in the launch the
     # benchmark uses (a large batch); sampled outputs checked one by one.
     # With the paper's stopping rule (||r||/||r0|| < 1e-10) the algebraic error
-    # of Q is ~1e-8; with 1e-12 the FP64 path agrees with the direct solve to
+    # of Q is ~1e-8; with 1e-13 the FP64 path agrees with the direct solve to
     # 1e-10.
     torch, pk = need_gpu()
     d = workloads.workload("lognormal_2layer_16to256", tol=tol)
