@@ -180,6 +180,33 @@ MLMC_API int mlmc_sample_fields(mlmc_ctx* ctx, int level, int64_t first, int64_t
 MLMC_API int mlmc_solve_k(mlmc_ctx* ctx, int32_t m, int64_t n, const double* k, double* p, double* q,
                  int32_t* iters);
 
+/* Same solve as mlmc_solve_k(), for callers that cannot allocate device
+ * memory: a plug-in inside a host application that has already reserved
+ * (nearly) all GPU memory for its own pool, or a latency-critical loop that
+ * cannot afford the device-wide synchronisation of cudaMalloc / cudaFree.
+ * The paper has no counterpart; this is a deployment variant of the solver.
+ * It needs no context and calls no allocating routine: the per-block solver
+ * workspace lives in a fixed 32 MiB array in the library's device memory,
+ * which every GPU that loads the library holds until the process exits.
+ *   device: CUDA device to run on (made current for the call, then restored).
+ *   m, n, k, p, q, iters: as in mlmc_solve_k() (k, p, q, iters device
+ *     pointers; p and iters may be NULL).
+ *   tol, max_it, prec: solver settings as in mlmc_model.
+ *   cuda_stream: cudaStream_t to queue the work on; the call returns after
+ *     queuing it (results are ready when the stream reaches this point).
+ * The first call on a device looks up the array's device address (one
+ * cudaGetSymbolAddress per device); make that first call before any stream
+ * capture.  Systems with m <= 32 use shared memory only; larger systems need
+ * their whole workspace in the array, so m > 512 returns MLMC_ERR_TOOBIG.
+ * Every call shares the one array and the solver initialises everything it
+ * reads, so nothing carries over between calls; calls that overlap on the
+ * GPU (other streams, other threads) race on the array and must be ordered
+ * by the caller.
+ * Errors: MLMC_ERR_ARG, MLMC_ERR_NODEV, MLMC_ERR_TOOBIG, MLMC_ERR_CUDA. */
+MLMC_API int mlmc_solve_k_static(int device, int32_t m, int64_t n, const double* k, double* p,
+                                 double* q, int32_t* iters, double tol, int32_t max_it,
+                                 int32_t prec, void* cuda_stream);
+
 /* Per-stage device timing of a context, collected with CUDA events on the
  * context's stream while enabled (used by the benchmark for the roofline). */
 typedef struct mlmc_profile_stats {

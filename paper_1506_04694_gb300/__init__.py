@@ -89,6 +89,10 @@ EXPORTS = {
                                           ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
     "mlmc_solve_k": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "mlmc_solve_k_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_void_p]),
     "mlmc_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "mlmc_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ProfileStats)]),
     "mlmc_error_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -268,6 +272,20 @@ class Context:
         _check(lib().mlmc_solve_k(self._h, m, n, _ptr(k.contiguous(), torch.float64), _ptr(p), _ptr(q),
                                   _ptr(it)), allow_failed=False)
         return p, q, it
+
+
+def solve_k_static(k, q, p=None, iters=None, tol=1e-10, max_it=500, prec=0, device=0, stream=None):
+    """mlmc_solve_k_static: the solver with no device allocation at all, for
+    callers that cannot allocate; the caller supplies every output tensor
+    (q float64 [n]; optional p float64 [n, m, m] and iters int32 [n]).  The
+    work is queued on `stream` (default: the current stream) and not waited for."""
+    import torch
+    n, m, _ = k.shape
+    rc = lib().mlmc_solve_k_static(device, m, n, _ptr(k, torch.float64), _ptr(p, torch.float64),
+                                   _ptr(q, torch.float64), _ptr(iters, torch.int32), tol, max_it, prec,
+                                   _stream_handle(stream))
+    if rc != 0:
+        raise MLMCError("mlmc_solve_k_static: %s" % lib().mlmc_error_string(rc).decode())
 
 
 def philox_words(seed, level, sample, stream_id, first_call, n_calls, device=0):

@@ -21,9 +21,13 @@
 //         coefficients are rounded to FP32 once and the FP64 residual uses
 //         exactly those values.
 // Outflow QoI M^(2) (Sec. 3.4): Q = sum_j T(m, j) p(m-1, j).
+#include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <mutex>
 #include <type_traits>
 
+#include "../../include/mlmc.h"
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -599,3 +603,95 @@ int const_fields_launch(const SolveArgs& a, int64_t n, double* g, cudaStream_t s
 }
 
 }  // namespace mlmc
+
+// ---------------------------------------------------------------------------
+// Solve entry point that allocates nothing.
+//
+// Some callers cannot call cudaMalloc: a plug-in living inside a host
+// application that has already reserved (nearly) all device memory for its
+// own pool, or a latency-critical loop that cannot afford the device-wide
+// synchronisation and unbounded latency of cudaMalloc / cudaFree.  For them,
+// mlmc_solve_k_static() runs the same solver as mlmc_solve_k() but takes its
+// per-block workspace from the fixed array below instead of a context.
+// ---------------------------------------------------------------------------
+namespace mlmc {
+
+// Scratch of the static entry point: 32 MiB, in the module's global memory.
+// Every GPU that loads this library holds it until the process exits.
+constexpr size_t kStaticScratchBytes = size_t(32) << 20;
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxDevices] = {};  // device address of g_static_scratch, per device
+}  // namespace
+
+}  // namespace mlmc
+
+extern "C" int mlmc_solve_k_static(int device, int32_t m, int64_t n, const double* k, double* p,
+                                   double* q, int32_t* iters, double tol, int32_t max_it,
+                                   int32_t prec, void* cuda_stream) {
+  using namespace mlmc;
+  if (device < 0 || device >= kMaxDevices || !k || !q || n < 0) return MLMC_ERR_ARG;
+  if (m < 1 || m > 4096 || (m & (m - 1))) return MLMC_ERR_ARG;
+  if (!(tol > 0) || max_it < 1 || (prec != 0 && prec != 1)) return MLMC_ERR_ARG;
+  if (n == 0) return MLMC_OK;
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) return MLMC_ERR_NODEV;
+  if (cudaSetDevice(device) != cudaSuccess) return MLMC_ERR_NODEV;
+  int rc = MLMC_OK;
+  do {
+    // set-up, once per device, with that device current: the host-side name
+    // g_static_scratch is only a stand-in; the kernel needs the device address
+    void* base = nullptr;
+    {
+      std::lock_guard<std::mutex> lock(g_static_mu);
+      if (!g_static_ptr[device]) {
+        void* ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) {
+          rc = MLMC_ERR_CUDA;
+          break;
+        }
+        g_static_ptr[device] = ptr;
+      }
+      base = g_static_ptr[device];
+    }
+    size_t smem = 0;
+    int use_smem = 0;
+    const int bpsm = solve_blocks_per_sm(m, prec, &smem, &use_smem);
+    int nsm = 0;
+    if (bpsm < 0 || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+      rc = MLMC_ERR_CUDA;
+      break;
+    }
+    SolveArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n_samples = n;
+    a.n_coarse = 0;
+    a.m = m;
+    a.ksrc = KSRC_ARRAY;
+    a.n_layers = 1;
+    a.k = k;
+    a.tol = tol;
+    a.max_it = max_it;
+    a.inner_tol = 1e-5;
+    a.q = q;
+    a.iters = iters;
+    a.p_out = p;
+    a.use_smem = use_smem;
+    int64_t nb = std::min<int64_t>(n, (int64_t)nsm * bpsm);
+    if (!use_smem) {
+      a.ws_stride = (solve_ws_bytes(m, prec) + 255) & ~(size_t)255;
+      if (a.ws_stride > kStaticScratchBytes) {  // m above the static maximum (512)
+        rc = MLMC_ERR_TOOBIG;
+        break;
+      }
+      nb = std::min<int64_t>(nb, (int64_t)(kStaticScratchBytes / a.ws_stride));
+      a.ws = reinterpret_cast<unsigned char*>(base);
+    }
+    if (solve_launch(a, prec, (int)nb, smem, (cudaStream_t)cuda_stream)) rc = MLMC_ERR_CUDA;
+  } while (0);
+  cudaSetDevice(prev);
+  return rc;
+}
