@@ -34,14 +34,15 @@
 namespace mlmc {
 
 constexpr int kMaxLevels = 14;
+constexpr int kArrays = 6;  // per level: tx, ty, diag, invd, e, f
 
 __host__ __device__ __forceinline__ size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
 // Workspace layout for an m x m system; element size ts of the solver
 // precision; mixed adds FP64 x and r.  Returns total bytes; fills offsets
-// when `off` is non-null: off[0..1] x64, r64; then per level l 5 offsets
-// (tx, ty, invd, e, f) at 2 + 5 l; level-0 extra PCG vectors x, p, q at
-// 2 + 5*kMaxLevels + {0, 1, 2}.
+// when `off` is non-null: off[0..1] x64, r64; then per level l the kArrays
+// offsets (tx, ty, diag, invd, e, f) at 2 + kArrays l; level-0 extra CG
+// vectors x, p, q at 2 + kArrays*kMaxLevels + {0, 1, 2}.
 __host__ __device__ inline size_t ws_layout(int m, int ts, bool mixed, size_t* off) {
   size_t o = 0;
   const size_t n = (size_t)m * m;
@@ -63,21 +64,15 @@ __host__ __device__ inline size_t ws_layout(int m, int ts, bool mixed, size_t* o
   while (true) {
     const size_t nl = (size_t)ml * ml;
     const size_t nf = (size_t)ml * (ml + 1);
-    const size_t a0 = take(nf * ts), a1 = take(nf * ts), a2 = take(nl * ts), a3 = take(nl * ts),
-                 a4 = take(nl * ts);
-    if (off) {
-      off[2 + 5 * l + 0] = a0;
-      off[2 + 5 * l + 1] = a1;
-      off[2 + 5 * l + 2] = a2;
-      off[2 + 5 * l + 3] = a3;
-      off[2 + 5 * l + 4] = a4;
+    const size_t sizes[kArrays] = {nf, nf, nl, nl, nl, nl};
+    for (int a = 0; a < kArrays; ++a) {
+      const size_t at = take(sizes[a] * ts);
+      if (off) off[2 + kArrays * l + a] = at;
     }
     if (l == 0) {
-      const size_t b0 = take(nl * ts), b1 = take(nl * ts), b2 = take(nl * ts);
-      if (off) {
-        off[2 + 5 * kMaxLevels + 0] = b0;
-        off[2 + 5 * kMaxLevels + 1] = b1;
-        off[2 + 5 * kMaxLevels + 2] = b2;
+      for (int b = 0; b < 3; ++b) {
+        const size_t at = take(nl * ts);
+        if (off) off[2 + kArrays * kMaxLevels + b] = at;
       }
     }
     if (ml == 1) break;
@@ -87,28 +82,32 @@ __host__ __device__ inline size_t ws_layout(int m, int ts, bool mixed, size_t* o
   return o;
 }
 
+constexpr int kLayoutSlots = 2 + kArrays * kMaxLevels + 3;
+
 template <typename T>
 struct Level {
   int m;
   T* tx;    // m rows x (m+1) faces
   T* ty;    // (m+1) face rows x m
+  T* diag;  // sum of the four faces
   T* invd;  // 1 / diagonal
   T* e;     // correction (level 0: CG z)
   T* f;     // right-hand side (level 0: CG r)
 };
 
-// (A v)_c = sum over the 4 faces of T (v_c - v_nbr), v_nbr = 0 outside.
+// (A v)_c = diag_c v_c - sum over the faces of T v_nbr (v_nbr = 0 outside:
+// Dirichlet faces carry T but no neighbour, no-flow faces carry T = 0).
 template <typename T>
-__device__ __forceinline__ T apply_row(const T* __restrict__ tx, const T* __restrict__ ty,
-                                       const T* __restrict__ v, int m, int i, int j) {
+__device__ __forceinline__ T apply_row(const Level<T>& L, const T* __restrict__ v, int i, int j) {
+  const int m = L.m;
   const int c = j * m + i;
   const int rf = j * (m + 1) + i;
-  const T vc = v[c];
-  const T vw = i > 0 ? v[c - 1] : T(0);
-  const T ve = i < m - 1 ? v[c + 1] : T(0);
-  const T vs = j > 0 ? v[c - m] : T(0);
-  const T vn = j < m - 1 ? v[c + m] : T(0);
-  return (tx[rf] * (vc - vw) + tx[rf + 1] * (vc - ve)) + (ty[c] * (vc - vs) + ty[c + m] * (vc - vn));
+  T s = L.diag[c] * v[c];
+  if (i > 0) s -= L.tx[rf] * v[c - 1];
+  if (i < m - 1) s -= L.tx[rf + 1] * v[c + 1];
+  if (j > 0) s -= L.ty[c] * v[c - m];
+  if (j < m - 1) s -= L.ty[c + m] * v[c + m];
+  return s;
 }
 
 // One red (color 0) or black (color 1) Gauss-Seidel half sweep; `zero_guess`
@@ -134,21 +133,19 @@ __device__ __forceinline__ void rb_sweep(const Level<T>& L, int color, bool zero
   __syncthreads();
 }
 
-// Coarse f = sum of the four fine residuals f - A e of each 2x2 aggregate.
+// Coarse f = sum of the fine residuals f - A e over each 2x2 aggregate.
+// Called right after a black half sweep, which leaves the residual at the
+// black cells zero, so only the two red cells (2I, 2J), (2I+1, 2J+1) of the
+// aggregate contribute.
 template <typename T>
 __device__ __forceinline__ void restrict_residual(const Level<T>& F, const Level<T>& C) {
   const int mc = C.m, m = F.m;
   for (int cc = threadIdx.x; cc < mc * mc; cc += blockDim.x) {
     const int J = cc / mc, I = cc - J * mc;
-    T acc = T(0);
-#pragma unroll
-    for (int b = 0; b < 2; ++b)
-#pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        const int i = 2 * I + a, j = 2 * J + b;
-        acc += F.f[j * m + i] - apply_row(F.tx, F.ty, F.e, m, i, j);
-      }
-    C.f[cc] = acc;
+    const int i0 = 2 * I, j0 = 2 * J;
+    const T r0 = F.f[j0 * m + i0] - apply_row(F, F.e, i0, j0);
+    const T r1 = F.f[(j0 + 1) * m + i0 + 1] - apply_row(F, F.e, i0 + 1, j0 + 1);
+    C.f[cc] = r0 + r1;
   }
   __syncthreads();
 }
@@ -182,19 +179,21 @@ __device__ __forceinline__ void build_coarse(const Level<T>& F, const Level<T>& 
 }
 
 template <typename T>
-__device__ __forceinline__ void build_invd(const Level<T>& L) {
+__device__ __forceinline__ void build_diag(const Level<T>& L) {
   const int m = L.m;
   for (int c = threadIdx.x; c < m * m; c += blockDim.x) {
     const int j = c / m, i = c - j * m;
     const int rf = j * (m + 1) + i;
-    L.invd[c] = T(1) / ((L.tx[rf] + L.tx[rf + 1]) + (L.ty[c] + L.ty[c + m]));
+    const T d = (L.tx[rf] + L.tx[rf + 1]) + (L.ty[c] + L.ty[c + m]);
+    L.diag[c] = d;
+    L.invd[c] = T(1) / d;
   }
   __syncthreads();
 }
 
 // Symmetric V-cycle: level-0 e <- B f.
 template <typename T>
-__device__ void vcycle(Level<T>* lev, int nl) {
+__device__ void vcycle(const Level<T>* lev, int nl) {
   for (int l = 0; l < nl - 1; ++l) {
     rb_sweep(lev[l], 0, true);
     rb_sweep(lev[l], 1, false);
@@ -216,15 +215,17 @@ __device__ void vcycle(Level<T>* lev, int nl) {
 // Stops when r.r <= thr; returns iterations, status 0 converged, 1 hit the
 // cap, 2 breakdown (p.Ap <= 0 or not finite).
 template <typename T>
-__device__ int pcg(Level<T>* lev, int nl, T* x, T* p, T* q, T thr, int max_it, T* red, int& par,
+__device__ int pcg(const Level<T>* lev, int nl, T* x, T* p, T* q, T thr, int max_it, T* red, int& par,
                    int& status) {
   const Level<T>& L0 = lev[0];
   const int m = L0.m, n = m * m;
   T* r = L0.f;
   T* z = L0.e;
-  for (int c = threadIdx.x; c < n; c += blockDim.x) x[c] = T(0);
   T rr = T(0);
-  for (int c = threadIdx.x; c < n; c += blockDim.x) rr += r[c] * r[c];
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    x[c] = T(0);
+    rr += r[c] * r[c];
+  }
   rr = block_sum(rr, red, par);
   status = 1;
   if (rr <= thr) {
@@ -244,7 +245,7 @@ __device__ int pcg(Level<T>* lev, int nl, T* x, T* p, T* q, T thr, int max_it, T
     T pq = T(0);
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
       const int j = c / m, i = c - j * m;
-      const T v = apply_row(L0.tx, L0.ty, p, m, i, j);
+      const T v = apply_row(L0, p, i, j);
       q[c] = v;
       pq += p[c] * v;
     }
@@ -316,16 +317,27 @@ __device__ void sample_layers(const SolveArgs& a, uint64_t sample, double* eta, 
   }
 }
 
+constexpr int kMaxThreads = 512;
+
+// Threads per block for an m x m system: about one cell per thread on the
+// finest red-black half sweep up to 512.
+__host__ __device__ inline int solve_threads(int m) { return m <= 16 ? 128 : (m <= 64 ? 256 : 512); }
+
 template <bool MIXED>
-__global__ void __launch_bounds__(256) solve_kernel(SolveArgs a) {
+__global__ void __launch_bounds__(kMaxThreads) solve_kernel(SolveArgs a) {
   using T = typename std::conditional<MIXED, float, double>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T red[132];
   __shared__ double red64[132];
   __shared__ double eta_s[MAX_LAYERS_DEV], kc_s[MAX_LAYERS_DEV];
+  __shared__ Level<T> lev[kMaxLevels];
+  __shared__ int nl_s;
+  __shared__ T *xv_s, *pv_s, *qv_s;
+  __shared__ double *x64_s, *r64_s;
   unsigned char* base = a.use_smem ? smem_raw : a.ws + (size_t)blockIdx.x * a.ws_stride;
   const int64_t n_sys = a.n_samples * (int64_t)(1 + a.n_coarse);
   int par = 0;
+  int m_prev = -1;
   for (int64_t sys = blockIdx.x; sys < n_sys; sys += gridDim.x) {
     int64_t sidx;
     int coarse = 0, ox = 0, oy = 0;
@@ -342,26 +354,40 @@ __global__ void __launch_bounds__(256) solve_kernel(SolveArgs a) {
     const int m = coarse ? a.m >> 1 : a.m;
     const int n = m * m;
     const uint64_t sample = (uint64_t)(a.first + sidx);
-    size_t off[2 + 5 * kMaxLevels + 3];
-    ws_layout(m, sizeof(T), MIXED, off);
-    Level<T> lev[kMaxLevels];
-    int nl = 0;
-    for (int ml = m; ; ml >>= 1) {
-      Level<T>& L = lev[nl];
-      L.m = ml;
-      L.tx = reinterpret_cast<T*>(base + off[2 + 5 * nl + 0]);
-      L.ty = reinterpret_cast<T*>(base + off[2 + 5 * nl + 1]);
-      L.invd = reinterpret_cast<T*>(base + off[2 + 5 * nl + 2]);
-      L.e = reinterpret_cast<T*>(base + off[2 + 5 * nl + 3]);
-      L.f = reinterpret_cast<T*>(base + off[2 + 5 * nl + 4]);
-      ++nl;
-      if (ml == 1) break;
+    if (m != m_prev) {  // level table of this system size, shared by the block
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        size_t off[kLayoutSlots];
+        ws_layout(m, sizeof(T), MIXED, off);
+        int l = 0;
+        for (int ml = m;; ml >>= 1, ++l) {
+          Level<T>& L = lev[l];
+          L.m = ml;
+          L.tx = reinterpret_cast<T*>(base + off[2 + kArrays * l + 0]);
+          L.ty = reinterpret_cast<T*>(base + off[2 + kArrays * l + 1]);
+          L.diag = reinterpret_cast<T*>(base + off[2 + kArrays * l + 2]);
+          L.invd = reinterpret_cast<T*>(base + off[2 + kArrays * l + 3]);
+          L.e = reinterpret_cast<T*>(base + off[2 + kArrays * l + 4]);
+          L.f = reinterpret_cast<T*>(base + off[2 + kArrays * l + 5]);
+          if (ml == 1) break;
+        }
+        nl_s = l + 1;
+        xv_s = reinterpret_cast<T*>(base + off[2 + kArrays * kMaxLevels + 0]);
+        pv_s = reinterpret_cast<T*>(base + off[2 + kArrays * kMaxLevels + 1]);
+        qv_s = reinterpret_cast<T*>(base + off[2 + kArrays * kMaxLevels + 2]);
+        x64_s = MIXED ? reinterpret_cast<double*>(base + off[0]) : reinterpret_cast<double*>(xv_s);
+        r64_s = MIXED ? reinterpret_cast<double*>(base + off[1]) : reinterpret_cast<double*>(lev[0].f);
+      }
+      __syncthreads();
+      m_prev = m;
     }
-    T* xv = reinterpret_cast<T*>(base + off[2 + 5 * kMaxLevels + 0]);
-    T* pv = reinterpret_cast<T*>(base + off[2 + 5 * kMaxLevels + 1]);
-    T* qv = reinterpret_cast<T*>(base + off[2 + 5 * kMaxLevels + 2]);
-    double* x64 = MIXED ? reinterpret_cast<double*>(base + off[0]) : reinterpret_cast<double*>(xv);
-    double* r64 = MIXED ? reinterpret_cast<double*>(base + off[1]) : reinterpret_cast<double*>(lev[0].f);
+    const int nl = nl_s;
+    T* xv = xv_s;
+    T* pv = pv_s;
+    T* qv = qv_s;
+    double* x64 = x64_s;
+    double* r64 = r64_s;
+    const Level<T>& L0 = lev[0];
 
     // ---- layers and per-cell permeability (into r64 as scratch) ----
     if (a.ksrc != KSRC_ARRAY) {
@@ -396,7 +422,6 @@ __global__ void __launch_bounds__(256) solve_kernel(SolveArgs a) {
     __syncthreads();
     // ---- faces (Eq. 3.3, harmonic averages; Dirichlet 2k; no-flow 0) ----
     {
-      const Level<T>& L = lev[0];
       const int nfx = m * (m + 1);
       for (int t = threadIdx.x; t < 2 * nfx; t += blockDim.x) {
         if (t < nfx) {
@@ -408,7 +433,7 @@ __global__ void __launch_bounds__(256) solve_kernel(SolveArgs a) {
             const T ka = (T)r64[j * m + ip - 1], kb = (T)r64[j * m + ip];
             v = T(2) * ka * kb / (ka + kb);
           }
-          L.tx[t] = v;
+          L0.tx[t] = v;
         } else {
           const int u = t - nfx;
           const int jp = u / m, i = u - jp * m;
@@ -417,19 +442,18 @@ __global__ void __launch_bounds__(256) solve_kernel(SolveArgs a) {
             const T ka = (T)r64[(jp - 1) * m + i], kb = (T)r64[jp * m + i];
             v = T(2) * ka * kb / (ka + kb);
           }
-          L.ty[u] = v;
+          L0.ty[u] = v;
         }
       }
       __syncthreads();
-      build_invd(L);
+      build_diag(L0);
     }
     for (int l = 1; l < nl; ++l) {
       build_coarse(lev[l - 1], lev[l]);
-      build_invd(lev[l]);
+      build_diag(lev[l]);
     }
     // ---- solve ----
     int status = 1, iters = 0;
-    const Level<T>& L0 = lev[0];
     if (!MIXED) {
       // r = b, bb = b.b; stop at r.r <= tol^2 b.b
       T bb = T(0);
@@ -485,14 +509,14 @@ __global__ void __launch_bounds__(256) solve_kernel(SolveArgs a) {
         for (int c = threadIdx.x; c < n; c += blockDim.x) {
           const int j = c / m, i = c - j * m;
           const int rf = j * (m + 1) + i;
-          const double vc = x64[c];
-          const double vw = i > 0 ? x64[c - 1] : 0.0;
-          const double ve = i < m - 1 ? x64[c + 1] : 0.0;
-          const double vs = j > 0 ? x64[c - m] : 0.0;
-          const double vn = j < m - 1 ? x64[c + m] : 0.0;
-          const double ax = ((double)L0.tx[rf] * (vc - vw) + (double)L0.tx[rf + 1] * (vc - ve)) +
-                            ((double)L0.ty[c] * (vc - vs) + (double)L0.ty[c + m] * (vc - vn));
-          const double bv = i == 0 ? (double)L0.tx[rf] : 0.0;
+          const double tw = (double)L0.tx[rf], te = (double)L0.tx[rf + 1];
+          const double ts = (double)L0.ty[c], tn = (double)L0.ty[c + m];
+          double ax = ((tw + te) + (ts + tn)) * x64[c];
+          if (i > 0) ax -= tw * x64[c - 1];
+          if (i < m - 1) ax -= te * x64[c + 1];
+          if (j > 0) ax -= ts * x64[c - m];
+          if (j < m - 1) ax -= tn * x64[c + m];
+          const double bv = i == 0 ? tw : 0.0;
           const double rv = bv - ax;
           r64[c] = rv;
           rr += rv * rv;
@@ -531,22 +555,24 @@ int solve_blocks_per_sm(int m, int prec, size_t* smem_bytes, int* use_smem) {
   *smem_bytes = *use_smem ? ws : 0;
   int nb = 0;
   cudaError_t e;
+  const int nt = solve_threads(m);
   if (prec) {
     cudaFuncSetAttribute(solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<true>, 256, *smem_bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<true>, nt, *smem_bytes);
   } else {
     cudaFuncSetAttribute(solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<false>, 256, *smem_bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<false>, nt, *smem_bytes);
   }
   if (e != cudaSuccess) return -1;
   return nb < 1 ? 1 : nb;
 }
 
 int solve_launch(const SolveArgs& a, int prec, int n_blocks, size_t smem_bytes, cudaStream_t st) {
+  const int nt = solve_threads(a.m);
   if (prec)
-    solve_kernel<true><<<n_blocks, 256, smem_bytes, st>>>(a);
+    solve_kernel<true><<<n_blocks, nt, smem_bytes, st>>>(a);
   else
-    solve_kernel<false><<<n_blocks, 256, smem_bytes, st>>>(a);
+    solve_kernel<false><<<n_blocks, nt, smem_bytes, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
