@@ -201,6 +201,40 @@ def config_block(args, d):
             "l2": "flushed between steps (256 MB device write)", "parallelism": "replicas%d" % args.gpus}
 
 
+def compare(args):
+    """Time-to-eps: the workload as configured (mixed precision + CGV) against
+    plain FP64 batched MLMC without CGV at the same eps and levels."""
+    import torch
+    import paper_1506_04694_gb300 as pk
+    import workloads
+    d = workloads.workload(args.compare)
+    arms = {"mixed_cgv": dict(d), "plain_fp64": dict(d, prec=0, cgv=0)}
+    out = {"compare": args.compare, "eps": d["eps"], "m_levels": [d["m0"] << l for l in range(d["L"] + 1)],
+           "steps": args.steps, "warmup": args.warmup}
+    for name, md in arms.items():
+        ctx = pk.Context(md)
+        for _ in range(args.warmup):
+            ctx.estimate(md["eps"], args.seed, n_pilot=64, cost_model=0)
+        torch.cuda.synchronize()
+        ts, est = [], None
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(ctx.stream)
+            est = ctx.estimate(md["eps"], args.seed, n_pilot=64, cost_model=0)
+            e1.record(ctx.stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        out[name] = {"time_to_eps_s": sum(ts) / len(ts), "N": est["N"], "V": est["V"], "q_hat": est["q_hat"],
+                     "var_hat": est["var_hat"], "level_samples_per_s": sum(est["N"]) / (sum(ts) / len(ts)),
+                     "prec": "fp64" if md["prec"] == 0 else "fp32-mg/fp64-refinement", "cgv": md["cgv"]}
+        ctx.close()
+        del ctx
+        torch.cuda.empty_cache()
+    out["speedup_mixed_cgv_vs_plain_fp64"] = out["plain_fp64"]["time_to_eps_s"] / out["mixed_cgv"]["time_to_eps_s"]
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -210,7 +244,13 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--compare", default=None,
+                    help="workload name: time-to-eps of its mixed-precision CGV form against plain FP64 "
+                         "batched MLMC (no CGV) at the same eps and level set; prints one JSON line")
     args = ap.parse_args()
+    if args.compare:
+        compare(args)
+        return
 
     import workloads
     d = workloads.workload(args.workload)

@@ -164,6 +164,16 @@ MLMC_API int mlmc_ce_info(mlmc_ctx* ctx, int level, int32_t* M_out, double* lam_
 MLMC_API int mlmc_philox_words(uint64_t seed, uint64_t level, uint64_t sample, uint64_t stream,
                       uint64_t first_call, int64_t n_calls, uint64_t* out, void* cuda_stream);
 
+/* Stage output for parity checks: the four standard normals of each Philox
+ * call first_call .. first_call+n_calls-1 of one (seed, level, sample,
+ * stream), in the order BM(u0,u1).re, BM(u0,u1).im, BM(u2,u3).re,
+ * BM(u2,u3).im, where BM(ua, ub) = sqrt(-2 ln ua) (cos 2 pi ub, sin 2 pi ub)
+ * (Box-Muller; the normals of Ex. 1 and of the circulant-embedding draw),
+ * computed by the routine the field kernels of the context's precision use.
+ * out: device pointer to 4*n_calls doubles. */
+MLMC_API int mlmc_normals(mlmc_ctx* ctx, uint64_t seed, uint64_t level, uint64_t sample, uint64_t stream,
+                          uint64_t first_call, int64_t n_calls, double* out);
+
 /* Stage output for parity checks: the per-layer fields g_t of the fine grid of
  * samples first .. first+n-1 of `level` (Ex. 1 constants or Ex. 2 fields),
  * g: device pointer to n * n_layers * m * m doubles ([sample][t][j][i]);

@@ -85,6 +85,8 @@ EXPORTS = {
     "mlmc_philox_words": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                          ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                          ctypes.c_void_p, ctypes.c_void_p]),
+    "mlmc_normals": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                    ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p]),
     "mlmc_sample_fields": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
                                           ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]),
     "mlmc_solve_k": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
@@ -248,6 +250,14 @@ class Context:
         hi = ctypes.c_double()
         _check(lib().mlmc_ce_info(self._h, level, ctypes.byref(M), ctypes.byref(lo), ctypes.byref(hi)))
         return M.value, lo.value, hi.value
+
+    def normals(self, seed, level, sample, stream_id, first_call, n_calls):
+        """mlmc_normals: the four Box-Muller normals of each Philox call, [n_calls, 4]."""
+        import torch
+        out = torch.empty((n_calls, 4), dtype=torch.float64, device="cuda:%d" % self.device)
+        _check(lib().mlmc_normals(self._h, seed, level, sample, stream_id, first_call, n_calls, _ptr(out)),
+               allow_failed=False)
+        return out
 
     def sample_fields(self, level, n, seed, first=0):
         """mlmc_sample_fields: fine per-layer fields g [n, n_layers, m, m] and

@@ -76,7 +76,7 @@ struct mlmc_ctx {
   mlmc_model model{};
   int nsm = 0;
   std::vector<LevelTable> lev;
-  Buf W, g, ws, qsys, itsys, oqf, oqc, oqg, oit, sums, itacc, g64;
+  Buf W, g, ws, qsys, itsys, oqf, oqc, oqg, oit, sums, itacc, g64, bm;
   bool prof_on = false;
   mlmc_profile_stats prof{};
 };
@@ -138,6 +138,8 @@ int run_fields(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t seed) 
   const LevelTable& T = c->lev[level];
   const bool f32 = md.prec != 0;
   CeLaunch L;
+  L.bm_sc = c->bm.as<double2>();
+  L.bm_lg = reinterpret_cast<const double*>(c->bm.as<double2>() + kSinCosTab);
   L.M = T.M;
   L.m = T.m;
   L.n_pairs = n_pairs(md);
@@ -171,28 +173,31 @@ int64_t chunk_samples(const mlmc_ctx* c, int level) {
   return std::max<int64_t>(1, std::min<int64_t>(s, 1 << 18));
 }
 
+// Bytes of global solver workspace a context may hold (bounds the number of
+// resident blocks for very large grids).
+constexpr size_t kWsBudget = size_t(16) << 30;
+
 // Solve the systems of one chunk; results into c->qsys / c->itsys.
 int run_solves(mlmc_ctx* c, SolveArgs a, int64_t n_samples, int nc, int64_t max_rows) {
   const int prec = c->model.prec;
   a.n_samples = n_samples;
   a.n_coarse = nc;
-  size_t smem = 0;
-  int use_smem = 0;
-  const int bpsm = solve_blocks_per_sm(a.m, prec, &smem, &use_smem);
-  if (bpsm < 0) return fail(MLMC_ERR_CUDA, "occupancy query failed");
+  SolvePlan P;
+  if (solve_plan(a.m, prec, &P)) return fail(MLMC_ERR_CUDA, "occupancy query failed");
   const int64_t n_sys = n_samples * (1 + nc);
-  const int64_t nb = std::min<int64_t>(n_sys, (int64_t)c->nsm * bpsm);
-  a.use_smem = use_smem;
-  a.ws_stride = (solve_ws_bytes(a.m, prec) + 255) & ~(size_t)255;
-  if (!use_smem) {
-    if (int e = c->ws.ensure(a.ws_stride * nb)) return e;
+  int64_t nb = std::min<int64_t>((n_sys + P.groups_per_block - 1) / P.groups_per_block,
+                                 (int64_t)c->nsm * P.blocks_per_sm);
+  if (!P.use_smem) {
+    const size_t per_block = P.ws_stride * P.groups_per_block;
+    nb = std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)(kWsBudget / per_block)));
+    if (int e = c->ws.ensure(per_block * nb)) return e;
     a.ws = c->ws.as<unsigned char>();
   }
   if (int e = c->qsys.ensure((size_t)std::max<int64_t>(n_sys, max_rows) * 8)) return e;
   if (int e = c->itsys.ensure((size_t)std::max<int64_t>(n_sys, max_rows) * 4)) return e;
   a.q = c->qsys.as<double>();
   a.iters = c->itsys.as<int32_t>();
-  if (solve_launch(a, prec, (int)nb, smem, c->st))
+  if (solve_launch(a, prec, P, (int)nb, c->st))
     return fail(MLMC_ERR_CUDA, std::string("solve kernel: ") + cudaGetErrorString(cudaGetLastError()));
   return 0;
 }
@@ -245,7 +250,7 @@ int level_batch_impl(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t 
   const int nc = n_coarse(md, level);
   const int64_t chunk = chunk_samples(c, level);
   if (int e = c->itacc.ensure(2 * sizeof(int64_t))) return e;
-  if (int e = c->sums.ensure(sizeof(LevelSumsDev))) return e;
+  if (int e = c->sums.ensure(256 + reduce_ws_bytes())) return e;  // sums at 0, partials at 256
   CUDA_TRY(cudaMemsetAsync(c->itacc.p, 0, 2 * sizeof(int64_t), c->st));
   const int m = md.m0 << level;
   const int M = c->lev[level].M;
@@ -280,9 +285,9 @@ int level_batch_impl(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t 
   {
     StageTimer t(c, 2);
     if (reduce_launch(qf, qc, qcg, n, md.cgv != 0, c->itacc.as<int64_t>(), c->sums.as<LevelSumsDev>(),
-                      c->st))
+                      c->sums.as<unsigned char>() + 256, c->st))
       return fail(MLMC_ERR_CUDA, "reduce kernel");
-    t.stop(1);
+    t.stop(2);
   }
   LevelSumsDev h;
   int64_t itc[2];
@@ -346,6 +351,10 @@ int mlmc_create(int device, const mlmc_model* model, void* cuda_stream, mlmc_ctx
   c->lev.resize(model->L + 1);
   int err = 0;
   Buf scratch, mm;
+  if ((err = c->bm.ensure(kSinCosTab * sizeof(double2) + 3 * kLogTab * sizeof(double))) == 0 &&
+      bm_tables_build(c->bm.as<double2>(), reinterpret_cast<double*>(c->bm.as<double2>() + kSinCosTab),
+                      c->st))
+    err = fail(MLMC_ERR_CUDA, "Box-Muller table kernel");
   for (int l = 0; l <= model->L && !err; ++l) {
     LevelTable& T = c->lev[l];
     T.m = model->m0 << l;
@@ -409,7 +418,7 @@ void mlmc_destroy(mlmc_ctx* c) {
     T.tw32.release();
   }
   for (Buf* b : {&c->W, &c->g, &c->ws, &c->qsys, &c->itsys, &c->oqf, &c->oqc, &c->oqg, &c->oit,
-                 &c->sums, &c->itacc, &c->g64})
+                 &c->sums, &c->itacc, &c->g64, &c->bm})
     b->release();
   delete c;
 }
@@ -560,6 +569,18 @@ int mlmc_philox_words(uint64_t seed, uint64_t level, uint64_t sample, uint64_t s
   if (philox_launch(seed, level, sample, stream, first_call, n_calls, out, (cudaStream_t)cuda_stream))
     return fail(MLMC_ERR_CUDA, "philox kernel");
   CUDA_TRY(cudaStreamSynchronize((cudaStream_t)cuda_stream));
+  return 0;
+}
+
+int mlmc_normals(mlmc_ctx* c, uint64_t seed, uint64_t level, uint64_t sample, uint64_t stream,
+                 uint64_t first_call, int64_t n_calls, double* out) {
+  if (!c || n_calls < 0 || (n_calls > 0 && !out)) return fail(MLMC_ERR_ARG, "bad argument");
+  CUDA_TRY(cudaSetDevice(c->device));
+  if (normals_launch(seed, level, sample, stream, first_call, n_calls, c->bm.as<double2>(),
+                     reinterpret_cast<const double*>(c->bm.as<double2>() + kSinCosTab), c->model.prec != 0,
+                     out, c->st))
+    return fail(MLMC_ERR_CUDA, "normals kernel");
+  CUDA_TRY(cudaStreamSynchronize(c->st));
   return 0;
 }
 

@@ -34,7 +34,20 @@ template <typename R>
 __device__ void block_fft_rows(Cplx<R>* s, int nrows, int M, int logM, const Cplx<R>* __restrict__ tw) {
   const int half = M >> 1;
   const int nb = nrows * half;
-  for (int st = 0; st < logM; ++st) {
+  // stages 0 and 1 together: their twiddles are 1 and -i (M >= 4)
+  const int nq = nrows * (M >> 2);
+  for (int t = threadIdx.x; t < nq; t += blockDim.x) {
+    Cplx<R>* x = s + 4 * t;  // rows are contiguous and M is a multiple of 4
+    const Cplx<R> x0 = x[0], x1 = x[1], x2 = x[2], x3 = x[3];
+    const Cplx<R> a0{x0.x + x1.x, x0.y + x1.y}, a1{x0.x - x1.x, x0.y - x1.y};
+    const Cplx<R> a2{x2.x + x3.x, x2.y + x3.y}, a3{x2.x - x3.x, x2.y - x3.y};
+    x[0] = Cplx<R>{a0.x + a2.x, a0.y + a2.y};
+    x[2] = Cplx<R>{a0.x - a2.x, a0.y - a2.y};
+    x[1] = Cplx<R>{a1.x + a3.y, a1.y - a3.x};
+    x[3] = Cplx<R>{a1.x - a3.y, a1.y + a3.x};
+  }
+  __syncthreads();
+  for (int st = 2; st < logM; ++st) {
     const int hs = 1 << st;
     const int tstride = half >> st;  // twiddle index step M / (2 hs)
     for (int t = threadIdx.x; t < nb; t += blockDim.x) {
@@ -147,6 +160,7 @@ __global__ void ce_rows_kernel(CeRowsArgs args, const R* __restrict__ scale,
   const uint64_t sample = (uint64_t)(args.first + sidx);
   const int q2_0 = rb * rows;
   const int halfM = M >> 1;
+  const BmTables tb{args.bm_sc, args.bm_lg};
   // one Philox call per pair of consecutive q1 (two complex normals)
   const int ncalls = rows * halfM;
   for (int t = threadIdx.x; t < ncalls; t += blockDim.x) {
@@ -156,8 +170,8 @@ __global__ void ce_rows_kernel(CeRowsArgs args, const R* __restrict__ scale,
     const uint64_t call = ((uint64_t)q2 * (uint64_t)M + (uint64_t)q1) >> 1;
     const Words4 w = philox4x64_10(call, sample, (uint64_t)args.level, kStreamField0 + f, args.seed);
     R re0, im0, re1, im1;
-    box_muller(uniform52(w.w0), uniform52(w.w1), re0, im0);
-    box_muller(uniform52(w.w2), uniform52(w.w3), re1, im1);
+    box_muller_tab(w.w0, w.w1, tb, re0, im0);
+    box_muller_tab(w.w2, w.w3, tb, re1, im1);
     const R s0 = scale[(int64_t)q2 * M + q1];
     const R s1 = scale[(int64_t)q2 * M + q1 + 1];
     s[r * M + brev_n(q1, logM)] = Cplx<R>{s0 * re0, s0 * im0};
@@ -241,6 +255,8 @@ static int ce_sample_impl(const CeLaunch& L, const R* scale, const void* tw, voi
   if (cols < 1) cols = 1;
   if (cols > L.m) cols = L.m;
   CeRowsArgs ra;
+  ra.bm_sc = L.bm_sc;
+  ra.bm_lg = L.bm_lg;
   ra.M = L.M; ra.logM = ilog2(L.M); ra.m = L.m; ra.rows_per_block = rows; ra.n_pairs = L.n_pairs;
   ra.level = L.level; ra.seed = L.seed; ra.first = L.first;
   CeColsArgs ca;
@@ -272,6 +288,26 @@ int ce_sample_fp64(const CeLaunch& L, const double* scale, const void* tw, void*
 int ce_sample_fp32(const CeLaunch& L, const float* scale, const void* tw, void* W, float* g,
                    cudaStream_t st) {
   return ce_sample_impl<float, float>(L, scale, tw, W, g, st);
+}
+
+__global__ void bm_tables_kernel(double2* sc, double* lg) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < kSinCosTab) {
+    double sv, cv;
+    sincospi(2.0 * (double)i / (double)kSinCosTab, &sv, &cv);
+    sc[i] = make_double2(cv, sv);
+  }
+  if (i < kLogTab) {
+    const double F = 0.5 + ((double)i + 0.5) / 256.0;
+    lg[3 * i] = F;
+    lg[3 * i + 1] = 1.0 / F;
+    lg[3 * i + 2] = log(F);
+  }
+}
+
+int bm_tables_build(double2* sc, double* lg, cudaStream_t st) {
+  bm_tables_kernel<<<(kSinCosTab + 255) / 256, 256, 0, st>>>(sc, lg);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 size_t ce_w_bytes_per_sample(int m, int M, int n_pairs, bool fp32) {

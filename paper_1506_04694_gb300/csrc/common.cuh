@@ -68,12 +68,94 @@ __device__ __forceinline__ void box_muller(double ua, double ub, double& re, dou
   im = rad * s;
 }
 
+// FP32 version for the mixed-precision field path.  The arguments are reduced
+// in FP64 first (both exactly): ln u = log1p(-(1 - u)) above 1/2, so that u
+// close to 1 keeps its distance from 1; 2 u = k + x with x in [-1/2, 1/2]
+// and k an integer, so the angle keeps FP32 accuracy (sincos pi (k + x) =
+// (-1)^k sincos pi x).  Absolute error of the normals ~1e-6.
 __device__ __forceinline__ void box_muller(double ua, double ub, float& re, float& im) {
-  const float rad = sqrtf(-2.0f * logf((float)ua));
+  const float lg = ua > 0.5 ? log1pf(-(float)(1.0 - ua)) : logf((float)ua);
+  const float rad = sqrtf(-2.0f * lg);
+  const double x2 = 2.0 * ub;
+  const double k = rint(x2);
   float s, c;
-  sincospif(2.0f * (float)ub, &s, &c);
+  sincospif((float)(x2 - k), &s, &c);
+  const float sg = ((long long)k & 1) ? -1.0f : 1.0f;
+  re = sg * rad * c;
+  im = sg * rad * s;
+}
+
+// ------------------------------------------- table-driven FP64 Box-Muller --
+// FP64 log and sincos(2 pi u) by table-driven argument reduction (the method
+// of P. T. P. Tang, "Table-driven implementation of the logarithm function
+// in IEEE floating-point arithmetic", ACM TOMS 16 (1990), and the analogous
+// reduction for the trigonometric functions), with Taylor polynomials on the
+// reduced interval.  Tables hold exact-argument values from the CUDA math
+// library, computed once per context (bm_tables_kernel):
+//   sc[j] = (cos(2 pi j/1024), sin(2 pi j/1024)), j < 1024;
+//   lg[3t .. 3t+2] = (F_t, 1/F_t, ln F_t), F_t = 1/2 + (t + 1/2)/256, t < 128.
+constexpr int kSinCosTab = 1024;
+constexpr int kLogTab = 128;
+
+struct BmTables {
+  const double2* sc;
+  const double* lg;
+};
+
+// ln u for u in (0, 1): u = 2^E v, v in [1/2, 1), v = F_t (1 + r) with
+// |r| <= 1/256 and ln(1 + r) from its Taylor series to r^7 (truncation
+// < 1e-20).  r = (v - F_t) / F_t is formed as the exact difference times the
+// rounded reciprocal, so the absolute error stays ~1e-19 near u = 1.
+__device__ __forceinline__ double tab_log01(double u, const double* __restrict__ lg) {
+  const long long bits = __double_as_longlong(u);
+  const int ex = (int)(bits >> 52);
+  const long long mant = bits & ((1LL << 52) - 1);
+  const int E = ex - 1022;
+  const double v = __longlong_as_double(mant | (1022LL << 52));
+  const int t = (int)(mant >> 45);
+  const double F = __ldg(lg + 3 * t), iF = __ldg(lg + 3 * t + 1), lF = __ldg(lg + 3 * t + 2);
+  const double r = (v - F) * iF;
+  double p = fma(1.0 / 7.0, r, -1.0 / 6.0);
+  p = fma(p, r, 1.0 / 5.0);
+  p = fma(p, r, -0.25);
+  p = fma(p, r, 1.0 / 3.0);
+  p = fma(p, r, -0.5);
+  const double l1 = fma(p, r * r, r);
+  return fma((double)E, 0.6931471805599453, lF + l1);
+}
+
+// (cos 2 pi u, sin 2 pi u) for u = ((w >> 12) + 1/2) 2^-52: u = j/1024 + b
+// with the nearest j (integer arithmetic on w, exact), theta = 2 pi b,
+// |theta| <= pi/1024, Taylor polynomials to theta^5 (truncation < 3e-18),
+// then the angle-addition formulas with the tabulated (cos, sin).
+__device__ __forceinline__ void tab_sincos2pi(uint64_t w, const double2* __restrict__ sc, double& c,
+                                              double& s) {
+  const long long K = (long long)(w >> 12);
+  const long long j = (K + (1LL << 41)) >> 42;
+  const long long D = K - (j << 42);
+  const double b = ((double)D + 0.5) * 0x1p-52;
+  const double th = b * 6.283185307179586;
+  const double t2 = th * th;
+  const double cm = t2 * fma(t2, 1.0 / 24.0, -0.5);              // cos(theta) - 1
+  const double sn = fma(th * t2, fma(t2, 1.0 / 120.0, -1.0 / 6.0), th);  // sin(theta)
+  const double2 cs = __ldg(sc + (j & (kSinCosTab - 1)));
+  c = cs.x + fma(cs.x, cm, -cs.y * sn);
+  s = cs.y + fma(cs.y, cm, cs.x * sn);
+}
+
+// Box-Muller pair from two words (same definition as box_muller()).
+__device__ __forceinline__ void box_muller_tab(uint64_t wa, uint64_t wb, const BmTables& tb, double& re,
+                                               double& im) {
+  const double rad = sqrt(-2.0 * tab_log01(uniform52(wa), tb.lg));
+  double c, s;
+  tab_sincos2pi(wb, tb.sc, c, s);
   re = rad * c;
   im = rad * s;
+}
+
+__device__ __forceinline__ void box_muller_tab(uint64_t wa, uint64_t wb, const BmTables&, float& re,
+                                               float& im) {
+  box_muller(uniform52(wa), uniform52(wb), re, im);
 }
 
 // ------------------------------------------------------------ reductions --

@@ -10,6 +10,8 @@ constexpr int MAX_LAYERS_DEV = 8;
 
 // ------------------------------------------------------------------- CE ---
 struct CeRowsArgs {
+  const double2* bm_sc;  // Box-Muller tables (common.cuh, BmTables)
+  const double* bm_lg;
   int M, logM, m, rows_per_block, n_pairs, level;
   uint64_t seed;
   int64_t first;     // sample index of chunk entry 0
@@ -23,6 +25,8 @@ struct CeColsArgs {
 };
 
 struct CeLaunch {
+  const double2* bm_sc;
+  const double* bm_lg;
   int M, m, n_pairs, n_layers, level;
   uint64_t seed;
   int64_t first, n_samples;
@@ -37,6 +41,8 @@ int ce_sample_fp64(const CeLaunch& L, const double* scale, const void* tw, void*
 int ce_sample_fp32(const CeLaunch& L, const float* scale, const void* tw, void* W, float* g,
                    cudaStream_t st);
 size_t ce_w_bytes_per_sample(int m, int M, int n_pairs, bool fp32);
+// Box-Muller tables: sc 1024 double2, lg 3*128 doubles.
+int bm_tables_build(double2* sc, double* lg, cudaStream_t st);
 
 // ---------------------------------------------------------------- solve ---
 // Where the permeability of a system comes from.
@@ -75,9 +81,21 @@ struct SolveArgs {
   double* p_out;       // optional pressure of fine systems [sample][j][i]
 };
 
+// Launch shape of the solver for one system size (solve.cu).
+struct SolvePlan {
+  int warp;              // one warp per system (else one block per system)
+  int threads;           // threads per block
+  int groups_per_block;  // systems solved side by side in one block
+  int blocks_per_sm;     // occupancy
+  int use_smem;          // workspace in shared memory (else global, ws_stride per group)
+  size_t ws_stride;      // bytes of workspace per group
+  size_t smem_bytes;     // dynamic shared memory per block
+};
+
 size_t solve_ws_bytes(int m, int prec);
-int solve_launch(const SolveArgs& a, int prec, int n_blocks, size_t smem_bytes, cudaStream_t st);
-int solve_blocks_per_sm(int m, int prec, size_t* smem_bytes, int* use_smem);
+int solve_plan(int m, int prec, SolvePlan* plan);
+// Global workspace (plan.use_smem == 0) must hold n_blocks * groups_per_block * ws_stride bytes.
+int solve_launch(const SolveArgs& a, int prec, const SolvePlan& plan, int n_blocks, cudaStream_t st);
 
 // --------------------------------------------------------------- reduce ---
 struct LevelSumsDev {
@@ -90,12 +108,18 @@ struct LevelSumsDev {
 int gather_launch(const double* q_sys, const int32_t* it_sys, int64_t n_samples, int n_coarse,
                   int cgv, int m, double* qf, double* qc, double* qcg, int32_t* iters, int64_t* it_acc,
                   cudaStream_t st);
+// Level sums in two launches (per-block partials, then a fixed-order
+// combine); ws must hold reduce_ws_bytes().
+size_t reduce_ws_bytes();
 int reduce_launch(const double* qf, const double* qc, const double* qcg, int64_t n, int cgv,
-                  const int64_t* it_acc, LevelSumsDev* out, cudaStream_t st);
+                  const int64_t* it_acc, LevelSumsDev* out, void* ws, cudaStream_t st);
 int philox_launch(uint64_t seed, uint64_t level, uint64_t sample, uint64_t stream,
                   uint64_t first_call, int64_t n_calls, uint64_t* out, cudaStream_t st);
 int interfaces_launch(const SolveArgs& a, int64_t n, double* eta, cudaStream_t st);
 int const_fields_launch(const SolveArgs& a, int64_t n, double* g, cudaStream_t st);
+int normals_launch(uint64_t seed, uint64_t level, uint64_t sample, uint64_t stream, uint64_t first_call,
+                   int64_t n_calls, const double2* sc, const double* lg, int fp32, double* out,
+                   cudaStream_t st);
 int f32_to_f64_launch(const float* in, double* out, int64_t n, cudaStream_t st);
 
 }  // namespace mlmc

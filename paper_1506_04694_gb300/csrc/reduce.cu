@@ -66,16 +66,25 @@ __device__ __forceinline__ void neu_merge(Neu& a, const Neu& b) {
   a.c = __dadd_rn(a.c, b.c);
 }
 
-constexpr int kRedThreads = 1024;
+constexpr int kRedThreads = 512;
+constexpr int kRedMaxBlocks = 256;
 
-__global__ void __launch_bounds__(kRedThreads) reduce_kernel(const double* qf, const double* qc,
-                                                             const double* qcg, int64_t n, int cgv,
-                                                             const int64_t* it_acc, LevelSumsDev* out) {
+struct RedPartial {
+  double s[10], c[10];
+  long long n, n_failed;
+};
+
+// Phase 1: block b sums the samples of its contiguous range with Neumaier
+// compensation, in a fixed order (threads strided, then a fixed tree).
+__global__ void __launch_bounds__(kRedThreads) reduce_partial_kernel(const double* qf, const double* qc,
+                                                                     const double* qcg, int64_t n, int cgv,
+                                                                     RedPartial* part) {
+  const int64_t lo = n * blockIdx.x / gridDim.x, hi = n * (blockIdx.x + 1) / gridDim.x;
   Neu acc[10];
 #pragma unroll
   for (int k = 0; k < 10; ++k) acc[k] = Neu{0.0, 0.0};
   long long nok = 0, nfail = 0;
-  for (int64_t s = threadIdx.x; s < n; s += blockDim.x) {
+  for (int64_t s = lo + threadIdx.x; s < hi; s += blockDim.x) {
     const double f = qf[s], c = qc[s];
     const double g = cgv ? qcg[s] : 0.0;
     if (!isfinite(f) || !isfinite(c) || !isfinite(g)) {
@@ -98,7 +107,6 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const double* qf, c
       neu_add(acc[9], __dmul_rn(yg, yg));
     }
   }
-  // fixed-order tree: within warps by shuffles, then across warps
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < 10; ++k) {
@@ -111,8 +119,8 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const double* qf, c
     nok += __shfl_down_sync(0xffffffffu, nok, o);
     nfail += __shfl_down_sync(0xffffffffu, nfail, o);
   }
-  __shared__ double ss[32][10], sc[32][10];
-  __shared__ long long sn[32], sf[32];
+  __shared__ double ss[kRedThreads / 32][10], sc[kRedThreads / 32][10];
+  __shared__ long long sn[kRedThreads / 32], sf[kRedThreads / 32];
   if (lane == 0) {
     for (int k = 0; k < 10; ++k) {
       ss[warp][k] = acc[k].s;
@@ -122,17 +130,38 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const double* qf, c
     sf[warp] = nfail;
   }
   __syncthreads();
+  if (threadIdx.x < 10) {
+    const int k = threadIdx.x;
+    Neu t{0.0, 0.0};
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) neu_merge(t, Neu{ss[w][k], sc[w][k]});
+    part[blockIdx.x].s[k] = t.s;
+    part[blockIdx.x].c[k] = t.c;
+  }
   if (threadIdx.x == 0) {
-    const int nw = blockDim.x >> 5;
     long long tn = 0, tf = 0;
-    for (int k = 0; k < 10; ++k) {
-      Neu t{0.0, 0.0};
-      for (int w = 0; w < nw; ++w) neu_merge(t, Neu{ss[w][k], sc[w][k]});
-      out->s[k] = __dadd_rn(t.s, t.c);
-    }
-    for (int w = 0; w < nw; ++w) {
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
       tn += sn[w];
       tf += sf[w];
+    }
+    part[blockIdx.x].n = tn;
+    part[blockIdx.x].n_failed = tf;
+  }
+}
+
+// Phase 2: one thread per sum combines the partials in block order.
+__global__ void reduce_final_kernel(const RedPartial* part, int nparts, const int64_t* it_acc,
+                                    LevelSumsDev* out) {
+  const int k = threadIdx.x;
+  if (k < 10) {
+    Neu t{0.0, 0.0};
+    for (int b = 0; b < nparts; ++b) neu_merge(t, Neu{part[b].s[k], part[b].c[k]});
+    out->s[k] = __dadd_rn(t.s, t.c);
+  }
+  if (k == 0) {
+    long long tn = 0, tf = 0;
+    for (int b = 0; b < nparts; ++b) {
+      tn += part[b].n;
+      tf += part[b].n_failed;
     }
     out->n = tn;
     out->n_failed = tf;
@@ -140,9 +169,15 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const double* qf, c
   }
 }
 
+size_t reduce_ws_bytes() { return sizeof(RedPartial) * kRedMaxBlocks; }
+
 int reduce_launch(const double* qf, const double* qc, const double* qcg, int64_t n, int cgv,
-                  const int64_t* it_acc, LevelSumsDev* out, cudaStream_t st) {
-  reduce_kernel<<<1, kRedThreads, 0, st>>>(qf, qc, qcg, n, cgv, it_acc, out);
+                  const int64_t* it_acc, LevelSumsDev* out, void* ws, cudaStream_t st) {
+  int64_t nb = (n + 8 * kRedThreads - 1) / (8 * kRedThreads);
+  nb = nb < 1 ? 1 : (nb > kRedMaxBlocks ? kRedMaxBlocks : nb);
+  RedPartial* part = reinterpret_cast<RedPartial*>(ws);
+  reduce_partial_kernel<<<(unsigned)nb, kRedThreads, 0, st>>>(qf, qc, qcg, n, cgv, part);
+  reduce_final_kernel<<<1, 32, 0, st>>>(part, (int)nb, it_acc, out);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -162,6 +197,35 @@ int philox_launch(uint64_t seed, uint64_t level, uint64_t sample, uint64_t strea
   if (n_calls <= 0) return 0;
   philox_kernel<<<(unsigned)((n_calls + 255) / 256), 256, 0, st>>>(seed, level, sample, stream,
                                                                    first_call, n_calls, out);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// The four normals of each call, by the same Box-Muller routine the field
+// kernels use (FP64 table-driven, or FP32 when fp32 != 0).
+__global__ void normals_kernel(uint64_t seed, uint64_t level, uint64_t sample, uint64_t stream,
+                               uint64_t first_call, int64_t n, BmTables tb, int fp32, double* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Words4 w = philox4x64_10(first_call + (uint64_t)i, sample, level, stream, seed);
+  if (fp32) {
+    float a, b, c, d;
+    box_muller_tab(w.w0, w.w1, tb, a, b);
+    box_muller_tab(w.w2, w.w3, tb, c, d);
+    out[4 * i] = a, out[4 * i + 1] = b, out[4 * i + 2] = c, out[4 * i + 3] = d;
+  } else {
+    double a, b, c, d;
+    box_muller_tab(w.w0, w.w1, tb, a, b);
+    box_muller_tab(w.w2, w.w3, tb, c, d);
+    out[4 * i] = a, out[4 * i + 1] = b, out[4 * i + 2] = c, out[4 * i + 3] = d;
+  }
+}
+
+int normals_launch(uint64_t seed, uint64_t level, uint64_t sample, uint64_t stream, uint64_t first_call,
+                   int64_t n_calls, const double2* sc, const double* lg, int fp32, double* out,
+                   cudaStream_t st) {
+  if (n_calls <= 0) return 0;
+  normals_kernel<<<(unsigned)((n_calls + 255) / 256), 256, 0, st>>>(seed, level, sample, stream, first_call,
+                                                                     n_calls, BmTables{sc, lg}, fp32, out);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -95,6 +95,28 @@ struct Level {
   T* f;     // right-hand side (level 0: CG r)
 };
 
+// Cooperating threads that solve one system: a whole thread block, or one
+// warp (small grids, no block barriers at all).
+struct BlockGroup {
+  __device__ __forceinline__ int rank() const { return threadIdx.x; }
+  __device__ __forceinline__ int size() const { return blockDim.x; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  template <typename T>
+  __device__ __forceinline__ T sum(T v, T* red, int& par) const {
+    return block_sum(v, red, par);
+  }
+};
+
+struct WarpGroup {
+  __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
+  __device__ __forceinline__ int size() const { return 32; }
+  __device__ __forceinline__ void sync() const { __syncwarp(); }
+  template <typename T>
+  __device__ __forceinline__ T sum(T v, T*, int&) const {
+    return warp_sum(v);
+  }
+};
+
 // (A v)_c = diag_c v_c - sum over the faces of T v_nbr (v_nbr = 0 outside:
 // Dirichlet faces carry T but no neighbour, no-flow faces carry T = 0).
 template <typename T>
@@ -112,11 +134,11 @@ __device__ __forceinline__ T apply_row(const Level<T>& L, const T* __restrict__ 
 
 // One red (color 0) or black (color 1) Gauss-Seidel half sweep; `zero_guess`
 // treats the other color as zero (first sweep of a cycle).
-template <typename T>
-__device__ __forceinline__ void rb_sweep(const Level<T>& L, int color, bool zero_guess) {
+template <typename T, typename G>
+__device__ __forceinline__ void rb_sweep(const G& g, const Level<T>& L, int color, bool zero_guess) {
   const int m = L.m, hm = m >> 1;
   const int nh = m * hm;
-  for (int h = threadIdx.x; h < nh; h += blockDim.x) {
+  for (int h = g.rank(); h < nh; h += g.size()) {
     const int j = h / hm;
     const int i = ((h - j * hm) << 1) + ((j + color) & 1);
     const int c = j * m + i;
@@ -130,42 +152,42 @@ __device__ __forceinline__ void rb_sweep(const Level<T>& L, int color, bool zero
     }
     L.e[c] = s * L.invd[c];
   }
-  __syncthreads();
+  g.sync();
 }
 
 // Coarse f = sum of the fine residuals f - A e over each 2x2 aggregate.
 // Called right after a black half sweep, which leaves the residual at the
 // black cells zero, so only the two red cells (2I, 2J), (2I+1, 2J+1) of the
 // aggregate contribute.
-template <typename T>
-__device__ __forceinline__ void restrict_residual(const Level<T>& F, const Level<T>& C) {
+template <typename T, typename G>
+__device__ __forceinline__ void restrict_residual(const G& g, const Level<T>& F, const Level<T>& C) {
   const int mc = C.m, m = F.m;
-  for (int cc = threadIdx.x; cc < mc * mc; cc += blockDim.x) {
+  for (int cc = g.rank(); cc < mc * mc; cc += g.size()) {
     const int J = cc / mc, I = cc - J * mc;
     const int i0 = 2 * I, j0 = 2 * J;
     const T r0 = F.f[j0 * m + i0] - apply_row(F, F.e, i0, j0);
     const T r1 = F.f[(j0 + 1) * m + i0 + 1] - apply_row(F, F.e, i0 + 1, j0 + 1);
     C.f[cc] = r0 + r1;
   }
-  __syncthreads();
+  g.sync();
 }
 
-template <typename T>
-__device__ __forceinline__ void prolong_add(const Level<T>& C, const Level<T>& F) {
+template <typename T, typename G>
+__device__ __forceinline__ void prolong_add(const G& g, const Level<T>& C, const Level<T>& F) {
   const int m = F.m, mc = C.m;
-  for (int c = threadIdx.x; c < m * m; c += blockDim.x) {
+  for (int c = g.rank(); c < m * m; c += g.size()) {
     const int j = c / m, i = c - j * m;
     F.e[c] += C.e[(j >> 1) * mc + (i >> 1)];
   }
-  __syncthreads();
+  g.sync();
 }
 
 // Coarse faces: mean of the two fine faces forming each coarse face.
-template <typename T>
-__device__ __forceinline__ void build_coarse(const Level<T>& F, const Level<T>& C) {
+template <typename T, typename G>
+__device__ __forceinline__ void build_coarse(const G& g, const Level<T>& F, const Level<T>& C) {
   const int m = F.m, mc = C.m;
   const int nfx = mc * (mc + 1);
-  for (int t = threadIdx.x; t < 2 * nfx; t += blockDim.x) {
+  for (int t = g.rank(); t < 2 * nfx; t += g.size()) {
     if (t < nfx) {
       const int J = t / (mc + 1), Ip = t - J * (mc + 1);
       C.tx[t] = T(0.5) * (F.tx[(2 * J) * (m + 1) + 2 * Ip] + F.tx[(2 * J + 1) * (m + 1) + 2 * Ip]);
@@ -175,106 +197,106 @@ __device__ __forceinline__ void build_coarse(const Level<T>& F, const Level<T>& 
       C.ty[u] = T(0.5) * (F.ty[(2 * Jp) * m + 2 * I] + F.ty[(2 * Jp) * m + 2 * I + 1]);
     }
   }
-  __syncthreads();
+  g.sync();
 }
 
-template <typename T>
-__device__ __forceinline__ void build_diag(const Level<T>& L) {
+template <typename T, typename G>
+__device__ __forceinline__ void build_diag(const G& g, const Level<T>& L) {
   const int m = L.m;
-  for (int c = threadIdx.x; c < m * m; c += blockDim.x) {
+  for (int c = g.rank(); c < m * m; c += g.size()) {
     const int j = c / m, i = c - j * m;
     const int rf = j * (m + 1) + i;
     const T d = (L.tx[rf] + L.tx[rf + 1]) + (L.ty[c] + L.ty[c + m]);
     L.diag[c] = d;
     L.invd[c] = T(1) / d;
   }
-  __syncthreads();
+  g.sync();
 }
 
 // Symmetric V-cycle: level-0 e <- B f.
-template <typename T>
-__device__ void vcycle(const Level<T>* lev, int nl) {
+template <typename T, typename G>
+__device__ void vcycle(const G& g, const Level<T>* lev, int nl) {
   for (int l = 0; l < nl - 1; ++l) {
-    rb_sweep(lev[l], 0, true);
-    rb_sweep(lev[l], 1, false);
-    restrict_residual(lev[l], lev[l + 1]);
+    rb_sweep(g, lev[l], 0, true);
+    rb_sweep(g, lev[l], 1, false);
+    restrict_residual(g, lev[l], lev[l + 1]);
   }
   {
     const Level<T>& Lc = lev[nl - 1];  // 1 x 1
-    if (threadIdx.x == 0) Lc.e[0] = Lc.f[0] * Lc.invd[0];
-    __syncthreads();
+    if (g.rank() == 0) Lc.e[0] = Lc.f[0] * Lc.invd[0];
+    g.sync();
   }
   for (int l = nl - 2; l >= 0; --l) {
-    prolong_add(lev[l + 1], lev[l]);
-    rb_sweep(lev[l], 1, false);
-    rb_sweep(lev[l], 0, false);
+    prolong_add(g, lev[l + 1], lev[l]);
+    rb_sweep(g, lev[l], 1, false);
+    rb_sweep(g, lev[l], 0, false);
   }
 }
 
 // Preconditioned CG on level-0 operator: x = 0 on entry, r = rhs.
 // Stops when r.r <= thr; returns iterations, status 0 converged, 1 hit the
 // cap, 2 breakdown (p.Ap <= 0 or not finite).
-template <typename T>
-__device__ int pcg(const Level<T>* lev, int nl, T* x, T* p, T* q, T thr, int max_it, T* red, int& par,
-                   int& status) {
+template <typename T, typename G>
+__device__ int pcg(const G& g, const Level<T>* lev, int nl, T* x, T* p, T* q, T thr, int max_it, T* red,
+                   int& par, int& status) {
   const Level<T>& L0 = lev[0];
   const int m = L0.m, n = m * m;
   T* r = L0.f;
   T* z = L0.e;
   T rr = T(0);
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+  for (int c = g.rank(); c < n; c += g.size()) {
     x[c] = T(0);
     rr += r[c] * r[c];
   }
-  rr = block_sum(rr, red, par);
+  rr = g.sum(rr, red, par);
   status = 1;
   if (rr <= thr) {
     status = 0;
     return 0;
   }
-  vcycle(lev, nl);
+  vcycle(g, lev, nl);
   T rz = T(0);
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+  for (int c = g.rank(); c < n; c += g.size()) {
     p[c] = z[c];
     rz += r[c] * z[c];
   }
-  rz = block_sum(rz, red, par);
+  rz = g.sum(rz, red, par);
   int it = 0;
   while (it < max_it) {
     ++it;
     T pq = T(0);
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    for (int c = g.rank(); c < n; c += g.size()) {
       const int j = c / m, i = c - j * m;
       const T v = apply_row(L0, p, i, j);
       q[c] = v;
       pq += p[c] * v;
     }
-    pq = block_sum(pq, red, par);
+    pq = g.sum(pq, red, par);
     if (!(pq > T(0)) || !isfinite(pq) || !isfinite(rz)) {
       status = 2;
       break;
     }
     const T alpha = rz / pq;
     rr = T(0);
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    for (int c = g.rank(); c < n; c += g.size()) {
       x[c] += alpha * p[c];
       const T rv = r[c] - alpha * q[c];
       r[c] = rv;
       rr += rv * rv;
     }
-    rr = block_sum(rr, red, par);
+    rr = g.sum(rr, red, par);
     if (rr <= thr) {
       status = 0;
       break;
     }
-    vcycle(lev, nl);
+    vcycle(g, lev, nl);
     T rzn = T(0);
-    for (int c = threadIdx.x; c < n; c += blockDim.x) rzn += r[c] * z[c];
-    rzn = block_sum(rzn, red, par);
+    for (int c = g.rank(); c < n; c += g.size()) rzn += r[c] * z[c];
+    rzn = g.sum(rzn, red, par);
     const T beta = rzn / rz;
     rz = rzn;
-    for (int c = threadIdx.x; c < n; c += blockDim.x) p[c] = z[c] + beta * p[c];
-    __syncthreads();
+    for (int c = g.rank(); c < n; c += g.size()) p[c] = z[c] + beta * p[c];
+    g.sync();
   }
   return it;
 }
@@ -318,228 +340,255 @@ __device__ void sample_layers(const SolveArgs& a, uint64_t sample, double* eta, 
 }
 
 constexpr int kMaxThreads = 512;
+constexpr int kWarpsPerBlock = 4;  // systems per block in warp mode
 
-// Threads per block for an m x m system: about one cell per thread on the
-// finest red-black half sweep up to 512.
-__host__ __device__ inline int solve_threads(int m) { return m <= 16 ? 128 : (m <= 64 ? 256 : 512); }
+// Per-system state shared by the threads of one group.
+template <typename T>
+struct GroupState {
+  Level<T> lev[kMaxLevels];
+  T *xv, *pv, *qv;
+  double *x64, *r64;
+  double eta[MAX_LAYERS_DEV], kc[MAX_LAYERS_DEV];
+  int nl;
+};
 
-template <bool MIXED>
-__global__ void __launch_bounds__(kMaxThreads) solve_kernel(SolveArgs a) {
+// Launch shape for an m x m system: small grids get one warp per system
+// (no block barriers), larger ones a block of about one thread per cell of
+// the finest red-black half sweep, up to 512.
+__host__ __device__ inline bool solve_warp_mode(int m) { return m <= 16; }
+__host__ __device__ inline int solve_threads(int m) {
+  return solve_warp_mode(m) ? 32 * kWarpsPerBlock : (m <= 64 ? 256 : 512);
+}
+
+// Assemble, solve and reduce the QoI of one system with group g.
+template <bool MIXED, typename G>
+__device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned char* base,
+                          GroupState<typename std::conditional<MIXED, float, double>::type>& gs,
+                          typename std::conditional<MIXED, float, double>::type* red, double* red64,
+                          int& par, int& m_prev) {
+  using T = typename std::conditional<MIXED, float, double>::type;
+  int64_t sidx;
+  int coarse = 0, ox = 0, oy = 0;
+  if (sys < a.n_samples) {
+    sidx = sys;
+  } else {
+    const int64_t t = sys - a.n_samples;
+    sidx = t / a.n_coarse;
+    const int o = (int)(t - sidx * a.n_coarse);
+    coarse = 1;
+    ox = o & 1;
+    oy = o >> 1;
+  }
+  const int m = coarse ? a.m >> 1 : a.m;
+  const int n = m * m;
+  const uint64_t sample = (uint64_t)(a.first + sidx);
+  if (m != m_prev) {  // level table of this system size
+    g.sync();
+    if (g.rank() == 0) {
+      size_t off[kLayoutSlots];
+      ws_layout(m, sizeof(T), MIXED, off);
+      int l = 0;
+      for (int ml = m;; ml >>= 1, ++l) {
+        Level<T>& L = gs.lev[l];
+        L.m = ml;
+        L.tx = reinterpret_cast<T*>(base + off[2 + kArrays * l + 0]);
+        L.ty = reinterpret_cast<T*>(base + off[2 + kArrays * l + 1]);
+        L.diag = reinterpret_cast<T*>(base + off[2 + kArrays * l + 2]);
+        L.invd = reinterpret_cast<T*>(base + off[2 + kArrays * l + 3]);
+        L.e = reinterpret_cast<T*>(base + off[2 + kArrays * l + 4]);
+        L.f = reinterpret_cast<T*>(base + off[2 + kArrays * l + 5]);
+        if (ml == 1) break;
+      }
+      gs.nl = l + 1;
+      gs.xv = reinterpret_cast<T*>(base + off[2 + kArrays * kMaxLevels + 0]);
+      gs.pv = reinterpret_cast<T*>(base + off[2 + kArrays * kMaxLevels + 1]);
+      gs.qv = reinterpret_cast<T*>(base + off[2 + kArrays * kMaxLevels + 2]);
+      gs.x64 = MIXED ? reinterpret_cast<double*>(base + off[0]) : reinterpret_cast<double*>(gs.xv);
+      gs.r64 = MIXED ? reinterpret_cast<double*>(base + off[1]) : reinterpret_cast<double*>(gs.lev[0].f);
+    }
+    g.sync();
+    m_prev = m;
+  }
+  const int nl = gs.nl;
+  T* xv = gs.xv;
+  T* pv = gs.pv;
+  T* qv = gs.qv;
+  double* x64 = gs.x64;
+  double* r64 = gs.r64;
+  const Level<T>* lev = gs.lev;
+  const Level<T>& L0 = lev[0];
+
+  // ---- layers and per-cell permeability (into r64 as scratch) ----
+  if (a.ksrc != KSRC_ARRAY) {
+    if (g.rank() == 0) sample_layers(a, sample, gs.eta, gs.kc);
+    g.sync();
+  }
+  const int n_if = a.n_layers - 1;
+  for (int c = g.rank(); c < n; c += g.size()) {
+    const int j = c / m, i = c - j * m;
+    double kk;
+    if (a.ksrc == KSRC_ARRAY) {
+      kk = a.k[sys * (int64_t)n + c];
+    } else {
+      // fine row of the value, and the row whose centre decides the layer
+      const int jf = coarse ? 2 * j + oy : j;
+      const int iff = coarse ? 2 * i + ox : i;
+      const double yc = (coarse && !a.cgv_on_k) ? ((double)j + 0.5) / (double)m
+                                                : ((double)jf + 0.5) / (double)a.m;
+      const int t = layer_at(gs.eta, n_if, yc);
+      if (a.ksrc == KSRC_CONST) {
+        kk = gs.kc[t];
+      } else if (MIXED) {
+        const float* gf = reinterpret_cast<const float*>(a.g);
+        kk = (double)expf(gf[((sidx * a.n_layers + t) * (int64_t)a.m + jf) * a.m + iff]);
+      } else {
+        const double* gd = reinterpret_cast<const double*>(a.g);
+        kk = exp(gd[((sidx * a.n_layers + t) * (int64_t)a.m + jf) * a.m + iff]);
+      }
+    }
+    r64[c] = kk;
+  }
+  g.sync();
+  // ---- faces (Eq. 3.3, harmonic averages; Dirichlet 2k; no-flow 0) ----
+  {
+    const int nfx = m * (m + 1);
+    for (int t = g.rank(); t < 2 * nfx; t += g.size()) {
+      if (t < nfx) {
+        const int j = t / (m + 1), ip = t - j * (m + 1);
+        T v;
+        if (ip == 0) v = T(2) * (T)r64[j * m];
+        else if (ip == m) v = T(2) * (T)r64[j * m + m - 1];
+        else {
+          const T ka = (T)r64[j * m + ip - 1], kb = (T)r64[j * m + ip];
+          v = T(2) * ka * kb / (ka + kb);
+        }
+        L0.tx[t] = v;
+      } else {
+        const int u = t - nfx;
+        const int jp = u / m, i = u - jp * m;
+        T v = T(0);
+        if (jp > 0 && jp < m) {
+          const T ka = (T)r64[(jp - 1) * m + i], kb = (T)r64[jp * m + i];
+          v = T(2) * ka * kb / (ka + kb);
+        }
+        L0.ty[u] = v;
+      }
+    }
+    g.sync();
+    build_diag(g, L0);
+  }
+  for (int l = 1; l < nl; ++l) {
+    build_coarse(g, lev[l - 1], lev[l]);
+    build_diag(g, lev[l]);
+  }
+  // ---- solve ----
+  int status = 1, iters = 0;
+  if (!MIXED) {
+    // r = b, bb = b.b; stop at r.r <= tol^2 b.b
+    T bb = T(0);
+    for (int c = g.rank(); c < n; c += g.size()) {
+      const int j = c / m, i = c - j * m;
+      const T bv = i == 0 ? L0.tx[j * (m + 1)] : T(0);
+      L0.f[c] = bv;
+      bb += bv * bv;
+    }
+    bb = g.sum(bb, red, par);
+    iters = pcg(g, lev, nl, xv, pv, qv, (T)(a.tol * a.tol) * bb, a.max_it, red, par, status);
+  } else {
+    // FP64 refinement: r64 = b - A64 x64 with A64 = the FP32 faces in FP64.
+    double bb = 0.0;
+    for (int c = g.rank(); c < n; c += g.size()) {
+      const int j = c / m, i = c - j * m;
+      const double bv = i == 0 ? (double)L0.tx[j * (m + 1)] : 0.0;
+      x64[c] = 0.0;
+      r64[c] = bv;
+      bb += bv * bv;
+    }
+    bb = g.sum(bb, red64, par);
+    double rr = bb;
+    const double thr = a.tol * a.tol * bb;
+    int sweeps = 0;
+    while (true) {
+      if (rr <= thr) {
+        status = 0;
+        break;
+      }
+      if (iters >= a.max_it || sweeps >= 40) {
+        status = 1;
+        break;
+      }
+      ++sweeps;
+      const double scl = sqrt(rr);
+      const double inv = 1.0 / scl;
+      T r32 = T(0);
+      for (int c = g.rank(); c < n; c += g.size()) {
+        const T v = (T)(r64[c] * inv);
+        L0.f[c] = v;
+        r32 += v * v;
+      }
+      r32 = g.sum(r32, red, par);
+      int st_in = 1;
+      const T thr_in = (T)(a.inner_tol * a.inner_tol) * r32;
+      const int it = pcg(g, lev, nl, xv, pv, qv, thr_in, a.max_it - iters, red, par, st_in);
+      iters += it;
+      // x64 += scl * d, then r64 = b - A64 x64 (FP64)
+      for (int c = g.rank(); c < n; c += g.size()) x64[c] += scl * (double)xv[c];
+      g.sync();
+      rr = 0.0;
+      for (int c = g.rank(); c < n; c += g.size()) {
+        const int j = c / m, i = c - j * m;
+        const int rf = j * (m + 1) + i;
+        const double tw = (double)L0.tx[rf], te = (double)L0.tx[rf + 1];
+        const double ts = (double)L0.ty[c], tn = (double)L0.ty[c + m];
+        double ax = ((tw + te) + (ts + tn)) * x64[c];
+        if (i > 0) ax -= tw * x64[c - 1];
+        if (i < m - 1) ax -= te * x64[c + 1];
+        if (j > 0) ax -= ts * x64[c - m];
+        if (j < m - 1) ax -= tn * x64[c + m];
+        const double bv = i == 0 ? tw : 0.0;
+        const double rv = bv - ax;
+        r64[c] = rv;
+        rr += rv * rv;
+      }
+      rr = g.sum(rr, red64, par);
+      if (it == 0 && st_in != 0) {  // inner solver made no progress
+        status = 2;
+        break;
+      }
+    }
+  }
+  // ---- outflow QoI and outputs ----
+  double qsum = 0.0;
+  for (int j = g.rank(); j < m; j += g.size()) qsum += (double)L0.tx[j * (m + 1) + m] * x64[j * m + m - 1];
+  qsum = g.sum(qsum, red64, par);
+  if (g.rank() == 0) {
+    a.q[sys] = status == 0 ? qsum : nan("");
+    if (a.iters) a.iters[sys] = iters;
+  }
+  if (a.p_out && !coarse)
+    for (int c = g.rank(); c < n; c += g.size()) a.p_out[sidx * (int64_t)n + c] = x64[c];
+  g.sync();
+}
+
+template <bool MIXED, bool WARP>
+__global__ void __launch_bounds__(WARP ? 32 * kWarpsPerBlock : kMaxThreads) solve_kernel(SolveArgs a) {
   using T = typename std::conditional<MIXED, float, double>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ T red[132];
-  __shared__ double red64[132];
-  __shared__ double eta_s[MAX_LAYERS_DEV], kc_s[MAX_LAYERS_DEV];
-  __shared__ Level<T> lev[kMaxLevels];
-  __shared__ int nl_s;
-  __shared__ T *xv_s, *pv_s, *qv_s;
-  __shared__ double *x64_s, *r64_s;
-  unsigned char* base = a.use_smem ? smem_raw : a.ws + (size_t)blockIdx.x * a.ws_stride;
+  constexpr int kGroups = WARP ? kWarpsPerBlock : 1;
+  __shared__ GroupState<T> gstate[kGroups];
+  __shared__ T red[WARP ? 1 : 132];
+  __shared__ double red64[WARP ? 1 : 132];
+  const int gid = WARP ? (int)(threadIdx.x >> 5) : 0;
+  unsigned char* base = a.use_smem ? smem_raw + (size_t)gid * a.ws_stride
+                                   : a.ws + ((size_t)blockIdx.x * kGroups + gid) * a.ws_stride;
   const int64_t n_sys = a.n_samples * (int64_t)(1 + a.n_coarse);
-  int par = 0;
-  int m_prev = -1;
-  for (int64_t sys = blockIdx.x; sys < n_sys; sys += gridDim.x) {
-    int64_t sidx;
-    int coarse = 0, ox = 0, oy = 0;
-    if (sys < a.n_samples) {
-      sidx = sys;
-    } else {
-      const int64_t t = sys - a.n_samples;
-      sidx = t / a.n_coarse;
-      const int o = (int)(t - sidx * a.n_coarse);
-      coarse = 1;
-      ox = o & 1;
-      oy = o >> 1;
-    }
-    const int m = coarse ? a.m >> 1 : a.m;
-    const int n = m * m;
-    const uint64_t sample = (uint64_t)(a.first + sidx);
-    if (m != m_prev) {  // level table of this system size, shared by the block
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        size_t off[kLayoutSlots];
-        ws_layout(m, sizeof(T), MIXED, off);
-        int l = 0;
-        for (int ml = m;; ml >>= 1, ++l) {
-          Level<T>& L = lev[l];
-          L.m = ml;
-          L.tx = reinterpret_cast<T*>(base + off[2 + kArrays * l + 0]);
-          L.ty = reinterpret_cast<T*>(base + off[2 + kArrays * l + 1]);
-          L.diag = reinterpret_cast<T*>(base + off[2 + kArrays * l + 2]);
-          L.invd = reinterpret_cast<T*>(base + off[2 + kArrays * l + 3]);
-          L.e = reinterpret_cast<T*>(base + off[2 + kArrays * l + 4]);
-          L.f = reinterpret_cast<T*>(base + off[2 + kArrays * l + 5]);
-          if (ml == 1) break;
-        }
-        nl_s = l + 1;
-        xv_s = reinterpret_cast<T*>(base + off[2 + kArrays * kMaxLevels + 0]);
-        pv_s = reinterpret_cast<T*>(base + off[2 + kArrays * kMaxLevels + 1]);
-        qv_s = reinterpret_cast<T*>(base + off[2 + kArrays * kMaxLevels + 2]);
-        x64_s = MIXED ? reinterpret_cast<double*>(base + off[0]) : reinterpret_cast<double*>(xv_s);
-        r64_s = MIXED ? reinterpret_cast<double*>(base + off[1]) : reinterpret_cast<double*>(lev[0].f);
-      }
-      __syncthreads();
-      m_prev = m;
-    }
-    const int nl = nl_s;
-    T* xv = xv_s;
-    T* pv = pv_s;
-    T* qv = qv_s;
-    double* x64 = x64_s;
-    double* r64 = r64_s;
-    const Level<T>& L0 = lev[0];
-
-    // ---- layers and per-cell permeability (into r64 as scratch) ----
-    if (a.ksrc != KSRC_ARRAY) {
-      if (threadIdx.x == 0) sample_layers(a, sample, eta_s, kc_s);
-      __syncthreads();
-    }
-    const int n_if = a.n_layers - 1;
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-      const int j = c / m, i = c - j * m;
-      double kk;
-      if (a.ksrc == KSRC_ARRAY) {
-        kk = a.k[sys * (int64_t)n + c];
-      } else {
-        // fine row of the value, and the row whose centre decides the layer
-        const int jf = coarse ? 2 * j + oy : j;
-        const int iff = coarse ? 2 * i + ox : i;
-        const double yc = (coarse && !a.cgv_on_k) ? ((double)j + 0.5) / (double)m
-                                                  : ((double)jf + 0.5) / (double)a.m;
-        const int t = layer_at(eta_s, n_if, yc);
-        if (a.ksrc == KSRC_CONST) {
-          kk = kc_s[t];
-        } else if (MIXED) {
-          const float* g = reinterpret_cast<const float*>(a.g);
-          kk = (double)expf(g[((sidx * a.n_layers + t) * (int64_t)a.m + jf) * a.m + iff]);
-        } else {
-          const double* g = reinterpret_cast<const double*>(a.g);
-          kk = exp(g[((sidx * a.n_layers + t) * (int64_t)a.m + jf) * a.m + iff]);
-        }
-      }
-      r64[c] = kk;
-    }
-    __syncthreads();
-    // ---- faces (Eq. 3.3, harmonic averages; Dirichlet 2k; no-flow 0) ----
-    {
-      const int nfx = m * (m + 1);
-      for (int t = threadIdx.x; t < 2 * nfx; t += blockDim.x) {
-        if (t < nfx) {
-          const int j = t / (m + 1), ip = t - j * (m + 1);
-          T v;
-          if (ip == 0) v = T(2) * (T)r64[j * m];
-          else if (ip == m) v = T(2) * (T)r64[j * m + m - 1];
-          else {
-            const T ka = (T)r64[j * m + ip - 1], kb = (T)r64[j * m + ip];
-            v = T(2) * ka * kb / (ka + kb);
-          }
-          L0.tx[t] = v;
-        } else {
-          const int u = t - nfx;
-          const int jp = u / m, i = u - jp * m;
-          T v = T(0);
-          if (jp > 0 && jp < m) {
-            const T ka = (T)r64[(jp - 1) * m + i], kb = (T)r64[jp * m + i];
-            v = T(2) * ka * kb / (ka + kb);
-          }
-          L0.ty[u] = v;
-        }
-      }
-      __syncthreads();
-      build_diag(L0);
-    }
-    for (int l = 1; l < nl; ++l) {
-      build_coarse(lev[l - 1], lev[l]);
-      build_diag(lev[l]);
-    }
-    // ---- solve ----
-    int status = 1, iters = 0;
-    if (!MIXED) {
-      // r = b, bb = b.b; stop at r.r <= tol^2 b.b
-      T bb = T(0);
-      for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        const int j = c / m, i = c - j * m;
-        const T bv = i == 0 ? L0.tx[j * (m + 1)] : T(0);
-        L0.f[c] = bv;
-        bb += bv * bv;
-      }
-      bb = block_sum(bb, red, par);
-      iters = pcg(lev, nl, xv, pv, qv, (T)(a.tol * a.tol) * bb, a.max_it, red, par, status);
-    } else {
-      // FP64 refinement: r64 = b - A64 x64 with A64 = the FP32 faces in FP64.
-      double bb = 0.0;
-      for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        const int j = c / m, i = c - j * m;
-        const double bv = i == 0 ? (double)L0.tx[j * (m + 1)] : 0.0;
-        x64[c] = 0.0;
-        r64[c] = bv;
-        bb += bv * bv;
-      }
-      bb = block_sum(bb, red64, par);
-      double rr = bb;
-      const double thr = a.tol * a.tol * bb;
-      int sweeps = 0;
-      while (true) {
-        if (rr <= thr) {
-          status = 0;
-          break;
-        }
-        if (iters >= a.max_it || sweeps >= 40) {
-          status = 1;
-          break;
-        }
-        ++sweeps;
-        const double scl = sqrt(rr);
-        const double inv = 1.0 / scl;
-        T r32 = T(0);
-        for (int c = threadIdx.x; c < n; c += blockDim.x) {
-          const T v = (T)(r64[c] * inv);
-          L0.f[c] = v;
-          r32 += v * v;
-        }
-        r32 = block_sum(r32, red, par);
-        int st_in = 1;
-        const T thr_in = (T)(a.inner_tol * a.inner_tol) * r32;
-        const int it = pcg(lev, nl, xv, pv, qv, thr_in, a.max_it - iters, red, par, st_in);
-        iters += it;
-        // x64 += scl * d, then r64 = b - A64 x64 (FP64)
-        for (int c = threadIdx.x; c < n; c += blockDim.x) x64[c] += scl * (double)xv[c];
-        __syncthreads();
-        rr = 0.0;
-        for (int c = threadIdx.x; c < n; c += blockDim.x) {
-          const int j = c / m, i = c - j * m;
-          const int rf = j * (m + 1) + i;
-          const double tw = (double)L0.tx[rf], te = (double)L0.tx[rf + 1];
-          const double ts = (double)L0.ty[c], tn = (double)L0.ty[c + m];
-          double ax = ((tw + te) + (ts + tn)) * x64[c];
-          if (i > 0) ax -= tw * x64[c - 1];
-          if (i < m - 1) ax -= te * x64[c + 1];
-          if (j > 0) ax -= ts * x64[c - m];
-          if (j < m - 1) ax -= tn * x64[c + m];
-          const double bv = i == 0 ? tw : 0.0;
-          const double rv = bv - ax;
-          r64[c] = rv;
-          rr += rv * rv;
-        }
-        rr = block_sum(rr, red64, par);
-        if (it == 0 && st_in != 0) {  // inner solver made no progress
-          status = 2;
-          break;
-        }
-      }
-    }
-    // ---- outflow QoI and outputs ----
-    double qsum = 0.0;
-    for (int j = threadIdx.x; j < m; j += blockDim.x)
-      qsum += (double)L0.tx[j * (m + 1) + m] * x64[j * m + m - 1];
-    qsum = block_sum(qsum, red64, par);
-    if (threadIdx.x == 0) {
-      a.q[sys] = status == 0 ? qsum : nan("");
-      if (a.iters) a.iters[sys] = iters;
-    }
-    if (a.p_out && !coarse)
-      for (int c = threadIdx.x; c < n; c += blockDim.x) a.p_out[sidx * (int64_t)n + c] = x64[c];
-    __syncthreads();
+  int par = 0, m_prev = -1;
+  const int64_t stride = (int64_t)gridDim.x * kGroups;
+  for (int64_t sys = (int64_t)blockIdx.x * kGroups + gid; sys < n_sys; sys += stride) {
+    if (WARP)
+      solve_one<MIXED>(WarpGroup(), a, sys, base, gstate[gid], red, red64, par, m_prev);
+    else
+      solve_one<MIXED>(BlockGroup(), a, sys, base, gstate[gid], red, red64, par, m_prev);
   }
 }
 
@@ -549,30 +598,41 @@ size_t solve_ws_bytes(int m, int prec) {
 
 static const size_t kSmemCap = 110 * 1024;
 
-int solve_blocks_per_sm(int m, int prec, size_t* smem_bytes, int* use_smem) {
-  const size_t ws = solve_ws_bytes(m, prec);
-  *use_smem = ws <= kSmemCap;
-  *smem_bytes = *use_smem ? ws : 0;
+template <bool MIXED, bool WARP>
+static int plan_impl(int m, SolvePlan* P) {
+  const size_t ws = solve_ws_bytes(m, MIXED);
+  P->warp = WARP;
+  P->threads = solve_threads(m);
+  P->groups_per_block = WARP ? kWarpsPerBlock : 1;
+  P->ws_stride = (ws + 255) & ~(size_t)255;
+  P->use_smem = P->ws_stride * P->groups_per_block <= kSmemCap;
+  P->smem_bytes = P->use_smem ? P->ws_stride * P->groups_per_block : 0;
+  cudaFuncSetAttribute(solve_kernel<MIXED, WARP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   int nb = 0;
-  cudaError_t e;
-  const int nt = solve_threads(m);
-  if (prec) {
-    cudaFuncSetAttribute(solve_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<true>, nt, *smem_bytes);
-  } else {
-    cudaFuncSetAttribute(solve_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<false>, nt, *smem_bytes);
-  }
-  if (e != cudaSuccess) return -1;
-  return nb < 1 ? 1 : nb;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<MIXED, WARP>, P->threads, P->smem_bytes) !=
+      cudaSuccess)
+    return -1;
+  P->blocks_per_sm = nb < 1 ? 1 : nb;
+  return 0;
 }
 
-int solve_launch(const SolveArgs& a, int prec, int n_blocks, size_t smem_bytes, cudaStream_t st) {
-  const int nt = solve_threads(a.m);
-  if (prec)
-    solve_kernel<true><<<n_blocks, nt, smem_bytes, st>>>(a);
-  else
-    solve_kernel<false><<<n_blocks, nt, smem_bytes, st>>>(a);
+int solve_plan(int m, int prec, SolvePlan* P) {
+  const bool w = solve_warp_mode(m);
+  if (prec) return w ? plan_impl<true, true>(m, P) : plan_impl<true, false>(m, P);
+  return w ? plan_impl<false, true>(m, P) : plan_impl<false, false>(m, P);
+}
+
+int solve_launch(const SolveArgs& a, int prec, const SolvePlan& P, int n_blocks, cudaStream_t st) {
+  SolveArgs b = a;
+  b.use_smem = P.use_smem;
+  b.ws_stride = P.ws_stride;
+  if (prec) {
+    if (P.warp) solve_kernel<true, true><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+    else solve_kernel<true, false><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+  } else {
+    if (P.warp) solve_kernel<false, true><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+    else solve_kernel<false, false><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -683,11 +743,10 @@ extern "C" int mlmc_solve_k_static(int device, int32_t m, int64_t n, const doubl
       }
       base = g_static_ptr[device];
     }
-    size_t smem = 0;
-    int use_smem = 0;
-    const int bpsm = solve_blocks_per_sm(m, prec, &smem, &use_smem);
+    SolvePlan P;
     int nsm = 0;
-    if (bpsm < 0 || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    if (solve_plan(m, prec, &P) ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
       rc = MLMC_ERR_CUDA;
       break;
     }
@@ -705,18 +764,18 @@ extern "C" int mlmc_solve_k_static(int device, int32_t m, int64_t n, const doubl
     a.q = q;
     a.iters = iters;
     a.p_out = p;
-    a.use_smem = use_smem;
-    int64_t nb = std::min<int64_t>(n, (int64_t)nsm * bpsm);
-    if (!use_smem) {
-      a.ws_stride = (solve_ws_bytes(m, prec) + 255) & ~(size_t)255;
-      if (a.ws_stride > kStaticScratchBytes) {  // m above the static maximum (512)
+    int64_t nb = std::min<int64_t>((n + P.groups_per_block - 1) / P.groups_per_block,
+                                   (int64_t)nsm * P.blocks_per_sm);
+    if (!P.use_smem) {
+      const size_t per_block = P.ws_stride * P.groups_per_block;
+      if (per_block > kStaticScratchBytes) {  // m above the static maximum (512)
         rc = MLMC_ERR_TOOBIG;
         break;
       }
-      nb = std::min<int64_t>(nb, (int64_t)(kStaticScratchBytes / a.ws_stride));
+      nb = std::min<int64_t>(nb, (int64_t)(kStaticScratchBytes / per_block));
       a.ws = reinterpret_cast<unsigned char*>(base);
     }
-    if (solve_launch(a, prec, (int)nb, smem, (cudaStream_t)cuda_stream)) rc = MLMC_ERR_CUDA;
+    if (solve_launch(a, prec, P, (int)nb, (cudaStream_t)cuda_stream)) rc = MLMC_ERR_CUDA;
   } while (0);
   cudaSetDevice(prev);
   return rc;

@@ -22,6 +22,29 @@ def test_philox_words_bit_exact(seed, level, sample, stream, first, n):
     assert np.array_equal(w, ref)
 
 
+@pytest.mark.parametrize("prec,atol", [(0, 2e-15), (1, 2e-6)])
+def test_normals_against_oracle(prec, atol):
+    # the field kernels' Box-Muller (table-driven FP64 log/sincos, or FP32)
+    # against the oracle's numpy log/cos/sin on a million calls, including
+    # uniforms next to 0 and 1 (the words with all high bits 0 or 1 come up
+    # among 2^22 draws only by chance, so the edge words are checked too)
+    torch, pk = need_gpu()
+    d = workloads.workload("lognormal_2layer_16to256", prec=prec)
+    n = 1 << 20
+    with pk.Context(d) as ctx:
+        z = ctx.normals(77, 3, 5, 2, 0, n).cpu().numpy()
+    ref = philox.call_normals(philox.stream_words(77, 3, 5, 2, np.arange(n, dtype=np.uint64)))
+    err = np.abs(z - ref)
+    assert err.max() <= atol * max(1.0, np.abs(ref).max()), err.max()
+    if prec == 0:
+        # the log part on its own: re^2 + im^2 = -2 ln u_a to ~1e-15 relative,
+        # ~1e-18 absolute as u_a -> 1 (the normal's absolute error stays ~1e-16)
+        u = philox.uniform(philox.stream_words(77, 3, 5, 2, np.arange(n, dtype=np.uint64)))
+        r2 = z[:, 0] ** 2 + z[:, 1] ** 2
+        ref2 = -2.0 * np.log(u[:, 0])
+        assert np.all(np.abs(r2 - ref2) <= 1e-15 * ref2 + 1e-18)
+
+
 @pytest.mark.parametrize("name", ["const_2layer_8to32", "lognormal_4layer_cgv_16to1024"])
 def test_interfaces_bit_exact(name):
     torch, pk = need_gpu()
