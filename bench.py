@@ -201,6 +201,20 @@ def config_block(args, d):
             "l2": "flushed between steps (256 MB device write)", "parallelism": "replicas%d" % args.gpus}
 
 
+def reduce_over_ranks(total_ms, n_total, device):
+    """Whole-job timing: the slowest rank's time and the samples of all ranks
+    (one replica per GPU; the only cross-rank communication of the benchmark)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(total_ms), float(n_total)
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(n_total)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(n.item())
+
+
 def compare(args):
     """Time-to-eps: the workload as configured (mixed precision + CGV) against
     plain FP64 batched MLMC without CGV at the same eps and levels."""
@@ -211,8 +225,11 @@ def compare(args):
     arms = {"mixed_cgv": dict(d), "plain_fp64": dict(d, prec=0, cgv=0)}
     out = {"compare": args.compare, "eps": d["eps"], "m_levels": [d["m0"] << l for l in range(d["L"] + 1)],
            "steps": args.steps, "warmup": args.warmup}
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     for name, md in arms.items():
-        ctx = pk.Context(md)
+        ctx = pk.Context(md, stream=stream)
+        ctx.autotune(seed=args.seed + 12345)
         for _ in range(args.warmup):
             ctx.estimate(md["eps"], args.seed, n_pilot=64, cost_model=0)
         torch.cuda.synchronize()
@@ -271,8 +288,11 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
+    # a non-default stream: lets the library capture each estimate round in a CUDA graph
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
     ctx = pk.Context(d, device=local, stream=stream)
+    tune = ctx.autotune(seed=args.seed + 12345)  # untimed set-up: launch plan per level
     eps = d["eps"]
     seed = args.seed + 7919 * rank
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
@@ -308,15 +328,7 @@ def main():
     ctx.profile(False)
     clk = clocks.stop()
     prof = ctx.profile_read()
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms, float(n_total)], dtype=torch.float64, device=dev)
-    if world > 1:
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_ms, n_all = float(tmax[0]), float(t[1])
-    else:
-        n_all = float(n_total)
+    total_ms, n_all = reduce_over_ranks(sum(step_ms), n_total, dev)
 
     # end to end through the host-buffer API: the estimate's per-level sample
     # counts run with per-sample results copied back to host memory
@@ -338,6 +350,8 @@ def main():
         return
     stage_ms = prof["ms"]
     dom = max(stage_ms, key=lambda k: stage_ms[k])
+    if stage_ms[dom] <= 0:
+        raise RuntimeError("no stage timing collected in the timed region")
     launches = int(sum(prof["launches"].values()))
     roof = None
     if dom == "solve" and d["prec"] == 0:
@@ -365,6 +379,8 @@ def main():
         "q_hat": est["q_hat"], "var_hat": est["var_hat"],
         "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
         "iters_per_cell_solve": prof["cell_iters"] / max(prof["cells"], 1.0),
+        "autotune": [{"m": d["m0"] << l, "threads": t["threads"], "warp": t["warp"],
+                      "cap_blocks_per_sm": t["cap_blocks_per_sm"]} for l, t in enumerate(tune)],
     }
     if not args.no_cpu_baseline:
         cores = min(host_cores(), 16)

@@ -153,6 +153,63 @@ MLMC_API int mlmc_level_batch_host(mlmc_ctx* ctx, int level, int64_t first, int6
 MLMC_API int mlmc_estimate(mlmc_ctx* ctx, double eps, uint64_t seed, int32_t n_pilot,
                   int32_t cost_model, mlmc_estimate_out* out);
 
+/* mlmc_estimate() with a cap on the number of top-up rounds (0 = pilot only);
+ * mlmc_estimate() is this call with max_rounds = 10.  After a call the
+ * context keeps the estimator state (per-level sums, costs, rounds, seed,
+ * eps) for mlmc_checkpoint(); after mlmc_resume() the next call with the same
+ * seed starts from the loaded state instead of a pilot (the Philox streams
+ * make the result identical to an uninterrupted run). */
+MLMC_API int mlmc_estimate_ex(mlmc_ctx* ctx, double eps, uint64_t seed, int32_t n_pilot, int32_t cost_model,
+                              int32_t max_rounds, mlmc_estimate_out* out);
+
+/* Write the estimator state of the last mlmc_estimate / _ex call to a text
+ * file (host path).  Errors: MLMC_ERR_ARG (no estimate yet, unwritable). */
+MLMC_API int mlmc_checkpoint(mlmc_ctx* ctx, const char* path);
+
+/* Load a state written by mlmc_checkpoint() for the same model; the next
+ * estimate continues from it.  Errors: MLMC_ERR_ARG (unreadable, other model). */
+MLMC_API int mlmc_resume(mlmc_ctx* ctx, const char* path);
+
+/* Levels 0 .. n_levels-1 in one call: samples first[l] .. first[l]+n[l]-1 of
+ * each level l (n[l] may be 0), queued back to back on the context stream
+ * with a single host synchronisation at the end; sums[l] (host array of
+ * n_levels) receives the level sums of Eq. 3.6 / Eq. 4.2 as in
+ * mlmc_level_batch().  use_graph != 0 captures the whole queue into one CUDA
+ * graph (kept and relaunched while the arguments repeat); it needs a context
+ * created on a non-default stream and is skipped while profiling is on (stage
+ * timing puts events between the launches).
+ * Per-sample values are not returned (use mlmc_level_batch for those).
+ * mlmc_estimate() runs its pilot and every top-up round through this call. */
+MLMC_API int mlmc_multilevel_batch(mlmc_ctx* ctx, int32_t n_levels, const int64_t* first, const int64_t* n,
+                                   uint64_t seed, int32_t use_graph, mlmc_level_sums* sums);
+
+/* Result of mlmc_autotune(), per level. */
+typedef struct mlmc_tune_report {
+  int32_t threads[MLMC_MAX_LEVELS];            /* threads per block chosen */
+  int32_t warp[MLMC_MAX_LEVELS];               /* 1: one warp per system */
+  int32_t cap_blocks_per_sm[MLMC_MAX_LEVELS];  /* 0: occupancy limit */
+  int32_t cluster[MLMC_MAX_LEVELS];            /* > 0: blocks of the cluster that solves one system */
+  int32_t candidates[MLMC_MAX_LEVELS];         /* plans timed */
+  double ms_default[MLMC_MAX_LEVELS];          /* ms per sample, default plan */
+  double ms_best[MLMC_MAX_LEVELS];             /* ms per sample, chosen plan */
+} mlmc_tune_report;
+
+/* Times the candidate launch plans of the solver (one warp, one block of
+ * 64/128/256/512 threads, or, for m >= 128, one thread-block cluster of 2, 4
+ * or 8 blocks per system; all resident blocks or one per SM) on a
+ * probe batch of each level (samples from index 2^40 on, so no sample of
+ * real use is consumed) and keeps the fastest for that level's solves.  The
+ * arithmetic of a system does not depend on the plan except for the
+ * summation order of the dot products.  rep: host pointer or NULL. */
+MLMC_API int mlmc_autotune(mlmc_ctx* ctx, uint64_t seed, mlmc_tune_report* rep);
+
+/* Fix the solver's launch plan of one level by hand (overrides
+ * mlmc_autotune): mode 0 = one block of `threads` (32..512, multiple of 32)
+ * per system, 1 = one warp per system, 2 = one thread-block cluster of
+ * `cluster` (2, 4, 8) blocks of 512 threads per system; mode < 0 restores
+ * the built-in default.  Errors: MLMC_ERR_ARG. */
+MLMC_API int mlmc_set_launch(mlmc_ctx* ctx, int level, int32_t mode, int32_t threads, int32_t cluster);
+
 /* Padding of level `level`: *M_out = M, and the smallest / largest raw
  * embedding eigenvalue before clipping (host pointers, any may be NULL). */
 MLMC_API int mlmc_ce_info(mlmc_ctx* ctx, int level, int32_t* M_out, double* lam_min, double* lam_max);

@@ -63,6 +63,13 @@ class ProfileStats(ctypes.Structure):
 STAGES = ("fields", "solve", "reduce")
 
 
+class TuneReport(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32 * MAX_LEVELS), ("warp", ctypes.c_int32 * MAX_LEVELS),
+                ("cap_blocks_per_sm", ctypes.c_int32 * MAX_LEVELS), ("cluster", ctypes.c_int32 * MAX_LEVELS),
+                ("candidates", ctypes.c_int32 * MAX_LEVELS),
+                ("ms_default", ctypes.c_double * MAX_LEVELS), ("ms_best", ctypes.c_double * MAX_LEVELS)]
+
+
 class MLMCError(RuntimeError):
     pass
 
@@ -80,6 +87,16 @@ EXPORTS = {
                                              ctypes.POINTER(LevelSums)]),
     "mlmc_estimate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_uint64, ctypes.c_int32,
                                      ctypes.c_int32, ctypes.POINTER(EstimateOut)]),
+    "mlmc_multilevel_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                             ctypes.POINTER(ctypes.c_int64), ctypes.c_uint64, ctypes.c_int32,
+                                             ctypes.POINTER(LevelSums)]),
+    "mlmc_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(TuneReport)]),
+    "mlmc_estimate_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_uint64, ctypes.c_int32,
+                                        ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(EstimateOut)]),
+    "mlmc_checkpoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "mlmc_resume": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "mlmc_set_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32]),
     "mlmc_ce_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "mlmc_philox_words": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
@@ -223,14 +240,49 @@ class Context:
         d["rc"] = rc
         return d, qf, qc, qg, it
 
-    def estimate(self, eps, seed, n_pilot=64, cost_model=0):
-        """mlmc_estimate: adaptive MLMC estimate with sampling error <= eps^2/2."""
+    def estimate(self, eps, seed, n_pilot=64, cost_model=0, max_rounds=None):
+        """mlmc_estimate (mlmc_estimate_ex with max_rounds): adaptive MLMC
+        estimate with sampling error <= eps^2/2."""
         out = EstimateOut()
-        rc = _check(lib().mlmc_estimate(self._h, eps, seed, n_pilot, cost_model, ctypes.byref(out)))
+        if max_rounds is None:
+            rc = _check(lib().mlmc_estimate(self._h, eps, seed, n_pilot, cost_model, ctypes.byref(out)))
+        else:
+            rc = _check(lib().mlmc_estimate_ex(self._h, eps, seed, n_pilot, cost_model, max_rounds,
+                                               ctypes.byref(out)))
         L = self.model.L + 1
         return {"q_hat": out.q_hat, "var_hat": out.var_hat, "N": list(out.N[:L]), "V": list(out.V[:L]),
                 "mean": list(out.mean[:L]), "C": list(out.C[:L]), "rounds": out.rounds,
                 "seconds": out.seconds, "sums": [out.sums[i].as_dict() for i in range(L)], "rc": rc}
+
+    def checkpoint(self, path):
+        """mlmc_checkpoint: write the last estimate's state to a file."""
+        _check(lib().mlmc_checkpoint(self._h, os.fsencode(path)), allow_failed=False)
+
+    def resume(self, path):
+        """mlmc_resume: the next estimate continues from a checkpoint file."""
+        _check(lib().mlmc_resume(self._h, os.fsencode(path)), allow_failed=False)
+
+    def multilevel_batch(self, n, seed, first=None, use_graph=True):
+        """mlmc_multilevel_batch: levels 0..len(n)-1 in one call; list of level-sum dicts."""
+        k = len(n)
+        first = first or [0] * k
+        S = (LevelSums * k)()
+        rc = _check(lib().mlmc_multilevel_batch(self._h, k, (ctypes.c_int64 * k)(*first), (ctypes.c_int64 * k)(*n),
+                                                seed, 1 if use_graph else 0, S))
+        out = [S[i].as_dict() for i in range(k)]
+        for o in out:
+            o["rc"] = rc
+        return out
+
+    def autotune(self, seed=0):
+        """mlmc_autotune: time the solver's launch plans per level, keep the fastest."""
+        r = TuneReport()
+        _check(lib().mlmc_autotune(self._h, seed, ctypes.byref(r)), allow_failed=False)
+        L = self.model.L + 1
+        return [{"threads": r.threads[i], "warp": r.warp[i], "cap_blocks_per_sm": r.cap_blocks_per_sm[i],
+                 "cluster": r.cluster[i],
+                 "candidates": r.candidates[i], "ms_per_sample_default": r.ms_default[i],
+                 "ms_per_sample_best": r.ms_best[i]} for i in range(L)]
 
     def profile(self, enable=True):
         """mlmc_profile: reset and start (or stop) per-stage event timing."""
@@ -243,6 +295,10 @@ class Context:
         return {"launches": dict(zip(STAGES, p.launches)), "ms": dict(zip(STAGES, p.ms)),
                 "cell_iters": p.cell_iters, "cells": p.cells, "fft_row_points": p.fft_row_points,
                 "fft_col_points": p.fft_col_points, "samples": p.samples}
+
+    def set_launch(self, level, mode, threads=256, cluster=0):
+        """mlmc_set_launch: fix a level's solver launch (0 block, 1 warp, 2 cluster; <0 default)."""
+        _check(lib().mlmc_set_launch(self._h, level, mode, threads, cluster), allow_failed=False)
 
     def ce_info(self, level):
         M = ctypes.c_int32()

@@ -1,6 +1,7 @@
 // C ABI of the MLMC level-batch library: context, level batches, the adaptive
 // estimator and stage outputs.  Declarations and contracts: include/mlmc.h.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -31,11 +32,16 @@ int fail(int code, const std::string& what) {
                   std::string(#expr) + ": " + cudaGetErrorString(_e));                    \
   } while (0)
 
+// Bumped on every device (re)allocation: a kept CUDA graph is only valid
+// while no buffer it points into has moved.
+std::atomic<long long> g_alloc_generation{0};
+
 struct Buf {
   void* p = nullptr;
   size_t cap = 0;
   int ensure(size_t bytes) {
     if (bytes <= cap) return 0;
+    ++g_alloc_generation;
     if (p) cudaFree(p);
     p = nullptr;
     cap = 0;
@@ -70,6 +76,18 @@ constexpr size_t kChunkBudget = size_t(2) << 30;  // bytes of per-sample buffers
 
 }  // namespace
 
+// A pair of events bracketing one stage (profiling).
+struct StagePend {
+  int stage, launches;
+  cudaEvent_t a, b;
+};
+
+// Device results of one enqueued level range, copied to pinned host memory.
+struct HostLevel {
+  LevelSumsDev s;
+  int64_t itc[2];
+};
+
 struct mlmc_ctx {
   int device = 0;
   cudaStream_t st = nullptr;
@@ -79,6 +97,27 @@ struct mlmc_ctx {
   Buf W, g, ws, qsys, itsys, oqf, oqc, oqg, oit, sums, itacc, g64, bm;
   bool prof_on = false;
   mlmc_profile_stats prof{};
+  // per-level slots of the multilevel batch (outputs, sums, iteration counters)
+  struct Slot {
+    Buf qf, qc, qg, sums, itacc;
+  } slot[MLMC_MAX_LEVELS];
+  HostLevel* host = nullptr;  // pinned, MLMC_MAX_LEVELS + 1 entries (last: single-level calls)
+  // launch plans chosen by mlmc_autotune(), per level
+  SolvePlan tuned[MLMC_MAX_LEVELS];
+  bool tuned_ok[MLMC_MAX_LEVELS] = {};
+  // estimator state: of the last estimate (for mlmc_checkpoint) and a loaded
+  // one that the next estimate continues from (mlmc_resume)
+  struct EstState {
+    bool valid = false;
+    double eps = 0;
+    uint64_t seed = 0;
+    int cost_model = 0, rounds = 0;
+    std::vector<mlmc_level_sums> S;
+    std::vector<double> C;
+  } last_est, resume_est;
+  // last captured multilevel graph and the arguments it was captured with
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<int64_t> gkey;
 };
 
 namespace {
@@ -178,19 +217,20 @@ int64_t chunk_samples(const mlmc_ctx* c, int level) {
 constexpr size_t kWsBudget = size_t(16) << 30;
 
 // Solve the systems of one chunk; results into c->qsys / c->itsys.
-int run_solves(mlmc_ctx* c, SolveArgs a, int64_t n_samples, int nc, int64_t max_rows) {
+int run_solves(mlmc_ctx* c, SolveArgs a, int64_t n_samples, int nc, int64_t max_rows,
+               const SolvePlan* plan = nullptr) {
   const int prec = c->model.prec;
   a.n_samples = n_samples;
   a.n_coarse = nc;
   SolvePlan P;
-  if (solve_plan(a.m, prec, &P)) return fail(MLMC_ERR_CUDA, "occupancy query failed");
+  if (plan) P = *plan;
+  else if (solve_plan(a.m, prec, &P)) return fail(MLMC_ERR_CUDA, "occupancy query failed");
   const int64_t n_sys = n_samples * (1 + nc);
-  int64_t nb = std::min<int64_t>((n_sys + P.groups_per_block - 1) / P.groups_per_block,
-                                 (int64_t)c->nsm * P.blocks_per_sm);
+  const int64_t cap = P.use_smem ? 0 : (int64_t)(kWsBudget / P.ws_stride);
+  int64_t nb = 0;
+  const int64_t groups = solve_groups(P, n_sys, c->nsm, cap, &nb);
   if (!P.use_smem) {
-    const size_t per_block = P.ws_stride * P.groups_per_block;
-    nb = std::max<int64_t>(1, std::min<int64_t>(nb, (int64_t)(kWsBudget / per_block)));
-    if (int e = c->ws.ensure(per_block * nb)) return e;
+    if (int e = c->ws.ensure(P.ws_stride * groups)) return e;
     a.ws = c->ws.as<unsigned char>();
   }
   if (int e = c->qsys.ensure((size_t)std::max<int64_t>(n_sys, max_rows) * 8)) return e;
@@ -216,23 +256,20 @@ struct StageTimer {
   void stop(int launches) {
     if (!c->prof_on) return;
     cudaEventRecord(e1, c->st);
-    c->prof.launches[stage] += launches;
-    pending().push_back({stage, e0, e1});
+    pending().push_back({stage, launches, e0, e1});
     e0 = e1 = nullptr;
   }
-  struct Pend {
-    int stage;
-    cudaEvent_t a, b;
-  };
-  static std::vector<Pend>& pending() {
-    static thread_local std::vector<Pend> v;
+  static std::vector<StagePend>& pending() {
+    static thread_local std::vector<StagePend> v;
     return v;
   }
-  // after a stream synchronisation: fold the elapsed times into the counters
+  // after a stream synchronisation: fold elapsed times and launch counts into
+  // the counters
   static void collect(mlmc_ctx* c) {
     for (auto& p : pending()) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) c->prof.ms[p.stage] += ms;
+      c->prof.launches[p.stage] += p.launches;
       cudaEventDestroy(p.a);
       cudaEventDestroy(p.b);
     }
@@ -244,14 +281,17 @@ double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-int level_batch_impl(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t seed, double* qf,
-                     double* qc, double* qcg, int32_t* iters, mlmc_level_sums* sums) {
+// Queue samples first .. first+n-1 of `level` on the context stream: fields,
+// solves and gathers chunk by chunk, then the level reduction into sums_dev
+// (256 bytes of sums + the reduction partials) and an asynchronous copy of
+// the sums and iteration counters into *host.  No host synchronisation.
+int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t seed, double* qf, double* qc,
+                  double* qcg, int32_t* iters, unsigned char* sums_dev, int64_t* itacc, HostLevel* host) {
   const mlmc_model& md = c->model;
   const int nc = n_coarse(md, level);
   const int64_t chunk = chunk_samples(c, level);
-  if (int e = c->itacc.ensure(2 * sizeof(int64_t))) return e;
-  if (int e = c->sums.ensure(256 + reduce_ws_bytes())) return e;  // sums at 0, partials at 256
-  CUDA_TRY(cudaMemsetAsync(c->itacc.p, 0, 2 * sizeof(int64_t), c->st));
+  const SolvePlan* plan = c->tuned_ok[level] ? &c->tuned[level] : nullptr;
+  CUDA_TRY(cudaMemsetAsync(itacc, 0, 2 * sizeof(int64_t), c->st));
   const int m = md.m0 << level;
   const int M = c->lev[level].M;
   for (int64_t c0 = 0; c0 < n; c0 += chunk) {
@@ -269,12 +309,12 @@ int level_batch_impl(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t 
     }
     {
       StageTimer t(c, 1);
-      if (int e = run_solves(c, a, cn, nc, 0)) return e;
+      if (int e = run_solves(c, a, cn, nc, 0, plan)) return e;
       t.stop(1);
     }
     StageTimer t(c, 2);
     if (gather_launch(c->qsys.as<double>(), c->itsys.as<int32_t>(), cn, nc, md.cgv, m, qf + c0,
-                      qc + c0, qcg + c0, iters ? iters + c0 : nullptr, c->itacc.as<int64_t>(), c->st))
+                      qc + c0, qcg + c0, iters ? iters + c0 : nullptr, itacc, c->st))
       return fail(MLMC_ERR_CUDA, "gather kernel");
     t.stop(1);
     if (c->prof_on) {
@@ -284,27 +324,151 @@ int level_batch_impl(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t 
   }
   {
     StageTimer t(c, 2);
-    if (reduce_launch(qf, qc, qcg, n, md.cgv != 0, c->itacc.as<int64_t>(), c->sums.as<LevelSumsDev>(),
-                      c->sums.as<unsigned char>() + 256, c->st))
+    if (reduce_launch(qf, qc, qcg, n, md.cgv != 0, itacc, reinterpret_cast<LevelSumsDev*>(sums_dev),
+                      sums_dev + 256, c->st))
       return fail(MLMC_ERR_CUDA, "reduce kernel");
     t.stop(2);
   }
-  LevelSumsDev h;
-  int64_t itc[2];
-  CUDA_TRY(cudaMemcpyAsync(&h, c->sums.p, sizeof(h), cudaMemcpyDeviceToHost, c->st));
-  CUDA_TRY(cudaMemcpyAsync(itc, c->itacc.p, sizeof(itc), cudaMemcpyDeviceToHost, c->st));
-  CUDA_TRY(cudaStreamSynchronize(c->st));
-  if (c->prof_on) {
-    StageTimer::collect(c);
-    c->prof.cell_iters += (double)itc[1];
-  }
-  sums->n = h.n;
-  sums->n_failed = h.n_failed;
-  sums->iters_total = h.iters;
+  CUDA_TRY(cudaMemcpyAsync(&host->s, sums_dev, sizeof(LevelSumsDev), cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(cudaMemcpyAsync(host->itc, itacc, sizeof(host->itc), cudaMemcpyDeviceToHost, c->st));
+  return 0;
+}
+
+// After the stream reached the copies of enqueue_level(): fill the sums.
+int finish_level(mlmc_ctx* c, const HostLevel& h, mlmc_level_sums* sums) {
+  const mlmc_model& md = c->model;
+  if (c->prof_on) c->prof.cell_iters += (double)h.itc[1];
+  sums->n = h.s.n;
+  sums->n_failed = h.s.n_failed;
+  sums->iters_total = h.s.iters;
   double* dst[10] = {&sums->s_qf, &sums->s_qf2, &sums->s_qc, &sums->s_qc2, &sums->s_y,
                      &sums->s_y2, &sums->s_qcg, &sums->s_qcg2, &sums->s_yg, &sums->s_yg2};
-  for (int k = 0; k < 10; ++k) *dst[k] = md.cgv || k < 6 ? h.s[k] : 0.0;
-  return h.n_failed ? MLMC_SOME_FAILED : MLMC_OK;
+  for (int k = 0; k < 10; ++k) *dst[k] = md.cgv || k < 6 ? h.s.s[k] : 0.0;
+  return h.s.n_failed ? MLMC_SOME_FAILED : MLMC_OK;
+}
+
+int level_batch_impl(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t seed, double* qf,
+                     double* qc, double* qcg, int32_t* iters, mlmc_level_sums* sums) {
+  if (int e = c->itacc.ensure(2 * sizeof(int64_t))) return e;
+  if (int e = c->sums.ensure(256 + reduce_ws_bytes())) return e;  // sums at 0, partials at 256
+  HostLevel* h = c->host + MLMC_MAX_LEVELS;
+  if (int e = enqueue_level(c, level, first, n, seed, qf, qc, qcg, iters, c->sums.as<unsigned char>(),
+                            c->itacc.as<int64_t>(), h))
+    return e;
+  CUDA_TRY(cudaStreamSynchronize(c->st));
+  if (c->prof_on) StageTimer::collect(c);
+  return finish_level(c, *h, sums);
+}
+
+// Allocate, outside any stream capture, every buffer a range of n samples of
+// `level` will touch.
+int prepare_level(mlmc_ctx* c, int level, int64_t n) {
+  const mlmc_model& md = c->model;
+  const int m = md.m0 << level;
+  const bool f32 = md.prec != 0;
+  const int nc = n_coarse(md, level);
+  const int64_t cn = std::min<int64_t>(n, chunk_samples(c, level));
+  if (md.k_kind == 1) {
+    if (int e = c->W.ensure(ce_w_bytes_per_sample(m, c->lev[level].M, n_pairs(md), f32) * cn)) return e;
+    if (int e = c->g.ensure((size_t)cn * md.n_layers * m * m * (f32 ? 4 : 8))) return e;
+  }
+  SolvePlan P;
+  if (c->tuned_ok[level]) P = c->tuned[level];
+  else if (solve_plan(m, md.prec, &P)) return fail(MLMC_ERR_CUDA, "occupancy query failed");
+  const int64_t n_sys = cn * (1 + nc);
+  if (!P.use_smem) {
+    int64_t nb = 0;
+    const int64_t groups = solve_groups(P, n_sys, c->nsm, (int64_t)(kWsBudget / P.ws_stride), &nb);
+    if (int e = c->ws.ensure(P.ws_stride * groups)) return e;
+  }
+  if (int e = c->qsys.ensure((size_t)n_sys * 8)) return e;
+  if (int e = c->itsys.ensure((size_t)n_sys * 4)) return e;
+  auto& S = c->slot[level];
+  if (int e = S.qf.ensure((size_t)n * 8)) return e;
+  if (int e = S.qc.ensure((size_t)n * 8)) return e;
+  if (int e = S.qg.ensure((size_t)n * 8)) return e;
+  if (int e = S.sums.ensure(256 + reduce_ws_bytes())) return e;
+  if (int e = S.itacc.ensure(2 * sizeof(int64_t))) return e;
+  return 0;
+}
+
+// All levels' ranges queued back to back with one host synchronisation;
+// with use_graph the queue is captured once into a CUDA graph (kept for the
+// next call with the same arguments) and launched as one graph.
+int multilevel_impl(mlmc_ctx* c, int n_levels, const int64_t* first, const int64_t* n, uint64_t seed,
+                    bool use_graph, mlmc_level_sums* sums) {
+  for (int l = 0; l < n_levels; ++l)
+    if (n[l] > 0)
+      if (int e = prepare_level(c, l, n[l])) return e;
+  auto enqueue_all = [&]() -> int {
+    for (int l = 0; l < n_levels; ++l) {
+      if (n[l] <= 0) continue;
+      auto& S = c->slot[l];
+      if (int e = enqueue_level(c, l, first[l], n[l], seed, S.qf.as<double>(), S.qc.as<double>(),
+                                S.qg.as<double>(), nullptr, S.sums.as<unsigned char>(), S.itacc.as<int64_t>(),
+                                c->host + l))
+        return e;
+    }
+    return 0;
+  };
+  // stage timing needs events between the launches, so profiling runs ungraphed
+  const bool graph = use_graph && c->st != nullptr && !c->prof_on;
+  if (graph) {
+    std::vector<int64_t> key = {(int64_t)n_levels, (int64_t)seed, (int64_t)g_alloc_generation.load()};
+    for (int l = 0; l < n_levels; ++l)
+      key.push_back(c->tuned_ok[l] ? ((int64_t)c->tuned[l].threads << 16) + (c->tuned[l].cluster << 8) +
+                                         (c->tuned[l].warp << 4) + c->tuned[l].cap_blocks_per_sm
+                                   : -1);
+    for (int l = 0; l < n_levels; ++l) {
+      key.push_back(first[l]);
+      key.push_back(n[l]);
+    }
+    if (!c->gexec || key != c->gkey) {
+      if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+      }
+      CUDA_TRY(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeRelaxed));
+      const int e = enqueue_all();
+      cudaGraph_t gr = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(c->st, &gr);
+      if (e) {
+        if (gr) cudaGraphDestroy(gr);
+        return e;
+      }
+      if (ce != cudaSuccess) return fail(MLMC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+      const cudaError_t ie = cudaGraphInstantiate(&c->gexec, gr, 0);
+      cudaGraphDestroy(gr);
+      if (ie != cudaSuccess) {
+        c->gexec = nullptr;
+        return fail(MLMC_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ie));
+      }
+      c->gkey = key;
+    }
+    CUDA_TRY(cudaGraphLaunch(c->gexec, c->st));
+    CUDA_TRY(cudaStreamSynchronize(c->st));
+  } else {
+    if (int e = enqueue_all()) return e;
+    CUDA_TRY(cudaStreamSynchronize(c->st));
+    if (c->prof_on) StageTimer::collect(c);
+  }
+  int rc = MLMC_OK;
+  for (int l = 0; l < n_levels; ++l) {
+    std::memset(&sums[l], 0, sizeof(sums[l]));
+    if (n[l] > 0) rc |= finish_level(c, c->host[l], &sums[l]);
+  }
+  return rc;
+}
+
+void add_sums(mlmc_level_sums& S, const mlmc_level_sums& add) {
+  S.n += add.n;
+  S.n_failed += add.n_failed;
+  S.iters_total += add.iters_total;
+  S.seconds += add.seconds;
+  double* a[10] = {&S.s_qf, &S.s_qf2, &S.s_qc, &S.s_qc2, &S.s_y, &S.s_y2, &S.s_qcg, &S.s_qcg2, &S.s_yg, &S.s_yg2};
+  const double* b[10] = {&add.s_qf, &add.s_qf2, &add.s_qc, &add.s_qc2, &add.s_y,
+                         &add.s_y2, &add.s_qcg, &add.s_qcg2, &add.s_yg, &add.s_yg2};
+  for (int k = 0; k < 10; ++k) *a[k] += *b[k];
 }
 
 int ensure_outputs(mlmc_ctx* c, int64_t n) {
@@ -351,6 +515,11 @@ int mlmc_create(int device, const mlmc_model* model, void* cuda_stream, mlmc_ctx
   c->lev.resize(model->L + 1);
   int err = 0;
   Buf scratch, mm;
+  if (cudaMallocHost(&c->host, sizeof(HostLevel) * (MLMC_MAX_LEVELS + 1)) != cudaSuccess) {
+    c->host = nullptr;
+    delete c;
+    return fail(MLMC_ERR_NOMEM, "pinned host buffer");
+  }
   if ((err = c->bm.ensure(kSinCosTab * sizeof(double2) + 3 * kLogTab * sizeof(double))) == 0 &&
       bm_tables_build(c->bm.as<double2>(), reinterpret_cast<double*>(c->bm.as<double2>() + kSinCosTab),
                       c->st))
@@ -420,6 +589,10 @@ void mlmc_destroy(mlmc_ctx* c) {
   for (Buf* b : {&c->W, &c->g, &c->ws, &c->qsys, &c->itsys, &c->oqf, &c->oqc, &c->oqg, &c->oit,
                  &c->sums, &c->itacc, &c->g64, &c->bm})
     b->release();
+  for (auto& S : c->slot)
+    for (Buf* b : {&S.qf, &S.qc, &S.qg, &S.sums, &S.itacc}) b->release();
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->host) cudaFreeHost(c->host);
   delete c;
 }
 
@@ -464,23 +637,46 @@ int mlmc_level_batch_host(mlmc_ctx* c, int level, int64_t first, int64_t n, uint
   return r;
 }
 
-int mlmc_estimate(mlmc_ctx* c, double eps, uint64_t seed, int32_t n_pilot, int32_t cost_model,
-                  mlmc_estimate_out* out) {
+int mlmc_estimate_ex(mlmc_ctx* c, double eps, uint64_t seed, int32_t n_pilot, int32_t cost_model,
+                     int32_t max_rounds, mlmc_estimate_out* out) {
   if (!c || !out) return fail(MLMC_ERR_ARG, "null argument");
-  if (!(eps > 0) || n_pilot < 2) return fail(MLMC_ERR_ARG, "eps must be > 0 and n_pilot >= 2");
+  if (!(eps > 0) || n_pilot < 2 || max_rounds < 0) return fail(MLMC_ERR_ARG, "eps > 0, n_pilot >= 2, max_rounds >= 0");
   std::memset(out, 0, sizeof(*out));
+  CUDA_TRY(cudaSetDevice(c->device));
   const double t0 = now_s();
   const mlmc_model& md = c->model;
   const int L = md.L;
+  const int NL = L + 1;
   int rc_any = 0;
-  std::vector<mlmc_level_sums> S(L + 1);
-  std::vector<double> C(L + 1);
-  for (int l = 0; l <= L; ++l) {
-    int r = mlmc_level_batch(c, l, 0, n_pilot, seed, nullptr, nullptr, nullptr, nullptr, &S[l]);
+  std::vector<mlmc_level_sums> S(NL);
+  std::vector<double> C(NL);
+  std::vector<int64_t> first(NL, 0), cnt(NL, n_pilot);
+  int rounds = 0;
+  if (c->resume_est.valid) {
+    // continue a checkpointed estimate: its sums stand in for the pilot and the
+    // rounds already done
+    if (c->resume_est.seed != seed || (int)c->resume_est.S.size() != NL)
+      return fail(MLMC_ERR_ARG, "resumed state has another seed or level count");
+    S = c->resume_est.S;
+    C = c->resume_est.C;
+    rounds = c->resume_est.rounds;
+    c->resume_est.valid = false;
+  } else if (cost_model == 1) {
+    // measured cost: the pilot runs level by level so that each is timed
+    for (int l = 0; l < NL; ++l) {
+      int r = mlmc_level_batch(c, l, 0, n_pilot, seed, nullptr, nullptr, nullptr, nullptr, &S[l]);
+      if (r < 0) return r;
+      rc_any |= r;
+      C[l] = S[l].seconds / n_pilot;
+    }
+  } else {
+    int r = multilevel_impl(c, NL, first.data(), cnt.data(), seed, true, S.data());
     if (r < 0) return r;
     rc_any |= r;
-    const double m2 = (double)(md.m0 << l) * (double)(md.m0 << l);
-    C[l] = cost_model == 1 ? S[l].seconds / n_pilot : m2 * (1.0 + 0.25 * n_coarse(md, l));
+    for (int l = 0; l < NL; ++l) {
+      const double m2 = (double)(md.m0 << l) * (double)(md.m0 << l);
+      C[l] = m2 * (1.0 + 0.25 * n_coarse(md, l));
+    }
   }
   auto stats = [&](int l, double* mean, double* var) {
     const bool g = md.cgv && l > 0;
@@ -490,41 +686,29 @@ int mlmc_estimate(mlmc_ctx* c, double eps, uint64_t seed, int32_t n_pilot, int32
     const double v = n > 1 ? (s2 - s1 * s1 / n) / (n - 1) : INFINITY;
     *var = v > 0 ? v : 0.0;
   };
-  int rounds = 0;
   while (true) {
-    std::vector<double> V(L + 1), mu(L + 1);
-    for (int l = 0; l <= L; ++l) stats(l, &mu[l], &V[l]);
+    std::vector<double> V(NL), mu(NL);
+    for (int l = 0; l < NL; ++l) stats(l, &mu[l], &V[l]);
     double tot = 0;
-    for (int l = 0; l <= L; ++l) tot += std::sqrt(V[l] * C[l]);
+    for (int l = 0; l < NL; ++l) tot += std::sqrt(V[l] * C[l]);
     bool any = false;
-    std::vector<int64_t> todo(L + 1, 0);
-    for (int l = 0; l <= L; ++l) {
+    for (int l = 0; l < NL; ++l) {
       const double nopt = std::ceil(2.0 / (eps * eps) * std::sqrt(V[l] / C[l]) * tot);
-      todo[l] = std::max<int64_t>(0, (int64_t)nopt - S[l].n);
-      any |= todo[l] > 0;
+      cnt[l] = std::max<int64_t>(0, (int64_t)nopt - S[l].n);
+      first[l] = S[l].n + S[l].n_failed;
+      any |= cnt[l] > 0;
     }
-    if (!any || rounds >= 10) break;
+    if (!any || rounds >= max_rounds) break;
     ++rounds;
-    for (int l = 0; l <= L; ++l) {
-      if (!todo[l]) continue;
-      mlmc_level_sums add;
-      const int64_t have = S[l].n + S[l].n_failed;
-      int r = mlmc_level_batch(c, l, have, todo[l], seed, nullptr, nullptr, nullptr, nullptr, &add);
-      if (r < 0) return r;
-      rc_any |= r;
-      S[l].n += add.n;
-      S[l].n_failed += add.n_failed;
-      S[l].iters_total += add.iters_total;
-      S[l].seconds += add.seconds;
-      double* a[10] = {&S[l].s_qf, &S[l].s_qf2, &S[l].s_qc, &S[l].s_qc2, &S[l].s_y,
-                       &S[l].s_y2, &S[l].s_qcg, &S[l].s_qcg2, &S[l].s_yg, &S[l].s_yg2};
-      const double* b[10] = {&add.s_qf, &add.s_qf2, &add.s_qc, &add.s_qc2, &add.s_y,
-                             &add.s_y2, &add.s_qcg, &add.s_qcg2, &add.s_yg, &add.s_yg2};
-      for (int k = 0; k < 10; ++k) *a[k] += *b[k];
-    }
+    std::vector<mlmc_level_sums> add(NL);
+    int r = multilevel_impl(c, NL, first.data(), cnt.data(), seed, true, add.data());
+    if (r < 0) return r;
+    rc_any |= r;
+    for (int l = 0; l < NL; ++l)
+      if (cnt[l] > 0) add_sums(S[l], add[l]);
   }
   double qh = 0, vh = 0;
-  for (int l = 0; l <= L; ++l) {
+  for (int l = 0; l < NL; ++l) {
     double mean, var;
     stats(l, &mean, &var);
     out->N[l] = S[l].n;
@@ -539,7 +723,158 @@ int mlmc_estimate(mlmc_ctx* c, double eps, uint64_t seed, int32_t n_pilot, int32
   out->var_hat = vh;
   out->rounds = rounds;
   out->seconds = now_s() - t0;
+  auto& st = c->last_est;
+  st.valid = true;
+  st.eps = eps;
+  st.seed = seed;
+  st.cost_model = cost_model;
+  st.rounds = rounds;
+  st.S = S;
+  st.C = C;
   return rc_any ? MLMC_SOME_FAILED : MLMC_OK;
+}
+
+int mlmc_estimate(mlmc_ctx* c, double eps, uint64_t seed, int32_t n_pilot, int32_t cost_model,
+                  mlmc_estimate_out* out) {
+  return mlmc_estimate_ex(c, eps, seed, n_pilot, cost_model, 10, out);
+}
+
+// Text format, one "key value..." per line; doubles with 17 significant
+// digits so that a resumed estimate is bit-identical to an uninterrupted one.
+int mlmc_checkpoint(mlmc_ctx* c, const char* path) {
+  if (!c || !path) return fail(MLMC_ERR_ARG, "null argument");
+  const auto& st = c->last_est;
+  if (!st.valid) return fail(MLMC_ERR_ARG, "no estimate to checkpoint");
+  FILE* f = std::fopen(path, "w");
+  if (!f) return fail(MLMC_ERR_ARG, std::string("cannot write ") + path);
+  const mlmc_model& md = c->model;
+  std::fprintf(f, "mlmc_checkpoint 1\n");
+  std::fprintf(f, "model %d %d %d %d %d %d %d\n", md.n_layers, md.k_kind, md.m0, md.L, md.cgv, md.prec, md.norm_r);
+  std::fprintf(f, "seed %llu\neps %.17g\ncost_model %d\nrounds %d\nlevels %d\n", (unsigned long long)st.seed,
+               st.eps, st.cost_model, st.rounds, (int)st.S.size());
+  for (size_t l = 0; l < st.S.size(); ++l) {
+    const auto& x = st.S[l];
+    std::fprintf(f, "level %zu %lld %lld %lld %.17g %.17g %.17g %.17g %.17g %.17g %.17g %.17g %.17g %.17g %.17g %.17g\n",
+                 l, (long long)x.n, (long long)x.n_failed, (long long)x.iters_total, x.s_qf, x.s_qf2, x.s_qc, x.s_qc2,
+                 x.s_y, x.s_y2, x.s_qcg, x.s_qcg2, x.s_yg, x.s_yg2, x.seconds, st.C[l]);
+  }
+  const bool ok = std::fclose(f) == 0;
+  return ok ? 0 : fail(MLMC_ERR_ARG, std::string("error writing ") + path);
+}
+
+int mlmc_resume(mlmc_ctx* c, const char* path) {
+  if (!c || !path) return fail(MLMC_ERR_ARG, "null argument");
+  FILE* f = std::fopen(path, "r");
+  if (!f) return fail(MLMC_ERR_ARG, std::string("cannot read ") + path);
+  mlmc_ctx::EstState st;
+  int ver = 0, nl = 0;
+  int mk[7];
+  unsigned long long seed = 0;
+  bool ok = std::fscanf(f, "mlmc_checkpoint %d\n", &ver) == 1 && ver == 1 &&
+            std::fscanf(f, "model %d %d %d %d %d %d %d\n", &mk[0], &mk[1], &mk[2], &mk[3], &mk[4], &mk[5], &mk[6]) == 7 &&
+            std::fscanf(f, "seed %llu\neps %lg\ncost_model %d\nrounds %d\nlevels %d\n", &seed, &st.eps,
+                        &st.cost_model, &st.rounds, &nl) == 5;
+  const mlmc_model& md = c->model;
+  if (ok && (mk[0] != md.n_layers || mk[1] != md.k_kind || mk[2] != md.m0 || mk[3] != md.L || mk[4] != md.cgv ||
+             mk[5] != md.prec || mk[6] != md.norm_r || nl != md.L + 1))
+    ok = false;
+  for (int l = 0; ok && l < nl; ++l) {
+    mlmc_level_sums x{};
+    long long a, b, cc;
+    size_t ll;
+    double cost;
+    ok = std::fscanf(f, "level %zu %lld %lld %lld %lg %lg %lg %lg %lg %lg %lg %lg %lg %lg %lg %lg\n", &ll, &a, &b,
+                     &cc, &x.s_qf, &x.s_qf2, &x.s_qc, &x.s_qc2, &x.s_y, &x.s_y2, &x.s_qcg, &x.s_qcg2, &x.s_yg,
+                     &x.s_yg2, &x.seconds, &cost) == 16 &&
+         ll == (size_t)l;
+    x.n = a;
+    x.n_failed = b;
+    x.iters_total = cc;
+    st.S.push_back(x);
+    st.C.push_back(cost);
+  }
+  std::fclose(f);
+  if (!ok) return fail(MLMC_ERR_ARG, std::string("not a checkpoint of this model: ") + path);
+  st.seed = seed;
+  st.valid = true;
+  c->resume_est = st;
+  return 0;
+}
+
+int mlmc_multilevel_batch(mlmc_ctx* c, int32_t n_levels, const int64_t* first, const int64_t* n, uint64_t seed,
+                          int32_t use_graph, mlmc_level_sums* sums) {
+  if (!c || !first || !n || !sums) return fail(MLMC_ERR_ARG, "null argument");
+  if (n_levels < 1 || n_levels > c->model.L + 1) return fail(MLMC_ERR_ARG, "n_levels out of range");
+  for (int l = 0; l < n_levels; ++l)
+    if (n[l] < 0 || first[l] < 0) return fail(MLMC_ERR_ARG, "negative sample range");
+  CUDA_TRY(cudaSetDevice(c->device));
+  const double t0 = now_s();
+  const int r = multilevel_impl(c, n_levels, first, n, seed, use_graph != 0, sums);
+  const double dt = now_s() - t0;
+  for (int l = 0; l < n_levels; ++l) sums[l].seconds = dt;
+  return r;
+}
+
+// Candidate launch plans of each level timed on a probe batch; the fastest
+// is kept for the level's solves.
+int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
+  if (!c) return fail(MLMC_ERR_ARG, "null context");
+  CUDA_TRY(cudaSetDevice(c->device));
+  const mlmc_model& md = c->model;
+  if (rep) std::memset(rep, 0, sizeof(*rep));
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  int err = 0;
+  for (int l = 0; l <= md.L && !err; ++l) {
+    c->tuned_ok[l] = false;
+    const int m = md.m0 << l;
+    const int nc = n_coarse(md, l);
+    int64_t n = std::max<int64_t>(16, std::min<int64_t>(65536, ((int64_t)1 << 24) / ((int64_t)m * m)));
+    n = std::min<int64_t>(n, chunk_samples(c, l));
+    if ((err = prepare_level(c, l, n))) break;
+    SolveArgs a = base_args(c, l, seed, (int64_t)1 << 40);
+    if (md.k_kind == 1) {
+      if ((err = run_fields(c, l, a.first, n, seed))) break;
+      a.g = c->g.p;
+    }
+    SolvePlan cand[16];
+    const int nk = solve_plan_candidates(m, md.prec, cand, 16);
+    float best = 1e30f, def_ms = 0.f;
+    int best_k = -1;
+    for (int k = 0; k < nk && !err; ++k) {
+      float ms = 1e30f;
+      for (int rep_i = 0; rep_i < 2 && !err; ++rep_i) {
+        cudaEventRecord(e0, c->st);
+        err = run_solves(c, a, n, nc, 0, &cand[k]);
+        cudaEventRecord(e1, c->st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) err = fail(MLMC_ERR_CUDA, "autotune timing");
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (rep_i) ms = t;  // the second run (first one warms up)
+      }
+      if (k == 0) def_ms = ms;
+      if (ms < best) {
+        best = ms;
+        best_k = k;
+      }
+    }
+    if (err || best_k < 0) break;
+    c->tuned[l] = cand[best_k];
+    c->tuned_ok[l] = true;
+    if (rep) {
+      rep->threads[l] = cand[best_k].threads;
+      rep->warp[l] = cand[best_k].warp;
+      rep->cap_blocks_per_sm[l] = cand[best_k].cap_blocks_per_sm;
+      rep->cluster[l] = cand[best_k].cluster;
+      rep->candidates[l] = nk;
+      rep->ms_default[l] = def_ms / n;
+      rep->ms_best[l] = best / n;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return err;
 }
 
 int mlmc_profile(mlmc_ctx* c, int enable) {
@@ -552,6 +887,24 @@ int mlmc_profile(mlmc_ctx* c, int enable) {
 int mlmc_profile_read(mlmc_ctx* c, mlmc_profile_stats* out) {
   if (!c || !out) return fail(MLMC_ERR_ARG, "null argument");
   *out = c->prof;
+  return 0;
+}
+
+int mlmc_set_launch(mlmc_ctx* c, int level, int32_t mode, int32_t threads, int32_t cluster) {
+  if (!c || level < 0 || level > c->model.L) return fail(MLMC_ERR_ARG, "bad context or level");
+  CUDA_TRY(cudaSetDevice(c->device));
+  if (mode < 0) {
+    c->tuned_ok[level] = false;
+    return 0;
+  }
+  if (mode > 2 || (mode == 0 && (threads < 32 || threads > 512 || threads % 32)) ||
+      (mode == 2 && (cluster < 2 || cluster > 8 || (cluster & (cluster - 1)))))
+    return fail(MLMC_ERR_ARG, "mode 0: threads 32..512 (multiple of 32); mode 2: cluster 2, 4 or 8");
+  SolvePlan P;
+  if (solve_plan_mode(c->model.m0 << level, c->model.prec, mode, mode == 0 ? threads : 512, cluster, &P))
+    return fail(MLMC_ERR_CUDA, "launch plan query failed");
+  c->tuned[level] = P;
+  c->tuned_ok[level] = true;
   return 0;
 }
 

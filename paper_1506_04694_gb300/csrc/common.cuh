@@ -68,19 +68,30 @@ __device__ __forceinline__ void box_muller(double ua, double ub, double& re, dou
   im = rad * s;
 }
 
-// FP32 version for the mixed-precision field path.  The arguments are reduced
-// in FP64 first (both exactly): ln u = log1p(-(1 - u)) above 1/2, so that u
-// close to 1 keeps its distance from 1; 2 u = k + x with x in [-1/2, 1/2]
-// and k an integer, so the angle keeps FP32 accuracy (sincos pi (k + x) =
-// (-1)^k sincos pi x).  Absolute error of the normals ~1e-6.
-__device__ __forceinline__ void box_muller(double ua, double ub, float& re, float& im) {
-  const float lg = ua > 0.5 ? log1pf(-(float)(1.0 - ua)) : logf((float)ua);
+// FP32 version for the mixed-precision field path, from the words directly,
+// with no FP64 arithmetic (GB300's FP64 rate is a small fraction of its FP32
+// rate).  u = (K + 1/2) 2^-52, K = w >> 12, as in uniform52():
+//  - ln u_a: above 1/2 as log1p(-(1 - u_a)) with 1 - u_a = (2^52 - 1 - K + 1/2)
+//    2^-52 formed in integers, so u_a close to 1 keeps its distance from 1;
+//    below 1/2 as ln u_a;
+//  - 2 u_b = k + x with k the nearest integer and x in [-1/2, 1/2] formed in
+//    integers, and sincos(pi (k + x)) = (-1)^k sincos(pi x).
+// Absolute error of the normals ~1e-6.
+__device__ __forceinline__ void box_muller_words(uint64_t wa, uint64_t wb, float& re, float& im) {
+  const uint64_t Ka = wa >> 12, Kb = wb >> 12;
+  float lg;
+  if (Ka >= (1ull << 51)) {
+    const uint64_t Kc = ((1ull << 52) - 1) - Ka;  // 1 - u = (Kc + 1/2) 2^-52
+    lg = log1pf(-((float)(2 * Kc + 1) * 0x1p-53f));
+  } else {
+    lg = logf((float)(2 * Ka + 1) * 0x1p-53f);
+  }
   const float rad = sqrtf(-2.0f * lg);
-  const double x2 = 2.0 * ub;
-  const double k = rint(x2);
+  const uint64_t k = (Kb + (1ull << 50)) >> 51;              // nearest integer to 2 u_b
+  const long long D = (long long)(2 * Kb + 1) - (long long)(k << 52);  // 2^52 x, |x| <= 1/2
   float s, c;
-  sincospif((float)(x2 - k), &s, &c);
-  const float sg = ((long long)k & 1) ? -1.0f : 1.0f;
+  sincospif((float)D * 0x1p-52f, &s, &c);
+  const float sg = (k & 1) ? -1.0f : 1.0f;
   re = sg * rad * c;
   im = sg * rad * s;
 }
@@ -155,7 +166,7 @@ __device__ __forceinline__ void box_muller_tab(uint64_t wa, uint64_t wb, const B
 
 __device__ __forceinline__ void box_muller_tab(uint64_t wa, uint64_t wb, const BmTables&, float& re,
                                                float& im) {
-  box_muller(uniform52(wa), uniform52(wb), re, im);
+  box_muller_words(wa, wb, re, im);
 }
 
 // ------------------------------------------------------------ reductions --

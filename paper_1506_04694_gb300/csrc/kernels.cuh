@@ -83,18 +83,29 @@ struct SolveArgs {
 
 // Launch shape of the solver for one system size (solve.cu).
 struct SolvePlan {
-  int warp;              // one warp per system (else one block per system)
+  int warp;              // one warp per system
+  int cluster;           // > 0: one thread-block cluster of this many blocks per system
+  int blocks_per_group;  // blocks per system (cluster size, else 1)
+  int max_groups;        // systems that can be resident at once on the GPU
   int threads;           // threads per block
   int groups_per_block;  // systems solved side by side in one block
   int blocks_per_sm;     // occupancy
   int use_smem;          // workspace in shared memory (else global, ws_stride per group)
   size_t ws_stride;      // bytes of workspace per group
   size_t smem_bytes;     // dynamic shared memory per block
+  int cap_blocks_per_sm; // > 0: launch at most this many blocks per SM (L2 residency)
 };
 
 size_t solve_ws_bytes(int m, int prec);
 int solve_plan(int m, int prec, SolvePlan* plan);
-// Global workspace (plan.use_smem == 0) must hold n_blocks * groups_per_block * ws_stride bytes.
+// An explicit plan: mode 0 block of `threads`, 1 warp, 2 cluster of `cluster` blocks.
+int solve_plan_mode(int m, int prec, int mode, int threads, int cluster, SolvePlan* plan);
+// Launch plans worth timing for one system size (the default first); returns the count.
+int solve_plan_candidates(int m, int prec, SolvePlan* out, int max_out);
+// Groups (systems in flight) and blocks of a launch for n_sys systems;
+// max_groups_cap > 0 bounds the groups (workspace budget).  The global
+// workspace (plan.use_smem == 0) must hold groups * ws_stride bytes.
+int64_t solve_groups(const SolvePlan& plan, int64_t n_sys, int nsm, int64_t max_groups_cap, int64_t* n_blocks);
 int solve_launch(const SolveArgs& a, int prec, const SolvePlan& plan, int n_blocks, cudaStream_t st);
 
 // --------------------------------------------------------------- reduce ---

@@ -28,8 +28,12 @@
 #include <type_traits>
 
 #include "../../include/mlmc.h"
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace mlmc {
 
@@ -98,6 +102,7 @@ struct Level {
 // Cooperating threads that solve one system: a whole thread block, or one
 // warp (small grids, no block barriers at all).
 struct BlockGroup {
+  __device__ __forceinline__ bool local_leader() const { return threadIdx.x == 0; }
   __device__ __forceinline__ int rank() const { return threadIdx.x; }
   __device__ __forceinline__ int size() const { return blockDim.x; }
   __device__ __forceinline__ void sync() const { __syncthreads(); }
@@ -108,12 +113,39 @@ struct BlockGroup {
 };
 
 struct WarpGroup {
+  __device__ __forceinline__ bool local_leader() const { return (threadIdx.x & 31) == 0; }
   __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
   __device__ __forceinline__ int size() const { return 32; }
   __device__ __forceinline__ void sync() const { __syncwarp(); }
   template <typename T>
   __device__ __forceinline__ T sum(T v, T*, int&) const {
     return warp_sum(v);
+  }
+};
+
+// All threads of a thread-block cluster (large grids: the system's
+// workspace is shared by the cluster's blocks through global memory / L2).
+// sync() is the hardware cluster barrier (release / acquire at cluster
+// scope, so global writes of one block are visible to the others after it);
+// sum() reduces in each block, then every thread adds the blocks' partials
+// in block-rank order through distributed shared memory, so all blocks hold
+// bit-identical sums and take identical branches.
+struct ClusterGroup {
+  unsigned nblk, brank;
+  double* part;  // two double slots in this block's shared memory
+  __device__ __forceinline__ bool local_leader() const { return threadIdx.x == 0; }
+  __device__ __forceinline__ int rank() const { return (int)(brank * blockDim.x + threadIdx.x); }
+  __device__ __forceinline__ int size() const { return (int)(nblk * blockDim.x); }
+  __device__ __forceinline__ void sync() const { cg::this_cluster().sync(); }
+  template <typename T>
+  __device__ __forceinline__ T sum(T v, T* red, int& par) const {
+    const int slot = par;  // block_sum toggles par; the partial slot follows it
+    const T b = block_sum(v, red, par);
+    if (threadIdx.x == 0) part[slot] = (double)b;
+    cg::this_cluster().sync();
+    double t = 0.0;
+    for (unsigned r = 0; r < nblk; ++r) t += *cg::this_cluster().map_shared_rank(part + slot, r);
+    return (T)t;
   }
 };
 
@@ -132,25 +164,47 @@ __device__ __forceinline__ T apply_row(const Level<T>& L, const T* __restrict__ 
   return s;
 }
 
-// One red (color 0) or black (color 1) Gauss-Seidel half sweep; `zero_guess`
+// Cell loops below process kU cells per thread at a time, all loads of the
+// batch before any store (the cells of one batch never read each other's
+// outputs: same-colour cells of a red-black sweep, or distinct cells of a
+// pointwise update).  Measured on GB300, batches of 2 or 4 raised register
+// use enough to lower occupancy and ran slower than kU = 1.
+constexpr int kU = 1;
+
+// Red (color 0) or black (color 1) Gauss-Seidel half sweep; `zero_guess`
 // treats the other color as zero (first sweep of a cycle).
 template <typename T, typename G>
 __device__ __forceinline__ void rb_sweep(const G& g, const Level<T>& L, int color, bool zero_guess) {
   const int m = L.m, hm = m >> 1;
   const int nh = m * hm;
-  for (int h = g.rank(); h < nh; h += g.size()) {
-    const int j = h / hm;
-    const int i = ((h - j * hm) << 1) + ((j + color) & 1);
-    const int c = j * m + i;
-    T s = L.f[c];
-    if (!zero_guess) {
-      const int rf = j * (m + 1) + i;
-      if (i > 0) s += L.tx[rf] * L.e[c - 1];
-      if (i < m - 1) s += L.tx[rf + 1] * L.e[c + 1];
-      if (j > 0) s += L.ty[c] * L.e[c - m];
-      if (j < m - 1) s += L.ty[c + m] * L.e[c + m];
+  const int step = g.size();
+  int h0 = g.rank();
+  for (; h0 < nh; h0 += kU * step) {
+    T val[kU];
+    int cc[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int h = h0 + u * step;
+      cc[u] = -1;
+      if (h < nh) {
+        const int j = h / hm;
+        const int i = ((h - j * hm) << 1) + ((j + color) & 1);
+        const int c = j * m + i;
+        T s = L.f[c];
+        if (!zero_guess) {
+          const int rf = j * (m + 1) + i;
+          if (i > 0) s += L.tx[rf] * L.e[c - 1];
+          if (i < m - 1) s += L.tx[rf + 1] * L.e[c + 1];
+          if (j > 0) s += L.ty[c] * L.e[c - m];
+          if (j < m - 1) s += L.ty[c + m] * L.e[c + m];
+        }
+        val[u] = s * L.invd[c];
+        cc[u] = c;
+      }
     }
-    L.e[c] = s * L.invd[c];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (cc[u] >= 0) L.e[cc[u]] = val[u];
   }
   g.sync();
 }
@@ -162,12 +216,24 @@ __device__ __forceinline__ void rb_sweep(const G& g, const Level<T>& L, int colo
 template <typename T, typename G>
 __device__ __forceinline__ void restrict_residual(const G& g, const Level<T>& F, const Level<T>& C) {
   const int mc = C.m, m = F.m;
-  for (int cc = g.rank(); cc < mc * mc; cc += g.size()) {
-    const int J = cc / mc, I = cc - J * mc;
-    const int i0 = 2 * I, j0 = 2 * J;
-    const T r0 = F.f[j0 * m + i0] - apply_row(F, F.e, i0, j0);
-    const T r1 = F.f[(j0 + 1) * m + i0 + 1] - apply_row(F, F.e, i0 + 1, j0 + 1);
-    C.f[cc] = r0 + r1;
+  const int nc = mc * mc, step = g.size();
+  for (int c0 = g.rank(); c0 < nc; c0 += kU * step) {
+    T val[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int cc = c0 + u * step;
+      val[u] = T(0);
+      if (cc < nc) {
+        const int J = cc / mc, I = cc - J * mc;
+        const int i0 = 2 * I, j0 = 2 * J;
+        const T r0 = F.f[j0 * m + i0] - apply_row(F, F.e, i0, j0);
+        const T r1 = F.f[(j0 + 1) * m + i0 + 1] - apply_row(F, F.e, i0 + 1, j0 + 1);
+        val[u] = r0 + r1;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (c0 + u * step < nc) C.f[c0 + u * step] = val[u];
   }
   g.sync();
 }
@@ -175,9 +241,20 @@ __device__ __forceinline__ void restrict_residual(const G& g, const Level<T>& F,
 template <typename T, typename G>
 __device__ __forceinline__ void prolong_add(const G& g, const Level<T>& C, const Level<T>& F) {
   const int m = F.m, mc = C.m;
-  for (int c = g.rank(); c < m * m; c += g.size()) {
-    const int j = c / m, i = c - j * m;
-    F.e[c] += C.e[(j >> 1) * mc + (i >> 1)];
+  const int n = m * m, step = g.size();
+  for (int c0 = g.rank(); c0 < n; c0 += kU * step) {
+    T val[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int c = c0 + u * step;
+      if (c < n) {
+        const int j = c / m, i = c - j * m;
+        val[u] = F.e[c] + C.e[(j >> 1) * mc + (i >> 1)];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (c0 + u * step < n) F.e[c0 + u * step] = val[u];
   }
   g.sync();
 }
@@ -237,14 +314,15 @@ __device__ void vcycle(const G& g, const Level<T>* lev, int nl) {
 // Stops when r.r <= thr; returns iterations, status 0 converged, 1 hit the
 // cap, 2 breakdown (p.Ap <= 0 or not finite).
 template <typename T, typename G>
-__device__ int pcg(const G& g, const Level<T>* lev, int nl, T* x, T* p, T* q, T thr, int max_it, T* red,
-                   int& par, int& status) {
+__device__ int pcg(const G& g, const Level<T>* lev, int nl, T* __restrict__ x, T* __restrict__ p,
+                   T* __restrict__ q, T thr, int max_it, T* red, int& par, int& status) {
   const Level<T>& L0 = lev[0];
   const int m = L0.m, n = m * m;
-  T* r = L0.f;
-  T* z = L0.e;
+  T* __restrict__ r = L0.f;
+  const T* __restrict__ z = L0.e;
+  const int step = g.size();
   T rr = T(0);
-  for (int c = g.rank(); c < n; c += g.size()) {
+  for (int c = g.rank(); c < n; c += step) {
     x[c] = T(0);
     rr += r[c] * r[c];
   }
@@ -256,7 +334,7 @@ __device__ int pcg(const G& g, const Level<T>* lev, int nl, T* x, T* p, T* q, T 
   }
   vcycle(g, lev, nl);
   T rz = T(0);
-  for (int c = g.rank(); c < n; c += g.size()) {
+  for (int c = g.rank(); c < n; c += step) {
     p[c] = z[c];
     rz += r[c] * z[c];
   }
@@ -265,11 +343,21 @@ __device__ int pcg(const G& g, const Level<T>* lev, int nl, T* x, T* p, T* q, T 
   while (it < max_it) {
     ++it;
     T pq = T(0);
-    for (int c = g.rank(); c < n; c += g.size()) {
-      const int j = c / m, i = c - j * m;
-      const T v = apply_row(L0, p, i, j);
-      q[c] = v;
-      pq += p[c] * v;
+    for (int c0 = g.rank(); c0 < n; c0 += kU * step) {
+      T val[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int c = c0 + u * step;
+        val[u] = T(0);
+        if (c < n) {
+          const int j = c / m, i = c - j * m;
+          val[u] = apply_row(L0, p, i, j);
+          pq += p[c] * val[u];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+        if (c0 + u * step < n) q[c0 + u * step] = val[u];
     }
     pq = g.sum(pq, red, par);
     if (!(pq > T(0)) || !isfinite(pq) || !isfinite(rz)) {
@@ -278,7 +366,7 @@ __device__ int pcg(const G& g, const Level<T>* lev, int nl, T* x, T* p, T* q, T 
     }
     const T alpha = rz / pq;
     rr = T(0);
-    for (int c = g.rank(); c < n; c += g.size()) {
+    for (int c = g.rank(); c < n; c += step) {
       x[c] += alpha * p[c];
       const T rv = r[c] - alpha * q[c];
       r[c] = rv;
@@ -291,11 +379,11 @@ __device__ int pcg(const G& g, const Level<T>* lev, int nl, T* x, T* p, T* q, T 
     }
     vcycle(g, lev, nl);
     T rzn = T(0);
-    for (int c = g.rank(); c < n; c += g.size()) rzn += r[c] * z[c];
+    for (int c = g.rank(); c < n; c += step) rzn += r[c] * z[c];
     rzn = g.sum(rzn, red, par);
     const T beta = rzn / rz;
     rz = rzn;
-    for (int c = g.rank(); c < n; c += g.size()) p[c] = z[c] + beta * p[c];
+    for (int c = g.rank(); c < n; c += step) p[c] = z[c] + beta * p[c];
     g.sync();
   }
   return it;
@@ -382,9 +470,9 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
   const int m = coarse ? a.m >> 1 : a.m;
   const int n = m * m;
   const uint64_t sample = (uint64_t)(a.first + sidx);
-  if (m != m_prev) {  // level table of this system size
+  if (m != m_prev) {  // level table of this system size (each block keeps its copy)
     g.sync();
-    if (g.rank() == 0) {
+    if (g.local_leader()) {
       size_t off[kLayoutSlots];
       ws_layout(m, sizeof(T), MIXED, off);
       int l = 0;
@@ -420,7 +508,7 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
 
   // ---- layers and per-cell permeability (into r64 as scratch) ----
   if (a.ksrc != KSRC_ARRAY) {
-    if (g.rank() == 0) sample_layers(a, sample, gs.eta, gs.kc);
+    if (g.local_leader()) sample_layers(a, sample, gs.eta, gs.kc);
     g.sync();
   }
   const int n_if = a.n_layers - 1;
@@ -570,22 +658,35 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
   g.sync();
 }
 
-template <bool MIXED, bool WARP>
-__global__ void __launch_bounds__(WARP ? 32 * kWarpsPerBlock : kMaxThreads) solve_kernel(SolveArgs a) {
+// MODE 0: one block per system; 1: one warp per system (kWarpsPerBlock
+// systems per block); 2: one thread-block cluster per system.
+template <bool MIXED, int MODE>
+__global__ void __launch_bounds__(MODE == 1 ? 32 * kWarpsPerBlock : kMaxThreads) solve_kernel(SolveArgs a) {
   using T = typename std::conditional<MIXED, float, double>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int kGroups = WARP ? kWarpsPerBlock : 1;
+  constexpr int kGroups = MODE == 1 ? kWarpsPerBlock : 1;
   __shared__ GroupState<T> gstate[kGroups];
-  __shared__ T red[WARP ? 1 : 132];
-  __shared__ double red64[WARP ? 1 : 132];
-  const int gid = WARP ? (int)(threadIdx.x >> 5) : 0;
-  unsigned char* base = a.use_smem ? smem_raw + (size_t)gid * a.ws_stride
-                                   : a.ws + ((size_t)blockIdx.x * kGroups + gid) * a.ws_stride;
+  __shared__ T red[MODE == 1 ? 1 : 132];
+  __shared__ double red64[MODE == 1 ? 1 : 132];
   const int64_t n_sys = a.n_samples * (int64_t)(1 + a.n_coarse);
   int par = 0, m_prev = -1;
+  if (MODE == 2) {
+    __shared__ double cl_part[2];
+    cg::cluster_group cl = cg::this_cluster();
+    const ClusterGroup g{cl.num_blocks(), cl.block_rank(), cl_part};
+    const int64_t cid = blockIdx.x / g.nblk, ncl = gridDim.x / g.nblk;
+    unsigned char* base = a.ws + (size_t)cid * a.ws_stride;
+    for (int64_t sys = cid; sys < n_sys; sys += ncl)
+      solve_one<MIXED>(g, a, sys, base, gstate[0], red, red64, par, m_prev);
+    cl.sync();  // no block leaves while others may still read its shared memory
+    return;
+  }
+  const int gid = MODE == 1 ? (int)(threadIdx.x >> 5) : 0;
+  unsigned char* base = a.use_smem ? smem_raw + (size_t)gid * a.ws_stride
+                                   : a.ws + ((size_t)blockIdx.x * kGroups + gid) * a.ws_stride;
   const int64_t stride = (int64_t)gridDim.x * kGroups;
   for (int64_t sys = (int64_t)blockIdx.x * kGroups + gid; sys < n_sys; sys += stride) {
-    if (WARP)
+    if (MODE == 1)
       solve_one<MIXED>(WarpGroup(), a, sys, base, gstate[gid], red, red64, par, m_prev);
     else
       solve_one<MIXED>(BlockGroup(), a, sys, base, gstate[gid], red, red64, par, m_prev);
@@ -598,42 +699,142 @@ size_t solve_ws_bytes(int m, int prec) {
 
 static const size_t kSmemCap = 110 * 1024;
 
-template <bool MIXED, bool WARP>
-static int plan_impl(int m, SolvePlan* P) {
+template <bool MIXED, int MODE>
+static int plan_fill(int m, int threads, int cluster, SolvePlan* P) {
   const size_t ws = solve_ws_bytes(m, MIXED);
-  P->warp = WARP;
-  P->threads = solve_threads(m);
-  P->groups_per_block = WARP ? kWarpsPerBlock : 1;
+  int nsm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+  P->warp = MODE == 1;
+  P->cluster = MODE == 2 ? cluster : 0;
+  P->threads = MODE == 1 ? 32 * kWarpsPerBlock : threads;
+  P->groups_per_block = MODE == 1 ? kWarpsPerBlock : 1;
+  P->blocks_per_group = MODE == 2 ? cluster : 1;
   P->ws_stride = (ws + 255) & ~(size_t)255;
-  P->use_smem = P->ws_stride * P->groups_per_block <= kSmemCap;
+  P->use_smem = MODE != 2 && P->ws_stride * P->groups_per_block <= kSmemCap;
   P->smem_bytes = P->use_smem ? P->ws_stride * P->groups_per_block : 0;
-  cudaFuncSetAttribute(solve_kernel<MIXED, WARP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+  P->cap_blocks_per_sm = 0;
+  cudaFuncSetAttribute(solve_kernel<MIXED, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<MIXED, WARP>, P->threads, P->smem_bytes) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<MIXED, MODE>, P->threads, P->smem_bytes) !=
       cudaSuccess)
     return -1;
   P->blocks_per_sm = nb < 1 ? 1 : nb;
+  P->max_groups = nsm * P->blocks_per_sm * P->groups_per_block;
+  if (MODE == 2) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cluster * nsm);
+    cfg.blockDim = dim3(P->threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int ncl = 0;
+    if (cudaOccupancyMaxActiveClusters(&ncl, solve_kernel<MIXED, MODE>, &cfg) != cudaSuccess || ncl < 1) return -1;
+    P->max_groups = ncl;
+  }
   return 0;
 }
 
+// mode: 0 block, 1 warp, 2 cluster of `cluster` blocks
+static int plan_fill(int m, int prec, int mode, int threads, int cluster, SolvePlan* P) {
+  if (prec) {
+    if (mode == 1) return plan_fill<true, 1>(m, threads, cluster, P);
+    if (mode == 2) return plan_fill<true, 2>(m, threads, cluster, P);
+    return plan_fill<true, 0>(m, threads, cluster, P);
+  }
+  if (mode == 1) return plan_fill<false, 1>(m, threads, cluster, P);
+  if (mode == 2) return plan_fill<false, 2>(m, threads, cluster, P);
+  return plan_fill<false, 0>(m, threads, cluster, P);
+}
+
 int solve_plan(int m, int prec, SolvePlan* P) {
-  const bool w = solve_warp_mode(m);
-  if (prec) return w ? plan_impl<true, true>(m, P) : plan_impl<true, false>(m, P);
-  return w ? plan_impl<false, true>(m, P) : plan_impl<false, false>(m, P);
+  return plan_fill(m, prec, solve_warp_mode(m) ? 1 : 0, solve_threads(m), 0, P);
+}
+
+int solve_plan_mode(int m, int prec, int mode, int threads, int cluster, SolvePlan* P) {
+  return plan_fill(m, prec, mode, threads, cluster, P);
+}
+
+int solve_plan_candidates(int m, int prec, SolvePlan* out, int max_out) {
+  int k = 0;
+  auto add = [&](const SolvePlan& P) {
+    if (k < max_out) out[k++] = P;
+  };
+  SolvePlan d;
+  if (solve_plan(m, prec, &d)) return 0;
+  add(d);
+  if (m <= 64 && !d.warp) {
+    SolvePlan w;
+    if (!plan_fill(m, prec, 1, 0, 0, &w)) add(w);
+  }
+  for (int t : {64, 128, 256, 512}) {
+    if (!d.warp && t == d.threads) continue;
+    if (t > 2 * m * m) continue;  // more threads than cells
+    SolvePlan b;
+    if (!plan_fill(m, prec, 0, t, 0, &b)) add(b);
+  }
+  // global-workspace plans also with one system per SM (smaller working set)
+  const int k0 = k;
+  for (int i = 0; i < k0; ++i)
+    if (!out[i].use_smem && out[i].blocks_per_sm > 1) {
+      SolvePlan c = out[i];
+      c.cap_blocks_per_sm = 1;
+      add(c);
+    }
+  // large grids: one cluster of 2, 4 or 8 blocks per system
+  if (m >= 128)
+    for (int cl : {2, 4, 8}) {
+      SolvePlan c;
+      if (!plan_fill(m, prec, 2, kMaxThreads, cl, &c)) add(c);
+    }
+  return k;
 }
 
 int solve_launch(const SolveArgs& a, int prec, const SolvePlan& P, int n_blocks, cudaStream_t st) {
   SolveArgs b = a;
   b.use_smem = P.use_smem;
   b.ws_stride = P.ws_stride;
+  if (P.cluster) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = P.cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(n_blocks);  // a multiple of the cluster size
+    cfg.blockDim = dim3(P.threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = prec ? cudaLaunchKernelEx(&cfg, solve_kernel<true, 2>, b)
+                               : cudaLaunchKernelEx(&cfg, solve_kernel<false, 2>, b);
+    return e == cudaSuccess ? 0 : -1;
+  }
   if (prec) {
-    if (P.warp) solve_kernel<true, true><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
-    else solve_kernel<true, false><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+    if (P.warp) solve_kernel<true, 1><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+    else solve_kernel<true, 0><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
   } else {
-    if (P.warp) solve_kernel<false, true><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
-    else solve_kernel<false, false><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+    if (P.warp) solve_kernel<false, 1><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+    else solve_kernel<false, 0><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// Blocks to launch for n_sys systems with plan P (at most max_groups_cap
+// groups resident; 0 = no cap), and the groups that launch serves.
+int64_t solve_groups(const SolvePlan& P, int64_t n_sys, int nsm, int64_t max_groups_cap, int64_t* n_blocks) {
+  int64_t g = P.max_groups;
+  if (P.cap_blocks_per_sm > 0) g = std::min<int64_t>(g, (int64_t)nsm * P.cap_blocks_per_sm * P.groups_per_block);
+  if (max_groups_cap > 0) g = std::min<int64_t>(g, max_groups_cap);
+  g = std::max<int64_t>(1, std::min<int64_t>(g, n_sys));
+  *n_blocks = P.cluster ? g * P.cluster : (g + P.groups_per_block - 1) / P.groups_per_block;
+  return g;
 }
 
 }  // namespace mlmc
@@ -764,17 +965,17 @@ extern "C" int mlmc_solve_k_static(int device, int32_t m, int64_t n, const doubl
     a.q = q;
     a.iters = iters;
     a.p_out = p;
-    int64_t nb = std::min<int64_t>((n + P.groups_per_block - 1) / P.groups_per_block,
-                                   (int64_t)nsm * P.blocks_per_sm);
+    int64_t cap = 0;
     if (!P.use_smem) {
-      const size_t per_block = P.ws_stride * P.groups_per_block;
-      if (per_block > kStaticScratchBytes) {  // m above the static maximum (512)
+      if (P.ws_stride > kStaticScratchBytes) {  // m above the static maximum (512)
         rc = MLMC_ERR_TOOBIG;
         break;
       }
-      nb = std::min<int64_t>(nb, (int64_t)(kStaticScratchBytes / per_block));
+      cap = (int64_t)(kStaticScratchBytes / P.ws_stride);
       a.ws = reinterpret_cast<unsigned char*>(base);
     }
+    int64_t nb = 0;
+    solve_groups(P, n, nsm, cap, &nb);
     if (solve_launch(a, prec, P, (int)nb, (cudaStream_t)cuda_stream)) rc = MLMC_ERR_CUDA;
   } while (0);
   cudaSetDevice(prev);

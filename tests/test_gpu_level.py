@@ -163,3 +163,103 @@ def test_estimate_parity_mode():
     assert est["N"] == ref["N"]
     assert abs(est["q_hat"] - ref["q_hat"]) < 1e-10 * abs(ref["q_hat"])
     assert est["var_hat"] <= eps * eps / 2 * (1 + 1e-9)
+
+
+def test_multilevel_batch_matches_level_batches():
+    # all levels queued in one call (with and without a CUDA graph) give the
+    # level sums of separate level batches exactly
+    torch, pk = need_gpu()
+    d = workloads.workload("lognormal_2layer_cgv_16to512", L=3)
+    n = [300, 80, 20, 6]
+    first = [5, 0, 11, 2]
+    stream = torch.cuda.Stream()
+    with pk.Context(d, stream=stream) as ctx:
+        ref = [ctx.level_batch(l, n[l], 9, first=first[l]) for l in range(4)]
+        for use_graph in (False, True, True):  # the third call relaunches the kept graph
+            got = ctx.multilevel_batch(n, 9, first=first, use_graph=use_graph)
+            for l in range(4):
+                for key in ("n", "n_failed", "iters_total") + pk.SUM_FIELDS:
+                    assert got[l][key] == ref[l][key], (use_graph, l, key)
+
+
+def test_autotune_keeps_parity():
+    torch, pk = need_gpu()
+    d = workloads.workload("lognormal_2layer_16to256", L=2, tol=1e-12)
+    model = darcy.Model.from_dict(d)
+    with pk.Context(d) as ctx:
+        rep = ctx.autotune(seed=1)
+        assert len(rep) == 3 and all(r["candidates"] >= 1 and r["threads"] > 0 for r in rep)
+        assert all(r["ms_per_sample_best"] <= r["ms_per_sample_default"] * 1.0001 for r in rep)
+        qf = torch.empty(6, dtype=torch.float64, device="cuda")
+        qc = torch.empty_like(qf)
+        ctx.level_batch(2, 6, 3, qf=qf, qc=qc)
+    qf, qc = qf.cpu().numpy(), qc.cpu().numpy()
+    for i in range(6):
+        r = darcy.sample(model, 3, 2, i)
+        assert abs(qf[i] - r["qf"]) <= RTOL64 * abs(r["qf"])
+        assert abs(qc[i] - r["qc"]) <= RTOL64 * abs(r["qc"])
+
+
+def test_checkpoint_resume_bit_identical(tmp_path):
+    # an estimate interrupted after its first top-up round, checkpointed and
+    # resumed in a fresh context, ends exactly where an uninterrupted one does
+    torch, pk = need_gpu()
+    d = workloads.workload("lognormal_2layer_16to256", L=2)
+    eps = 4e-3
+    with pk.Context(d) as ctx:
+        full = ctx.estimate(eps, seed=21, n_pilot=32, max_rounds=10)
+    path = str(tmp_path / "est.ckpt")
+    with pk.Context(d) as ctx:
+        part = ctx.estimate(eps, seed=21, n_pilot=32, max_rounds=1)
+        ctx.checkpoint(path)
+    assert part["rounds"] == 1 and full["rounds"] >= 1
+    with pk.Context(d) as ctx:
+        ctx.resume(path)
+        rest = ctx.estimate(eps, seed=21, n_pilot=32, max_rounds=10)
+    assert rest["N"] == full["N"] and rest["rounds"] == full["rounds"]
+    assert rest["q_hat"] == full["q_hat"] and rest["var_hat"] == full["var_hat"]
+    # a checkpoint of another model is refused
+    with pk.Context(dict(d, m0=8)) as ctx:
+        with pytest.raises(pk.MLMCError):
+            ctx.resume(path)
+
+
+def test_nan_permeability_reported_as_failure():
+    # fault injection on the host side: a non-finite k makes the solve break
+    # down; the system reports NaN instead of a value and no GPU fault occurs
+    torch, pk = need_gpu()
+    k = workloads.random_k(16, seed=3, n=4)
+    k[2, 5, 7] = np.nan
+    with pk.Context(workloads.workload("const_2layer_8to32")) as ctx:
+        _, q, it = ctx.solve_k(torch.from_numpy(k).cuda(), want_p=False)
+    q = q.cpu().numpy()
+    assert np.isnan(q[2]) and np.all(np.isfinite(q[[0, 1, 3]]))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_launch_modes_agree(prec):
+    # one system per block (64..512 threads), per warp, or per thread-block
+    # cluster of 2/4/8 blocks: the same systems give the same Q (only the
+    # summation order of the dot products differs) and agree with the oracle
+    torch, pk = need_gpu()
+    d = workloads.workload("lognormal_2layer_cgv_16to512", prec=prec, cgv=1, tol=1e-12, m0=16, L=4)
+    model = darcy.Model.from_dict(d)
+    level, n = 3, 10   # m = 128: fine 128^2 and four 64^2 coarse systems per sample
+    modes = [(0, 512, 0), (0, 64, 0), (1, 0, 0), (2, 512, 2), (2, 512, 4), (2, 512, 8)]
+    res = []
+    with pk.Context(d) as ctx:
+        for mode, threads, cl in modes:
+            ctx.set_launch(level, mode, threads, cl)
+            qf = torch.empty(n, dtype=torch.float64, device="cuda")
+            qg = torch.empty_like(qf)
+            s = ctx.level_batch(level, n, 4, qf=qf, qc_cgv=qg)
+            assert s["n"] == n and s["n_failed"] == 0, (mode, threads, cl)
+            res.append((qf.cpu().numpy(), qg.cpu().numpy()))
+    tol = 1e-10 if prec == 0 else RTOL_MIX
+    for qf, qg in res[1:]:
+        np.testing.assert_allclose(qf, res[0][0], rtol=tol, atol=0)
+        np.testing.assert_allclose(qg, res[0][1], rtol=tol, atol=0)
+    for i in (0, n - 1):
+        r = darcy.sample(model, 4, level, i)
+        assert abs(res[-1][0][i] - r["qf"]) <= tol * abs(r["qf"])
+        assert abs(res[-1][1][i] - r["qc_cgv"]) <= tol * abs(r["qc_cgv"])
