@@ -416,8 +416,9 @@ int multilevel_impl(mlmc_ctx* c, int n_levels, const int64_t* first, const int64
   if (graph) {
     std::vector<int64_t> key = {(int64_t)n_levels, (int64_t)seed, (int64_t)g_alloc_generation.load()};
     for (int l = 0; l < n_levels; ++l)
-      key.push_back(c->tuned_ok[l] ? ((int64_t)c->tuned[l].threads << 16) + (c->tuned[l].cluster << 8) +
-                                         (c->tuned[l].warp << 4) + c->tuned[l].cap_blocks_per_sm
+      key.push_back(c->tuned_ok[l] ? ((int64_t)c->tuned[l].gamma << 24) + ((int64_t)c->tuned[l].threads << 16) +
+                                         (c->tuned[l].cluster << 8) + (c->tuned[l].warp << 4) +
+                                         c->tuned[l].cap_blocks_per_sm
                                    : -1);
     for (int l = 0; l < n_levels; ++l) {
       key.push_back(first[l]);
@@ -830,7 +831,8 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
     c->tuned_ok[l] = false;
     const int m = md.m0 << l;
     const int nc = n_coarse(md, l);
-    int64_t n = std::max<int64_t>(16, std::min<int64_t>(65536, ((int64_t)1 << 24) / ((int64_t)m * m)));
+    // probe: enough systems to fill the GPU, few enough to stay short
+    int64_t n = std::max<int64_t>(4, std::min<int64_t>(65536, ((int64_t)1 << 24) / ((int64_t)m * m)));
     n = std::min<int64_t>(n, chunk_samples(c, l));
     if ((err = prepare_level(c, l, n))) break;
     SolveArgs a = base_args(c, l, seed, (int64_t)1 << 40);
@@ -838,26 +840,41 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
       if ((err = run_fields(c, l, a.first, n, seed))) break;
       a.g = c->g.p;
     }
-    SolvePlan cand[16];
-    const int nk = solve_plan_candidates(m, md.prec, cand, 16);
+    SolvePlan cand[17];
+    int nk = solve_plan_candidates(m, md.prec, cand, 16);
     float best = 1e30f, def_ms = 0.f;
     int best_k = -1;
-    for (int k = 0; k < nk && !err; ++k) {
+    auto time_plan = [&](const SolvePlan& P) -> float {
       float ms = 1e30f;
       for (int rep_i = 0; rep_i < 2 && !err; ++rep_i) {
         cudaEventRecord(e0, c->st);
-        err = run_solves(c, a, n, nc, 0, &cand[k]);
+        err = run_solves(c, a, n, nc, 0, &P);
         cudaEventRecord(e1, c->st);
         if (cudaEventSynchronize(e1) != cudaSuccess) err = fail(MLMC_ERR_CUDA, "autotune timing");
         float t = 0.f;
         cudaEventElapsedTime(&t, e0, e1);
-        if (rep_i) ms = t;  // the second run (first one warms up)
+        ms = t;
+        if (rep_i == 0 && t > 3.f * best) break;  // clearly slower: one run is enough
       }
+      return ms;
+    };
+    for (int k = 0; k < nk && !err; ++k) {
+      const float ms = time_plan(cand[k]);
       if (k == 0) def_ms = ms;
       if (ms < best) {
         best = ms;
         best_k = k;
       }
+    }
+    if (!err && best_k >= 0) {  // the fastest plan once more with W-cycles
+      cand[nk] = cand[best_k];
+      cand[nk].gamma = 2;
+      const float ms = time_plan(cand[nk]);
+      if (ms < best) {
+        best = ms;
+        best_k = nk;
+      }
+      ++nk;
     }
     if (err || best_k < 0) break;
     c->tuned[l] = cand[best_k];
@@ -867,6 +884,7 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
       rep->warp[l] = cand[best_k].warp;
       rep->cap_blocks_per_sm[l] = cand[best_k].cap_blocks_per_sm;
       rep->cluster[l] = cand[best_k].cluster;
+      rep->gamma[l] = cand[best_k].gamma;
       rep->candidates[l] = nk;
       rep->ms_default[l] = def_ms / n;
       rep->ms_best[l] = best / n;
@@ -890,7 +908,7 @@ int mlmc_profile_read(mlmc_ctx* c, mlmc_profile_stats* out) {
   return 0;
 }
 
-int mlmc_set_launch(mlmc_ctx* c, int level, int32_t mode, int32_t threads, int32_t cluster) {
+int mlmc_set_launch(mlmc_ctx* c, int level, int32_t mode, int32_t threads, int32_t cluster, int32_t gamma) {
   if (!c || level < 0 || level > c->model.L) return fail(MLMC_ERR_ARG, "bad context or level");
   CUDA_TRY(cudaSetDevice(c->device));
   if (mode < 0) {
@@ -901,8 +919,10 @@ int mlmc_set_launch(mlmc_ctx* c, int level, int32_t mode, int32_t threads, int32
       (mode == 2 && (cluster < 2 || cluster > 8 || (cluster & (cluster - 1)))))
     return fail(MLMC_ERR_ARG, "mode 0: threads 32..512 (multiple of 32); mode 2: cluster 2, 4 or 8");
   SolvePlan P;
+  if (gamma < 1 || gamma > 2) return fail(MLMC_ERR_ARG, "gamma must be 1 (V-cycle) or 2 (W-cycle)");
   if (solve_plan_mode(c->model.m0 << level, c->model.prec, mode, mode == 0 ? threads : 512, cluster, &P))
     return fail(MLMC_ERR_CUDA, "launch plan query failed");
+  P.gamma = gamma;
   c->tuned[level] = P;
   c->tuned_ok[level] = true;
   return 0;

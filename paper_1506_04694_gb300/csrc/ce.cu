@@ -30,8 +30,12 @@ __device__ __forceinline__ unsigned brev_n(unsigned v, int logn) {
 
 // In-place radix-2 DIT FFTs of `nrows` contiguous rows of length M (rows
 // already in bit-reversed order) in shared memory; tw[k] = exp(-2 pi i k/M).
+// Only the outputs k < nkeep of each row are needed (nkeep a power of two,
+// 4 <= nkeep <= M): stages whose half-span hs is >= nkeep compute, in each
+// group, the nkeep upper outputs u + w v only.
 template <typename R>
-__device__ void block_fft_rows(Cplx<R>* s, int nrows, int M, int logM, const Cplx<R>* __restrict__ tw) {
+__device__ void block_fft_rows(Cplx<R>* s, int nrows, int M, int logM, const Cplx<R>* __restrict__ tw,
+                               int nkeep) {
   const int half = M >> 1;
   const int nb = nrows * half;
   // stages 0 and 1 together: their twiddles are 1 and -i (M >= 4)
@@ -50,6 +54,23 @@ __device__ void block_fft_rows(Cplx<R>* s, int nrows, int M, int logM, const Cpl
   for (int st = 2; st < logM; ++st) {
     const int hs = 1 << st;
     const int tstride = half >> st;  // twiddle index step M / (2 hs)
+    if (hs >= nkeep) {  // pruned stage: upper outputs of the first nkeep positions
+      const int ngrp = M >> (st + 1);
+      const int np = nrows * ngrp * nkeep;
+      for (int t = threadIdx.x; t < np; t += blockDim.x) {
+        const int pos = t & (nkeep - 1);
+        const int rg = t / nkeep;
+        const int row = rg / ngrp, grp = rg - row * ngrp;
+        Cplx<R>* base = s + row * M;
+        const int i0 = (grp << (st + 1)) + pos;
+        const Cplx<R> w = tw[pos * tstride];
+        const Cplx<R> u = base[i0];
+        const Cplx<R> v = base[i0 + hs];
+        base[i0] = Cplx<R>{u.x + (w.x * v.x - w.y * v.y), u.y + (w.x * v.y + w.y * v.x)};
+      }
+      __syncthreads();
+      continue;
+    }
     for (int t = threadIdx.x; t < nb; t += blockDim.x) {
       const int row = t / half;
       const int b = t - row * half;
@@ -101,7 +122,7 @@ __global__ void fft_rows_full_kernel(Cplx<double>* data, int M, int logM, const 
   Cplx<double>* row = data + (int64_t)blockIdx.x * M;
   for (int t = threadIdx.x; t < M; t += blockDim.x) s[brev_n(t, logM)] = row[t];
   __syncthreads();
-  block_fft_rows(s, 1, M, logM, tw);
+  block_fft_rows(s, 1, M, logM, tw, M);
   for (int t = threadIdx.x; t < M; t += blockDim.x) row[t] = s[t];
 }
 
@@ -170,15 +191,13 @@ __global__ void ce_rows_kernel(CeRowsArgs args, const R* __restrict__ scale,
     const uint64_t call = ((uint64_t)q2 * (uint64_t)M + (uint64_t)q1) >> 1;
     const Words4 w = philox4x64_10(call, sample, (uint64_t)args.level, kStreamField0 + f, args.seed);
     R re0, im0, re1, im1;
-    box_muller_tab(w.w0, w.w1, tb, re0, im0);
-    box_muller_tab(w.w2, w.w3, tb, re1, im1);
-    const R s0 = scale[(int64_t)q2 * M + q1];
-    const R s1 = scale[(int64_t)q2 * M + q1 + 1];
-    s[r * M + brev_n(q1, logM)] = Cplx<R>{s0 * re0, s0 * im0};
-    s[r * M + brev_n(q1 + 1, logM)] = Cplx<R>{s1 * re1, s1 * im1};
+    box_muller_tab(w.w0, w.w1, tb, re0, im0, scale[(int64_t)q2 * M + q1]);
+    box_muller_tab(w.w2, w.w3, tb, re1, im1, scale[(int64_t)q2 * M + q1 + 1]);
+    s[r * M + brev_n(q1, logM)] = Cplx<R>{re0, im0};
+    s[r * M + brev_n(q1 + 1, logM)] = Cplx<R>{re1, im1};
   }
   __syncthreads();
-  block_fft_rows(s, rows, M, logM, tw);
+  block_fft_rows(s, rows, M, logM, tw, m >= 4 ? m : M);
   Cplx<R>* out = W + ((sidx * args.n_pairs + f) * (int64_t)M + q2_0) * m;
   for (int t = threadIdx.x; t < rows * m; t += blockDim.x) {
     const int r = t / m, a = t - r * m;
@@ -204,7 +223,7 @@ __global__ void ce_cols_kernel(CeColsArgs args, const Cplx<R>* __restrict__ tw,
     s[cc * M + brev_n(q2, logM)] = in[(int64_t)q2 * m + cc];
   }
   __syncthreads();
-  block_fft_rows(s, C, M, logM, tw);
+  block_fft_rows(s, C, M, logM, tw, m >= 4 ? m : M);
   const int t0 = 2 * f, t1 = 2 * f + 1;
   const double mu0 = args.mu[t0];
   const double mu1 = t1 < args.n_layers ? args.mu[t1] : 0.0;
@@ -298,7 +317,7 @@ __global__ void bm_tables_kernel(double2* sc, double* lg) {
     sc[i] = make_double2(cv, sv);
   }
   if (i < kLogTab) {
-    const double F = 0.5 + ((double)i + 0.5) / 256.0;
+    const double F = 0.5 + ((double)i + 0.5) / 2048.0;
     lg[3 * i] = F;
     lg[3 * i + 1] = 1.0 / F;
     lg[3 * i + 2] = log(F);

@@ -104,9 +104,9 @@ __device__ __forceinline__ void box_muller_words(uint64_t wa, uint64_t wb, float
 // reduced interval.  Tables hold exact-argument values from the CUDA math
 // library, computed once per context (bm_tables_kernel):
 //   sc[j] = (cos(2 pi j/1024), sin(2 pi j/1024)), j < 1024;
-//   lg[3t .. 3t+2] = (F_t, 1/F_t, ln F_t), F_t = 1/2 + (t + 1/2)/256, t < 128.
+//   lg[3t .. 3t+2] = (F_t, 1/F_t, ln F_t), F_t = 1/2 + (t + 1/2)/2048, t < 1024.
 constexpr int kSinCosTab = 1024;
-constexpr int kLogTab = 128;
+constexpr int kLogTab = 1024;
 
 struct BmTables {
   const double2* sc;
@@ -114,8 +114,8 @@ struct BmTables {
 };
 
 // ln u for u in (0, 1): u = 2^E v, v in [1/2, 1), v = F_t (1 + r) with
-// |r| <= 1/256 and ln(1 + r) from its Taylor series to r^7 (truncation
-// < 1e-20).  r = (v - F_t) / F_t is formed as the exact difference times the
+// |r| <= 1/2048 and ln(1 + r) from its Taylor series to r^4 (truncation
+// < 6e-18).  r = (v - F_t) / F_t is formed as the exact difference times the
 // rounded reciprocal, so the absolute error stays ~1e-19 near u = 1.
 __device__ __forceinline__ double tab_log01(double u, const double* __restrict__ lg) {
   const long long bits = __double_as_longlong(u);
@@ -123,13 +123,10 @@ __device__ __forceinline__ double tab_log01(double u, const double* __restrict__
   const long long mant = bits & ((1LL << 52) - 1);
   const int E = ex - 1022;
   const double v = __longlong_as_double(mant | (1022LL << 52));
-  const int t = (int)(mant >> 45);
+  const int t = (int)(mant >> 42);
   const double F = __ldg(lg + 3 * t), iF = __ldg(lg + 3 * t + 1), lF = __ldg(lg + 3 * t + 2);
   const double r = (v - F) * iF;
-  double p = fma(1.0 / 7.0, r, -1.0 / 6.0);
-  p = fma(p, r, 1.0 / 5.0);
-  p = fma(p, r, -0.25);
-  p = fma(p, r, 1.0 / 3.0);
+  double p = fma(-0.25, r, 1.0 / 3.0);
   p = fma(p, r, -0.5);
   const double l1 = fma(p, r * r, r);
   return fma((double)E, 0.6931471805599453, lF + l1);
@@ -154,10 +151,11 @@ __device__ __forceinline__ void tab_sincos2pi(uint64_t w, const double2* __restr
   s = cs.y + fma(cs.y, cm, cs.x * sn);
 }
 
-// Box-Muller pair from two words (same definition as box_muller()).
+// Box-Muller pair from two words (same definition as box_muller()), each
+// normal times `scale` (folded into the radius).
 __device__ __forceinline__ void box_muller_tab(uint64_t wa, uint64_t wb, const BmTables& tb, double& re,
-                                               double& im) {
-  const double rad = sqrt(-2.0 * tab_log01(uniform52(wa), tb.lg));
+                                               double& im, double scale = 1.0) {
+  const double rad = sqrt(-2.0 * tab_log01(uniform52(wa), tb.lg)) * scale;
   double c, s;
   tab_sincos2pi(wb, tb.sc, c, s);
   re = rad * c;
@@ -165,8 +163,10 @@ __device__ __forceinline__ void box_muller_tab(uint64_t wa, uint64_t wb, const B
 }
 
 __device__ __forceinline__ void box_muller_tab(uint64_t wa, uint64_t wb, const BmTables&, float& re,
-                                               float& im) {
+                                               float& im, float scale = 1.0f) {
   box_muller_words(wa, wb, re, im);
+  re *= scale;
+  im *= scale;
 }
 
 // ------------------------------------------------------------ reductions --

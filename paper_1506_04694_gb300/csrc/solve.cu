@@ -102,6 +102,7 @@ struct Level {
 // Cooperating threads that solve one system: a whole thread block, or one
 // warp (small grids, no block barriers at all).
 struct BlockGroup {
+  static constexpr int kU = 1;  // cells per thread per batch in the cell loops
   __device__ __forceinline__ bool local_leader() const { return threadIdx.x == 0; }
   __device__ __forceinline__ int rank() const { return threadIdx.x; }
   __device__ __forceinline__ int size() const { return blockDim.x; }
@@ -113,6 +114,7 @@ struct BlockGroup {
 };
 
 struct WarpGroup {
+  static constexpr int kU = 1;
   __device__ __forceinline__ bool local_leader() const { return (threadIdx.x & 31) == 0; }
   __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
   __device__ __forceinline__ int size() const { return 32; }
@@ -131,6 +133,7 @@ struct WarpGroup {
 // in block-rank order through distributed shared memory, so all blocks hold
 // bit-identical sums and take identical branches.
 struct ClusterGroup {
+  static constexpr int kU = 1;
   unsigned nblk, brank;
   double* part;  // two double slots in this block's shared memory
   __device__ __forceinline__ bool local_leader() const { return threadIdx.x == 0; }
@@ -164,12 +167,12 @@ __device__ __forceinline__ T apply_row(const Level<T>& L, const T* __restrict__ 
   return s;
 }
 
-// Cell loops below process kU cells per thread at a time, all loads of the
-// batch before any store (the cells of one batch never read each other's
+// Cell loops below process G::kU cells per thread at a time, all loads of
+// the batch before any store (the cells of one batch never read each other's
 // outputs: same-colour cells of a red-black sweep, or distinct cells of a
 // pointwise update).  Measured on GB300, batches of 2 or 4 raised register
-// use enough to lower occupancy and ran slower than kU = 1.
-constexpr int kU = 1;
+// use enough to lower occupancy and ran slower in every plan (the cluster
+// plan at m = 2048: 22 -> 66 ms per sample), so all plans use 1.
 
 // Red (color 0) or black (color 1) Gauss-Seidel half sweep; `zero_guess`
 // treats the other color as zero (first sweep of a cycle).
@@ -179,11 +182,11 @@ __device__ __forceinline__ void rb_sweep(const G& g, const Level<T>& L, int colo
   const int nh = m * hm;
   const int step = g.size();
   int h0 = g.rank();
-  for (; h0 < nh; h0 += kU * step) {
-    T val[kU];
-    int cc[kU];
+  for (; h0 < nh; h0 += G::kU * step) {
+    T val[G::kU];
+    int cc[G::kU];
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
+    for (int u = 0; u < G::kU; ++u) {
       const int h = h0 + u * step;
       cc[u] = -1;
       if (h < nh) {
@@ -203,7 +206,7 @@ __device__ __forceinline__ void rb_sweep(const G& g, const Level<T>& L, int colo
       }
     }
 #pragma unroll
-    for (int u = 0; u < kU; ++u)
+    for (int u = 0; u < G::kU; ++u)
       if (cc[u] >= 0) L.e[cc[u]] = val[u];
   }
   g.sync();
@@ -217,10 +220,10 @@ template <typename T, typename G>
 __device__ __forceinline__ void restrict_residual(const G& g, const Level<T>& F, const Level<T>& C) {
   const int mc = C.m, m = F.m;
   const int nc = mc * mc, step = g.size();
-  for (int c0 = g.rank(); c0 < nc; c0 += kU * step) {
-    T val[kU];
+  for (int c0 = g.rank(); c0 < nc; c0 += G::kU * step) {
+    T val[G::kU];
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
+    for (int u = 0; u < G::kU; ++u) {
       const int cc = c0 + u * step;
       val[u] = T(0);
       if (cc < nc) {
@@ -232,7 +235,7 @@ __device__ __forceinline__ void restrict_residual(const G& g, const Level<T>& F,
       }
     }
 #pragma unroll
-    for (int u = 0; u < kU; ++u)
+    for (int u = 0; u < G::kU; ++u)
       if (c0 + u * step < nc) C.f[c0 + u * step] = val[u];
   }
   g.sync();
@@ -242,10 +245,10 @@ template <typename T, typename G>
 __device__ __forceinline__ void prolong_add(const G& g, const Level<T>& C, const Level<T>& F) {
   const int m = F.m, mc = C.m;
   const int n = m * m, step = g.size();
-  for (int c0 = g.rank(); c0 < n; c0 += kU * step) {
-    T val[kU];
+  for (int c0 = g.rank(); c0 < n; c0 += G::kU * step) {
+    T val[G::kU];
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
+    for (int u = 0; u < G::kU; ++u) {
       const int c = c0 + u * step;
       if (c < n) {
         const int j = c / m, i = c - j * m;
@@ -253,7 +256,7 @@ __device__ __forceinline__ void prolong_add(const G& g, const Level<T>& C, const
       }
     }
 #pragma unroll
-    for (int u = 0; u < kU; ++u)
+    for (int u = 0; u < G::kU; ++u)
       if (c0 + u * step < n) F.e[c0 + u * step] = val[u];
   }
   g.sync();
@@ -290,7 +293,54 @@ __device__ __forceinline__ void build_diag(const G& g, const Level<T>& L) {
   g.sync();
 }
 
-// Symmetric V-cycle: level-0 e <- B f.
+// Symmetric multigrid cycle e_0 <- B f_0: on each level red-black then
+// black-red Gauss-Seidel around the coarse correction, which itself is
+// gamma cycles on the next level (gamma = 1: V-cycle, 2: W-cycle; one visit
+// when the next level is the 1 x 1 grid, solved exactly).  Written as a loop
+// over an explicit per-level visit count (no recursion: the device stack
+// stays fixed).  With adjoint pre- and post-smoothing the cycle is a
+// symmetric positive definite preconditioner for any gamma.
+template <typename T, typename G>
+__device__ void mg_cycle(const G& g, const Level<T>* lev, int nl, int gamma) {
+  int done[kMaxLevels];   // visits of level l+1 finished in the current cycle on level l
+  bool zero[kMaxLevels];  // level l starts from e_l = 0
+  int l = 0;
+  zero[0] = true;
+  while (true) {
+    if (l < nl - 1) {  // descend: pre-smooth, restrict, enter the next level
+      rb_sweep(g, lev[l], 0, zero[l]);
+      rb_sweep(g, lev[l], 1, false);
+      restrict_residual(g, lev[l], lev[l + 1]);
+      done[l] = 0;
+      zero[l + 1] = true;
+      ++l;
+      continue;
+    }
+    {  // coarsest (1 x 1): exact
+      const Level<T>& Lc = lev[l];
+      if (g.rank() == 0) Lc.e[0] = Lc.f[0] * Lc.invd[0];
+      g.sync();
+    }
+    // ascend until a level wants another visit of the level below it
+    bool revisit = false;
+    while (l > 0) {
+      const int up = l - 1;
+      const int visits = (up + 1 == nl - 1) ? 1 : gamma;
+      if (++done[up] < visits) {
+        zero[l] = false;  // visit level `l` again, from its current e
+        revisit = true;
+        break;
+      }
+      prolong_add(g, lev[l], lev[up]);
+      rb_sweep(g, lev[up], 1, false);
+      rb_sweep(g, lev[up], 0, false);
+      l = up;
+    }
+    if (!revisit) return;
+  }
+}
+
+// Symmetric V-cycle: level-0 e <- B f (the loop form of mg_cycle, gamma 1).
 template <typename T, typename G>
 __device__ void vcycle(const G& g, const Level<T>* lev, int nl) {
   for (int l = 0; l < nl - 1; ++l) {
@@ -310,11 +360,19 @@ __device__ void vcycle(const G& g, const Level<T>* lev, int nl) {
   }
 }
 
+template <typename T, typename G>
+__device__ __forceinline__ void precond(const G& g, const Level<T>* lev, int nl, int gamma) {
+  if (gamma <= 1)
+    vcycle(g, lev, nl);
+  else
+    mg_cycle(g, lev, nl, gamma);
+}
+
 // Preconditioned CG on level-0 operator: x = 0 on entry, r = rhs.
 // Stops when r.r <= thr; returns iterations, status 0 converged, 1 hit the
 // cap, 2 breakdown (p.Ap <= 0 or not finite).
 template <typename T, typename G>
-__device__ int pcg(const G& g, const Level<T>* lev, int nl, T* __restrict__ x, T* __restrict__ p,
+__device__ int pcg(const G& g, const Level<T>* lev, int nl, int gamma, T* __restrict__ x, T* __restrict__ p,
                    T* __restrict__ q, T thr, int max_it, T* red, int& par, int& status) {
   const Level<T>& L0 = lev[0];
   const int m = L0.m, n = m * m;
@@ -332,7 +390,7 @@ __device__ int pcg(const G& g, const Level<T>* lev, int nl, T* __restrict__ x, T
     status = 0;
     return 0;
   }
-  vcycle(g, lev, nl);
+  precond(g, lev, nl, gamma);
   T rz = T(0);
   for (int c = g.rank(); c < n; c += step) {
     p[c] = z[c];
@@ -343,10 +401,10 @@ __device__ int pcg(const G& g, const Level<T>* lev, int nl, T* __restrict__ x, T
   while (it < max_it) {
     ++it;
     T pq = T(0);
-    for (int c0 = g.rank(); c0 < n; c0 += kU * step) {
-      T val[kU];
+    for (int c0 = g.rank(); c0 < n; c0 += G::kU * step) {
+      T val[G::kU];
 #pragma unroll
-      for (int u = 0; u < kU; ++u) {
+      for (int u = 0; u < G::kU; ++u) {
         const int c = c0 + u * step;
         val[u] = T(0);
         if (c < n) {
@@ -356,7 +414,7 @@ __device__ int pcg(const G& g, const Level<T>* lev, int nl, T* __restrict__ x, T
         }
       }
 #pragma unroll
-      for (int u = 0; u < kU; ++u)
+      for (int u = 0; u < G::kU; ++u)
         if (c0 + u * step < n) q[c0 + u * step] = val[u];
     }
     pq = g.sum(pq, red, par);
@@ -377,7 +435,7 @@ __device__ int pcg(const G& g, const Level<T>* lev, int nl, T* __restrict__ x, T
       status = 0;
       break;
     }
-    vcycle(g, lev, nl);
+    precond(g, lev, nl, gamma);
     T rzn = T(0);
     for (int c = g.rank(); c < n; c += step) rzn += r[c] * z[c];
     rzn = g.sum(rzn, red, par);
@@ -473,26 +531,41 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
   if (m != m_prev) {  // level table of this system size (each block keeps its copy)
     g.sync();
     if (g.local_leader()) {
-      size_t off[kLayoutSlots];
-      ws_layout(m, sizeof(T), MIXED, off);
+      // walk the layout of ws_layout() (same order, same alignment)
+      size_t o = 0;
+      const size_t n0 = (size_t)m * m;
+      auto take = [&](size_t bytes) {
+        unsigned char* p = base + o;
+        o += align16(bytes);
+        return p;
+      };
+      if (MIXED) {
+        gs.x64 = reinterpret_cast<double*>(take(n0 * 8));
+        gs.r64 = reinterpret_cast<double*>(take(n0 * 8));
+      }
       int l = 0;
       for (int ml = m;; ml >>= 1, ++l) {
+        const size_t nlv = (size_t)ml * ml, nf = (size_t)ml * (ml + 1);
         Level<T>& L = gs.lev[l];
         L.m = ml;
-        L.tx = reinterpret_cast<T*>(base + off[2 + kArrays * l + 0]);
-        L.ty = reinterpret_cast<T*>(base + off[2 + kArrays * l + 1]);
-        L.diag = reinterpret_cast<T*>(base + off[2 + kArrays * l + 2]);
-        L.invd = reinterpret_cast<T*>(base + off[2 + kArrays * l + 3]);
-        L.e = reinterpret_cast<T*>(base + off[2 + kArrays * l + 4]);
-        L.f = reinterpret_cast<T*>(base + off[2 + kArrays * l + 5]);
+        L.tx = reinterpret_cast<T*>(take(nf * sizeof(T)));
+        L.ty = reinterpret_cast<T*>(take(nf * sizeof(T)));
+        L.diag = reinterpret_cast<T*>(take(nlv * sizeof(T)));
+        L.invd = reinterpret_cast<T*>(take(nlv * sizeof(T)));
+        L.e = reinterpret_cast<T*>(take(nlv * sizeof(T)));
+        L.f = reinterpret_cast<T*>(take(nlv * sizeof(T)));
+        if (l == 0) {
+          gs.xv = reinterpret_cast<T*>(take(nlv * sizeof(T)));
+          gs.pv = reinterpret_cast<T*>(take(nlv * sizeof(T)));
+          gs.qv = reinterpret_cast<T*>(take(nlv * sizeof(T)));
+        }
         if (ml == 1) break;
       }
       gs.nl = l + 1;
-      gs.xv = reinterpret_cast<T*>(base + off[2 + kArrays * kMaxLevels + 0]);
-      gs.pv = reinterpret_cast<T*>(base + off[2 + kArrays * kMaxLevels + 1]);
-      gs.qv = reinterpret_cast<T*>(base + off[2 + kArrays * kMaxLevels + 2]);
-      gs.x64 = MIXED ? reinterpret_cast<double*>(base + off[0]) : reinterpret_cast<double*>(gs.xv);
-      gs.r64 = MIXED ? reinterpret_cast<double*>(base + off[1]) : reinterpret_cast<double*>(gs.lev[0].f);
+      if (!MIXED) {
+        gs.x64 = reinterpret_cast<double*>(gs.xv);
+        gs.r64 = reinterpret_cast<double*>(gs.lev[0].f);
+      }
     }
     g.sync();
     m_prev = m;
@@ -581,7 +654,7 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
       bb += bv * bv;
     }
     bb = g.sum(bb, red, par);
-    iters = pcg(g, lev, nl, xv, pv, qv, (T)(a.tol * a.tol) * bb, a.max_it, red, par, status);
+    iters = pcg(g, lev, nl, a.mg_gamma, xv, pv, qv, (T)(a.tol * a.tol) * bb, a.max_it, red, par, status);
   } else {
     // FP64 refinement: r64 = b - A64 x64 with A64 = the FP32 faces in FP64.
     double bb = 0.0;
@@ -617,7 +690,7 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
       r32 = g.sum(r32, red, par);
       int st_in = 1;
       const T thr_in = (T)(a.inner_tol * a.inner_tol) * r32;
-      const int it = pcg(g, lev, nl, xv, pv, qv, thr_in, a.max_it - iters, red, par, st_in);
+      const int it = pcg(g, lev, nl, a.mg_gamma, xv, pv, qv, thr_in, a.max_it - iters, red, par, st_in);
       iters += it;
       // x64 += scl * d, then r64 = b - A64 x64 (FP64)
       for (int c = g.rank(); c < n; c += g.size()) x64[c] += scl * (double)xv[c];
@@ -661,7 +734,8 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
 // MODE 0: one block per system; 1: one warp per system (kWarpsPerBlock
 // systems per block); 2: one thread-block cluster per system.
 template <bool MIXED, int MODE>
-__global__ void __launch_bounds__(MODE == 1 ? 32 * kWarpsPerBlock : kMaxThreads) solve_kernel(SolveArgs a) {
+__global__ void __launch_bounds__(MODE == 1 ? 32 * kWarpsPerBlock : kMaxThreads, MODE == 1 ? 5 : 2)
+    solve_kernel(SolveArgs a) {
   using T = typename std::conditional<MIXED, float, double>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int kGroups = MODE == 1 ? kWarpsPerBlock : 1;
@@ -714,6 +788,7 @@ static int plan_fill(int m, int threads, int cluster, SolvePlan* P) {
   P->use_smem = MODE != 2 && P->ws_stride * P->groups_per_block <= kSmemCap;
   P->smem_bytes = P->use_smem ? P->ws_stride * P->groups_per_block : 0;
   P->cap_blocks_per_sm = 0;
+  P->gamma = 1;
   cudaFuncSetAttribute(solve_kernel<MIXED, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<MIXED, MODE>, P->threads, P->smem_bytes) !=
@@ -752,7 +827,11 @@ static int plan_fill(int m, int prec, int mode, int threads, int cluster, SolveP
   return plan_fill<false, 0>(m, threads, cluster, P);
 }
 
+// Default plan (measured on GB300 with the autotuner): a warp per system up
+// to m = 16, a block up to m = 256, a cluster of 4 blocks at m = 512 and of 8
+// above (the system's working set then sits in L2 instead of streaming).
 int solve_plan(int m, int prec, SolvePlan* P) {
+  if (m >= 512) return plan_fill(m, prec, 2, kMaxThreads, m >= 1024 ? 8 : 4, P);
   return plan_fill(m, prec, solve_warp_mode(m) ? 1 : 0, solve_threads(m), 0, P);
 }
 
@@ -768,12 +847,17 @@ int solve_plan_candidates(int m, int prec, SolvePlan* out, int max_out) {
   SolvePlan d;
   if (solve_plan(m, prec, &d)) return 0;
   add(d);
+  if (d.cluster) {  // also the one-block plan
+    SolvePlan b;
+    if (!plan_fill(m, prec, 0, kMaxThreads, 0, &b)) add(b);
+  }
   if (m <= 64 && !d.warp) {
     SolvePlan w;
     if (!plan_fill(m, prec, 1, 0, 0, &w)) add(w);
   }
   for (int t : {64, 128, 256, 512}) {
-    if (!d.warp && t == d.threads) continue;
+    if (!d.warp && !d.cluster && t == d.threads) continue;
+    if (d.cluster && t == kMaxThreads) continue;
     if (t > 2 * m * m) continue;  // more threads than cells
     SolvePlan b;
     if (!plan_fill(m, prec, 0, t, 0, &b)) add(b);
@@ -789,6 +873,7 @@ int solve_plan_candidates(int m, int prec, SolvePlan* out, int max_out) {
   // large grids: one cluster of 2, 4 or 8 blocks per system
   if (m >= 128)
     for (int cl : {2, 4, 8}) {
+      if (cl == d.cluster) continue;
       SolvePlan c;
       if (!plan_fill(m, prec, 2, kMaxThreads, cl, &c)) add(c);
     }
@@ -799,6 +884,7 @@ int solve_launch(const SolveArgs& a, int prec, const SolvePlan& P, int n_blocks,
   SolveArgs b = a;
   b.use_smem = P.use_smem;
   b.ws_stride = P.ws_stride;
+  b.mg_gamma = P.gamma;
   if (P.cluster) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
