@@ -21,7 +21,10 @@
  *    they are owned by the caller.  "host pointer" arguments are owned by the
  *    caller too.  The context owns every internal workspace and table.
  *  - All GPU work is issued on the stream given to mlmc_create(); a call
- *    returns after its host-visible results are complete.
+ *    returns after its host-visible results are complete (except
+ *    mlmc_solve_k_static, which only queues its work).
+ *  - A context is used by one host thread at a time; different contexts
+ *    are independent.
  *  - There is no CPU fallback: without a usable GPU, mlmc_create() fails.
  *  - Grid layout: level l has m = m0 * 2^l cells per side; cell (i, j),
  *    0-based, has centre ((i + 1/2)/m, (j + 1/2)/m); per-sample arrays are
@@ -190,6 +193,7 @@ typedef struct mlmc_tune_report {
   int32_t cap_blocks_per_sm[MLMC_MAX_LEVELS];  /* 0: occupancy limit */
   int32_t cluster[MLMC_MAX_LEVELS];            /* > 0: blocks of the cluster that solves one system */
   int32_t gamma[MLMC_MAX_LEVELS];              /* multigrid cycle: 1 V, 2 W */
+  int32_t nu[MLMC_MAX_LEVELS];                 /* red-black sweep pairs per smoothing */
   int32_t candidates[MLMC_MAX_LEVELS];         /* plans timed */
   double ms_default[MLMC_MAX_LEVELS];          /* ms per sample, default plan */
   double ms_best[MLMC_MAX_LEVELS];             /* ms per sample, chosen plan */
@@ -197,8 +201,8 @@ typedef struct mlmc_tune_report {
 
 /* Times the candidate launch plans of the solver (one warp, one block of
  * 64/128/256/512 threads, or, for m >= 128, one thread-block cluster of 2, 4
- * or 8 blocks per system; all resident blocks or one per SM; V- or
- * W-cycles in the preconditioner) on a
+ * or 8 blocks per system; all resident blocks or one per SM; for the
+ * fastest of those, W-cycles or two smoothing sweep pairs) on a
  * probe batch of each level (samples from index 2^40 on, so no sample of
  * real use is consumed) and keeps the fastest for that level's solves.  The
  * arithmetic of a system does not depend on the plan except for the
@@ -209,10 +213,11 @@ MLMC_API int mlmc_autotune(mlmc_ctx* ctx, uint64_t seed, mlmc_tune_report* rep);
  * mlmc_autotune): mode 0 = one block of `threads` (32..512, multiple of 32)
  * per system, 1 = one warp per system, 2 = one thread-block cluster of
  * `cluster` (2, 4, 8) blocks of 512 threads per system; gamma 1 = V-cycle,
- * 2 = W-cycle preconditioner; mode < 0 restores the built-in default
- * (V-cycle).  Errors: MLMC_ERR_ARG. */
+ * 2 = W-cycle preconditioner; nu = 1..4 red-black sweep pairs before and
+ * after each coarse correction; mode < 0 restores the built-in default
+ * (V-cycle, nu = 1).  Errors: MLMC_ERR_ARG. */
 MLMC_API int mlmc_set_launch(mlmc_ctx* ctx, int level, int32_t mode, int32_t threads, int32_t cluster,
-                             int32_t gamma);
+                             int32_t gamma, int32_t nu);
 
 /* Padding of level `level`: *M_out = M, and the smallest / largest raw
  * embedding eigenvalue before clipping (host pointers, any may be NULL). */

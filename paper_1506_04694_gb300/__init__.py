@@ -66,7 +66,7 @@ STAGES = ("fields", "solve", "reduce")
 class TuneReport(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32 * MAX_LEVELS), ("warp", ctypes.c_int32 * MAX_LEVELS),
                 ("cap_blocks_per_sm", ctypes.c_int32 * MAX_LEVELS), ("cluster", ctypes.c_int32 * MAX_LEVELS),
-                ("gamma", ctypes.c_int32 * MAX_LEVELS),
+                ("gamma", ctypes.c_int32 * MAX_LEVELS), ("nu", ctypes.c_int32 * MAX_LEVELS),
                 ("candidates", ctypes.c_int32 * MAX_LEVELS),
                 ("ms_default", ctypes.c_double * MAX_LEVELS), ("ms_best", ctypes.c_double * MAX_LEVELS)]
 
@@ -97,7 +97,7 @@ EXPORTS = {
     "mlmc_checkpoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "mlmc_resume": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "mlmc_set_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
-                                       ctypes.c_int32, ctypes.c_int32]),
+                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "mlmc_ce_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "mlmc_philox_words": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
@@ -281,7 +281,7 @@ class Context:
         _check(lib().mlmc_autotune(self._h, seed, ctypes.byref(r)), allow_failed=False)
         L = self.model.L + 1
         return [{"threads": r.threads[i], "warp": r.warp[i], "cap_blocks_per_sm": r.cap_blocks_per_sm[i],
-                 "cluster": r.cluster[i], "gamma": r.gamma[i],
+                 "cluster": r.cluster[i], "gamma": r.gamma[i], "nu": r.nu[i],
                  "candidates": r.candidates[i], "ms_per_sample_default": r.ms_default[i],
                  "ms_per_sample_best": r.ms_best[i]} for i in range(L)]
 
@@ -297,10 +297,10 @@ class Context:
                 "cell_iters": p.cell_iters, "cells": p.cells, "fft_row_points": p.fft_row_points,
                 "fft_col_points": p.fft_col_points, "samples": p.samples}
 
-    def set_launch(self, level, mode, threads=256, cluster=0, gamma=1):
-        """mlmc_set_launch: fix a level's solver launch (0 block, 1 warp, 2 cluster; <0 default)
-        and its multigrid cycle (gamma 1 V, 2 W)."""
-        _check(lib().mlmc_set_launch(self._h, level, mode, threads, cluster, gamma), allow_failed=False)
+    def set_launch(self, level, mode, threads=256, cluster=0, gamma=1, nu=1):
+        """mlmc_set_launch: fix a level's solver launch (0 block, 1 warp, 2 cluster; <0 default),
+        its multigrid cycle (gamma 1 V, 2 W) and smoothing sweep pairs nu."""
+        _check(lib().mlmc_set_launch(self._h, level, mode, threads, cluster, gamma, nu), allow_failed=False)
 
     def ce_info(self, level):
         M = ctypes.c_int32()

@@ -416,7 +416,8 @@ int multilevel_impl(mlmc_ctx* c, int n_levels, const int64_t* first, const int64
   if (graph) {
     std::vector<int64_t> key = {(int64_t)n_levels, (int64_t)seed, (int64_t)g_alloc_generation.load()};
     for (int l = 0; l < n_levels; ++l)
-      key.push_back(c->tuned_ok[l] ? ((int64_t)c->tuned[l].gamma << 24) + ((int64_t)c->tuned[l].threads << 16) +
+      key.push_back(c->tuned_ok[l] ? ((int64_t)c->tuned[l].nu << 28) + ((int64_t)c->tuned[l].gamma << 24) +
+                                         ((int64_t)c->tuned[l].threads << 16) +
                                          (c->tuned[l].cluster << 8) + (c->tuned[l].warp << 4) +
                                          c->tuned[l].cap_blocks_per_sm
                                    : -1);
@@ -840,7 +841,7 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
       if ((err = run_fields(c, l, a.first, n, seed))) break;
       a.g = c->g.p;
     }
-    SolvePlan cand[17];
+    SolvePlan cand[18];
     int nk = solve_plan_candidates(m, md.prec, cand, 16);
     float best = 1e30f, def_ms = 0.f;
     int best_k = -1;
@@ -866,15 +867,19 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
         best_k = k;
       }
     }
-    if (!err && best_k >= 0) {  // the fastest plan once more with W-cycles
-      cand[nk] = cand[best_k];
-      cand[nk].gamma = 2;
-      const float ms = time_plan(cand[nk]);
-      if (ms < best) {
-        best = ms;
-        best_k = nk;
+    if (!err && best_k >= 0) {  // the fastest plan once more with W-cycles, and with two sweep pairs
+      const SolvePlan base = cand[best_k];
+      for (int v = 0; v < 2 && !err; ++v) {
+        cand[nk] = base;
+        if (v == 0) cand[nk].gamma = 2;
+        else cand[nk].nu = 2;
+        const float ms = time_plan(cand[nk]);
+        if (ms < best) {
+          best = ms;
+          best_k = nk;
+        }
+        ++nk;
       }
-      ++nk;
     }
     if (err || best_k < 0) break;
     c->tuned[l] = cand[best_k];
@@ -885,6 +890,7 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
       rep->cap_blocks_per_sm[l] = cand[best_k].cap_blocks_per_sm;
       rep->cluster[l] = cand[best_k].cluster;
       rep->gamma[l] = cand[best_k].gamma;
+      rep->nu[l] = cand[best_k].nu;
       rep->candidates[l] = nk;
       rep->ms_default[l] = def_ms / n;
       rep->ms_best[l] = best / n;
@@ -908,7 +914,8 @@ int mlmc_profile_read(mlmc_ctx* c, mlmc_profile_stats* out) {
   return 0;
 }
 
-int mlmc_set_launch(mlmc_ctx* c, int level, int32_t mode, int32_t threads, int32_t cluster, int32_t gamma) {
+int mlmc_set_launch(mlmc_ctx* c, int level, int32_t mode, int32_t threads, int32_t cluster, int32_t gamma,
+                    int32_t nu) {
   if (!c || level < 0 || level > c->model.L) return fail(MLMC_ERR_ARG, "bad context or level");
   CUDA_TRY(cudaSetDevice(c->device));
   if (mode < 0) {
@@ -920,9 +927,11 @@ int mlmc_set_launch(mlmc_ctx* c, int level, int32_t mode, int32_t threads, int32
     return fail(MLMC_ERR_ARG, "mode 0: threads 32..512 (multiple of 32); mode 2: cluster 2, 4 or 8");
   SolvePlan P;
   if (gamma < 1 || gamma > 2) return fail(MLMC_ERR_ARG, "gamma must be 1 (V-cycle) or 2 (W-cycle)");
+  if (nu < 1 || nu > 4) return fail(MLMC_ERR_ARG, "nu must be 1..4");
   if (solve_plan_mode(c->model.m0 << level, c->model.prec, mode, mode == 0 ? threads : 512, cluster, &P))
     return fail(MLMC_ERR_CUDA, "launch plan query failed");
   P.gamma = gamma;
+  P.nu = nu;
   c->tuned[level] = P;
   c->tuned_ok[level] = true;
   return 0;

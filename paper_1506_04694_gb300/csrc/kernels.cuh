@@ -72,6 +72,7 @@ struct SolveArgs {
   int max_it;
   double inner_tol;    // mixed: relative tolerance of each FP32 inner solve
   int mg_gamma;        // multigrid cycle: 1 V, 2 W (set from the launch plan)
+  int mg_nu;           // red-black sweep pairs before and after the coarse correction
   // workspace
   int use_smem;
   size_t ws_stride;    // bytes per block slot (global workspace)
@@ -96,6 +97,7 @@ struct SolvePlan {
   size_t smem_bytes;     // dynamic shared memory per block
   int cap_blocks_per_sm; // > 0: launch at most this many blocks per SM (L2 residency)
   int gamma;             // multigrid cycle index: 1 V-cycle, 2 W-cycle
+  int nu;                // smoothing: red-black sweep pairs before and after the coarse correction
 };
 
 size_t solve_ws_bytes(int m, int prec);

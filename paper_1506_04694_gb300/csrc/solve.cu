@@ -301,15 +301,17 @@ __device__ __forceinline__ void build_diag(const G& g, const Level<T>& L) {
 // stays fixed).  With adjoint pre- and post-smoothing the cycle is a
 // symmetric positive definite preconditioner for any gamma.
 template <typename T, typename G>
-__device__ void mg_cycle(const G& g, const Level<T>* lev, int nl, int gamma) {
+__device__ void mg_cycle(const G& g, const Level<T>* lev, int nl, int gamma, int nu) {
   int done[kMaxLevels];   // visits of level l+1 finished in the current cycle on level l
   bool zero[kMaxLevels];  // level l starts from e_l = 0
   int l = 0;
   zero[0] = true;
   while (true) {
     if (l < nl - 1) {  // descend: pre-smooth, restrict, enter the next level
-      rb_sweep(g, lev[l], 0, zero[l]);
-      rb_sweep(g, lev[l], 1, false);
+      for (int s = 0; s < nu; ++s) {
+        rb_sweep(g, lev[l], 0, zero[l] && s == 0);
+        rb_sweep(g, lev[l], 1, false);
+      }
       restrict_residual(g, lev[l], lev[l + 1]);
       done[l] = 0;
       zero[l + 1] = true;
@@ -332,8 +334,10 @@ __device__ void mg_cycle(const G& g, const Level<T>* lev, int nl, int gamma) {
         break;
       }
       prolong_add(g, lev[l], lev[up]);
-      rb_sweep(g, lev[up], 1, false);
-      rb_sweep(g, lev[up], 0, false);
+      for (int s = 0; s < nu; ++s) {
+        rb_sweep(g, lev[up], 1, false);
+        rb_sweep(g, lev[up], 0, false);
+      }
       l = up;
     }
     if (!revisit) return;
@@ -361,18 +365,18 @@ __device__ void vcycle(const G& g, const Level<T>* lev, int nl) {
 }
 
 template <typename T, typename G>
-__device__ __forceinline__ void precond(const G& g, const Level<T>* lev, int nl, int gamma) {
-  if (gamma <= 1)
+__device__ __forceinline__ void precond(const G& g, const Level<T>* lev, int nl, int gamma, int nu) {
+  if (gamma <= 1 && nu <= 1)
     vcycle(g, lev, nl);
   else
-    mg_cycle(g, lev, nl, gamma);
+    mg_cycle(g, lev, nl, gamma < 1 ? 1 : gamma, nu < 1 ? 1 : nu);
 }
 
 // Preconditioned CG on level-0 operator: x = 0 on entry, r = rhs.
 // Stops when r.r <= thr; returns iterations, status 0 converged, 1 hit the
 // cap, 2 breakdown (p.Ap <= 0 or not finite).
 template <typename T, typename G>
-__device__ int pcg(const G& g, const Level<T>* lev, int nl, int gamma, T* __restrict__ x, T* __restrict__ p,
+__device__ int pcg(const G& g, const Level<T>* lev, int nl, int gamma, int nu, T* __restrict__ x, T* __restrict__ p,
                    T* __restrict__ q, T thr, int max_it, T* red, int& par, int& status) {
   const Level<T>& L0 = lev[0];
   const int m = L0.m, n = m * m;
@@ -390,7 +394,7 @@ __device__ int pcg(const G& g, const Level<T>* lev, int nl, int gamma, T* __rest
     status = 0;
     return 0;
   }
-  precond(g, lev, nl, gamma);
+  precond(g, lev, nl, gamma, nu);
   T rz = T(0);
   for (int c = g.rank(); c < n; c += step) {
     p[c] = z[c];
@@ -435,7 +439,7 @@ __device__ int pcg(const G& g, const Level<T>* lev, int nl, int gamma, T* __rest
       status = 0;
       break;
     }
-    precond(g, lev, nl, gamma);
+    precond(g, lev, nl, gamma, nu);
     T rzn = T(0);
     for (int c = g.rank(); c < n; c += step) rzn += r[c] * z[c];
     rzn = g.sum(rzn, red, par);
@@ -654,7 +658,7 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
       bb += bv * bv;
     }
     bb = g.sum(bb, red, par);
-    iters = pcg(g, lev, nl, a.mg_gamma, xv, pv, qv, (T)(a.tol * a.tol) * bb, a.max_it, red, par, status);
+    iters = pcg(g, lev, nl, a.mg_gamma, a.mg_nu, xv, pv, qv, (T)(a.tol * a.tol) * bb, a.max_it, red, par, status);
   } else {
     // FP64 refinement: r64 = b - A64 x64 with A64 = the FP32 faces in FP64.
     double bb = 0.0;
@@ -690,7 +694,7 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
       r32 = g.sum(r32, red, par);
       int st_in = 1;
       const T thr_in = (T)(a.inner_tol * a.inner_tol) * r32;
-      const int it = pcg(g, lev, nl, a.mg_gamma, xv, pv, qv, thr_in, a.max_it - iters, red, par, st_in);
+      const int it = pcg(g, lev, nl, a.mg_gamma, a.mg_nu, xv, pv, qv, thr_in, a.max_it - iters, red, par, st_in);
       iters += it;
       // x64 += scl * d, then r64 = b - A64 x64 (FP64)
       for (int c = g.rank(); c < n; c += g.size()) x64[c] += scl * (double)xv[c];
@@ -789,6 +793,7 @@ static int plan_fill(int m, int threads, int cluster, SolvePlan* P) {
   P->smem_bytes = P->use_smem ? P->ws_stride * P->groups_per_block : 0;
   P->cap_blocks_per_sm = 0;
   P->gamma = 1;
+  P->nu = 1;
   cudaFuncSetAttribute(solve_kernel<MIXED, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<MIXED, MODE>, P->threads, P->smem_bytes) !=
@@ -885,6 +890,7 @@ int solve_launch(const SolveArgs& a, int prec, const SolvePlan& P, int n_blocks,
   b.use_smem = P.use_smem;
   b.ws_stride = P.ws_stride;
   b.mg_gamma = P.gamma;
+  b.mg_nu = P.nu;
   if (P.cluster) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];

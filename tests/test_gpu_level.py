@@ -239,22 +239,24 @@ def test_nan_permeability_reported_as_failure():
 @pytest.mark.parametrize("prec", [0, 1])
 def test_launch_modes_agree(prec):
     # one system per block (64..512 threads), per warp, or per thread-block
-    # cluster of 2/4/8 blocks, with V- or W-cycles: the same systems give the
-    # same Q to the solver tolerance and agree with the oracle
+    # cluster of 2/4/8 blocks, with V- or W-cycles and one or two smoothing
+    # sweep pairs: the same systems give the same Q to the solver tolerance
+    # and agree with the oracle
     torch, pk = need_gpu()
     d = workloads.workload("lognormal_2layer_cgv_16to512", prec=prec, cgv=1, tol=1e-13, m0=16, L=4)
     model = darcy.Model.from_dict(d)
     level, n = 3, 10   # m = 128: fine 128^2 and four 64^2 coarse systems per sample
-    modes = [(0, 512, 0, 1), (0, 64, 0, 1), (1, 0, 0, 1), (2, 512, 2, 1), (2, 512, 4, 1), (2, 512, 8, 1),
-             (0, 256, 0, 2), (1, 0, 0, 2), (2, 512, 4, 2)]
+    modes = [(0, 512, 0, 1, 1), (0, 64, 0, 1, 1), (1, 0, 0, 1, 1), (2, 512, 2, 1, 1), (2, 512, 4, 1, 1),
+             (2, 512, 8, 1, 1), (0, 256, 0, 2, 1), (1, 0, 0, 2, 1), (2, 512, 4, 2, 1), (0, 256, 0, 1, 2),
+             (2, 512, 4, 1, 2), (1, 0, 0, 2, 2)]
     res = []
     with pk.Context(d) as ctx:
-        for mode, threads, cl, gamma in modes:
-            ctx.set_launch(level, mode, threads, cl, gamma)
+        for mode, threads, cl, gamma, nu in modes:
+            ctx.set_launch(level, mode, threads, cl, gamma, nu)
             qf = torch.empty(n, dtype=torch.float64, device="cuda")
             qg = torch.empty_like(qf)
             s = ctx.level_batch(level, n, 4, qf=qf, qc_cgv=qg)
-            assert s["n"] == n and s["n_failed"] == 0, (mode, threads, cl, gamma)
+            assert s["n"] == n and s["n_failed"] == 0, (mode, threads, cl, gamma, nu)
             res.append((qf.cpu().numpy(), qg.cpu().numpy()))
     tol = 1e-10 if prec == 0 else RTOL_MIX
     for qf, qg in res[1:]:
