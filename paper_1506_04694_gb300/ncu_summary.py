@@ -1,6 +1,8 @@
 """Summarise an ncu launch list (``--metrics gpu__time_duration.sum --csv``):
 per kernel, launches, total device time and share.  Usage:
-    python -m paper_1506_04694_gb300.ncu_summary launches.csv"""
+    python -m paper_1506_04694_gb300.ncu_summary launches.csv [--skip N]
+--skip N leaves out the first N launches (e.g. the set-up of a benchmark:
+embedding tables and the launch-plan autotuner)."""
 import collections
 import csv
 import sys
@@ -9,14 +11,17 @@ UNITS = {"ns": 1.0, "nsecond": 1.0, "us": 1e3, "usecond": 1e3, "ms": 1e6, "mseco
          "s": 1e9, "second": 1e9}
 
 
-def summarise(path):
+def summarise(path, skip=0):
     rows = list(csv.reader(open(path)))
     start = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
     hdr = rows[start]
     ki, vi, ui = hdr.index("Kernel Name"), hdr.index("Metric Value"), hdr.index("Metric Unit")
+    idi = hdr.index("ID") if "ID" in hdr else None
     agg = collections.OrderedDict()
-    for r in rows[start + 1:]:
+    for n, r in enumerate(rows[start + 1:]):
         if len(r) <= vi or not r[vi]:
+            continue
+        if (int(r[idi]) if idi is not None else n) < skip:
             continue
         name = r[ki].split("(")[0].strip()
         ns = float(r[vi].replace(",", "")) * UNITS[r[ui].strip()]
@@ -32,4 +37,5 @@ def summarise(path):
 
 
 if __name__ == "__main__":
-    print(summarise(sys.argv[1]))
+    skip = int(sys.argv[sys.argv.index("--skip") + 1]) if "--skip" in sys.argv else 0
+    print(summarise(sys.argv[1], skip))
