@@ -28,12 +28,6 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 DEFAULT_WORKLOAD = "lognormal_2layer_16to256"
-# Algorithmic FP64 flops of one CG iteration per fine cell of the FP64 solver:
-# operator apply 11 + p.q 2; x, r updates and r.r 6; symmetric V(1,1) cycle
-# ~29.5 per finest cell (half-sweep zero-guess 0.5, black sweep 5, fused
-# residual + restriction 13, prolongation 1, two post half-sweeps 10) times
-# 4/3 for the coarser grids; r.z 2; p update 2.
-FLOPS_PER_CELL_ITER = 13 + 6 + 29.5 * 4.0 / 3.0 + 4
 # FP64 vector peak of GB300 (nominal 1.25 TFLOP/s: 152 SMs x 2 FP64 FMA/clk x
 # 2 flop x ~2.06 GHz).
 FP64_PEAK_TFLOPS = 1.25
@@ -355,7 +349,8 @@ def main():
     launches = int(sum(prof["launches"].values()))
     roof = None
     if dom == "solve" and d["prec"] == 0:
-        flops = FLOPS_PER_CELL_ITER * prof["cell_iters"]
+        # algorithmic flops counted by the library per level from its cycle (V/W, sweeps)
+        flops = prof["solve_flops"]
         ach = flops / (stage_ms["solve"] / 1e3) / 1e12
         roof = {"kernel": "solve_kernel<false> (assembly + MG-PCG + QoI, FP64)", "bound": "alu",
                 "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
@@ -379,8 +374,9 @@ def main():
         "q_hat": est["q_hat"], "var_hat": est["var_hat"],
         "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
         "iters_per_cell_solve": prof["cell_iters"] / max(prof["cells"], 1.0),
-        "autotune": [{"m": d["m0"] << l, "threads": t["threads"], "warp": t["warp"],
-                      "cap_blocks_per_sm": t["cap_blocks_per_sm"]} for l, t in enumerate(tune)],
+        "autotune": [{"m": d["m0"] << l, "threads": t["threads"], "warp": t["warp"], "cluster": t["cluster"],
+                      "cap_blocks_per_sm": t["cap_blocks_per_sm"], "gamma": t["gamma"], "nu": t["nu"]}
+                     for l, t in enumerate(tune)],
     }
     if not args.no_cpu_baseline:
         cores = min(host_cores(), 16)

@@ -86,6 +86,12 @@ typedef struct mlmc_model {
                                      FP32 circulant-embedding FFT */
   double tol;                  /* stop when ||b - A x||_2 < tol ||b||_2 (Sec. 3.5 uses 1e-10) */
   int32_t max_it;              /* cap on CG iterations per solve (sum over refinement sweeps) */
+  int32_t problem;             /* 0 or 2: Model Problem 2 of Sec. 3.4 (p = 1 / 0 at x1 = 0 / 1, no
+                                     flow elsewhere, Q = outflow at x1 = 1);
+                                  1: Model Problem 1 of Sec. 3.4 (f = 1, p = 0 on the whole
+                                     boundary, Q = mean of p over the box qoi_box) */
+  double qoi_box[4];           /* problem 1: D* = [x0, x1] x [y0, y1] inside (0,1)^2; all zero
+                                  selects [7/16, 9/16]^2 around x* = (1/2, 1/2) */
 } mlmc_model;
 
 /* Level sums over a range of samples (Eq. 3.6 and Eq. 4.2): Q_f is Q_l of the
@@ -294,6 +300,9 @@ typedef struct mlmc_profile_stats {
   double fft_row_points;   /* sum of M*M complex points transformed by the row pass */
   double fft_col_points;   /* sum of m*M complex points transformed by the column pass */
   double samples;          /* samples processed */
+  double solve_flops;      /* algorithmic flops of the CG iterations: per cell-iteration 21 for CG
+                              plus (2.25 + 18 nu) per finest cell for the multigrid cycle, times 4/3
+                              (V-cycle) or 2 (W-cycle) for the coarser grids */
 } mlmc_profile_stats;
 
 /* enable != 0: reset the counters and start collecting; 0: stop. */

@@ -14,6 +14,8 @@ Follows the paper section by section:
   flux.
 * Sec. 3.4, Model Problem 2: p = 1 at x1 = 0, p = 0 at x1 = 1, no flow on
   x2 = 0 and x2 = 1; the quantity of interest M^(2) is the outflow at x1 = 1.
+* Sec. 3.4, Model Problem 1: f = 1, p = 0 on the whole boundary; the quantity
+  of interest M^(1) is the mean of p over a small box D* around x*.
 
 Layout: a grid of m x m cells, cell (i, j) 0-based with centre
 ((i + 1/2) h, (j + 1/2) h), h = 1/m; arrays are indexed [j, i] (x1 = flow
@@ -48,6 +50,8 @@ class Model:
         per-layer Gaussian fields, 2 CGV subsampling the composed k.
     tol: relative residual tolerance of iterative solvers (unused by the
         direct solve of the oracle).
+    problem: 2 (or 0) = Model Problem 2, outflow; 1 = Model Problem 1, local
+        average of p over the box qoi_box = (x0, x1, y0, y1).
     """
     n_layers: int = 2
     k_kind: int = 0
@@ -63,10 +67,14 @@ class Model:
     prec: int = 0
     tol: float = 1e-12
     max_it: int = 200
+    problem: int = 2
+    qoi_box: List[float] = field(default_factory=lambda: [7 / 16, 9 / 16, 7 / 16, 9 / 16])
 
     @classmethod
     def from_dict(cls, d):
         kw = {k: d[k] for k in cls.__dataclass_fields__ if k in d}
+        if kw.get("problem", 2) == 0:
+            kw["problem"] = 2
         for key in ("mu", "sigma2", "lam"):
             if key in kw:
                 v = list(kw[key]) + [kw[key][-1]] * (8 - len(kw[key]))
@@ -180,14 +188,15 @@ def compose_k(g, rows_layer):
 
 
 # ----------------------------------------------------------------- TPFA -----
-def transmissibilities(k):
+def transmissibilities(k, problem=2):
     """Face coefficients of Eq. 3.3 with harmonic face averages.
 
     tx[j, i'] for the m+1 faces x1 = i'/m of row j: interior faces
     2 k_a k_b / (k_a + k_b); Dirichlet faces (i' = 0, m) 2 k_cell from the
     one-sided difference over half a cell.
     ty[j', i] for the m+1 faces x2 = j'/m of column i: interior faces harmonic;
-    the no-flow faces (j' = 0, m) carry 0."""
+    the faces j' = 0, m carry 0 (no flow, Model Problem 2) or 2 k_cell
+    (Dirichlet, Model Problem 1)."""
     m = k.shape[0]
     tx = np.zeros((m, m + 1))
     ty = np.zeros((m + 1, m))
@@ -197,13 +206,20 @@ def transmissibilities(k):
     tx[:, m] = 2.0 * k[:, m - 1]
     ka, kb = k[:-1, :], k[1:, :]
     ty[1:m, :] = 2.0 * ka * kb / (ka + kb)
+    if problem == 1:
+        ty[0, :] = 2.0 * k[0, :]
+        ty[m, :] = 2.0 * k[m - 1, :]
     return tx, ty
 
 
-def rhs(tx):
-    """Right-hand side: the Dirichlet value p = 1 at x1 = 0 enters through the
-    west boundary face of column i = 0 (f = 0 in Model Problem 2)."""
+def rhs(tx, problem=2):
+    """Right-hand side.  Model Problem 2: the Dirichlet value p = 1 at x1 = 0
+    enters through the west boundary face of column i = 0 (f = 0).  Model
+    Problem 1: f = 1 by the midpoint rule, f / m^2 in every cell (p = 0 on the
+    boundary adds nothing)."""
     m = tx.shape[0]
+    if problem == 1:
+        return np.full((m, m), 1.0 / (m * m))
     b = np.zeros((m, m))
     b[:, 0] = tx[:, 0] * 1.0
     return b
@@ -245,11 +261,27 @@ def inflow(tx, p):
     return float(np.sum(tx[:, 0] * (1.0 - p[:, 0])))
 
 
-def solve_k(k):
-    """Assemble and solve for one permeability array; returns (p, Q)."""
-    tx, ty = transmissibilities(k)
-    p = solve_direct(tx, ty, rhs(tx))
-    return p, outflow(tx, p)
+def box_weights(m, box):
+    """Weights w[j, i] = |cell (i, j) & D*| / |D*| of the box D* = [x0, x1] x
+    [y0, y1]: M^(1) of the piecewise constant p is sum w p."""
+    x0, x1, y0, y1 = box
+    e = np.arange(m + 1) / m
+    ox = np.clip(np.minimum(e[1:], x1) - np.maximum(e[:-1], x0), 0.0, None)
+    oy = np.clip(np.minimum(e[1:], y1) - np.maximum(e[:-1], y0), 0.0, None)
+    return np.outer(oy, ox) / ((x1 - x0) * (y1 - y0))
+
+
+def local_average(p, box):
+    """M^(1): mean of the piecewise constant p over D*."""
+    return float(np.sum(box_weights(p.shape[0], box) * p))
+
+
+def solve_k(k, problem=2, box=(7 / 16, 9 / 16, 7 / 16, 9 / 16)):
+    """Assemble and solve for one permeability array; returns (p, Q) with Q the
+    outflow (Model Problem 2) or the local average (Model Problem 1)."""
+    tx, ty = transmissibilities(k, problem)
+    p = solve_direct(tx, ty, rhs(tx, problem))
+    return p, (local_average(p, box) if problem == 1 else outflow(tx, p))
 
 
 # ------------------------------------------------------- one MLMC sample ----
@@ -290,7 +322,9 @@ def sample(model, seed, level, i, ce_cache=None, want_fields=False):
     rows = layer_of_rows(eta, m)
     g = layer_fields(model, seed, level, i, m, ce_cache)
     k = compose_k(g, rows)
-    p, qf = solve_k(k)
+    prob = 1 if model.problem == 1 else 2
+    box = tuple(model.qoi_box)
+    p, qf = solve_k(k, prob, box)
     out = {"qf": qf, "qc": 0.0, "qc_cgv": float("nan"), "eta": eta, "rows": rows,
            "inflow": inflow(transmissibilities(k)[0], p)}
     if want_fields:
@@ -298,10 +332,10 @@ def sample(model, seed, level, i, ce_cache=None, want_fields=False):
     if level > 0:
         if model.cgv == 0:
             (kc,) = coarse_samples(model, g, k, eta, 0)
-            out["qc"] = solve_k(kc)[1]
+            out["qc"] = solve_k(kc, prob, box)[1]
         else:
             kcs = coarse_samples(model, g, k, eta, model.cgv)
-            qcs = [solve_k(kc)[1] for kc in kcs]
+            qcs = [solve_k(kc, prob, box)[1] for kc in kcs]
             out["qc"] = qcs[0]
             out["qc_cgv"] = 0.25 * (((qcs[0] + qcs[1]) + qcs[2]) + qcs[3])
             out["qc_each"] = qcs

@@ -30,6 +30,7 @@ class Model(ctypes.Structure):
         ("norm_r", ctypes.c_int32), ("m0", ctypes.c_int32), ("L", ctypes.c_int32),
         ("cgv", ctypes.c_int32), ("prec", ctypes.c_int32),
         ("tol", ctypes.c_double), ("max_it", ctypes.c_int32),
+        ("problem", ctypes.c_int32), ("qoi_box", ctypes.c_double * 4),
     ]
 
 
@@ -57,7 +58,7 @@ class ProfileStats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64 * 3), ("ms", ctypes.c_double * 3),
                 ("cell_iters", ctypes.c_double), ("cells", ctypes.c_double),
                 ("fft_row_points", ctypes.c_double), ("fft_col_points", ctypes.c_double),
-                ("samples", ctypes.c_double)]
+                ("samples", ctypes.c_double), ("solve_flops", ctypes.c_double)]
 
 
 STAGES = ("fields", "solve", "reduce")
@@ -152,6 +153,8 @@ def make_model(d):
         if name in ("mu", "sigma2", "lam"):
             arr = list(v) + [v[-1]] * (MAX_LAYERS - len(v))
             setattr(m, name, (ctypes.c_double * MAX_LAYERS)(*arr[:MAX_LAYERS]))
+        elif name == "qoi_box":
+            setattr(m, name, (ctypes.c_double * 4)(*v))
         else:
             setattr(m, name, v)
     return m
@@ -295,7 +298,7 @@ class Context:
         _check(lib().mlmc_profile_read(self._h, ctypes.byref(p)), allow_failed=False)
         return {"launches": dict(zip(STAGES, p.launches)), "ms": dict(zip(STAGES, p.ms)),
                 "cell_iters": p.cell_iters, "cells": p.cells, "fft_row_points": p.fft_row_points,
-                "fft_col_points": p.fft_col_points, "samples": p.samples}
+                "fft_col_points": p.fft_col_points, "samples": p.samples, "solve_flops": p.solve_flops}
 
     def set_launch(self, level, mode, threads=256, cluster=0, gamma=1, nu=1):
         """mlmc_set_launch: fix a level's solver launch (0 block, 1 warp, 2 cluster; <0 default),

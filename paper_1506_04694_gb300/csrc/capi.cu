@@ -141,6 +141,13 @@ int check_model(const mlmc_model& md) {
     if (!(md.sigma2[t] >= 0)) return fail(MLMC_ERR_ARG, "sigma2 must be >= 0");
     if (md.k_kind == 1 && !(md.lam[t] > 0)) return fail(MLMC_ERR_ARG, "lam must be > 0");
   }
+  if (md.problem != 0 && md.problem != 1 && md.problem != 2) return fail(MLMC_ERR_ARG, "problem must be 0, 1 or 2");
+  if (md.problem == 1) {
+    const double* b = md.qoi_box;
+    const bool zero = b[0] == 0 && b[1] == 0 && b[2] == 0 && b[3] == 0;
+    if (!zero && !(b[0] >= 0 && b[1] <= 1 && b[0] < b[1] && b[2] >= 0 && b[3] <= 1 && b[2] < b[3]))
+      return fail(MLMC_ERR_ARG, "qoi_box must be x0 < x1, y0 < y1 inside [0, 1]");
+  }
   if (md.k_kind == 1)
     for (int f = 0; 2 * f + 1 < md.n_layers; ++f)
       if (md.sigma2[2 * f] != md.sigma2[2 * f + 1] || md.lam[2 * f] != md.lam[2 * f + 1])
@@ -167,6 +174,10 @@ SolveArgs base_args(const mlmc_ctx* c, int level, uint64_t seed, int64_t first) 
   a.cgv_on_k = md.cgv == 2;
   a.tol = md.tol;
   a.max_it = md.max_it;
+  a.problem = md.problem == 1 ? 1 : 2;
+  const bool zero_box = md.qoi_box[0] == 0 && md.qoi_box[1] == 0 && md.qoi_box[2] == 0 && md.qoi_box[3] == 0;
+  const double dflt[4] = {7.0 / 16, 9.0 / 16, 7.0 / 16, 9.0 / 16};
+  for (int k = 0; k < 4; ++k) a.box[k] = zero_box ? dflt[k] : md.qoi_box[k];
   a.inner_tol = 1e-5;
   return a;
 }
@@ -334,10 +345,26 @@ int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t see
   return 0;
 }
 
+// Algorithmic flops per cell and CG iteration (FMA = 2): operator apply 9,
+// p.q 2, x, r, r.r 6, r.z 2, p update 2; on the finest grid of the cycle a
+// zero-guess red half sweep 0.5, black 4.5, every further sweep pair 9, the
+// red-cell residual restriction 5.25, prolongation 1 and 9 per post-sweep
+// pair; coarser grids add 1/3 (V) or 1 (W) of that.
+double flops_per_cell_iter(int gamma, int nu) {
+  const double fine = 2.25 + 18.0 * nu;
+  return 21.0 + fine * (gamma >= 2 ? 2.0 : 4.0 / 3.0);
+}
+
 // After the stream reached the copies of enqueue_level(): fill the sums.
-int finish_level(mlmc_ctx* c, const HostLevel& h, mlmc_level_sums* sums) {
+int finish_level(mlmc_ctx* c, int level, const HostLevel& h, mlmc_level_sums* sums) {
   const mlmc_model& md = c->model;
-  if (c->prof_on) c->prof.cell_iters += (double)h.itc[1];
+  if (c->prof_on) {
+    c->prof.cell_iters += (double)h.itc[1];
+    SolvePlan P;
+    if (c->tuned_ok[level]) P = c->tuned[level];
+    else if (solve_plan(md.m0 << level, md.prec, &P)) P.gamma = P.nu = 1;
+    c->prof.solve_flops += (double)h.itc[1] * flops_per_cell_iter(P.gamma, P.nu);
+  }
   sums->n = h.s.n;
   sums->n_failed = h.s.n_failed;
   sums->iters_total = h.s.iters;
@@ -357,7 +384,7 @@ int level_batch_impl(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t 
     return e;
   CUDA_TRY(cudaStreamSynchronize(c->st));
   if (c->prof_on) StageTimer::collect(c);
-  return finish_level(c, *h, sums);
+  return finish_level(c, level, *h, sums);
 }
 
 // Allocate, outside any stream capture, every buffer a range of n samples of
@@ -457,7 +484,7 @@ int multilevel_impl(mlmc_ctx* c, int n_levels, const int64_t* first, const int64
   int rc = MLMC_OK;
   for (int l = 0; l < n_levels; ++l) {
     std::memset(&sums[l], 0, sizeof(sums[l]));
-    if (n[l] > 0) rc |= finish_level(c, c->host[l], &sums[l]);
+    if (n[l] > 0) rc |= finish_level(c, l, c->host[l], &sums[l]);
   }
   return rc;
 }

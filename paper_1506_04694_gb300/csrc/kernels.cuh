@@ -70,6 +70,8 @@ struct SolveArgs {
   const double* k;     // KSRC_ARRAY: [system][j][i]
   double tol;
   int max_it;
+  int problem;         // 2: outflow (Model Problem 2); 1: local average, f = 1, Dirichlet 0 (Model Problem 1)
+  double box[4];       // problem 1: x0, x1, y0, y1 of D*
   double inner_tol;    // mixed: relative tolerance of each FP32 inner solve
   int mg_gamma;        // multigrid cycle: 1 V, 2 W (set from the launch plan)
   int mg_nu;           // red-black sweep pairs before and after the coarse correction

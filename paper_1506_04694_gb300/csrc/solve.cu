@@ -635,6 +635,8 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
         if (jp > 0 && jp < m) {
           const T ka = (T)r64[(jp - 1) * m + i], kb = (T)r64[jp * m + i];
           v = T(2) * ka * kb / (ka + kb);
+        } else if (a.problem == 1) {  // Dirichlet p = 0 half a cell away
+          v = T(2) * (T)r64[(jp == 0 ? 0 : m - 1) * m + i];
         }
         L0.ty[u] = v;
       }
@@ -651,9 +653,10 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
   if (!MIXED) {
     // r = b, bb = b.b; stop at r.r <= tol^2 b.b
     T bb = T(0);
+    const T fmid = (T)(1.0 / ((double)m * (double)m));  // Model Problem 1: f / m^2
     for (int c = g.rank(); c < n; c += g.size()) {
       const int j = c / m, i = c - j * m;
-      const T bv = i == 0 ? L0.tx[j * (m + 1)] : T(0);
+      const T bv = a.problem == 1 ? fmid : (i == 0 ? L0.tx[j * (m + 1)] : T(0));
       L0.f[c] = bv;
       bb += bv * bv;
     }
@@ -662,9 +665,10 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
   } else {
     // FP64 refinement: r64 = b - A64 x64 with A64 = the FP32 faces in FP64.
     double bb = 0.0;
+    const double fmid = 1.0 / ((double)m * (double)m);  // Model Problem 1: f / m^2
     for (int c = g.rank(); c < n; c += g.size()) {
       const int j = c / m, i = c - j * m;
-      const double bv = i == 0 ? (double)L0.tx[j * (m + 1)] : 0.0;
+      const double bv = a.problem == 1 ? fmid : (i == 0 ? (double)L0.tx[j * (m + 1)] : 0.0);
       x64[c] = 0.0;
       r64[c] = bv;
       bb += bv * bv;
@@ -710,7 +714,7 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
         if (i < m - 1) ax -= te * x64[c + 1];
         if (j > 0) ax -= ts * x64[c - m];
         if (j < m - 1) ax -= tn * x64[c + m];
-        const double bv = i == 0 ? tw : 0.0;
+        const double bv = a.problem == 1 ? fmid : (i == 0 ? tw : 0.0);
         const double rv = bv - ax;
         r64[c] = rv;
         rr += rv * rv;
@@ -722,9 +726,22 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
       }
     }
   }
-  // ---- outflow QoI and outputs ----
+  // ---- QoI and outputs ----
   double qsum = 0.0;
-  for (int j = g.rank(); j < m; j += g.size()) qsum += (double)L0.tx[j * (m + 1) + m] * x64[j * m + m - 1];
+  if (a.problem == 1) {
+    // M^(1): sum over cells of |cell & D*| / |D*| p (p piecewise constant)
+    const double h = 1.0 / (double)m;
+    const double inv_area = 1.0 / ((a.box[1] - a.box[0]) * (a.box[3] - a.box[2]));
+    for (int c = g.rank(); c < n; c += g.size()) {
+      const int j = c / m, i = c - j * m;
+      const double ox = fmin((i + 1) * h, a.box[1]) - fmax(i * h, a.box[0]);
+      const double oy = fmin((j + 1) * h, a.box[3]) - fmax(j * h, a.box[2]);
+      if (ox > 0.0 && oy > 0.0) qsum += ox * oy * inv_area * x64[c];
+    }
+  } else {
+    // M^(2): outflow through x1 = 1
+    for (int j = g.rank(); j < m; j += g.size()) qsum += (double)L0.tx[j * (m + 1) + m] * x64[j * m + m - 1];
+  }
   qsum = g.sum(qsum, red64, par);
   if (g.rank() == 0) {
     a.q[sys] = status == 0 ? qsum : nan("");

@@ -266,3 +266,28 @@ def test_launch_modes_agree(prec):
         r = darcy.sample(model, 4, level, i)
         assert abs(res[-1][0][i] - r["qf"]) <= tol * abs(r["qf"])
         assert abs(res[-1][1][i] - r["qc_cgv"]) <= tol * abs(r["qc_cgv"])
+
+
+@pytest.mark.parametrize("prec,cgv,level,n", [(0, 0, 0, 30), (0, 0, 2, 6), (0, 1, 1, 10), (1, 1, 2, 6)])
+def test_model_problem_1(prec, cgv, level, n):
+    # Sec. 3.4 Model Problem 1: f = 1, p = 0 on the whole boundary, Q = mean of p
+    # over D* = [7/16, 9/16]^2, plain and CGV coupling, FP64 and mixed
+    d = workloads.workload("lognormal_2layer_cgv_16to512", problem=1, prec=prec, cgv=cgv,
+                           tol=1e-12 if prec == 0 else 1e-10)
+    check_against_oracle(d, level, n, seed=13, first=0, rtol=RTOL64 if prec == 0 else RTOL_MIX)
+
+
+def test_model_problem_1_box_and_solve_k():
+    torch, pk = need_gpu()
+    box = [0.05, 0.32, 0.6, 0.61]
+    d = workloads.workload("const_2layer_8to32", problem=1, qoi_box=box, tol=1e-13)
+    k = workloads.random_k(32, seed=77, n=3, contrast=3.0)
+    with pk.Context(d) as ctx:
+        p, q, _ = ctx.solve_k(torch.from_numpy(k).cuda())
+    p, q = p.cpu().numpy(), q.cpu().numpy()
+    for s in range(3):
+        p_ref, q_ref = darcy.solve_k(k[s], problem=1, box=tuple(box))
+        assert np.max(np.abs(p[s] - p_ref)) < 1e-9 * np.max(p_ref)
+        assert abs(q[s] - q_ref) <= RTOL64 * abs(q_ref)
+    with pytest.raises(pk.MLMCError):
+        pk.Context(dict(d, qoi_box=[0.5, 0.4, 0.1, 0.2]))
