@@ -52,6 +52,9 @@ class Model:
         direct solve of the oracle).
     problem: 2 (or 0) = Model Problem 2, outflow; 1 = Model Problem 1, local
         average of p over the box qoi_box = (x0, x1, y0, y1).
+    geometry: 0 = horizontal interfaces (above); 1 = the three layers of Sec. 3.4
+        cut by the straight lines (0, y1)-(1, y2) and (0, y3)-(1, y4), with
+        y_t ~ U(line_lo[t], line_hi[t]).
     """
     n_layers: int = 2
     k_kind: int = 0
@@ -69,6 +72,9 @@ class Model:
     max_it: int = 200
     problem: int = 2
     qoi_box: List[float] = field(default_factory=lambda: [7 / 16, 9 / 16, 7 / 16, 9 / 16])
+    geometry: int = 0
+    line_lo: List[float] = field(default_factory=lambda: [0.8, 0.6, 0.2, 0.4])
+    line_hi: List[float] = field(default_factory=lambda: [0.9, 0.7, 0.3, 0.5])
 
     @classmethod
     def from_dict(cls, d):
@@ -87,9 +93,17 @@ class Model:
 
 # ---------------------------------------------------------------- layers ----
 def interfaces(model, seed, level, sample):
-    """Sorted interface heights eta_t ~ U(if_lo, if_hi) (Sec. 2, random partition).
+    """Random partition (Sec. 2): sorted interface heights eta_t ~ U(if_lo,
+    if_hi) (geometry 0), or the four line end heights y_1..y_4 ~ U(line_lo[t],
+    line_hi[t]) of the sloped layers of Sec. 3.4 (geometry 1).
 
-    eta = lo + (hi - lo) * u, each operation rounded once (no fused multiply-add)."""
+    Each value is lo + (hi - lo) * u, every operation rounded once (no fused
+    multiply-add)."""
+    if model.geometry == 1:
+        u = philox.interface_uniforms(seed, level, sample, 4)
+        lo = np.asarray(model.line_lo, dtype=np.float64)
+        width = np.asarray(model.line_hi, dtype=np.float64) - lo
+        return lo + width * u
     n_if = model.n_layers - 1
     if n_if == 0:
         return np.zeros(0)
@@ -97,6 +111,42 @@ def interfaces(model, seed, level, sample):
     width = np.float64(model.if_hi) - np.float64(model.if_lo)
     eta = np.float64(model.if_lo) + width * u
     return np.sort(eta)
+
+
+def layer_map(model, ends, m):
+    """Layer index of every cell centre ((i + 1/2)/m, (j + 1/2)/m), as an array
+    [j, i].  Geometry 0: the number of interfaces at or below the row centre.
+    Geometry 1: the number of the two lines (0, y3)-(1, y4) (lower) and
+    (0, y1)-(1, y2) (upper) at or below the centre, the line height at x being
+    y_a + ((y_b - y_a) * x) with each operation rounded once."""
+    if model.geometry != 1:
+        rows = layer_of_rows(ends, m)
+        return np.repeat(rows[:, None], m, axis=1)
+    c = (np.arange(m) + 0.5) / m
+    x, y = c[None, :], c[:, None]
+    lower = ends[2] + (ends[3] - ends[2]) * x
+    upper = ends[0] + (ends[1] - ends[0]) * x
+    return (lower <= y).astype(np.int64) + (upper <= y).astype(np.int64)
+
+
+def field_slots(model):
+    """Which complex circulant-embedding draw feeds which layer: layers are
+    taken in order and paired greedily with an earlier layer of the same
+    (sigma2, lambda) whose draw still has its imaginary part free; returns
+    (slots, params) with slots[t] = (pair f, 0 for Re / 1 for Im) and params[f]
+    = (sigma2, lambda).  Draw f uses Philox stream 2 + f."""
+    slots, params, open_im = [], [], {}
+    for t in range(model.n_layers):
+        key = (model.sigma2[t], model.lam[t])
+        if key in open_im:
+            f = open_im.pop(key)
+            slots.append((f, 1))
+        else:
+            f = len(params)
+            params.append(key)
+            open_im[key] = f
+            slots.append((f, 0))
+    return slots, params
 
 
 def layer_of_rows(eta, m):
@@ -162,29 +212,29 @@ def layer_fields(model, seed, level, sample, m, ce_cache=None):
         for t in range(nl):
             g[t] = model.mu[t] + np.sqrt(model.sigma2[t]) * z[t]
         return g
-    for f in range((nl + 1) // 2):
-        t0, t1 = 2 * f, min(2 * f + 1, nl - 1)
-        if (model.sigma2[t0], model.lam[t0]) != (model.sigma2[t1], model.lam[t1]):
-            raise ValueError("layers of one field pair must share sigma2 and lambda")
-        key = (m, model.sigma2[t0], model.lam[t0], model.norm_r)
+    slots, params = field_slots(model)
+    for f, (sigma2, lam) in enumerate(params):
+        key = (m, sigma2, lam, model.norm_r)
         if ce_cache is not None and key in ce_cache:
             M, lam_q = ce_cache[key]
         else:
-            M, lam_q = ce_padding(m, model.sigma2[t0], model.lam[t0], model.norm_r)
+            M, lam_q = ce_padding(m, sigma2, lam, model.norm_r)
             if ce_cache is not None:
                 ce_cache[key] = (M, lam_q)
         xi = philox.field_normals(seed, level, sample, f, M)
-        re, im = ce_pair(lam_q, xi, m)
-        g[t0] = model.mu[t0] + re
-        if 2 * f + 1 < nl:
-            g[t1] = model.mu[t1] + im
+        parts = ce_pair(lam_q, xi, m)
+        for t in range(nl):
+            if slots[t][0] == f:
+                g[t] = model.mu[t] + parts[slots[t][1]]
     return g
 
 
-def compose_k(g, rows_layer):
-    """k at the cell centres: k[j, i] = exp(g_{layer(j)}[j, i])."""
+def compose_k(g, layers):
+    """k at the cell centres: k[j, i] = exp(g_{layer}[j, i]), with `layers` the
+    layer of each row (array [m]) or of each cell (array [m, m])."""
     m = g.shape[1]
-    return np.exp(g[rows_layer[:, None], np.arange(m)[:, None], np.arange(m)[None, :]])
+    lay = layers[:, None] if layers.ndim == 1 else layers
+    return np.exp(g[lay, np.arange(m)[:, None], np.arange(m)[None, :]])
 
 
 # ----------------------------------------------------------------- TPFA -----
@@ -299,7 +349,7 @@ def coarse_samples(model, g_fine, k_fine, eta, mode):
     mode 2 (CGV on k): the 4 strided sub-vectors of the composed fine k."""
     m = g_fine.shape[1]
     mc = m // 2
-    rows_c = layer_of_rows(eta, mc)
+    rows_c = layer_map(model, eta, mc)
     offsets = CGV_OFFSETS[:1] if mode == 0 else CGV_OFFSETS
     out = []
     for ox, oy in offsets:
@@ -319,7 +369,7 @@ def sample(model, seed, level, i, ce_cache=None, want_fields=False):
     cgv == 0), and diagnostics."""
     m = model.m(level)
     eta = interfaces(model, seed, level, i)
-    rows = layer_of_rows(eta, m)
+    rows = layer_map(model, eta, m)
     g = layer_fields(model, seed, level, i, m, ce_cache)
     k = compose_k(g, rows)
     prob = 1 if model.problem == 1 else 2

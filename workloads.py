@@ -16,6 +16,13 @@ exercise the MLMC level batch (Sec. 2 Ex. 1 / Ex. 2, Sec. 3.4 Model Problem 2):
                             sigma^2 = 3, lambda = 0.1, m = 16 .. 1024
   lognormal_2layer_cgv_32to2048 interface ~U(0.2, 0.8), sigma^2 = 1,
                             lambda = 0.05, m = 32 .. 2048, eps = 2e-4
+  paper_3layer_const_16to128  the three sloped layers of Sec. 3.4 (lines
+                            (0,y1)-(1,y2), (0,y3)-(1,y4), y1~U(.8,.9),
+                            y2~U(.6,.7), y3~U(.2,.3), y4~U(.4,.5)) with
+                            k = exp(z), z ~ N(0, 1) per layer
+  paper_3layer_lognormal_16to128  the same layers with log-normal fields:
+                            outer layers mu = 0, lambda = 0.3, middle layer
+                            mu = 4, lambda = 0.1, sigma^2 = 1, 2-norm
 """
 import numpy as np
 
@@ -40,6 +47,13 @@ WORKLOADS = {
         n_layers=2, k_kind=1, if_lo=0.2, if_hi=0.8, mu=[0.0, 0.0], sigma2=[1.0, 1.0],
         lam=[0.05, 0.05], norm_r=2, m0=32, L=6, cgv=1, prec=1, tol=1e-10, max_it=500,
         eps=2e-4, seed=0),
+    "paper_3layer_const_16to128": dict(
+        n_layers=3, k_kind=0, geometry=1, mu=[0.0] * 3, sigma2=[1.0] * 3, lam=[0.3] * 3, norm_r=2,
+        m0=16, L=3, cgv=0, prec=0, tol=1e-10, max_it=500, eps=2e-3, seed=0),
+    "paper_3layer_lognormal_16to128": dict(
+        n_layers=3, k_kind=1, geometry=1, mu=[0.0, 4.0, 0.0], sigma2=[1.0, 1.0, 1.0],
+        lam=[0.3, 0.1, 0.3], norm_r=2, m0=16, L=3, cgv=0, prec=0, tol=1e-10, max_it=500,
+        eps=2e-2, seed=0),
 }
 
 
