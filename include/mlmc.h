@@ -70,9 +70,10 @@ typedef struct mlmc_model {
                                   sorted ascending; a row whose centre lies at or above
                                   interface t is above it */
   double mu[MLMC_MAX_LAYERS], sigma2[MLMC_MAX_LAYERS], lam[MLMC_MAX_LAYERS];
-                               /* k_kind 1: one embedding table per level serves all layers
-                                  (layers 2f and 2f+1 share one complex draw), so every layer
-                                  must have the same sigma2 and lam */
+                               /* k_kind 1: layers are taken in order and paired greedily
+                                  with an earlier layer of equal (sigma2, lam) whose complex
+                                  draw has its imaginary part free; each draw f (Philox
+                                  stream 2 + f) has its own embedding table per level */
   int32_t norm_r;              /* 1 or 2: the l_r norm of Eq. 2.3 */
   int32_t m0, L;               /* coarsest cells per side (power of two, 2..4096); finest level */
   int32_t cgv;                 /* 0: plain coupling, coarse sample = fine fields at the even
@@ -92,6 +93,14 @@ typedef struct mlmc_model {
                                      boundary, Q = mean of p over the box qoi_box) */
   double qoi_box[4];           /* problem 1: D* = [x0, x1] x [y0, y1] inside (0,1)^2; all zero
                                   selects [7/16, 9/16]^2 around x* = (1/2, 1/2) */
+  int32_t geometry;            /* 0: horizontal interfaces (if_lo, if_hi above);
+                                  1: the three layers of Sec. 3.4 cut by the lines
+                                     (0, y1)-(1, y2) (upper) and (0, y3)-(1, y4) (lower),
+                                     y_t ~ U(line_lo[t], line_hi[t]); needs n_layers = 3; a cell
+                                     belongs to the layer counted by the lines at or below its
+                                     centre */
+  double line_lo[4], line_hi[4];  /* geometry 1; all zero selects the paper's ranges
+                                  (0.8, 0.9), (0.6, 0.7), (0.2, 0.3), (0.4, 0.5) */
 } mlmc_model;
 
 /* Level sums over a range of samples (Eq. 3.6 and Eq. 4.2): Q_f is Q_l of the
@@ -225,8 +234,9 @@ MLMC_API int mlmc_autotune(mlmc_ctx* ctx, uint64_t seed, mlmc_tune_report* rep);
 MLMC_API int mlmc_set_launch(mlmc_ctx* ctx, int level, int32_t mode, int32_t threads, int32_t cluster,
                              int32_t gamma, int32_t nu);
 
-/* Padding of level `level`: *M_out = M, and the smallest / largest raw
- * embedding eigenvalue before clipping (host pointers, any may be NULL). */
+/* Padding of level `level` for the first embedding draw (pair 0): *M_out = M,
+ * and the smallest / largest raw embedding eigenvalue before clipping (host
+ * pointers, any may be NULL). */
 MLMC_API int mlmc_ce_info(mlmc_ctx* ctx, int level, int32_t* M_out, double* lam_min, double* lam_max);
 
 /* Raw Philox4x64-10 words for calls first_call .. first_call+n_calls-1 of one
@@ -249,7 +259,9 @@ MLMC_API int mlmc_normals(mlmc_ctx* ctx, uint64_t seed, uint64_t level, uint64_t
 /* Stage output for parity checks: the per-layer fields g_t of the fine grid of
  * samples first .. first+n-1 of `level` (Ex. 1 constants or Ex. 2 fields),
  * g: device pointer to n * n_layers * m * m doubles ([sample][t][j][i]);
- * eta: device pointer to n * (n_layers - 1) doubles (sorted interfaces) or NULL. */
+ * eta: device pointer to n * n_ends doubles or NULL: the sorted interfaces
+ *   (geometry 0, n_ends = n_layers - 1) or the line ends y1..y4 (geometry 1,
+ *   n_ends = 4). */
 MLMC_API int mlmc_sample_fields(mlmc_ctx* ctx, int level, int64_t first, int64_t n, uint64_t seed,
                        double* g, double* eta);
 

@@ -31,6 +31,7 @@ class Model(ctypes.Structure):
         ("cgv", ctypes.c_int32), ("prec", ctypes.c_int32),
         ("tol", ctypes.c_double), ("max_it", ctypes.c_int32),
         ("problem", ctypes.c_int32), ("qoi_box", ctypes.c_double * 4),
+        ("geometry", ctypes.c_int32), ("line_lo", ctypes.c_double * 4), ("line_hi", ctypes.c_double * 4),
     ]
 
 
@@ -153,7 +154,7 @@ def make_model(d):
         if name in ("mu", "sigma2", "lam"):
             arr = list(v) + [v[-1]] * (MAX_LAYERS - len(v))
             setattr(m, name, (ctypes.c_double * MAX_LAYERS)(*arr[:MAX_LAYERS]))
-        elif name == "qoi_box":
+        elif name in ("qoi_box", "line_lo", "line_hi"):
             setattr(m, name, (ctypes.c_double * 4)(*v))
         else:
             setattr(m, name, v)
@@ -327,10 +328,11 @@ class Context:
         m = self.m(level)
         nl = self.model.n_layers
         g = torch.empty((n, nl, m, m), dtype=torch.float64, device="cuda:%d" % self.device)
-        eta = torch.empty((n, max(nl - 1, 1)), dtype=torch.float64, device=g.device)
+        n_ends = 4 if self.model.geometry == 1 else nl - 1
+        eta = torch.empty((n, max(n_ends, 1)), dtype=torch.float64, device=g.device)
         _check(lib().mlmc_sample_fields(self._h, level, first, n, seed, _ptr(g), _ptr(eta)),
                allow_failed=False)
-        return g, eta[:, :nl - 1]
+        return g, eta[:, :n_ends]
 
     def solve_k(self, k, want_p=True):
         """mlmc_solve_k: solve the systems of a CUDA float64 tensor k [n, m, m];

@@ -66,10 +66,16 @@ struct Buf {
   }
 };
 
-struct LevelTable {
-  int m = 0, M = 0;
+// Embedding table of one complex draw (pair) on one level.
+struct PairTable {
+  int M = 0;
   double lam_min = 0, lam_max = 0;
   Buf s64, s32, tw64, tw32;
+};
+
+struct LevelTable {
+  int m = 0;
+  std::vector<PairTable> pair;  // one per embedding draw
 };
 
 constexpr size_t kChunkBudget = size_t(2) << 30;  // bytes of per-sample buffers per chunk
@@ -94,6 +100,11 @@ struct mlmc_ctx {
   mlmc_model model{};
   int nsm = 0;
   std::vector<LevelTable> lev;
+  // layers onto embedding draws: layer t is part part_of[t] (0 Re, 1 Im) of
+  // draw pair_of[t]; draw f has covariance (pair_sigma2[f], pair_lam[f])
+  int n_draws = 0;
+  int pair_of[MLMC_MAX_LAYERS], part_of[MLMC_MAX_LAYERS];
+  double pair_sigma2[MLMC_MAX_LAYERS], pair_lam[MLMC_MAX_LAYERS];
   Buf W, g, ws, qsys, itsys, oqf, oqc, oqg, oit, sums, itacc, g64, bm;
   bool prof_on = false;
   mlmc_profile_stats prof{};
@@ -122,7 +133,46 @@ struct mlmc_ctx {
 
 namespace {
 
-int n_pairs(const mlmc_model& md) { return (md.n_layers + 1) / 2; }
+// Greedy pairing (same rule as the model documentation): layers in order,
+// each joins an earlier draw of equal (sigma2, lam) whose Im part is free.
+void pair_layers(mlmc_ctx* c) {
+  const mlmc_model& md = c->model;
+  int open_im[MLMC_MAX_LAYERS];
+  int n_open = 0;
+  c->n_draws = 0;
+  for (int t = 0; t < md.n_layers; ++t) {
+    int hit = -1;
+    for (int k = 0; k < n_open; ++k) {
+      const int f = open_im[k];
+      if (c->pair_sigma2[f] == md.sigma2[t] && c->pair_lam[f] == md.lam[t]) {
+        hit = k;
+        break;
+      }
+    }
+    if (hit >= 0) {
+      c->pair_of[t] = open_im[hit];
+      c->part_of[t] = 1;
+      open_im[hit] = open_im[--n_open];
+      // keep the remaining open draws in creation order
+      for (int a = 0; a + 1 < n_open; ++a)
+        for (int b = a + 1; b < n_open; ++b)
+          if (open_im[b] < open_im[a]) std::swap(open_im[a], open_im[b]);
+    } else {
+      const int f = c->n_draws++;
+      c->pair_sigma2[f] = md.sigma2[t];
+      c->pair_lam[f] = md.lam[t];
+      c->pair_of[t] = f;
+      c->part_of[t] = 0;
+      open_im[n_open++] = f;
+    }
+  }
+}
+
+int max_M(const mlmc_ctx* c, int level) {
+  int M = 0;
+  for (const auto& T : c->lev[level].pair) M = std::max(M, T.M);
+  return M;
+}
 int n_coarse(const mlmc_model& md, int level) { return level == 0 ? 0 : (md.cgv ? 4 : 1); }
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
@@ -148,10 +198,15 @@ int check_model(const mlmc_model& md) {
     if (!zero && !(b[0] >= 0 && b[1] <= 1 && b[0] < b[1] && b[2] >= 0 && b[3] <= 1 && b[2] < b[3]))
       return fail(MLMC_ERR_ARG, "qoi_box must be x0 < x1, y0 < y1 inside [0, 1]");
   }
-  if (md.k_kind == 1)
-    for (int f = 0; 2 * f + 1 < md.n_layers; ++f)
-      if (md.sigma2[2 * f] != md.sigma2[2 * f + 1] || md.lam[2 * f] != md.lam[2 * f + 1])
-        return fail(MLMC_ERR_ARG, "layers 2f and 2f+1 must share sigma2 and lam");
+  if (md.geometry != 0 && md.geometry != 1) return fail(MLMC_ERR_ARG, "geometry must be 0 or 1");
+  if (md.geometry == 1) {
+    if (md.n_layers != 3) return fail(MLMC_ERR_ARG, "geometry 1 has three layers");
+    bool zero = true;
+    for (int t = 0; t < 4; ++t) zero = zero && md.line_lo[t] == 0 && md.line_hi[t] == 0;
+    for (int t = 0; t < 4 && !zero; ++t)
+      if (!(md.line_lo[t] <= md.line_hi[t] && md.line_lo[t] >= 0 && md.line_hi[t] <= 1))
+        return fail(MLMC_ERR_ARG, "line_lo[t] <= line_hi[t] inside [0, 1]");
+  }
   return 0;
 }
 
@@ -164,8 +219,18 @@ SolveArgs base_args(const mlmc_ctx* c, int level, uint64_t seed, int64_t first) 
   a.seed = seed;
   a.first = first;
   a.n_layers = md.n_layers;
+  a.geometry = md.geometry;
   a.if_lo = md.if_lo;
   a.if_hi = md.if_hi;
+  {
+    bool zero = true;
+    for (int t = 0; t < 4; ++t) zero = zero && md.line_lo[t] == 0 && md.line_hi[t] == 0;
+    const double lo[4] = {0.8, 0.6, 0.2, 0.4}, hi[4] = {0.9, 0.7, 0.3, 0.5};
+    for (int t = 0; t < 4; ++t) {
+      a.line_lo[t] = zero ? lo[t] : md.line_lo[t];
+      a.line_hi[t] = zero ? hi[t] : md.line_hi[t];
+    }
+  }
   for (int t = 0; t < MAX_LAYERS_DEV; ++t) {
     a.mu[t] = md.mu[t];
     a.sigma[t] = std::sqrt(md.sigma2[t]);
@@ -185,28 +250,35 @@ SolveArgs base_args(const mlmc_ctx* c, int level, uint64_t seed, int64_t first) 
 // Fields of chunk samples [first, first + n) of `level` into c->g.
 int run_fields(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t seed) {
   const mlmc_model& md = c->model;
-  const LevelTable& T = c->lev[level];
+  const LevelTable& LT = c->lev[level];
   const bool f32 = md.prec != 0;
-  CeLaunch L;
-  L.bm_sc = c->bm.as<double2>();
-  L.bm_lg = reinterpret_cast<const double*>(c->bm.as<double2>() + kSinCosTab);
-  L.M = T.M;
-  L.m = T.m;
-  L.n_pairs = n_pairs(md);
-  L.n_layers = md.n_layers;
-  L.level = level;
-  L.seed = seed;
-  L.first = first;
-  L.n_samples = n;
-  for (int t = 0; t < MAX_LAYERS_DEV; ++t) L.mu[t] = md.mu[t];
-  int r;
-  if (int e = c->W.ensure(ce_w_bytes_per_sample(T.m, T.M, L.n_pairs, f32) * n)) return e;
-  if (int e = c->g.ensure((size_t)n * md.n_layers * T.m * T.m * (f32 ? 4 : 8))) return e;
-  if (f32)
-    r = ce_sample_fp32(L, T.s32.as<float>(), T.tw32.p, c->W.p, c->g.as<float>(), c->st);
-  else
-    r = ce_sample_fp64(L, T.s64.as<double>(), T.tw64.p, c->W.p, c->g.as<double>(), c->st);
-  if (r) return fail(MLMC_ERR_CUDA, std::string("field kernels: ") + cudaGetErrorString(cudaGetLastError()));
+  if (int e = c->W.ensure(ce_w_bytes_per_sample(LT.m, max_M(c, level), f32) * n)) return e;
+  if (int e = c->g.ensure((size_t)n * md.n_layers * LT.m * LT.m * (f32 ? 4 : 8))) return e;
+  for (int f = 0; f < c->n_draws; ++f) {  // one draw at a time, W reused
+    const PairTable& T = LT.pair[f];
+    CeLaunch L;
+    L.bm_sc = c->bm.as<double2>();
+    L.bm_lg = reinterpret_cast<const double*>(c->bm.as<double2>() + kSinCosTab);
+    L.M = T.M;
+    L.m = LT.m;
+    L.pair = f;
+    L.n_layers = md.n_layers;
+    L.level = level;
+    L.seed = seed;
+    L.first = first;
+    L.n_samples = n;
+    L.t_re = L.t_im = -1;
+    for (int t = 0; t < md.n_layers; ++t)
+      if (c->pair_of[t] == f) (c->part_of[t] == 0 ? L.t_re : L.t_im) = t;
+    L.mu_re = md.mu[L.t_re];
+    L.mu_im = L.t_im >= 0 ? md.mu[L.t_im] : 0.0;
+    int r;
+    if (f32)
+      r = ce_sample_fp32(L, T.s32.as<float>(), T.tw32.p, c->W.p, c->g.as<float>(), c->st);
+    else
+      r = ce_sample_fp64(L, T.s64.as<double>(), T.tw64.p, c->W.p, c->g.as<double>(), c->st);
+    if (r) return fail(MLMC_ERR_CUDA, std::string("field kernels: ") + cudaGetErrorString(cudaGetLastError()));
+  }
   return 0;
 }
 
@@ -216,7 +288,7 @@ int64_t chunk_samples(const mlmc_ctx* c, int level) {
   const bool f32 = md.prec != 0;
   size_t per = (size_t)(1 + n_coarse(md, level)) * 12;
   if (md.k_kind == 1) {
-    per += ce_w_bytes_per_sample(m, c->lev[level].M, n_pairs(md), f32);
+    per += ce_w_bytes_per_sample(m, max_M(c, level), f32);
     per += (size_t)md.n_layers * m * m * (f32 ? 4 : 8);
   }
   int64_t s = (int64_t)(kChunkBudget / per);
@@ -304,18 +376,22 @@ int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t see
   const SolvePlan* plan = c->tuned_ok[level] ? &c->tuned[level] : nullptr;
   CUDA_TRY(cudaMemsetAsync(itacc, 0, 2 * sizeof(int64_t), c->st));
   const int m = md.m0 << level;
-  const int M = c->lev[level].M;
+  double sumM2 = 0, sumM = 0;  // transformed points per sample over the draws
+  for (const auto& T : c->lev[level].pair) {
+    sumM2 += (double)T.M * T.M;
+    sumM += (double)T.M;
+  }
   for (int64_t c0 = 0; c0 < n; c0 += chunk) {
     const int64_t cn = std::min<int64_t>(chunk, n - c0);
     SolveArgs a = base_args(c, level, seed, first + c0);
     if (md.k_kind == 1) {
       StageTimer t(c, 0);
       if (int e = run_fields(c, level, first + c0, cn, seed)) return e;
-      t.stop(2 * (int)((cn + 65534) / 65535));
+      t.stop(2 * c->n_draws * (int)((cn + 65534) / 65535));
       a.g = c->g.p;
       if (c->prof_on) {
-        c->prof.fft_row_points += (double)cn * n_pairs(md) * M * M;
-        c->prof.fft_col_points += (double)cn * n_pairs(md) * M * m;
+        c->prof.fft_row_points += (double)cn * sumM2;
+        c->prof.fft_col_points += (double)cn * sumM * m;
       }
     }
     {
@@ -396,7 +472,7 @@ int prepare_level(mlmc_ctx* c, int level, int64_t n) {
   const int nc = n_coarse(md, level);
   const int64_t cn = std::min<int64_t>(n, chunk_samples(c, level));
   if (md.k_kind == 1) {
-    if (int e = c->W.ensure(ce_w_bytes_per_sample(m, c->lev[level].M, n_pairs(md), f32) * cn)) return e;
+    if (int e = c->W.ensure(ce_w_bytes_per_sample(m, max_M(c, level), f32) * cn)) return e;
     if (int e = c->g.ensure((size_t)cn * md.n_layers * m * m * (f32 ? 4 : 8))) return e;
   }
   SolvePlan P;
@@ -553,48 +629,48 @@ int mlmc_create(int device, const mlmc_model* model, void* cuda_stream, mlmc_ctx
       bm_tables_build(c->bm.as<double2>(), reinterpret_cast<double*>(c->bm.as<double2>() + kSinCosTab),
                       c->st))
     err = fail(MLMC_ERR_CUDA, "Box-Muller table kernel");
+  pair_layers(c);
   for (int l = 0; l <= model->L && !err; ++l) {
-    LevelTable& T = c->lev[l];
-    T.m = model->m0 << l;
-    T.M = 0;
+    LevelTable& LT = c->lev[l];
+    LT.m = model->m0 << l;
     if (model->k_kind != 1) continue;
+    LT.pair.resize(c->n_draws);
     if ((err = mm.ensure(2 * sizeof(double)))) break;
-    for (int p = 2; p <= 16; p *= 2) {
-      const int M = p * T.m;
-      if (M > 16384) {
-        err = fail(MLMC_ERR_TOOBIG, "embedding size M above 16384");
-        break;
+    for (int f = 0; f < c->n_draws && !err; ++f) {
+      PairTable& T = LT.pair[f];
+      T.M = 0;
+      for (int p = 2; p <= 16; p *= 2) {
+        const int M = p * LT.m;
+        if (M > 16384) {
+          err = fail(MLMC_ERR_TOOBIG, "embedding size M above 16384");
+          break;
+        }
+        if ((err = scratch.ensure((size_t)2 * M * M * 16))) break;
+        if ((err = T.s64.ensure((size_t)M * M * 8)) || (err = T.s32.ensure((size_t)M * M * 4)) ||
+            (err = T.tw64.ensure((size_t)M * 8)) || (err = T.tw32.ensure((size_t)M * 4)))
+          break;
+        if (ce_build_table(LT.m, M, c->pair_sigma2[f], c->pair_lam[f], model->norm_r, scratch.p,
+                           T.s64.as<double>(), T.s32.as<float>(), mm.as<double>(), T.tw64.p, T.tw32.p,
+                           c->st)) {
+          err = fail(MLMC_ERR_CUDA, "embedding set-up kernels");
+          break;
+        }
+        double h[2];
+        if (cudaMemcpyAsync(h, mm.p, sizeof(h), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+            cudaStreamSynchronize(c->st) != cudaSuccess) {
+          err = fail(MLMC_ERR_CUDA, "embedding set-up copy");
+          break;
+        }
+        T.lam_min = h[0];
+        T.lam_max = h[1];
+        if (h[0] >= -1e-13 * h[1]) {
+          T.M = M;
+          break;
+        }
       }
-      if ((err = scratch.ensure((size_t)2 * M * M * 16))) break;
-      if ((err = T.s64.ensure((size_t)M * M * 8)) || (err = T.s32.ensure((size_t)M * M * 4)) ||
-          (err = T.tw64.ensure((size_t)M * 8)) || (err = T.tw32.ensure((size_t)M * 4)))
-        break;
-      if (ce_build_table(T.m, M, model->sigma2[0], model->lam[0], model->norm_r, scratch.p,
-                         T.s64.as<double>(), T.s32.as<float>(), mm.as<double>(), T.tw64.p, T.tw32.p,
-                         c->st)) {
-        err = fail(MLMC_ERR_CUDA, "embedding set-up kernels");
-        break;
-      }
-      double h[2];
-      if (cudaMemcpyAsync(h, mm.p, sizeof(h), cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
-          cudaStreamSynchronize(c->st) != cudaSuccess) {
-        err = fail(MLMC_ERR_CUDA, "embedding set-up copy");
-        break;
-      }
-      T.lam_min = h[0];
-      T.lam_max = h[1];
-      if (h[0] >= -1e-13 * h[1]) {
-        T.M = M;
-        break;
-      }
+      if (!err && T.M == 0) err = fail(MLMC_ERR_EMBED, "embedding negative at padding 16");
     }
-    if (!err && T.M == 0) err = fail(MLMC_ERR_EMBED, "embedding negative at padding 16");
   }
-  // layer pairs other than the first must have the same covariance as pair 0
-  if (!err && model->k_kind == 1)
-    for (int t = 1; t < model->n_layers; ++t)
-      if (model->sigma2[t] != model->sigma2[0] || model->lam[t] != model->lam[0])
-        err = fail(MLMC_ERR_ARG, "all layers must share sigma2 and lam (one embedding table per level)");
   scratch.release();
   mm.release();
   if (err) {
@@ -609,12 +685,13 @@ void mlmc_destroy(mlmc_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->st);
-  for (auto& T : c->lev) {
-    T.s64.release();
-    T.s32.release();
-    T.tw64.release();
-    T.tw32.release();
-  }
+  for (auto& LT : c->lev)
+    for (auto& T : LT.pair) {
+      T.s64.release();
+      T.s32.release();
+      T.tw64.release();
+      T.tw32.release();
+    }
   for (Buf* b : {&c->W, &c->g, &c->ws, &c->qsys, &c->itsys, &c->oqf, &c->oqc, &c->oqg, &c->oit,
                  &c->sums, &c->itacc, &c->g64, &c->bm})
     b->release();
@@ -966,9 +1043,10 @@ int mlmc_set_launch(mlmc_ctx* c, int level, int32_t mode, int32_t threads, int32
 
 int mlmc_ce_info(mlmc_ctx* c, int level, int32_t* M_out, double* lam_min, double* lam_max) {
   if (!c || level < 0 || level > c->model.L) return fail(MLMC_ERR_ARG, "bad context or level");
-  if (M_out) *M_out = c->lev[level].M;
-  if (lam_min) *lam_min = c->lev[level].lam_min;
-  if (lam_max) *lam_max = c->lev[level].lam_max;
+  const bool any = !c->lev[level].pair.empty();
+  if (M_out) *M_out = any ? c->lev[level].pair[0].M : 0;
+  if (lam_min) *lam_min = any ? c->lev[level].pair[0].lam_min : 0.0;
+  if (lam_max) *lam_max = any ? c->lev[level].pair[0].lam_max : 0.0;
   return 0;
 }
 

@@ -167,16 +167,16 @@ __global__ void scale_kernel(const Cplx<double>* lam, double* s64, float* s32, i
 }
 
 // ------------------------------------------------------------ pass 1 -------
-// Block (row block rb, pair f, sample s): rows q2 in [rb*R, rb*R + R) of the
-// M x M draw of field pair f, FFT along q1, keep a < m.
-// W layout: [sample][pair][q2][a] complex.
+// Block (row block rb, sample s): rows q2 in [rb*R, rb*R + R) of the M x M
+// draw of field pair args.pair, FFT along q1, keep a < m.
+// W layout: [sample][q2][a] complex (one draw at a time).
 template <typename R>
 __global__ void ce_rows_kernel(CeRowsArgs args, const R* __restrict__ scale,
                                const Cplx<R>* __restrict__ tw, Cplx<R>* __restrict__ W) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cplx<R>* s = reinterpret_cast<Cplx<R>*>(smem_raw);
   const int M = args.M, logM = args.logM, m = args.m, rows = args.rows_per_block;
-  const int rb = blockIdx.x, f = blockIdx.y;
+  const int rb = blockIdx.x, f = args.pair;
   const int64_t sidx = blockIdx.z + args.z_offset;
   const uint64_t sample = (uint64_t)(args.first + sidx);
   const int q2_0 = rb * rows;
@@ -198,7 +198,7 @@ __global__ void ce_rows_kernel(CeRowsArgs args, const R* __restrict__ scale,
   }
   __syncthreads();
   block_fft_rows(s, rows, M, logM, tw, m >= 4 ? m : M);
-  Cplx<R>* out = W + ((sidx * args.n_pairs + f) * (int64_t)M + q2_0) * m;
+  Cplx<R>* out = W + (sidx * (int64_t)M + q2_0) * m;
   for (int t = threadIdx.x; t < rows * m; t += blockDim.x) {
     const int r = t / m, a = t - r * m;
     out[(int64_t)r * m + a] = s[r * M + a];
@@ -206,34 +206,33 @@ __global__ void ce_rows_kernel(CeRowsArgs args, const R* __restrict__ scale,
 }
 
 // ------------------------------------------------------------ pass 2 -------
-// Block (column block cb, pair f, sample s): columns a in [cb*C, cb*C + C),
-// FFT along q2, keep b < m; g layout [sample][layer][b][a].
+// Block (column block cb, sample s): columns a in [cb*C, cb*C + C), FFT
+// along q2, keep b < m; g layout [sample][layer][b][a]; Re goes to layer
+// t_re, Im to layer t_im (if any).
 template <typename R, typename G>
 __global__ void ce_cols_kernel(CeColsArgs args, const Cplx<R>* __restrict__ tw,
                                const Cplx<R>* __restrict__ W, G* __restrict__ g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cplx<R>* s = reinterpret_cast<Cplx<R>*>(smem_raw);
   const int M = args.M, logM = args.logM, m = args.m, C = args.cols_per_block;
-  const int cb = blockIdx.x, f = blockIdx.y;
+  const int cb = blockIdx.x;
   const int64_t sidx = blockIdx.z + args.z_offset;
   const int a0 = cb * C;
-  const Cplx<R>* in = W + ((sidx * args.n_pairs + f) * (int64_t)M) * m + a0;
+  const Cplx<R>* in = W + (sidx * (int64_t)M) * m + a0;
   for (int t = threadIdx.x; t < M * C; t += blockDim.x) {
     const int q2 = t / C, cc = t - q2 * C;
     s[cc * M + brev_n(q2, logM)] = in[(int64_t)q2 * m + cc];
   }
   __syncthreads();
   block_fft_rows(s, C, M, logM, tw, m >= 4 ? m : M);
-  const int t0 = 2 * f, t1 = 2 * f + 1;
-  const double mu0 = args.mu[t0];
-  const double mu1 = t1 < args.n_layers ? args.mu[t1] : 0.0;
-  G* g0 = g + ((sidx * args.n_layers + t0) * (int64_t)m) * m;
-  G* g1 = g + ((sidx * args.n_layers + t1) * (int64_t)m) * m;
+  const bool has_im = args.t_im >= 0;
+  G* g0 = g + ((sidx * args.n_layers + args.t_re) * (int64_t)m) * m;
+  G* g1 = g + ((sidx * args.n_layers + (has_im ? args.t_im : args.t_re)) * (int64_t)m) * m;
   for (int t = threadIdx.x; t < m * C; t += blockDim.x) {
     const int b = t / C, cc = t - b * C;
     const Cplx<R> v = s[cc * M + b];
-    g0[(int64_t)b * m + a0 + cc] = (G)(mu0 + (double)v.x);
-    if (t1 < args.n_layers) g1[(int64_t)b * m + a0 + cc] = (G)(mu1 + (double)v.y);
+    g0[(int64_t)b * m + a0 + cc] = (G)(args.mu_re + (double)v.x);
+    if (has_im) g1[(int64_t)b * m + a0 + cc] = (G)(args.mu_im + (double)v.y);
   }
 }
 
@@ -276,12 +275,11 @@ static int ce_sample_impl(const CeLaunch& L, const R* scale, const void* tw, voi
   CeRowsArgs ra;
   ra.bm_sc = L.bm_sc;
   ra.bm_lg = L.bm_lg;
-  ra.M = L.M; ra.logM = ilog2(L.M); ra.m = L.m; ra.rows_per_block = rows; ra.n_pairs = L.n_pairs;
+  ra.M = L.M; ra.logM = ilog2(L.M); ra.m = L.m; ra.rows_per_block = rows; ra.pair = L.pair;
   ra.level = L.level; ra.seed = L.seed; ra.first = L.first;
   CeColsArgs ca;
-  ca.M = L.M; ca.logM = ra.logM; ca.m = L.m; ca.cols_per_block = cols; ca.n_pairs = L.n_pairs;
-  ca.n_layers = L.n_layers;
-  for (int t = 0; t < MAX_LAYERS_DEV; ++t) ca.mu[t] = L.mu[t];
+  ca.M = L.M; ca.logM = ra.logM; ca.m = L.m; ca.cols_per_block = cols; ca.n_layers = L.n_layers;
+  ca.t_re = L.t_re; ca.t_im = L.t_im; ca.mu_re = L.mu_re; ca.mu_im = L.mu_im;
   const size_t sm_r = (size_t)rows * L.M * esz;
   const size_t sm_c = (size_t)cols * L.M * esz;
   cudaFuncSetAttribute(ce_rows_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_r);
@@ -291,9 +289,9 @@ static int ce_sample_impl(const CeLaunch& L, const R* scale, const void* tw, voi
     const unsigned nz = (unsigned)((L.n_samples - z0) < 65535 ? (L.n_samples - z0) : 65535);
     ra.z_offset = z0;
     ca.z_offset = z0;
-    dim3 gr((unsigned)(L.M / rows), (unsigned)L.n_pairs, nz);
+    dim3 gr((unsigned)(L.M / rows), 1u, nz);
     ce_rows_kernel<R><<<gr, 256, sm_r, st>>>(ra, scale, (const Cplx<R>*)tw, (Cplx<R>*)W);
-    dim3 gc((unsigned)(L.m / cols), (unsigned)L.n_pairs, nz);
+    dim3 gc((unsigned)(L.m / cols), 1u, nz);
     ce_cols_kernel<R, G><<<gc, 256, sm_c, st>>>(ca, (const Cplx<R>*)tw, (const Cplx<R>*)W, g);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
@@ -329,8 +327,8 @@ int bm_tables_build(double2* sc, double* lg, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-size_t ce_w_bytes_per_sample(int m, int M, int n_pairs, bool fp32) {
-  return (size_t)n_pairs * M * m * (fp32 ? sizeof(Cplx<float>) : sizeof(Cplx<double>));
+size_t ce_w_bytes_per_sample(int m, int M, bool fp32) {
+  return (size_t)M * m * (fp32 ? sizeof(Cplx<float>) : sizeof(Cplx<double>));
 }
 
 }  // namespace mlmc

@@ -12,25 +12,28 @@ constexpr int MAX_LAYERS_DEV = 8;
 struct CeRowsArgs {
   const double2* bm_sc;  // Box-Muller tables (common.cuh, BmTables)
   const double* bm_lg;
-  int M, logM, m, rows_per_block, n_pairs, level;
+  int M, logM, m, rows_per_block, pair, level;
   uint64_t seed;
   int64_t first;     // sample index of chunk entry 0
   int64_t z_offset;  // chunk entry of blockIdx.z == 0
 };
 
 struct CeColsArgs {
-  int M, logM, m, cols_per_block, n_pairs, n_layers;
+  int M, logM, m, cols_per_block, n_layers;
+  int t_re, t_im;  // layers fed by Re and Im of this draw (t_im < 0: none)
+  double mu_re, mu_im;
   int64_t z_offset;
-  double mu[MAX_LAYERS_DEV];
 };
 
+// One complex embedding draw (pair) for a chunk of samples.
 struct CeLaunch {
   const double2* bm_sc;
   const double* bm_lg;
-  int M, m, n_pairs, n_layers, level;
+  int M, m, pair, n_layers, level;
+  int t_re, t_im;
+  double mu_re, mu_im;
   uint64_t seed;
   int64_t first, n_samples;
-  double mu[MAX_LAYERS_DEV];
 };
 
 int ce_build_table(int m, int M, double sigma2, double lam, int norm_r, void* scratch,
@@ -40,7 +43,7 @@ int ce_sample_fp64(const CeLaunch& L, const double* scale, const void* tw, void*
                    cudaStream_t st);
 int ce_sample_fp32(const CeLaunch& L, const float* scale, const void* tw, void* W, float* g,
                    cudaStream_t st);
-size_t ce_w_bytes_per_sample(int m, int M, int n_pairs, bool fp32);
+size_t ce_w_bytes_per_sample(int m, int M, bool fp32);
 // Box-Muller tables: sc 1024 double2, lg 3*128 doubles.
 int bm_tables_build(double2* sc, double* lg, cudaStream_t st);
 
@@ -63,7 +66,9 @@ struct SolveArgs {
   uint64_t seed;
   int64_t first;       // sample index of chunk entry 0
   int n_layers;
+  int geometry;        // 0 horizontal interfaces; 1 sloped lines (four ends)
   double if_lo, if_hi;
+  double line_lo[4], line_hi[4];
   double mu[MAX_LAYERS_DEV];
   double sigma[MAX_LAYERS_DEV];
   const void* g;       // fields [sample][layer][j][i] (double or float by precision)

@@ -457,10 +457,27 @@ __device__ __forceinline__ int layer_at(const double* eta, int n_if, double y) {
   return t;
 }
 
-// Interfaces of one sample (sorted) and, for Ex. 1, the layer constants.
+// Layer of the point (x, y): geometry 0 counts the interfaces at or below y;
+// geometry 1 counts the lines (0, e2)-(1, e3) and (0, e0)-(1, e1) at or below
+// it, the line height e_a + ((e_b - e_a) x) rounded once per operation.
+__device__ __forceinline__ int layer_at_point(int geometry, const double* eta, int n_if, double x, double y) {
+  if (geometry != 1) return layer_at(eta, n_if, y);
+  const double lower = __dadd_rn(eta[2], __dmul_rn(__dadd_rn(eta[3], -eta[2]), x));
+  const double upper = __dadd_rn(eta[0], __dmul_rn(__dadd_rn(eta[1], -eta[0]), x));
+  return (lower <= y ? 1 : 0) + (upper <= y ? 1 : 0);
+}
+
+// Interfaces of one sample (sorted; geometry 1: the four line ends, in order)
+// and, for Ex. 1, the layer constants.
 __device__ void sample_layers(const SolveArgs& a, uint64_t sample, double* eta, double* kc) {
-  const int n_if = a.n_layers - 1;
+  const int n_if = a.geometry == 1 ? 0 : a.n_layers - 1;
   const double width = __dadd_rn(a.if_hi, -a.if_lo);
+  if (a.geometry == 1) {
+    const Words4 w = philox4x64_10(0, sample, (uint64_t)a.level, kStreamInterface, a.seed);
+    const uint64_t ws[4] = {w.w0, w.w1, w.w2, w.w3};
+    for (int t = 0; t < 4; ++t)
+      eta[t] = __dadd_rn(a.line_lo[t], __dmul_rn(__dadd_rn(a.line_hi[t], -a.line_lo[t]), uniform52(ws[t])));
+  }
   for (int t = 0; t < n_if; ++t) {
     const Words4 w = philox4x64_10((uint64_t)(t >> 2), sample, (uint64_t)a.level, kStreamInterface,
                                    a.seed);
@@ -588,19 +605,20 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
     if (g.local_leader()) sample_layers(a, sample, gs.eta, gs.kc);
     g.sync();
   }
-  const int n_if = a.n_layers - 1;
+  const int n_if = a.geometry == 1 ? 0 : a.n_layers - 1;
   for (int c = g.rank(); c < n; c += g.size()) {
     const int j = c / m, i = c - j * m;
     double kk;
     if (a.ksrc == KSRC_ARRAY) {
       kk = a.k[sys * (int64_t)n + c];
     } else {
-      // fine row of the value, and the row whose centre decides the layer
+      // fine cell of the value, and the centre that decides the layer
       const int jf = coarse ? 2 * j + oy : j;
       const int iff = coarse ? 2 * i + ox : i;
-      const double yc = (coarse && !a.cgv_on_k) ? ((double)j + 0.5) / (double)m
-                                                : ((double)jf + 0.5) / (double)a.m;
-      const int t = layer_at(gs.eta, n_if, yc);
+      const bool own = coarse && !a.cgv_on_k;  // layer at the coarse centre
+      const double yc = own ? ((double)j + 0.5) / (double)m : ((double)jf + 0.5) / (double)a.m;
+      const double xc = own ? ((double)i + 0.5) / (double)m : ((double)iff + 0.5) / (double)a.m;
+      const int t = layer_at_point(a.geometry, gs.eta, n_if, xc, yc);
       if (a.ksrc == KSRC_CONST) {
         kk = gs.kc[t];
       } else if (MIXED) {
@@ -958,11 +976,12 @@ __global__ void interfaces_kernel(SolveArgs a, int64_t n, double* eta) {
   SolveArgs b = a;
   b.ksrc = KSRC_FIELDS;  // interfaces only
   sample_layers(b, (uint64_t)(a.first + s), e, kc);
-  for (int t = 0; t < a.n_layers - 1; ++t) eta[s * (a.n_layers - 1) + t] = e[t];
+  const int ne = a.geometry == 1 ? 4 : a.n_layers - 1;
+  for (int t = 0; t < ne; ++t) eta[s * ne + t] = e[t];
 }
 
 int interfaces_launch(const SolveArgs& a, int64_t n, double* eta, cudaStream_t st) {
-  if (n <= 0 || a.n_layers < 2) return 0;
+  if (n <= 0 || (a.geometry != 1 && a.n_layers < 2)) return 0;
   interfaces_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a, n, eta);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

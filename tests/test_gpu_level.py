@@ -145,7 +145,9 @@ def test_bad_arguments_rejected():
     with pytest.raises(pk.MLMCError):
         pk.Context(workloads.workload("const_2layer_8to32", m0=12))
     with pytest.raises(pk.MLMCError):
-        pk.Context(workloads.workload("lognormal_2layer_16to256", sigma2=[1.0, 2.0]))
+        pk.Context(workloads.workload("paper_3layer_const_16to128", n_layers=2))
+    with pytest.raises(pk.MLMCError):
+        pk.Context(workloads.workload("lognormal_2layer_16to256", problem=5))
     with pk.Context(workloads.workload("const_2layer_8to32")) as ctx:
         with pytest.raises(pk.MLMCError):
             ctx.level_batch(5, 10, 0)
@@ -291,3 +293,12 @@ def test_model_problem_1_box_and_solve_k():
         assert abs(q[s] - q_ref) <= RTOL64 * abs(q_ref)
     with pytest.raises(pk.MLMCError):
         pk.Context(dict(d, qoi_box=[0.5, 0.4, 0.1, 0.2]))
+
+
+@pytest.mark.parametrize("name,prec,cgv,level,n", [
+    ("paper_3layer_const_16to128", 0, 0, 1, 30), ("paper_3layer_lognormal_16to128", 0, 0, 1, 10),
+    ("paper_3layer_lognormal_16to128", 0, 1, 2, 4), ("paper_3layer_lognormal_16to128", 1, 1, 1, 8)])
+def test_paper_geometry_levels(name, prec, cgv, level, n):
+    # Sec. 3.4's three sloped layers (per-cell layer map, per-layer parameters)
+    d = workloads.workload(name, prec=prec, cgv=cgv, tol=1e-12 if prec == 0 else 1e-10)
+    check_against_oracle(d, level, n, seed=17, first=0, rtol=RTOL64 if prec == 0 else RTOL_MIX)

@@ -143,3 +143,21 @@ def test_constant_k_closed_form_gpu():
         assert abs(q.item() - 2.5) < 1e-10 * 2.5
         x = (np.arange(m) + 0.5) / m
         assert np.max(np.abs(p.cpu().numpy()[0] - (1 - x)[None, :])) < 1e-9
+
+
+def test_paper_geometry_line_ends_and_fields():
+    # the sloped three-layer geometry of Sec. 3.4: line ends bit-exact, per-layer
+    # fields (outer layers lambda = 0.3 on one draw, middle layer lambda = 0.1 on
+    # its own draw) equal to the oracle's
+    torch, pk = need_gpu()
+    d = workloads.workload("paper_3layer_lognormal_16to128", prec=0)
+    model = darcy.Model.from_dict(d)
+    cache = {}
+    with pk.Context(d) as ctx:
+        for level in (0, 1):
+            g, ends = ctx.sample_fields(level, 5, seed=6, first=3)
+            g, ends = g.cpu().numpy(), ends.cpu().numpy()
+            for s in range(5):
+                assert np.array_equal(ends[s], darcy.interfaces(model, 6, level, 3 + s))
+                ref = darcy.layer_fields(model, 6, level, 3 + s, model.m(level), cache)
+                np.testing.assert_allclose(g[s], ref, rtol=0, atol=1e-12)
