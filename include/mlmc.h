@@ -209,6 +209,7 @@ typedef struct mlmc_tune_report {
   int32_t cluster[MLMC_MAX_LEVELS];            /* > 0: blocks of the cluster that solves one system */
   int32_t gamma[MLMC_MAX_LEVELS];              /* multigrid cycle: 1 V, 2 W */
   int32_t nu[MLMC_MAX_LEVELS];                 /* red-black sweep pairs per smoothing */
+  double inner_tol[MLMC_MAX_LEVELS];           /* prec 1: relative tolerance of the FP32 inner solves */
   int32_t candidates[MLMC_MAX_LEVELS];         /* plans timed */
   double ms_default[MLMC_MAX_LEVELS];          /* ms per sample, default plan */
   double ms_best[MLMC_MAX_LEVELS];             /* ms per sample, chosen plan */
@@ -217,7 +218,8 @@ typedef struct mlmc_tune_report {
 /* Times the candidate launch plans of the solver (one warp, one block of
  * 64/128/256/512 threads, or, for m >= 128, one thread-block cluster of 2, 4
  * or 8 blocks per system; all resident blocks or one per SM; for the
- * fastest of those, W-cycles or two smoothing sweep pairs) on a
+ * fastest of those, W-cycles or two smoothing sweep pairs, and with mixed
+ * precision an FP32 inner tolerance of 1e-4, 1e-5 or 1e-6) on a
  * probe batch of each level (samples from index 2^40 on, so no sample of
  * real use is consumed) and keeps the fastest for that level's solves.  The
  * arithmetic of a system does not depend on the plan except for the

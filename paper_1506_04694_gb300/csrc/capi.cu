@@ -518,12 +518,16 @@ int multilevel_impl(mlmc_ctx* c, int n_levels, const int64_t* first, const int64
   const bool graph = use_graph && c->st != nullptr && !c->prof_on;
   if (graph) {
     std::vector<int64_t> key = {(int64_t)n_levels, (int64_t)seed, (int64_t)g_alloc_generation.load()};
-    for (int l = 0; l < n_levels; ++l)
+    for (int l = 0; l < n_levels; ++l) {
       key.push_back(c->tuned_ok[l] ? ((int64_t)c->tuned[l].nu << 28) + ((int64_t)c->tuned[l].gamma << 24) +
                                          ((int64_t)c->tuned[l].threads << 16) +
                                          (c->tuned[l].cluster << 8) + (c->tuned[l].warp << 4) +
                                          c->tuned[l].cap_blocks_per_sm
                                    : -1);
+      int64_t tol_bits = 0;
+      if (c->tuned_ok[l]) std::memcpy(&tol_bits, &c->tuned[l].inner_tol, sizeof tol_bits);
+      key.push_back(tol_bits);
+    }
     for (int l = 0; l < n_levels; ++l) {
       key.push_back(first[l]);
       key.push_back(n[l]);
@@ -945,7 +949,7 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
       if ((err = run_fields(c, l, a.first, n, seed))) break;
       a.g = c->g.p;
     }
-    SolvePlan cand[18];
+    SolvePlan cand[20];
     int nk = solve_plan_candidates(m, md.prec, cand, 16);
     float best = 1e30f, def_ms = 0.f;
     int best_k = -1;
@@ -985,6 +989,20 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
         ++nk;
       }
     }
+    if (!err && best_k >= 0 && md.prec != 0) {  // mixed: looser or tighter FP32 inner solves
+      const SolvePlan base = cand[best_k];
+      for (double it : {1e-4, 1e-6}) {
+        if (err) break;
+        cand[nk] = base;
+        cand[nk].inner_tol = it;
+        const float ms = time_plan(cand[nk]);
+        if (ms < best) {
+          best = ms;
+          best_k = nk;
+        }
+        ++nk;
+      }
+    }
     if (err || best_k < 0) break;
     c->tuned[l] = cand[best_k];
     c->tuned_ok[l] = true;
@@ -995,6 +1013,7 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
       rep->cluster[l] = cand[best_k].cluster;
       rep->gamma[l] = cand[best_k].gamma;
       rep->nu[l] = cand[best_k].nu;
+      rep->inner_tol[l] = cand[best_k].inner_tol;
       rep->candidates[l] = nk;
       rep->ms_default[l] = def_ms / n;
       rep->ms_best[l] = best / n;

@@ -105,6 +105,7 @@ struct SolvePlan {
   int cap_blocks_per_sm; // > 0: launch at most this many blocks per SM (L2 residency)
   int gamma;             // multigrid cycle index: 1 V-cycle, 2 W-cycle
   int nu;                // smoothing: red-black sweep pairs before and after the coarse correction
+  double inner_tol;      // mixed precision: relative tolerance of each FP32 inner solve
 };
 
 size_t solve_ws_bytes(int m, int prec);

@@ -829,6 +829,7 @@ static int plan_fill(int m, int threads, int cluster, SolvePlan* P) {
   P->cap_blocks_per_sm = 0;
   P->gamma = 1;
   P->nu = 1;
+  P->inner_tol = 1e-5;
   cudaFuncSetAttribute(solve_kernel<MIXED, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<MIXED, MODE>, P->threads, P->smem_bytes) !=
@@ -926,6 +927,7 @@ int solve_launch(const SolveArgs& a, int prec, const SolvePlan& P, int n_blocks,
   b.ws_stride = P.ws_stride;
   b.mg_gamma = P.gamma;
   b.mg_nu = P.nu;
+  b.inner_tol = P.inner_tol;
   if (P.cluster) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];

@@ -202,6 +202,26 @@ def test_autotune_keeps_parity():
         assert abs(qc[i] - r["qc"]) <= RTOL64 * abs(r["qc"])
 
 
+def test_autotune_mixed_keeps_parity():
+    # the mixed-precision knobs (FP32 inner tolerance among them) change the
+    # iteration path, not the FP64 stopping test
+    torch, pk = need_gpu()
+    d = workloads.workload("lognormal_2layer_cgv_16to512", L=3, tol=1e-12)
+    model = darcy.Model.from_dict(d)
+    with pk.Context(d) as ctx:
+        rep = ctx.autotune(seed=2)
+        assert len(rep) == 4 and all(r["inner_tol"] in (1e-4, 1e-5, 1e-6) for r in rep)
+        qf = torch.empty(5, dtype=torch.float64, device="cuda")
+        qc = torch.empty_like(qf)
+        qg = torch.empty_like(qf)
+        ctx.level_batch(3, 5, 4, qf=qf, qc=qc, qc_cgv=qg)
+    qf, qg = qf.cpu().numpy(), qg.cpu().numpy()
+    for i in range(5):
+        r = darcy.sample(model, 4, 3, i)
+        assert abs(qf[i] - r["qf"]) <= RTOL_MIX * abs(r["qf"])
+        assert abs(qg[i] - r["qc_cgv"]) <= RTOL_MIX * abs(r["qc_cgv"])
+
+
 def test_checkpoint_resume_bit_identical(tmp_path):
     # an estimate interrupted after its first top-up round, checkpointed and
     # resumed in a fresh context, ends exactly where an uninterrupted one does
