@@ -190,7 +190,7 @@ def metric_name(d, args):
 def config_block(args, d):
     return {"workload": args.workload, "m_levels": [d["m0"] << l for l in range(d["L"] + 1)],
             "eps": d["eps"], "sigma2": d["sigma2"][0], "lambda": d["lam"][0], "layers": d["n_layers"],
-            "cgv": d["cgv"], "prec": "fp64" if d["prec"] == 0 else "fp32-mg/fp64-refinement",
+            "cgv": d["cgv"], "prec": PREC_NAMES[d["prec"]],
             "solver_tol": d["tol"], "seed": args.seed, "cost_model": "deterministic m_l^2 (1 + n_coarse/4)",
             "l2": "flushed between steps (256 MB device write)", "parallelism": "replicas%d" % args.gpus}
 
@@ -209,14 +209,20 @@ def reduce_over_ranks(total_ms, n_total, device):
     return float(t.item()), float(n.item())
 
 
+PREC_NAMES = {0: "fp64", 1: "fp32-mg/fp64-refinement", 2: "fp32-mg-bf16-faces/fp64-refinement"}
+
+
 def compare(args):
     """Time-to-eps: the workload as configured (mixed precision + CGV) against
-    plain FP64 batched MLMC without CGV at the same eps and levels."""
+    plain FP64 batched MLMC without CGV at the same eps and levels; with
+    --bf16-arm also the mixed CGV form with BF16 multigrid faces (prec 2)."""
     import torch
     import paper_1506_04694_gb300 as pk
     import workloads
     d = workloads.workload(args.compare)
     arms = {"mixed_cgv": dict(d), "plain_fp64": dict(d, prec=0, cgv=0)}
+    if args.bf16_arm:
+        arms["mixed_cgv_bf16_faces"] = dict(d, prec=2)
     out = {"compare": args.compare, "eps": d["eps"], "m_levels": [d["m0"] << l for l in range(d["L"] + 1)],
            "steps": args.steps, "warmup": args.warmup}
     stream = torch.cuda.Stream()
@@ -238,11 +244,16 @@ def compare(args):
             ts.append(e0.elapsed_time(e1) / 1e3)
         out[name] = {"time_to_eps_s": sum(ts) / len(ts), "N": est["N"], "V": est["V"], "q_hat": est["q_hat"],
                      "var_hat": est["var_hat"], "level_samples_per_s": sum(est["N"]) / (sum(ts) / len(ts)),
-                     "prec": "fp64" if md["prec"] == 0 else "fp32-mg/fp64-refinement", "cgv": md["cgv"]}
+                     "iters_per_sample": [round(x["iters_total"] / max(x["n"], 1), 2) for x in est["sums"]],
+                     "prec": PREC_NAMES[md["prec"]],
+                     "cgv": md["cgv"]}
         ctx.close()
         del ctx
         torch.cuda.empty_cache()
     out["speedup_mixed_cgv_vs_plain_fp64"] = out["plain_fp64"]["time_to_eps_s"] / out["mixed_cgv"]["time_to_eps_s"]
+    if args.bf16_arm:
+        out["speedup_bf16_faces_vs_fp32_faces"] = (out["mixed_cgv"]["time_to_eps_s"] /
+                                                   out["mixed_cgv_bf16_faces"]["time_to_eps_s"])
     print(json.dumps(out), flush=True)
 
 
@@ -258,6 +269,8 @@ def main():
     ap.add_argument("--compare", default=None,
                     help="workload name: time-to-eps of its mixed-precision CGV form against plain FP64 "
                          "batched MLMC (no CGV) at the same eps and level set; prints one JSON line")
+    ap.add_argument("--bf16-arm", action="store_true",
+                    help="with --compare: add the mixed CGV arm with BF16 multigrid faces (prec 2)")
     args = ap.parse_args()
     if args.compare:
         compare(args)

@@ -84,7 +84,10 @@ typedef struct mlmc_model {
   int32_t prec;                /* 0: FP64 throughout;
                                   1: FP32 multigrid-preconditioned CG inside FP64 iterative
                                      refinement (FP64 residual, solution, QoI and sums),
-                                     FP32 circulant-embedding FFT */
+                                     FP32 circulant-embedding FFT;
+                                  2: as 1, with the multigrid preconditioner's face
+                                     coefficients stored in BF16 on every level (the CG
+                                     operator and the FP64 residual keep FP32 faces) */
   double tol;                  /* stop when ||b - A x||_2 < tol ||b||_2 (Sec. 3.5 uses 1e-10) */
   int32_t max_it;              /* cap on CG iterations per solve (sum over refinement sweeps) */
   int32_t problem;             /* 0 or 2: Model Problem 2 of Sec. 3.4 (p = 1 / 0 at x1 = 0 / 1, no
@@ -209,7 +212,7 @@ typedef struct mlmc_tune_report {
   int32_t cluster[MLMC_MAX_LEVELS];            /* > 0: blocks of the cluster that solves one system */
   int32_t gamma[MLMC_MAX_LEVELS];              /* multigrid cycle: 1 V, 2 W */
   int32_t nu[MLMC_MAX_LEVELS];                 /* red-black sweep pairs per smoothing */
-  double inner_tol[MLMC_MAX_LEVELS];           /* prec 1: relative tolerance of the FP32 inner solves */
+  double inner_tol[MLMC_MAX_LEVELS];           /* prec 1, 2: relative tolerance of the FP32 inner solves */
   int32_t candidates[MLMC_MAX_LEVELS];         /* plans timed */
   double ms_default[MLMC_MAX_LEVELS];          /* ms per sample, default plan */
   double ms_best[MLMC_MAX_LEVELS];             /* ms per sample, chosen plan */

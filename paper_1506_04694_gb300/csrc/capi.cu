@@ -184,7 +184,7 @@ int check_model(const mlmc_model& md) {
   if (md.L < 0 || md.L >= MLMC_MAX_LEVELS) return fail(MLMC_ERR_ARG, "L must be 0..11");
   if ((int64_t)md.m0 << md.L > 4096) return fail(MLMC_ERR_TOOBIG, "m0 * 2^L must be <= 4096");
   if (md.cgv < 0 || md.cgv > 2) return fail(MLMC_ERR_ARG, "cgv must be 0, 1 or 2");
-  if (md.prec < 0 || md.prec > 1) return fail(MLMC_ERR_ARG, "prec must be 0 or 1");
+  if (md.prec < 0 || md.prec > 2) return fail(MLMC_ERR_ARG, "prec must be 0, 1 or 2");
   if (!(md.tol > 0) || md.max_it < 1) return fail(MLMC_ERR_ARG, "tol must be > 0 and max_it >= 1");
   if (!(md.if_hi >= md.if_lo)) return fail(MLMC_ERR_ARG, "if_hi must be >= if_lo");
   for (int t = 0; t < md.n_layers; ++t) {

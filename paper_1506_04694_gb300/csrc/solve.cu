@@ -20,6 +20,11 @@
 //         and QoI in FP64) around an FP32 CG with FP32 multigrid; the face
 //         coefficients are rounded to FP32 once and the FP64 residual uses
 //         exactly those values.
+// prec 2: prec 1 with the multigrid preconditioner's face coefficients held
+//         in BF16 on every level (the CG operator and the FP64 residual keep
+//         the FP32 faces; each multigrid level's diagonal is the sum of its
+//         own BF16 faces, so the preconditioner stays symmetric positive
+//         definite).
 // Outflow QoI M^(2) (Sec. 3.4): Q = sum_j T(m, j) p(m-1, j).
 #include <algorithm>
 #include <cmath>
@@ -29,6 +34,7 @@
 
 #include "../../include/mlmc.h"
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -38,63 +44,61 @@ namespace cg = cooperative_groups;
 namespace mlmc {
 
 constexpr int kMaxLevels = 14;
-constexpr int kArrays = 6;  // per level: tx, ty, diag, invd, e, f
 
 __host__ __device__ __forceinline__ size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
-// Workspace layout for an m x m system; element size ts of the solver
-// precision; mixed adds FP64 x and r.  Returns total bytes; fills offsets
-// when `off` is non-null: off[0..1] x64, r64; then per level l the kArrays
-// offsets (tx, ty, diag, invd, e, f) at 2 + kArrays l; level-0 extra CG
-// vectors x, p, q at 2 + kArrays*kMaxLevels + {0, 1, 2}.
-__host__ __device__ inline size_t ws_layout(int m, int ts, bool mixed, size_t* off) {
+// Workspace bytes of an m x m system, in the order solve_one() lays it out:
+// prec 1, 2: FP64 x and r; prec 2: the CG operator's FP32 faces and diagonal;
+// per level: faces tx, ty (solver type, BF16 with prec 2), diag, invd, e, f;
+// after level 0 the CG vectors x, p, q.  Each array starts 16-byte aligned.
+__host__ __device__ inline size_t ws_layout(int m, int prec) {
+  const size_t ts = prec ? 4 : 8, fs = prec == 2 ? 2 : ts;
   size_t o = 0;
   const size_t n = (size_t)m * m;
-  auto take = [&](size_t bytes) {
-    const size_t r = o;
-    o += align16(bytes);
-    return r;
-  };
-  size_t x64 = 0, r64 = 0;
-  if (mixed) {
-    x64 = take(n * 8);
-    r64 = take(n * 8);
+  auto take = [&](size_t bytes) { o += align16(bytes); };
+  if (prec) {
+    take(n * 8);
+    take(n * 8);
   }
-  if (off) {
-    off[0] = x64;
-    off[1] = r64;
+  if (prec == 2) {
+    take((size_t)m * (m + 1) * 4);
+    take((size_t)m * (m + 1) * 4);
+    take(n * 4);
   }
-  int ml = m, l = 0;
-  while (true) {
-    const size_t nl = (size_t)ml * ml;
-    const size_t nf = (size_t)ml * (ml + 1);
-    const size_t sizes[kArrays] = {nf, nf, nl, nl, nl, nl};
-    for (int a = 0; a < kArrays; ++a) {
-      const size_t at = take(sizes[a] * ts);
-      if (off) off[2 + kArrays * l + a] = at;
-    }
-    if (l == 0) {
-      for (int b = 0; b < 3; ++b) {
-        const size_t at = take(nl * ts);
-        if (off) off[2 + kArrays * kMaxLevels + b] = at;
-      }
-    }
+  for (int ml = m, l = 0;; ml >>= 1, ++l) {
+    const size_t nl = (size_t)ml * ml, nf = (size_t)ml * (ml + 1);
+    take(nf * fs);
+    take(nf * fs);
+    for (int a = 0; a < 4; ++a) take(nl * ts);
+    if (l == 0)
+      for (int b = 0; b < 3; ++b) take(nl * ts);
     if (ml == 1) break;
-    ml >>= 1;
-    ++l;
   }
   return o;
 }
 
-constexpr int kLayoutSlots = 2 + kArrays * kMaxLevels + 3;
-
+// Face coefficients are stored as F and used in the arithmetic type T.
 template <typename T>
+__device__ __forceinline__ T face_ld(T v) {
+  return v;
+}
+__device__ __forceinline__ float face_ld(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename F, typename T>
+__device__ __forceinline__ F face_st(T v) {
+  return v;
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 face_st<__nv_bfloat16, float>(float v) {
+  return __float2bfloat16_rn(v);
+}
+
+template <typename T, typename F = T>
 struct Level {
   int m;
-  T* tx;    // m rows x (m+1) faces
-  T* ty;    // (m+1) face rows x m
+  F* tx;    // m rows x (m+1) faces
+  F* ty;    // (m+1) face rows x m
   T* diag;  // sum of the four faces
-  T* invd;  // 1 / diagonal
+  T* invd;  // 1 / diagonal (null for the CG operator of prec 2)
   T* e;     // correction (level 0: CG z)
   T* f;     // right-hand side (level 0: CG r)
 };
@@ -154,16 +158,16 @@ struct ClusterGroup {
 
 // (A v)_c = diag_c v_c - sum over the faces of T v_nbr (v_nbr = 0 outside:
 // Dirichlet faces carry T but no neighbour, no-flow faces carry T = 0).
-template <typename T>
-__device__ __forceinline__ T apply_row(const Level<T>& L, const T* __restrict__ v, int i, int j) {
+template <typename T, typename F>
+__device__ __forceinline__ T apply_row(const Level<T, F>& L, const T* __restrict__ v, int i, int j) {
   const int m = L.m;
   const int c = j * m + i;
   const int rf = j * (m + 1) + i;
   T s = L.diag[c] * v[c];
-  if (i > 0) s -= L.tx[rf] * v[c - 1];
-  if (i < m - 1) s -= L.tx[rf + 1] * v[c + 1];
-  if (j > 0) s -= L.ty[c] * v[c - m];
-  if (j < m - 1) s -= L.ty[c + m] * v[c + m];
+  if (i > 0) s -= face_ld(L.tx[rf]) * v[c - 1];
+  if (i < m - 1) s -= face_ld(L.tx[rf + 1]) * v[c + 1];
+  if (j > 0) s -= face_ld(L.ty[c]) * v[c - m];
+  if (j < m - 1) s -= face_ld(L.ty[c + m]) * v[c + m];
   return s;
 }
 
@@ -176,8 +180,8 @@ __device__ __forceinline__ T apply_row(const Level<T>& L, const T* __restrict__ 
 
 // Red (color 0) or black (color 1) Gauss-Seidel half sweep; `zero_guess`
 // treats the other color as zero (first sweep of a cycle).
-template <typename T, typename G>
-__device__ __forceinline__ void rb_sweep(const G& g, const Level<T>& L, int color, bool zero_guess) {
+template <typename T, typename F, typename G>
+__device__ __forceinline__ void rb_sweep(const G& g, const Level<T, F>& L, int color, bool zero_guess) {
   const int m = L.m, hm = m >> 1;
   const int nh = m * hm;
   const int step = g.size();
@@ -196,10 +200,10 @@ __device__ __forceinline__ void rb_sweep(const G& g, const Level<T>& L, int colo
         T s = L.f[c];
         if (!zero_guess) {
           const int rf = j * (m + 1) + i;
-          if (i > 0) s += L.tx[rf] * L.e[c - 1];
-          if (i < m - 1) s += L.tx[rf + 1] * L.e[c + 1];
-          if (j > 0) s += L.ty[c] * L.e[c - m];
-          if (j < m - 1) s += L.ty[c + m] * L.e[c + m];
+          if (i > 0) s += face_ld(L.tx[rf]) * L.e[c - 1];
+          if (i < m - 1) s += face_ld(L.tx[rf + 1]) * L.e[c + 1];
+          if (j > 0) s += face_ld(L.ty[c]) * L.e[c - m];
+          if (j < m - 1) s += face_ld(L.ty[c + m]) * L.e[c + m];
         }
         val[u] = s * L.invd[c];
         cc[u] = c;
@@ -216,8 +220,8 @@ __device__ __forceinline__ void rb_sweep(const G& g, const Level<T>& L, int colo
 // Called right after a black half sweep, which leaves the residual at the
 // black cells zero, so only the two red cells (2I, 2J), (2I+1, 2J+1) of the
 // aggregate contribute.
-template <typename T, typename G>
-__device__ __forceinline__ void restrict_residual(const G& g, const Level<T>& F, const Level<T>& C) {
+template <typename T, typename FT, typename G>
+__device__ __forceinline__ void restrict_residual(const G& g, const Level<T, FT>& F, const Level<T, FT>& C) {
   const int mc = C.m, m = F.m;
   const int nc = mc * mc, step = g.size();
   for (int c0 = g.rank(); c0 < nc; c0 += G::kU * step) {
@@ -241,8 +245,8 @@ __device__ __forceinline__ void restrict_residual(const G& g, const Level<T>& F,
   g.sync();
 }
 
-template <typename T, typename G>
-__device__ __forceinline__ void prolong_add(const G& g, const Level<T>& C, const Level<T>& F) {
+template <typename T, typename FT, typename G>
+__device__ __forceinline__ void prolong_add(const G& g, const Level<T, FT>& C, const Level<T, FT>& F) {
   const int m = F.m, mc = C.m;
   const int n = m * m, step = g.size();
   for (int c0 = g.rank(); c0 < n; c0 += G::kU * step) {
@@ -263,32 +267,34 @@ __device__ __forceinline__ void prolong_add(const G& g, const Level<T>& C, const
 }
 
 // Coarse faces: mean of the two fine faces forming each coarse face.
-template <typename T, typename G>
-__device__ __forceinline__ void build_coarse(const G& g, const Level<T>& F, const Level<T>& C) {
+template <typename T, typename FT, typename G>
+__device__ __forceinline__ void build_coarse(const G& g, const Level<T, FT>& F, const Level<T, FT>& C) {
   const int m = F.m, mc = C.m;
   const int nfx = mc * (mc + 1);
   for (int t = g.rank(); t < 2 * nfx; t += g.size()) {
     if (t < nfx) {
       const int J = t / (mc + 1), Ip = t - J * (mc + 1);
-      C.tx[t] = T(0.5) * (F.tx[(2 * J) * (m + 1) + 2 * Ip] + F.tx[(2 * J + 1) * (m + 1) + 2 * Ip]);
+      C.tx[t] = face_st<FT>(T(0.5) * (face_ld(F.tx[(2 * J) * (m + 1) + 2 * Ip]) +
+                                      face_ld(F.tx[(2 * J + 1) * (m + 1) + 2 * Ip])));
     } else {
       const int u = t - nfx;
       const int Jp = u / mc, I = u - Jp * mc;
-      C.ty[u] = T(0.5) * (F.ty[(2 * Jp) * m + 2 * I] + F.ty[(2 * Jp) * m + 2 * I + 1]);
+      C.ty[u] = face_st<FT>(T(0.5) * (face_ld(F.ty[(2 * Jp) * m + 2 * I]) + face_ld(F.ty[(2 * Jp) * m + 2 * I + 1])));
     }
   }
   g.sync();
 }
 
-template <typename T, typename G>
-__device__ __forceinline__ void build_diag(const G& g, const Level<T>& L) {
+// Diagonal (sum of the four faces) and, with INV, its reciprocal.
+template <bool INV, typename T, typename FT, typename G>
+__device__ __forceinline__ void build_diag(const G& g, const Level<T, FT>& L) {
   const int m = L.m;
   for (int c = g.rank(); c < m * m; c += g.size()) {
     const int j = c / m, i = c - j * m;
     const int rf = j * (m + 1) + i;
-    const T d = (L.tx[rf] + L.tx[rf + 1]) + (L.ty[c] + L.ty[c + m]);
+    const T d = (face_ld(L.tx[rf]) + face_ld(L.tx[rf + 1])) + (face_ld(L.ty[c]) + face_ld(L.ty[c + m]));
     L.diag[c] = d;
-    L.invd[c] = T(1) / d;
+    if (INV) L.invd[c] = T(1) / d;
   }
   g.sync();
 }
@@ -300,8 +306,8 @@ __device__ __forceinline__ void build_diag(const G& g, const Level<T>& L) {
 // over an explicit per-level visit count (no recursion: the device stack
 // stays fixed).  With adjoint pre- and post-smoothing the cycle is a
 // symmetric positive definite preconditioner for any gamma.
-template <typename T, typename G>
-__device__ void mg_cycle(const G& g, const Level<T>* lev, int nl, int gamma, int nu) {
+template <typename T, typename F, typename G>
+__device__ void mg_cycle(const G& g, const Level<T, F>* lev, int nl, int gamma, int nu) {
   int done[kMaxLevels];   // visits of level l+1 finished in the current cycle on level l
   bool zero[kMaxLevels];  // level l starts from e_l = 0
   int l = 0;
@@ -319,7 +325,7 @@ __device__ void mg_cycle(const G& g, const Level<T>* lev, int nl, int gamma, int
       continue;
     }
     {  // coarsest (1 x 1): exact
-      const Level<T>& Lc = lev[l];
+      const Level<T, F>& Lc = lev[l];
       if (g.rank() == 0) Lc.e[0] = Lc.f[0] * Lc.invd[0];
       g.sync();
     }
@@ -345,15 +351,15 @@ __device__ void mg_cycle(const G& g, const Level<T>* lev, int nl, int gamma, int
 }
 
 // Symmetric V-cycle: level-0 e <- B f (the loop form of mg_cycle, gamma 1).
-template <typename T, typename G>
-__device__ void vcycle(const G& g, const Level<T>* lev, int nl) {
+template <typename T, typename F, typename G>
+__device__ void vcycle(const G& g, const Level<T, F>* lev, int nl) {
   for (int l = 0; l < nl - 1; ++l) {
     rb_sweep(g, lev[l], 0, true);
     rb_sweep(g, lev[l], 1, false);
     restrict_residual(g, lev[l], lev[l + 1]);
   }
   {
-    const Level<T>& Lc = lev[nl - 1];  // 1 x 1
+    const Level<T, F>& Lc = lev[nl - 1];  // 1 x 1
     if (g.rank() == 0) Lc.e[0] = Lc.f[0] * Lc.invd[0];
     g.sync();
   }
@@ -364,21 +370,23 @@ __device__ void vcycle(const G& g, const Level<T>* lev, int nl) {
   }
 }
 
-template <typename T, typename G>
-__device__ __forceinline__ void precond(const G& g, const Level<T>* lev, int nl, int gamma, int nu) {
+template <typename T, typename F, typename G>
+__device__ __forceinline__ void precond(const G& g, const Level<T, F>* lev, int nl, int gamma, int nu) {
   if (gamma <= 1 && nu <= 1)
     vcycle(g, lev, nl);
   else
     mg_cycle(g, lev, nl, gamma < 1 ? 1 : gamma, nu < 1 ? 1 : nu);
 }
 
-// Preconditioned CG on level-0 operator: x = 0 on entry, r = rhs.
-// Stops when r.r <= thr; returns iterations, status 0 converged, 1 hit the
-// cap, 2 breakdown (p.Ap <= 0 or not finite).
-template <typename T, typename G>
-__device__ int pcg(const G& g, const Level<T>* lev, int nl, int gamma, int nu, T* __restrict__ x, T* __restrict__ p,
-                   T* __restrict__ q, T thr, int max_it, T* red, int& par, int& status) {
-  const Level<T>& L0 = lev[0];
+// CG on the operator A (faces and diagonal of the finest grid), multigrid
+// preconditioner on lev (r = lev[0].f, z = lev[0].e): x = 0 on entry,
+// r = rhs.  Stops when r.r <= thr; returns iterations, status 0 converged,
+// 1 hit the cap, 2 breakdown (p.Ap <= 0 or not finite).
+template <typename T, typename F, typename G>
+__device__ int pcg(const G& g, const Level<T>& A, const Level<T, F>* lev, int nl, int gamma, int nu,
+                   T* __restrict__ x, T* __restrict__ p, T* __restrict__ q, T thr, int max_it, T* red, int& par,
+                   int& status) {
+  const Level<T, F>& L0 = lev[0];
   const int m = L0.m, n = m * m;
   T* __restrict__ r = L0.f;
   const T* __restrict__ z = L0.e;
@@ -413,7 +421,7 @@ __device__ int pcg(const G& g, const Level<T>* lev, int nl, int gamma, int nu, T
         val[u] = T(0);
         if (c < n) {
           const int j = c / m, i = c - j * m;
-          val[u] = apply_row(L0, p, i, j);
+          val[u] = apply_row(A, p, i, j);
           pq += p[c] * val[u];
         }
       }
@@ -509,10 +517,13 @@ __device__ void sample_layers(const SolveArgs& a, uint64_t sample, double* eta, 
 constexpr int kMaxThreads = 512;
 constexpr int kWarpsPerBlock = 4;  // systems per block in warp mode
 
-// Per-system state shared by the threads of one group.
-template <typename T>
+// Per-system state shared by the threads of one group: the multigrid
+// hierarchy and the CG operator (the finest level's arrays, or with prec 2
+// separate FP32 faces and diagonal).
+template <typename T, typename F>
 struct GroupState {
-  Level<T> lev[kMaxLevels];
+  Level<T, F> lev[kMaxLevels];
+  Level<T> op;
   T *xv, *pv, *qv;
   double *x64, *r64;
   double eta[MAX_LAYERS_DEV], kc[MAX_LAYERS_DEV];
@@ -527,13 +538,29 @@ __host__ __device__ inline int solve_threads(int m) {
   return solve_warp_mode(m) ? 32 * kWarpsPerBlock : (m <= 64 ? 256 : 512);
 }
 
+// The CG operator: separate FP32 arrays with prec 2, else the finest level.
+template <int PREC, typename T, typename F>
+__device__ __forceinline__ const Level<T>& cg_operator(const GroupState<T, F>& gs) {
+  if constexpr (PREC == 2)
+    return gs.op;
+  else
+    return gs.lev[0];
+}
+
+template <int PREC>
+struct SolverTypes {
+  using T = typename std::conditional<PREC != 0, float, double>::type;       // arithmetic
+  using F = typename std::conditional<PREC == 2, __nv_bfloat16, T>::type;  // multigrid faces
+};
+
 // Assemble, solve and reduce the QoI of one system with group g.
-template <bool MIXED, typename G>
+template <int PREC, typename G>
 __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned char* base,
-                          GroupState<typename std::conditional<MIXED, float, double>::type>& gs,
-                          typename std::conditional<MIXED, float, double>::type* red, double* red64,
-                          int& par, int& m_prev) {
-  using T = typename std::conditional<MIXED, float, double>::type;
+                          GroupState<typename SolverTypes<PREC>::T, typename SolverTypes<PREC>::F>& gs,
+                          typename SolverTypes<PREC>::T* red, double* red64, int& par, int& m_prev) {
+  using T = typename SolverTypes<PREC>::T;
+  using F = typename SolverTypes<PREC>::F;
+  constexpr bool MIXED = PREC != 0;
   int64_t sidx;
   int coarse = 0, ox = 0, oy = 0;
   if (sys < a.n_samples) {
@@ -564,13 +591,20 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
         gs.x64 = reinterpret_cast<double*>(take(n0 * 8));
         gs.r64 = reinterpret_cast<double*>(take(n0 * 8));
       }
+      if (PREC == 2) {
+        const size_t nf0 = (size_t)m * (m + 1);
+        gs.op.tx = reinterpret_cast<T*>(take(nf0 * sizeof(T)));
+        gs.op.ty = reinterpret_cast<T*>(take(nf0 * sizeof(T)));
+        gs.op.diag = reinterpret_cast<T*>(take(n0 * sizeof(T)));
+        gs.op.invd = nullptr;
+      }
       int l = 0;
       for (int ml = m;; ml >>= 1, ++l) {
         const size_t nlv = (size_t)ml * ml, nf = (size_t)ml * (ml + 1);
-        Level<T>& L = gs.lev[l];
+        Level<T, F>& L = gs.lev[l];
         L.m = ml;
-        L.tx = reinterpret_cast<T*>(take(nf * sizeof(T)));
-        L.ty = reinterpret_cast<T*>(take(nf * sizeof(T)));
+        L.tx = reinterpret_cast<F*>(take(nf * sizeof(F)));
+        L.ty = reinterpret_cast<F*>(take(nf * sizeof(F)));
         L.diag = reinterpret_cast<T*>(take(nlv * sizeof(T)));
         L.invd = reinterpret_cast<T*>(take(nlv * sizeof(T)));
         L.e = reinterpret_cast<T*>(take(nlv * sizeof(T)));
@@ -583,6 +617,9 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
         if (ml == 1) break;
       }
       gs.nl = l + 1;
+      gs.op.m = m;
+      gs.op.e = gs.lev[0].e;
+      gs.op.f = gs.lev[0].f;
       if (!MIXED) {
         gs.x64 = reinterpret_cast<double*>(gs.xv);
         gs.r64 = reinterpret_cast<double*>(gs.lev[0].f);
@@ -597,8 +634,9 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
   T* qv = gs.qv;
   double* x64 = gs.x64;
   double* r64 = gs.r64;
-  const Level<T>* lev = gs.lev;
-  const Level<T>& L0 = lev[0];
+  const Level<T, F>* lev = gs.lev;
+  const Level<T, F>& L0 = lev[0];
+  const Level<T>& A = cg_operator<PREC>(gs);
 
   // ---- layers and per-cell permeability (into r64 as scratch) ----
   if (a.ksrc != KSRC_ARRAY) {
@@ -645,7 +683,8 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
           const T ka = (T)r64[j * m + ip - 1], kb = (T)r64[j * m + ip];
           v = T(2) * ka * kb / (ka + kb);
         }
-        L0.tx[t] = v;
+        A.tx[t] = v;
+        if (PREC == 2) L0.tx[t] = face_st<F>(v);
       } else {
         const int u = t - nfx;
         const int jp = u / m, i = u - jp * m;
@@ -656,15 +695,17 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
         } else if (a.problem == 1) {  // Dirichlet p = 0 half a cell away
           v = T(2) * (T)r64[(jp == 0 ? 0 : m - 1) * m + i];
         }
-        L0.ty[u] = v;
+        A.ty[u] = v;
+        if (PREC == 2) L0.ty[u] = face_st<F>(v);
       }
     }
     g.sync();
-    build_diag(g, L0);
+    if (PREC == 2) build_diag<false>(g, A);
+    build_diag<true>(g, L0);
   }
   for (int l = 1; l < nl; ++l) {
     build_coarse(g, lev[l - 1], lev[l]);
-    build_diag(g, lev[l]);
+    build_diag<true>(g, lev[l]);
   }
   // ---- solve ----
   int status = 1, iters = 0;
@@ -674,19 +715,20 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
     const T fmid = (T)(1.0 / ((double)m * (double)m));  // Model Problem 1: f / m^2
     for (int c = g.rank(); c < n; c += g.size()) {
       const int j = c / m, i = c - j * m;
-      const T bv = a.problem == 1 ? fmid : (i == 0 ? L0.tx[j * (m + 1)] : T(0));
+      const T bv = a.problem == 1 ? fmid : (i == 0 ? A.tx[j * (m + 1)] : T(0));
       L0.f[c] = bv;
       bb += bv * bv;
     }
     bb = g.sum(bb, red, par);
-    iters = pcg(g, lev, nl, a.mg_gamma, a.mg_nu, xv, pv, qv, (T)(a.tol * a.tol) * bb, a.max_it, red, par, status);
+    iters = pcg(g, A, lev, nl, a.mg_gamma, a.mg_nu, xv, pv, qv, (T)(a.tol * a.tol) * bb, a.max_it, red, par,
+                status);
   } else {
     // FP64 refinement: r64 = b - A64 x64 with A64 = the FP32 faces in FP64.
     double bb = 0.0;
     const double fmid = 1.0 / ((double)m * (double)m);  // Model Problem 1: f / m^2
     for (int c = g.rank(); c < n; c += g.size()) {
       const int j = c / m, i = c - j * m;
-      const double bv = a.problem == 1 ? fmid : (i == 0 ? (double)L0.tx[j * (m + 1)] : 0.0);
+      const double bv = a.problem == 1 ? fmid : (i == 0 ? (double)A.tx[j * (m + 1)] : 0.0);
       x64[c] = 0.0;
       r64[c] = bv;
       bb += bv * bv;
@@ -716,7 +758,8 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
       r32 = g.sum(r32, red, par);
       int st_in = 1;
       const T thr_in = (T)(a.inner_tol * a.inner_tol) * r32;
-      const int it = pcg(g, lev, nl, a.mg_gamma, a.mg_nu, xv, pv, qv, thr_in, a.max_it - iters, red, par, st_in);
+      const int it =
+          pcg(g, A, lev, nl, a.mg_gamma, a.mg_nu, xv, pv, qv, thr_in, a.max_it - iters, red, par, st_in);
       iters += it;
       // x64 += scl * d, then r64 = b - A64 x64 (FP64)
       for (int c = g.rank(); c < n; c += g.size()) x64[c] += scl * (double)xv[c];
@@ -725,8 +768,8 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
       for (int c = g.rank(); c < n; c += g.size()) {
         const int j = c / m, i = c - j * m;
         const int rf = j * (m + 1) + i;
-        const double tw = (double)L0.tx[rf], te = (double)L0.tx[rf + 1];
-        const double ts = (double)L0.ty[c], tn = (double)L0.ty[c + m];
+        const double tw = (double)A.tx[rf], te = (double)A.tx[rf + 1];
+        const double ts = (double)A.ty[c], tn = (double)A.ty[c + m];
         double ax = ((tw + te) + (ts + tn)) * x64[c];
         if (i > 0) ax -= tw * x64[c - 1];
         if (i < m - 1) ax -= te * x64[c + 1];
@@ -758,7 +801,7 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
     }
   } else {
     // M^(2): outflow through x1 = 1
-    for (int j = g.rank(); j < m; j += g.size()) qsum += (double)L0.tx[j * (m + 1) + m] * x64[j * m + m - 1];
+    for (int j = g.rank(); j < m; j += g.size()) qsum += (double)A.tx[j * (m + 1) + m] * x64[j * m + m - 1];
   }
   qsum = g.sum(qsum, red64, par);
   if (g.rank() == 0) {
@@ -772,13 +815,14 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
 
 // MODE 0: one block per system; 1: one warp per system (kWarpsPerBlock
 // systems per block); 2: one thread-block cluster per system.
-template <bool MIXED, int MODE>
+template <int PREC, int MODE>
 __global__ void __launch_bounds__(MODE == 1 ? 32 * kWarpsPerBlock : kMaxThreads, MODE == 1 ? 5 : 2)
     solve_kernel(SolveArgs a) {
-  using T = typename std::conditional<MIXED, float, double>::type;
+  using T = typename SolverTypes<PREC>::T;
+  using F = typename SolverTypes<PREC>::F;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int kGroups = MODE == 1 ? kWarpsPerBlock : 1;
-  __shared__ GroupState<T> gstate[kGroups];
+  __shared__ GroupState<T, F> gstate[kGroups];
   __shared__ T red[MODE == 1 ? 1 : 132];
   __shared__ double red64[MODE == 1 ? 1 : 132];
   const int64_t n_sys = a.n_samples * (int64_t)(1 + a.n_coarse);
@@ -790,7 +834,7 @@ __global__ void __launch_bounds__(MODE == 1 ? 32 * kWarpsPerBlock : kMaxThreads,
     const int64_t cid = blockIdx.x / g.nblk, ncl = gridDim.x / g.nblk;
     unsigned char* base = a.ws + (size_t)cid * a.ws_stride;
     for (int64_t sys = cid; sys < n_sys; sys += ncl)
-      solve_one<MIXED>(g, a, sys, base, gstate[0], red, red64, par, m_prev);
+      solve_one<PREC>(g, a, sys, base, gstate[0], red, red64, par, m_prev);
     cl.sync();  // no block leaves while others may still read its shared memory
     return;
   }
@@ -800,21 +844,19 @@ __global__ void __launch_bounds__(MODE == 1 ? 32 * kWarpsPerBlock : kMaxThreads,
   const int64_t stride = (int64_t)gridDim.x * kGroups;
   for (int64_t sys = (int64_t)blockIdx.x * kGroups + gid; sys < n_sys; sys += stride) {
     if (MODE == 1)
-      solve_one<MIXED>(WarpGroup(), a, sys, base, gstate[gid], red, red64, par, m_prev);
+      solve_one<PREC>(WarpGroup(), a, sys, base, gstate[gid], red, red64, par, m_prev);
     else
-      solve_one<MIXED>(BlockGroup(), a, sys, base, gstate[gid], red, red64, par, m_prev);
+      solve_one<PREC>(BlockGroup(), a, sys, base, gstate[gid], red, red64, par, m_prev);
   }
 }
 
-size_t solve_ws_bytes(int m, int prec) {
-  return ws_layout(m, prec ? 4 : 8, prec != 0, nullptr);
-}
+size_t solve_ws_bytes(int m, int prec) { return ws_layout(m, prec); }
 
 static const size_t kSmemCap = 110 * 1024;
 
-template <bool MIXED, int MODE>
+template <int PREC, int MODE>
 static int plan_fill(int m, int threads, int cluster, SolvePlan* P) {
-  const size_t ws = solve_ws_bytes(m, MIXED);
+  const size_t ws = solve_ws_bytes(m, PREC);
   int nsm = 0, dev = 0;
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
@@ -830,9 +872,9 @@ static int plan_fill(int m, int threads, int cluster, SolvePlan* P) {
   P->gamma = 1;
   P->nu = 1;
   P->inner_tol = 1e-5;
-  cudaFuncSetAttribute(solve_kernel<MIXED, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
+  cudaFuncSetAttribute(solve_kernel<PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<MIXED, MODE>, P->threads, P->smem_bytes) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<PREC, MODE>, P->threads, P->smem_bytes) !=
       cudaSuccess)
     return -1;
   P->blocks_per_sm = nb < 1 ? 1 : nb;
@@ -850,22 +892,24 @@ static int plan_fill(int m, int threads, int cluster, SolvePlan* P) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int ncl = 0;
-    if (cudaOccupancyMaxActiveClusters(&ncl, solve_kernel<MIXED, MODE>, &cfg) != cudaSuccess || ncl < 1) return -1;
+    if (cudaOccupancyMaxActiveClusters(&ncl, solve_kernel<PREC, MODE>, &cfg) != cudaSuccess || ncl < 1) return -1;
     P->max_groups = ncl;
   }
   return 0;
 }
 
 // mode: 0 block, 1 warp, 2 cluster of `cluster` blocks
+template <int PREC>
+static int plan_fill_mode(int m, int mode, int threads, int cluster, SolvePlan* P) {
+  if (mode == 1) return plan_fill<PREC, 1>(m, threads, cluster, P);
+  if (mode == 2) return plan_fill<PREC, 2>(m, threads, cluster, P);
+  return plan_fill<PREC, 0>(m, threads, cluster, P);
+}
+
 static int plan_fill(int m, int prec, int mode, int threads, int cluster, SolvePlan* P) {
-  if (prec) {
-    if (mode == 1) return plan_fill<true, 1>(m, threads, cluster, P);
-    if (mode == 2) return plan_fill<true, 2>(m, threads, cluster, P);
-    return plan_fill<true, 0>(m, threads, cluster, P);
-  }
-  if (mode == 1) return plan_fill<false, 1>(m, threads, cluster, P);
-  if (mode == 2) return plan_fill<false, 2>(m, threads, cluster, P);
-  return plan_fill<false, 0>(m, threads, cluster, P);
+  if (prec == 2) return plan_fill_mode<2>(m, mode, threads, cluster, P);
+  if (prec == 1) return plan_fill_mode<1>(m, mode, threads, cluster, P);
+  return plan_fill_mode<0>(m, mode, threads, cluster, P);
 }
 
 // Default plan (measured on GB300 with the autotuner): a warp per system up
@@ -941,16 +985,20 @@ int solve_launch(const SolveArgs& a, int prec, const SolvePlan& P, int n_blocks,
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const cudaError_t e = prec ? cudaLaunchKernelEx(&cfg, solve_kernel<true, 2>, b)
-                               : cudaLaunchKernelEx(&cfg, solve_kernel<false, 2>, b);
+    const cudaError_t e = prec == 2   ? cudaLaunchKernelEx(&cfg, solve_kernel<2, 2>, b)
+                          : prec == 1 ? cudaLaunchKernelEx(&cfg, solve_kernel<1, 2>, b)
+                                      : cudaLaunchKernelEx(&cfg, solve_kernel<0, 2>, b);
     return e == cudaSuccess ? 0 : -1;
   }
-  if (prec) {
-    if (P.warp) solve_kernel<true, 1><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
-    else solve_kernel<true, 0><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+  if (prec == 2) {
+    if (P.warp) solve_kernel<2, 1><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+    else solve_kernel<2, 0><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+  } else if (prec == 1) {
+    if (P.warp) solve_kernel<1, 1><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+    else solve_kernel<1, 0><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
   } else {
-    if (P.warp) solve_kernel<false, 1><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
-    else solve_kernel<false, 0><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+    if (P.warp) solve_kernel<0, 1><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+    else solve_kernel<0, 0><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -1052,7 +1100,7 @@ extern "C" int mlmc_solve_k_static(int device, int32_t m, int64_t n, const doubl
   using namespace mlmc;
   if (device < 0 || device >= kMaxDevices || !k || !q || n < 0) return MLMC_ERR_ARG;
   if (m < 1 || m > 4096 || (m & (m - 1))) return MLMC_ERR_ARG;
-  if (!(tol > 0) || max_it < 1 || (prec != 0 && prec != 1)) return MLMC_ERR_ARG;
+  if (!(tol > 0) || max_it < 1 || prec < 0 || prec > 2) return MLMC_ERR_ARG;
   if (n == 0) return MLMC_OK;
   int prev = -1;
   if (cudaGetDevice(&prev) != cudaSuccess) return MLMC_ERR_NODEV;

@@ -81,6 +81,20 @@ def test_four_layers_mixed():
     check_against_oracle(d, 1, 8, seed=3, first=0, rtol=RTOL_MIX)
 
 
+@pytest.mark.parametrize("level,n", [(0, 20), (1, 8), (2, 4)])
+def test_bf16_faces_in_multigrid(level, n):
+    # prec 2: BF16 faces only inside the multigrid preconditioner; the FP64
+    # refinement still solves the FP32-face operator to tol, so Q agrees with
+    # the oracle as closely as with FP32 faces, at a few more iterations
+    d = workloads.workload("lognormal_4layer_cgv_16to1024", tol=1e-10, prec=2)
+    _, qf2, _, qg2, it2 = check_against_oracle(d, level, n, seed=3, first=0, rtol=RTOL_MIX)
+    torch, pk = need_gpu()
+    _, qf1, _, qg1, it1 = run_gpu(pk, torch, dict(d, prec=1), level, n, 3)
+    np.testing.assert_allclose(qf2, qf1, rtol=1e-8, atol=0)
+    np.testing.assert_allclose(qg2, qg1, rtol=1e-8, atol=0)
+    assert it2.sum() <= 1.5 * it1.sum() + n
+
+
 @pytest.mark.parametrize("tol,rtol", [(1e-13, RTOL64), (1e-10, 1e-7)])
 def test_full_size_sampled_fp64(tol, rtol):
     # the benchmark's finest level (m = 256, M = 1024) in the launch the
@@ -258,7 +272,7 @@ def test_nan_permeability_reported_as_failure():
     assert np.isnan(q[2]) and np.all(np.isfinite(q[[0, 1, 3]]))
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_launch_modes_agree(prec):
     # one system per block (64..512 threads), per warp, or per thread-block
     # cluster of 2/4/8 blocks, with V- or W-cycles and one or two smoothing
@@ -290,7 +304,8 @@ def test_launch_modes_agree(prec):
         assert abs(res[-1][1][i] - r["qc_cgv"]) <= tol * abs(r["qc_cgv"])
 
 
-@pytest.mark.parametrize("prec,cgv,level,n", [(0, 0, 0, 30), (0, 0, 2, 6), (0, 1, 1, 10), (1, 1, 2, 6)])
+@pytest.mark.parametrize("prec,cgv,level,n", [(0, 0, 0, 30), (0, 0, 2, 6), (0, 1, 1, 10), (1, 1, 2, 6),
+                                              (2, 1, 2, 6)])
 def test_model_problem_1(prec, cgv, level, n):
     # Sec. 3.4 Model Problem 1: f = 1, p = 0 on the whole boundary, Q = mean of p
     # over D* = [7/16, 9/16]^2, plain and CGV coupling, FP64 and mixed

@@ -120,12 +120,12 @@ def test_solve_k_fp64(m):
     assert it.max() < 100
 
 
-@pytest.mark.parametrize("m", [16, 64, 256])
-def test_solve_k_mixed(m):
+@pytest.mark.parametrize("m,prec", [(16, 1), (64, 1), (256, 1), (16, 2), (64, 2), (256, 2)])
+def test_solve_k_mixed(m, prec):
     torch, pk = need_gpu()
     n = 6
     k = workloads.random_k(m, seed=100 + m, n=n, contrast=4.0)
-    d = workloads.workload("const_2layer_8to32", tol=1e-12, max_it=1000, prec=1)
+    d = workloads.workload("const_2layer_8to32", tol=1e-12, max_it=1000, prec=prec)
     with pk.Context(d) as ctx:
         _, q, it = ctx.solve_k(torch.from_numpy(k).cuda(), want_p=False)
         q = q.cpu().numpy()
