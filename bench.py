@@ -31,6 +31,7 @@ DEFAULT_WORKLOAD = "lognormal_2layer_16to256"
 # FP64 vector peak of GB300 (nominal 1.25 TFLOP/s: 152 SMs x 2 FP64 FMA/clk x
 # 2 flop x ~2.06 GHz).
 FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 80.5
 # Sample of the oracle timed for the CPU baseline: samples per level.
 CPU_SAMPLE = {0: 512, 1: 128, 2: 48, 3: 16, 4: 8, 5: 2, 6: 1}
 
@@ -183,7 +184,8 @@ def run_reference(args, d):
 
 def metric_name(d, args):
     return ("level solves/s: MLMC time-to-RMSE eps=%g, %d-layer piecewise log-normal, m=%d..%d, %s%s"
-            % (d["eps"], d["n_layers"], d["m0"], d["m0"] << d["L"], "FP64" if d["prec"] == 0 else "mixed FP32-MG",
+            % (d["eps"], d["n_layers"], d["m0"], d["m0"] << d["L"], {0: "FP64", 1: "mixed FP32-MG", 2: "mixed FP32-MG (BF16 faces)",
+                                                         3: "FP64 CG with FP32-MG preconditioner"}[d["prec"]],
                ", CGV" if d["cgv"] else ""))
 
 
@@ -209,13 +211,16 @@ def reduce_over_ranks(total_ms, n_total, device):
     return float(t.item()), float(n.item())
 
 
-PREC_NAMES = {0: "fp64", 1: "fp32-mg/fp64-refinement", 2: "fp32-mg-bf16-faces/fp64-refinement"}
+PREC_NAMES = {0: "fp64", 1: "fp32-mg/fp64-refinement", 2: "fp32-mg-bf16-faces/fp64-refinement",
+              3: "fp64-cg/fp32-mg-preconditioner"}
 
 
 def compare(args):
     """Time-to-eps: the workload as configured (mixed precision + CGV) against
     plain FP64 batched MLMC without CGV at the same eps and levels; with
-    --bf16-arm also the mixed CGV form with BF16 multigrid faces (prec 2)."""
+    --bf16-arm also the mixed CGV form with BF16 multigrid faces (prec 2), with
+    --fp64cg-arm the CGV form with FP64 fields and CG around an FP32
+    multigrid preconditioner (prec 3)."""
     import torch
     import paper_1506_04694_gb300 as pk
     import workloads
@@ -223,6 +228,8 @@ def compare(args):
     arms = {"mixed_cgv": dict(d), "plain_fp64": dict(d, prec=0, cgv=0)}
     if args.bf16_arm:
         arms["mixed_cgv_bf16_faces"] = dict(d, prec=2)
+    if args.fp64cg_arm:
+        arms["fp64cg_fp32mg_cgv"] = dict(d, prec=3)
     out = {"compare": args.compare, "eps": d["eps"], "m_levels": [d["m0"] << l for l in range(d["L"] + 1)],
            "steps": args.steps, "warmup": args.warmup}
     stream = torch.cuda.Stream()
@@ -254,6 +261,9 @@ def compare(args):
     if args.bf16_arm:
         out["speedup_bf16_faces_vs_fp32_faces"] = (out["mixed_cgv"]["time_to_eps_s"] /
                                                    out["mixed_cgv_bf16_faces"]["time_to_eps_s"])
+    if args.fp64cg_arm:
+        out["speedup_fp64cg_fp32mg_cgv_vs_plain_fp64"] = (out["plain_fp64"]["time_to_eps_s"] /
+                                                          out["fp64cg_fp32mg_cgv"]["time_to_eps_s"])
     print(json.dumps(out), flush=True)
 
 
@@ -271,6 +281,10 @@ def main():
                          "batched MLMC (no CGV) at the same eps and level set; prints one JSON line")
     ap.add_argument("--bf16-arm", action="store_true",
                     help="with --compare: add the mixed CGV arm with BF16 multigrid faces (prec 2)")
+    ap.add_argument("--fp64cg-arm", action="store_true",
+                    help="with --compare: add the CGV arm with FP64 CG around an FP32 multigrid (prec 3)")
+    ap.add_argument("--prec", type=int, default=None, choices=[0, 1, 2, 3],
+                    help="override the workload's solver precision mode")
     args = ap.parse_args()
     if args.compare:
         compare(args)
@@ -278,6 +292,8 @@ def main():
 
     import workloads
     d = workloads.workload(args.workload)
+    if args.prec is not None:
+        d["prec"] = args.prec
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -360,28 +376,35 @@ def main():
     if stage_ms[dom] <= 0:
         raise RuntimeError("no stage timing collected in the timed region")
     launches = int(sum(prof["launches"].values()))
-    roof = None
-    if dom == "solve" and d["prec"] == 0:
-        # algorithmic flops counted by the library per level from its cycle (V/W, sweeps)
-        flops = prof["solve_flops"]
+    prec = d["prec"]
+    fp64_src = "nominal FP64 vector rate (152 SMs x 2 DFMA/clk x 2.06 GHz)"
+    fp32_src = "nominal FP32 vector rate (152 SMs x 128 FFMA/clk x 2.07 GHz)"
+    if dom == "solve":
+        # algorithmic flops counted by the library per level from its cycle (V/W, sweeps); with
+        # prec 3 only the FP64 CG part (23 per cell-iteration) is set against the FP64 peak
+        if prec == 0:
+            flops, peak, src, what = prof["solve_flops"], FP64_PEAK_TFLOPS, fp64_src, "FP64 MG-PCG"
+        elif prec == 3:
+            flops, peak, src, what = 23.0 * prof["cell_iters"], FP64_PEAK_TFLOPS, fp64_src, "FP64 CG part"
+        else:
+            flops, peak, src, what = prof["solve_flops"], FP32_PEAK_TFLOPS, fp32_src, "FP32 MG-PCG"
         ach = flops / (stage_ms["solve"] / 1e3) / 1e12
-        roof = {"kernel": "solve_kernel<false> (assembly + MG-PCG + QoI, FP64)", "bound": "alu",
-                "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": None, "peak_source": "nominal FP64 vector rate (152 SMs x 2 DFMA/clk x 2.06 GHz)"}
-    elif dom == "fields" and d["prec"] == 0:
-        # radix-2 FFT: 5 N log2 N flops per length-N transform
-        pts_r, pts_c = prof["fft_row_points"], prof["fft_col_points"]
-        M = ctx.ce_info(d["L"])[0]
-        lg = math.log2(M)
-        flops = 5 * (pts_r + pts_c) * lg
-        ach = flops / (stage_ms["fields"] / 1e3) / 1e12
-        roof = {"kernel": "ce_rows/ce_cols (Philox + Box-Muller + FFT, FP64)", "bound": "alu", "achieved": ach,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None}
+        roof = {"kernel": "solve_kernel<%d, mode> (assembly + MG-PCG + QoI; %s)" % (prec, what), "bound": "alu",
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "peak_source": src}
+    else:
+        # radix-2 FFT count, 5 log2(M) flops per point of each length-M transform, per level
+        f32 = prec in (1, 2)
+        peak = FP32_PEAK_TFLOPS if f32 else FP64_PEAK_TFLOPS
+        ach = prof["fft_flops"] / (stage_ms["fields"] / 1e3) / 1e12
+        roof = {"kernel": "ce_rows/ce_cols (Philox + Box-Muller + FFT, %s)" % ("FP32" if f32 else "FP64"),
+                "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "peak_source": fp32_src if f32 else fp64_src}
     out = {
         "metric": metric_name(d, args), "value": n_all / (total_ms / 1e3), "unit": "level-samples/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if d["prec"] == 0 else "f32+f64", "data": "synthetic (Philox4x64-10 streams)",
+        "dtype": "f64" if d["prec"] == 0 else "f64+f32-mg" if d["prec"] == 3 else "f32+f64", "data": "synthetic (Philox4x64-10 streams)",
         "config": config_block(args, d), "roofline": roof, "e2e": e2e, "gpu_launches": launches // 1,
         "clocks": clk, "time_to_eps_s": total_ms / args.steps / 1e3, "N_per_level": est["N"],
         "q_hat": est["q_hat"], "var_hat": est["var_hat"],

@@ -87,7 +87,10 @@ typedef struct mlmc_model {
                                      FP32 circulant-embedding FFT;
                                   2: as 1, with the multigrid preconditioner's face
                                      coefficients stored in BF16 on every level (the CG
-                                     operator and the FP64 residual keep FP32 faces) */
+                                     operator and the FP64 residual keep FP32 faces);
+                                  3: FP64 fields, faces, CG (flexible, Polak-Ribiere beta),
+                                     stopping test and QoI, with an FP32 multigrid
+                                     preconditioner (faces rounded to FP32) */
   double tol;                  /* stop when ||b - A x||_2 < tol ||b||_2 (Sec. 3.5 uses 1e-10) */
   int32_t max_it;              /* cap on CG iterations per solve (sum over refinement sweeps) */
   int32_t problem;             /* 0 or 2: Model Problem 2 of Sec. 3.4 (p = 1 / 0 at x1 = 0 / 1, no
@@ -318,8 +321,11 @@ typedef struct mlmc_profile_stats {
   double fft_col_points;   /* sum of m*M complex points transformed by the column pass */
   double samples;          /* samples processed */
   double solve_flops;      /* algorithmic flops of the CG iterations: per cell-iteration 21 for CG
-                              plus (2.25 + 18 nu) per finest cell for the multigrid cycle, times 4/3
-                              (V-cycle) or 2 (W-cycle) for the coarser grids */
+                              (23 with prec 3) plus (2.25 + 18 nu) per finest cell for the
+                              multigrid cycle, times 4/3 (V-cycle) or 2 (W-cycle) for the coarser
+                              grids; the cycle runs in FP32 with prec 1, 2, 3 */
+  double fft_flops;        /* 5 log2(M) flops per complex point of every length-M transform of the
+                              row and column passes (the radix-2 count), summed over levels */
 } mlmc_profile_stats;
 
 /* enable != 0: reset the counters and start collecting; 0: stop. */

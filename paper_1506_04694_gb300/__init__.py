@@ -59,7 +59,7 @@ class ProfileStats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64 * 3), ("ms", ctypes.c_double * 3),
                 ("cell_iters", ctypes.c_double), ("cells", ctypes.c_double),
                 ("fft_row_points", ctypes.c_double), ("fft_col_points", ctypes.c_double),
-                ("samples", ctypes.c_double), ("solve_flops", ctypes.c_double)]
+                ("samples", ctypes.c_double), ("solve_flops", ctypes.c_double), ("fft_flops", ctypes.c_double)]
 
 
 STAGES = ("fields", "solve", "reduce")
@@ -300,7 +300,8 @@ class Context:
         _check(lib().mlmc_profile_read(self._h, ctypes.byref(p)), allow_failed=False)
         return {"launches": dict(zip(STAGES, p.launches)), "ms": dict(zip(STAGES, p.ms)),
                 "cell_iters": p.cell_iters, "cells": p.cells, "fft_row_points": p.fft_row_points,
-                "fft_col_points": p.fft_col_points, "samples": p.samples, "solve_flops": p.solve_flops}
+                "fft_col_points": p.fft_col_points, "samples": p.samples, "solve_flops": p.solve_flops,
+                "fft_flops": p.fft_flops}
 
     def set_launch(self, level, mode, threads=256, cluster=0, gamma=1, nu=1):
         """mlmc_set_launch: fix a level's solver launch (0 block, 1 warp, 2 cluster; <0 default),

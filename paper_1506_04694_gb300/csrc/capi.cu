@@ -184,7 +184,7 @@ int check_model(const mlmc_model& md) {
   if (md.L < 0 || md.L >= MLMC_MAX_LEVELS) return fail(MLMC_ERR_ARG, "L must be 0..11");
   if ((int64_t)md.m0 << md.L > 4096) return fail(MLMC_ERR_TOOBIG, "m0 * 2^L must be <= 4096");
   if (md.cgv < 0 || md.cgv > 2) return fail(MLMC_ERR_ARG, "cgv must be 0, 1 or 2");
-  if (md.prec < 0 || md.prec > 2) return fail(MLMC_ERR_ARG, "prec must be 0, 1 or 2");
+  if (md.prec < 0 || md.prec > 3) return fail(MLMC_ERR_ARG, "prec must be 0, 1, 2 or 3");
   if (!(md.tol > 0) || md.max_it < 1) return fail(MLMC_ERR_ARG, "tol must be > 0 and max_it >= 1");
   if (!(md.if_hi >= md.if_lo)) return fail(MLMC_ERR_ARG, "if_hi must be >= if_lo");
   for (int t = 0; t < md.n_layers; ++t) {
@@ -247,11 +247,14 @@ SolveArgs base_args(const mlmc_ctx* c, int level, uint64_t seed, int64_t first) 
   return a;
 }
 
+// prec 1 and 2 sample the fields in FP32; prec 0 and 3 in FP64.
+static bool fields_f32(const mlmc_model& md) { return md.prec == 1 || md.prec == 2; }
+
 // Fields of chunk samples [first, first + n) of `level` into c->g.
 int run_fields(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t seed) {
   const mlmc_model& md = c->model;
   const LevelTable& LT = c->lev[level];
-  const bool f32 = md.prec != 0;
+  const bool f32 = fields_f32(md);
   if (int e = c->W.ensure(ce_w_bytes_per_sample(LT.m, max_M(c, level), f32) * n)) return e;
   if (int e = c->g.ensure((size_t)n * md.n_layers * LT.m * LT.m * (f32 ? 4 : 8))) return e;
   for (int f = 0; f < c->n_draws; ++f) {  // one draw at a time, W reused
@@ -285,7 +288,7 @@ int run_fields(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t seed) 
 int64_t chunk_samples(const mlmc_ctx* c, int level) {
   const mlmc_model& md = c->model;
   const int m = md.m0 << level;
-  const bool f32 = md.prec != 0;
+  const bool f32 = fields_f32(md);
   size_t per = (size_t)(1 + n_coarse(md, level)) * 12;
   if (md.k_kind == 1) {
     per += ce_w_bytes_per_sample(m, max_M(c, level), f32);
@@ -376,10 +379,11 @@ int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t see
   const SolvePlan* plan = c->tuned_ok[level] ? &c->tuned[level] : nullptr;
   CUDA_TRY(cudaMemsetAsync(itacc, 0, 2 * sizeof(int64_t), c->st));
   const int m = md.m0 << level;
-  double sumM2 = 0, sumM = 0;  // transformed points per sample over the draws
+  double sumM2 = 0, sumM = 0, fftf = 0;  // transformed points and FFT flops per sample over the draws
   for (const auto& T : c->lev[level].pair) {
     sumM2 += (double)T.M * T.M;
     sumM += (double)T.M;
+    fftf += 5.0 * std::log2((double)T.M) * ((double)T.M * T.M + (double)T.M * m);
   }
   for (int64_t c0 = 0; c0 < n; c0 += chunk) {
     const int64_t cn = std::min<int64_t>(chunk, n - c0);
@@ -392,6 +396,7 @@ int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t see
       if (c->prof_on) {
         c->prof.fft_row_points += (double)cn * sumM2;
         c->prof.fft_col_points += (double)cn * sumM * m;
+        c->prof.fft_flops += (double)cn * fftf;
       }
     }
     {
@@ -425,10 +430,11 @@ int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t see
 // p.q 2, x, r, r.r 6, r.z 2, p update 2; on the finest grid of the cycle a
 // zero-guess red half sweep 0.5, black 4.5, every further sweep pair 9, the
 // red-cell residual restriction 5.25, prolongation 1 and 9 per post-sweep
-// pair; coarser grids add 1/3 (V) or 1 (W) of that.
-double flops_per_cell_iter(int gamma, int nu) {
+// pair; coarser grids add 1/3 (V) or 1 (W) of that.  The flexible CG of
+// prec 3 adds the dot product r_new.z_old (2).
+double flops_per_cell_iter(int prec, int gamma, int nu) {
   const double fine = 2.25 + 18.0 * nu;
-  return 21.0 + fine * (gamma >= 2 ? 2.0 : 4.0 / 3.0);
+  return (prec == 3 ? 23.0 : 21.0) + fine * (gamma >= 2 ? 2.0 : 4.0 / 3.0);
 }
 
 // After the stream reached the copies of enqueue_level(): fill the sums.
@@ -439,7 +445,7 @@ int finish_level(mlmc_ctx* c, int level, const HostLevel& h, mlmc_level_sums* su
     SolvePlan P;
     if (c->tuned_ok[level]) P = c->tuned[level];
     else if (solve_plan(md.m0 << level, md.prec, &P)) P.gamma = P.nu = 1;
-    c->prof.solve_flops += (double)h.itc[1] * flops_per_cell_iter(P.gamma, P.nu);
+    c->prof.solve_flops += (double)h.itc[1] * flops_per_cell_iter(md.prec, P.gamma, P.nu);
   }
   sums->n = h.s.n;
   sums->n_failed = h.s.n_failed;
@@ -468,7 +474,7 @@ int level_batch_impl(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t 
 int prepare_level(mlmc_ctx* c, int level, int64_t n) {
   const mlmc_model& md = c->model;
   const int m = md.m0 << level;
-  const bool f32 = md.prec != 0;
+  const bool f32 = fields_f32(md);
   const int nc = n_coarse(md, level);
   const int64_t cn = std::min<int64_t>(n, chunk_samples(c, level));
   if (md.k_kind == 1) {
@@ -989,7 +995,7 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
         ++nk;
       }
     }
-    if (!err && best_k >= 0 && md.prec != 0) {  // mixed: looser or tighter FP32 inner solves
+    if (!err && best_k >= 0 && (md.prec == 1 || md.prec == 2)) {  // mixed: looser or tighter FP32 inner solves
       const SolvePlan base = cand[best_k];
       for (double it : {1e-4, 1e-6}) {
         if (err) break;
@@ -1083,7 +1089,7 @@ int mlmc_normals(mlmc_ctx* c, uint64_t seed, uint64_t level, uint64_t sample, ui
   if (!c || n_calls < 0 || (n_calls > 0 && !out)) return fail(MLMC_ERR_ARG, "bad argument");
   CUDA_TRY(cudaSetDevice(c->device));
   if (normals_launch(seed, level, sample, stream, first_call, n_calls, c->bm.as<double2>(),
-                     reinterpret_cast<const double*>(c->bm.as<double2>() + kSinCosTab), c->model.prec != 0,
+                     reinterpret_cast<const double*>(c->bm.as<double2>() + kSinCosTab), fields_f32(c->model),
                      out, c->st))
     return fail(MLMC_ERR_CUDA, "normals kernel");
   CUDA_TRY(cudaStreamSynchronize(c->st));
@@ -1105,7 +1111,7 @@ int mlmc_sample_fields(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_
   } else {
     if (int e = run_fields(c, level, first, n, seed)) return e;
     const int64_t cnt = n * md.n_layers * (int64_t)m * m;
-    if (md.prec)
+    if (fields_f32(md))
       f32_to_f64_launch(c->g.as<float>(), g, cnt, c->st);
     else
       CUDA_TRY(cudaMemcpyAsync(g, c->g.p, cnt * 8, cudaMemcpyDeviceToDevice, c->st));

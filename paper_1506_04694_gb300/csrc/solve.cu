@@ -25,6 +25,11 @@
 //         the FP32 faces; each multigrid level's diagonal is the sum of its
 //         own BF16 faces, so the preconditioner stays symmetric positive
 //         definite).
+// prec 3: FP64 faces, CG vectors, operator, dot products and stopping test;
+//         only the multigrid preconditioner runs in FP32 (its faces rounded
+//         from the FP64 ones, z = B (float) r widened to FP64).  The CG uses
+//         the Polak-Ribiere beta (flexible CG), which tolerates a
+//         preconditioner that is symmetric only to FP32 rounding.
 // Outflow QoI M^(2) (Sec. 3.4): Q = sum_j T(m, j) p(m-1, j).
 #include <algorithm>
 #include <cmath>
@@ -54,23 +59,22 @@ __host__ __device__ __forceinline__ size_t align16(size_t v) { return (v + 15) &
 __host__ __device__ inline size_t ws_layout(int m, int prec) {
   const size_t ts = prec ? 4 : 8, fs = prec == 2 ? 2 : ts;
   size_t o = 0;
-  const size_t n = (size_t)m * m;
+  const size_t n = (size_t)m * m, nf0 = (size_t)m * (m + 1);
   auto take = [&](size_t bytes) { o += align16(bytes); };
-  if (prec) {
-    take(n * 8);
-    take(n * 8);
-  }
-  if (prec == 2) {
-    take((size_t)m * (m + 1) * 4);
-    take((size_t)m * (m + 1) * 4);
-    take(n * 4);
+  if (prec)  // x64, r64 (prec 3 also p64, q64, z64)
+    for (int v = 0; v < (prec == 3 ? 5 : 2); ++v) take(n * 8);
+  if (prec >= 2) {  // the CG operator's own faces and diagonal (FP32, or FP64 with prec 3)
+    const size_t os = prec == 3 ? 8 : 4;
+    take(nf0 * os);
+    take(nf0 * os);
+    take(n * os);
   }
   for (int ml = m, l = 0;; ml >>= 1, ++l) {
     const size_t nl = (size_t)ml * ml, nf = (size_t)ml * (ml + 1);
     take(nf * fs);
     take(nf * fs);
     for (int a = 0; a < 4; ++a) take(nl * ts);
-    if (l == 0)
+    if (l == 0 && prec != 3)
       for (int b = 0; b < 3; ++b) take(nl * ts);
     if (ml == 1) break;
   }
@@ -459,6 +463,91 @@ __device__ int pcg(const G& g, const Level<T>& A, const Level<T, F>* lev, int nl
   return it;
 }
 
+// prec 3: CG in FP64 on the FP64 operator A with the FP32 multigrid
+// preconditioner on lev: z = (double) B (float) r.  r = rhs on entry, x = 0
+// is set here.  beta = r_new.(z_new - z_old) / r_old.z_old (Polak-Ribiere,
+// the flexible-CG form), so the preconditioner's FP32 rounding (a slightly
+// varying, slightly unsymmetric B) does not stall the iteration.  Stops when
+// r.r <= thr; status 0 converged, 1 cap, 2 breakdown.
+template <typename G>
+__device__ int pcg64_mg32(const G& g, const Level<double>& A, const Level<float>* lev, int nl, int gamma, int nu,
+                          double* __restrict__ x, double* __restrict__ r, double* __restrict__ p,
+                          double* __restrict__ q, double* __restrict__ z, double thr, int max_it, double* red,
+                          int& par, int& status) {
+  const Level<float>& L0 = lev[0];
+  const int m = A.m, n = m * m;
+  const int step = g.size();
+  double rr = 0.0;
+  for (int c = g.rank(); c < n; c += step) {
+    x[c] = 0.0;
+    const double rv = r[c];
+    L0.f[c] = (float)rv;
+    rr += rv * rv;
+  }
+  rr = g.sum(rr, red, par);
+  status = 1;
+  if (rr <= thr) {
+    status = 0;
+    return 0;
+  }
+  g.sync();
+  precond(g, lev, nl, gamma, nu);
+  double rz = 0.0;
+  for (int c = g.rank(); c < n; c += step) {
+    const double zv = (double)L0.e[c];
+    z[c] = zv;
+    p[c] = zv;
+    rz += r[c] * zv;
+  }
+  rz = g.sum(rz, red, par);
+  int it = 0;
+  while (it < max_it) {
+    ++it;
+    double pq = 0.0;
+    for (int c = g.rank(); c < n; c += step) {
+      const int j = c / m, i = c - j * m;
+      const double v = apply_row(A, p, i, j);
+      q[c] = v;
+      pq += p[c] * v;
+    }
+    pq = g.sum(pq, red, par);
+    if (!(pq > 0.0) || !isfinite(pq) || !(rz > 0.0) || !isfinite(rz)) {
+      status = 2;
+      break;
+    }
+    const double alpha = rz / pq;
+    rr = 0.0;
+    double rzo = 0.0;  // r_new . z_old
+    for (int c = g.rank(); c < n; c += step) {
+      x[c] += alpha * p[c];
+      const double rv = r[c] - alpha * q[c];
+      r[c] = rv;
+      L0.f[c] = (float)rv;
+      rr += rv * rv;
+      rzo += rv * z[c];
+    }
+    rr = g.sum(rr, red, par);
+    rzo = g.sum(rzo, red, par);
+    if (rr <= thr) {
+      status = 0;
+      break;
+    }
+    precond(g, lev, nl, gamma, nu);
+    double rzn = 0.0;
+    for (int c = g.rank(); c < n; c += step) {
+      const double zv = (double)L0.e[c];
+      z[c] = zv;
+      rzn += r[c] * zv;
+    }
+    rzn = g.sum(rzn, red, par);
+    const double beta = (rzn - rzo) / rz;
+    rz = rzn;
+    for (int c = g.rank(); c < n; c += step) p[c] = z[c] + beta * p[c];
+    g.sync();
+  }
+  return it;
+}
+
 __device__ __forceinline__ int layer_at(const double* eta, int n_if, double y) {
   int t = 0;
   for (int s = 0; s < n_if; ++s) t += (eta[s] <= y) ? 1 : 0;
@@ -524,8 +613,9 @@ template <typename T, typename F>
 struct GroupState {
   Level<T, F> lev[kMaxLevels];
   Level<T> op;
+  Level<double> op64;  // prec 3: the FP64 CG operator
   T *xv, *pv, *qv;
-  double *x64, *r64;
+  double *x64, *r64, *p64, *q64, *z64;
   double eta[MAX_LAYERS_DEV], kc[MAX_LAYERS_DEV];
   int nl;
 };
@@ -549,7 +639,7 @@ __device__ __forceinline__ const Level<T>& cg_operator(const GroupState<T, F>& g
 
 template <int PREC>
 struct SolverTypes {
-  using T = typename std::conditional<PREC != 0, float, double>::type;       // arithmetic
+  using T = typename std::conditional<PREC != 0, float, double>::type;       // arithmetic (multigrid)
   using F = typename std::conditional<PREC == 2, __nv_bfloat16, T>::type;  // multigrid faces
 };
 
@@ -560,7 +650,8 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
                           typename SolverTypes<PREC>::T* red, double* red64, int& par, int& m_prev) {
   using T = typename SolverTypes<PREC>::T;
   using F = typename SolverTypes<PREC>::F;
-  constexpr bool MIXED = PREC != 0;
+  using TF = typename std::conditional<PREC == 3, double, T>::type;  // face assembly
+  constexpr bool REFINE = PREC == 1 || PREC == 2;                    // FP32 CG in FP64 refinement
   int64_t sidx;
   int coarse = 0, ox = 0, oy = 0;
   if (sys < a.n_samples) {
@@ -587,9 +678,20 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
         o += align16(bytes);
         return p;
       };
-      if (MIXED) {
+      if (PREC != 0) {
         gs.x64 = reinterpret_cast<double*>(take(n0 * 8));
         gs.r64 = reinterpret_cast<double*>(take(n0 * 8));
+      }
+      if (PREC == 3) {
+        const size_t nf0 = (size_t)m * (m + 1);
+        gs.p64 = reinterpret_cast<double*>(take(n0 * 8));
+        gs.q64 = reinterpret_cast<double*>(take(n0 * 8));
+        gs.z64 = reinterpret_cast<double*>(take(n0 * 8));
+        gs.op64.m = m;
+        gs.op64.tx = reinterpret_cast<double*>(take(nf0 * 8));
+        gs.op64.ty = reinterpret_cast<double*>(take(nf0 * 8));
+        gs.op64.diag = reinterpret_cast<double*>(take(n0 * 8));
+        gs.op64.invd = nullptr;
       }
       if (PREC == 2) {
         const size_t nf0 = (size_t)m * (m + 1);
@@ -609,7 +711,7 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
         L.invd = reinterpret_cast<T*>(take(nlv * sizeof(T)));
         L.e = reinterpret_cast<T*>(take(nlv * sizeof(T)));
         L.f = reinterpret_cast<T*>(take(nlv * sizeof(T)));
-        if (l == 0) {
+        if (l == 0 && PREC != 3) {
           gs.xv = reinterpret_cast<T*>(take(nlv * sizeof(T)));
           gs.pv = reinterpret_cast<T*>(take(nlv * sizeof(T)));
           gs.qv = reinterpret_cast<T*>(take(nlv * sizeof(T)));
@@ -620,7 +722,7 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
       gs.op.m = m;
       gs.op.e = gs.lev[0].e;
       gs.op.f = gs.lev[0].f;
-      if (!MIXED) {
+      if (PREC == 0) {
         gs.x64 = reinterpret_cast<double*>(gs.xv);
         gs.r64 = reinterpret_cast<double*>(gs.lev[0].f);
       }
@@ -659,7 +761,7 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
       const int t = layer_at_point(a.geometry, gs.eta, n_if, xc, yc);
       if (a.ksrc == KSRC_CONST) {
         kk = gs.kc[t];
-      } else if (MIXED) {
+      } else if (REFINE) {
         const float* gf = reinterpret_cast<const float*>(a.g);
         kk = (double)expf(gf[((sidx * a.n_layers + t) * (int64_t)a.m + jf) * a.m + iff]);
       } else {
@@ -676,31 +778,34 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
     for (int t = g.rank(); t < 2 * nfx; t += g.size()) {
       if (t < nfx) {
         const int j = t / (m + 1), ip = t - j * (m + 1);
-        T v;
-        if (ip == 0) v = T(2) * (T)r64[j * m];
-        else if (ip == m) v = T(2) * (T)r64[j * m + m - 1];
+        TF v;
+        if (ip == 0) v = TF(2) * (TF)r64[j * m];
+        else if (ip == m) v = TF(2) * (TF)r64[j * m + m - 1];
         else {
-          const T ka = (T)r64[j * m + ip - 1], kb = (T)r64[j * m + ip];
-          v = T(2) * ka * kb / (ka + kb);
+          const TF ka = (TF)r64[j * m + ip - 1], kb = (TF)r64[j * m + ip];
+          v = TF(2) * ka * kb / (ka + kb);
         }
-        A.tx[t] = v;
-        if (PREC == 2) L0.tx[t] = face_st<F>(v);
+        A.tx[t] = (T)v;
+        if (PREC == 2) L0.tx[t] = face_st<F>((T)v);
+        if (PREC == 3) gs.op64.tx[t] = (double)v;
       } else {
         const int u = t - nfx;
         const int jp = u / m, i = u - jp * m;
-        T v = T(0);
+        TF v = TF(0);
         if (jp > 0 && jp < m) {
-          const T ka = (T)r64[(jp - 1) * m + i], kb = (T)r64[jp * m + i];
-          v = T(2) * ka * kb / (ka + kb);
+          const TF ka = (TF)r64[(jp - 1) * m + i], kb = (TF)r64[jp * m + i];
+          v = TF(2) * ka * kb / (ka + kb);
         } else if (a.problem == 1) {  // Dirichlet p = 0 half a cell away
-          v = T(2) * (T)r64[(jp == 0 ? 0 : m - 1) * m + i];
+          v = TF(2) * (TF)r64[(jp == 0 ? 0 : m - 1) * m + i];
         }
-        A.ty[u] = v;
-        if (PREC == 2) L0.ty[u] = face_st<F>(v);
+        A.ty[u] = (T)v;
+        if (PREC == 2) L0.ty[u] = face_st<F>((T)v);
+        if (PREC == 3) gs.op64.ty[u] = (double)v;
       }
     }
     g.sync();
     if (PREC == 2) build_diag<false>(g, A);
+    if (PREC == 3) build_diag<false>(g, gs.op64);
     build_diag<true>(g, L0);
   }
   for (int l = 1; l < nl; ++l) {
@@ -709,7 +814,20 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
   }
   // ---- solve ----
   int status = 1, iters = 0;
-  if (!MIXED) {
+  if constexpr (PREC == 3) {
+    const Level<double>& A64 = gs.op64;
+    double bb = 0.0;
+    const double fmid = 1.0 / ((double)m * (double)m);  // Model Problem 1: f / m^2
+    for (int c = g.rank(); c < n; c += g.size()) {
+      const int j = c / m, i = c - j * m;
+      const double bv = a.problem == 1 ? fmid : (i == 0 ? A64.tx[j * (m + 1)] : 0.0);
+      r64[c] = bv;
+      bb += bv * bv;
+    }
+    bb = g.sum(bb, red64, par);
+    iters = pcg64_mg32(g, A64, lev, nl, a.mg_gamma, a.mg_nu, x64, r64, gs.p64, gs.q64, gs.z64,
+                       a.tol * a.tol * bb, a.max_it, red64, par, status);
+  } else if (PREC == 0) {
     // r = b, bb = b.b; stop at r.r <= tol^2 b.b
     T bb = T(0);
     const T fmid = (T)(1.0 / ((double)m * (double)m));  // Model Problem 1: f / m^2
@@ -801,7 +919,10 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
     }
   } else {
     // M^(2): outflow through x1 = 1
-    for (int j = g.rank(); j < m; j += g.size()) qsum += (double)A.tx[j * (m + 1) + m] * x64[j * m + m - 1];
+    for (int j = g.rank(); j < m; j += g.size()) {
+      const double te = PREC == 3 ? gs.op64.tx[j * (m + 1) + m] : (double)A.tx[j * (m + 1) + m];
+      qsum += te * x64[j * m + m - 1];
+    }
   }
   qsum = g.sum(qsum, red64, par);
   if (g.rank() == 0) {
@@ -907,6 +1028,7 @@ static int plan_fill_mode(int m, int mode, int threads, int cluster, SolvePlan* 
 }
 
 static int plan_fill(int m, int prec, int mode, int threads, int cluster, SolvePlan* P) {
+  if (prec == 3) return plan_fill_mode<3>(m, mode, threads, cluster, P);
   if (prec == 2) return plan_fill_mode<2>(m, mode, threads, cluster, P);
   if (prec == 1) return plan_fill_mode<1>(m, mode, threads, cluster, P);
   return plan_fill_mode<0>(m, mode, threads, cluster, P);
@@ -985,12 +1107,16 @@ int solve_launch(const SolveArgs& a, int prec, const SolvePlan& P, int n_blocks,
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const cudaError_t e = prec == 2   ? cudaLaunchKernelEx(&cfg, solve_kernel<2, 2>, b)
+    const cudaError_t e = prec == 3   ? cudaLaunchKernelEx(&cfg, solve_kernel<3, 2>, b)
+                          : prec == 2 ? cudaLaunchKernelEx(&cfg, solve_kernel<2, 2>, b)
                           : prec == 1 ? cudaLaunchKernelEx(&cfg, solve_kernel<1, 2>, b)
                                       : cudaLaunchKernelEx(&cfg, solve_kernel<0, 2>, b);
     return e == cudaSuccess ? 0 : -1;
   }
-  if (prec == 2) {
+  if (prec == 3) {
+    if (P.warp) solve_kernel<3, 1><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+    else solve_kernel<3, 0><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+  } else if (prec == 2) {
     if (P.warp) solve_kernel<2, 1><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
     else solve_kernel<2, 0><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
   } else if (prec == 1) {
@@ -1100,7 +1226,7 @@ extern "C" int mlmc_solve_k_static(int device, int32_t m, int64_t n, const doubl
   using namespace mlmc;
   if (device < 0 || device >= kMaxDevices || !k || !q || n < 0) return MLMC_ERR_ARG;
   if (m < 1 || m > 4096 || (m & (m - 1))) return MLMC_ERR_ARG;
-  if (!(tol > 0) || max_it < 1 || prec < 0 || prec > 2) return MLMC_ERR_ARG;
+  if (!(tol > 0) || max_it < 1 || prec < 0 || prec > 3) return MLMC_ERR_ARG;
   if (n == 0) return MLMC_OK;
   int prev = -1;
   if (cudaGetDevice(&prev) != cudaSuccess) return MLMC_ERR_NODEV;

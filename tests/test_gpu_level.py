@@ -81,6 +81,18 @@ def test_four_layers_mixed():
     check_against_oracle(d, 1, 8, seed=3, first=0, rtol=RTOL_MIX)
 
 
+@pytest.mark.parametrize("cgv,level,n", [(0, 0, 40), (0, 1, 20), (0, 3, 6), (1, 1, 12), (1, 2, 6)])
+def test_fp64_cg_fp32_multigrid(cgv, level, n):
+    # prec 3: FP64 fields, operator and CG with an FP32 multigrid
+    # preconditioner reach the FP64 path's agreement with the oracle
+    d = workloads.workload("lognormal_2layer_cgv_16to512", prec=3, cgv=cgv, tol=1e-12)
+    _, qf3, qc3, _, it3 = check_against_oracle(d, level, n, seed=6, first=0, rtol=RTOL64)
+    torch, pk = need_gpu()
+    _, qf0, qc0, _, it0 = run_gpu(pk, torch, dict(d, prec=0), level, n, 6)
+    np.testing.assert_allclose(qf3, qf0, rtol=1e-10, atol=0)
+    assert it3.sum() <= 1.3 * it0.sum() + n
+
+
 @pytest.mark.parametrize("level,n", [(0, 20), (1, 8), (2, 4)])
 def test_bf16_faces_in_multigrid(level, n):
     # prec 2: BF16 faces only inside the multigrid preconditioner; the FP64
@@ -95,15 +107,15 @@ def test_bf16_faces_in_multigrid(level, n):
     assert it2.sum() <= 1.5 * it1.sum() + n
 
 
-@pytest.mark.parametrize("tol,rtol", [(1e-13, RTOL64), (1e-10, 1e-7)])
-def test_full_size_sampled_fp64(tol, rtol):
+@pytest.mark.parametrize("tol,rtol,prec", [(1e-13, RTOL64, 0), (1e-10, 1e-7, 0), (1e-13, RTOL64, 3)])
+def test_full_size_sampled_fp64(tol, rtol, prec):
     # the benchmark's finest level (m = 256, M = 1024) in the launch the
     # benchmark uses (a large batch); sampled outputs checked one by one.
     # With the paper's stopping rule (||r||/||r0|| < 1e-10) the algebraic error
     # of Q is ~1e-8; with 1e-13 the FP64 path agrees with the direct solve to
     # 1e-10.
     torch, pk = need_gpu()
-    d = workloads.workload("lognormal_2layer_16to256", tol=tol)
+    d = workloads.workload("lognormal_2layer_16to256", tol=tol, prec=prec)
     model = darcy.Model.from_dict(d)
     n = 400
     s, qf, qc, qg, it = run_gpu(pk, torch, d, 4, n, seed=0)
@@ -272,7 +284,7 @@ def test_nan_permeability_reported_as_failure():
     assert np.isnan(q[2]) and np.all(np.isfinite(q[[0, 1, 3]]))
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_launch_modes_agree(prec):
     # one system per block (64..512 threads), per warp, or per thread-block
     # cluster of 2/4/8 blocks, with V- or W-cycles and one or two smoothing
@@ -294,7 +306,7 @@ def test_launch_modes_agree(prec):
             s = ctx.level_batch(level, n, 4, qf=qf, qc_cgv=qg)
             assert s["n"] == n and s["n_failed"] == 0, (mode, threads, cl, gamma, nu)
             res.append((qf.cpu().numpy(), qg.cpu().numpy()))
-    tol = 1e-10 if prec == 0 else RTOL_MIX
+    tol = 1e-10 if prec in (0, 3) else RTOL_MIX
     for qf, qg in res[1:]:
         np.testing.assert_allclose(qf, res[0][0], rtol=tol, atol=0)
         np.testing.assert_allclose(qg, res[0][1], rtol=tol, atol=0)
@@ -305,13 +317,13 @@ def test_launch_modes_agree(prec):
 
 
 @pytest.mark.parametrize("prec,cgv,level,n", [(0, 0, 0, 30), (0, 0, 2, 6), (0, 1, 1, 10), (1, 1, 2, 6),
-                                              (2, 1, 2, 6)])
+                                              (2, 1, 2, 6), (3, 1, 2, 6)])
 def test_model_problem_1(prec, cgv, level, n):
     # Sec. 3.4 Model Problem 1: f = 1, p = 0 on the whole boundary, Q = mean of p
     # over D* = [7/16, 9/16]^2, plain and CGV coupling, FP64 and mixed
     d = workloads.workload("lognormal_2layer_cgv_16to512", problem=1, prec=prec, cgv=cgv,
-                           tol=1e-12 if prec == 0 else 1e-10)
-    check_against_oracle(d, level, n, seed=13, first=0, rtol=RTOL64 if prec == 0 else RTOL_MIX)
+                           tol=1e-12 if prec in (0, 3) else 1e-10)
+    check_against_oracle(d, level, n, seed=13, first=0, rtol=RTOL64 if prec in (0, 3) else RTOL_MIX)
 
 
 def test_model_problem_1_box_and_solve_k():

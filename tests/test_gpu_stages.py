@@ -120,18 +120,21 @@ def test_solve_k_fp64(m):
     assert it.max() < 100
 
 
-@pytest.mark.parametrize("m,prec", [(16, 1), (64, 1), (256, 1), (16, 2), (64, 2), (256, 2)])
+@pytest.mark.parametrize("m,prec", [(16, 1), (64, 1), (256, 1), (16, 2), (64, 2), (256, 2), (16, 3), (64, 3),
+                                    (256, 3)])
 def test_solve_k_mixed(m, prec):
     torch, pk = need_gpu()
     n = 6
     k = workloads.random_k(m, seed=100 + m, n=n, contrast=4.0)
-    d = workloads.workload("const_2layer_8to32", tol=1e-12, max_it=1000, prec=prec)
+    # these log-normal k with layer jumps are ill-conditioned: a relative
+    # residual of 1e-12 leaves Q errors up to ~7e-10, 1e-13 below 1e-10
+    d = workloads.workload("const_2layer_8to32", tol=1e-13 if prec == 3 else 1e-12, max_it=1000, prec=prec)
     with pk.Context(d) as ctx:
         _, q, it = ctx.solve_k(torch.from_numpy(k).cuda(), want_p=False)
         q = q.cpu().numpy()
     for s in range(n):
         _, q_ref = darcy.solve_k(k[s])
-        assert abs(q[s] - q_ref) <= 1e-6 * abs(q_ref), (s, q[s], q_ref)
+        assert abs(q[s] - q_ref) <= (1e-10 if prec == 3 else 1e-6) * abs(q_ref), (s, q[s], q_ref)
 
 
 def test_constant_k_closed_form_gpu():

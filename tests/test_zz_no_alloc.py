@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 RTOL = 1e-10
 
 
-@pytest.mark.parametrize("m,prec", [(16, 0), (64, 0), (128, 0), (256, 0), (128, 1), (128, 2)])
+@pytest.mark.parametrize("m,prec", [(16, 0), (64, 0), (128, 0), (256, 0), (128, 1), (128, 2), (128, 3)])
 def test_static_scratch_matches_context_solve(m, prec):
     torch, pk = need_gpu()
     n = 24 if m <= 64 else 6
