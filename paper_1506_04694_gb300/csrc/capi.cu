@@ -635,7 +635,7 @@ int mlmc_create(int device, const mlmc_model* model, void* cuda_stream, mlmc_ctx
     delete c;
     return fail(MLMC_ERR_NOMEM, "pinned host buffer");
   }
-  if ((err = c->bm.ensure(kSinCosTab * sizeof(double2) + 3 * kLogTab * sizeof(double))) == 0 &&
+  if ((err = c->bm.ensure(kSinCosTab * sizeof(double2) + kBmLgDoubles * sizeof(double))) == 0 &&
       bm_tables_build(c->bm.as<double2>(), reinterpret_cast<double*>(c->bm.as<double2>() + kSinCosTab),
                       c->st))
     err = fail(MLMC_ERR_CUDA, "Box-Muller table kernel");

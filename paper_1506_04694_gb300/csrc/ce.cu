@@ -317,9 +317,10 @@ __global__ void bm_tables_kernel(double2* sc, double* lg) {
   if (i < kLogTab) {
     const double F = 0.5 + ((double)i + 0.5) / 2048.0;
     lg[3 * i] = F;
-    lg[3 * i + 1] = 1.0 / F;
-    lg[3 * i + 2] = log(F);
+    lg[3 * i + 1] = -2.0 / F;
+    lg[3 * i + 2] = -2.0 * log(F);
   }
+  if (i < kLogExpTab) lg[3 * kLogTab + i] = -2.0 * log(ldexp(1.0, -i));  // 2 i ln 2
 }
 
 int bm_tables_build(double2* sc, double* lg, cudaStream_t st) {

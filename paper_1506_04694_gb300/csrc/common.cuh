@@ -97,69 +97,76 @@ __device__ __forceinline__ void box_muller_words(uint64_t wa, uint64_t wb, float
 }
 
 // ------------------------------------------- table-driven FP64 Box-Muller --
-// FP64 log and sincos(2 pi u) by table-driven argument reduction (the method
-// of P. T. P. Tang, "Table-driven implementation of the logarithm function
-// in IEEE floating-point arithmetic", ACM TOMS 16 (1990), and the analogous
-// reduction for the trigonometric functions), with Taylor polynomials on the
-// reduced interval.  Tables hold exact-argument values from the CUDA math
-// library, computed once per context (bm_tables_kernel):
+// FP64 -2 ln u and (cos, sin)(2 pi u) by table-driven argument reduction (the
+// method of P. T. P. Tang, "Table-driven implementation of the logarithm
+// function in IEEE floating-point arithmetic", ACM TOMS 16 (1990), and the
+// analogous reduction for the trigonometric functions), with Taylor
+// polynomials on the reduced interval, working from the integer K = w >> 12
+// of u = (K + 1/2) 2^-52 = (2K + 1) 2^-53 so that no integer-to-FP64
+// conversion and no scaling of u is needed.  Tables hold exact-argument
+// values from the CUDA math library, computed once per context
+// (bm_tables_kernel):
 //   sc[j] = (cos(2 pi j/1024), sin(2 pi j/1024)), j < 1024;
-//   lg[3t .. 3t+2] = (F_t, 1/F_t, ln F_t), F_t = 1/2 + (t + 1/2)/2048, t < 1024.
+//   lg[3t .. 3t+2] = (F_t, -2/F_t, -2 ln F_t), F_t = 1/2 + (t + 1/2)/2048,
+//     t < 1024;
+//   lg[3072 + e] = 2 e ln 2, e = 0 .. 52.
 constexpr int kSinCosTab = 1024;
 constexpr int kLogTab = 1024;
+constexpr int kLogExpTab = 53;
+constexpr int kBmLgDoubles = 3 * kLogTab + kLogExpTab;
 
 struct BmTables {
   const double2* sc;
   const double* lg;
 };
 
-// ln u for u in (0, 1): u = 2^E v, v in [1/2, 1), v = F_t (1 + r) with
-// |r| <= 1/2048 and ln(1 + r) from its Taylor series to r^4 (truncation
-// < 6e-18).  r = (v - F_t) / F_t is formed as the exact difference times the
-// rounded reciprocal, so the absolute error stays ~1e-19 near u = 1.
-__device__ __forceinline__ double tab_log01(double u, const double* __restrict__ lg) {
-  const long long bits = __double_as_longlong(u);
-  const int ex = (int)(bits >> 52);
-  const long long mant = bits & ((1LL << 52) - 1);
-  const int E = ex - 1022;
-  const double v = __longlong_as_double(mant | (1022LL << 52));
-  const int t = (int)(mant >> 42);
-  const double F = __ldg(lg + 3 * t), iF = __ldg(lg + 3 * t + 1), lF = __ldg(lg + 3 * t + 2);
-  const double r = (v - F) * iF;
-  double p = fma(-0.25, r, 1.0 / 3.0);
-  p = fma(p, r, -0.5);
-  const double l1 = fma(p, r * r, r);
-  return fma((double)E, 0.6931471805599453, lF + l1);
+// -2 ln u for u = (2K + 1) 2^-53 (K < 2^52): N = 2K + 1 = v 2^(53 - e) with
+// v in [1/2, 1) read off the bits of N (e = 0 .. 52); v = F_t (1 + r),
+// |r| <= 1/2048; with s = -2 r, -2 ln(1 + r) = s + s^2/4 + s^3/12 + s^4/32
+// (truncation |s|^5/80 < 1.2e-17), so -2 ln u = 2 e ln 2 - 2 ln F_t + that.
+// s = (v - F_t)(-2/F_t) is the exact difference times the rounded factor, so
+// the absolute error stays ~1e-19 near u = 1.
+__device__ __forceinline__ double tab_m2log(uint64_t K, const double* __restrict__ lg) {
+  const uint64_t N = 2 * K + 1;
+  const int lz = __clzll((long long)N);  // 11 .. 63
+  const uint64_t Nn = N << lz;            // leading one at bit 63; the low lz bits are zero
+  const int e = lz - 11;
+  const double v = __longlong_as_double((long long)((1022ull << 52) | ((Nn >> 11) & ((1ull << 52) - 1))));
+  const int t = (int)((Nn >> 53) & (kLogTab - 1));
+  const double F = __ldg(lg + 3 * t), m2iF = __ldg(lg + 3 * t + 1), m2lF = __ldg(lg + 3 * t + 2);
+  const double sv = (v - F) * m2iF;
+  double q = fma(sv, 1.0 / 32.0, 1.0 / 12.0);
+  q = fma(q, sv, 0.25);
+  const double l1 = fma(q, sv * sv, sv);
+  return __ldg(lg + 3 * kLogTab + e) + (m2lF + l1);
 }
 
-// (cos 2 pi u, sin 2 pi u) for u = ((w >> 12) + 1/2) 2^-52: u = j/1024 + b
-// with the nearest j (integer arithmetic on w, exact), theta = 2 pi b,
-// |theta| <= pi/1024, Taylor polynomials to theta^5 (truncation < 3e-18),
-// then the angle-addition formulas with the tabulated (cos, sin).
-__device__ __forceinline__ void tab_sincos2pi(uint64_t w, const double2* __restrict__ sc, double& c,
-                                              double& s) {
+// r (cos 2 pi u, sin 2 pi u) for u = (2K + 1) 2^-53, K = w >> 12: u = j/1024
+// + b with the nearest j (integer arithmetic, exact), theta = 2 pi b =
+// (2D + 1) pi 2^-52 with |theta| <= pi/1024 (2D + 1 is exact in FP64),
+// Taylor polynomials to theta^5 (truncation < 3e-18), then the
+// angle-addition formulas with the tabulated (cos, sin) scaled by r.
+__device__ __forceinline__ void tab_polar(uint64_t w, double r, const double2* __restrict__ sc, double& x,
+                                          double& y) {
   const long long K = (long long)(w >> 12);
   const long long j = (K + (1LL << 41)) >> 42;
   const long long D = K - (j << 42);
-  const double b = ((double)D + 0.5) * 0x1p-52;
-  const double th = b * 6.283185307179586;
+  const double th = (double)(2 * D + 1) * 0x1.921fb54442d18p-51;  // pi 2^-52
   const double t2 = th * th;
-  const double cm = t2 * fma(t2, 1.0 / 24.0, -0.5);              // cos(theta) - 1
+  const double cm = t2 * fma(t2, 1.0 / 24.0, -0.5);                      // cos(theta) - 1
   const double sn = fma(th * t2, fma(t2, 1.0 / 120.0, -1.0 / 6.0), th);  // sin(theta)
   const double2 cs = __ldg(sc + (j & (kSinCosTab - 1)));
-  c = cs.x + fma(cs.x, cm, -cs.y * sn);
-  s = cs.y + fma(cs.y, cm, cs.x * sn);
+  const double rc = r * cs.x, rs = r * cs.y;
+  x = fma(rc, cm, fma(-rs, sn, rc));
+  y = fma(rs, cm, fma(rc, sn, rs));
 }
 
 // Box-Muller pair from two words (same definition as box_muller()), each
 // normal times `scale` (folded into the radius).
 __device__ __forceinline__ void box_muller_tab(uint64_t wa, uint64_t wb, const BmTables& tb, double& re,
                                                double& im, double scale = 1.0) {
-  const double rad = sqrt(-2.0 * tab_log01(uniform52(wa), tb.lg)) * scale;
-  double c, s;
-  tab_sincos2pi(wb, tb.sc, c, s);
-  re = rad * c;
-  im = rad * s;
+  const double rad = sqrt(tab_m2log(wa >> 12, tb.lg)) * scale;
+  tab_polar(wb, rad, tb.sc, re, im);
 }
 
 __device__ __forceinline__ void box_muller_tab(uint64_t wa, uint64_t wb, const BmTables&, float& re,

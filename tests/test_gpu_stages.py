@@ -37,12 +37,14 @@ def test_normals_against_oracle(prec, atol):
     err = np.abs(z - ref)
     assert err.max() <= atol * max(1.0, np.abs(ref).max()), err.max()
     if prec == 0:
-        # the log part on its own: re^2 + im^2 = -2 ln u_a to ~1e-15 relative,
-        # ~1e-18 absolute as u_a -> 1 (the normal's absolute error stays ~1e-16)
+        # the log part on its own: re^2 + im^2 = -2 ln u_a to a few ulp
+        # (re, im within ~2 ulp of r cos, r sin each, plus the two roundings
+        # of the sum of squares here: <= 9 ulp = 2e-15 relative), and ~1e-18
+        # absolute as u_a -> 1, where -2 ln u_a cancels in its table form
         u = philox.uniform(philox.stream_words(77, 3, 5, 2, np.arange(n, dtype=np.uint64)))
         r2 = z[:, 0] ** 2 + z[:, 1] ** 2
         ref2 = -2.0 * np.log(u[:, 0])
-        assert np.all(np.abs(r2 - ref2) <= 1e-15 * ref2 + 1e-18)
+        assert np.all(np.abs(r2 - ref2) <= 2e-15 * ref2 + 1e-18)
 
 
 @pytest.mark.parametrize("name", ["const_2layer_8to32", "lognormal_4layer_cgv_16to1024"])
