@@ -214,7 +214,8 @@ typedef struct mlmc_tune_report {
   int32_t cap_blocks_per_sm[MLMC_MAX_LEVELS];  /* 0: occupancy limit */
   int32_t cluster[MLMC_MAX_LEVELS];            /* > 0: blocks of the cluster that solves one system */
   int32_t gamma[MLMC_MAX_LEVELS];              /* multigrid cycle: 1 V, 2 W */
-  int32_t nu[MLMC_MAX_LEVELS];                 /* red-black sweep pairs per smoothing */
+  int32_t nu[MLMC_MAX_LEVELS];                 /* red-black sweep pairs per smoothing, finest grid */
+  int32_t nu_coarse[MLMC_MAX_LEVELS];          /* the same on the coarser grids */
   double inner_tol[MLMC_MAX_LEVELS];           /* prec 1, 2: relative tolerance of the FP32 inner solves */
   int32_t candidates[MLMC_MAX_LEVELS];         /* plans timed */
   double ms_default[MLMC_MAX_LEVELS];          /* ms per sample, default plan */
@@ -224,12 +225,14 @@ typedef struct mlmc_tune_report {
 /* Times the candidate launch plans of the solver (one warp, one block of
  * 64/128/256/512 threads, or, for m >= 128, one thread-block cluster of 2, 4
  * or 8 blocks per system; all resident blocks or one per SM; for the
- * fastest of those, W-cycles or two smoothing sweep pairs, and with mixed
- * precision an FP32 inner tolerance of 1e-4, 1e-5 or 1e-6) on a
- * probe batch of each level (samples from index 2^40 on, so no sample of
- * real use is consumed) and keeps the fastest for that level's solves.  The
- * arithmetic of a system does not depend on the plan except for the
- * summation order of the dot products.  rep: host pointer or NULL. */
+ * fastest of those, W-cycles, two smoothing sweep pairs on every grid, two
+ * or three on the finest grid with one on the coarser ones, and with prec 1
+ * or 2 an FP32 inner tolerance of 1e-4, 1e-5 or 1e-6) on a probe batch of
+ * each level (samples from index 2^40 on, so no sample of real use is
+ * consumed) and keeps the fastest for that level's solves.  A plan changes
+ * the path of the iteration (cycle, smoothing, inner tolerance, summation
+ * order of the dot products), never the stopping test, so results agree to
+ * the solver tolerance.  rep: host pointer or NULL. */
 MLMC_API int mlmc_autotune(mlmc_ctx* ctx, uint64_t seed, mlmc_tune_report* rep);
 
 /* Fix the solver's launch plan of one level by hand (overrides

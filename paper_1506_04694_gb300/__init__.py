@@ -69,6 +69,7 @@ class TuneReport(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32 * MAX_LEVELS), ("warp", ctypes.c_int32 * MAX_LEVELS),
                 ("cap_blocks_per_sm", ctypes.c_int32 * MAX_LEVELS), ("cluster", ctypes.c_int32 * MAX_LEVELS),
                 ("gamma", ctypes.c_int32 * MAX_LEVELS), ("nu", ctypes.c_int32 * MAX_LEVELS),
+                ("nu_coarse", ctypes.c_int32 * MAX_LEVELS),
                 ("inner_tol", ctypes.c_double * MAX_LEVELS),
                 ("candidates", ctypes.c_int32 * MAX_LEVELS),
                 ("ms_default", ctypes.c_double * MAX_LEVELS), ("ms_best", ctypes.c_double * MAX_LEVELS)]
@@ -286,7 +287,8 @@ class Context:
         _check(lib().mlmc_autotune(self._h, seed, ctypes.byref(r)), allow_failed=False)
         L = self.model.L + 1
         return [{"threads": r.threads[i], "warp": r.warp[i], "cap_blocks_per_sm": r.cap_blocks_per_sm[i],
-                 "cluster": r.cluster[i], "gamma": r.gamma[i], "nu": r.nu[i], "inner_tol": r.inner_tol[i],
+                 "cluster": r.cluster[i], "gamma": r.gamma[i], "nu": r.nu[i], "nu_coarse": r.nu_coarse[i],
+                 "inner_tol": r.inner_tol[i],
                  "candidates": r.candidates[i], "ms_per_sample_default": r.ms_default[i],
                  "ms_per_sample_best": r.ms_best[i]} for i in range(L)]
 

@@ -430,11 +430,11 @@ int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t see
 // p.q 2, x, r, r.r 6, r.z 2, p update 2; on the finest grid of the cycle a
 // zero-guess red half sweep 0.5, black 4.5, every further sweep pair 9, the
 // red-cell residual restriction 5.25, prolongation 1 and 9 per post-sweep
-// pair; coarser grids add 1/3 (V) or 1 (W) of that.  The flexible CG of
-// prec 3 adds the dot product r_new.z_old (2).
-double flops_per_cell_iter(int prec, int gamma, int nu) {
-  const double fine = 2.25 + 18.0 * nu;
-  return (prec == 3 ? 23.0 : 21.0) + fine * (gamma >= 2 ? 2.0 : 4.0 / 3.0);
+// pair; coarser grids (nuc sweep pairs) add 1/3 (V) or 1 (W) of that.  The
+// flexible CG of prec 3 adds the dot product r_new.z_old (2).
+double flops_per_cell_iter(int prec, int gamma, int nu, int nuc) {
+  const double fine = 2.25 + 18.0 * nu, coarse = 2.25 + 18.0 * (nuc > 0 ? nuc : nu);
+  return (prec == 3 ? 23.0 : 21.0) + fine + coarse * (gamma >= 2 ? 1.0 : 1.0 / 3.0);
 }
 
 // After the stream reached the copies of enqueue_level(): fill the sums.
@@ -445,7 +445,7 @@ int finish_level(mlmc_ctx* c, int level, const HostLevel& h, mlmc_level_sums* su
     SolvePlan P;
     if (c->tuned_ok[level]) P = c->tuned[level];
     else if (solve_plan(md.m0 << level, md.prec, &P)) P.gamma = P.nu = 1;
-    c->prof.solve_flops += (double)h.itc[1] * flops_per_cell_iter(md.prec, P.gamma, P.nu);
+    c->prof.solve_flops += (double)h.itc[1] * flops_per_cell_iter(md.prec, P.gamma, P.nu, P.nu_coarse);
   }
   sums->n = h.s.n;
   sums->n_failed = h.s.n_failed;
@@ -533,6 +533,7 @@ int multilevel_impl(mlmc_ctx* c, int n_levels, const int64_t* first, const int64
       int64_t tol_bits = 0;
       if (c->tuned_ok[l]) std::memcpy(&tol_bits, &c->tuned[l].inner_tol, sizeof tol_bits);
       key.push_back(tol_bits);
+      key.push_back(c->tuned_ok[l] ? c->tuned[l].nu_coarse : -1);
     }
     for (int l = 0; l < n_levels; ++l) {
       key.push_back(first[l]);
@@ -657,7 +658,7 @@ int mlmc_create(int device, const mlmc_model* model, void* cuda_stream, mlmc_ctx
         }
         if ((err = scratch.ensure((size_t)2 * M * M * 16))) break;
         if ((err = T.s64.ensure((size_t)M * M * 8)) || (err = T.s32.ensure((size_t)M * M * 4)) ||
-            (err = T.tw64.ensure((size_t)M * 8)) || (err = T.tw32.ensure((size_t)M * 4)))
+            (err = T.tw64.ensure((size_t)M * 16)) || (err = T.tw32.ensure((size_t)M * 8)))
           break;
         if (ce_build_table(LT.m, M, c->pair_sigma2[f], c->pair_lam[f], model->norm_r, scratch.p,
                            T.s64.as<double>(), T.s32.as<float>(), mm.as<double>(), T.tw64.p, T.tw32.p,
@@ -955,7 +956,7 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
       if ((err = run_fields(c, l, a.first, n, seed))) break;
       a.g = c->g.p;
     }
-    SolvePlan cand[20];
+    SolvePlan cand[24];
     int nk = solve_plan_candidates(m, md.prec, cand, 16);
     float best = 1e30f, def_ms = 0.f;
     int best_k = -1;
@@ -995,6 +996,21 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
         ++nk;
       }
     }
+    if (!err && best_k >= 0) {  // stronger smoothing on the finest grid only: (nu, nuc) = (2, 1), (3, 1)
+      const SolvePlan base = cand[best_k];
+      for (int nu : {2, 3}) {
+        if (err) break;
+        cand[nk] = base;
+        cand[nk].nu = nu;
+        cand[nk].nu_coarse = 1;
+        const float ms = time_plan(cand[nk]);
+        if (ms < best) {
+          best = ms;
+          best_k = nk;
+        }
+        ++nk;
+      }
+    }
     if (!err && best_k >= 0 && (md.prec == 1 || md.prec == 2)) {  // mixed: looser or tighter FP32 inner solves
       const SolvePlan base = cand[best_k];
       for (double it : {1e-4, 1e-6}) {
@@ -1019,6 +1035,7 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
       rep->cluster[l] = cand[best_k].cluster;
       rep->gamma[l] = cand[best_k].gamma;
       rep->nu[l] = cand[best_k].nu;
+      rep->nu_coarse[l] = cand[best_k].nu_coarse > 0 ? cand[best_k].nu_coarse : cand[best_k].nu;
       rep->inner_tol[l] = cand[best_k].inner_tol;
       rep->candidates[l] = nk;
       rep->ms_default[l] = def_ms / n;

@@ -28,11 +28,16 @@ __device__ __forceinline__ unsigned brev_n(unsigned v, int logn) {
   return logn ? (__brev(v) >> (32 - logn)) : 0u;
 }
 
-// In-place radix-2 DIT FFTs of `nrows` contiguous rows of length M (rows
-// already in bit-reversed order) in shared memory; tw[k] = exp(-2 pi i k/M).
-// Only the outputs k < nkeep of each row are needed (nkeep a power of two,
-// 4 <= nkeep <= M): stages whose half-span hs is >= nkeep compute, in each
-// group, the nkeep upper outputs u + w v only.
+// In-place DIT FFTs of `nrows` contiguous rows of length M (rows already in
+// bit-reversed order) in shared memory; tw[k] = exp(-2 pi i k/M), k < M.
+// Stages 0 and 1 run as one twiddle-free radix-4 pass; further pairs of full
+// stages as radix-4 passes (the two radix-2 stages of half-spans h and 2h
+// fused: three twiddles W^2p, W^p, W^3p of the 4h-point span, then a
+// twiddle-free 4-point butterfly; 28 instead of 32 real operations per four
+// points and one shared-memory pass instead of two).  Only the outputs
+// k < nkeep of each row are needed (nkeep a power of two, 4 <= nkeep <= M):
+// stages whose half-span hs is >= nkeep compute, in each group, the nkeep
+// upper outputs u + w v only.
 template <typename R>
 __device__ void block_fft_rows(Cplx<R>* s, int nrows, int M, int logM, const Cplx<R>* __restrict__ tw,
                                int nkeep) {
@@ -51,7 +56,30 @@ __device__ void block_fft_rows(Cplx<R>* s, int nrows, int M, int logM, const Cpl
     x[3] = Cplx<R>{a1.x - a3.y, a1.y + a3.x};
   }
   __syncthreads();
-  for (int st = 2; st < logM; ++st) {
+  int st = 2;
+  for (; st + 1 < logM && (2 << st) < nkeep; st += 2) {  // radix-4: stages st, st + 1 (both full)
+    const int h = 1 << st;
+    const int ts4 = M >> (st + 2);  // twiddle index step M / (4 h)
+    for (int t = threadIdx.x; t < nq; t += blockDim.x) {
+      const int row = t / (M >> 2);
+      const int b = t - row * (M >> 2);
+      const int p = b & (h - 1);
+      Cplx<R>* x = s + row * M + ((b >> st) << (st + 2)) + p;
+      const Cplx<R> w1 = tw[2 * p * ts4], w2 = tw[p * ts4], w3 = tw[3 * p * ts4];
+      const Cplx<R> a = x[0], v1 = x[h], v2 = x[2 * h], v3 = x[3 * h];
+      const Cplx<R> b1{w1.x * v1.x - w1.y * v1.y, w1.x * v1.y + w1.y * v1.x};
+      const Cplx<R> c1{w2.x * v2.x - w2.y * v2.y, w2.x * v2.y + w2.y * v2.x};
+      const Cplx<R> d1{w3.x * v3.x - w3.y * v3.y, w3.x * v3.y + w3.y * v3.x};
+      const Cplx<R> t0{a.x + b1.x, a.y + b1.y}, t1{a.x - b1.x, a.y - b1.y};
+      const Cplx<R> t2{c1.x + d1.x, c1.y + d1.y}, t3{c1.x - d1.x, c1.y - d1.y};
+      x[0] = Cplx<R>{t0.x + t2.x, t0.y + t2.y};
+      x[2 * h] = Cplx<R>{t0.x - t2.x, t0.y - t2.y};
+      x[h] = Cplx<R>{t1.x + t3.y, t1.y - t3.x};      // t1 - i t3
+      x[3 * h] = Cplx<R>{t1.x - t3.y, t1.y + t3.x};  // t1 + i t3
+    }
+    __syncthreads();
+  }
+  for (; st < logM; ++st) {
     const int hs = 1 << st;
     const int tstride = half >> st;  // twiddle index step M / (2 hs)
     if (hs >= nkeep) {  // pruned stage: upper outputs of the first nkeep positions
@@ -95,7 +123,7 @@ __device__ void block_fft_rows(Cplx<R>* s, int nrows, int M, int logM, const Cpl
 template <typename R>
 __global__ void twiddle_kernel(Cplx<R>* tw, int M) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < M / 2) {
+  if (k < M) {
     double s, c;
     sincospi(-2.0 * (double)k / (double)M, &s, &c);
     tw[k] = Cplx<R>{(R)c, (R)s};
@@ -246,8 +274,8 @@ int ce_build_table(int m, int M, double sigma2, double lam, int norm_r, void* sc
   const int64_t n = (int64_t)M * M;
   const int nt = 256;
   const unsigned nblk = (unsigned)((n + nt - 1) / nt);
-  twiddle_kernel<double><<<(M / 2 + nt - 1) / nt, nt, 0, st>>>((Cplx<double>*)tw64, M);
-  twiddle_kernel<float><<<(M / 2 + nt - 1) / nt, nt, 0, st>>>((Cplx<float>*)tw32, M);
+  twiddle_kernel<double><<<(M + nt - 1) / nt, nt, 0, st>>>((Cplx<double>*)tw64, M);
+  twiddle_kernel<float><<<(M + nt - 1) / nt, nt, 0, st>>>((Cplx<float>*)tw32, M);
   covariance_kernel<<<nblk, nt, 0, st>>>(a, m, M, sigma2, lam, norm_r);
   const size_t sm = (size_t)M * sizeof(Cplx<double>);
   cudaFuncSetAttribute(fft_rows_full_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -80,6 +80,7 @@ struct SolveArgs {
   double inner_tol;    // mixed: relative tolerance of each FP32 inner solve
   int mg_gamma;        // multigrid cycle: 1 V, 2 W (set from the launch plan)
   int mg_nu;           // red-black sweep pairs before and after the coarse correction
+  int mg_nu_coarse;    // the same on the coarser levels (0: mg_nu)
   // workspace
   int use_smem;
   size_t ws_stride;    // bytes per block slot (global workspace)
@@ -105,6 +106,7 @@ struct SolvePlan {
   int cap_blocks_per_sm; // > 0: launch at most this many blocks per SM (L2 residency)
   int gamma;             // multigrid cycle index: 1 V-cycle, 2 W-cycle
   int nu;                // smoothing: red-black sweep pairs before and after the coarse correction
+  int nu_coarse;         // the same on the coarser levels (0: nu)
   double inner_tol;      // mixed precision: relative tolerance of each FP32 inner solve
 };
 

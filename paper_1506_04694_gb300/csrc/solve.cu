@@ -304,21 +304,23 @@ __device__ __forceinline__ void build_diag(const G& g, const Level<T, FT>& L) {
 }
 
 // Symmetric multigrid cycle e_0 <- B f_0: on each level red-black then
-// black-red Gauss-Seidel around the coarse correction, which itself is
+// black-red Gauss-Seidel (nu sweep pairs on the finest level, nuc on the
+// coarser ones) around the coarse correction, which itself is
 // gamma cycles on the next level (gamma = 1: V-cycle, 2: W-cycle; one visit
 // when the next level is the 1 x 1 grid, solved exactly).  Written as a loop
 // over an explicit per-level visit count (no recursion: the device stack
 // stays fixed).  With adjoint pre- and post-smoothing the cycle is a
 // symmetric positive definite preconditioner for any gamma.
 template <typename T, typename F, typename G>
-__device__ void mg_cycle(const G& g, const Level<T, F>* lev, int nl, int gamma, int nu) {
+__device__ void mg_cycle(const G& g, const Level<T, F>* lev, int nl, int gamma, int nu, int nuc) {
   int done[kMaxLevels];   // visits of level l+1 finished in the current cycle on level l
   bool zero[kMaxLevels];  // level l starts from e_l = 0
   int l = 0;
   zero[0] = true;
   while (true) {
     if (l < nl - 1) {  // descend: pre-smooth, restrict, enter the next level
-      for (int s = 0; s < nu; ++s) {
+      const int ns = l == 0 ? nu : nuc;
+      for (int s = 0; s < ns; ++s) {
         rb_sweep(g, lev[l], 0, zero[l] && s == 0);
         rb_sweep(g, lev[l], 1, false);
       }
@@ -344,7 +346,8 @@ __device__ void mg_cycle(const G& g, const Level<T, F>* lev, int nl, int gamma, 
         break;
       }
       prolong_add(g, lev[l], lev[up]);
-      for (int s = 0; s < nu; ++s) {
+      const int ns = up == 0 ? nu : nuc;
+      for (int s = 0; s < ns; ++s) {
         rb_sweep(g, lev[up], 1, false);
         rb_sweep(g, lev[up], 0, false);
       }
@@ -375,11 +378,12 @@ __device__ void vcycle(const G& g, const Level<T, F>* lev, int nl) {
 }
 
 template <typename T, typename F, typename G>
-__device__ __forceinline__ void precond(const G& g, const Level<T, F>* lev, int nl, int gamma, int nu) {
-  if (gamma <= 1 && nu <= 1)
+__device__ __forceinline__ void precond(const G& g, const Level<T, F>* lev, int nl, int gamma, int nu, int nuc) {
+  if (nuc < 1) nuc = nu;
+  if (gamma <= 1 && nu <= 1 && nuc <= 1)
     vcycle(g, lev, nl);
   else
-    mg_cycle(g, lev, nl, gamma < 1 ? 1 : gamma, nu < 1 ? 1 : nu);
+    mg_cycle(g, lev, nl, gamma < 1 ? 1 : gamma, nu < 1 ? 1 : nu, nuc);
 }
 
 // CG on the operator A (faces and diagonal of the finest grid), multigrid
@@ -387,7 +391,7 @@ __device__ __forceinline__ void precond(const G& g, const Level<T, F>* lev, int 
 // r = rhs.  Stops when r.r <= thr; returns iterations, status 0 converged,
 // 1 hit the cap, 2 breakdown (p.Ap <= 0 or not finite).
 template <typename T, typename F, typename G>
-__device__ int pcg(const G& g, const Level<T>& A, const Level<T, F>* lev, int nl, int gamma, int nu,
+__device__ int pcg(const G& g, const Level<T>& A, const Level<T, F>* lev, int nl, int gamma, int nu, int nuc,
                    T* __restrict__ x, T* __restrict__ p, T* __restrict__ q, T thr, int max_it, T* red, int& par,
                    int& status) {
   const Level<T, F>& L0 = lev[0];
@@ -406,7 +410,7 @@ __device__ int pcg(const G& g, const Level<T>& A, const Level<T, F>* lev, int nl
     status = 0;
     return 0;
   }
-  precond(g, lev, nl, gamma, nu);
+  precond(g, lev, nl, gamma, nu, nuc);
   T rz = T(0);
   for (int c = g.rank(); c < n; c += step) {
     p[c] = z[c];
@@ -451,7 +455,7 @@ __device__ int pcg(const G& g, const Level<T>& A, const Level<T, F>* lev, int nl
       status = 0;
       break;
     }
-    precond(g, lev, nl, gamma, nu);
+    precond(g, lev, nl, gamma, nu, nuc);
     T rzn = T(0);
     for (int c = g.rank(); c < n; c += step) rzn += r[c] * z[c];
     rzn = g.sum(rzn, red, par);
@@ -470,7 +474,7 @@ __device__ int pcg(const G& g, const Level<T>& A, const Level<T, F>* lev, int nl
 // varying, slightly unsymmetric B) does not stall the iteration.  Stops when
 // r.r <= thr; status 0 converged, 1 cap, 2 breakdown.
 template <typename G>
-__device__ int pcg64_mg32(const G& g, const Level<double>& A, const Level<float>* lev, int nl, int gamma, int nu,
+__device__ int pcg64_mg32(const G& g, const Level<double>& A, const Level<float>* lev, int nl, int gamma, int nu, int nuc,
                           double* __restrict__ x, double* __restrict__ r, double* __restrict__ p,
                           double* __restrict__ q, double* __restrict__ z, double thr, int max_it, double* red,
                           int& par, int& status) {
@@ -491,7 +495,7 @@ __device__ int pcg64_mg32(const G& g, const Level<double>& A, const Level<float>
     return 0;
   }
   g.sync();
-  precond(g, lev, nl, gamma, nu);
+  precond(g, lev, nl, gamma, nu, nuc);
   double rz = 0.0;
   for (int c = g.rank(); c < n; c += step) {
     const double zv = (double)L0.e[c];
@@ -532,7 +536,7 @@ __device__ int pcg64_mg32(const G& g, const Level<double>& A, const Level<float>
       status = 0;
       break;
     }
-    precond(g, lev, nl, gamma, nu);
+    precond(g, lev, nl, gamma, nu, nuc);
     double rzn = 0.0;
     for (int c = g.rank(); c < n; c += step) {
       const double zv = (double)L0.e[c];
@@ -825,7 +829,7 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
       bb += bv * bv;
     }
     bb = g.sum(bb, red64, par);
-    iters = pcg64_mg32(g, A64, lev, nl, a.mg_gamma, a.mg_nu, x64, r64, gs.p64, gs.q64, gs.z64,
+    iters = pcg64_mg32(g, A64, lev, nl, a.mg_gamma, a.mg_nu, a.mg_nu_coarse, x64, r64, gs.p64, gs.q64, gs.z64,
                        a.tol * a.tol * bb, a.max_it, red64, par, status);
   } else if (PREC == 0) {
     // r = b, bb = b.b; stop at r.r <= tol^2 b.b
@@ -838,7 +842,8 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
       bb += bv * bv;
     }
     bb = g.sum(bb, red, par);
-    iters = pcg(g, A, lev, nl, a.mg_gamma, a.mg_nu, xv, pv, qv, (T)(a.tol * a.tol) * bb, a.max_it, red, par,
+    iters = pcg(g, A, lev, nl, a.mg_gamma, a.mg_nu, a.mg_nu_coarse, xv, pv, qv, (T)(a.tol * a.tol) * bb, a.max_it,
+                red, par,
                 status);
   } else {
     // FP64 refinement: r64 = b - A64 x64 with A64 = the FP32 faces in FP64.
@@ -877,7 +882,8 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
       int st_in = 1;
       const T thr_in = (T)(a.inner_tol * a.inner_tol) * r32;
       const int it =
-          pcg(g, A, lev, nl, a.mg_gamma, a.mg_nu, xv, pv, qv, thr_in, a.max_it - iters, red, par, st_in);
+          pcg(g, A, lev, nl, a.mg_gamma, a.mg_nu, a.mg_nu_coarse, xv, pv, qv, thr_in, a.max_it - iters, red, par,
+              st_in);
       iters += it;
       // x64 += scl * d, then r64 = b - A64 x64 (FP64)
       for (int c = g.rank(); c < n; c += g.size()) x64[c] += scl * (double)xv[c];
@@ -992,6 +998,7 @@ static int plan_fill(int m, int threads, int cluster, SolvePlan* P) {
   P->cap_blocks_per_sm = 0;
   P->gamma = 1;
   P->nu = 1;
+  P->nu_coarse = 0;
   P->inner_tol = 1e-5;
   cudaFuncSetAttribute(solve_kernel<PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   int nb = 0;
@@ -1093,6 +1100,7 @@ int solve_launch(const SolveArgs& a, int prec, const SolvePlan& P, int n_blocks,
   b.ws_stride = P.ws_stride;
   b.mg_gamma = P.gamma;
   b.mg_nu = P.nu;
+  b.mg_nu_coarse = P.nu_coarse;
   b.inner_tol = P.inner_tol;
   if (P.cluster) {
     cudaLaunchConfig_t cfg = {};
