@@ -55,6 +55,7 @@ class Model:
     geometry: 0 = horizontal interfaces (above); 1 = the three layers of Sec. 3.4
         cut by the straight lines (0, y1)-(1, y2) and (0, y3)-(1, y4), with
         y_t ~ U(line_lo[t], line_hi[t]).
+    dim: 2, or 3 for the extruded 3-D medium of Sec. 3.4 (oracle/darcy3.py).
     """
     n_layers: int = 2
     k_kind: int = 0
@@ -75,6 +76,7 @@ class Model:
     geometry: int = 0
     line_lo: List[float] = field(default_factory=lambda: [0.8, 0.6, 0.2, 0.4])
     line_hi: List[float] = field(default_factory=lambda: [0.9, 0.7, 0.3, 0.5])
+    dim: int = 2
 
     @classmethod
     def from_dict(cls, d):
@@ -366,7 +368,10 @@ def sample(model, seed, level, i, ce_cache=None, want_fields=False):
 
     Returns a dict with qf, qc (plain coupling, offset (0,0); 0 at l = 0),
     qc_cgv (mean of the 4 CGV coarse Q's, in CGV_OFFSETS order; NaN if
-    cgv == 0), and diagnostics."""
+    cgv == 0), and diagnostics.  dim = 3 models go to darcy3.sample."""
+    if model.dim == 3:
+        from . import darcy3
+        return darcy3.sample(model, seed, level, i, ce_cache, want_fields)
     m = model.m(level)
     eta = interfaces(model, seed, level, i)
     rows = layer_map(model, eta, m)

@@ -85,12 +85,14 @@ def optimal_samples(eps, V, C):
 
 
 def parity_cost(model, level):
-    """Deterministic cost model: fine cells plus coarse cells solved per sample."""
-    m2 = float(model.m(level) ** 2)
+    """Deterministic cost model: fine cells plus coarse cells solved per sample
+    (m^d (1 + n_coarse / 2^d), n_coarse = 2^d with CGV, else 1)."""
+    d = getattr(model, "dim", 2)
+    md = float(model.m(level) ** d)
     if level == 0:
-        return m2
-    nc = 4 if model.cgv else 1
-    return m2 * (1.0 + 0.25 * nc)
+        return md
+    nc = 2 ** d if model.cgv else 1
+    return md * (1.0 + nc / 2.0 ** d)
 
 
 def estimate(model, eps, seed, n_pilot=64, max_rounds=10, cost=None):

@@ -120,10 +120,12 @@ def layer_normals(seed, level, sample, n):
     return call_normals(stream_words(seed, level, sample, STREAM_LAYER_Z, calls)).reshape(-1)[:n]
 
 
-def field_normals(seed, level, sample, pair, M):
-    """Complex normals xi[q2, q1] (M x M) of field pair ``pair``."""
-    nq = M * M
+def field_normals(seed, level, sample, pair, M, dim=2):
+    """Complex normals of field pair ``pair``: xi[q2, q1] (M x M), or with
+    dim = 3 xi[q3, q2, q1] (M x M x M); the flat index q = q1 + M q2 (+ M^2 q3)
+    is the complex index of the Philox stream."""
+    nq = M ** dim
     calls = np.arange(nq // 2)
     z = call_normals(stream_words(seed, level, sample, STREAM_FIELD0 + pair, calls)).reshape(-1)
     xi = z[0::2] + 1j * z[1::2]  # entry 2q is Re xi_q, entry 2q+1 is Im xi_q
-    return xi.reshape(M, M)
+    return xi.reshape((M,) * dim)

@@ -23,6 +23,11 @@ exercise the MLMC level batch (Sec. 2 Ex. 1 / Ex. 2, Sec. 3.4 Model Problem 2):
   paper_3layer_lognormal_16to128  the same layers with log-normal fields:
                             outer layers mu = 0, lambda = 0.3, middle layer
                             mu = 4, lambda = 0.1, sigma^2 = 1, 2-norm
+  lognormal_3d_cgv_8to32    the unit cube (Sec. 3.4, 2-D layers extruded
+                            along x3): two layers, interface ~U(0.3, 0.7),
+                            log-normal fields with the 1-norm covariance of
+                            the CGV experiments (Sec. 4.2), sigma^2 = 1,
+                            lambda = 0.3, m = 8, 16, 32, CGV with 8 offsets
 """
 import numpy as np
 
@@ -50,6 +55,9 @@ WORKLOADS = {
     "paper_3layer_const_16to128": dict(
         n_layers=3, k_kind=0, geometry=1, mu=[0.0] * 3, sigma2=[1.0] * 3, lam=[0.3] * 3, norm_r=2,
         m0=16, L=3, cgv=0, prec=0, tol=1e-10, max_it=500, eps=2e-3, seed=0),
+    "lognormal_3d_cgv_8to32": dict(
+        dim=3, n_layers=2, k_kind=1, if_lo=0.3, if_hi=0.7, mu=[0.0, 0.0], sigma2=[1.0, 1.0],
+        lam=[0.3, 0.3], norm_r=1, m0=8, L=2, cgv=1, prec=1, tol=1e-10, max_it=500, eps=2e-3, seed=0),
     "paper_3layer_lognormal_16to128": dict(
         n_layers=3, k_kind=1, geometry=1, mu=[0.0, 4.0, 0.0], sigma2=[1.0, 1.0, 1.0],
         lam=[0.3, 0.1, 0.3], norm_r=2, m0=16, L=3, cgv=0, prec=0, tol=1e-10, max_it=500,
