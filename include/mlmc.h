@@ -107,11 +107,19 @@ typedef struct mlmc_model {
                                      centre */
   double line_lo[4], line_hi[4];  /* geometry 1; all zero selects the paper's ranges
                                   (0.8, 0.9), (0.6, 0.7), (0.2, 0.3), (0.4, 0.5) */
+  int32_t dim;                 /* 0 or 2: the unit square; 3: the unit cube of Sec. 3.4, the layers
+                                  extruded along x3 (a cell's layer depends on (x1, x2) only),
+                                  m^3 cells with the seven-point system (face coefficients as in
+                                  2-D, Q = h * outflow face sum), 3-D embedding draws, CGV over
+                                  the 8 offsets (ox, oy, oz) in the order ox fastest; needs
+                                  m0 * 2^L <= 128, prec 0 or 1; problem 1 takes D* = [x0, x1] x
+                                  [y0, y1] x [y0, y1] */
 } mlmc_model;
 
 /* Level sums over a range of samples (Eq. 3.6 and Eq. 4.2): Q_f is Q_l of the
  * sample, Q_c the plain coarse Q_{l-1} (0 at level 0), Y = Q_f - Q_c;
- * Q_cg = (1/4) sum of the four CGV coarse Q's, Y_g = Q_f - Q_cg (zero when
+ * Q_cg = the mean of the 2^d CGV coarse Q's (four in 2-D, eight in 3-D,
+ * summed in offset order), Y_g = Q_f - Q_cg (zero when
  * cgv == 0).  Sums are FP64 with Neumaier compensation in a fixed order. */
 typedef struct mlmc_level_sums {
   int64_t n;                   /* samples summed (converged ones) */
@@ -269,7 +277,8 @@ MLMC_API int mlmc_normals(mlmc_ctx* ctx, uint64_t seed, uint64_t level, uint64_t
 
 /* Stage output for parity checks: the per-layer fields g_t of the fine grid of
  * samples first .. first+n-1 of `level` (Ex. 1 constants or Ex. 2 fields),
- * g: device pointer to n * n_layers * m * m doubles ([sample][t][j][i]);
+ * g: device pointer to n * n_layers * m * m doubles ([sample][t][j][i]; 3-D
+ *   contexts n * n_layers * m^3, [sample][t][l][j][i]);
  * eta: device pointer to n * n_ends doubles or NULL: the sorted interfaces
  *   (geometry 0, n_ends = n_layers - 1) or the line ends y1..y4 (geometry 1,
  *   n_ends = 4). */
@@ -277,9 +286,10 @@ MLMC_API int mlmc_sample_fields(mlmc_ctx* ctx, int level, int64_t first, int64_t
                        double* g, double* eta);
 
 /* Solve n independent systems of size m x m (m a power of two, 1..4096)
- * for given cell permeabilities, with the context's solver settings.
- * k: device pointer to n*m*m doubles ([s][j][i]), all > 0.
- * p: device pointer to n*m*m doubles (pressure) or NULL.
+ * for given cell permeabilities, with the context's solver settings; a 3-D
+ * context (dim 3) solves m x m x m systems (m <= 128), k and p [s][l][j][i].
+ * k: device pointer to n*m*m (3-D: n*m*m*m) doubles ([s][j][i]), all > 0.
+ * p: device pointer to n*m*m (3-D: n*m*m*m) doubles (pressure) or NULL.
  * q: device pointer to n doubles (outflow Q; NaN if not converged), required.
  * iters: device pointer to n int32 or NULL. */
 MLMC_API int mlmc_solve_k(mlmc_ctx* ctx, int32_t m, int64_t n, const double* k, double* p, double* q,

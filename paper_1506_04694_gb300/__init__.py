@@ -32,6 +32,7 @@ class Model(ctypes.Structure):
         ("tol", ctypes.c_double), ("max_it", ctypes.c_int32),
         ("problem", ctypes.c_int32), ("qoi_box", ctypes.c_double * 4),
         ("geometry", ctypes.c_int32), ("line_lo", ctypes.c_double * 4), ("line_hi", ctypes.c_double * 4),
+        ("dim", ctypes.c_int32),
     ]
 
 
@@ -326,12 +327,14 @@ class Context:
         return out
 
     def sample_fields(self, level, n, seed, first=0):
-        """mlmc_sample_fields: fine per-layer fields g [n, n_layers, m, m] and
-        sorted interfaces [n, n_layers-1], as CUDA float64 tensors."""
+        """mlmc_sample_fields: fine per-layer fields g [n, n_layers, m, m] (3-D:
+        [n, n_layers, m, m, m]) and sorted interfaces [n, n_layers-1], as CUDA
+        float64 tensors."""
         import torch
         m = self.m(level)
         nl = self.model.n_layers
-        g = torch.empty((n, nl, m, m), dtype=torch.float64, device="cuda:%d" % self.device)
+        shape = (n, nl, m, m, m) if self.model.dim == 3 else (n, nl, m, m)
+        g = torch.empty(shape, dtype=torch.float64, device="cuda:%d" % self.device)
         n_ends = 4 if self.model.geometry == 1 else nl - 1
         eta = torch.empty((n, max(n_ends, 1)), dtype=torch.float64, device=g.device)
         _check(lib().mlmc_sample_fields(self._h, level, first, n, seed, _ptr(g), _ptr(eta)),
@@ -339,10 +342,10 @@ class Context:
         return g, eta[:, :n_ends]
 
     def solve_k(self, k, want_p=True):
-        """mlmc_solve_k: solve the systems of a CUDA float64 tensor k [n, m, m];
-        returns (p or None, Q, iterations)."""
+        """mlmc_solve_k: solve the systems of a CUDA float64 tensor k [n, m, m]
+        (3-D contexts: [n, m, m, m]); returns (p or None, Q, iterations)."""
         import torch
-        n, m, _ = k.shape
+        n, m = k.shape[0], k.shape[1]
         q = torch.empty(n, dtype=torch.float64, device=k.device)
         it = torch.empty(n, dtype=torch.int32, device=k.device)
         p = torch.empty_like(k) if want_p else None

@@ -173,7 +173,14 @@ int max_M(const mlmc_ctx* c, int level) {
   for (const auto& T : c->lev[level].pair) M = std::max(M, T.M);
   return M;
 }
-int n_coarse(const mlmc_model& md, int level) { return level == 0 ? 0 : (md.cgv ? 4 : 1); }
+int dim_of(const mlmc_model& md) { return md.dim == 3 ? 3 : 2; }
+// Cells of an m^d grid.
+int64_t cells_of(const mlmc_model& md, int m) { return dim_of(md) == 3 ? (int64_t)m * m * m : (int64_t)m * m; }
+int n_coarse(const mlmc_model& md, int level) { return level == 0 ? 0 : (md.cgv ? (dim_of(md) == 3 ? 8 : 4) : 1); }
+// Solver plan / launch of the model's dimension.
+int plan_of(const mlmc_model& md, int m, SolvePlan* P) {
+  return dim_of(md) == 3 ? solve3_plan(m, md.prec, P) : solve_plan(m, md.prec, P);
+}
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 int check_model(const mlmc_model& md) {
@@ -199,6 +206,11 @@ int check_model(const mlmc_model& md) {
       return fail(MLMC_ERR_ARG, "qoi_box must be x0 < x1, y0 < y1 inside [0, 1]");
   }
   if (md.geometry != 0 && md.geometry != 1) return fail(MLMC_ERR_ARG, "geometry must be 0 or 1");
+  if (md.dim != 0 && md.dim != 2 && md.dim != 3) return fail(MLMC_ERR_ARG, "dim must be 0, 2 or 3");
+  if (md.dim == 3) {
+    if ((int64_t)md.m0 << md.L > 128) return fail(MLMC_ERR_TOOBIG, "3-D: m0 * 2^L must be <= 128");
+    if (md.prec != 0 && md.prec != 1) return fail(MLMC_ERR_ARG, "3-D: prec must be 0 or 1");
+  }
   if (md.geometry == 1) {
     if (md.n_layers != 3) return fail(MLMC_ERR_ARG, "geometry 1 has three layers");
     bool zero = true;
@@ -255,8 +267,8 @@ int run_fields(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t seed) 
   const mlmc_model& md = c->model;
   const LevelTable& LT = c->lev[level];
   const bool f32 = fields_f32(md);
-  if (int e = c->W.ensure(ce_w_bytes_per_sample(LT.m, max_M(c, level), f32) * n)) return e;
-  if (int e = c->g.ensure((size_t)n * md.n_layers * LT.m * LT.m * (f32 ? 4 : 8))) return e;
+  if (int e = c->W.ensure(ce_w_bytes_per_sample(LT.m, max_M(c, level), f32, dim_of(md)) * n)) return e;
+  if (int e = c->g.ensure((size_t)n * md.n_layers * cells_of(md, LT.m) * (f32 ? 4 : 8))) return e;
   for (int f = 0; f < c->n_draws; ++f) {  // one draw at a time, W reused
     const PairTable& T = LT.pair[f];
     CeLaunch L;
@@ -264,6 +276,7 @@ int run_fields(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t seed) 
     L.bm_lg = reinterpret_cast<const double*>(c->bm.as<double2>() + kSinCosTab);
     L.M = T.M;
     L.m = LT.m;
+    L.dim = dim_of(md);
     L.pair = f;
     L.n_layers = md.n_layers;
     L.level = level;
@@ -291,8 +304,8 @@ int64_t chunk_samples(const mlmc_ctx* c, int level) {
   const bool f32 = fields_f32(md);
   size_t per = (size_t)(1 + n_coarse(md, level)) * 12;
   if (md.k_kind == 1) {
-    per += ce_w_bytes_per_sample(m, max_M(c, level), f32);
-    per += (size_t)md.n_layers * m * m * (f32 ? 4 : 8);
+    per += ce_w_bytes_per_sample(m, max_M(c, level), f32, dim_of(md));
+    per += (size_t)md.n_layers * cells_of(md, m) * (f32 ? 4 : 8);
   }
   int64_t s = (int64_t)(kChunkBudget / per);
   return std::max<int64_t>(1, std::min<int64_t>(s, 1 << 18));
@@ -310,7 +323,7 @@ int run_solves(mlmc_ctx* c, SolveArgs a, int64_t n_samples, int nc, int64_t max_
   a.n_coarse = nc;
   SolvePlan P;
   if (plan) P = *plan;
-  else if (solve_plan(a.m, prec, &P)) return fail(MLMC_ERR_CUDA, "occupancy query failed");
+  else if (plan_of(c->model, a.m, &P)) return fail(MLMC_ERR_CUDA, "occupancy query failed");
   const int64_t n_sys = n_samples * (1 + nc);
   const int64_t cap = P.use_smem ? 0 : (int64_t)(kWsBudget / P.ws_stride);
   int64_t nb = 0;
@@ -323,8 +336,8 @@ int run_solves(mlmc_ctx* c, SolveArgs a, int64_t n_samples, int nc, int64_t max_
   if (int e = c->itsys.ensure((size_t)std::max<int64_t>(n_sys, max_rows) * 4)) return e;
   a.q = c->qsys.as<double>();
   a.iters = c->itsys.as<int32_t>();
-  if (solve_launch(a, prec, P, (int)nb, c->st))
-    return fail(MLMC_ERR_CUDA, std::string("solve kernel: ") + cudaGetErrorString(cudaGetLastError()));
+  const int lr = dim_of(c->model) == 3 ? solve3_launch(a, prec, P, (int)nb, c->st) : solve_launch(a, prec, P, (int)nb, c->st);
+  if (lr) return fail(MLMC_ERR_CUDA, std::string("solve kernel: ") + cudaGetErrorString(cudaGetLastError()));
   return 0;
 }
 
@@ -380,10 +393,12 @@ int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t see
   CUDA_TRY(cudaMemsetAsync(itacc, 0, 2 * sizeof(int64_t), c->st));
   const int m = md.m0 << level;
   double sumM2 = 0, sumM = 0, fftf = 0;  // transformed points and FFT flops per sample over the draws
+  const bool d3 = dim_of(md) == 3;
   for (const auto& T : c->lev[level].pair) {
-    sumM2 += (double)T.M * T.M;
-    sumM += (double)T.M;
-    fftf += 5.0 * std::log2((double)T.M) * ((double)T.M * T.M + (double)T.M * m);
+    const double Md = T.M;
+    sumM2 += d3 ? Md * Md * Md : Md * Md;              // points of the row pass
+    sumM += d3 ? Md * Md + Md * m : Md;                // (3-D: middle and last passes) / m
+    fftf += 5.0 * std::log2(Md) * (d3 ? Md * Md * Md + Md * Md * m + Md * m * m : Md * Md + Md * m);
   }
   for (int64_t c0 = 0; c0 < n; c0 += chunk) {
     const int64_t cn = std::min<int64_t>(chunk, n - c0);
@@ -405,12 +420,13 @@ int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t see
       t.stop(1);
     }
     StageTimer t(c, 2);
-    if (gather_launch(c->qsys.as<double>(), c->itsys.as<int32_t>(), cn, nc, md.cgv, m, qf + c0,
+    if (gather_launch(c->qsys.as<double>(), c->itsys.as<int32_t>(), cn, nc, md.cgv, cells_of(md, m),
+                      cells_of(md, m / 2), qf + c0,
                       qc + c0, qcg + c0, iters ? iters + c0 : nullptr, itacc, c->st))
       return fail(MLMC_ERR_CUDA, "gather kernel");
     t.stop(1);
     if (c->prof_on) {
-      c->prof.cells += (double)cn * ((double)m * m + nc * (double)(m / 2) * (m / 2));
+      c->prof.cells += (double)cn * ((double)cells_of(md, m) + nc * (double)cells_of(md, m / 2));
       c->prof.samples += (double)cn;
     }
   }
@@ -432,6 +448,15 @@ int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t see
 // red-cell residual restriction 5.25, prolongation 1 and 9 per post-sweep
 // pair; coarser grids (nuc sweep pairs) add 1/3 (V) or 1 (W) of that.  The
 // flexible CG of prec 3 adds the dot product r_new.z_old (2).
+// 3-D: operator apply 13, CG vectors 12; on the finest grid of the cycle the
+// zero-guess red half sweep 0.5, black 6.5, every further sweep pair 13, the
+// red-cell restriction 7.4, prolongation 1 and 13 per post-sweep pair;
+// coarser grids add 1/7 (V) or 1/3 (W) of that.
+double flops_per_cell_iter3(int gamma, int nu, int nuc) {
+  const double fine = 2.4 + 26.0 * nu, coarse = 2.4 + 26.0 * (nuc > 0 ? nuc : nu);
+  return 25.0 + fine + coarse * (gamma >= 2 ? 1.0 / 3.0 : 1.0 / 7.0);
+}
+
 double flops_per_cell_iter(int prec, int gamma, int nu, int nuc) {
   const double fine = 2.25 + 18.0 * nu, coarse = 2.25 + 18.0 * (nuc > 0 ? nuc : nu);
   return (prec == 3 ? 23.0 : 21.0) + fine + coarse * (gamma >= 2 ? 1.0 : 1.0 / 3.0);
@@ -444,8 +469,9 @@ int finish_level(mlmc_ctx* c, int level, const HostLevel& h, mlmc_level_sums* su
     c->prof.cell_iters += (double)h.itc[1];
     SolvePlan P;
     if (c->tuned_ok[level]) P = c->tuned[level];
-    else if (solve_plan(md.m0 << level, md.prec, &P)) P.gamma = P.nu = 1;
-    c->prof.solve_flops += (double)h.itc[1] * flops_per_cell_iter(md.prec, P.gamma, P.nu, P.nu_coarse);
+    else if (plan_of(md, md.m0 << level, &P)) P.gamma = P.nu = 1;
+    c->prof.solve_flops += (double)h.itc[1] * (dim_of(md) == 3 ? flops_per_cell_iter3(P.gamma, P.nu, P.nu_coarse)
+                                                               : flops_per_cell_iter(md.prec, P.gamma, P.nu, P.nu_coarse));
   }
   sums->n = h.s.n;
   sums->n_failed = h.s.n_failed;
@@ -478,12 +504,12 @@ int prepare_level(mlmc_ctx* c, int level, int64_t n) {
   const int nc = n_coarse(md, level);
   const int64_t cn = std::min<int64_t>(n, chunk_samples(c, level));
   if (md.k_kind == 1) {
-    if (int e = c->W.ensure(ce_w_bytes_per_sample(m, max_M(c, level), f32) * cn)) return e;
-    if (int e = c->g.ensure((size_t)cn * md.n_layers * m * m * (f32 ? 4 : 8))) return e;
+    if (int e = c->W.ensure(ce_w_bytes_per_sample(m, max_M(c, level), f32, dim_of(md)) * cn)) return e;
+    if (int e = c->g.ensure((size_t)cn * md.n_layers * cells_of(md, m) * (f32 ? 4 : 8))) return e;
   }
   SolvePlan P;
   if (c->tuned_ok[level]) P = c->tuned[level];
-  else if (solve_plan(m, md.prec, &P)) return fail(MLMC_ERR_CUDA, "occupancy query failed");
+  else if (plan_of(md, m, &P)) return fail(MLMC_ERR_CUDA, "occupancy query failed");
   const int64_t n_sys = cn * (1 + nc);
   if (!P.use_smem) {
     int64_t nb = 0;
@@ -650,19 +676,25 @@ int mlmc_create(int device, const mlmc_model* model, void* cuda_stream, mlmc_ctx
     for (int f = 0; f < c->n_draws && !err; ++f) {
       PairTable& T = LT.pair[f];
       T.M = 0;
+      const bool d3 = dim_of(*model) == 3;
       for (int p = 2; p <= 16; p *= 2) {
         const int M = p * LT.m;
-        if (M > 16384) {
-          err = fail(MLMC_ERR_TOOBIG, "embedding size M above 16384");
+        if (M > (d3 ? 256 : 16384)) {
+          err = fail(MLMC_ERR_TOOBIG, d3 ? "3-D embedding size M above 256" : "embedding size M above 16384");
           break;
         }
-        if ((err = scratch.ensure((size_t)2 * M * M * 16))) break;
-        if ((err = T.s64.ensure((size_t)M * M * 8)) || (err = T.s32.ensure((size_t)M * M * 4)) ||
+        const size_t npts = d3 ? (size_t)M * M * M : (size_t)M * M;
+        if ((err = scratch.ensure((d3 ? 1 : 2) * npts * 16))) break;
+        if ((err = T.s64.ensure(npts * 8)) || (err = T.s32.ensure(npts * 4)) ||
             (err = T.tw64.ensure((size_t)M * 16)) || (err = T.tw32.ensure((size_t)M * 8)))
           break;
-        if (ce_build_table(LT.m, M, c->pair_sigma2[f], c->pair_lam[f], model->norm_r, scratch.p,
-                           T.s64.as<double>(), T.s32.as<float>(), mm.as<double>(), T.tw64.p, T.tw32.p,
-                           c->st)) {
+        const int br = d3 ? ce_build_table3(LT.m, M, c->pair_sigma2[f], c->pair_lam[f], model->norm_r, scratch.p,
+                                            T.s64.as<double>(), T.s32.as<float>(), mm.as<double>(), T.tw64.p,
+                                            T.tw32.p, c->st)
+                          : ce_build_table(LT.m, M, c->pair_sigma2[f], c->pair_lam[f], model->norm_r, scratch.p,
+                                           T.s64.as<double>(), T.s32.as<float>(), mm.as<double>(), T.tw64.p,
+                                           T.tw32.p, c->st);
+        if (br) {
           err = fail(MLMC_ERR_CUDA, "embedding set-up kernels");
           break;
         }
@@ -791,8 +823,8 @@ int mlmc_estimate_ex(mlmc_ctx* c, double eps, uint64_t seed, int32_t n_pilot, in
     if (r < 0) return r;
     rc_any |= r;
     for (int l = 0; l < NL; ++l) {
-      const double m2 = (double)(md.m0 << l) * (double)(md.m0 << l);
-      C[l] = m2 * (1.0 + 0.25 * n_coarse(md, l));
+      const double md_cells = (double)cells_of(md, md.m0 << l);
+      C[l] = md_cells * (1.0 + n_coarse(md, l) / (dim_of(md) == 3 ? 8.0 : 4.0));
     }
   }
   auto stats = [&](int l, double* mean, double* var) {
@@ -866,7 +898,8 @@ int mlmc_checkpoint(mlmc_ctx* c, const char* path) {
   if (!f) return fail(MLMC_ERR_ARG, std::string("cannot write ") + path);
   const mlmc_model& md = c->model;
   std::fprintf(f, "mlmc_checkpoint 1\n");
-  std::fprintf(f, "model %d %d %d %d %d %d %d\n", md.n_layers, md.k_kind, md.m0, md.L, md.cgv, md.prec, md.norm_r);
+  std::fprintf(f, "model %d %d %d %d %d %d %d %d\n", md.n_layers, md.k_kind, md.m0, md.L, md.cgv, md.prec, md.norm_r,
+               dim_of(md));
   std::fprintf(f, "seed %llu\neps %.17g\ncost_model %d\nrounds %d\nlevels %d\n", (unsigned long long)st.seed,
                st.eps, st.cost_model, st.rounds, (int)st.S.size());
   for (size_t l = 0; l < st.S.size(); ++l) {
@@ -885,15 +918,16 @@ int mlmc_resume(mlmc_ctx* c, const char* path) {
   if (!f) return fail(MLMC_ERR_ARG, std::string("cannot read ") + path);
   mlmc_ctx::EstState st;
   int ver = 0, nl = 0;
-  int mk[7];
+  int mk[8];
   unsigned long long seed = 0;
   bool ok = std::fscanf(f, "mlmc_checkpoint %d\n", &ver) == 1 && ver == 1 &&
-            std::fscanf(f, "model %d %d %d %d %d %d %d\n", &mk[0], &mk[1], &mk[2], &mk[3], &mk[4], &mk[5], &mk[6]) == 7 &&
+            std::fscanf(f, "model %d %d %d %d %d %d %d %d\n", &mk[0], &mk[1], &mk[2], &mk[3], &mk[4], &mk[5], &mk[6],
+                        &mk[7]) == 8 &&
             std::fscanf(f, "seed %llu\neps %lg\ncost_model %d\nrounds %d\nlevels %d\n", &seed, &st.eps,
                         &st.cost_model, &st.rounds, &nl) == 5;
   const mlmc_model& md = c->model;
   if (ok && (mk[0] != md.n_layers || mk[1] != md.k_kind || mk[2] != md.m0 || mk[3] != md.L || mk[4] != md.cgv ||
-             mk[5] != md.prec || mk[6] != md.norm_r || nl != md.L + 1))
+             mk[5] != md.prec || mk[6] != md.norm_r || mk[7] != dim_of(md) || nl != md.L + 1))
     ok = false;
   for (int l = 0; ok && l < nl; ++l) {
     mlmc_level_sums x{};
@@ -948,7 +982,7 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
     const int m = md.m0 << l;
     const int nc = n_coarse(md, l);
     // probe: enough systems to fill the GPU, few enough to stay short
-    int64_t n = std::max<int64_t>(4, std::min<int64_t>(65536, ((int64_t)1 << 24) / ((int64_t)m * m)));
+    int64_t n = std::max<int64_t>(4, std::min<int64_t>(65536, ((int64_t)1 << 24) / cells_of(md, m)));
     n = std::min<int64_t>(n, chunk_samples(c, l));
     if ((err = prepare_level(c, l, n))) break;
     SolveArgs a = base_args(c, l, seed, (int64_t)1 << 40);
@@ -957,7 +991,7 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
       a.g = c->g.p;
     }
     SolvePlan cand[24];
-    int nk = solve_plan_candidates(m, md.prec, cand, 16);
+    int nk = dim_of(md) == 3 ? solve3_plan_candidates(m, md.prec, cand, 16) : solve_plan_candidates(m, md.prec, cand, 16);
     float best = 1e30f, def_ms = 0.f;
     int best_k = -1;
     auto time_plan = [&](const SolvePlan& P) -> float {
@@ -1074,7 +1108,10 @@ int mlmc_set_launch(mlmc_ctx* c, int level, int32_t mode, int32_t threads, int32
   SolvePlan P;
   if (gamma < 1 || gamma > 2) return fail(MLMC_ERR_ARG, "gamma must be 1 (V-cycle) or 2 (W-cycle)");
   if (nu < 1 || nu > 4) return fail(MLMC_ERR_ARG, "nu must be 1..4");
-  if (solve_plan_mode(c->model.m0 << level, c->model.prec, mode, mode == 0 ? threads : 512, cluster, &P))
+  const int lm = c->model.m0 << level;
+  const int mr = dim_of(c->model) == 3 ? solve3_plan_mode(lm, c->model.prec, mode, mode == 0 ? threads : 512, cluster, &P)
+                                       : solve_plan_mode(lm, c->model.prec, mode, mode == 0 ? threads : 512, cluster, &P);
+  if (mr)
     return fail(MLMC_ERR_CUDA, "launch plan query failed");
   P.gamma = gamma;
   P.nu = nu;
@@ -1124,10 +1161,10 @@ int mlmc_sample_fields(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_
   SolveArgs a = base_args(c, level, seed, first);
   if (eta && interfaces_launch(a, n, eta, c->st)) return fail(MLMC_ERR_CUDA, "interfaces kernel");
   if (md.k_kind == 0) {
-    if (const_fields_launch(a, n, g, c->st)) return fail(MLMC_ERR_CUDA, "fields kernel");
+    if (const_fields_launch(a, n, cells_of(md, m), g, c->st)) return fail(MLMC_ERR_CUDA, "fields kernel");
   } else {
     if (int e = run_fields(c, level, first, n, seed)) return e;
-    const int64_t cnt = n * md.n_layers * (int64_t)m * m;
+    const int64_t cnt = n * md.n_layers * cells_of(md, m);
     if (fields_f32(md))
       f32_to_f64_launch(c->g.as<float>(), g, cnt, c->st);
     else
@@ -1140,7 +1177,8 @@ int mlmc_sample_fields(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_
 int mlmc_solve_k(mlmc_ctx* c, int32_t m, int64_t n, const double* k, double* p, double* q,
                  int32_t* iters) {
   if (!c || !k || !q || n < 0) return fail(MLMC_ERR_ARG, "bad argument");
-  if (!is_pow2(m) || m > 4096) return fail(MLMC_ERR_ARG, "m must be a power of two <= 4096");
+  if (!is_pow2(m) || m > (dim_of(c->model) == 3 ? 128 : 4096))
+    return fail(MLMC_ERR_ARG, "m must be a power of two <= 4096 (2-D) or 128 (3-D)");
   if (n == 0) return 0;
   CUDA_TRY(cudaSetDevice(c->device));
   SolveArgs a = base_args(c, 0, 0, 0);

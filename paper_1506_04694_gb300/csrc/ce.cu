@@ -14,6 +14,8 @@
 //                     written as g_t = mu_t + Re/Im y.
 // Each FFT of length M runs in shared memory: bit-reversed load, then log2 M
 // radix-2 decimation-in-time stages.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -194,10 +196,59 @@ __global__ void scale_kernel(const Cplx<double>* lam, double* s64, float* s32, i
   s32[id] = (float)v;
 }
 
+// 3-D torus covariance c[c3][b][a] (Eq. 2.3 in d = 3, cell-centre offsets).
+__global__ void covariance3_kernel(Cplx<double>* c, int m, int M, double sigma2, double lam, int norm_r) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t M2 = (int64_t)M * M;
+  if (id >= M2 * M) return;
+  const int c3 = (int)(id / M2);
+  const int64_t r = id - (int64_t)c3 * M2;
+  const int b = (int)(r / M), a = (int)(r - (int64_t)b * M);
+  const double dx = (double)min(a, M - a) / (double)m;
+  const double dy = (double)min(b, M - b) / (double)m;
+  const double dz = (double)min(c3, M - c3) / (double)m;
+  const double dist = norm_r == 1 ? (fabs(dx) + fabs(dy)) + fabs(dz) : sqrt(dx * dx + dy * dy + dz * dz);
+  c[id] = Cplx<double>{sigma2 * exp(-dist / lam), 0.0};
+}
+
+// Full in-place FFT along one axis of an M^3 array: line `blockIdx.x` =
+// (u, v) over the other two axes, elements base + k * stride.
+__global__ void fft_line3_kernel(Cplx<double>* data, int M, int logM, const Cplx<double>* tw, int axis) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cplx<double>* s = reinterpret_cast<Cplx<double>*>(smem_raw);
+  const int64_t M2 = (int64_t)M * M;
+  const int u = (int)(blockIdx.x / M), v = (int)(blockIdx.x - (int64_t)u * M);
+  int64_t base, stride;
+  if (axis == 0) {
+    base = (int64_t)u * M2 + (int64_t)v * M;
+    stride = 1;
+  } else if (axis == 1) {
+    base = (int64_t)u * M2 + v;
+    stride = M;
+  } else {
+    base = (int64_t)u * M + v;
+    stride = M2;
+  }
+  for (int t = threadIdx.x; t < M; t += blockDim.x) s[brev_n(t, logM)] = data[base + t * stride];
+  __syncthreads();
+  block_fft_rows(s, 1, M, logM, tw, M);
+  for (int t = threadIdx.x; t < M; t += blockDim.x) data[base + t * stride] = s[t];
+}
+
+// s = sqrt(max(Lambda, 0) / M^3) in FP64 and FP32 (3-D scaling).
+__global__ void scale3_kernel(const Cplx<double>* lam, double* s64, float* s32, int64_t n, double inv_n) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= n) return;
+  const double v = sqrt(fmax(lam[id].x, 0.0) * inv_n);
+  s64[id] = v;
+  s32[id] = (float)v;
+}
+
 // ------------------------------------------------------------ pass 1 -------
-// Block (row block rb, sample s): rows q2 in [rb*R, rb*R + R) of the M x M
-// draw of field pair args.pair, FFT along q1, keep a < m.
-// W layout: [sample][q2][a] complex (one draw at a time).
+// Block (row block rb, sample s): rows r in [rb*R, rb*R + R) of the draw of
+// field pair args.pair (2-D: r = q2 of the M x M draw; 3-D: r = q3 M + q2 of
+// the M^3 draw; args.n_rows = M^(d-1) rows per sample), FFT along q1, keep
+// a < m.  W layout: [sample][r][a] complex (one draw at a time).
 template <typename R>
 __global__ void ce_rows_kernel(CeRowsArgs args, const R* __restrict__ scale,
                                const Cplx<R>* __restrict__ tw, Cplx<R>* __restrict__ W) {
@@ -216,7 +267,7 @@ __global__ void ce_rows_kernel(CeRowsArgs args, const R* __restrict__ scale,
     const int r = t / halfM;
     const int q1 = (t - r * halfM) << 1;
     const int q2 = q2_0 + r;
-    const uint64_t call = ((uint64_t)q2 * (uint64_t)M + (uint64_t)q1) >> 1;
+    const uint64_t call = ((uint64_t)q2 * (uint64_t)M + (uint64_t)q1) >> 1;  // q = r M + q1
     const Words4 w = philox4x64_10(call, sample, (uint64_t)args.level, kStreamField0 + f, args.seed);
     R re0, im0, re1, im1;
     box_muller_tab(w.w0, w.w1, tb, re0, im0, scale[(int64_t)q2 * M + q1]);
@@ -226,7 +277,7 @@ __global__ void ce_rows_kernel(CeRowsArgs args, const R* __restrict__ scale,
   }
   __syncthreads();
   block_fft_rows(s, rows, M, logM, tw, m >= 4 ? m : M);
-  Cplx<R>* out = W + (sidx * (int64_t)M + q2_0) * m;
+  Cplx<R>* out = W + (sidx * (int64_t)args.n_rows + q2_0) * m;
   for (int t = threadIdx.x; t < rows * m; t += blockDim.x) {
     const int r = t / m, a = t - r * m;
     out[(int64_t)r * m + a] = s[r * M + a];
@@ -234,33 +285,62 @@ __global__ void ce_rows_kernel(CeRowsArgs args, const R* __restrict__ scale,
 }
 
 // ------------------------------------------------------------ pass 2 -------
-// Block (column block cb, sample s): columns a in [cb*C, cb*C + C), FFT
-// along q2, keep b < m; g layout [sample][layer][b][a]; Re goes to layer
-// t_re, Im to layer t_im (if any).
+// Block (column block cb, sample s): columns a in [cb*C, cb*C + C) of the
+// M x ncols array of the sample (2-D: ncols = m, the row-pass output; 3-D:
+// ncols = m^2, the middle-pass output indexed [q3][b][a]), FFT along its M
+// rows, keep the first m outputs; g layout [sample][layer][row][column]
+// with m rows of ncols; Re goes to layer t_re, Im to layer t_im (if any).
 template <typename R, typename G>
 __global__ void ce_cols_kernel(CeColsArgs args, const Cplx<R>* __restrict__ tw,
                                const Cplx<R>* __restrict__ W, G* __restrict__ g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cplx<R>* s = reinterpret_cast<Cplx<R>*>(smem_raw);
   const int M = args.M, logM = args.logM, m = args.m, C = args.cols_per_block;
+  const int64_t nc = args.ncols;
   const int cb = blockIdx.x;
   const int64_t sidx = blockIdx.z + args.z_offset;
-  const int a0 = cb * C;
-  const Cplx<R>* in = W + (sidx * (int64_t)M) * m + a0;
+  const int64_t a0 = (int64_t)cb * C;
+  const Cplx<R>* in = W + (sidx * (int64_t)M) * nc + a0;
+  for (int t = threadIdx.x; t < M * C; t += blockDim.x) {
+    const int q2 = t / C, cc = t - q2 * C;
+    s[cc * M + brev_n(q2, logM)] = in[(int64_t)q2 * nc + cc];
+  }
+  __syncthreads();
+  block_fft_rows(s, C, M, logM, tw, m >= 4 ? m : M);
+  const bool has_im = args.t_im >= 0;
+  G* g0 = g + (sidx * args.n_layers + args.t_re) * (int64_t)m * nc;
+  G* g1 = g + (sidx * args.n_layers + (has_im ? args.t_im : args.t_re)) * (int64_t)m * nc;
+  for (int t = threadIdx.x; t < m * C; t += blockDim.x) {
+    const int b = t / C, cc = t - b * C;
+    const Cplx<R> v = s[cc * M + b];
+    g0[(int64_t)b * nc + a0 + cc] = (G)(args.mu_re + (double)v.x);
+    if (has_im) g1[(int64_t)b * nc + a0 + cc] = (G)(args.mu_im + (double)v.y);
+  }
+}
+
+// ------------------------------------------------------ 3-D middle pass -----
+// Block (column block cb, slab q3, sample s): columns a in [cb*C, cb*C + C)
+// of the M x m slab q3 of the row-pass output W1[s][q3][q2][a], FFT along q2,
+// keep b < m; output W2[s][q3][b][a] complex.
+template <typename R>
+__global__ void ce_mid_kernel(CeColsArgs args, const Cplx<R>* __restrict__ tw,
+                              const Cplx<R>* __restrict__ W1, Cplx<R>* __restrict__ W2) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Cplx<R>* s = reinterpret_cast<Cplx<R>*>(smem_raw);
+  const int M = args.M, logM = args.logM, m = args.m, C = args.cols_per_block;
+  const int a0 = blockIdx.x * C, q3 = blockIdx.y;
+  const int64_t sidx = blockIdx.z + args.z_offset;
+  const Cplx<R>* in = W1 + ((sidx * M + q3) * (int64_t)M) * m + a0;
   for (int t = threadIdx.x; t < M * C; t += blockDim.x) {
     const int q2 = t / C, cc = t - q2 * C;
     s[cc * M + brev_n(q2, logM)] = in[(int64_t)q2 * m + cc];
   }
   __syncthreads();
   block_fft_rows(s, C, M, logM, tw, m >= 4 ? m : M);
-  const bool has_im = args.t_im >= 0;
-  G* g0 = g + ((sidx * args.n_layers + args.t_re) * (int64_t)m) * m;
-  G* g1 = g + ((sidx * args.n_layers + (has_im ? args.t_im : args.t_re)) * (int64_t)m) * m;
+  Cplx<R>* out = W2 + ((sidx * M + q3) * (int64_t)m) * m + a0;
   for (int t = threadIdx.x; t < m * C; t += blockDim.x) {
     const int b = t / C, cc = t - b * C;
-    const Cplx<R> v = s[cc * M + b];
-    g0[(int64_t)b * m + a0 + cc] = (G)(args.mu_re + (double)v.x);
-    if (has_im) g1[(int64_t)b * m + a0 + cc] = (G)(args.mu_im + (double)v.y);
+    out[(int64_t)b * m + cc] = s[cc * M + b];
   }
 }
 
@@ -288,9 +368,66 @@ int ce_build_table(int m, int M, double sigma2, double lam, int norm_r, void* sc
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+int ce_build_table3(int m, int M, double sigma2, double lam, int norm_r, void* scratch, double* s64,
+                    float* s32, double* minmax_dev, void* tw64, void* tw32, cudaStream_t st) {
+  const int logM = ilog2(M);
+  Cplx<double>* a = reinterpret_cast<Cplx<double>*>(scratch);
+  const int64_t n = (int64_t)M * M * M;
+  const int nt = 256;
+  const unsigned nblk = (unsigned)((n + nt - 1) / nt);
+  twiddle_kernel<double><<<(M + nt - 1) / nt, nt, 0, st>>>((Cplx<double>*)tw64, M);
+  twiddle_kernel<float><<<(M + nt - 1) / nt, nt, 0, st>>>((Cplx<float>*)tw32, M);
+  covariance3_kernel<<<nblk, nt, 0, st>>>(a, m, M, sigma2, lam, norm_r);
+  const size_t sm = (size_t)M * sizeof(Cplx<double>);
+  cudaFuncSetAttribute(fft_line3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  for (int axis = 0; axis < 3; ++axis)
+    fft_line3_kernel<<<(unsigned)((int64_t)M * M), 256, sm, st>>>(a, M, logM, (const Cplx<double>*)tw64, axis);
+  minmax_kernel<<<1, 1024, 0, st>>>(a, n, minmax_dev);
+  scale3_kernel<<<nblk, nt, 0, st>>>(a, s64, s32, n, 1.0 / (double)n);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename R, typename G>
+static int ce_sample3_impl(const CeLaunch& L, const R* scale, const void* tw, void* W, G* g, cudaStream_t st) {
+  const size_t esz = sizeof(Cplx<R>);
+  const int budget = (int)(65536 / sizeof(Cplx<double>)) * (int)(sizeof(Cplx<double>) / esz);
+  const int M = L.M, m = L.m;
+  const int per = std::max(1, std::min(budget / M, M));  // rows (pass 1) or columns per block
+  const int rows = std::min(per, M);
+  const int cmid = std::min(per, m);
+  const int64_t ncol3 = (int64_t)m * m;
+  const int c3 = (int)std::min<int64_t>(per, ncol3);
+  Cplx<R>* W1 = reinterpret_cast<Cplx<R>*>(W);
+  Cplx<R>* W2 = W1 + (int64_t)M * M * m * L.n_samples;
+  CeRowsArgs ra;
+  ra.bm_sc = L.bm_sc;
+  ra.bm_lg = L.bm_lg;
+  ra.M = M; ra.logM = ilog2(M); ra.m = m; ra.rows_per_block = rows; ra.pair = L.pair;
+  ra.level = L.level; ra.seed = L.seed; ra.first = L.first; ra.n_rows = M * M;
+  CeColsArgs ma;
+  ma.M = M; ma.logM = ra.logM; ma.m = m; ma.cols_per_block = cmid; ma.n_layers = L.n_layers; ma.ncols = m;
+  ma.t_re = L.t_re; ma.t_im = L.t_im; ma.mu_re = L.mu_re; ma.mu_im = L.mu_im;
+  CeColsArgs ca = ma;
+  ca.cols_per_block = c3;
+  ca.ncols = ncol3;
+  const size_t sm_r = (size_t)rows * M * esz, sm_m = (size_t)cmid * M * esz, sm_c = (size_t)c3 * M * esz;
+  cudaFuncSetAttribute(ce_rows_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_r);
+  cudaFuncSetAttribute(ce_mid_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_m);
+  cudaFuncSetAttribute(ce_cols_kernel<R, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_c);
+  for (int64_t z0 = 0; z0 < L.n_samples; z0 += 65535) {
+    const unsigned nz = (unsigned)((L.n_samples - z0) < 65535 ? (L.n_samples - z0) : 65535);
+    ra.z_offset = ma.z_offset = ca.z_offset = z0;
+    ce_rows_kernel<R><<<dim3((unsigned)(M * M / rows), 1u, nz), 256, sm_r, st>>>(ra, scale, (const Cplx<R>*)tw, W1);
+    ce_mid_kernel<R><<<dim3((unsigned)(m / cmid), (unsigned)M, nz), 256, sm_m, st>>>(ma, (const Cplx<R>*)tw, W1, W2);
+    ce_cols_kernel<R, G><<<dim3((unsigned)(ncol3 / c3), 1u, nz), 256, sm_c, st>>>(ca, (const Cplx<R>*)tw, W2, g);
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
 template <typename R, typename G>
 static int ce_sample_impl(const CeLaunch& L, const R* scale, const void* tw, void* W, G* g,
                           cudaStream_t st) {
+  if (L.dim == 3) return ce_sample3_impl<R, G>(L, scale, tw, W, g, st);
   const size_t esz = sizeof(Cplx<R>);
   // rows / columns per block: at most 64 KB of FP64 (128 KB of FP32) per block
   const int budget = (int)(65536 / sizeof(Cplx<double>)) * (int)(sizeof(Cplx<double>) / esz);
@@ -304,9 +441,9 @@ static int ce_sample_impl(const CeLaunch& L, const R* scale, const void* tw, voi
   ra.bm_sc = L.bm_sc;
   ra.bm_lg = L.bm_lg;
   ra.M = L.M; ra.logM = ilog2(L.M); ra.m = L.m; ra.rows_per_block = rows; ra.pair = L.pair;
-  ra.level = L.level; ra.seed = L.seed; ra.first = L.first;
+  ra.level = L.level; ra.seed = L.seed; ra.first = L.first; ra.n_rows = L.M;
   CeColsArgs ca;
-  ca.M = L.M; ca.logM = ra.logM; ca.m = L.m; ca.cols_per_block = cols; ca.n_layers = L.n_layers;
+  ca.M = L.M; ca.logM = ra.logM; ca.m = L.m; ca.cols_per_block = cols; ca.n_layers = L.n_layers; ca.ncols = L.m;
   ca.t_re = L.t_re; ca.t_im = L.t_im; ca.mu_re = L.mu_re; ca.mu_im = L.mu_im;
   const size_t sm_r = (size_t)rows * L.M * esz;
   const size_t sm_c = (size_t)cols * L.M * esz;
@@ -356,8 +493,10 @@ int bm_tables_build(double2* sc, double* lg, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-size_t ce_w_bytes_per_sample(int m, int M, bool fp32) {
-  return (size_t)M * m * (fp32 ? sizeof(Cplx<float>) : sizeof(Cplx<double>));
+size_t ce_w_bytes_per_sample(int m, int M, bool fp32, int dim) {
+  const size_t e = fp32 ? sizeof(Cplx<float>) : sizeof(Cplx<double>);
+  if (dim == 3) return ((size_t)M * M * m + (size_t)M * m * m) * e;  // W1 then W2
+  return (size_t)M * m * e;
 }
 
 }  // namespace mlmc

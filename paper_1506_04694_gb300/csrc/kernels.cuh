@@ -13,6 +13,7 @@ struct CeRowsArgs {
   const double2* bm_sc;  // Box-Muller tables (common.cuh, BmTables)
   const double* bm_lg;
   int M, logM, m, rows_per_block, pair, level;
+  int n_rows;        // rows of M points per sample: M (2-D) or M^2 (3-D)
   uint64_t seed;
   int64_t first;     // sample index of chunk entry 0
   int64_t z_offset;  // chunk entry of blockIdx.z == 0
@@ -20,6 +21,7 @@ struct CeRowsArgs {
 
 struct CeColsArgs {
   int M, logM, m, cols_per_block, n_layers;
+  int64_t ncols;   // columns of the M-row input: m (2-D), m (3-D middle pass) or m^2 (3-D last pass)
   int t_re, t_im;  // layers fed by Re and Im of this draw (t_im < 0: none)
   double mu_re, mu_im;
   int64_t z_offset;
@@ -30,6 +32,7 @@ struct CeLaunch {
   const double2* bm_sc;
   const double* bm_lg;
   int M, m, pair, n_layers, level;
+  int dim;  // 2 or 3
   int t_re, t_im;
   double mu_re, mu_im;
   uint64_t seed;
@@ -39,11 +42,13 @@ struct CeLaunch {
 int ce_build_table(int m, int M, double sigma2, double lam, int norm_r, void* scratch,
                    double* s64, float* s32, double* minmax_dev, void* tw64, void* tw32,
                    cudaStream_t st);
+int ce_build_table3(int m, int M, double sigma2, double lam, int norm_r, void* scratch, double* s64,
+                    float* s32, double* minmax_dev, void* tw64, void* tw32, cudaStream_t st);
 int ce_sample_fp64(const CeLaunch& L, const double* scale, const void* tw, void* W, double* g,
                    cudaStream_t st);
 int ce_sample_fp32(const CeLaunch& L, const float* scale, const void* tw, void* W, float* g,
                    cudaStream_t st);
-size_t ce_w_bytes_per_sample(int m, int M, bool fp32);
+size_t ce_w_bytes_per_sample(int m, int M, bool fp32, int dim);
 // Box-Muller tables: sc 1024 double2, lg 3*128 doubles.
 int bm_tables_build(double2* sc, double* lg, cudaStream_t st);
 
@@ -121,6 +126,12 @@ int solve_plan_candidates(int m, int prec, SolvePlan* out, int max_out);
 // workspace (plan.use_smem == 0) must hold groups * ws_stride bytes.
 int64_t solve_groups(const SolvePlan& plan, int64_t n_sys, int nsm, int64_t max_groups_cap, int64_t* n_blocks);
 int solve_launch(const SolveArgs& a, int prec, const SolvePlan& plan, int n_blocks, cudaStream_t st);
+// The same for the 3-D seven-point systems (solve3.cu; prec 0 or 1; modes 0 block, 2 cluster).
+size_t solve3_ws_bytes(int m, int prec);
+int solve3_plan(int m, int prec, SolvePlan* plan);
+int solve3_plan_mode(int m, int prec, int mode, int threads, int cluster, SolvePlan* plan);
+int solve3_plan_candidates(int m, int prec, SolvePlan* out, int max_out);
+int solve3_launch(const SolveArgs& a, int prec, const SolvePlan& plan, int n_blocks, cudaStream_t st);
 
 // --------------------------------------------------------------- reduce ---
 struct LevelSumsDev {
@@ -130,9 +141,11 @@ struct LevelSumsDev {
 
 // Gather system Q's of a chunk into the per-sample outputs.
 // it_acc[0] += iterations of all systems, it_acc[1] += cells x iterations.
+// cells_f / cells_c: cells of a fine / coarse system; Q_cgv is the mean of the
+// n_coarse (4 or 8) coarse Q's, summed left to right.
 int gather_launch(const double* q_sys, const int32_t* it_sys, int64_t n_samples, int n_coarse,
-                  int cgv, int m, double* qf, double* qc, double* qcg, int32_t* iters, int64_t* it_acc,
-                  cudaStream_t st);
+                  int cgv, int64_t cells_f, int64_t cells_c, double* qf, double* qc, double* qcg,
+                  int32_t* iters, int64_t* it_acc, cudaStream_t st);
 // Level sums in two launches (per-block partials, then a fixed-order
 // combine); ws must hold reduce_ws_bytes().
 size_t reduce_ws_bytes();
@@ -141,7 +154,7 @@ int reduce_launch(const double* qf, const double* qc, const double* qcg, int64_t
 int philox_launch(uint64_t seed, uint64_t level, uint64_t sample, uint64_t stream,
                   uint64_t first_call, int64_t n_calls, uint64_t* out, cudaStream_t st);
 int interfaces_launch(const SolveArgs& a, int64_t n, double* eta, cudaStream_t st);
-int const_fields_launch(const SolveArgs& a, int64_t n, double* g, cudaStream_t st);
+int const_fields_launch(const SolveArgs& a, int64_t n, int64_t cells, double* g, cudaStream_t st);
 int normals_launch(uint64_t seed, uint64_t level, uint64_t sample, uint64_t stream, uint64_t first_call,
                    int64_t n_calls, const double2* sc, const double* lg, int fp32, double* out,
                    cudaStream_t st);

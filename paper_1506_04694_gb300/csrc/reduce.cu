@@ -8,14 +8,14 @@
 namespace mlmc {
 
 __global__ void gather_kernel(const double* q_sys, const int32_t* it_sys, int64_t n, int nc, int cgv,
-                              int m, double* qf, double* qc, double* qcg, int32_t* iters,
-                              unsigned long long* it_acc) {
+                              int64_t cells_f, int64_t cells_c, double* qf, double* qc, double* qcg,
+                              int32_t* iters, unsigned long long* it_acc) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   long long it = 0, itc = 0;
   if (s < n) {
     qf[s] = q_sys[s];
     it = it_sys[s];
-    itc = (long long)it_sys[s] * m * m;
+    itc = (long long)it_sys[s] * cells_f;
     if (iters) iters[s] = it_sys[s];
     if (nc == 0) {
       qc[s] = 0.0;
@@ -23,11 +23,13 @@ __global__ void gather_kernel(const double* q_sys, const int32_t* it_sys, int64_
     } else {
       const double* qq = q_sys + n + s * nc;
       qc[s] = qq[0];
+      double acc = qq[0];
       for (int o = 0; o < nc; ++o) {
         it += it_sys[n + s * nc + o];
-        itc += (long long)it_sys[n + s * nc + o] * (m / 2) * (m / 2);
+        itc += (long long)it_sys[n + s * nc + o] * cells_c;
+        if (o) acc += qq[o];
       }
-      qcg[s] = nc == 4 ? 0.25 * (((qq[0] + qq[1]) + qq[2]) + qq[3]) : nan("");
+      qcg[s] = nc >= 4 ? acc * (1.0 / nc) : nan("");
     }
   }
   it = warp_sum(it);
@@ -38,12 +40,12 @@ __global__ void gather_kernel(const double* q_sys, const int32_t* it_sys, int64_
   }
 }
 
-int gather_launch(const double* q_sys, const int32_t* it_sys, int64_t n, int n_coarse, int cgv, int m,
-                  double* qf, double* qc, double* qcg, int32_t* iters, int64_t* it_acc,
-                  cudaStream_t st) {
+int gather_launch(const double* q_sys, const int32_t* it_sys, int64_t n, int n_coarse, int cgv,
+                  int64_t cells_f, int64_t cells_c, double* qf, double* qc, double* qcg, int32_t* iters,
+                  int64_t* it_acc, cudaStream_t st) {
   if (n <= 0) return 0;
   gather_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-      q_sys, it_sys, n, n_coarse, cgv, m, qf, qc, qcg, iters, (unsigned long long*)it_acc);
+      q_sys, it_sys, n, n_coarse, cgv, cells_f, cells_c, qf, qc, qcg, iters, (unsigned long long*)it_acc);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

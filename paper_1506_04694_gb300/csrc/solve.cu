@@ -43,6 +43,8 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "groups.cuh"
+#include "layers.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -105,59 +107,6 @@ struct Level {
   T* invd;  // 1 / diagonal (null for the CG operator of prec 2)
   T* e;     // correction (level 0: CG z)
   T* f;     // right-hand side (level 0: CG r)
-};
-
-// Cooperating threads that solve one system: a whole thread block, or one
-// warp (small grids, no block barriers at all).
-struct BlockGroup {
-  static constexpr int kU = 1;  // cells per thread per batch in the cell loops
-  __device__ __forceinline__ bool local_leader() const { return threadIdx.x == 0; }
-  __device__ __forceinline__ int rank() const { return threadIdx.x; }
-  __device__ __forceinline__ int size() const { return blockDim.x; }
-  __device__ __forceinline__ void sync() const { __syncthreads(); }
-  template <typename T>
-  __device__ __forceinline__ T sum(T v, T* red, int& par) const {
-    return block_sum(v, red, par);
-  }
-};
-
-struct WarpGroup {
-  static constexpr int kU = 1;
-  __device__ __forceinline__ bool local_leader() const { return (threadIdx.x & 31) == 0; }
-  __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
-  __device__ __forceinline__ int size() const { return 32; }
-  __device__ __forceinline__ void sync() const { __syncwarp(); }
-  template <typename T>
-  __device__ __forceinline__ T sum(T v, T*, int&) const {
-    return warp_sum(v);
-  }
-};
-
-// All threads of a thread-block cluster (large grids: the system's
-// workspace is shared by the cluster's blocks through global memory / L2).
-// sync() is the hardware cluster barrier (release / acquire at cluster
-// scope, so global writes of one block are visible to the others after it);
-// sum() reduces in each block, then every thread adds the blocks' partials
-// in block-rank order through distributed shared memory, so all blocks hold
-// bit-identical sums and take identical branches.
-struct ClusterGroup {
-  static constexpr int kU = 1;
-  unsigned nblk, brank;
-  double* part;  // two double slots in this block's shared memory
-  __device__ __forceinline__ bool local_leader() const { return threadIdx.x == 0; }
-  __device__ __forceinline__ int rank() const { return (int)(brank * blockDim.x + threadIdx.x); }
-  __device__ __forceinline__ int size() const { return (int)(nblk * blockDim.x); }
-  __device__ __forceinline__ void sync() const { cg::this_cluster().sync(); }
-  template <typename T>
-  __device__ __forceinline__ T sum(T v, T* red, int& par) const {
-    const int slot = par;  // block_sum toggles par; the partial slot follows it
-    const T b = block_sum(v, red, par);
-    if (threadIdx.x == 0) part[slot] = (double)b;
-    cg::this_cluster().sync();
-    double t = 0.0;
-    for (unsigned r = 0; r < nblk; ++r) t += *cg::this_cluster().map_shared_rank(part + slot, r);
-    return (T)t;
-  }
 };
 
 // (A v)_c = diag_c v_c - sum over the faces of T v_nbr (v_nbr = 0 outside:
@@ -550,61 +499,6 @@ __device__ int pcg64_mg32(const G& g, const Level<double>& A, const Level<float>
     g.sync();
   }
   return it;
-}
-
-__device__ __forceinline__ int layer_at(const double* eta, int n_if, double y) {
-  int t = 0;
-  for (int s = 0; s < n_if; ++s) t += (eta[s] <= y) ? 1 : 0;
-  return t;
-}
-
-// Layer of the point (x, y): geometry 0 counts the interfaces at or below y;
-// geometry 1 counts the lines (0, e2)-(1, e3) and (0, e0)-(1, e1) at or below
-// it, the line height e_a + ((e_b - e_a) x) rounded once per operation.
-__device__ __forceinline__ int layer_at_point(int geometry, const double* eta, int n_if, double x, double y) {
-  if (geometry != 1) return layer_at(eta, n_if, y);
-  const double lower = __dadd_rn(eta[2], __dmul_rn(__dadd_rn(eta[3], -eta[2]), x));
-  const double upper = __dadd_rn(eta[0], __dmul_rn(__dadd_rn(eta[1], -eta[0]), x));
-  return (lower <= y ? 1 : 0) + (upper <= y ? 1 : 0);
-}
-
-// Interfaces of one sample (sorted; geometry 1: the four line ends, in order)
-// and, for Ex. 1, the layer constants.
-__device__ void sample_layers(const SolveArgs& a, uint64_t sample, double* eta, double* kc) {
-  const int n_if = a.geometry == 1 ? 0 : a.n_layers - 1;
-  const double width = __dadd_rn(a.if_hi, -a.if_lo);
-  if (a.geometry == 1) {
-    const Words4 w = philox4x64_10(0, sample, (uint64_t)a.level, kStreamInterface, a.seed);
-    const uint64_t ws[4] = {w.w0, w.w1, w.w2, w.w3};
-    for (int t = 0; t < 4; ++t)
-      eta[t] = __dadd_rn(a.line_lo[t], __dmul_rn(__dadd_rn(a.line_hi[t], -a.line_lo[t]), uniform52(ws[t])));
-  }
-  for (int t = 0; t < n_if; ++t) {
-    const Words4 w = philox4x64_10((uint64_t)(t >> 2), sample, (uint64_t)a.level, kStreamInterface,
-                                   a.seed);
-    const uint64_t wt = (t & 3) == 0 ? w.w0 : (t & 3) == 1 ? w.w1 : (t & 3) == 2 ? w.w2 : w.w3;
-    eta[t] = __dadd_rn(a.if_lo, __dmul_rn(width, uniform52(wt)));
-  }
-  for (int t = 1; t < n_if; ++t) {  // insertion sort, ascending
-    const double v = eta[t];
-    int s = t - 1;
-    while (s >= 0 && eta[s] > v) {
-      eta[s + 1] = eta[s];
-      --s;
-    }
-    eta[s + 1] = v;
-  }
-  if (a.ksrc == KSRC_CONST) {
-    for (int t = 0; t < a.n_layers; t += 4) {
-      const Words4 w = philox4x64_10((uint64_t)(t >> 2), sample, (uint64_t)a.level, kStreamLayerZ,
-                                     a.seed);
-      double z[4];
-      box_muller(uniform52(w.w0), uniform52(w.w1), z[0], z[1]);
-      box_muller(uniform52(w.w2), uniform52(w.w3), z[2], z[3]);
-      for (int u = 0; u < 4 && t + u < a.n_layers; ++u)
-        kc[t + u] = exp(a.mu[t + u] + a.sigma[t + u] * z[u]);
-    }
-  }
 }
 
 constexpr int kMaxThreads = 512;
@@ -1171,7 +1065,7 @@ int interfaces_launch(const SolveArgs& a, int64_t n, double* eta, cudaStream_t s
 }
 
 // Ex. 1 fields: g_t = mu_t + sigma_t Z_t on every cell (stage output).
-__global__ void const_fields_kernel(SolveArgs a, int64_t n, double* g) {
+__global__ void const_fields_kernel(SolveArgs a, int64_t n, int64_t cells, double* g) {
   const int64_t s = blockIdx.x;
   if (s >= n) return;
   __shared__ double e[MAX_LAYERS_DEV], kc[MAX_LAYERS_DEV], gz[MAX_LAYERS_DEV];
@@ -1190,14 +1084,14 @@ __global__ void const_fields_kernel(SolveArgs a, int64_t n, double* g) {
     }
   }
   __syncthreads();
-  const int64_t mm = (int64_t)a.m * a.m;
+  const int64_t mm = cells;  // cells per layer: m^2 or m^3
   for (int64_t c = threadIdx.x; c < mm * a.n_layers; c += blockDim.x)
     g[s * mm * a.n_layers + c] = gz[c / mm];
 }
 
-int const_fields_launch(const SolveArgs& a, int64_t n, double* g, cudaStream_t st) {
+int const_fields_launch(const SolveArgs& a, int64_t n, int64_t cells, double* g, cudaStream_t st) {
   if (n <= 0) return 0;
-  const_fields_kernel<<<(unsigned)n, 256, 0, st>>>(a, n, g);
+  const_fields_kernel<<<(unsigned)n, 256, 0, st>>>(a, n, cells, g);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
