@@ -169,7 +169,7 @@ def run_reference(args, d):
             values.append(sum(N) / t_eps)
     value = sum(values) / len(values)
     ms = 1000 * sum(times) / len(times)
-    sample = ("oracle (numpy/scipy FP64, banded Cholesky) on %d spawned processes; per step %s samples "
+    sample = ("oracle (numpy/scipy FP64; banded Cholesky in 2-D, sparse LU in 3-D) on %d spawned processes; per step %s samples "
               "of levels %s timed, time-to-eps extrapolated as sum_l N_l / rate_l with N_l from the "
               "oracle's pilot variances" % (cores, [CPU_SAMPLE.get(lv, 1) for lv in levels], levels))
     return {"impl": "reference", "metric": metric_name(d, args), "value": value, "unit": "level-samples/s",
@@ -183,8 +183,8 @@ def run_reference(args, d):
 
 
 def metric_name(d, args):
-    return ("level solves/s: MLMC time-to-RMSE eps=%g, %d-layer piecewise log-normal, m=%d..%d, %s%s"
-            % (d["eps"], d["n_layers"], d["m0"], d["m0"] << d["L"], {0: "FP64", 1: "mixed FP32-MG", 2: "mixed FP32-MG (BF16 faces)",
+    return ("level solves/s: MLMC time-to-RMSE eps=%g, %d-layer piecewise log-normal%s, m=%d..%d, %s%s"
+            % (d["eps"], d["n_layers"], ", 3-D" if d.get("dim", 2) == 3 else "", d["m0"], d["m0"] << d["L"], {0: "FP64", 1: "mixed FP32-MG", 2: "mixed FP32-MG (BF16 faces)",
                                                          3: "FP64 CG with FP32-MG preconditioner"}[d["prec"]],
                ", CGV" if d["cgv"] else ""))
 
@@ -192,6 +192,7 @@ def metric_name(d, args):
 def config_block(args, d):
     return {"workload": args.workload, "m_levels": [d["m0"] << l for l in range(d["L"] + 1)],
             "eps": d["eps"], "sigma2": d["sigma2"][0], "lambda": d["lam"][0], "layers": d["n_layers"],
+            "dim": d.get("dim", 2), "norm_r": d["norm_r"],
             "cgv": d["cgv"], "prec": PREC_NAMES[d["prec"]],
             "solver_tol": d["tol"], "seed": args.seed, "cost_model": "deterministic m_l^2 (1 + n_coarse/4)",
             "l2": "flushed between steps (256 MB device write)", "parallelism": "replicas%d" % args.gpus}

@@ -57,7 +57,7 @@ WORKLOADS = {
         m0=16, L=3, cgv=0, prec=0, tol=1e-10, max_it=500, eps=2e-3, seed=0),
     "lognormal_3d_cgv_8to32": dict(
         dim=3, n_layers=2, k_kind=1, if_lo=0.3, if_hi=0.7, mu=[0.0, 0.0], sigma2=[1.0, 1.0],
-        lam=[0.3, 0.3], norm_r=1, m0=8, L=2, cgv=1, prec=1, tol=1e-10, max_it=500, eps=2e-3, seed=0),
+        lam=[0.3, 0.3], norm_r=1, m0=8, L=2, cgv=1, prec=1, tol=1e-10, max_it=500, eps=5e-4, seed=0),
     "paper_3layer_lognormal_16to128": dict(
         n_layers=3, k_kind=1, geometry=1, mu=[0.0, 4.0, 0.0], sigma2=[1.0, 1.0, 1.0],
         lam=[0.3, 0.1, 0.3], norm_r=2, m0=16, L=3, cgv=0, prec=0, tol=1e-10, max_it=500,
