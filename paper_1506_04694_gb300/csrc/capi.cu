@@ -331,6 +331,9 @@ int run_solves(mlmc_ctx* c, SolveArgs a, int64_t n_samples, int nc, int64_t max_
   if (!P.use_smem) {
     if (int e = c->ws.ensure(P.ws_stride * groups)) return e;
     a.ws = c->ws.as<unsigned char>();
+  } else if (P.ws64_stride) {
+    if (int e = c->ws.ensure(P.ws64_stride * groups)) return e;
+    a.ws64 = c->ws.as<unsigned char>();
   }
   if (int e = c->qsys.ensure((size_t)std::max<int64_t>(n_sys, max_rows) * 8)) return e;
   if (int e = c->itsys.ensure((size_t)std::max<int64_t>(n_sys, max_rows) * 4)) return e;
@@ -511,10 +514,11 @@ int prepare_level(mlmc_ctx* c, int level, int64_t n) {
   if (c->tuned_ok[level]) P = c->tuned[level];
   else if (plan_of(md, m, &P)) return fail(MLMC_ERR_CUDA, "occupancy query failed");
   const int64_t n_sys = cn * (1 + nc);
-  if (!P.use_smem) {
+  if (!P.use_smem || P.ws64_stride) {
     int64_t nb = 0;
-    const int64_t groups = solve_groups(P, n_sys, c->nsm, (int64_t)(kWsBudget / P.ws_stride), &nb);
-    if (int e = c->ws.ensure(P.ws_stride * groups)) return e;
+    const int64_t groups =
+        solve_groups(P, n_sys, c->nsm, P.use_smem ? 0 : (int64_t)(kWsBudget / P.ws_stride), &nb);
+    if (int e = c->ws.ensure((P.use_smem ? P.ws64_stride : P.ws_stride) * groups)) return e;
   }
   if (int e = c->qsys.ensure((size_t)n_sys * 8)) return e;
   if (int e = c->itsys.ensure((size_t)n_sys * 4)) return e;

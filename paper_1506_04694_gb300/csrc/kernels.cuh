@@ -90,6 +90,8 @@ struct SolveArgs {
   int use_smem;
   size_t ws_stride;    // bytes per block slot (global workspace)
   unsigned char* ws;   // global workspace base (n_blocks * ws_stride)
+  size_t ws64_stride;  // > 0: bytes per group of FP64 refinement vectors in global memory at ws64
+  unsigned char* ws64;
   // outputs per system
   double* q;           // outflow Q (NaN when not converged)
   int32_t* iters;      // CG iterations
@@ -107,6 +109,7 @@ struct SolvePlan {
   int blocks_per_sm;     // occupancy
   int use_smem;          // workspace in shared memory (else global, ws_stride per group)
   size_t ws_stride;      // bytes of workspace per group
+  size_t ws64_stride;    // > 0 (prec 1, 2 on chip): global bytes per group of the FP64 refinement vectors
   size_t smem_bytes;     // dynamic shared memory per block
   int cap_blocks_per_sm; // > 0: launch at most this many blocks per SM (L2 residency)
   int gamma;             // multigrid cycle index: 1 V-cycle, 2 W-cycle

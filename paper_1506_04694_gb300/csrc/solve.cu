@@ -545,7 +545,8 @@ struct SolverTypes {
 template <int PREC, typename G>
 __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned char* base,
                           GroupState<typename SolverTypes<PREC>::T, typename SolverTypes<PREC>::F>& gs,
-                          typename SolverTypes<PREC>::T* red, double* red64, int& par, int& m_prev) {
+                          typename SolverTypes<PREC>::T* red, double* red64, int& par, int& m_prev,
+                          unsigned char* base64) {
   using T = typename SolverTypes<PREC>::T;
   using F = typename SolverTypes<PREC>::F;
   using TF = typename std::conditional<PREC == 3, double, T>::type;  // face assembly
@@ -577,8 +578,13 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
         return p;
       };
       if (PREC != 0) {
-        gs.x64 = reinterpret_cast<double*>(take(n0 * 8));
-        gs.r64 = reinterpret_cast<double*>(take(n0 * 8));
+        if (base64) {  // FP64 refinement vectors in global memory, the rest on chip
+          gs.x64 = reinterpret_cast<double*>(base64);
+          gs.r64 = reinterpret_cast<double*>(base64 + align16(n0 * 8));
+        } else {
+          gs.x64 = reinterpret_cast<double*>(take(n0 * 8));
+          gs.r64 = reinterpret_cast<double*>(take(n0 * 8));
+        }
       }
       if (PREC == 3) {
         const size_t nf0 = (size_t)m * (m + 1);
@@ -855,19 +861,20 @@ __global__ void __launch_bounds__(MODE == 1 ? 32 * kWarpsPerBlock : kMaxThreads,
     const int64_t cid = blockIdx.x / g.nblk, ncl = gridDim.x / g.nblk;
     unsigned char* base = a.ws + (size_t)cid * a.ws_stride;
     for (int64_t sys = cid; sys < n_sys; sys += ncl)
-      solve_one<PREC>(g, a, sys, base, gstate[0], red, red64, par, m_prev);
+      solve_one<PREC>(g, a, sys, base, gstate[0], red, red64, par, m_prev, nullptr);
     cl.sync();  // no block leaves while others may still read its shared memory
     return;
   }
   const int gid = MODE == 1 ? (int)(threadIdx.x >> 5) : 0;
-  unsigned char* base = a.use_smem ? smem_raw + (size_t)gid * a.ws_stride
-                                   : a.ws + ((size_t)blockIdx.x * kGroups + gid) * a.ws_stride;
+  const size_t slot = (size_t)blockIdx.x * kGroups + gid;
+  unsigned char* base = a.use_smem ? smem_raw + (size_t)gid * a.ws_stride : a.ws + slot * a.ws_stride;
+  unsigned char* base64 = a.ws64_stride ? a.ws64 + slot * a.ws64_stride : nullptr;
   const int64_t stride = (int64_t)gridDim.x * kGroups;
   for (int64_t sys = (int64_t)blockIdx.x * kGroups + gid; sys < n_sys; sys += stride) {
     if (MODE == 1)
-      solve_one<PREC>(WarpGroup(), a, sys, base, gstate[gid], red, red64, par, m_prev);
+      solve_one<PREC>(WarpGroup(), a, sys, base, gstate[gid], red, red64, par, m_prev, base64);
     else
-      solve_one<PREC>(BlockGroup(), a, sys, base, gstate[gid], red, red64, par, m_prev);
+      solve_one<PREC>(BlockGroup(), a, sys, base, gstate[gid], red, red64, par, m_prev, base64);
   }
 }
 
@@ -886,8 +893,14 @@ static int plan_fill(int m, int threads, int cluster, SolvePlan* P) {
   P->threads = MODE == 1 ? 32 * kWarpsPerBlock : threads;
   P->groups_per_block = MODE == 1 ? kWarpsPerBlock : 1;
   P->blocks_per_group = MODE == 2 ? cluster : 1;
-  P->ws_stride = (ws + 255) & ~(size_t)255;
-  P->use_smem = MODE != 2 && P->ws_stride * P->groups_per_block <= kSmemCap;
+  // prec 1, 2: the FP64 solution and residual of the refinement (touched once
+  // per refinement sweep) stay in global memory when the rest of the
+  // workspace fits on chip, so more systems fit per SM
+  const size_t v64 = (PREC == 1 || PREC == 2) ? 2 * align16((size_t)m * m * 8) : 0;
+  const size_t chip = ((ws - v64) + 255) & ~(size_t)255;
+  P->use_smem = MODE != 2 && chip * P->groups_per_block <= kSmemCap;
+  P->ws_stride = P->use_smem ? chip : (ws + 255) & ~(size_t)255;
+  P->ws64_stride = P->use_smem && v64 ? (v64 + 255) & ~(size_t)255 : 0;
   P->smem_bytes = P->use_smem ? P->ws_stride * P->groups_per_block : 0;
   P->cap_blocks_per_sm = 0;
   P->gamma = 1;
@@ -992,6 +1005,7 @@ int solve_launch(const SolveArgs& a, int prec, const SolvePlan& P, int n_blocks,
   SolveArgs b = a;
   b.use_smem = P.use_smem;
   b.ws_stride = P.ws_stride;
+  b.ws64_stride = P.ws64_stride;
   b.mg_gamma = P.gamma;
   b.mg_nu = P.nu;
   b.mg_nu_coarse = P.nu_coarse;
@@ -1179,6 +1193,9 @@ extern "C" int mlmc_solve_k_static(int device, int32_t m, int64_t n, const doubl
       }
       cap = (int64_t)(kStaticScratchBytes / P.ws_stride);
       a.ws = reinterpret_cast<unsigned char*>(base);
+    } else if (P.ws64_stride) {  // the refinement's FP64 vectors
+      cap = (int64_t)(kStaticScratchBytes / P.ws64_stride);
+      a.ws64 = reinterpret_cast<unsigned char*>(base);
     }
     int64_t nb = 0;
     solve_groups(P, n, nsm, cap, &nb);
