@@ -705,6 +705,17 @@ int solve3_plan_candidates(int m, int prec, SolvePlan* out, int max_out) {
     SolvePlan b;
     if (!plan_fill3(m, prec, 0, t, 0, &b)) add(b);
   }
+  // global-workspace block plans also with one or two systems per SM (the
+  // systems in flight then keep their working set in L2)
+  const int k0 = k;
+  for (int i = 0; i < k0; ++i)
+    if (!out[i].use_smem && !out[i].cluster && out[i].blocks_per_sm > 1)
+      for (int cap : {1, 2}) {
+        if (cap >= out[i].blocks_per_sm) continue;
+        SolvePlan c = out[i];
+        c.cap_blocks_per_sm = cap;
+        add(c);
+      }
   if (m >= 16)
     for (int cl : {2, 4, 8}) {
       if (cl == d.cluster) continue;

@@ -13,6 +13,10 @@ kernel the benchmark times.  Cases:
                 level 0 (65535 samples, m = 16) and level 1 (16384, m = 32)
   mixed_large   the CGV model m = 32..2048: level 5 (8 samples, m = 1024,
                 clusters of 8 blocks)
+  mixed_3d      the 3-D CGV workload (FP32 multigrid in FP64 refinement):
+                level 1 (4096 samples, m = 16, eight m = 8 coarse systems
+                each, blocks of 128 threads) and level 2 (512 samples,
+                m = 32, blocks of 256)
 """
 import sys
 
@@ -27,6 +31,7 @@ CASES = {
                      [(0, 65535, (1, 0, 0, 1, 2)), (3, 1024, (0, 512, 0, 1, 2))]),
     "mixed_small": ("lognormal_2layer_cgv_16to512", {}, [(0, 65535, (1, 0, 0, 1, 1)), (1, 16384, (1, 0, 0, 1, 2))]),
     "mixed_large": ("lognormal_2layer_cgv_32to2048", {}, [(5, 8, (2, 512, 8, 1, 2))]),
+    "mixed_3d": ("lognormal_3d_cgv_8to32", {}, [(1, 4096, (0, 128, 0, 1, 2)), (2, 512, (0, 256, 0, 1, 2))]),
 }
 
 
