@@ -13,7 +13,8 @@
 // a constant k), restriction = sum of the four fine residuals, prolongation =
 // piecewise constant, red-black Gauss-Seidel smoothing (red-black before the
 // coarse correction, black-red after it, so the cycle is symmetric), exact
-// solve on the 1 x 1 grid.
+// solve on the 4 x 4 grid (a dense inverse formed once per system; on an idle
+// warp-wide grid the smaller levels cost as much as the 8 x 8 one).
 //
 // prec 0: CG and multigrid in FP64.
 // prec 1: FP64 iterative refinement (solution, residual b - A x, stopping test
@@ -51,6 +52,9 @@ namespace cg = cooperative_groups;
 namespace mlmc {
 
 constexpr int kMaxLevels = 14;
+// The coarsening stops at the 4 x 4 grid (or at the finest grid when m < 4),
+// which is solved exactly with a dense inverse formed once per system.
+constexpr int kCoarseSide = 4;
 
 __host__ __device__ __forceinline__ size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
@@ -78,7 +82,11 @@ __host__ __device__ inline size_t ws_layout(int m, int prec) {
     for (int a = 0; a < 4; ++a) take(nl * ts);
     if (l == 0 && prec != 3)
       for (int b = 0; b < 3; ++b) take(nl * ts);
-    if (ml == 1) break;
+    if (ml <= kCoarseSide) {  // coarsest grid: its dense inverse and a pivot buffer
+      take(nl * nl * ts);
+      take((2 * nl + 1) * ts);
+      break;
+    }
   }
   return o;
 }
@@ -107,6 +115,8 @@ struct Level {
   T* invd;  // 1 / diagonal (null for the CG operator of prec 2)
   T* e;     // correction (level 0: CG z)
   T* f;     // right-hand side (level 0: CG r)
+  T* cinv;  // coarsest level only: dense inverse [m^2][m^2]
+  T* cbuf;  // coarsest level only: pivot row, pivot column (2 m^2 + 1)
 };
 
 // (A v)_c = diag_c v_c - sum over the faces of T v_nbr (v_nbr = 0 outside:
@@ -252,11 +262,64 @@ __device__ __forceinline__ void build_diag(const G& g, const Level<T, FT>& L) {
   g.sync();
 }
 
+// Dense inverse of the coarsest grid's operator (n = m^2 <= 16 unknowns) by
+// in-place Gauss-Jordan elimination without pivoting (the matrix is SPD, so
+// every pivot, a Schur-complement diagonal, is positive): at step k with
+// pivot p, row r_j = B[k][j] and column c_i = B[i][k],
+//   B[k][k] <- 1/p, B[k][j] <- r_j / p, B[i][k] <- -c_i / p,
+//   B[i][j] <- B[i][j] - c_i r_j / p;  after n steps B = A^-1.
+template <typename T, typename F, typename G>
+__device__ void build_coarse_inverse(const G& g, const Level<T, F>& L) {
+  const int m = L.m, n = m * m, nn = n * n;
+  T* B = L.cinv;
+  T* buf = L.cbuf;
+  for (int idx = g.rank(); idx < nn; idx += g.size()) {
+    const int r = idx / n, c = idx - r * n;
+    const int jr = r / m, ir = r - jr * m, jc = c / m, ic = c - jc * m;
+    T v = T(0);
+    if (r == c) v = L.diag[r];
+    else if (jr == jc && (ir - ic == 1 || ic - ir == 1)) v = -face_ld(L.tx[jr * (m + 1) + (ir > ic ? ir : ic)]);
+    else if (ir == ic && (jr - jc == 1 || jc - jr == 1)) v = -face_ld(L.ty[(jr > jc ? jr : jc) * m + ir]);
+    B[idx] = v;
+  }
+  g.sync();
+  for (int k = 0; k < n; ++k) {
+    for (int t = g.rank(); t < n; t += g.size()) {
+      buf[t] = B[k * n + t];
+      buf[n + t] = B[t * n + k];
+    }
+    g.sync();
+    const T ip = T(1) / buf[k];
+    for (int idx = g.rank(); idx < nn; idx += g.size()) {
+      const int i = idx / n, j = idx - i * n;
+      T v;
+      if (i == k) v = j == k ? ip : buf[j] * ip;
+      else if (j == k) v = -buf[n + i] * ip;
+      else v = B[idx] - buf[n + i] * ip * buf[j];
+      B[idx] = v;
+    }
+    g.sync();
+  }
+}
+
+// Exact solve on the coarsest grid: e = A^-1 f.
+template <typename T, typename F, typename G>
+__device__ __forceinline__ void coarse_solve(const G& g, const Level<T, F>& L) {
+  const int n = L.m * L.m;
+  for (int r = g.rank(); r < n; r += g.size()) {
+    const T* row = L.cinv + r * n;
+    T s = T(0);
+    for (int c = 0; c < n; ++c) s += row[c] * L.f[c];
+    L.e[r] = s;
+  }
+  g.sync();
+}
+
 // Symmetric multigrid cycle e_0 <- B f_0: on each level red-black then
 // black-red Gauss-Seidel (nu sweep pairs on the finest level, nuc on the
 // coarser ones) around the coarse correction, which itself is
 // gamma cycles on the next level (gamma = 1: V-cycle, 2: W-cycle; one visit
-// when the next level is the 1 x 1 grid, solved exactly).  Written as a loop
+// when the next level is the coarsest grid, solved exactly).  Written as a loop
 // over an explicit per-level visit count (no recursion: the device stack
 // stays fixed).  With adjoint pre- and post-smoothing the cycle is a
 // symmetric positive definite preconditioner for any gamma.
@@ -279,11 +342,7 @@ __device__ void mg_cycle(const G& g, const Level<T, F>* lev, int nl, int gamma, 
       ++l;
       continue;
     }
-    {  // coarsest (1 x 1): exact
-      const Level<T, F>& Lc = lev[l];
-      if (g.rank() == 0) Lc.e[0] = Lc.f[0] * Lc.invd[0];
-      g.sync();
-    }
+    coarse_solve(g, lev[l]);  // coarsest grid: exact
     // ascend until a level wants another visit of the level below it
     bool revisit = false;
     while (l > 0) {
@@ -314,11 +373,7 @@ __device__ void vcycle(const G& g, const Level<T, F>* lev, int nl) {
     rb_sweep(g, lev[l], 1, false);
     restrict_residual(g, lev[l], lev[l + 1]);
   }
-  {
-    const Level<T, F>& Lc = lev[nl - 1];  // 1 x 1
-    if (g.rank() == 0) Lc.e[0] = Lc.f[0] * Lc.invd[0];
-    g.sync();
-  }
+  coarse_solve(g, lev[nl - 1]);  // coarsest grid: exact
   for (int l = nl - 2; l >= 0; --l) {
     prolong_add(g, lev[l + 1], lev[l]);
     rb_sweep(g, lev[l], 1, false);
@@ -620,7 +675,12 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
           gs.pv = reinterpret_cast<T*>(take(nlv * sizeof(T)));
           gs.qv = reinterpret_cast<T*>(take(nlv * sizeof(T)));
         }
-        if (ml == 1) break;
+        L.cinv = L.cbuf = nullptr;
+        if (ml <= kCoarseSide) {
+          L.cinv = reinterpret_cast<T*>(take(nlv * nlv * sizeof(T)));
+          L.cbuf = reinterpret_cast<T*>(take((2 * nlv + 1) * sizeof(T)));
+          break;
+        }
       }
       gs.nl = l + 1;
       gs.op.m = m;
@@ -716,6 +776,7 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
     build_coarse(g, lev[l - 1], lev[l]);
     build_diag<true>(g, lev[l]);
   }
+  build_coarse_inverse(g, lev[nl - 1]);
   // ---- solve ----
   int status = 1, iters = 0;
   if constexpr (PREC == 3) {
