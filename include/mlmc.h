@@ -79,7 +79,8 @@ typedef struct mlmc_model {
   int32_t cgv;                 /* 0: plain coupling, coarse sample = fine fields at the even
                                      cells (offset (0,0)) composed on the coarse layer map;
                                   1: Coarse Grid Variates, Eq. 4.1 / 4.2, the four offsets
-                                     (0,0), (1,0), (0,1), (1,1) of the per-layer fields;
+                                     (0,0), (1,0), (0,1), (1,1) of the per-layer fields (3-D:
+                                     the eight offsets, ox fastest);
                                   2: Coarse Grid Variates on the composed k */
   int32_t prec;                /* 0: FP64 throughout;
                                   1: FP32 multigrid-preconditioned CG inside FP64 iterative
@@ -179,8 +180,8 @@ MLMC_API int mlmc_level_batch_host(mlmc_ctx* ctx, int level, int64_t first, int6
 /* Adaptive MLMC estimate with sampling error sum_l V_l/N_l <= eps^2/2 (the
  * even split of Eq. 3.7): n_pilot samples per level, then repeated top-ups
  * to N_l = ceil(2 eps^-2 sqrt(V_l/C_l) sum_k sqrt(V_k C_k)) until no level
- * needs more (at most 10 rounds).  cost_model 0: C_l = m_l^2 (1 + n_coarse/4)
- * with n_coarse = 0 at level 0, 1 plain, 4 CGV (deterministic); 1: C_l =
+ * needs more (at most 10 rounds).  cost_model 0: C_l = m_l^d (1 + n_coarse/2^d)
+ * with n_coarse = 0 at level 0, 1 plain, 2^d CGV (deterministic); 1: C_l =
  * measured seconds per sample of the pilot.  out: host pointer, required. */
 MLMC_API int mlmc_estimate(mlmc_ctx* ctx, double eps, uint64_t seed, int32_t n_pilot,
                   int32_t cost_model, mlmc_estimate_out* out);
