@@ -194,7 +194,7 @@ def config_block(args, d):
             "eps": d["eps"], "sigma2": d["sigma2"][0], "lambda": d["lam"][0], "layers": d["n_layers"],
             "dim": d.get("dim", 2), "norm_r": d["norm_r"],
             "cgv": d["cgv"], "prec": PREC_NAMES[d["prec"]],
-            "solver_tol": d["tol"], "seed": args.seed, "cost_model": "deterministic m_l^2 (1 + n_coarse/4)",
+            "solver_tol": d["tol"], "seed": args.seed, "cost_model": "deterministic m_l^d (1 + n_coarse/2^d)",
             "l2": "flushed between steps (256 MB device write)", "parallelism": "replicas%d" % args.gpus}
 
 
