@@ -226,6 +226,7 @@ typedef struct mlmc_tune_report {
   int32_t nu[MLMC_MAX_LEVELS];                 /* red-black sweep pairs per smoothing, finest grid */
   int32_t nu_coarse[MLMC_MAX_LEVELS];          /* the same on the coarser grids */
   double inner_tol[MLMC_MAX_LEVELS];           /* prec 1, 2: relative tolerance of the FP32 inner solves */
+  int32_t reliable[MLMC_MAX_LEVELS];           /* prec 1, 2: 1 = reliable updates (mlmc_set_solver) */
   int32_t candidates[MLMC_MAX_LEVELS];         /* plans timed */
   double ms_default[MLMC_MAX_LEVELS];          /* ms per sample, default plan */
   double ms_best[MLMC_MAX_LEVELS];             /* ms per sample, chosen plan */
@@ -236,7 +237,8 @@ typedef struct mlmc_tune_report {
  * or 8 blocks per system; all resident blocks or one per SM; for the
  * fastest of those, W-cycles, two smoothing sweep pairs on every grid, two
  * or three on the finest grid with one on the coarser ones, and with prec 1
- * or 2 an FP32 inner tolerance of 1e-4, 1e-5 or 1e-6) on a probe batch of
+ * or 2 an FP32 inner tolerance of 1e-4, 1e-5 or 1e-6, and reliable updates
+ * after a residual drop of 1e-2 or 1e-3) on a probe batch of
  * each level (samples from index 2^40 on, so no sample of real use is
  * consumed) and keeps the fastest for that level's solves.  A plan changes
  * the path of the iteration (cycle, smoothing, inner tolerance, summation
@@ -253,6 +255,19 @@ MLMC_API int mlmc_autotune(mlmc_ctx* ctx, uint64_t seed, mlmc_tune_report* rep);
  * (V-cycle, nu = 1).  Errors: MLMC_ERR_ARG. */
 MLMC_API int mlmc_set_launch(mlmc_ctx* ctx, int level, int32_t mode, int32_t threads, int32_t cluster,
                              int32_t gamma, int32_t nu);
+
+/* Mixed precision (prec 1, 2) of one level's solver, on top of its launch
+ * plan (the autotuned or set one, else the default): reliable = 0 runs FP32
+ * multigrid-preconditioned CG solves to the relative tolerance inner_tol
+ * inside FP64 iterative refinement (each refinement sweep restarts the CG);
+ * reliable = 1 runs one FP32 CG with reliable updates (Sleijpen and van der
+ * Vorst, 1996): whenever its residual has fallen by inner_tol since the last
+ * update, or after 16 iterations, the correction is added to the FP64
+ * solution and the FP64 residual b - A x replaces the FP32 one, and the CG
+ * carries on with its search direction.  Both stop on the same FP64 test
+ * ||b - A x|| < tol ||b||.  inner_tol in (0, 0.5]; reliable = 1 needs a 2-D
+ * context.  Errors: MLMC_ERR_ARG. */
+MLMC_API int mlmc_set_solver(mlmc_ctx* ctx, int level, int32_t reliable, double inner_tol);
 
 /* Padding of level `level` for the first embedding draw (pair 0): *M_out = M,
  * and the smallest / largest raw embedding eigenvalue before clipping (host

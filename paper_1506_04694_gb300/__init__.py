@@ -71,7 +71,7 @@ class TuneReport(ctypes.Structure):
                 ("cap_blocks_per_sm", ctypes.c_int32 * MAX_LEVELS), ("cluster", ctypes.c_int32 * MAX_LEVELS),
                 ("gamma", ctypes.c_int32 * MAX_LEVELS), ("nu", ctypes.c_int32 * MAX_LEVELS),
                 ("nu_coarse", ctypes.c_int32 * MAX_LEVELS),
-                ("inner_tol", ctypes.c_double * MAX_LEVELS),
+                ("inner_tol", ctypes.c_double * MAX_LEVELS), ("reliable", ctypes.c_int32 * MAX_LEVELS),
                 ("candidates", ctypes.c_int32 * MAX_LEVELS),
                 ("ms_default", ctypes.c_double * MAX_LEVELS), ("ms_best", ctypes.c_double * MAX_LEVELS)]
 
@@ -103,6 +103,7 @@ EXPORTS = {
     "mlmc_resume": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "mlmc_set_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "mlmc_set_solver": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_double]),
     "mlmc_ce_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "mlmc_philox_words": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
@@ -289,7 +290,7 @@ class Context:
         L = self.model.L + 1
         return [{"threads": r.threads[i], "warp": r.warp[i], "cap_blocks_per_sm": r.cap_blocks_per_sm[i],
                  "cluster": r.cluster[i], "gamma": r.gamma[i], "nu": r.nu[i], "nu_coarse": r.nu_coarse[i],
-                 "inner_tol": r.inner_tol[i],
+                 "inner_tol": r.inner_tol[i], "reliable": r.reliable[i],
                  "candidates": r.candidates[i], "ms_per_sample_default": r.ms_default[i],
                  "ms_per_sample_best": r.ms_best[i]} for i in range(L)]
 
@@ -310,6 +311,11 @@ class Context:
         """mlmc_set_launch: fix a level's solver launch (0 block, 1 warp, 2 cluster; <0 default),
         its multigrid cycle (gamma 1 V, 2 W) and smoothing sweep pairs nu."""
         _check(lib().mlmc_set_launch(self._h, level, mode, threads, cluster, gamma, nu), allow_failed=False)
+
+    def set_solver(self, level, reliable, inner_tol):
+        """mlmc_set_solver: mixed-precision scheme of a level (reliable updates or restarted
+        refinement) and its FP32 tolerance."""
+        _check(lib().mlmc_set_solver(self._h, level, reliable, inner_tol), allow_failed=False)
 
     def ce_info(self, level):
         M = ctypes.c_int32()

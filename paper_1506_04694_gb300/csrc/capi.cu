@@ -564,6 +564,7 @@ int multilevel_impl(mlmc_ctx* c, int n_levels, const int64_t* first, const int64
       if (c->tuned_ok[l]) std::memcpy(&tol_bits, &c->tuned[l].inner_tol, sizeof tol_bits);
       key.push_back(tol_bits);
       key.push_back(c->tuned_ok[l] ? c->tuned[l].nu_coarse : -1);
+      key.push_back(c->tuned_ok[l] ? c->tuned[l].reliable : -1);
     }
     for (int l = 0; l < n_levels; ++l) {
       key.push_back(first[l]);
@@ -994,7 +995,7 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
       if ((err = run_fields(c, l, a.first, n, seed))) break;
       a.g = c->g.p;
     }
-    SolvePlan cand[24];
+    SolvePlan cand[28];
     int nk = dim_of(md) == 3 ? solve3_plan_candidates(m, md.prec, cand, 16) : solve_plan_candidates(m, md.prec, cand, 16);
     float best = 1e30f, def_ms = 0.f;
     int best_k = -1;
@@ -1062,6 +1063,19 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
         }
         ++nk;
       }
+      // one FP32 CG with reliable updates instead of restarted refinement (2-D)
+      for (double it : {1e-2, 1e-3}) {
+        if (err || dim_of(md) == 3) break;
+        cand[nk] = base;
+        cand[nk].reliable = 1;
+        cand[nk].inner_tol = it;
+        const float ms = time_plan(cand[nk]);
+        if (ms < best) {
+          best = ms;
+          best_k = nk;
+        }
+        ++nk;
+      }
     }
     if (err || best_k < 0) break;
     c->tuned[l] = cand[best_k];
@@ -1075,6 +1089,7 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
       rep->nu[l] = cand[best_k].nu;
       rep->nu_coarse[l] = cand[best_k].nu_coarse > 0 ? cand[best_k].nu_coarse : cand[best_k].nu;
       rep->inner_tol[l] = cand[best_k].inner_tol;
+      rep->reliable[l] = cand[best_k].reliable;
       rep->candidates[l] = nk;
       rep->ms_default[l] = def_ms / n;
       rep->ms_best[l] = best / n;
@@ -1121,6 +1136,23 @@ int mlmc_set_launch(mlmc_ctx* c, int level, int32_t mode, int32_t threads, int32
   P.nu = nu;
   c->tuned[level] = P;
   c->tuned_ok[level] = true;
+  return 0;
+}
+
+int mlmc_set_solver(mlmc_ctx* c, int level, int32_t reliable, double inner_tol) {
+  if (!c || level < 0 || level > c->model.L) return fail(MLMC_ERR_ARG, "bad context or level");
+  if ((reliable != 0 && reliable != 1) || !(inner_tol > 0 && inner_tol <= 0.5))
+    return fail(MLMC_ERR_ARG, "reliable must be 0 or 1 and inner_tol in (0, 0.5]");
+  if (reliable && dim_of(c->model) == 3) return fail(MLMC_ERR_ARG, "reliable updates are 2-D only");
+  CUDA_TRY(cudaSetDevice(c->device));
+  if (!c->tuned_ok[level]) {
+    SolvePlan P;
+    if (plan_of(c->model, c->model.m0 << level, &P)) return fail(MLMC_ERR_CUDA, "launch plan query failed");
+    c->tuned[level] = P;
+    c->tuned_ok[level] = true;
+  }
+  c->tuned[level].reliable = reliable;
+  c->tuned[level].inner_tol = inner_tol;
   return 0;
 }
 

@@ -82,7 +82,8 @@ struct SolveArgs {
   int max_it;
   int problem;         // 2: outflow (Model Problem 2); 1: local average, f = 1, Dirichlet 0 (Model Problem 1)
   double box[4];       // problem 1: x0, x1, y0, y1 of D*
-  double inner_tol;    // mixed: relative tolerance of each FP32 inner solve
+  double inner_tol;    // mixed: relative tolerance of each FP32 inner solve (reliable: the update trigger)
+  int reliable;        // mixed: FP32 CG with reliable updates instead of restarted refinement
   int mg_gamma;        // multigrid cycle: 1 V, 2 W (set from the launch plan)
   int mg_nu;           // red-black sweep pairs before and after the coarse correction
   int mg_nu_coarse;    // the same on the coarser levels (0: mg_nu)
@@ -116,6 +117,7 @@ struct SolvePlan {
   int nu;                // smoothing: red-black sweep pairs before and after the coarse correction
   int nu_coarse;         // the same on the coarser levels (0: nu)
   double inner_tol;      // mixed precision: relative tolerance of each FP32 inner solve
+  int reliable;          // mixed precision: reliable updates (inner_tol = residual drop between updates)
 };
 
 size_t solve_ws_bytes(int m, int prec);

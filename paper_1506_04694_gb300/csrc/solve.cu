@@ -820,8 +820,121 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
     bb = g.sum(bb, red64, par);
     double rr = bb;
     const double thr = a.tol * a.tol * bb;
+    // r64 = b - A64 x64 and its squared norm
+    auto residual64 = [&]() -> double {
+      double s2 = 0.0;
+      for (int c = g.rank(); c < n; c += g.size()) {
+        const int j = c / m, i = c - j * m;
+        const int rf = j * (m + 1) + i;
+        const double tw = (double)A.tx[rf], te = (double)A.tx[rf + 1];
+        const double ts = (double)A.ty[c], tn = (double)A.ty[c + m];
+        double ax = ((tw + te) + (ts + tn)) * x64[c];
+        if (i > 0) ax -= tw * x64[c - 1];
+        if (i < m - 1) ax -= te * x64[c + 1];
+        if (j > 0) ax -= ts * x64[c - m];
+        if (j < m - 1) ax -= tn * x64[c + m];
+        const double bv = a.problem == 1 ? fmid : (i == 0 ? tw : 0.0);
+        const double rv = bv - ax;
+        r64[c] = rv;
+        s2 += rv * rv;
+      }
+      return g.sum(s2, red64, par);
+    };
     int sweeps = 0;
-    while (true) {
+    if (a.reliable) {
+      // FP32 CG with reliable updates (Sleijpen and van der Vorst, 1996): the
+      // FP32 recursion runs on the correction, in units of the last true
+      // residual norm; once its residual has fallen by inner_tol (or every 16
+      // iterations) the correction is added to the FP64 solution, the true
+      // residual is recomputed in FP64 and replaces the FP32 one, and the
+      // search direction carries on (the Krylov recursion is not restarted,
+      // unlike the refinement loop below).  Same FP64 stopping test.
+      status = 1;
+      if (rr <= thr) status = 0;
+      double scl = sqrt(rr);
+      T rr32 = T(0);
+      for (int c = g.rank(); c < n; c += g.size()) {
+        const T v = (T)(r64[c] / scl);
+        L0.f[c] = v;
+        xv[c] = T(0);
+        rr32 += v * v;
+      }
+      rr32 = g.sum(rr32, red, par);
+      g.sync();
+      T rr_ref = rr32;
+      const T d2 = (T)(a.inner_tol * a.inner_tol);
+      const int nuc = a.mg_nu_coarse;
+      T rz = T(0);
+      if (status != 0) {
+        precond(g, lev, nl, a.mg_gamma, a.mg_nu, nuc);
+        for (int c = g.rank(); c < n; c += g.size()) {
+          pv[c] = L0.e[c];
+          rz += L0.f[c] * L0.e[c];
+        }
+        rz = g.sum(rz, red, par);
+      }
+      int since = 0;
+      while (status != 0 && iters < a.max_it) {
+        ++iters;
+        ++since;
+        T pq = T(0);
+        for (int c = g.rank(); c < n; c += g.size()) {
+          const int j = c / m, i = c - j * m;
+          const T v = apply_row(A, pv, i, j);
+          qv[c] = v;
+          pq += pv[c] * v;
+        }
+        pq = g.sum(pq, red, par);
+        if (!(pq > T(0)) || !isfinite(pq) || !isfinite(rz)) {
+          status = 2;
+          break;
+        }
+        const T alpha = rz / pq;
+        rr32 = T(0);
+        for (int c = g.rank(); c < n; c += g.size()) {
+          xv[c] += alpha * pv[c];
+          const T rv = L0.f[c] - alpha * qv[c];
+          L0.f[c] = rv;
+          rr32 += rv * rv;
+        }
+        rr32 = g.sum(rr32, red, par);
+        if ((double)rr32 * scl * scl <= thr || rr32 <= d2 * rr_ref || since >= 16) {  // reliable update
+          for (int c = g.rank(); c < n; c += g.size()) x64[c] += scl * (double)xv[c];
+          g.sync();
+          rr = residual64();
+          ++sweeps;
+          if (rr <= thr) {
+            status = 0;
+            break;
+          }
+          const double scl_new = sqrt(rr);
+          const T ratio = (T)(scl / scl_new);
+          rr32 = T(0);
+          for (int c = g.rank(); c < n; c += g.size()) {
+            const T v = (T)(r64[c] / scl_new);
+            L0.f[c] = v;
+            xv[c] = T(0);
+            pv[c] *= ratio;
+            rr32 += v * v;
+          }
+          rr32 = g.sum(rr32, red, par);
+          g.sync();
+          rz *= ratio * ratio;
+          scl = scl_new;
+          rr_ref = rr32;
+          since = 0;
+        }
+        precond(g, lev, nl, a.mg_gamma, a.mg_nu, nuc);
+        T rzn = T(0);
+        for (int c = g.rank(); c < n; c += g.size()) rzn += L0.f[c] * L0.e[c];
+        rzn = g.sum(rzn, red, par);
+        const T beta = rzn / rz;
+        rz = rzn;
+        for (int c = g.rank(); c < n; c += g.size()) pv[c] = L0.e[c] + beta * pv[c];
+        g.sync();
+      }
+    }
+    while (!a.reliable) {
       if (rr <= thr) {
         status = 0;
         break;
@@ -849,23 +962,7 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
       // x64 += scl * d, then r64 = b - A64 x64 (FP64)
       for (int c = g.rank(); c < n; c += g.size()) x64[c] += scl * (double)xv[c];
       g.sync();
-      rr = 0.0;
-      for (int c = g.rank(); c < n; c += g.size()) {
-        const int j = c / m, i = c - j * m;
-        const int rf = j * (m + 1) + i;
-        const double tw = (double)A.tx[rf], te = (double)A.tx[rf + 1];
-        const double ts = (double)A.ty[c], tn = (double)A.ty[c + m];
-        double ax = ((tw + te) + (ts + tn)) * x64[c];
-        if (i > 0) ax -= tw * x64[c - 1];
-        if (i < m - 1) ax -= te * x64[c + 1];
-        if (j > 0) ax -= ts * x64[c - m];
-        if (j < m - 1) ax -= tn * x64[c + m];
-        const double bv = a.problem == 1 ? fmid : (i == 0 ? tw : 0.0);
-        const double rv = bv - ax;
-        r64[c] = rv;
-        rr += rv * rv;
-      }
-      rr = g.sum(rr, red64, par);
+      rr = residual64();
       if (it == 0 && st_in != 0) {  // inner solver made no progress
         status = 2;
         break;
@@ -968,6 +1065,7 @@ static int plan_fill(int m, int threads, int cluster, SolvePlan* P) {
   P->nu = 1;
   P->nu_coarse = 0;
   P->inner_tol = 1e-5;
+  P->reliable = 0;
   cudaFuncSetAttribute(solve_kernel<PREC, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, solve_kernel<PREC, MODE>, P->threads, P->smem_bytes) !=
@@ -1071,6 +1169,7 @@ int solve_launch(const SolveArgs& a, int prec, const SolvePlan& P, int n_blocks,
   b.mg_nu = P.nu;
   b.mg_nu_coarse = P.nu_coarse;
   b.inner_tol = P.inner_tol;
+  b.reliable = P.reliable;
   if (P.cluster) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];

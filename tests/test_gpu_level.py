@@ -93,6 +93,37 @@ def test_fp64_cg_fp32_multigrid(cgv, level, n):
     assert it3.sum() <= 1.3 * it0.sum() + n
 
 
+@pytest.mark.parametrize("prec,mode,threads,cluster", [(1, 1, 0, 0), (1, 0, 256, 0), (1, 2, 512, 4), (2, 0, 512, 0)])
+def test_reliable_updates(prec, mode, threads, cluster):
+    # one FP32 CG with reliable FP64 residual replacement instead of
+    # restarted refinement: the same FP64 stopping test, so the same Q to the
+    # tolerance, in every launch mode, and no more iterations
+    torch, pk = need_gpu()
+    d = workloads.workload("lognormal_2layer_cgv_16to512", prec=prec, tol=1e-10, L=3)
+    model = darcy.Model.from_dict(d)
+    level, n = 3, 6
+    out = {}
+    for reliable, itol in ((0, 1e-5), (1, 1e-2), (1, 1e-3)):
+        with pk.Context(d) as ctx:
+            ctx.set_launch(level, mode, threads, cluster, 1, 2)
+            ctx.set_solver(level, reliable, itol)
+            qf = torch.empty(n, dtype=torch.float64, device="cuda")
+            qg = torch.empty_like(qf)
+            it = torch.empty(n, dtype=torch.int32, device="cuda")
+            s = ctx.level_batch(level, n, 5, qf=qf, qc_cgv=qg, iters=it)
+            assert s["n"] == n and s["n_failed"] == 0
+            out[(reliable, itol)] = (qf.cpu().numpy(), qg.cpu().numpy(), int(it.sum()))
+    for i in range(n):
+        r = darcy.sample(model, 5, level, i)
+        for qf, qg, _ in out.values():
+            assert abs(qf[i] - r["qf"]) <= RTOL_MIX * abs(r["qf"])
+            assert abs(qg[i] - r["qc_cgv"]) <= RTOL_MIX * abs(r["qc_cgv"])
+    assert min(out[(1, 1e-2)][2], out[(1, 1e-3)][2]) <= out[(0, 1e-5)][2]
+    with pk.Context(d) as ctx:
+        with pytest.raises(pk.MLMCError):
+            ctx.set_solver(level, 1, 0.0)
+
+
 @pytest.mark.parametrize("level,n", [(0, 20), (1, 8), (2, 4)])
 def test_bf16_faces_in_multigrid(level, n):
     # prec 2: BF16 faces only inside the multigrid preconditioner; the FP64
