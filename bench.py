@@ -20,6 +20,7 @@ import json
 import math
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -97,10 +98,10 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, path=None):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+        self.path = path or os.path.join(tempfile.gettempdir(), "mlmc_clocks_%d.csv" % os.getpid())
 
     def start(self):
         try:
@@ -284,6 +285,8 @@ def main():
                     help="with --compare: add the mixed CGV arm with BF16 multigrid faces (prec 2)")
     ap.add_argument("--fp64cg-arm", action="store_true",
                     help="with --compare: add the CGV arm with FP64 CG around an FP32 multigrid (prec 3)")
+    ap.add_argument("--clocks-out", default=None,
+                    help="file for the raw nvidia-smi clock samples of the timed region (default: a temp file)")
     ap.add_argument("--prec", type=int, default=None, choices=[0, 1, 2, 3],
                     help="override the workload's solver precision mode")
     args = ap.parse_args()
@@ -331,7 +334,7 @@ def main():
 
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     phys = vis.split(",")[local] if vis else str(local)
-    clocks = ClockSampler(phys)
+    clocks = ClockSampler(phys, args.clocks_out)
     clocks.start()
     barrier()
     torch.cuda.synchronize(dev)
