@@ -204,8 +204,11 @@ MLMC_API int mlmc_checkpoint(mlmc_ctx* ctx, const char* path);
 MLMC_API int mlmc_resume(mlmc_ctx* ctx, const char* path);
 
 /* Levels 0 .. n_levels-1 in one call: samples first[l] .. first[l]+n[l]-1 of
- * each level l (n[l] may be 0), queued back to back on the context stream
- * with a single host synchronisation at the end; sums[l] (host array of
+ * each level l (n[l] may be 0), the levels side by side on streams of their
+ * own (forked from and joined back into the context stream; one after
+ * another on the context stream while profiling is on), each with work
+ * buffers of its own that the context keeps between calls, with a single
+ * host synchronisation at the end; sums[l] (host array of
  * n_levels) receives the level sums of Eq. 3.6 / Eq. 4.2 as in
  * mlmc_level_batch().  use_graph != 0 captures the whole queue into one CUDA
  * graph (kept and relaunched while the arguments repeat); it needs a context

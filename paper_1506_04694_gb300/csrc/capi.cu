@@ -80,6 +80,15 @@ struct LevelTable {
 
 constexpr size_t kChunkBudget = size_t(2) << 30;  // bytes of per-sample buffers per chunk
 
+// Work buffers of a chain of chunk launches: the embedding intermediate W,
+// the fields g, the solver workspace ws and the per-system outputs.
+struct WorkBufs {
+  Buf W, g, ws, qsys, itsys;
+  void release() {
+    for (Buf* b : {&W, &g, &ws, &qsys, &itsys}) b->release();
+  }
+};
+
 }  // namespace
 
 // A pair of events bracketing one stage (profiling).
@@ -98,6 +107,7 @@ struct mlmc_ctx {
   int device = 0;
   cudaStream_t st = nullptr;
   mlmc_model model{};
+
   int nsm = 0;
   std::vector<LevelTable> lev;
   // layers onto embedding draws: layer t is part part_of[t] (0 Re, 1 Im) of
@@ -105,12 +115,22 @@ struct mlmc_ctx {
   int n_draws = 0;
   int pair_of[MLMC_MAX_LAYERS], part_of[MLMC_MAX_LAYERS];
   double pair_sigma2[MLMC_MAX_LAYERS], pair_lam[MLMC_MAX_LAYERS];
-  Buf W, g, ws, qsys, itsys, oqf, oqc, oqg, oit, sums, itacc, g64, bm;
+  Buf oqf, oqc, oqg, oit, sums, itacc, g64, bm;
+  // work buffers and stream of the chain being queued: `misc` on the context
+  // stream for single-level calls and set-up, a level's own set on its own
+  // stream when the levels of a round run side by side
+  WorkBufs misc;
+  WorkBufs* wb = &misc;
+  cudaStream_t wst = nullptr;
+  cudaStream_t lst[MLMC_MAX_LEVELS] = {};
+  cudaEvent_t lev_done[MLMC_MAX_LEVELS] = {};
+  cudaEvent_t fork = nullptr;
   bool prof_on = false;
   mlmc_profile_stats prof{};
   // per-level slots of the multilevel batch (outputs, sums, iteration counters)
   struct Slot {
     Buf qf, qc, qg, sums, itacc;
+    WorkBufs wb;
   } slot[MLMC_MAX_LEVELS];
   HostLevel* host = nullptr;  // pinned, MLMC_MAX_LEVELS + 1 entries (last: single-level calls)
   // launch plans chosen by mlmc_autotune(), per level
@@ -130,6 +150,24 @@ struct mlmc_ctx {
   cudaGraphExec_t gexec = nullptr;
   std::vector<int64_t> gkey;
 };
+
+namespace {
+// Queue the next chunk launches with these buffers on this stream (restored
+// on scope exit).
+struct UseBufs {
+  mlmc_ctx* c;
+  WorkBufs* wb0;
+  cudaStream_t st0;
+  UseBufs(mlmc_ctx* c_, WorkBufs* wb, cudaStream_t st) : c(c_), wb0(c_->wb), st0(c_->wst) {
+    c->wb = wb;
+    c->wst = st;
+  }
+  ~UseBufs() {
+    c->wb = wb0;
+    c->wst = st0;
+  }
+};
+}  // namespace
 
 namespace {
 
@@ -262,13 +300,14 @@ SolveArgs base_args(const mlmc_ctx* c, int level, uint64_t seed, int64_t first) 
 // prec 1 and 2 sample the fields in FP32; prec 0 and 3 in FP64.
 static bool fields_f32(const mlmc_model& md) { return md.prec == 1 || md.prec == 2; }
 
-// Fields of chunk samples [first, first + n) of `level` into c->g.
+// Fields of chunk samples [first, first + n) of `level` into the selected work buffers (c->wb).
 int run_fields(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t seed) {
   const mlmc_model& md = c->model;
   const LevelTable& LT = c->lev[level];
   const bool f32 = fields_f32(md);
-  if (int e = c->W.ensure(ce_w_bytes_per_sample(LT.m, max_M(c, level), f32, dim_of(md)) * n)) return e;
-  if (int e = c->g.ensure((size_t)n * md.n_layers * cells_of(md, LT.m) * (f32 ? 4 : 8))) return e;
+  WorkBufs& B = *c->wb;
+  if (int e = B.W.ensure(ce_w_bytes_per_sample(LT.m, max_M(c, level), f32, dim_of(md)) * n)) return e;
+  if (int e = B.g.ensure((size_t)n * md.n_layers * cells_of(md, LT.m) * (f32 ? 4 : 8))) return e;
   for (int f = 0; f < c->n_draws; ++f) {  // one draw at a time, W reused
     const PairTable& T = LT.pair[f];
     CeLaunch L;
@@ -290,9 +329,9 @@ int run_fields(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t seed) 
     L.mu_im = L.t_im >= 0 ? md.mu[L.t_im] : 0.0;
     int r;
     if (f32)
-      r = ce_sample_fp32(L, T.s32.as<float>(), T.tw32.p, c->W.p, c->g.as<float>(), c->st);
+      r = ce_sample_fp32(L, T.s32.as<float>(), T.tw32.p, B.W.p, B.g.as<float>(), c->wst);
     else
-      r = ce_sample_fp64(L, T.s64.as<double>(), T.tw64.p, c->W.p, c->g.as<double>(), c->st);
+      r = ce_sample_fp64(L, T.s64.as<double>(), T.tw64.p, B.W.p, B.g.as<double>(), c->wst);
     if (r) return fail(MLMC_ERR_CUDA, std::string("field kernels: ") + cudaGetErrorString(cudaGetLastError()));
   }
   return 0;
@@ -315,7 +354,7 @@ int64_t chunk_samples(const mlmc_ctx* c, int level) {
 // resident blocks for very large grids).
 constexpr size_t kWsBudget = size_t(16) << 30;
 
-// Solve the systems of one chunk; results into c->qsys / c->itsys.
+// Solve the systems of one chunk; results into the selected work buffers (qsys, itsys).
 int run_solves(mlmc_ctx* c, SolveArgs a, int64_t n_samples, int nc, int64_t max_rows,
                const SolvePlan* plan = nullptr) {
   const int prec = c->model.prec;
@@ -328,18 +367,19 @@ int run_solves(mlmc_ctx* c, SolveArgs a, int64_t n_samples, int nc, int64_t max_
   const int64_t cap = P.use_smem ? 0 : (int64_t)(kWsBudget / P.ws_stride);
   int64_t nb = 0;
   const int64_t groups = solve_groups(P, n_sys, c->nsm, cap, &nb);
+  WorkBufs& B = *c->wb;
   if (!P.use_smem) {
-    if (int e = c->ws.ensure(P.ws_stride * groups)) return e;
-    a.ws = c->ws.as<unsigned char>();
+    if (int e = B.ws.ensure(P.ws_stride * groups)) return e;
+    a.ws = B.ws.as<unsigned char>();
   } else if (P.ws64_stride) {
-    if (int e = c->ws.ensure(P.ws64_stride * groups)) return e;
-    a.ws64 = c->ws.as<unsigned char>();
+    if (int e = B.ws.ensure(P.ws64_stride * groups)) return e;
+    a.ws64 = B.ws.as<unsigned char>();
   }
-  if (int e = c->qsys.ensure((size_t)std::max<int64_t>(n_sys, max_rows) * 8)) return e;
-  if (int e = c->itsys.ensure((size_t)std::max<int64_t>(n_sys, max_rows) * 4)) return e;
-  a.q = c->qsys.as<double>();
-  a.iters = c->itsys.as<int32_t>();
-  const int lr = dim_of(c->model) == 3 ? solve3_launch(a, prec, P, (int)nb, c->st) : solve_launch(a, prec, P, (int)nb, c->st);
+  if (int e = B.qsys.ensure((size_t)std::max<int64_t>(n_sys, max_rows) * 8)) return e;
+  if (int e = B.itsys.ensure((size_t)std::max<int64_t>(n_sys, max_rows) * 4)) return e;
+  a.q = B.qsys.as<double>();
+  a.iters = B.itsys.as<int32_t>();
+  const int lr = dim_of(c->model) == 3 ? solve3_launch(a, prec, P, (int)nb, c->wst) : solve_launch(a, prec, P, (int)nb, c->wst);
   if (lr) return fail(MLMC_ERR_CUDA, std::string("solve kernel: ") + cudaGetErrorString(cudaGetLastError()));
   return 0;
 }
@@ -353,11 +393,11 @@ struct StageTimer {
     if (!c->prof_on) return;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    cudaEventRecord(e0, c->st);
+    cudaEventRecord(e0, c->wst);
   }
   void stop(int launches) {
     if (!c->prof_on) return;
-    cudaEventRecord(e1, c->st);
+    cudaEventRecord(e1, c->wst);
     pending().push_back({stage, launches, e0, e1});
     e0 = e1 = nullptr;
   }
@@ -393,7 +433,7 @@ int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t see
   const int nc = n_coarse(md, level);
   const int64_t chunk = chunk_samples(c, level);
   const SolvePlan* plan = c->tuned_ok[level] ? &c->tuned[level] : nullptr;
-  CUDA_TRY(cudaMemsetAsync(itacc, 0, 2 * sizeof(int64_t), c->st));
+  CUDA_TRY(cudaMemsetAsync(itacc, 0, 2 * sizeof(int64_t), c->wst));
   const int m = md.m0 << level;
   double sumM2 = 0, sumM = 0, fftf = 0;  // transformed points and FFT flops per sample over the draws
   const bool d3 = dim_of(md) == 3;
@@ -410,7 +450,7 @@ int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t see
       StageTimer t(c, 0);
       if (int e = run_fields(c, level, first + c0, cn, seed)) return e;
       t.stop(2 * c->n_draws * (int)((cn + 65534) / 65535));
-      a.g = c->g.p;
+      a.g = c->wb->g.p;
       if (c->prof_on) {
         c->prof.fft_row_points += (double)cn * sumM2;
         c->prof.fft_col_points += (double)cn * sumM * m;
@@ -423,9 +463,9 @@ int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t see
       t.stop(1);
     }
     StageTimer t(c, 2);
-    if (gather_launch(c->qsys.as<double>(), c->itsys.as<int32_t>(), cn, nc, md.cgv, cells_of(md, m),
+    if (gather_launch(c->wb->qsys.as<double>(), c->wb->itsys.as<int32_t>(), cn, nc, md.cgv, cells_of(md, m),
                       cells_of(md, m / 2), qf + c0,
-                      qc + c0, qcg + c0, iters ? iters + c0 : nullptr, itacc, c->st))
+                      qc + c0, qcg + c0, iters ? iters + c0 : nullptr, itacc, c->wst))
       return fail(MLMC_ERR_CUDA, "gather kernel");
     t.stop(1);
     if (c->prof_on) {
@@ -436,12 +476,12 @@ int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t see
   {
     StageTimer t(c, 2);
     if (reduce_launch(qf, qc, qcg, n, md.cgv != 0, itacc, reinterpret_cast<LevelSumsDev*>(sums_dev),
-                      sums_dev + 256, c->st))
+                      sums_dev + 256, c->wst))
       return fail(MLMC_ERR_CUDA, "reduce kernel");
     t.stop(2);
   }
-  CUDA_TRY(cudaMemcpyAsync(&host->s, sums_dev, sizeof(LevelSumsDev), cudaMemcpyDeviceToHost, c->st));
-  CUDA_TRY(cudaMemcpyAsync(host->itc, itacc, sizeof(host->itc), cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(cudaMemcpyAsync(&host->s, sums_dev, sizeof(LevelSumsDev), cudaMemcpyDeviceToHost, c->wst));
+  CUDA_TRY(cudaMemcpyAsync(host->itc, itacc, sizeof(host->itc), cudaMemcpyDeviceToHost, c->wst));
   return 0;
 }
 
@@ -506,9 +546,10 @@ int prepare_level(mlmc_ctx* c, int level, int64_t n) {
   const bool f32 = fields_f32(md);
   const int nc = n_coarse(md, level);
   const int64_t cn = std::min<int64_t>(n, chunk_samples(c, level));
+  WorkBufs& B = c->slot[level].wb;
   if (md.k_kind == 1) {
-    if (int e = c->W.ensure(ce_w_bytes_per_sample(m, max_M(c, level), f32, dim_of(md)) * cn)) return e;
-    if (int e = c->g.ensure((size_t)cn * md.n_layers * cells_of(md, m) * (f32 ? 4 : 8))) return e;
+    if (int e = B.W.ensure(ce_w_bytes_per_sample(m, max_M(c, level), f32, dim_of(md)) * cn)) return e;
+    if (int e = B.g.ensure((size_t)cn * md.n_layers * cells_of(md, m) * (f32 ? 4 : 8))) return e;
   }
   SolvePlan P;
   if (c->tuned_ok[level]) P = c->tuned[level];
@@ -518,10 +559,10 @@ int prepare_level(mlmc_ctx* c, int level, int64_t n) {
     int64_t nb = 0;
     const int64_t groups =
         solve_groups(P, n_sys, c->nsm, P.use_smem ? 0 : (int64_t)(kWsBudget / P.ws_stride), &nb);
-    if (int e = c->ws.ensure((P.use_smem ? P.ws64_stride : P.ws_stride) * groups)) return e;
+    if (int e = B.ws.ensure((P.use_smem ? P.ws64_stride : P.ws_stride) * groups)) return e;
   }
-  if (int e = c->qsys.ensure((size_t)n_sys * 8)) return e;
-  if (int e = c->itsys.ensure((size_t)n_sys * 4)) return e;
+  if (int e = B.qsys.ensure((size_t)n_sys * 8)) return e;
+  if (int e = B.itsys.ensure((size_t)n_sys * 4)) return e;
   auto& S = c->slot[level];
   if (int e = S.qf.ensure((size_t)n * 8)) return e;
   if (int e = S.qc.ensure((size_t)n * 8)) return e;
@@ -539,14 +580,28 @@ int multilevel_impl(mlmc_ctx* c, int n_levels, const int64_t* first, const int64
   for (int l = 0; l < n_levels; ++l)
     if (n[l] > 0)
       if (int e = prepare_level(c, l, n[l])) return e;
+  // the levels run side by side, each on its own stream with its own work
+  // buffers, forked from and joined back into the context stream; with
+  // stage profiling on they run one after another on the context stream, so
+  // that every stage's CUDA-event time is its own
+  const bool side_by_side = !c->prof_on;
   auto enqueue_all = [&]() -> int {
+    if (side_by_side && cudaEventRecord(c->fork, c->st) != cudaSuccess) return fail(MLMC_ERR_CUDA, "fork event");
     for (int l = 0; l < n_levels; ++l) {
       if (n[l] <= 0) continue;
       auto& S = c->slot[l];
-      if (int e = enqueue_level(c, l, first[l], n[l], seed, S.qf.as<double>(), S.qc.as<double>(),
-                                S.qg.as<double>(), nullptr, S.sums.as<unsigned char>(), S.itacc.as<int64_t>(),
-                                c->host + l))
-        return e;
+      const cudaStream_t ls = side_by_side ? c->lst[l] : c->st;
+      if (side_by_side && cudaStreamWaitEvent(ls, c->fork, 0) != cudaSuccess) return fail(MLMC_ERR_CUDA, "fork wait");
+      {
+        UseBufs use(c, &S.wb, ls);
+        if (int e = enqueue_level(c, l, first[l], n[l], seed, S.qf.as<double>(), S.qc.as<double>(),
+                                  S.qg.as<double>(), nullptr, S.sums.as<unsigned char>(), S.itacc.as<int64_t>(),
+                                  c->host + l))
+          return e;
+      }
+      if (side_by_side && (cudaEventRecord(c->lev_done[l], ls) != cudaSuccess ||
+                           cudaStreamWaitEvent(c->st, c->lev_done[l], 0) != cudaSuccess))
+        return fail(MLMC_ERR_CUDA, "join event");
     }
     return 0;
   };
@@ -657,6 +712,7 @@ int mlmc_create(int device, const mlmc_model* model, void* cuda_stream, mlmc_ctx
   mlmc_ctx* c = new mlmc_ctx();
   c->device = device;
   c->st = (cudaStream_t)cuda_stream;
+  c->wst = c->st;
   c->model = *model;
   cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, device);
   c->lev.resize(model->L + 1);
@@ -671,6 +727,12 @@ int mlmc_create(int device, const mlmc_model* model, void* cuda_stream, mlmc_ctx
       bm_tables_build(c->bm.as<double2>(), reinterpret_cast<double*>(c->bm.as<double2>() + kSinCosTab),
                       c->st))
     err = fail(MLMC_ERR_CUDA, "Box-Muller table kernel");
+  if (!err && cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess)
+    err = fail(MLMC_ERR_CUDA, "event");
+  for (int l = 0; l <= model->L && !err; ++l)
+    if (cudaStreamCreateWithFlags(&c->lst[l], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->lev_done[l], cudaEventDisableTiming) != cudaSuccess)
+      err = fail(MLMC_ERR_CUDA, "level stream");
   pair_layers(c);
   for (int l = 0; l <= model->L && !err; ++l) {
     LevelTable& LT = c->lev[l];
@@ -740,11 +802,17 @@ void mlmc_destroy(mlmc_ctx* c) {
       T.tw64.release();
       T.tw32.release();
     }
-  for (Buf* b : {&c->W, &c->g, &c->ws, &c->qsys, &c->itsys, &c->oqf, &c->oqc, &c->oqg, &c->oit,
-                 &c->sums, &c->itacc, &c->g64, &c->bm})
-    b->release();
-  for (auto& S : c->slot)
+  for (Buf* b : {&c->oqf, &c->oqc, &c->oqg, &c->oit, &c->sums, &c->itacc, &c->g64, &c->bm}) b->release();
+  c->misc.release();
+  for (auto& S : c->slot) {
     for (Buf* b : {&S.qf, &S.qc, &S.qg, &S.sums, &S.itacc}) b->release();
+    S.wb.release();
+  }
+  for (int l = 0; l < MLMC_MAX_LEVELS; ++l) {
+    if (c->lst[l]) cudaStreamDestroy(c->lst[l]);
+    if (c->lev_done[l]) cudaEventDestroy(c->lev_done[l]);
+  }
+  if (c->fork) cudaEventDestroy(c->fork);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->host) cudaFreeHost(c->host);
   delete c;
@@ -993,7 +1061,7 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
     SolveArgs a = base_args(c, l, seed, (int64_t)1 << 40);
     if (md.k_kind == 1) {
       if ((err = run_fields(c, l, a.first, n, seed))) break;
-      a.g = c->g.p;
+      a.g = c->wb->g.p;
     }
     SolvePlan cand[28];
     int nk = dim_of(md) == 3 ? solve3_plan_candidates(m, md.prec, cand, 16) : solve_plan_candidates(m, md.prec, cand, 16);
@@ -1202,9 +1270,9 @@ int mlmc_sample_fields(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_
     if (int e = run_fields(c, level, first, n, seed)) return e;
     const int64_t cnt = n * md.n_layers * cells_of(md, m);
     if (fields_f32(md))
-      f32_to_f64_launch(c->g.as<float>(), g, cnt, c->st);
+      f32_to_f64_launch(c->wb->g.as<float>(), g, cnt, c->st);
     else
-      CUDA_TRY(cudaMemcpyAsync(g, c->g.p, cnt * 8, cudaMemcpyDeviceToDevice, c->st));
+      CUDA_TRY(cudaMemcpyAsync(g, c->wb->g.p, cnt * 8, cudaMemcpyDeviceToDevice, c->st));
   }
   CUDA_TRY(cudaStreamSynchronize(c->st));
   return 0;
@@ -1223,8 +1291,8 @@ int mlmc_solve_k(mlmc_ctx* c, int32_t m, int64_t n, const double* k, double* p, 
   a.k = k;
   a.p_out = p;
   if (int e = run_solves(c, a, n, 0, n)) return e;
-  CUDA_TRY(cudaMemcpyAsync(q, c->qsys.p, n * 8, cudaMemcpyDeviceToDevice, c->st));
-  if (iters) CUDA_TRY(cudaMemcpyAsync(iters, c->itsys.p, n * 4, cudaMemcpyDeviceToDevice, c->st));
+  CUDA_TRY(cudaMemcpyAsync(q, c->wb->qsys.p, n * 8, cudaMemcpyDeviceToDevice, c->st));
+  if (iters) CUDA_TRY(cudaMemcpyAsync(iters, c->wb->itsys.p, n * 4, cudaMemcpyDeviceToDevice, c->st));
   CUDA_TRY(cudaStreamSynchronize(c->st));
   return 0;
 }
