@@ -1212,6 +1212,10 @@ int64_t solve_groups(const SolvePlan& P, int64_t n_sys, int nsm, int64_t max_gro
   if (P.cap_blocks_per_sm > 0) g = std::min<int64_t>(g, (int64_t)nsm * P.cap_blocks_per_sm * P.groups_per_block);
   if (max_groups_cap > 0) g = std::min<int64_t>(g, max_groups_cap);
   g = std::max<int64_t>(1, std::min<int64_t>(g, n_sys));
+  // a capped launch that does not hold every system keeps whole blocks of
+  // groups, so no group slot lies beyond the workspace of g groups (slots
+  // past n_sys never run)
+  if (g < n_sys && g > P.groups_per_block) g -= g % P.groups_per_block;
   *n_blocks = P.cluster ? g * P.cluster : (g + P.groups_per_block - 1) / P.groups_per_block;
   return g;
 }

@@ -331,7 +331,7 @@ template <bool MIXED, typename G>
 __device__ void solve_one3(const G& g, const SolveArgs& a, int64_t sys, unsigned char* base,
                            GroupState3<typename std::conditional<MIXED, float, double>::type>& gs,
                            typename std::conditional<MIXED, float, double>::type* red, double* red64, int& par,
-                           int& m_prev) {
+                           int& m_prev, unsigned char* base64) {
   using T = typename std::conditional<MIXED, float, double>::type;
   int64_t sidx;
   int coarse = 0, ox = 0, oy = 0, oz = 0;
@@ -360,8 +360,13 @@ __device__ void solve_one3(const G& g, const SolveArgs& a, int64_t sys, unsigned
         return p;
       };
       if (MIXED) {
-        gs.x64 = reinterpret_cast<double*>(take(n0 * 8));
-        gs.r64 = reinterpret_cast<double*>(take(n0 * 8));
+        if (base64) {  // FP64 refinement vectors in global memory, the rest on chip
+          gs.x64 = reinterpret_cast<double*>(base64);
+          gs.r64 = reinterpret_cast<double*>(base64 + align16_3(n0 * 8));
+        } else {
+          gs.x64 = reinterpret_cast<double*>(take(n0 * 8));
+          gs.r64 = reinterpret_cast<double*>(take(n0 * 8));
+        }
       }
       int l = 0;
       for (int ml = m;; ml >>= 1, ++l) {
@@ -589,14 +594,21 @@ __device__ void solve_one3(const G& g, const SolveArgs& a, int64_t sys, unsigned
   g.sync();
 }
 
-// MODE 0: one block per system; 2: one thread-block cluster per system.
+constexpr int kWarpsPerBlock3 = 4;  // systems per block in warp mode
+
+// MODE 0: one block per system; 1: one warp per system (kWarpsPerBlock3
+// systems per block, no block barriers); 2: one thread-block cluster per
+// system.
 template <bool MIXED, int MODE>
-__global__ void __launch_bounds__(kMaxThreads3, 2) solve3_kernel(SolveArgs a) {
+__global__ void __launch_bounds__(MODE == 1 ? 32 * kWarpsPerBlock3 : kMaxThreads3, MODE == 1 ? 5 : 2)
+    solve3_kernel(SolveArgs a) {
   using T = typename std::conditional<MIXED, float, double>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ GroupState3<T> gstate;
-  __shared__ T red[132];
-  __shared__ double red64[132];
+  constexpr int kGroups = MODE == 1 ? kWarpsPerBlock3 : 1;
+  __shared__ GroupState3<T> gstates[kGroups];
+  GroupState3<T>& gstate = gstates[0];
+  __shared__ T red[MODE == 1 ? 1 : 132];
+  __shared__ double red64[MODE == 1 ? 1 : 132];
   const int64_t n_sys = a.n_samples * (int64_t)(1 + a.n_coarse);
   int par = 0, m_prev = -1;
   if (MODE == 2) {
@@ -606,13 +618,21 @@ __global__ void __launch_bounds__(kMaxThreads3, 2) solve3_kernel(SolveArgs a) {
     const int64_t cid = blockIdx.x / g.nblk, ncl = gridDim.x / g.nblk;
     unsigned char* base = a.ws + (size_t)cid * a.ws_stride;
     for (int64_t sys = cid; sys < n_sys; sys += ncl)
-      solve_one3<MIXED>(g, a, sys, base, gstate, red, red64, par, m_prev);
+      solve_one3<MIXED>(g, a, sys, base, gstate, red, red64, par, m_prev, nullptr);
     cl.sync();  // no block leaves while others may still read its shared memory
     return;
   }
-  unsigned char* base = a.use_smem ? smem_raw : a.ws + (size_t)blockIdx.x * a.ws_stride;
-  for (int64_t sys = blockIdx.x; sys < n_sys; sys += gridDim.x)
-    solve_one3<MIXED>(BlockGroup(), a, sys, base, gstate, red, red64, par, m_prev);
+  const int gid = MODE == 1 ? (int)(threadIdx.x >> 5) : 0;
+  const size_t slot = (size_t)blockIdx.x * kGroups + gid;
+  unsigned char* base = a.use_smem ? smem_raw + (size_t)gid * a.ws_stride : a.ws + slot * a.ws_stride;
+  unsigned char* base64 = a.ws64_stride ? a.ws64 + slot * a.ws64_stride : nullptr;
+  const int64_t stride = (int64_t)gridDim.x * kGroups;
+  for (int64_t sys = (int64_t)blockIdx.x * kGroups + gid; sys < n_sys; sys += stride) {
+    if (MODE == 1)
+      solve_one3<MIXED>(WarpGroup(), a, sys, base, gstates[gid], red, red64, par, m_prev, base64);
+    else
+      solve_one3<MIXED>(BlockGroup(), a, sys, base, gstate, red, red64, par, m_prev, base64);
+  }
 }
 
 const size_t kSmemCap3 = 110 * 1024;
@@ -624,14 +644,19 @@ int plan_fill3(int m, int threads, int cluster, SolvePlan* P) {
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
   std::memset(P, 0, sizeof(*P));
-  P->warp = 0;
+  P->warp = MODE == 1;
   P->cluster = MODE == 2 ? cluster : 0;
-  P->threads = threads;
-  P->groups_per_block = 1;
+  P->threads = MODE == 1 ? 32 * kWarpsPerBlock3 : threads;
+  P->groups_per_block = MODE == 1 ? kWarpsPerBlock3 : 1;
   P->blocks_per_group = MODE == 2 ? cluster : 1;
-  P->ws_stride = (ws + 255) & ~(size_t)255;
-  P->use_smem = MODE != 2 && P->ws_stride <= kSmemCap3;
-  P->smem_bytes = P->use_smem ? P->ws_stride : 0;
+  // prec 1: the FP64 refinement vectors stay in global memory when the rest
+  // of the workspace fits on chip
+  const size_t v64 = MIXED ? 2 * align16_3((size_t)m * m * m * 8) : 0;
+  const size_t chip = ((ws - v64) + 255) & ~(size_t)255;
+  P->use_smem = MODE != 2 && chip * P->groups_per_block <= kSmemCap3;
+  P->ws_stride = P->use_smem ? chip : (ws + 255) & ~(size_t)255;
+  P->ws64_stride = P->use_smem && v64 ? (v64 + 255) & ~(size_t)255 : 0;
+  P->smem_bytes = P->use_smem ? P->ws_stride * P->groups_per_block : 0;
   P->gamma = 1;
   P->nu = 1;
   P->nu_coarse = 0;
@@ -642,7 +667,7 @@ int plan_fill3(int m, int threads, int cluster, SolvePlan* P) {
       cudaSuccess)
     return -1;
   P->blocks_per_sm = nb < 1 ? 1 : nb;
-  P->max_groups = nsm * P->blocks_per_sm;
+  P->max_groups = nsm * P->blocks_per_sm * P->groups_per_block;
   if (MODE == 2) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -663,7 +688,11 @@ int plan_fill3(int m, int threads, int cluster, SolvePlan* P) {
 }
 
 int plan_fill3(int m, int prec, int mode, int threads, int cluster, SolvePlan* P) {
-  if (prec) return mode == 2 ? plan_fill3<true, 2>(m, threads, cluster, P) : plan_fill3<true, 0>(m, threads, 0, P);
+  if (prec) {
+    if (mode == 1) return plan_fill3<true, 1>(m, threads, 0, P);
+    return mode == 2 ? plan_fill3<true, 2>(m, threads, cluster, P) : plan_fill3<true, 0>(m, threads, 0, P);
+  }
+  if (mode == 1) return plan_fill3<false, 1>(m, threads, 0, P);
   return mode == 2 ? plan_fill3<false, 2>(m, threads, cluster, P) : plan_fill3<false, 0>(m, threads, 0, P);
 }
 
@@ -687,7 +716,6 @@ int solve3_plan(int m, int prec, SolvePlan* P) {
 }
 
 int solve3_plan_mode(int m, int prec, int mode, int threads, int cluster, SolvePlan* P) {
-  if (mode == 1) return -1;  // no warp-per-system plan in 3-D
   return plan_fill3(m, prec, mode, mode == 2 ? kMaxThreads3 : threads, cluster, P);
 }
 
@@ -699,6 +727,10 @@ int solve3_plan_candidates(int m, int prec, SolvePlan* out, int max_out) {
   SolvePlan d;
   if (solve3_plan(m, prec, &d)) return 0;
   add(d);
+  if (m <= 16) {  // one warp per system
+    SolvePlan w;
+    if (!plan_fill3(m, prec, 1, 0, 0, &w)) add(w);
+  }
   for (int t : {64, 128, 256, 512}) {
     if (!d.cluster && t == d.threads) continue;
     if ((int64_t)t > (int64_t)m * m * m) continue;
@@ -733,6 +765,7 @@ int solve3_launch(const SolveArgs& a, int prec, const SolvePlan& P, int n_blocks
   b.mg_nu = P.nu;
   b.mg_nu_coarse = P.nu_coarse;
   b.inner_tol = P.inner_tol;
+  b.ws64_stride = P.ws64_stride;
   if (P.cluster) {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -750,8 +783,13 @@ int solve3_launch(const SolveArgs& a, int prec, const SolvePlan& P, int n_blocks
                                : cudaLaunchKernelEx(&cfg, solve3_kernel<false, 2>, b);
     return e == cudaSuccess ? 0 : -1;
   }
-  if (prec) solve3_kernel<true, 0><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
-  else solve3_kernel<false, 0><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+  if (prec) {
+    if (P.warp) solve3_kernel<true, 1><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+    else solve3_kernel<true, 0><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+  } else {
+    if (P.warp) solve3_kernel<false, 1><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+    else solve3_kernel<false, 0><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+  }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

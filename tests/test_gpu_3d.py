@@ -113,7 +113,7 @@ def test_3d_launch_modes_agree(prec):
     d = workloads.workload("lognormal_3d_cgv_8to32", prec=prec, tol=1e-13 if prec == 0 else 1e-10)
     level, n = 1, 6  # m = 16 fine and eight m = 8 coarse systems per sample
     modes = [(0, 512, 0, 1, 1), (0, 128, 0, 1, 1), (2, 512, 2, 1, 1), (2, 512, 4, 1, 1), (0, 256, 0, 2, 1),
-             (0, 256, 0, 1, 2)]
+             (0, 256, 0, 1, 2), (1, 0, 0, 1, 1), (1, 0, 0, 1, 2)]
     res = []
     with pk.Context(d) as ctx:
         for mode, threads, cl, gamma, nu in modes:
@@ -159,7 +159,7 @@ def test_3d_autotune_and_multilevel():
     stream = torch.cuda.Stream()
     with pk.Context(d, stream=stream) as ctx:
         rep = ctx.autotune(seed=3)
-        assert len(rep) == 3 and all(r["warp"] == 0 for r in rep)
+        assert len(rep) == 3
         ref = [ctx.level_batch(l, n, 9) for l, n in enumerate((64, 16, 4))]
         got = ctx.multilevel_batch([64, 16, 4], 9, use_graph=True)
         for l in range(3):
