@@ -13,6 +13,10 @@ kernel the benchmark times.  Cases:
                 level 0 (65535 samples, m = 16) and level 1 (16384, m = 32)
   mixed_large   the CGV model m = 32..2048: level 5 (8 samples, m = 1024,
                 clusters of 8 blocks)
+  fp64_m256     the default workload's finest level, FP64: level 4 (512
+                samples, m = 256, one block of 512 threads per system)
+  mixed_m256    the CGV model, level 4 (1024 samples, m = 256, blocks of 512,
+                FP32 CG with reliable FP64 updates, inner_tol 1e-3)
   mixed_3d      the 3-D CGV workload (FP32 multigrid in FP64 refinement):
                 level 1 (4096 samples, m = 16, eight m = 8 coarse systems
                 each, blocks of 128 threads) and level 2 (512 samples,
@@ -31,6 +35,8 @@ CASES = {
                      [(0, 65535, (1, 0, 0, 1, 2)), (3, 1024, (0, 512, 0, 1, 2))]),
     "mixed_small": ("lognormal_2layer_cgv_16to512", {}, [(0, 65535, (1, 0, 0, 1, 1)), (1, 16384, (1, 0, 0, 1, 2))]),
     "mixed_large": ("lognormal_2layer_cgv_32to2048", {}, [(5, 8, (2, 512, 8, 1, 2))]),
+    "fp64_m256": ("lognormal_2layer_16to256", {}, [(4, 512, (0, 512, 0, 1, 2))]),
+    "mixed_m256": ("lognormal_2layer_cgv_16to512", {}, [(4, 1024, (0, 512, 0, 1, 2))]),
     "mixed_3d": ("lognormal_3d_cgv_8to32", {}, [(1, 4096, (0, 128, 0, 1, 2)), (2, 512, (0, 256, 0, 1, 2))]),
 }
 
@@ -40,6 +46,8 @@ def run(case):
     with pk.Context(workloads.workload(name, **over)) as ctx:
         for level, n, (mode, threads, cluster, gamma, nu) in levels:
             ctx.set_launch(level, mode, threads, cluster, gamma, nu)
+            if case == "mixed_m256":
+                ctx.set_solver(level, 1, 1e-3)
             s = ctx.level_batch(level, n, 0)
             torch.cuda.synchronize()
             print(case, "level", level, "m", ctx.m(level), "samples", s["n"], "iterations", s["iters_total"],
