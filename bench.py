@@ -252,6 +252,7 @@ def compare(args):
             e1.synchronize()
             ts.append(e0.elapsed_time(e1) / 1e3)
         out[name] = {"time_to_eps_s": sum(ts) / len(ts), "N": est["N"], "V": est["V"], "q_hat": est["q_hat"],
+                     "bias_estimate": est["bias"], "alpha": est["alpha"],
                      "var_hat": est["var_hat"], "level_samples_per_s": sum(est["N"]) / (sum(ts) / len(ts)),
                      "iters_per_sample": [round(x["iters_total"] / max(x["n"], 1), 2) for x in est["sums"]],
                      "prec": PREC_NAMES[md["prec"]],
@@ -411,7 +412,8 @@ def main():
         "dtype": "f64" if d["prec"] == 0 else "f64+f32-mg" if d["prec"] == 3 else "f32+f64", "data": "synthetic (Philox4x64-10 streams)",
         "config": config_block(args, d), "roofline": roof, "e2e": e2e, "gpu_launches": launches // 1,
         "clocks": clk, "time_to_eps_s": total_ms / args.steps / 1e3, "N_per_level": est["N"],
-        "q_hat": est["q_hat"], "var_hat": est["var_hat"],
+        "q_hat": est["q_hat"], "var_hat": est["var_hat"], "alpha": est["alpha"], "bias_estimate": est["bias"],
+        "bias_flag": est["bias_flag"],
         "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
         "iters_per_cell_solve": prof["cell_iters"] / max(prof["cells"], 1.0),
         "autotune": [{"m": d["m0"] << l, "threads": t["threads"], "warp": t["warp"], "cluster": t["cluster"],

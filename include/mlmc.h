@@ -144,6 +144,15 @@ typedef struct mlmc_estimate_out {
   mlmc_level_sums sums[MLMC_MAX_LEVELS];
   int32_t rounds;                      /* top-up rounds after the pilot */
   double seconds;                      /* wall time */
+  /* Bias of the finest level, reported only (L is fixed by the model; the
+   * sample-size rule controls the sampling error alone, Eq. 3.7): the weak
+   * rate alpha is the least-squares slope of -log2 |mean_l| over the levels
+   * l >= 1 with a nonzero mean (at least two of them; else alpha = 1, the
+   * rate Sec. 3.4 observes for the outflow), floored at 0.5, and
+   * bias = |mean_L| / (2^alpha - 1).  NaN when L = 0. */
+  double alpha;
+  double bias;
+  int32_t bias_flag;                   /* 1: bias > eps / sqrt(2), the bias half of the MSE budget */
 } mlmc_estimate_out;
 
 typedef struct mlmc_ctx mlmc_ctx;

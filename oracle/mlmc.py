@@ -123,5 +123,26 @@ def estimate(model, eps, seed, n_pilot=64, max_rounds=10, cost=None):
                 sums[lvl] = merge_sums(sums[lvl], b["sums"])
     stats = [level_stats(sums[lvl], model.cgv != 0 and lvl > 0) for lvl in range(L + 1)]
     q_hat = math.fsum(mu for mu, _ in stats)
+    mean = [mu for mu, _ in stats]
+    alpha, bias = bias_estimate(mean)
     return {"q_hat": q_hat, "N": [s["n"] for s in sums], "V": [v for _, v in stats],
-            "mean": [mu for mu, _ in stats], "C": C, "rounds": rounds, "sums": sums}
+            "mean": mean, "C": C, "rounds": rounds, "sums": sums, "alpha": alpha, "bias": bias,
+            "bias_flag": int(bias > eps / math.sqrt(2.0)) if not math.isnan(bias) else 0}
+
+
+def bias_estimate(mean):
+    """Weak-error rate and bias of the finest level from the level-correction
+    means (reported, not controlled: L is fixed): E[Y_l] ~ 2^(-alpha l), alpha
+    from a straight-line fit of log2 |mean_l| over the levels l >= 1 with a
+    nonzero mean (alpha = 1, the outflow rate observed in Sec. 3.4, with fewer
+    than two), floored at 0.5; bias = |mean_L| / (2^alpha - 1), the tail of
+    the geometric series of the omitted corrections.  (nan, nan) when L = 0."""
+    L = len(mean) - 1
+    if L < 1:
+        return float("nan"), float("nan")
+    lv = [l for l in range(1, L + 1) if mean[l] != 0.0]
+    alpha = 1.0
+    if len(lv) >= 2:
+        alpha = -np.polyfit(np.array(lv, dtype=float), np.log2(np.abs([mean[l] for l in lv])), 1)[0]
+    alpha = max(alpha, 0.5)
+    return alpha, abs(mean[L]) / (2.0 ** alpha - 1.0)

@@ -53,6 +53,7 @@ class EstimateOut(ctypes.Structure):
         ("N", ctypes.c_int64 * MAX_LEVELS), ("V", ctypes.c_double * MAX_LEVELS),
         ("mean", ctypes.c_double * MAX_LEVELS), ("C", ctypes.c_double * MAX_LEVELS),
         ("sums", LevelSums * MAX_LEVELS), ("rounds", ctypes.c_int32), ("seconds", ctypes.c_double),
+        ("alpha", ctypes.c_double), ("bias", ctypes.c_double), ("bias_flag", ctypes.c_int32),
     ]
 
 
@@ -261,7 +262,8 @@ class Context:
         L = self.model.L + 1
         return {"q_hat": out.q_hat, "var_hat": out.var_hat, "N": list(out.N[:L]), "V": list(out.V[:L]),
                 "mean": list(out.mean[:L]), "C": list(out.C[:L]), "rounds": out.rounds,
-                "seconds": out.seconds, "sums": [out.sums[i].as_dict() for i in range(L)], "rc": rc}
+                "seconds": out.seconds, "sums": [out.sums[i].as_dict() for i in range(L)], "rc": rc,
+                "alpha": out.alpha, "bias": out.bias, "bias_flag": out.bias_flag}
 
     def checkpoint(self, path):
         """mlmc_checkpoint: write the last estimate's state to a file."""

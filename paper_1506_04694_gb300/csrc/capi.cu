@@ -944,6 +944,28 @@ int mlmc_estimate_ex(mlmc_ctx* c, double eps, uint64_t seed, int32_t n_pilot, in
   out->q_hat = qh;
   out->var_hat = vh;
   out->rounds = rounds;
+  // weak-error rate and bias of the finest level (reported, not controlled)
+  out->alpha = out->bias = std::nan("");
+  out->bias_flag = 0;
+  if (NL >= 2) {
+    double sl = 0, sy = 0, sll = 0, sly = 0;
+    int k = 0;
+    for (int l = 1; l < NL; ++l)
+      if (out->mean[l] != 0.0) {
+        const double y = std::log2(std::fabs(out->mean[l]));
+        sl += l;
+        sy += y;
+        sll += (double)l * l;
+        sly += l * y;
+        ++k;
+      }
+    double alpha = 1.0;
+    if (k >= 2) alpha = -(k * sly - sl * sy) / (k * sll - sl * sl);
+    alpha = std::max(alpha, 0.5);
+    out->alpha = alpha;
+    out->bias = std::fabs(out->mean[NL - 1]) / (std::exp2(alpha) - 1.0);
+    out->bias_flag = out->bias > eps / std::sqrt(2.0) ? 1 : 0;
+  }
   out->seconds = now_s() - t0;
   auto& st = c->last_est;
   st.valid = true;

@@ -222,6 +222,9 @@ def test_estimate_parity_mode():
     assert est["N"] == ref["N"]
     assert abs(est["q_hat"] - ref["q_hat"]) < 1e-10 * abs(ref["q_hat"])
     assert est["var_hat"] <= eps * eps / 2 * (1 + 1e-9)
+    # the reported weak rate and finest-level bias follow from the same means
+    assert abs(est["alpha"] - ref["alpha"]) < 1e-8 and abs(est["bias"] - ref["bias"]) < 1e-8 * ref["bias"] + 1e-14
+    assert est["bias_flag"] == ref["bias_flag"]
 
 
 def test_multilevel_batch_matches_level_batches():

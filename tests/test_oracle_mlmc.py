@@ -163,3 +163,22 @@ def test_cgv_variance_reduction():
         ratios.append(np.var(b["qf"] - b["qc"], ddof=1) / np.var(b["qf"] - b["qc_cgv"], ddof=1))
     assert ratios[0] > 10 and ratios[1] > 30 and ratios[2] > 100
     assert ratios[0] < ratios[1] < ratios[2]
+
+
+def test_bias_estimate_geometric_tail():
+    # means c 2^(-alpha l): the fitted rate is alpha and the bias is the tail
+    # sum of the omitted corrections, sum_{k > L} c 2^(-alpha k)
+    from oracle import mlmc
+    for alpha, L in ((1.5, 4), (1.0, 3), (2.0, 5)):
+        mean = [1.7] + [0.3 * 2.0 ** (-alpha * l) for l in range(1, L + 1)]
+        a, b = mlmc.bias_estimate(mean)
+        tail = sum(0.3 * 2.0 ** (-alpha * k) for k in range(L + 1, L + 400))
+        assert abs(a - alpha) < 1e-12
+        assert abs(b - tail) < 1e-12 * tail
+    # alternating signs use |mean|; slow decay is floored at 0.5; one level: alpha = 1; L = 0: nan
+    a, _ = mlmc.bias_estimate([1.0, -0.4, 0.1, -0.025])
+    assert abs(a - 2.0) < 1e-12
+    assert mlmc.bias_estimate([1.0, 0.2, 0.18, 0.17])[0] == 0.5
+    a, b = mlmc.bias_estimate([1.0, 0.2])
+    assert a == 1.0 and abs(b - 0.2) < 1e-15
+    assert all(math.isnan(v) for v in mlmc.bias_estimate([1.0]))
