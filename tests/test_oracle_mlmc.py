@@ -182,3 +182,38 @@ def test_bias_estimate_geometric_tail():
     a, b = mlmc.bias_estimate([1.0, 0.2])
     assert a == 1.0 and abs(b - 0.2) < 1e-15
     assert all(math.isnan(v) for v in mlmc.bias_estimate([1.0]))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_nested_levels_telescope(dim):
+    # Nested mode (Eq. 3.6 with Eq. 4.1 applied repeatedly): every level is
+    # taken from one fine field by subsampling at offset 0.  The coarse term of
+    # the level-l sample is then exactly the fine term of the nested level
+    # l - 1, so the corrections Y_0 = Q_0, Y_l = Q_l - Q_{l-1} telescope to Q_L.
+    if dim == 2:
+        L = 3
+        model = darcy.Model.from_dict(workloads.workload("lognormal_2layer_cgv_16to512", m0=4, L=L))
+        lmap, comp, cs, solve, stride = darcy.layer_map, darcy.compose_k, darcy.coarse_samples, darcy.solve_k, \
+            (lambda g, s: g[:, ::s, ::s])
+        r = darcy.sample(model, 6, L, 2, want_fields=True)
+    else:
+        from oracle import darcy3
+        L = 2
+        model = darcy.Model.from_dict(workloads.workload("lognormal_3d_cgv_8to32", m0=2, L=L))
+        lmap, comp, cs, solve, stride = darcy3.layer_map3, darcy3.compose_k3, darcy3.coarse_samples3, \
+            darcy3.solve_k3, (lambda g, s: g[:, ::s, ::s, ::s])
+        r = darcy3.sample(model, 6, L, 2, want_fields=True)
+    g_top, eta = r["g"], r["eta"]
+    q = []
+    for lvl in range(L + 1):
+        s = 2 ** (L - lvl)
+        g = stride(g_top, s)
+        k = comp(g, lmap(model, eta, model.m(lvl)))
+        q.append(solve(k)[1])
+        if lvl:
+            (kc,) = cs(model, g, k, eta, 0)
+            assert solve(kc)[1] == q[lvl - 1]
+    assert q[L] == r["qf"]
+    y = [q[0]] + [q[lvl] - q[lvl - 1] for lvl in range(1, L + 1)]
+    assert abs(math.fsum(y) - q[L]) <= 4e-16 * abs(q[L])
+    assert abs(r["qc"] - q[L - 1]) == 0.0
