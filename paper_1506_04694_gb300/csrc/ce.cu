@@ -96,7 +96,8 @@ __device__ void block_fft_rows(Cplx<R>* s, int nrows, int M, int logM, const Cpl
         const Cplx<R> w = tw[pos * tstride];
         const Cplx<R> u = base[i0];
         const Cplx<R> v = base[i0 + hs];
-        base[i0] = Cplx<R>{u.x + (w.x * v.x - w.y * v.y), u.y + (w.x * v.y + w.y * v.x)};
+        // u + w v as two fused multiply-add chains per component
+        base[i0] = Cplx<R>{fma(w.x, v.x, fma(-w.y, v.y, u.x)), fma(w.x, v.y, fma(w.y, v.x, u.y))};
       }
       __syncthreads();
       continue;

@@ -143,9 +143,12 @@ __device__ __forceinline__ double tab_m2log(uint64_t K, const double* __restrict
 
 // r (cos 2 pi u, sin 2 pi u) for u = (2K + 1) 2^-53, K = w >> 12: u = j/1024
 // + b with the nearest j (integer arithmetic, exact), theta = 2 pi b =
-// (2D + 1) pi 2^-52 with |theta| <= pi/1024 (2D + 1 is exact in FP64),
-// Taylor polynomials to theta^5 (truncation < 3e-18), then the
-// angle-addition formulas with the tabulated (cos, sin) scaled by r.
+// (2D + 1) pi 2^-52 with |theta| <= pi/1024 (2D + 1 is exact in FP64).  The
+// angle addition in tangent form, cos(a + theta) = cos(theta) (cos a -
+// tan(theta) sin a) and sin(a + theta) = cos(theta) (sin a + tan(theta)
+// cos a), with the tabulated (cos a, sin a) and Taylor polynomials of
+// tan(theta) to theta^5 and cos(theta) to theta^4 (truncation < 2e-18);
+// r cos(theta) scales both.
 __device__ __forceinline__ void tab_polar(uint64_t w, double r, const double2* __restrict__ sc, double& x,
                                           double& y) {
   const long long K = (long long)(w >> 12);
@@ -153,12 +156,11 @@ __device__ __forceinline__ void tab_polar(uint64_t w, double r, const double2* _
   const long long D = K - (j << 42);
   const double th = (double)(2 * D + 1) * 0x1.921fb54442d18p-51;  // pi 2^-52
   const double t2 = th * th;
-  const double cm = t2 * fma(t2, 1.0 / 24.0, -0.5);                      // cos(theta) - 1
-  const double sn = fma(th * t2, fma(t2, 1.0 / 120.0, -1.0 / 6.0), th);  // sin(theta)
+  const double tn = fma(th * t2, fma(t2, 2.0 / 15.0, 1.0 / 3.0), th);  // tan(theta)
+  const double rc = r * fma(t2, fma(t2, 1.0 / 24.0, -0.5), 1.0);      // r cos(theta)
   const double2 cs = __ldg(sc + (j & (kSinCosTab - 1)));
-  const double rc = r * cs.x, rs = r * cs.y;
-  x = fma(rc, cm, fma(-rs, sn, rc));
-  y = fma(rs, cm, fma(rc, sn, rs));
+  x = rc * fma(-tn, cs.y, cs.x);
+  y = rc * fma(tn, cs.x, cs.y);
 }
 
 // Box-Muller pair from two words (same definition as box_muller()), each

@@ -267,7 +267,9 @@ __device__ __forceinline__ void build_diag(const G& g, const Level<T, FT>& L) {
 // every pivot, a Schur-complement diagonal, is positive): at step k with
 // pivot p, row r_j = B[k][j] and column c_i = B[i][k],
 //   B[k][k] <- 1/p, B[k][j] <- r_j / p, B[i][k] <- -c_i / p,
-//   B[i][j] <- B[i][j] - c_i r_j / p;  after n steps B = A^-1.
+//   B[i][j] <- B[i][j] - c_i (r_j / p);  after n steps B = A^-1.
+// The scaled pivot row is formed once per step, and the reciprocal of the
+// next pivot by the one thread that writes it (into buf[2n]).
 template <typename T, typename F, typename G>
 __device__ void build_coarse_inverse(const G& g, const Level<T, F>& L) {
   const int m = L.m, n = m * m, nn = n * n;
@@ -281,22 +283,25 @@ __device__ void build_coarse_inverse(const G& g, const Level<T, F>& L) {
     else if (jr == jc && (ir - ic == 1 || ic - ir == 1)) v = -face_ld(L.tx[jr * (m + 1) + (ir > ic ? ir : ic)]);
     else if (ir == ic && (jr - jc == 1 || jc - jr == 1)) v = -face_ld(L.ty[(jr > jc ? jr : jc) * m + ir]);
     B[idx] = v;
+    if (idx == 0) buf[2 * n] = T(1) / v;
   }
   g.sync();
   for (int k = 0; k < n; ++k) {
+    const T ip = buf[2 * n];
     for (int t = g.rank(); t < n; t += g.size()) {
-      buf[t] = B[k * n + t];
+      buf[t] = t == k ? ip : B[k * n + t] * ip;
       buf[n + t] = B[t * n + k];
     }
     g.sync();
-    const T ip = T(1) / buf[k];
+    const int next = (k + 1) * (n + 1);  // B[k+1][k+1]
     for (int idx = g.rank(); idx < nn; idx += g.size()) {
       const int i = idx / n, j = idx - i * n;
       T v;
-      if (i == k) v = j == k ? ip : buf[j] * ip;
+      if (i == k) v = buf[j];
       else if (j == k) v = -buf[n + i] * ip;
-      else v = B[idx] - buf[n + i] * ip * buf[j];
+      else v = fma(-buf[n + i], buf[j], B[idx]);
       B[idx] = v;
+      if (idx == next && k + 1 < n) buf[2 * n] = T(1) / v;
     }
     g.sync();
   }
@@ -710,6 +715,9 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
     g.sync();
   }
   const int n_if = a.geometry == 1 ? 0 : a.n_layers - 1;
+  // m and a.m are powers of two: scaling by the reciprocal is exact, so the
+  // centre (j + 1/2) / m is the same double as the quotient
+  const double inv_m = 1.0 / (double)m, inv_mf = 1.0 / (double)a.m;
   for (int c = g.rank(); c < n; c += g.size()) {
     const int j = c / m, i = c - j * m;
     double kk;
@@ -720,8 +728,8 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
       const int jf = coarse ? 2 * j + oy : j;
       const int iff = coarse ? 2 * i + ox : i;
       const bool own = coarse && !a.cgv_on_k;  // layer at the coarse centre
-      const double yc = own ? ((double)j + 0.5) / (double)m : ((double)jf + 0.5) / (double)a.m;
-      const double xc = own ? ((double)i + 0.5) / (double)m : ((double)iff + 0.5) / (double)a.m;
+      const double yc = own ? ((double)j + 0.5) * inv_m : ((double)jf + 0.5) * inv_mf;
+      const double xc = own ? ((double)i + 0.5) * inv_m : ((double)iff + 0.5) * inv_mf;
       const int t = layer_at_point(a.geometry, gs.eta, n_if, xc, yc);
       if (a.ksrc == KSRC_CONST) {
         kk = gs.kc[t];

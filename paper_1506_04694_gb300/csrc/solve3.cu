@@ -412,6 +412,8 @@ __device__ void solve_one3(const G& g, const SolveArgs& a, int64_t sys, unsigned
   }
   const int n_if = a.geometry == 1 ? 0 : a.n_layers - 1;
   const int mf = a.m;
+  // m and mf are powers of two: scaling by the reciprocal is exact
+  const double inv_m = 1.0 / (double)m, inv_mf = 1.0 / (double)mf;
   for (int c = g.rank(); c < n; c += g.size()) {
     const int l = c / m2;
     const int rem = c - l * m2;
@@ -424,8 +426,8 @@ __device__ void solve_one3(const G& g, const SolveArgs& a, int64_t sys, unsigned
       const int iff = coarse ? 2 * i + ox : i;
       const int lf = coarse ? 2 * l + oz : l;
       const bool own = coarse && !a.cgv_on_k;  // layer at the coarse centre
-      const double yc = own ? ((double)j + 0.5) / (double)m : ((double)jf + 0.5) / (double)mf;
-      const double xc = own ? ((double)i + 0.5) / (double)m : ((double)iff + 0.5) / (double)mf;
+      const double yc = own ? ((double)j + 0.5) * inv_m : ((double)jf + 0.5) * inv_mf;
+      const double xc = own ? ((double)i + 0.5) * inv_m : ((double)iff + 0.5) * inv_mf;
       const int t = layer_at_point(a.geometry, gs.eta, n_if, xc, yc);
       const int64_t gi = (((sidx * a.n_layers + t) * (int64_t)mf + lf) * mf + jf) * mf + iff;
       if (a.ksrc == KSRC_CONST) kk = gs.kc[t];
