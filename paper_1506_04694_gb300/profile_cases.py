@@ -13,6 +13,8 @@ kernel the benchmark times.  Cases:
                 level 0 (65535 samples, m = 16) and level 1 (16384, m = 32)
   mixed_large   the CGV model m = 32..2048: level 5 (8 samples, m = 1024,
                 clusters of 8 blocks)
+  mixed_1024    the CGV model m = 32..2048: level 5 in steady state (32
+                samples, m = 1024, 32 + 128 systems on clusters of 8 blocks)
   fp64_m256     the default workload's finest level, FP64: level 4 (512
                 samples, m = 256, one block of 512 threads per system)
   mixed_m256    the CGV model, level 4 (1024 samples, m = 256, blocks of 512,
@@ -35,6 +37,7 @@ CASES = {
                      [(0, 65535, (1, 0, 0, 1, 2)), (3, 1024, (0, 512, 0, 1, 2))]),
     "mixed_small": ("lognormal_2layer_cgv_16to512", {}, [(0, 65535, (1, 0, 0, 1, 1)), (1, 16384, (1, 0, 0, 1, 2))]),
     "mixed_large": ("lognormal_2layer_cgv_32to2048", {}, [(5, 8, (2, 512, 8, 1, 2))]),
+    "mixed_1024": ("lognormal_2layer_cgv_32to2048", {}, [(5, 32, (2, 512, 8, 1, 2))]),
     "fp64_m256": ("lognormal_2layer_16to256", {}, [(4, 512, (0, 512, 0, 1, 2))]),
     "mixed_m256": ("lognormal_2layer_cgv_16to512", {}, [(4, 1024, (0, 512, 0, 1, 2))]),
     "mixed_3d": ("lognormal_3d_cgv_8to32", {}, [(1, 4096, (0, 128, 0, 1, 2)), (2, 512, (0, 256, 0, 1, 2))]),
