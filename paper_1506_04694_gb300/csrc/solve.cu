@@ -119,18 +119,46 @@ struct Level {
   T* cbuf;  // coarsest level only: pivot row, pivot column (2 m^2 + 1)
 };
 
+// Cell arrays (solution, right-hand side, diagonal, CG vectors) are stored
+// colour by colour: first the cells with i + j even ("red"), row by row with
+// i/2 inside a row, then those with i + j odd ("black").  A red-black half
+// sweep then reads and writes unit-stride runs of both colours.  Faces keep
+// the natural layout (tx: m rows of m + 1, ty: m + 1 rows of m).  m is a
+// power of two (m = 1: a single cell).
+__device__ __forceinline__ int log2_pow2(int v) { return 31 - __clz(v); }  // v a power of two
+
+struct RbIndex {
+  int m, hm, lhm, half;  // side, m/2, log2(m/2), cells of colour 0
+  __device__ __forceinline__ explicit RbIndex(int m_) {
+    m = m_;
+    hm = m_ >> 1;
+    lhm = m_ >= 2 ? log2_pow2(hm) : 0;
+    half = (m_ * m_ + 1) >> 1;
+  }
+  __device__ __forceinline__ int at(int i, int j) const { return ((i + j) & 1) * half + j * hm + (i >> 1); }
+  __device__ __forceinline__ void cell(int c, int& i, int& j) const {
+    const int col = c >= half ? 1 : 0;
+    const int r = c - col * half;
+    j = r >> lhm;
+    i = ((r - (j << lhm)) << 1) + ((j + col) & 1);
+  }
+};
+
 // (A v)_c = diag_c v_c - sum over the faces of T v_nbr (v_nbr = 0 outside:
-// Dirichlet faces carry T but no neighbour, no-flow faces carry T = 0).
+// Dirichlet faces carry T but no neighbour, no-flow faces carry T = 0), for
+// the cell (i, j) stored at c.  The four neighbours have the other colour:
+// row j of that colour starts at ob, rows j -/+ 1 at ob -/+ m/2.
 template <typename T, typename F>
-__device__ __forceinline__ T apply_row(const Level<T, F>& L, const T* __restrict__ v, int i, int j) {
+__device__ __forceinline__ T apply_at(const Level<T, F>& L, const T* __restrict__ v, const RbIndex& R, int c, int i,
+                                      int j) {
   const int m = L.m;
-  const int c = j * m + i;
+  const int ob = (((i + j) & 1) ^ 1) * R.half + j * R.hm;
   const int rf = j * (m + 1) + i;
   T s = L.diag[c] * v[c];
-  if (i > 0) s -= face_ld(L.tx[rf]) * v[c - 1];
-  if (i < m - 1) s -= face_ld(L.tx[rf + 1]) * v[c + 1];
-  if (j > 0) s -= face_ld(L.ty[c]) * v[c - m];
-  if (j < m - 1) s -= face_ld(L.ty[c + m]) * v[c + m];
+  if (i > 0) s -= face_ld(L.tx[rf]) * v[ob + ((i - 1) >> 1)];
+  if (i < m - 1) s -= face_ld(L.tx[rf + 1]) * v[ob + ((i + 1) >> 1)];
+  if (j > 0) s -= face_ld(L.ty[j * m + i]) * v[ob - R.hm + (i >> 1)];
+  if (j < m - 1) s -= face_ld(L.ty[(j + 1) * m + i]) * v[ob + R.hm + (i >> 1)];
   return s;
 }
 
@@ -145,8 +173,10 @@ __device__ __forceinline__ T apply_row(const Level<T, F>& L, const T* __restrict
 // treats the other color as zero (first sweep of a cycle).
 template <typename T, typename F, typename G>
 __device__ __forceinline__ void rb_sweep(const G& g, const Level<T, F>& L, int color, bool zero_guess) {
-  const int m = L.m, hm = m >> 1;
-  const int nh = m * hm;
+  const int m = L.m;
+  const RbIndex R(m);
+  const int nh = m * R.hm;  // cells of one colour
+  const int own0 = color * R.half, oth0 = (color ^ 1) * R.half;
   const int step = g.size();
   int h0 = g.rank();
   for (; h0 < nh; h0 += G::kU * step) {
@@ -157,16 +187,19 @@ __device__ __forceinline__ void rb_sweep(const G& g, const Level<T, F>& L, int c
       const int h = h0 + u * step;
       cc[u] = -1;
       if (h < nh) {
-        const int j = h / hm;
-        const int i = ((h - j * hm) << 1) + ((j + color) & 1);
-        const int c = j * m + i;
+        const int j = h >> R.lhm;
+        const int k = h - (j << R.lhm);
+        const int sh = (j + color) & 1;  // i = 2k + sh; west neighbour at k - 1 + sh, east at k + sh
+        const int i = (k << 1) + sh;
+        const int c = own0 + h;
         T s = L.f[c];
         if (!zero_guess) {
           const int rf = j * (m + 1) + i;
-          if (i > 0) s += face_ld(L.tx[rf]) * L.e[c - 1];
-          if (i < m - 1) s += face_ld(L.tx[rf + 1]) * L.e[c + 1];
-          if (j > 0) s += face_ld(L.ty[c]) * L.e[c - m];
-          if (j < m - 1) s += face_ld(L.ty[c + m]) * L.e[c + m];
+          const int ob = oth0 + j * R.hm + k;
+          if (i > 0) s += face_ld(L.tx[rf]) * L.e[ob - 1 + sh];
+          if (i < m - 1) s += face_ld(L.tx[rf + 1]) * L.e[ob + sh];
+          if (j > 0) s += face_ld(L.ty[j * m + i]) * L.e[ob - R.hm];
+          if (j < m - 1) s += face_ld(L.ty[(j + 1) * m + i]) * L.e[ob + R.hm];
         }
         val[u] = s * L.invd[c];
         cc[u] = c;
@@ -186,24 +219,29 @@ __device__ __forceinline__ void rb_sweep(const G& g, const Level<T, F>& L, int c
 template <typename T, typename FT, typename G>
 __device__ __forceinline__ void restrict_residual(const G& g, const Level<T, FT>& F, const Level<T, FT>& C) {
   const int mc = C.m, m = F.m;
+  const RbIndex Rf(m), Rc(mc);
+  const int lmc = log2_pow2(mc);
   const int nc = mc * mc, step = g.size();
   for (int c0 = g.rank(); c0 < nc; c0 += G::kU * step) {
     T val[G::kU];
+    int dst[G::kU];
 #pragma unroll
     for (int u = 0; u < G::kU; ++u) {
-      const int cc = c0 + u * step;
-      val[u] = T(0);
-      if (cc < nc) {
-        const int J = cc / mc, I = cc - J * mc;
+      const int t = c0 + u * step;  // coarse cell (I, J) in natural order
+      dst[u] = -1;
+      if (t < nc) {
+        const int J = t >> lmc, I = t - (J << lmc);
         const int i0 = 2 * I, j0 = 2 * J;
-        const T r0 = F.f[j0 * m + i0] - apply_row(F, F.e, i0, j0);
-        const T r1 = F.f[(j0 + 1) * m + i0 + 1] - apply_row(F, F.e, i0 + 1, j0 + 1);
+        const int f0 = J * m + I, f1 = f0 + Rf.hm;  // the red cells (2I, 2J) and (2I+1, 2J+1)
+        const T r0 = F.f[f0] - apply_at(F, F.e, Rf, f0, i0, j0);
+        const T r1 = F.f[f1] - apply_at(F, F.e, Rf, f1, i0 + 1, j0 + 1);
         val[u] = r0 + r1;
+        dst[u] = Rc.at(I, J);
       }
     }
 #pragma unroll
     for (int u = 0; u < G::kU; ++u)
-      if (c0 + u * step < nc) C.f[c0 + u * step] = val[u];
+      if (dst[u] >= 0) C.f[dst[u]] = val[u];
   }
   g.sync();
 }
@@ -211,6 +249,7 @@ __device__ __forceinline__ void restrict_residual(const G& g, const Level<T, FT>
 template <typename T, typename FT, typename G>
 __device__ __forceinline__ void prolong_add(const G& g, const Level<T, FT>& C, const Level<T, FT>& F) {
   const int m = F.m, mc = C.m;
+  const RbIndex Rf(m), Rc(mc);
   const int n = m * m, step = g.size();
   for (int c0 = g.rank(); c0 < n; c0 += G::kU * step) {
     T val[G::kU];
@@ -218,8 +257,9 @@ __device__ __forceinline__ void prolong_add(const G& g, const Level<T, FT>& C, c
     for (int u = 0; u < G::kU; ++u) {
       const int c = c0 + u * step;
       if (c < n) {
-        const int j = c / m, i = c - j * m;
-        val[u] = F.e[c] + C.e[(j >> 1) * mc + (i >> 1)];
+        int i, j;
+        Rf.cell(c, i, j);
+        val[u] = F.e[c] + C.e[Rc.at(i >> 1, j >> 1)];
       }
     }
 #pragma unroll
@@ -252,10 +292,13 @@ __device__ __forceinline__ void build_coarse(const G& g, const Level<T, FT>& F, 
 template <bool INV, typename T, typename FT, typename G>
 __device__ __forceinline__ void build_diag(const G& g, const Level<T, FT>& L) {
   const int m = L.m;
+  const RbIndex R(m);
   for (int c = g.rank(); c < m * m; c += g.size()) {
-    const int j = c / m, i = c - j * m;
+    int i, j;
+    R.cell(c, i, j);
     const int rf = j * (m + 1) + i;
-    const T d = (face_ld(L.tx[rf]) + face_ld(L.tx[rf + 1])) + (face_ld(L.ty[c]) + face_ld(L.ty[c + m]));
+    const T d = (face_ld(L.tx[rf]) + face_ld(L.tx[rf + 1])) +
+                (face_ld(L.ty[j * m + i]) + face_ld(L.ty[(j + 1) * m + i]));
     L.diag[c] = d;
     if (INV) L.invd[c] = T(1) / d;
   }
@@ -273,11 +316,14 @@ __device__ __forceinline__ void build_diag(const G& g, const Level<T, FT>& L) {
 template <typename T, typename F, typename G>
 __device__ void build_coarse_inverse(const G& g, const Level<T, F>& L) {
   const int m = L.m, n = m * m, nn = n * n;
+  const RbIndex R(m);
   T* B = L.cinv;
   T* buf = L.cbuf;
   for (int idx = g.rank(); idx < nn; idx += g.size()) {
-    const int r = idx / n, c = idx - r * n;
-    const int jr = r / m, ir = r - jr * m, jc = c / m, ic = c - jc * m;
+    const int r = idx / n, c = idx - r * n;  // cells in storage order
+    int ir, jr, ic, jc;
+    R.cell(r, ir, jr);
+    R.cell(c, ic, jc);
     T v = T(0);
     if (r == c) v = L.diag[r];
     else if (jr == jc && (ir - ic == 1 || ic - ir == 1)) v = -face_ld(L.tx[jr * (m + 1) + (ir > ic ? ir : ic)]);
@@ -408,6 +454,7 @@ __device__ int pcg(const G& g, const Level<T>& A, const Level<T, F>* lev, int nl
   T* __restrict__ r = L0.f;
   const T* __restrict__ z = L0.e;
   const int step = g.size();
+  const RbIndex R(m);
   T rr = T(0);
   for (int c = g.rank(); c < n; c += step) {
     x[c] = T(0);
@@ -437,8 +484,9 @@ __device__ int pcg(const G& g, const Level<T>& A, const Level<T, F>* lev, int nl
         const int c = c0 + u * step;
         val[u] = T(0);
         if (c < n) {
-          const int j = c / m, i = c - j * m;
-          val[u] = apply_row(A, p, i, j);
+          int i, j;
+          R.cell(c, i, j);
+          val[u] = apply_at(A, p, R, c, i, j);
           pq += p[c] * val[u];
         }
       }
@@ -490,6 +538,7 @@ __device__ int pcg64_mg32(const G& g, const Level<double>& A, const Level<float>
   const Level<float>& L0 = lev[0];
   const int m = A.m, n = m * m;
   const int step = g.size();
+  const RbIndex R(m);
   double rr = 0.0;
   for (int c = g.rank(); c < n; c += step) {
     x[c] = 0.0;
@@ -518,8 +567,9 @@ __device__ int pcg64_mg32(const G& g, const Level<double>& A, const Level<float>
     ++it;
     double pq = 0.0;
     for (int c = g.rank(); c < n; c += step) {
-      const int j = c / m, i = c - j * m;
-      const double v = apply_row(A, p, i, j);
+      int i, j;
+      R.cell(c, i, j);
+      const double v = apply_at(A, p, R, c, i, j);
       q[c] = v;
       pq += p[c] * v;
     }
@@ -708,6 +758,7 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
   const Level<T, F>* lev = gs.lev;
   const Level<T, F>& L0 = lev[0];
   const Level<T>& A = cg_operator<PREC>(gs);
+  const RbIndex R(m);  // cell-array layout (colour by colour)
 
   // ---- layers and per-cell permeability (into r64 as scratch) ----
   if (a.ksrc != KSRC_ARRAY) {
@@ -719,10 +770,11 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
   // centre (j + 1/2) / m is the same double as the quotient
   const double inv_m = 1.0 / (double)m, inv_mf = 1.0 / (double)a.m;
   for (int c = g.rank(); c < n; c += g.size()) {
-    const int j = c / m, i = c - j * m;
+    int i, j;
+    R.cell(c, i, j);
     double kk;
     if (a.ksrc == KSRC_ARRAY) {
-      kk = a.k[sys * (int64_t)n + c];
+      kk = a.k[sys * (int64_t)n + j * m + i];  // natural layout in the caller's array
     } else {
       // fine cell of the value, and the centre that decides the layer
       const int jf = coarse ? 2 * j + oy : j;
@@ -751,10 +803,10 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
       if (t < nfx) {
         const int j = t / (m + 1), ip = t - j * (m + 1);
         TF v;
-        if (ip == 0) v = TF(2) * (TF)r64[j * m];
-        else if (ip == m) v = TF(2) * (TF)r64[j * m + m - 1];
+        if (ip == 0) v = TF(2) * (TF)r64[R.at(0, j)];
+        else if (ip == m) v = TF(2) * (TF)r64[R.at(m - 1, j)];
         else {
-          const TF ka = (TF)r64[j * m + ip - 1], kb = (TF)r64[j * m + ip];
+          const TF ka = (TF)r64[R.at(ip - 1, j)], kb = (TF)r64[R.at(ip, j)];
           v = TF(2) * ka * kb / (ka + kb);
         }
         A.tx[t] = (T)v;
@@ -765,10 +817,10 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
         const int jp = u / m, i = u - jp * m;
         TF v = TF(0);
         if (jp > 0 && jp < m) {
-          const TF ka = (TF)r64[(jp - 1) * m + i], kb = (TF)r64[jp * m + i];
+          const TF ka = (TF)r64[R.at(i, jp - 1)], kb = (TF)r64[R.at(i, jp)];
           v = TF(2) * ka * kb / (ka + kb);
         } else if (a.problem == 1) {  // Dirichlet p = 0 half a cell away
-          v = TF(2) * (TF)r64[(jp == 0 ? 0 : m - 1) * m + i];
+          v = TF(2) * (TF)r64[R.at(i, jp == 0 ? 0 : m - 1)];
         }
         A.ty[u] = (T)v;
         if (PREC == 2) L0.ty[u] = face_st<F>((T)v);
@@ -792,7 +844,8 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
     double bb = 0.0;
     const double fmid = 1.0 / ((double)m * (double)m);  // Model Problem 1: f / m^2
     for (int c = g.rank(); c < n; c += g.size()) {
-      const int j = c / m, i = c - j * m;
+      int i, j;
+      R.cell(c, i, j);
       const double bv = a.problem == 1 ? fmid : (i == 0 ? A64.tx[j * (m + 1)] : 0.0);
       r64[c] = bv;
       bb += bv * bv;
@@ -805,7 +858,8 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
     T bb = T(0);
     const T fmid = (T)(1.0 / ((double)m * (double)m));  // Model Problem 1: f / m^2
     for (int c = g.rank(); c < n; c += g.size()) {
-      const int j = c / m, i = c - j * m;
+      int i, j;
+      R.cell(c, i, j);
       const T bv = a.problem == 1 ? fmid : (i == 0 ? A.tx[j * (m + 1)] : T(0));
       L0.f[c] = bv;
       bb += bv * bv;
@@ -819,7 +873,8 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
     double bb = 0.0;
     const double fmid = 1.0 / ((double)m * (double)m);  // Model Problem 1: f / m^2
     for (int c = g.rank(); c < n; c += g.size()) {
-      const int j = c / m, i = c - j * m;
+      int i, j;
+      R.cell(c, i, j);
       const double bv = a.problem == 1 ? fmid : (i == 0 ? (double)A.tx[j * (m + 1)] : 0.0);
       x64[c] = 0.0;
       r64[c] = bv;
@@ -832,15 +887,17 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
     auto residual64 = [&]() -> double {
       double s2 = 0.0;
       for (int c = g.rank(); c < n; c += g.size()) {
-        const int j = c / m, i = c - j * m;
+        int i, j;
+        R.cell(c, i, j);
         const int rf = j * (m + 1) + i;
         const double tw = (double)A.tx[rf], te = (double)A.tx[rf + 1];
-        const double ts = (double)A.ty[c], tn = (double)A.ty[c + m];
+        const double ts = (double)A.ty[j * m + i], tn = (double)A.ty[(j + 1) * m + i];
+        const int ob = (((i + j) & 1) ^ 1) * R.half + j * R.hm;  // row j of the other colour
         double ax = ((tw + te) + (ts + tn)) * x64[c];
-        if (i > 0) ax -= tw * x64[c - 1];
-        if (i < m - 1) ax -= te * x64[c + 1];
-        if (j > 0) ax -= ts * x64[c - m];
-        if (j < m - 1) ax -= tn * x64[c + m];
+        if (i > 0) ax -= tw * x64[ob + ((i - 1) >> 1)];
+        if (i < m - 1) ax -= te * x64[ob + ((i + 1) >> 1)];
+        if (j > 0) ax -= ts * x64[ob - R.hm + (i >> 1)];
+        if (j < m - 1) ax -= tn * x64[ob + R.hm + (i >> 1)];
         const double bv = a.problem == 1 ? fmid : (i == 0 ? tw : 0.0);
         const double rv = bv - ax;
         r64[c] = rv;
@@ -887,8 +944,9 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
         ++since;
         T pq = T(0);
         for (int c = g.rank(); c < n; c += g.size()) {
-          const int j = c / m, i = c - j * m;
-          const T v = apply_row(A, pv, i, j);
+          int i, j;
+          R.cell(c, i, j);
+          const T v = apply_at(A, pv, R, c, i, j);
           qv[c] = v;
           pq += pv[c] * v;
         }
@@ -984,7 +1042,8 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
     const double h = 1.0 / (double)m;
     const double inv_area = 1.0 / ((a.box[1] - a.box[0]) * (a.box[3] - a.box[2]));
     for (int c = g.rank(); c < n; c += g.size()) {
-      const int j = c / m, i = c - j * m;
+      int i, j;
+      R.cell(c, i, j);
       const double ox = fmin((i + 1) * h, a.box[1]) - fmax(i * h, a.box[0]);
       const double oy = fmin((j + 1) * h, a.box[3]) - fmax(j * h, a.box[2]);
       if (ox > 0.0 && oy > 0.0) qsum += ox * oy * inv_area * x64[c];
@@ -993,7 +1052,7 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
     // M^(2): outflow through x1 = 1
     for (int j = g.rank(); j < m; j += g.size()) {
       const double te = PREC == 3 ? gs.op64.tx[j * (m + 1) + m] : (double)A.tx[j * (m + 1) + m];
-      qsum += te * x64[j * m + m - 1];
+      qsum += te * x64[R.at(m - 1, j)];
     }
   }
   qsum = g.sum(qsum, red64, par);
@@ -1002,7 +1061,11 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
     if (a.iters) a.iters[sys] = iters;
   }
   if (a.p_out && !coarse)
-    for (int c = g.rank(); c < n; c += g.size()) a.p_out[sidx * (int64_t)n + c] = x64[c];
+    for (int c = g.rank(); c < n; c += g.size()) {  // natural layout in the caller's array
+      int i, j;
+      R.cell(c, i, j);
+      a.p_out[sidx * (int64_t)n + j * m + i] = x64[c];
+    }
   g.sync();
 }
 
