@@ -13,10 +13,17 @@ namespace cg = cooperative_groups;
 // warp (small grids, no block barriers at all).
 struct BlockGroup {
   static constexpr int kU = 1;  // cells per thread per batch in the cell loops
+  static constexpr bool kStaged = false;  // runs the shared-memory staged half sweeps
   __device__ __forceinline__ bool local_leader() const { return threadIdx.x == 0; }
   __device__ __forceinline__ int rank() const { return threadIdx.x; }
   __device__ __forceinline__ int size() const { return blockDim.x; }
   __device__ __forceinline__ void sync() const { __syncthreads(); }
+  // the group's blocks (one here) and this thread's place in its own block
+  __device__ __forceinline__ int nblocks() const { return 1; }
+  __device__ __forceinline__ int block_index() const { return 0; }
+  __device__ __forceinline__ int lrank() const { return threadIdx.x; }
+  __device__ __forceinline__ int lsize() const { return blockDim.x; }
+  __device__ __forceinline__ void lsync() const { __syncthreads(); }
   template <typename T>
   __device__ __forceinline__ T sum(T v, T* red, int& par) const {
     return block_sum(v, red, par);
@@ -25,10 +32,16 @@ struct BlockGroup {
 
 struct WarpGroup {
   static constexpr int kU = 1;
+  static constexpr bool kStaged = false;
   __device__ __forceinline__ bool local_leader() const { return (threadIdx.x & 31) == 0; }
   __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
   __device__ __forceinline__ int size() const { return 32; }
   __device__ __forceinline__ void sync() const { __syncwarp(); }
+  __device__ __forceinline__ int nblocks() const { return 1; }
+  __device__ __forceinline__ int block_index() const { return 0; }
+  __device__ __forceinline__ int lrank() const { return threadIdx.x & 31; }
+  __device__ __forceinline__ int lsize() const { return 32; }
+  __device__ __forceinline__ void lsync() const { __syncwarp(); }
   template <typename T>
   __device__ __forceinline__ T sum(T v, T*, int&) const {
     return warp_sum(v);
@@ -44,12 +57,18 @@ struct WarpGroup {
 // bit-identical sums and take identical branches.
 struct ClusterGroup {
   static constexpr int kU = 1;
+  static constexpr bool kStaged = true;
   unsigned nblk, brank;
   double* part;  // two double slots in this block's shared memory
   __device__ __forceinline__ bool local_leader() const { return threadIdx.x == 0; }
   __device__ __forceinline__ int rank() const { return (int)(brank * blockDim.x + threadIdx.x); }
   __device__ __forceinline__ int size() const { return (int)(nblk * blockDim.x); }
   __device__ __forceinline__ void sync() const { cg::this_cluster().sync(); }
+  __device__ __forceinline__ int nblocks() const { return (int)nblk; }
+  __device__ __forceinline__ int block_index() const { return (int)brank; }
+  __device__ __forceinline__ int lrank() const { return threadIdx.x; }
+  __device__ __forceinline__ int lsize() const { return blockDim.x; }
+  __device__ __forceinline__ void lsync() const { __syncthreads(); }
   template <typename T>
   __device__ __forceinline__ T sum(T v, T* red, int& par) const {
     const int slot = par;  // block_sum toggles par; the partial slot follows it

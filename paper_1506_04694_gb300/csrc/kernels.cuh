@@ -93,6 +93,7 @@ struct SolveArgs {
   unsigned char* ws;   // global workspace base (n_blocks * ws_stride)
   size_t ws64_stride;  // > 0: bytes per group of FP64 refinement vectors in global memory at ws64
   unsigned char* ws64;
+  size_t stage_bytes;  // > 0: dynamic shared memory per block for the staged half sweeps
   // outputs per system
   double* q;           // outflow Q (NaN when not converged)
   int32_t* iters;      // CG iterations
@@ -112,6 +113,7 @@ struct SolvePlan {
   size_t ws_stride;      // bytes of workspace per group
   size_t ws64_stride;    // > 0 (prec 1, 2 on chip): global bytes per group of the FP64 refinement vectors
   size_t smem_bytes;     // dynamic shared memory per block
+  size_t stage_bytes;    // of which the staging buffers of the streamed half sweeps (0: none)
   int cap_blocks_per_sm; // > 0: launch at most this many blocks per SM (L2 residency)
   int gamma;             // multigrid cycle index: 1 V-cycle, 2 W-cycle
   int nu;                // smoothing: red-black sweep pairs before and after the coarse correction

@@ -117,6 +117,8 @@ struct Level {
   T* f;     // right-hand side (level 0: CG r)
   T* cinv;  // coarsest level only: dense inverse [m^2][m^2]
   T* cbuf;  // coarsest level only: pivot row, pivot column (2 m^2 + 1)
+  unsigned char* stage;  // shared-memory staging of the half sweeps (null: direct loads)
+  int stage_rows;        // rows per staged chunk
 };
 
 // Cell arrays (solution, right-hand side, diagonal, CG vectors) are stored
@@ -171,8 +173,163 @@ __device__ __forceinline__ T apply_at(const Level<T, F>& L, const T* __restrict_
 
 // Red (color 0) or black (color 1) Gauss-Seidel half sweep; `zero_guess`
 // treats the other color as zero (first sweep of a cycle).
+// ---- staged half sweeps ------------------------------------------------------
+// In the cluster plans (workspace in global memory) a half sweep on a grid
+// of side m >= kStageMin runs over chunks of `rows` grid rows: the chunk's right-hand side and
+// inverse diagonal (own colour), the neighbour-colour rows j0 - 1 .. j0 + rows,
+// and the faces of its rows are copied into shared memory with asynchronous
+// 16-byte copies while the previous chunk is updated from shared memory (two
+// buffers), so each thread keeps many loads in flight without holding
+// registers for them.  The update is rb_sweep's, term for term.
+constexpr int kStageMin = 128;
+
+template <typename T>
+struct StageVec {
+  static constexpr int V = 16 / (int)sizeof(T);  // elements per 16-byte copy
+};
+
+// Element offsets of one chunk buffer (rows r at side m), each a multiple of
+// 16 bytes: f, invd (r m/2 each), neighbour-colour rows ((r + 2) m/2), tx (the
+// run of r (m + 1) faces widened to 16-byte boundaries), ty ((r + 1) m); size
+// = the buffer's elements.
+struct StageLayout {
+  int f, d, e, x, y, size;
+};
+template <typename T>
+__host__ __device__ inline StageLayout stage_layout(int m, int r) {
+  const int V = StageVec<T>::V;
+  const int hm = m / 2;
+  auto up = [V](int n) { return (n + V - 1) / V * V; };
+  StageLayout S;
+  S.f = 0;
+  S.d = S.f + up(r * hm);
+  S.e = S.d + up(r * hm);
+  S.x = S.e + up((r + 2) * hm);
+  S.y = S.x + up(r * (m + 1) + 2 * V);
+  S.size = S.y + up((r + 1) * m);
+  return S;
+}
+
+// Rows per chunk: about one cell of the half sweep per thread of a block.
+__host__ __device__ inline int stage_rows_for(int m, int threads) {
+  const int r = threads / (m / 2);
+  return r < 1 ? 1 : r;
+}
+
+// Shared-memory bytes of the two chunk buffers of a level of side ml.
+template <typename T>
+__host__ __device__ inline size_t stage_level_bytes(int ml, int threads) {
+  return 2 * (size_t)stage_layout<T>(ml, stage_rows_for(ml, threads)).size * sizeof(T);
+}
+
+// A level is staged when ml >= kStageMin and its buffers fit in kStageCap;
+// the launch reserves the largest of those (0: no level is staged).
+constexpr size_t kStageCap = 96 * 1024;
+template <typename T>
+inline size_t stage_bytes_for(int m, int threads) {
+  size_t best = 0;
+  for (int ml = m; ml >= kStageMin; ml >>= 1) {
+    const size_t bytes = stage_level_bytes<T>(ml, threads);
+    if (bytes <= kStageCap && bytes > best) best = bytes;
+  }
+  return best;
+}
+
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src_global) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src_global) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Copy `count` elements (a multiple of 16 bytes; both ends 16-byte aligned).
+template <typename T>
+__device__ __forceinline__ void stage_copy(T* dst, const T* src, int count, int tid, int nt) {
+  constexpr int V = StageVec<T>::V;
+  for (int q = tid * V; q < count; q += nt * V) cp_async16(dst + q, src + q);
+}
+
+// Issue the copies of chunk q (rows q*rows ..) into chunk buffer s.
+template <typename T>
+__device__ __forceinline__ void stage_issue(const Level<T, T>& L, const StageLayout& S, T* s, int q, int rows,
+                                            int hm, int own0, int oth0, bool zero_guess, int tid, int nt) {
+  constexpr int V = StageVec<T>::V;
+  const int m = L.m;
+  const int j0 = q * rows;
+  const int nr = min(rows, m - j0);
+  stage_copy(s + S.f, L.f + own0 + j0 * hm, nr * hm, tid, nt);
+  stage_copy(s + S.d, L.invd + own0 + j0 * hm, nr * hm, tid, nt);
+  if (!zero_guess) {
+    const int jlo = max(j0 - 1, 0), jhi = min(j0 + nr, m - 1);
+    stage_copy(s + S.e, L.e + oth0 + jlo * hm, (jhi - jlo + 1) * hm, tid, nt);
+    const int x0 = j0 * (m + 1), xa = x0 & ~(V - 1), xe = (j0 + nr) * (m + 1);
+    stage_copy(s + S.x, L.tx + xa, (xe - xa + V - 1) & ~(V - 1), tid, nt);
+    stage_copy(s + S.y, L.ty + j0 * m, (nr + 1) * m, tid, nt);
+  }
+  cp_async_commit();
+}
+
+template <typename T, typename G>
+__device__ void rb_sweep_staged(const G& g, const Level<T, T>& L, int color, bool zero_guess) {
+  constexpr int V = StageVec<T>::V;
+  const int m = L.m;
+  const RbIndex R(m);
+  const int hm = R.hm;
+  const int rows = L.stage_rows;
+  const StageLayout S = stage_layout<T>(m, rows);
+  const int of = S.f, od = S.d, oe = S.e, ox = S.x, oy = S.y, bsz = S.size;
+  T* const buf = reinterpret_cast<T*>(L.stage);
+  const int own0 = color * R.half, oth0 = (color ^ 1) * R.half;
+  const int nchunk = (m + rows - 1) / rows;
+  const int tid = g.lrank(), nt = g.lsize(), np = g.nblocks();
+  int q = g.block_index(), t = 0;
+  if (q < nchunk) stage_issue(L, S, buf, q, rows, hm, own0, oth0, zero_guess, tid, nt);
+  for (; q < nchunk; q += np, ++t) {
+    if (q + np < nchunk) {
+      stage_issue(L, S, buf + ((t + 1) & 1) * bsz, q + np, rows, hm, own0, oth0, zero_guess, tid, nt);
+      cp_async_wait<1>();  // this thread's copies of chunk q are done
+    } else {
+      cp_async_wait<0>();
+    }
+    g.lsync();  // and every thread's
+    const T* s = buf + (t & 1) * bsz;
+    const int j0 = q * rows, nr = min(rows, m - j0);
+    const int jlo = max(j0 - 1, 0);
+    const int x0 = j0 * (m + 1), xd = x0 - (x0 & ~(V - 1));
+    T* const out = L.e + own0 + j0 * hm;
+    for (int h = tid; h < nr * hm; h += nt) {
+      const int jr = h >> R.lhm, k = h - (jr << R.lhm);
+      const int j = j0 + jr;
+      const int sh = (j + color) & 1;
+      const int i = (k << 1) + sh;
+      T v = s[of + h];
+      if (!zero_guess) {
+        const T* e = s + oe + (j - jlo) * hm + k;
+        const T* tx = s + ox + xd + jr * (m + 1) + i;
+        const T* ty = s + oy + jr * m + i;
+        if (i > 0) v += tx[0] * e[sh - 1];
+        if (i < m - 1) v += tx[1] * e[sh];
+        if (j > 0) v += ty[0] * e[-hm];
+        if (j < m - 1) v += ty[m] * e[hm];
+      }
+      out[h] = v * s[od + h];
+    }
+    g.lsync();  // buffer t & 1 is refilled two chunks later
+  }
+  g.sync();
+}
+
 template <typename T, typename F, typename G>
 __device__ __forceinline__ void rb_sweep(const G& g, const Level<T, F>& L, int color, bool zero_guess) {
+  if constexpr (std::is_same<T, F>::value && G::kStaged) {
+    if (L.stage) {
+      rb_sweep_staged(g, L, color, zero_guess);
+      return;
+    }
+  }
   const int m = L.m;
   const RbIndex R(m);
   const int nh = m * R.hm;  // cells of one colour
@@ -656,7 +813,7 @@ template <int PREC, typename G>
 __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned char* base,
                           GroupState<typename SolverTypes<PREC>::T, typename SolverTypes<PREC>::F>& gs,
                           typename SolverTypes<PREC>::T* red, double* red64, int& par, int& m_prev,
-                          unsigned char* base64) {
+                          unsigned char* base64, unsigned char* stage) {
   using T = typename SolverTypes<PREC>::T;
   using F = typename SolverTypes<PREC>::F;
   using TF = typename std::conditional<PREC == 3, double, T>::type;  // face assembly
@@ -731,6 +888,13 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
           gs.qv = reinterpret_cast<T*>(take(nlv * sizeof(T)));
         }
         L.cinv = L.cbuf = nullptr;
+        L.stage = nullptr;
+        L.stage_rows = 0;
+        if (std::is_same<T, F>::value && stage && ml >= kStageMin &&
+            stage_level_bytes<T>(ml, (int)blockDim.x) <= a.stage_bytes) {
+          L.stage = stage;
+          L.stage_rows = stage_rows_for(ml, (int)blockDim.x);
+        }
         if (ml <= kCoarseSide) {
           L.cinv = reinterpret_cast<T*>(take(nlv * nlv * sizeof(T)));
           L.cbuf = reinterpret_cast<T*>(take((2 * nlv + 1) * sizeof(T)));
@@ -1089,8 +1253,9 @@ __global__ void __launch_bounds__(MODE == 1 ? 32 * kWarpsPerBlock : kMaxThreads,
     const ClusterGroup g{cl.num_blocks(), cl.block_rank(), cl_part};
     const int64_t cid = blockIdx.x / g.nblk, ncl = gridDim.x / g.nblk;
     unsigned char* base = a.ws + (size_t)cid * a.ws_stride;
+    unsigned char* stage = a.stage_bytes ? smem_raw : nullptr;
     for (int64_t sys = cid; sys < n_sys; sys += ncl)
-      solve_one<PREC>(g, a, sys, base, gstate[0], red, red64, par, m_prev, nullptr);
+      solve_one<PREC>(g, a, sys, base, gstate[0], red, red64, par, m_prev, nullptr, stage);
     cl.sync();  // no block leaves while others may still read its shared memory
     return;
   }
@@ -1101,9 +1266,9 @@ __global__ void __launch_bounds__(MODE == 1 ? 32 * kWarpsPerBlock : kMaxThreads,
   const int64_t stride = (int64_t)gridDim.x * kGroups;
   for (int64_t sys = (int64_t)blockIdx.x * kGroups + gid; sys < n_sys; sys += stride) {
     if (MODE == 1)
-      solve_one<PREC>(WarpGroup(), a, sys, base, gstate[gid], red, red64, par, m_prev, base64);
+      solve_one<PREC>(WarpGroup(), a, sys, base, gstate[gid], red, red64, par, m_prev, base64, nullptr);
     else
-      solve_one<PREC>(BlockGroup(), a, sys, base, gstate[gid], red, red64, par, m_prev, base64);
+      solve_one<PREC>(BlockGroup(), a, sys, base, gstate[gid], red, red64, par, m_prev, base64, nullptr);
   }
 }
 
@@ -1131,6 +1296,16 @@ static int plan_fill(int m, int threads, int cluster, SolvePlan* P) {
   P->ws_stride = P->use_smem ? chip : (ws + 255) & ~(size_t)255;
   P->ws64_stride = P->use_smem && v64 ? (v64 + 255) & ~(size_t)255 : 0;
   P->smem_bytes = P->use_smem ? P->ws_stride * P->groups_per_block : 0;
+  // cluster plans (streamed workspace): shared memory stages the half sweeps
+  // of the large levels.  Measured on GB300 the staging pays there (m = 512 /
+  // 1024 / 2048: 8 / 11 / 18 % less time per sample) and costs 5-7 % in the
+  // one-block-per-system plans at m = 128, 256, which stay on direct loads.
+  P->stage_bytes = 0;
+  if (MODE == 2 && !P->use_smem && PREC != 2) {
+    using TS = typename SolverTypes<PREC>::T;
+    P->stage_bytes = stage_bytes_for<TS>(m, P->threads);
+    P->smem_bytes = P->stage_bytes;
+  }
   P->cap_blocks_per_sm = 0;
   P->gamma = 1;
   P->nu = 1;
@@ -1153,7 +1328,7 @@ static int plan_fill(int m, int threads, int cluster, SolvePlan* P) {
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(cluster * nsm);
     cfg.blockDim = dim3(P->threads);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = P->smem_bytes;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int ncl = 0;
@@ -1236,6 +1411,7 @@ int solve_launch(const SolveArgs& a, int prec, const SolvePlan& P, int n_blocks,
   b.use_smem = P.use_smem;
   b.ws_stride = P.ws_stride;
   b.ws64_stride = P.ws64_stride;
+  b.stage_bytes = P.stage_bytes;
   b.mg_gamma = P.gamma;
   b.mg_nu = P.nu;
   b.mg_nu_coarse = P.nu_coarse;
@@ -1250,7 +1426,7 @@ int solve_launch(const SolveArgs& a, int prec, const SolvePlan& P, int n_blocks,
     attr[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(n_blocks);  // a multiple of the cluster size
     cfg.blockDim = dim3(P.threads);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = P.smem_bytes;
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;

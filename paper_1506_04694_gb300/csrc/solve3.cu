@@ -659,6 +659,7 @@ int plan_fill3(int m, int threads, int cluster, SolvePlan* P) {
   P->ws_stride = P->use_smem ? chip : (ws + 255) & ~(size_t)255;
   P->ws64_stride = P->use_smem && v64 ? (v64 + 255) & ~(size_t)255 : 0;
   P->smem_bytes = P->use_smem ? P->ws_stride * P->groups_per_block : 0;
+  P->stage_bytes = 0;
   P->gamma = 1;
   P->nu = 1;
   P->nu_coarse = 0;
