@@ -330,6 +330,7 @@ def test_launch_modes_agree(prec):
     d = workloads.workload("lognormal_2layer_cgv_16to512", prec=prec, cgv=1, tol=1e-13, m0=16, L=4)
     model = darcy.Model.from_dict(d)
     level, n = 3, 10   # m = 128: fine 128^2 and four 64^2 coarse systems per sample
+    # (the cluster plans stage the m = 128 half sweeps through shared memory)
     modes = [(0, 512, 0, 1, 1), (0, 64, 0, 1, 1), (1, 0, 0, 1, 1), (2, 512, 2, 1, 1), (2, 512, 4, 1, 1),
              (2, 512, 8, 1, 1), (0, 256, 0, 2, 1), (1, 0, 0, 2, 1), (2, 512, 4, 2, 1), (0, 256, 0, 1, 2),
              (2, 512, 4, 1, 2), (1, 0, 0, 2, 2)]
