@@ -1,5 +1,6 @@
-// Fused assembly + multigrid-preconditioned CG + outflow QoI, one thread
-// block per linear system (many systems per launch, grid-stride over systems).
+// Fused assembly + multigrid-preconditioned CG + outflow QoI, one warp, one
+// thread block or one thread-block cluster per linear system (many systems
+// per launch, grid-stride over systems).
 //
 // System of one sample (Sec. 3.1 Eq. 3.3 with harmonic faces, Sec. 3.4 Model
 // Problem 2): unknown p on m x m cells,
