@@ -26,6 +26,8 @@ from typing import List
 
 import numpy as np
 import scipy.linalg
+import scipy.sparse
+import scipy.sparse.linalg
 
 from . import philox
 
@@ -294,11 +296,42 @@ def banded_upper(tx, ty):
     return ab
 
 
+# Grids up to this side use the banded Cholesky; larger ones a sparse LU
+# (storage of the band grows as m^3, its work as m^4).
+BANDED_MAX_M = 256
+
+
+def sparse_matrix(tx, ty):
+    """The SPD five-point matrix as a scipy CSC matrix, unknown n = j*m + i:
+    diagonal = sum of the four faces, off-diagonals = -face."""
+    m = tx.shape[0]
+    n = m * m
+    diag = (tx[:, :m] + tx[:, 1:] + ty[:m, :] + ty[1:, :]).reshape(-1)
+    east = np.zeros((m, m))
+    east[:, :m - 1] = -tx[:, 1:m]
+    e = east.reshape(-1)[:-1]
+    north = -ty[1:m, :].reshape(-1)
+    return scipy.sparse.diags([diag, e, e, north, north], [0, 1, -1, m, -m], shape=(n, n), format="csc")
+
+
+def solve_sparse(tx, ty, b):
+    """Direct sparse LU solve of the five-point system (SuperLU, minimum
+    degree ordering of A^T + A, which keeps the fill of a 2-D grid near
+    n log n)."""
+    m = tx.shape[0]
+    lu = scipy.sparse.linalg.splu(sparse_matrix(tx, ty), permc_spec="MMD_AT_PLUS_A",
+                                  options=dict(SymmetricMode=True))
+    return lu.solve(b.reshape(-1)).reshape(m, m)
+
+
 def solve_direct(tx, ty, b):
-    """Direct banded Cholesky solve of the five-point system (LAPACK pbsv)."""
+    """Direct solve of the five-point system: banded Cholesky (LAPACK pbsv)
+    for m <= BANDED_MAX_M, sparse LU above."""
     m = tx.shape[0]
     if m == 1:
         return (b / (tx[:, :1] + tx[:, 1:] + ty[:1, :] + ty[1:, :])).reshape(1, 1)
+    if m > BANDED_MAX_M:
+        return solve_sparse(tx, ty, b)
     p = scipy.linalg.solveh_banded(banded_upper(tx, ty), b.reshape(-1), lower=False)
     return p.reshape(m, m)
 
