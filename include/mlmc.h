@@ -205,11 +205,31 @@ MLMC_API int mlmc_estimate_ex(mlmc_ctx* ctx, double eps, uint64_t seed, int32_t 
                               int32_t max_rounds, mlmc_estimate_out* out);
 
 /* Write the estimator state of the last mlmc_estimate / _ex call to a text
- * file (host path).  Errors: MLMC_ERR_ARG (no estimate yet, unwritable). */
+ * file (host path).  Format (version 2), one key per line: "mlmc_checkpoint
+ * 2"; "model" n_layers k_kind norm_r m0 L cgv prec max_it problem geometry
+ * dim; "model_if" if_lo if_hi; "model_tol" tol; "model_mu", "model_sigma2",
+ * "model_lam" (8 values each), "model_qoi_box", "model_line_lo",
+ * "model_line_hi" (4 each); then seed, eps, cost_model, rounds, levels and
+ * one "level" line of counts, sums and cost per level.  Doubles carry 17
+ * significant digits, so they read back exactly.
+ * Errors: MLMC_ERR_ARG (no estimate yet, unwritable). */
 MLMC_API int mlmc_checkpoint(mlmc_ctx* ctx, const char* path);
 
-/* Load a state written by mlmc_checkpoint() for the same model; the next
- * estimate continues from it.  Errors: MLMC_ERR_ARG (unreadable, other model). */
+/* Check, on the host alone (no context or GPU needed), that the checkpoint
+ * at `path` was written for `model`: every field that changes a sample's Q
+ * or its failure must be equal (per-layer mu, sigma2 and, for log-normal
+ * fields, lam and norm_r below n_layers; the interface range with horizontal
+ * layers; the box with Model Problem 1; the line ranges with the sloped
+ * geometry; n_layers, k_kind, m0, L, cgv, prec, tol, max_it, problem,
+ * geometry and dim always).  Merging level sums of another model into an
+ * estimate would bias the telescoping sum of Eq. 3.6 without any error, so
+ * mlmc_resume() runs this check first.  Returns 0 or MLMC_ERR_ARG, with the
+ * first differing field named in mlmc_last_error(). */
+MLMC_API int mlmc_checkpoint_check(const mlmc_model* model, const char* path);
+
+/* Load a state written by mlmc_checkpoint() for the same model (checked by
+ * mlmc_checkpoint_check()); the next estimate continues from it.
+ * Errors: MLMC_ERR_ARG (unreadable, other model). */
 MLMC_API int mlmc_resume(mlmc_ctx* ctx, const char* path);
 
 /* Levels 0 .. n_levels-1 in one call: samples first[l] .. first[l]+n[l]-1 of
@@ -339,12 +359,17 @@ MLMC_API int mlmc_solve_k(mlmc_ctx* ctx, int32_t m, int64_t n, const double* k, 
  *     queuing it (results are ready when the stream reaches this point).
  * The first call on a device looks up the array's device address (one
  * cudaGetSymbolAddress per device); make that first call before any stream
- * capture.  Systems with m <= 32 use shared memory only; larger systems need
- * their whole workspace in the array, so m > 512 returns MLMC_ERR_TOOBIG.
+ * capture.  Only systems with m <= 32 and prec 0 or 3 run in shared memory
+ * alone; every other call keeps workspace in the array (with prec 1 or 2 and
+ * m <= 32, the FP64 refinement vectors; above m = 32, the whole workspace of
+ * each system in flight), so m > 512 returns MLMC_ERR_TOOBIG.  The array
+ * bounds the systems in flight: at m = 256 it holds 5 to 8 of them, at
+ * m = 512 one or two (the rest wait their turn), so large batches run with
+ * less parallelism than mlmc_solve_k().
  * Every call shares the one array and the solver initialises everything it
  * reads, so nothing carries over between calls; calls that overlap on the
  * GPU (other streams, other threads) race on the array and must be ordered
- * by the caller.
+ * by the caller.  On an error the text of mlmc_last_error() describes it.
  * Errors: MLMC_ERR_ARG, MLMC_ERR_NODEV, MLMC_ERR_TOOBIG, MLMC_ERR_CUDA. */
 MLMC_API int mlmc_solve_k_static(int device, int32_t m, int64_t n, const double* k, double* p,
                                  double* q, int32_t* iters, double tol, int32_t max_it,

@@ -102,6 +102,7 @@ EXPORTS = {
                                         ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(EstimateOut)]),
     "mlmc_checkpoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "mlmc_resume": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "mlmc_checkpoint_check": (ctypes.c_int, [ctypes.POINTER(Model), ctypes.c_char_p]),
     "mlmc_set_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "mlmc_set_solver": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_double]),
@@ -353,7 +354,9 @@ class Context:
         """mlmc_solve_k: solve the systems of a CUDA float64 tensor k [n, m, m]
         (3-D contexts: [n, m, m, m]); returns (p or None, Q, iterations)."""
         import torch
-        n, m = k.shape[0], k.shape[1]
+        n, m = _check_systems(k, 3 if self.model.dim == 3 else 2)
+        if k.device != torch.device("cuda", self.device):
+            raise MLMCError("k is on %s, the context on cuda:%d" % (k.device, self.device))
         q = torch.empty(n, dtype=torch.float64, device=k.device)
         it = torch.empty(n, dtype=torch.int32, device=k.device)
         p = torch.empty_like(k) if want_p else None
@@ -362,18 +365,52 @@ class Context:
         return p, q, it
 
 
-def solve_k_static(k, q, p=None, iters=None, tol=1e-10, max_it=500, prec=0, device=0, stream=None):
+def _check_systems(k, dim=2):
+    """Shape checks of a solver input k [n, m, m] (3-D: [n, m, m, m])."""
+    if k.dim() != dim + 1 or any(k.shape[d] != k.shape[1] for d in range(2, dim + 1)):
+        raise MLMCError("k must be [n, m, m]%s with equal sides, got %s"
+                        % (" (3-D: [n, m, m, m])" if dim == 3 else "", tuple(k.shape)))
+    return k.shape[0], k.shape[1]
+
+
+def solve_k_static(k, q, p=None, iters=None, tol=1e-10, max_it=500, prec=0, stream=None):
     """mlmc_solve_k_static: the solver with no device allocation at all, for
     callers that cannot allocate; the caller supplies every output tensor
-    (q float64 [n]; optional p float64 [n, m, m] and iters int32 [n]).  The
-    work is queued on `stream` (default: the current stream) and not waited for."""
+    (q float64 [n]; optional p float64 [n, m, m] and iters int32 [n]), all on
+    k's device.  The work is queued on `stream` (default: the current stream
+    of k's device) and not waited for."""
     import torch
-    n, m, _ = k.shape
-    rc = lib().mlmc_solve_k_static(device, m, n, _ptr(k, torch.float64), _ptr(p, torch.float64),
+    n, m = _check_systems(k)
+    dev = k.device
+    if dev.type != "cuda":
+        raise MLMCError("k must be a CUDA tensor")
+    for name, t in (("q", q), ("p", p), ("iters", iters)):
+        if t is not None and t.device != dev:
+            raise MLMCError("%s is on %s, k on %s: every tensor must be on k's device" % (name, t.device, dev))
+    if q.numel() < n:
+        raise MLMCError("q holds %d values, needs n = %d" % (q.numel(), n))
+    if iters is not None and iters.numel() < n:
+        raise MLMCError("iters holds %d values, needs n = %d" % (iters.numel(), n))
+    if p is not None and tuple(p.shape) != tuple(k.shape):
+        raise MLMCError("p must have k's shape %s, got %s" % (tuple(k.shape), tuple(p.shape)))
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    elif stream.device != dev:
+        raise MLMCError("the stream belongs to %s, k to %s" % (stream.device, dev))
+    rc = lib().mlmc_solve_k_static(dev.index, m, n, _ptr(k, torch.float64), _ptr(p, torch.float64),
                                    _ptr(q, torch.float64), _ptr(iters, torch.int32), tol, max_it, prec,
-                                   _stream_handle(stream))
+                                   ctypes.c_void_p(stream.cuda_stream))
     if rc != 0:
-        raise MLMCError("mlmc_solve_k_static: %s" % lib().mlmc_error_string(rc).decode())
+        raise MLMCError("mlmc_solve_k_static: %s: %s" % (lib().mlmc_error_string(rc).decode(),
+                                                        lib().mlmc_last_error().decode()))
+
+
+def checkpoint_check(model, path):
+    """mlmc_checkpoint_check: raises MLMCError unless the checkpoint file at
+    `path` was written for `model` (a dict with the fields of ``Model``);
+    needs no GPU."""
+    m = make_model(model)
+    _check(lib().mlmc_checkpoint_check(ctypes.byref(m), os.fsencode(path)), allow_failed=False)
 
 
 def philox_words(seed, level, sample, stream_id, first_call, n_calls, device=0):

@@ -91,6 +91,14 @@ struct WorkBufs {
 
 }  // namespace
 
+namespace mlmc {
+cudaError_t& last_launch_error() {
+  static thread_local cudaError_t e = cudaSuccess;
+  return e;
+}
+int set_error(int code, const char* what) { return fail(code, what); }
+}  // namespace mlmc
+
 // A pair of events bracketing one stage (profiling).
 struct StagePend {
   int stage, launches;
@@ -380,7 +388,7 @@ int run_solves(mlmc_ctx* c, SolveArgs a, int64_t n_samples, int nc, int64_t max_
   a.q = B.qsys.as<double>();
   a.iters = B.itsys.as<int32_t>();
   const int lr = dim_of(c->model) == 3 ? solve3_launch(a, prec, P, (int)nb, c->wst) : solve_launch(a, prec, P, (int)nb, c->wst);
-  if (lr) return fail(MLMC_ERR_CUDA, std::string("solve kernel: ") + cudaGetErrorString(cudaGetLastError()));
+  if (lr) return fail(MLMC_ERR_CUDA, std::string("solve kernel launch: ") + cudaGetErrorString(last_launch_error()));
   return 0;
 }
 
@@ -671,6 +679,75 @@ void add_sums(mlmc_level_sums& S, const mlmc_level_sums& add) {
   const double* b[10] = {&add.s_qf, &add.s_qf2, &add.s_qc, &add.s_qc2, &add.s_y,
                          &add.s_y2, &add.s_qcg, &add.s_qcg2, &add.s_yg, &add.s_yg2};
   for (int k = 0; k < 10; ++k) *a[k] += *b[k];
+}
+
+// The model block of a checkpoint: every field of mlmc_model that changes a
+// sample's Q (or which samples fail), doubles at 17 significant digits.
+void write_model_block(FILE* f, const mlmc_model& md) {
+  std::fprintf(f, "model %d %d %d %d %d %d %d %d %d %d %d\n", md.n_layers, md.k_kind, md.norm_r, md.m0, md.L,
+               md.cgv, md.prec, md.max_it, md.problem, md.geometry, dim_of(md));
+  std::fprintf(f, "model_if %.17g %.17g\nmodel_tol %.17g\n", md.if_lo, md.if_hi, md.tol);
+  auto arr = [&](const char* key, const double* v, int n) {
+    std::fprintf(f, "%s", key);
+    for (int k = 0; k < n; ++k) std::fprintf(f, " %.17g", v[k]);
+    std::fprintf(f, "\n");
+  };
+  arr("model_mu", md.mu, MLMC_MAX_LAYERS);
+  arr("model_sigma2", md.sigma2, MLMC_MAX_LAYERS);
+  arr("model_lam", md.lam, MLMC_MAX_LAYERS);
+  arr("model_qoi_box", md.qoi_box, 4);
+  arr("model_line_lo", md.line_lo, 4);
+  arr("model_line_hi", md.line_hi, 4);
+}
+
+bool read_model_block(FILE* f, mlmc_model* md) {
+  if (std::fscanf(f, "model %d %d %d %d %d %d %d %d %d %d %d\n", &md->n_layers, &md->k_kind, &md->norm_r, &md->m0,
+                  &md->L, &md->cgv, &md->prec, &md->max_it, &md->problem, &md->geometry, &md->dim) != 11)
+    return false;
+  if (std::fscanf(f, "model_if %lg %lg\nmodel_tol %lg\n", &md->if_lo, &md->if_hi, &md->tol) != 3) return false;
+  auto arr = [&](const char* key, double* v, int n) {
+    char name[32] = {};
+    if (std::fscanf(f, "%31s", name) != 1 || std::strcmp(name, key) != 0) return false;
+    for (int k = 0; k < n; ++k)
+      if (std::fscanf(f, " %lg", &v[k]) != 1) return false;
+    return std::fscanf(f, "\n") == 0;
+  };
+  return arr("model_mu", md->mu, MLMC_MAX_LAYERS) && arr("model_sigma2", md->sigma2, MLMC_MAX_LAYERS) &&
+         arr("model_lam", md->lam, MLMC_MAX_LAYERS) && arr("model_qoi_box", md->qoi_box, 4) &&
+         arr("model_line_lo", md->line_lo, 4) && arr("model_line_hi", md->line_hi, 4);
+}
+
+// The first field in which two models differ where the difference changes a
+// sample's Q or its failure (per-layer entries only below n_layers, the
+// interface range only with horizontal layers, the correlation lengths only
+// for log-normal fields, the box only for Model Problem 1, the line ranges
+// only for the sloped geometry); nullptr when they agree.
+const char* model_difference(const mlmc_model& a, const mlmc_model& b) {
+  if (a.n_layers != b.n_layers) return "n_layers";
+  if (a.k_kind != b.k_kind) return "k_kind";
+  if (a.m0 != b.m0) return "m0";
+  if (a.L != b.L) return "L";
+  if (a.cgv != b.cgv) return "cgv";
+  if (a.prec != b.prec) return "prec";
+  if (a.max_it != b.max_it) return "max_it";
+  if (a.tol != b.tol) return "tol";
+  if ((a.problem == 1) != (b.problem == 1)) return "problem";
+  if (a.geometry != b.geometry) return "geometry";
+  if (dim_of(a) != dim_of(b)) return "dim";
+  for (int t = 0; t < a.n_layers; ++t) {
+    if (a.mu[t] != b.mu[t]) return "mu";
+    if (a.sigma2[t] != b.sigma2[t]) return "sigma2";
+    if (a.k_kind == 1 && a.lam[t] != b.lam[t]) return "lam";
+  }
+  if (a.k_kind == 1 && a.norm_r != b.norm_r) return "norm_r";
+  if (a.geometry == 0 && a.n_layers > 1 && (a.if_lo != b.if_lo || a.if_hi != b.if_hi)) return "if_lo/if_hi";
+  if (a.problem == 1)
+    for (int k = 0; k < 4; ++k)
+      if (a.qoi_box[k] != b.qoi_box[k]) return "qoi_box";
+  if (a.geometry == 1)
+    for (int k = 0; k < 4; ++k)
+      if (a.line_lo[k] != b.line_lo[k] || a.line_hi[k] != b.line_hi[k]) return "line_lo/line_hi";
+  return nullptr;
 }
 
 int ensure_outputs(mlmc_ctx* c, int64_t n) {
@@ -984,17 +1061,16 @@ int mlmc_estimate(mlmc_ctx* c, double eps, uint64_t seed, int32_t n_pilot, int32
 }
 
 // Text format, one "key value..." per line; doubles with 17 significant
-// digits so that a resumed estimate is bit-identical to an uninterrupted one.
+// digits so that a resumed estimate is bit-identical to an uninterrupted one,
+// and so that the model fields read back exactly.
 int mlmc_checkpoint(mlmc_ctx* c, const char* path) {
   if (!c || !path) return fail(MLMC_ERR_ARG, "null argument");
   const auto& st = c->last_est;
   if (!st.valid) return fail(MLMC_ERR_ARG, "no estimate to checkpoint");
   FILE* f = std::fopen(path, "w");
   if (!f) return fail(MLMC_ERR_ARG, std::string("cannot write ") + path);
-  const mlmc_model& md = c->model;
-  std::fprintf(f, "mlmc_checkpoint 1\n");
-  std::fprintf(f, "model %d %d %d %d %d %d %d %d\n", md.n_layers, md.k_kind, md.m0, md.L, md.cgv, md.prec, md.norm_r,
-               dim_of(md));
+  std::fprintf(f, "mlmc_checkpoint 2\n");
+  write_model_block(f, c->model);
   std::fprintf(f, "seed %llu\neps %.17g\ncost_model %d\nrounds %d\nlevels %d\n", (unsigned long long)st.seed,
                st.eps, st.cost_model, st.rounds, (int)st.S.size());
   for (size_t l = 0; l < st.S.size(); ++l) {
@@ -1007,23 +1083,35 @@ int mlmc_checkpoint(mlmc_ctx* c, const char* path) {
   return ok ? 0 : fail(MLMC_ERR_ARG, std::string("error writing ") + path);
 }
 
+int mlmc_checkpoint_check(const mlmc_model* model, const char* path) {
+  if (!model || !path) return fail(MLMC_ERR_ARG, "null argument");
+  FILE* f = std::fopen(path, "r");
+  if (!f) return fail(MLMC_ERR_ARG, std::string("cannot read ") + path);
+  int ver = 0;
+  int r = std::fscanf(f, "mlmc_checkpoint %d\n", &ver) == 1 && ver == 2 ? 0
+          : fail(MLMC_ERR_ARG, std::string("not a version-2 checkpoint: ") + path);
+  mlmc_model other{};
+  if (!r) r = read_model_block(f, &other) ? 0 : fail(MLMC_ERR_ARG, std::string("unreadable model block: ") + path);
+  std::fclose(f);
+  if (r) return r;
+  const char* diff = model_difference(*model, other);
+  if (diff) return fail(MLMC_ERR_ARG, std::string("checkpoint of another model (") + diff + " differs): " + path);
+  return 0;
+}
+
 int mlmc_resume(mlmc_ctx* c, const char* path) {
   if (!c || !path) return fail(MLMC_ERR_ARG, "null argument");
+  if (int e = mlmc_checkpoint_check(&c->model, path)) return e;
   FILE* f = std::fopen(path, "r");
   if (!f) return fail(MLMC_ERR_ARG, std::string("cannot read ") + path);
   mlmc_ctx::EstState st;
   int ver = 0, nl = 0;
-  int mk[8];
   unsigned long long seed = 0;
-  bool ok = std::fscanf(f, "mlmc_checkpoint %d\n", &ver) == 1 && ver == 1 &&
-            std::fscanf(f, "model %d %d %d %d %d %d %d %d\n", &mk[0], &mk[1], &mk[2], &mk[3], &mk[4], &mk[5], &mk[6],
-                        &mk[7]) == 8 &&
+  mlmc_model skip{};
+  bool ok = std::fscanf(f, "mlmc_checkpoint %d\n", &ver) == 1 && read_model_block(f, &skip) &&
             std::fscanf(f, "seed %llu\neps %lg\ncost_model %d\nrounds %d\nlevels %d\n", &seed, &st.eps,
-                        &st.cost_model, &st.rounds, &nl) == 5;
-  const mlmc_model& md = c->model;
-  if (ok && (mk[0] != md.n_layers || mk[1] != md.k_kind || mk[2] != md.m0 || mk[3] != md.L || mk[4] != md.cgv ||
-             mk[5] != md.prec || mk[6] != md.norm_r || mk[7] != dim_of(md) || nl != md.L + 1))
-    ok = false;
+                        &st.cost_model, &st.rounds, &nl) == 5 &&
+            nl == c->model.L + 1;
   for (int l = 0; ok && l < nl; ++l) {
     mlmc_level_sums x{};
     long long a, b, cc;
@@ -1040,7 +1128,7 @@ int mlmc_resume(mlmc_ctx* c, const char* path) {
     st.C.push_back(cost);
   }
   std::fclose(f);
-  if (!ok) return fail(MLMC_ERR_ARG, std::string("not a checkpoint of this model: ") + path);
+  if (!ok) return fail(MLMC_ERR_ARG, std::string("unreadable estimator state: ") + path);
   st.seed = seed;
   st.valid = true;
   c->resume_est = st;

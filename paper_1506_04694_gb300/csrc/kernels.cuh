@@ -167,4 +167,10 @@ int normals_launch(uint64_t seed, uint64_t level, uint64_t sample, uint64_t stre
                    cudaStream_t st);
 int f32_to_f64_launch(const float* in, double* out, int64_t n, cudaStream_t st);
 
+// Status of the last solver launch made by this host thread (solve_launch,
+// solve3_launch), so that a caller can report the launch's own error.
+cudaError_t& last_launch_error();
+// Record `what` as this thread's mlmc_last_error() text; returns `code`.
+int set_error(int code, const char* what);
+
 }  // namespace mlmc

@@ -37,6 +37,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <string>
 #include <type_traits>
 
 #include "../../include/mlmc.h"
@@ -1418,39 +1419,42 @@ int solve_launch(const SolveArgs& a, int prec, const SolvePlan& P, int n_blocks,
   b.mg_nu_coarse = P.nu_coarse;
   b.inner_tol = P.inner_tol;
   b.reliable = P.reliable;
+  // every plan goes through cudaLaunchKernelEx, whose return value is this
+  // launch's own status (an error left pending by earlier work of the caller
+  // is neither reported nor cleared here)
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.gridDim = dim3(n_blocks);  // cluster plans: a multiple of the cluster size
+  cfg.blockDim = dim3(P.threads);
+  cfg.dynamicSmemBytes = P.smem_bytes;
+  cfg.stream = st;
   if (P.cluster) {
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = P.cluster;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(n_blocks);  // a multiple of the cluster size
-    cfg.blockDim = dim3(P.threads);
-    cfg.dynamicSmemBytes = P.smem_bytes;
-    cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const cudaError_t e = prec == 3   ? cudaLaunchKernelEx(&cfg, solve_kernel<3, 2>, b)
-                          : prec == 2 ? cudaLaunchKernelEx(&cfg, solve_kernel<2, 2>, b)
-                          : prec == 1 ? cudaLaunchKernelEx(&cfg, solve_kernel<1, 2>, b)
-                                      : cudaLaunchKernelEx(&cfg, solve_kernel<0, 2>, b);
-    return e == cudaSuccess ? 0 : -1;
   }
-  if (prec == 3) {
-    if (P.warp) solve_kernel<3, 1><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
-    else solve_kernel<3, 0><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
-  } else if (prec == 2) {
-    if (P.warp) solve_kernel<2, 1><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
-    else solve_kernel<2, 0><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
-  } else if (prec == 1) {
-    if (P.warp) solve_kernel<1, 1><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
-    else solve_kernel<1, 0><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
-  } else {
-    if (P.warp) solve_kernel<0, 1><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
-    else solve_kernel<0, 0><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
+  const int mode = P.cluster ? 2 : P.warp ? 1 : 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (prec * 3 + mode) {
+    case 0: e = cudaLaunchKernelEx(&cfg, solve_kernel<0, 0>, b); break;
+    case 1: e = cudaLaunchKernelEx(&cfg, solve_kernel<0, 1>, b); break;
+    case 2: e = cudaLaunchKernelEx(&cfg, solve_kernel<0, 2>, b); break;
+    case 3: e = cudaLaunchKernelEx(&cfg, solve_kernel<1, 0>, b); break;
+    case 4: e = cudaLaunchKernelEx(&cfg, solve_kernel<1, 1>, b); break;
+    case 5: e = cudaLaunchKernelEx(&cfg, solve_kernel<1, 2>, b); break;
+    case 6: e = cudaLaunchKernelEx(&cfg, solve_kernel<2, 0>, b); break;
+    case 7: e = cudaLaunchKernelEx(&cfg, solve_kernel<2, 1>, b); break;
+    case 8: e = cudaLaunchKernelEx(&cfg, solve_kernel<2, 2>, b); break;
+    case 9: e = cudaLaunchKernelEx(&cfg, solve_kernel<3, 0>, b); break;
+    case 10: e = cudaLaunchKernelEx(&cfg, solve_kernel<3, 1>, b); break;
+    case 11: e = cudaLaunchKernelEx(&cfg, solve_kernel<3, 2>, b); break;
+    default: break;
   }
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  last_launch_error() = e;
+  return e == cudaSuccess ? 0 : -1;
 }
 
 // Blocks to launch for n_sys systems with plan P (at most max_groups_cap
@@ -1552,13 +1556,15 @@ extern "C" int mlmc_solve_k_static(int device, int32_t m, int64_t n, const doubl
                                    double* q, int32_t* iters, double tol, int32_t max_it,
                                    int32_t prec, void* cuda_stream) {
   using namespace mlmc;
-  if (device < 0 || device >= kMaxDevices || !k || !q || n < 0) return MLMC_ERR_ARG;
-  if (m < 1 || m > 4096 || (m & (m - 1))) return MLMC_ERR_ARG;
-  if (!(tol > 0) || max_it < 1 || prec < 0 || prec > 3) return MLMC_ERR_ARG;
+  if (device < 0 || device >= kMaxDevices) return set_error(MLMC_ERR_ARG, "mlmc_solve_k_static: device index out of range");
+  if (!k || !q || n < 0) return set_error(MLMC_ERR_ARG, "mlmc_solve_k_static: k and q are required, n >= 0");
+  if (m < 1 || m > 4096 || (m & (m - 1))) return set_error(MLMC_ERR_ARG, "mlmc_solve_k_static: m must be a power of two, 1..4096");
+  if (!(tol > 0) || max_it < 1 || prec < 0 || prec > 3)
+    return set_error(MLMC_ERR_ARG, "mlmc_solve_k_static: tol > 0, max_it >= 1, prec 0..3");
   if (n == 0) return MLMC_OK;
   int prev = -1;
-  if (cudaGetDevice(&prev) != cudaSuccess) return MLMC_ERR_NODEV;
-  if (cudaSetDevice(device) != cudaSuccess) return MLMC_ERR_NODEV;
+  if (cudaGetDevice(&prev) != cudaSuccess) return set_error(MLMC_ERR_NODEV, "mlmc_solve_k_static: no usable CUDA device");
+  if (cudaSetDevice(device) != cudaSuccess) return set_error(MLMC_ERR_NODEV, "mlmc_solve_k_static: cannot select the device");
   int rc = MLMC_OK;
   do {
     // set-up, once per device, with that device current: the host-side name
@@ -1568,8 +1574,10 @@ extern "C" int mlmc_solve_k_static(int device, int32_t m, int64_t n, const doubl
       std::lock_guard<std::mutex> lock(g_static_mu);
       if (!g_static_ptr[device]) {
         void* ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_static_scratch) != cudaSuccess || !ptr) {
-          rc = MLMC_ERR_CUDA;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess || !ptr) {
+          rc = set_error(MLMC_ERR_CUDA, (std::string("mlmc_solve_k_static: cudaGetSymbolAddress: ") +
+                                         cudaGetErrorString(e)).c_str());
           break;
         }
         g_static_ptr[device] = ptr;
@@ -1580,7 +1588,7 @@ extern "C" int mlmc_solve_k_static(int device, int32_t m, int64_t n, const doubl
     int nsm = 0;
     if (solve_plan(m, prec, &P) ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
-      rc = MLMC_ERR_CUDA;
+      rc = set_error(MLMC_ERR_CUDA, "mlmc_solve_k_static: launch plan (occupancy query) failed");
       break;
     }
     SolveArgs a;
@@ -1600,7 +1608,7 @@ extern "C" int mlmc_solve_k_static(int device, int32_t m, int64_t n, const doubl
     int64_t cap = 0;
     if (!P.use_smem) {
       if (P.ws_stride > kStaticScratchBytes) {  // m above the static maximum (512)
-        rc = MLMC_ERR_TOOBIG;
+        rc = set_error(MLMC_ERR_TOOBIG, "mlmc_solve_k_static: m above the maximum of 512 for the 32 MiB scratch array");
         break;
       }
       cap = (int64_t)(kStaticScratchBytes / P.ws_stride);
@@ -1611,7 +1619,9 @@ extern "C" int mlmc_solve_k_static(int device, int32_t m, int64_t n, const doubl
     }
     int64_t nb = 0;
     solve_groups(P, n, nsm, cap, &nb);
-    if (solve_launch(a, prec, P, (int)nb, (cudaStream_t)cuda_stream)) rc = MLMC_ERR_CUDA;
+    if (solve_launch(a, prec, P, (int)nb, (cudaStream_t)cuda_stream))
+      rc = set_error(MLMC_ERR_CUDA, (std::string("mlmc_solve_k_static: solve kernel launch: ") +
+                                     cudaGetErrorString(last_launch_error())).c_str());
   } while (0);
   cudaSetDevice(prev);
   return rc;

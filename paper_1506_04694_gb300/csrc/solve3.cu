@@ -769,31 +769,27 @@ int solve3_launch(const SolveArgs& a, int prec, const SolvePlan& P, int n_blocks
   b.mg_nu_coarse = P.nu_coarse;
   b.inner_tol = P.inner_tol;
   b.ws64_stride = P.ws64_stride;
+  // cudaLaunchKernelEx for every plan: its return value is this launch's status
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.gridDim = dim3(n_blocks);
+  cfg.blockDim = dim3(P.threads);
+  cfg.dynamicSmemBytes = P.cluster ? 0 : P.smem_bytes;
+  cfg.stream = st;
   if (P.cluster) {
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = P.cluster;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(n_blocks);
-    cfg.blockDim = dim3(P.threads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const cudaError_t e = prec ? cudaLaunchKernelEx(&cfg, solve3_kernel<true, 2>, b)
-                               : cudaLaunchKernelEx(&cfg, solve3_kernel<false, 2>, b);
-    return e == cudaSuccess ? 0 : -1;
   }
-  if (prec) {
-    if (P.warp) solve3_kernel<true, 1><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
-    else solve3_kernel<true, 0><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
-  } else {
-    if (P.warp) solve3_kernel<false, 1><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
-    else solve3_kernel<false, 0><<<n_blocks, P.threads, P.smem_bytes, st>>>(b);
-  }
-  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+  cudaError_t e;
+  if (P.cluster) e = prec ? cudaLaunchKernelEx(&cfg, solve3_kernel<true, 2>, b) : cudaLaunchKernelEx(&cfg, solve3_kernel<false, 2>, b);
+  else if (P.warp) e = prec ? cudaLaunchKernelEx(&cfg, solve3_kernel<true, 1>, b) : cudaLaunchKernelEx(&cfg, solve3_kernel<false, 1>, b);
+  else e = prec ? cudaLaunchKernelEx(&cfg, solve3_kernel<true, 0>, b) : cudaLaunchKernelEx(&cfg, solve3_kernel<false, 0>, b);
+  last_launch_error() = e;
+  return e == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace mlmc

@@ -84,3 +84,60 @@ def test_bad_model_rejected_before_device(pk):
                        "norm_r": 2})
     h = ctypes.c_void_p()
     assert pk.lib().mlmc_create(0, ctypes.byref(m), None, ctypes.byref(h)) == -1
+
+
+def _checkpoint_text(d, levels):
+    """A checkpoint file in the documented version-2 text format (model block,
+    estimator header, one line per level), written without a GPU."""
+    pad = lambda v, n: list(v) + [v[-1]] * (n - len(v))
+    g = lambda x: "%.17g" % x
+    lines = ["mlmc_checkpoint 2",
+             "model %d %d %d %d %d %d %d %d %d %d %d" % (
+                 d["n_layers"], d["k_kind"], d["norm_r"], d["m0"], d["L"], d["cgv"], d["prec"], d["max_it"],
+                 d.get("problem", 0), d.get("geometry", 0), d.get("dim", 2)),
+             "model_if %s %s" % (g(d["if_lo"]), g(d["if_hi"])), "model_tol %s" % g(d["tol"])]
+    for key in ("mu", "sigma2", "lam"):
+        lines.append("model_%s %s" % (key, " ".join(g(x) for x in pad(d[key], 8))))
+    for key in ("qoi_box", "line_lo", "line_hi"):
+        lines.append("model_%s %s" % (key, " ".join(g(x) for x in d.get(key, [0.0] * 4))))
+    lines += ["seed 0", "eps 0.001", "cost_model 0", "rounds 1", "levels %d" % levels]
+    for l in range(levels):
+        lines.append("level %d 64 0 640 %s" % (l, " ".join(["1"] * 12)))
+    return "\n".join(lines) + "\n"
+
+
+def test_checkpoint_check_rejects_other_models(pk, tmp_path):
+    # merging the level sums of another model would bias the telescoping sum of
+    # Eq. 3.6 silently, so a checkpoint must match every field that changes Q
+    import workloads
+    d = workloads.workload("lognormal_2layer_16to256")
+    path = tmp_path / "ck.txt"
+    path.write_text(_checkpoint_text(d, d["L"] + 1))
+    pk.checkpoint_check(d, str(path))  # the same model is accepted
+    for key, val in (("sigma2", [1.5, 1.5]), ("lam", [0.2, 0.2]), ("mu", [0.0, 0.1]), ("tol", 1e-12),
+                     ("if_lo", 0.25), ("if_hi", 0.75), ("norm_r", 1), ("prec", 1), ("cgv", 1), ("m0", 8),
+                     ("max_it", 100)):
+        with pytest.raises(pk.MLMCError, match="differs"):
+            pk.checkpoint_check(dict(d, **{key: val}), str(path))
+    # fields that do not change Q for this model are not compared: the box of
+    # Model Problem 1 and the line ranges of the sloped geometry
+    pk.checkpoint_check(dict(d, qoi_box=[0.1, 0.2, 0.3, 0.4]), str(path))
+    pk.checkpoint_check(dict(d, line_lo=[0.1] * 4, line_hi=[0.2] * 4), str(path))
+    # a version-1 file (model line without the per-layer parameters) is refused
+    old = tmp_path / "v1.txt"
+    old.write_text("mlmc_checkpoint 1\nmodel 2 1 16 4 0 0 2 2\n")
+    with pytest.raises(pk.MLMCError, match="version-2"):
+        pk.checkpoint_check(d, str(old))
+
+
+def test_solve_wrappers_check_shapes_on_host(pk):
+    # the binding rejects tensors of the wrong shape or device before any C
+    # call, so no wrong-sized pointer reaches a kernel
+    import torch
+    q = torch.empty(2, dtype=torch.float64)
+    with pytest.raises(pk.MLMCError, match="equal sides"):
+        pk.solve_k_static(torch.ones((2, 8, 4), dtype=torch.float64), q)
+    with pytest.raises(pk.MLMCError, match="equal sides"):
+        pk.solve_k_static(torch.ones((8, 8), dtype=torch.float64), q)
+    with pytest.raises(pk.MLMCError, match="CUDA"):
+        pk.solve_k_static(torch.ones((2, 8, 8), dtype=torch.float64), q)

@@ -302,10 +302,13 @@ def test_checkpoint_resume_bit_identical(tmp_path):
         rest = ctx.estimate(eps, seed=21, n_pilot=32, max_rounds=10)
     assert rest["N"] == full["N"] and rest["rounds"] == full["rounds"]
     assert rest["q_hat"] == full["q_hat"] and rest["var_hat"] == full["var_hat"]
-    # a checkpoint of another model is refused
-    with pk.Context(dict(d, m0=8)) as ctx:
-        with pytest.raises(pk.MLMCError):
-            ctx.resume(path)
+    # a checkpoint of another model is refused: another grid, and the same
+    # grid with another variance or correlation length (merging those level
+    # sums would bias the estimate without any error)
+    for other in (dict(d, m0=8), dict(d, sigma2=[1.5, 1.5]), dict(d, lam=[0.2, 0.2])):
+        with pk.Context(other) as ctx:
+            with pytest.raises(pk.MLMCError, match="differs"):
+                ctx.resume(path)
 
 
 def test_nan_permeability_reported_as_failure():

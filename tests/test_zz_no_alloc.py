@@ -15,10 +15,14 @@ pytestmark = pytest.mark.gpu
 RTOL = 1e-10
 
 
-@pytest.mark.parametrize("m,prec", [(16, 0), (64, 0), (128, 0), (256, 0), (128, 1), (128, 2), (128, 3)])
+# (16, 0): shared memory only; (32, 1), (32, 2): shared memory with the FP64
+# refinement vectors in the array; 64 ... 256: whole workspaces in the array;
+# 512: the documented maximum, where the array holds one or two systems.
+@pytest.mark.parametrize("m,prec", [(16, 0), (32, 1), (32, 2), (64, 0), (128, 0), (256, 0), (128, 1), (128, 2),
+                                    (128, 3), (512, 0), (512, 1)])
 def test_static_scratch_matches_context_solve(m, prec):
     torch, pk = need_gpu()
-    n = 24 if m <= 64 else 6
+    n = 24 if m <= 64 else 6 if m <= 256 else 3
     d = workloads.workload("const_2layer_8to32", tol=1e-12, max_it=500, prec=prec)
     with pk.Context(d) as ctx:
         for call in range(2):  # two calls in a row on the shared array
