@@ -31,9 +31,10 @@ import scipy.sparse.linalg
 
 from . import philox
 
-# Padding rule of the circulant embedding: grow M = p*m (p = 2, 4, 8, ...)
-# until every eigenvalue of the embedding is >= -CE_NEG_TOL * max eigenvalue;
-# eigenvalues inside that band are clipped to zero.
+# Padding rule of the circulant embedding: try the embeddings of
+# padding_candidates (M = 2m, the cut-off one at 3m, then 4m, 8m, 16m) until
+# every eigenvalue is >= -CE_NEG_TOL * the largest; eigenvalues inside that
+# band are clipped to zero.
 CE_NEG_TOL = 1e-13
 CE_MAX_PAD = 16
 
@@ -58,6 +59,8 @@ class Model:
         cut by the straight lines (0, y1)-(1, y2) and (0, y3)-(1, y4), with
         y_t ~ U(line_lo[t], line_hi[t]).
     dim: 2, or 3 for the extruded 3-D medium of Sec. 3.4 (oracle/darcy3.py).
+    embed: 0 = the cut-off embedding at M = 3m may be chosen (2-D, 2-norm),
+        1 = periodic embeddings with M = 2m, 4m, 8m, 16m only.
     """
     n_layers: int = 2
     k_kind: int = 0
@@ -79,6 +82,7 @@ class Model:
     line_lo: List[float] = field(default_factory=lambda: [0.8, 0.6, 0.2, 0.4])
     line_hi: List[float] = field(default_factory=lambda: [0.9, 0.7, 0.3, 0.5])
     dim: int = 2
+    embed: int = 0
 
     @classmethod
     def from_dict(cls, d):
@@ -162,9 +166,35 @@ def layer_of_rows(eta, m):
 
 
 # ------------------------------------------------------ circulant embedding --
-def covariance_torus(m, M, sigma2, lam, norm_r):
+def cutoff_radii(m, M):
+    """(R0, R1) of the cut-off embedding: R0 = sqrt(2) (m - 1) h, the largest
+    distance between two cell centres of the unit square, and R1 = M h / 2,
+    half the side of the torus (h = 1/m)."""
+    return np.sqrt(2.0) * (m - 1) / m, M / (2.0 * m)
+
+
+def cutoff_covariance(r, m, M, sigma2, lam):
+    """The radial function of the cut-off embedding (2-norm): the covariance
+    of Eq. 2.3, sigma2 exp(-r/lam), up to R0; between R0 and R1 the cubic
+    that continues it with the same value and slope at R0 and reaches zero
+    with zero slope at R1; zero beyond R1.  It equals Eq. 2.3 at every
+    distance between two cell centres, and with R1 <= M h / 2 its periodic
+    copies on the M x M torus do not overlap."""
+    R0, R1 = cutoff_radii(m, M)
+    r = np.asarray(r, dtype=np.float64)
+    c = sigma2 * np.exp(-r / lam)
+    w = R1 - R0
+    t = (r - R0) / w
+    c0 = sigma2 * np.exp(-R0 / lam)      # value at R0
+    d0 = -c0 / lam * w                   # slope at R0, in units of t
+    taper = c0 * (2 * t ** 3 - 3 * t ** 2 + 1) + d0 * (t ** 3 - 2 * t ** 2 + t)
+    return np.where(r <= R0, c, np.where(r < R1, taper, 0.0))
+
+
+def covariance_torus(m, M, sigma2, lam, norm_r, cutoff=False):
     """c[b, a] = sigma2 * exp(-||(d_a h, d_b h)||_r / lam) on the M x M torus of
-    cell-centre offsets (Eq. 2.3), d_a = min(a, M - a), h = 1/m."""
+    cell-centre offsets (Eq. 2.3), d_a = min(a, M - a), h = 1/m; with cutoff
+    (2-norm only) the cut-off radial function of the same distance."""
     a = np.arange(M)
     d = np.minimum(a, M - a) / m
     dx = d[None, :]
@@ -173,27 +203,39 @@ def covariance_torus(m, M, sigma2, lam, norm_r):
         dist = np.abs(dx) + np.abs(dy)
     else:
         dist = np.sqrt(dx * dx + dy * dy)
+    if cutoff:
+        assert norm_r == 2
+        return cutoff_covariance(dist, m, M, sigma2, lam)
     return sigma2 * np.exp(-dist / lam)
 
 
-def ce_eigenvalues(m, M, sigma2, lam, norm_r):
+def ce_eigenvalues(m, M, sigma2, lam, norm_r, cutoff=False):
     """Eigenvalues of the block-circulant embedding: the unnormalised forward
     2-D DFT of the torus covariance (real because c is even)."""
-    return np.fft.fft2(covariance_torus(m, M, sigma2, lam, norm_r)).real
+    return np.fft.fft2(covariance_torus(m, M, sigma2, lam, norm_r, cutoff)).real
 
 
-def ce_padding(m, sigma2, lam, norm_r):
-    """Smallest M = p*m, p in {2, 4, 8, 16}, whose embedding is non-negative up to
-    the clipping band; returns (M, eigenvalues clipped to >= 0)."""
-    p = 2
-    while True:
+def padding_candidates(m, norm_r, embed=0):
+    """The embeddings tried, in order, as (p, cutoff): the periodic embedding
+    at p = 2, then (2-norm, m >= 8, embed == 0) the cut-off embedding at
+    p = 3, then the periodic one at p = 4, 8, 16.  The cut-off needs the
+    torus half-side M h / 2 above the largest centre distance sqrt(2), which
+    p = 3 gives and p = 2 does not."""
+    out = [(2, False)]
+    if embed == 0 and norm_r == 2 and m >= 8:
+        out.append((3, True))
+    return out + [(4, False), (8, False), (16, False)]
+
+
+def ce_padding(m, sigma2, lam, norm_r, embed=0):
+    """The first embedding of padding_candidates whose eigenvalues are all
+    >= -CE_NEG_TOL * max; returns (M, eigenvalues clipped to >= 0)."""
+    for p, cut in padding_candidates(m, norm_r, embed):
         M = p * m
-        lam_q = ce_eigenvalues(m, M, sigma2, lam, norm_r)
-        if lam_q.min() >= -CE_NEG_TOL * lam_q.max() or p >= CE_MAX_PAD:
-            if lam_q.min() < -CE_NEG_TOL * lam_q.max():
-                raise ValueError("circulant embedding not non-negative at p=%d" % p)
+        lam_q = ce_eigenvalues(m, M, sigma2, lam, norm_r, cut)
+        if lam_q.min() >= -CE_NEG_TOL * lam_q.max():
             return M, np.maximum(lam_q, 0.0)
-        p *= 2
+    raise ValueError("circulant embedding not non-negative at p=%d" % CE_MAX_PAD)
 
 
 def ce_pair(lam_q, xi, m):
@@ -218,11 +260,11 @@ def layer_fields(model, seed, level, sample, m, ce_cache=None):
         return g
     slots, params = field_slots(model)
     for f, (sigma2, lam) in enumerate(params):
-        key = (m, sigma2, lam, model.norm_r)
+        key = (m, sigma2, lam, model.norm_r, model.embed)
         if ce_cache is not None and key in ce_cache:
             M, lam_q = ce_cache[key]
         else:
-            M, lam_q = ce_padding(m, sigma2, lam, model.norm_r)
+            M, lam_q = ce_padding(m, sigma2, lam, model.norm_r, model.embed)
             if ce_cache is not None:
                 ce_cache[key] = (M, lam_q)
         xi = philox.field_normals(seed, level, sample, f, M)

@@ -66,18 +66,72 @@ def test_exact_covariance_of_sampler(norm_r, lam, s2):
 
 
 def test_padding_rule():
-    # lambda = 0.3, 2-norm: the minimal non-negative padding grows with m
-    # (p = 2 up to m = 16, then 4, then 8 at m = 512); short correlation
-    # lengths embed at p = 2.
-    got = {m: darcy.ce_padding(m, 1.0, 0.3, 2)[0] // m for m in (8, 16, 32, 64, 128, 256)}
-    assert got == {8: 2, 16: 2, 32: 4, 64: 4, 128: 4, 256: 4}
+    # lambda = 0.3, 2-norm: the periodic embedding at p = 2 holds up to m = 16;
+    # above, the cut-off embedding at p = 3 (up to m = 1024), where the
+    # periodic one needs p = 4 (m = 32 ... 256) and p = 8 (m = 512, the
+    # embed = 1 rule); short correlation lengths embed at p = 2.
+    got = {m: darcy.ce_padding(m, 1.0, 0.3, 2)[0] // m for m in (8, 16, 32, 64, 128, 256, 512)}
+    assert got == {8: 2, 16: 2, 32: 3, 64: 3, 128: 3, 256: 3, 512: 3}
+    old = {m: darcy.ce_padding(m, 1.0, 0.3, 2, embed=1)[0] // m for m in (8, 16, 32, 64, 128, 256, 512)}
+    assert old == {8: 2, 16: 2, 32: 4, 64: 4, 128: 4, 256: 4, 512: 8}
     assert darcy.ce_padding(64, 3.0, 0.1, 2)[0] == 128
     assert darcy.ce_padding(64, 1.0, 0.05, 2)[0] == 128
+    assert darcy.ce_padding(64, 1.0, 0.3, 1)[0] == 128  # the 1-norm never takes the cut-off
     for m in (8, 32, 64):
         M, lam_q = darcy.ce_padding(m, 1.0, 0.3, 2)
-        raw = darcy.ce_eigenvalues(m, M, 1.0, 0.3, 2)
+        raw = darcy.ce_eigenvalues(m, M, 1.0, 0.3, 2, cutoff=(M == 3 * m))
         assert raw.min() >= -darcy.CE_NEG_TOL * raw.max()
         assert lam_q.min() >= 0.0
+
+
+def test_cutoff_radial_function():
+    # equal to Eq. 2.3 up to R0 (the largest centre distance), C^1 at R0 and
+    # R1, zero from R1 = M h / 2 on
+    m, M, s2, lam = 32, 96, 1.7, 0.3
+    R0, R1 = darcy.cutoff_radii(m, M)
+    assert R0 == pytest.approx(math.sqrt(2) * 31 / 32) and R1 == 1.5
+    r = np.linspace(0, R0, 1001)
+    np.testing.assert_allclose(darcy.cutoff_covariance(r, m, M, s2, lam), s2 * np.exp(-r / lam), rtol=1e-15)
+    f = lambda x: float(darcy.cutoff_covariance(np.array(x), m, M, s2, lam))
+    h = 1e-6
+    for R in (R0, R1):
+        left = 2 * f(R - h) - f(R - 2 * h)   # value at R extrapolated from either side
+        right = 2 * f(R + h) - f(R + 2 * h)
+        assert abs(left - right) < 1e-10                             # continuous
+        slope_l = (f(R - h) - f(R - 2 * h)) / h
+        slope_r = (f(R + 2 * h) - f(R + h)) / h
+        assert abs(slope_l - slope_r) < 1e-4                         # continuous slope
+    assert f(R1) == 0.0 and f(R1 + 0.3) == 0.0 and f(0.5 * (R0 + R1)) > 0.0
+    # the torus table holds the same values at every lag of two cell centres
+    c = darcy.covariance_torus(m, M, s2, lam, 2, cutoff=True)
+    a = np.arange(m)
+    np.testing.assert_allclose(c[:m, :m], s2 * np.exp(-np.hypot(a[None, :], a[:, None]) / m / lam), rtol=1e-15)
+
+
+@pytest.mark.parametrize("m,forced", [(8, True), (32, False)])
+def test_exact_covariance_of_cutoff_sampler(m, forced):
+    # The cut-off embedding changes the covariance only at lags beyond the
+    # grid, so the linear sampling map still reproduces Eq. 2.3 exactly at
+    # every pair of cell centres (m = 8: the cut-off forced at M = 24; m = 32:
+    # the embedding the padding rule picks, M = 96).
+    lam, s2 = 0.3, 1.0
+    if forced:
+        M = 3 * m
+        raw = darcy.ce_eigenvalues(m, M, s2, lam, 2, cutoff=True)
+        assert raw.min() >= 0.0
+        lam_q = raw
+    else:
+        M, lam_q = darcy.ce_padding(m, s2, lam, 2)
+        assert M == 3 * m
+    B = sampling_map(m, M, lam_q)
+    A_re = np.hstack([B.real, -B.imag])
+    A_im = np.hstack([B.imag, B.real])
+    jj, ii = np.divmod(np.arange(m * m), m)
+    dist = np.hypot(np.abs(ii[:, None] - ii[None, :]) / m, np.abs(jj[:, None] - jj[None, :]) / m)
+    target = s2 * np.exp(-dist / lam)
+    np.testing.assert_allclose(A_re @ A_re.T, target, atol=1e-12)
+    np.testing.assert_allclose(A_im @ A_im.T, target, atol=1e-12)
+    assert np.abs(A_re @ A_im.T).max() < 1e-12
 
 
 @pytest.mark.parametrize("p_small", [2])
