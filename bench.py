@@ -3,43 +3,59 @@
 
 One step = one complete adaptive MLMC estimate to RMSE eps (pilot batches on
 every level, then top-ups to the cost-optimal N_l until the sampling error is
-<= eps^2/2), i.e. one pass of every stage of the hot path: Philox normals,
-circulant-embedding fields, TPFA assembly, multigrid-preconditioned CG, the
-outflow QoI, the level reduction and the estimator.  Default workload: two
-layers, piecewise log-normal fields (sigma^2 = 1, lambda = 0.3, 2-norm),
-levels m = 16 .. 256, eps = 1e-3, FP64.
+<= eps^2/2): one pass of every stage of the hot path over every level --
+Philox normals, circulant-embedding fields, TPFA assembly, the multigrid-
+preconditioned CG, the outflow QoI, the level reduction and the estimator.
 
-value = level samples solved per second (sum_l N_l over all ranks / time);
-ms_per_step = the time-to-eps of one estimate.
+Default workload: two layers, piecewise log-normal fields (sigma^2 = 1,
+lambda = 0.3, 2-norm), levels m = 16 .. 512, eps = 5e-4, in the mixed form
+with Coarse Grid Variates (FP32 fields and multigrid inside FP64 refinement;
+FP64 residual, QoI and sums).  The same estimate in plain FP64 batched MLMC
+(no CGV) at the same eps and level set is timed in the same run, and the
+line reports both times-to-eps and their ratio.
+
+value = level samples solved per second by the mixed CGV arm (sum_l N_l over
+all ranks / time); ms_per_step = its time-to-eps.  The timed estimates run
+with the levels of each round side by side under one CUDA graph; the stage
+and per-level timings of the roofline come from a separate, untimed pass
+with CUDA events around every stage (levels one after another).
 
 --impl reference times the CPU FP64 oracle on the host cores on a bounded
 sample of the same workload and prints the same line with "impl": "reference".
+--profile-case CASE runs one of the fixed small cases used for ncu captures;
+--ncu-summary CSV summarises an ncu launch list (kernel, launches, time, share).
 """
 import argparse
+import collections
+import csv
 import json
-import math
 import os
 import subprocess
-import tempfile
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-DEFAULT_WORKLOAD = "lognormal_2layer_16to256"
-# FP64 vector peak of GB300 (nominal 1.25 TFLOP/s: 152 SMs x 2 FP64 FMA/clk x
-# 2 flop x ~2.06 GHz).
-FP64_PEAK_TFLOPS = 1.25
-FP32_PEAK_TFLOPS = 80.5
-# Sample of the oracle timed for the CPU baseline: samples per level.
-CPU_SAMPLE = {0: 512, 1: 128, 2: 48, 3: 16, 4: 8, 5: 2, 6: 1}
+DEFAULT_WORKLOAD = "lognormal_2layer_cgv_16to512"
+# Copy-bandwidth fallback (an earlier GB300 measurement) when the measured
+# peaks file is absent.
+HBM_FALLBACK_GBS = 6800.0
+# Samples per level of one bounded oracle sample (CPU baseline and reference arm).
+CPU_SAMPLE = {0: 256, 1: 64, 2: 32, 3: 16, 4: 16, 5: 16, 6: 2}
+PREC_NAMES = {0: "fp64", 1: "fp32-mg/fp64-refinement", 2: "fp32-mg-bf16-faces/fp64-refinement",
+              3: "fp64-cg/fp32-mg-preconditioner"}
 
 
+# ------------------------------------------------------------- oracle side --
 def _worker_init():
     os.environ["OMP_NUM_THREADS"] = "1"
     os.environ["OPENBLAS_NUM_THREADS"] = "1"
+
+
+_CE_CACHE = {}  # embedding tables of a worker process, per workload
 
 
 def _oracle_worker(job):
@@ -50,8 +66,8 @@ def _oracle_worker(job):
     from oracle import darcy
     name, overrides, level, first, n, seed = job
     model = darcy.Model.from_dict(workloads.workload(name, **overrides))
-    cache = {}
-    darcy.layer_fields(model, seed, level, first, model.m(level), cache)  # embedding table
+    cache = _CE_CACHE.setdefault((name, tuple(sorted(overrides.items()))), {})
+    darcy.layer_fields(model, seed, level, first, model.m(level), cache)  # embedding table (once per process)
     t = time.perf_counter()
     out = []
     for i in range(first, first + n):
@@ -60,28 +76,34 @@ def _oracle_worker(job):
     return level, time.perf_counter() - t, out
 
 
-def oracle_rates(name, overrides, levels, seed, cores):
+def oracle_rates(name, overrides, levels, seed, cores, pool=None):
     """Per-level oracle throughput (samples/s) on `cores` spawned processes,
-    plus the per-sample results."""
+    the per-sample results, and the wall time of the whole sample."""
     import multiprocessing as mp
-    ctx = mp.get_context("spawn")
     jobs = []
     for lvl in levels:
         n = CPU_SAMPLE.get(lvl, 1)
         per = max(1, n // cores)
         for c0 in range(0, n, per):
             jobs.append((name, overrides, lvl, 10_000_000 + c0, min(per, n - c0), seed))
+    own = pool is None
+    if own:
+        pool = mp.get_context("spawn").Pool(cores, initializer=_worker_init)
     rates, results = {}, {}
-    with ctx.Pool(cores, initializer=_worker_init) as pool:
+    t_all = time.perf_counter()
+    try:
         for lvl in levels:
             lj = [j for j in jobs if j[2] == lvl]
             t = time.perf_counter()
             res = pool.map(_oracle_worker, lj)
             wall = time.perf_counter() - t
-            n = sum(j[4] for j in lj)
-            rates[lvl] = n / wall
+            rates[lvl] = sum(j[4] for j in lj) / wall
             results[lvl] = [x for r in res for x in r[2]]
-    return rates, results
+    finally:
+        if own:
+            pool.close()
+            pool.join()
+    return rates, results, time.perf_counter() - t_all
 
 
 def host_cores():
@@ -91,6 +113,7 @@ def host_cores():
         return os.cpu_count() or 1
 
 
+# ------------------------------------------------------------------ clocks --
 class ClockSampler:
     """nvidia-smi clock / throttle-reason sampling during the timed region."""
 
@@ -105,7 +128,9 @@ class ClockSampler:
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            d = os.path.dirname(self.path)
+            if d:
+                os.makedirs(d, exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
@@ -144,59 +169,24 @@ class ClockSampler:
             return None
 
 
-def run_reference(args, d):
-    """The CPU oracle on the host cores, bounded sample; same metric and unit."""
-    cores = min(host_cores(), 16)
-    L = d["L"]
-    levels = list(range(L + 1))
-    times, values = [], []
-    from oracle import mlmc
-    import numpy as np
-    for step in range(args.warmup + args.steps):
-        rates, results = oracle_rates(args.workload, {}, levels, args.seed, cores)
-        # sample sizes from the oracle's own pilot variances (deterministic cost model)
-        V = []
-        for lvl in levels:
-            arr = np.array(results[lvl])
-            y = arr[:, 0] - (arr[:, 2] if (d["cgv"] and lvl) else arr[:, 1])
-            V.append(float(np.var(y, ddof=1)) if len(y) > 1 else float(np.var(arr[:, 0])))
-        from oracle import darcy
-        model = darcy.Model.from_dict(d)
-        C = [mlmc.parity_cost(model, lvl) for lvl in levels]
-        N = mlmc.optimal_samples(d["eps"], V, C)
-        t_eps = sum(n / rates[lvl] for lvl, n in zip(levels, N))
-        if step >= args.warmup:
-            times.append(t_eps)
-            values.append(sum(N) / t_eps)
-    value = sum(values) / len(values)
-    ms = 1000 * sum(times) / len(times)
-    sample = ("oracle (numpy/scipy FP64; banded Cholesky in 2-D, sparse LU in 3-D) on %d spawned processes; per step %s samples "
-              "of levels %s timed, time-to-eps extrapolated as sum_l N_l / rate_l with N_l from the "
-              "oracle's pilot variances" % (cores, [CPU_SAMPLE.get(lv, 1) for lv in levels], levels))
-    return {"impl": "reference", "metric": metric_name(d, args), "value": value, "unit": "level-samples/s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (Philox4x64-10 streams)", "config": config_block(args, d),
-            "cpu_baseline": {"value": value, "unit": "level-samples/s", "cores": cores, "kind": "oracle",
-                             "sample": sample},
-            "e2e": {"value": value, "unit": "level-samples/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+# ---------------------------------------------------------------- helpers --
+def metric_name(d):
+    return ("level solves/s and time-to-RMSE eps=%g: %d-layer piecewise log-normal%s, m=%d..%d, %s%s"
+            % (d["eps"], d["n_layers"], ", 3-D" if d.get("dim", 2) == 3 else "", d["m0"], d["m0"] << d["L"],
+               {0: "plain FP64", 1: "mixed FP32-MG/FP64", 2: "mixed FP32-MG (BF16 faces)/FP64",
+                3: "FP64 CG with FP32-MG preconditioner"}[d["prec"]], " + CGV" if d["cgv"] else ""))
 
 
-def metric_name(d, args):
-    return ("level solves/s: MLMC time-to-RMSE eps=%g, %d-layer piecewise log-normal%s, m=%d..%d, %s%s"
-            % (d["eps"], d["n_layers"], ", 3-D" if d.get("dim", 2) == 3 else "", d["m0"], d["m0"] << d["L"], {0: "FP64", 1: "mixed FP32-MG", 2: "mixed FP32-MG (BF16 faces)",
-                                                         3: "FP64 CG with FP32-MG preconditioner"}[d["prec"]],
-               ", CGV" if d["cgv"] else ""))
-
-
-def config_block(args, d):
-    return {"workload": args.workload, "m_levels": [d["m0"] << l for l in range(d["L"] + 1)],
-            "eps": d["eps"], "sigma2": d["sigma2"][0], "lambda": d["lam"][0], "layers": d["n_layers"],
-            "dim": d.get("dim", 2), "norm_r": d["norm_r"],
-            "cgv": d["cgv"], "prec": PREC_NAMES[d["prec"]],
-            "solver_tol": d["tol"], "seed": args.seed, "cost_model": "deterministic m_l^d (1 + n_coarse/2^d)",
-            "l2": "flushed between steps (256 MB device write)", "parallelism": "replicas%d" % args.gpus}
+def config_block(args, d, baseline):
+    c = {"workload": args.workload, "m_levels": [d["m0"] << l for l in range(d["L"] + 1)],
+         "eps": d["eps"], "sigma2": d["sigma2"][0], "lambda": d["lam"][0], "layers": d["n_layers"],
+         "dim": d.get("dim", 2), "norm_r": d["norm_r"], "cgv": d["cgv"], "prec": PREC_NAMES[d["prec"]],
+         "solver_tol": d["tol"], "seed": args.seed, "cost_model": "deterministic m_l^d (1 + n_coarse/2^d)",
+         "l2": "flushed between steps (256 MB device write)", "parallelism": "replicas%d" % args.gpus,
+         "graph": "levels of a round side by side under one CUDA graph"}
+    if baseline is not None:
+        c["baseline_arm"] = {"prec": PREC_NAMES[baseline["prec"]], "cgv": baseline["cgv"]}
+    return c
 
 
 def reduce_over_ranks(total_ms, n_total, device):
@@ -213,16 +203,284 @@ def reduce_over_ranks(total_ms, n_total, device):
     return float(t.item()), float(n.item())
 
 
-PREC_NAMES = {0: "fp64", 1: "fp32-mg/fp64-refinement", 2: "fp32-mg-bf16-faces/fp64-refinement",
-              3: "fp64-cg/fp32-mg-preconditioner"}
+def measured_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        v = float(json.load(open(p))["hbm_gbs"])
+        return v, "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"
 
 
+def timed_estimates(ctx, d, seed, steps, warmup, flush, stream):
+    """`warmup` untimed estimates, then `steps` timed ones (CUDA events on the
+    context's stream, L2 flushed before each); returns (ms list, last estimate)."""
+    import torch
+    for _ in range(warmup):
+        ctx.estimate(d["eps"], seed, n_pilot=64, cost_model=0)
+    torch.cuda.synchronize()
+    ms, est = [], None
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        est = ctx.estimate(d["eps"], seed, n_pilot=64, cost_model=0)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms, est
+
+
+def solve_kernel_name(prec, t):
+    mode = 2 if t["cluster"] else 1 if t["warp"] else 0
+    return "solve_kernel<%d, %d>" % (prec, mode)
+
+
+def profiled_pass(ctx, d, est, seed, tune):
+    """Untimed: one estimate with stage events (levels in series), then every
+    level alone at the estimate's N_l with stage events.  Returns the stage
+    totals per step and the per-level records."""
+    ctx.profile(True)
+    ctx.estimate(d["eps"], seed, n_pilot=64, cost_model=0)
+    tot = ctx.profile_read()
+    ctx.profile(False)
+    per = []
+    for lvl, n in enumerate(est["N"]):
+        ctx.profile(True)
+        s = ctx.level_batch(lvl, n, seed)
+        p = ctx.profile_read()
+        ctx.profile(False)
+        t = tune[lvl]
+        per.append({"level": lvl, "m": d["m0"] << lvl, "N": n, "fields_ms": p["ms"]["fields"],
+                    "solve_ms": p["ms"]["solve"], "reduce_ms": p["ms"]["reduce"],
+                    "iters_per_sample": s["iters_total"] / max(s["n"], 1),
+                    "cell_iters": p["cell_iters"], "solve_bytes": p["solve_bytes"],
+                    "solve_flops": p["solve_flops"], "fft_flops": p["fft_flops"], "fft_bytes": p["fft_bytes"],
+                    "solve_kernel": solve_kernel_name(d["prec"], t), "smem": t["smem"],
+                    "plan": {"threads": t["threads"], "warp": t["warp"], "cluster": t["cluster"], "nu": t["nu"],
+                             "nu_coarse": t["nu_coarse"], "gamma": t["gamma"], "reliable": t["reliable"],
+                             "inner_tol": t["inner_tol"], "cap_blocks_per_sm": t["cap_blocks_per_sm"]}})
+    return tot, per
+
+
+def roofline(d, per, peaks):
+    """Roofline of the dominant kernel of the per-level pass: the solve kernel
+    instantiation (one per launch plan kind) or the field passes with the
+    largest summed time.  Streamed solver plans (workspace in global memory)
+    are set against the copy bandwidth with the library's algorithmic bytes;
+    shared-memory plans and the field passes against the measured FMA peak
+    of their precision with the algorithmic flops."""
+    by = collections.OrderedDict()
+    for r in per:
+        k = by.setdefault(r["solve_kernel"], {"ms": 0.0, "bytes": 0.0, "flops": 0.0, "levels": [], "stream": 0})
+        k["ms"] += r["solve_ms"]
+        k["bytes"] += r["solve_bytes"]
+        k["flops"] += r["solve_flops"]
+        k["levels"].append(r["m"])
+        k["stream"] += 0 if r["smem"] else r["solve_ms"]
+        f = by.setdefault("ce_rows+ce_cols", {"ms": 0.0, "bytes": 0.0, "flops": 0.0, "levels": [], "stream": 0})
+        f["ms"] += r["fields_ms"]
+        f["bytes"] += r["fft_bytes"]
+        f["flops"] += r["fft_flops"]
+        f["levels"].append(r["m"])
+    total = sum(k["ms"] for k in by.values())
+    name = max(by, key=lambda n: by[n]["ms"])
+    k = by[name]
+    f32 = d["prec"] in (1, 2)
+    shares = {n: round(v["ms"] / total, 4) for n, v in by.items()}
+    if name.startswith("solve") and k["stream"] >= 0.5 * k["ms"]:
+        ach = k["bytes"] / (k["ms"] / 1e3) / 1e9
+        out = {"kernel": name, "levels_m": k["levels"], "bound": "hbm", "achieved": ach, "peak": peaks["hbm"],
+               "unit": "GB/s", "frac": ach / peaks["hbm"], "traffic": None, "peak_source": peaks["hbm_src"],
+               "note": "algorithmic bytes = cells x CG iterations x bytes per cell-iteration of the streaming "
+                       "model (every pass reads its operands and writes its results once); traffic null: no "
+                       "counter capture of this kernel version"}
+    else:
+        # the field passes compute in FP32 with prec 1, 2; a shared-memory solver plan's
+        # multigrid (most of its flops) in FP32 with prec 1, 2, 3
+        use32 = f32 if name.startswith("ce") else d["prec"] != 0
+        pk_t = peaks["fp32"] if use32 else peaks["fp64"]
+        src = "measured by mlmc_fma_peak (independent FMA chains, %s) on this GPU" % ("FP32" if use32 else "FP64")
+        ach = k["flops"] / (k["ms"] / 1e3) / 1e12
+        out = {"kernel": name, "levels_m": k["levels"], "bound": "alu", "achieved": ach, "peak": pk_t,
+               "unit": "TFLOP/s", "frac": ach / pk_t, "traffic": None, "peak_source": src}
+    out["time_share"] = shares
+    return out
+
+
+def host_estimate_e2e(ctx, d, seed):
+    """The same adaptive estimate driven from the host through the host-buffer
+    entry point mlmc_level_batch_host: pilot and every top-up round copy the
+    per-sample Q_f, Q_c, Q_cgv and iteration counts to host arrays, and the
+    sample sizes come from those host values (same rule as mlmc_estimate).
+    Returns (seconds, sum N_l, d2h bytes)."""
+    import numpy as np
+    L = d["L"]
+    eps = d["eps"]
+    dim = d.get("dim", 2)
+    C = []
+    for l in range(L + 1):
+        nc = 0 if l == 0 else (2 ** dim if d["cgv"] else 1)
+        C.append(float((d["m0"] << l) ** dim) * (1.0 + nc / 2.0 ** dim))
+    ys = [np.empty(0) for _ in range(L + 1)]
+    tried = [0] * (L + 1)  # samples drawn per level, converged or not
+    d2h = 0
+    t0 = time.perf_counter()
+    want = [64] * (L + 1)
+    for _ in range(11):  # the pilot and at most ten top-up rounds
+        for l in range(L + 1):
+            n = want[l] - len(ys[l])
+            if n <= 0:
+                continue
+            s, qf, qc, qg, it = ctx.level_batch_host(l, n, seed, first=tried[l])
+            tried[l] += n
+            d2h += n * (3 * 8 + 4)
+            y = qf - (qg if (d["cgv"] and l > 0) else qc)
+            ys[l] = np.concatenate([ys[l], y[np.isfinite(y)]])
+        V = [float(np.var(y, ddof=1)) for y in ys]
+        tot = sum((v * c) ** 0.5 for v, c in zip(V, C))
+        nxt = [max(len(ys[l]), int(np.ceil(2.0 / eps ** 2 * (V[l] / C[l]) ** 0.5 * tot))) for l in range(L + 1)]
+        if nxt == [len(y) for y in ys]:
+            break
+        want = nxt
+    return time.perf_counter() - t0, sum(len(y) for y in ys), d2h
+
+
+# --------------------------------------------------------------- reference --
+def run_reference(args, d):
+    """The CPU oracle on the host cores, bounded sample per step; same metric
+    and unit.  ms_per_step is the measured wall time of one bounded sample;
+    the level-samples/s value uses the measured per-level rates with the
+    sample sizes N_l of the oracle's own pilot variances, and the time-to-eps
+    they extrapolate to is reported under its own key."""
+    import multiprocessing as mp
+    import numpy as np
+    from oracle import darcy, mlmc
+    cores = min(host_cores(), 16)
+    levels = list(range(d["L"] + 1))
+    model = darcy.Model.from_dict(d)
+    C = [mlmc.parity_cost(model, lvl) for lvl in levels]
+    walls, values, t_eps = [], [], []
+    with mp.get_context("spawn").Pool(cores, initializer=_worker_init) as pool:
+        for step in range(args.warmup + args.steps):
+            rates, results, wall = oracle_rates(args.workload, {}, levels, args.seed, cores, pool)
+            V = []
+            for lvl in levels:
+                arr = np.array(results[lvl])
+                y = arr[:, 0] - (arr[:, 2] if (d["cgv"] and lvl) else arr[:, 1])
+                V.append(float(np.var(y, ddof=1)) if len(y) > 1 else float(np.var(arr[:, 0])))
+            N = mlmc.optimal_samples(d["eps"], V, C)
+            te = sum(n / rates[lvl] for lvl, n in zip(levels, N))
+            if step >= args.warmup:
+                walls.append(wall)
+                values.append(sum(N) / te)
+                t_eps.append(te)
+    value = sum(values) / len(values)
+    sample = ("oracle (numpy/scipy FP64; banded Cholesky up to m = 256, sparse LU above, sparse LU in 3-D) on "
+              "%d spawned processes; per step %s samples of levels %s timed (wall %.1f s)"
+              % (cores, [CPU_SAMPLE.get(lv, 1) for lv in levels], levels, sum(walls) / len(walls)))
+    return {"impl": "reference", "metric": metric_name(d), "value": value, "unit": "level-samples/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * sum(walls) / len(walls), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (Philox4x64-10 streams)",
+            "config": config_block(args, d, None),
+            "time_to_eps_extrapolated_s": sum(t_eps) / len(t_eps),
+            "cpu_baseline": {"value": value, "unit": "level-samples/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "level-samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# -------------------------------------------------- fixed cases for ncu ----
+# Small fixed workloads for ncu captures of single kernels, each a complete
+# program that exits 0 on its own (run it once without ncu first).  Launch
+# plans are fixed by hand to those the autotuner picks in the benchmark;
+# entries: (workload, overrides, [(level, samples, (mode, threads, cluster,
+# gamma, nu), solver)]) with solver None or (reliable, inner_tol).
+PROFILE_CASES = {
+    "fp64_levels": ("lognormal_2layer_16to256", {},
+                    [(0, 65535, (1, 0, 0, 1, 2), None), (3, 1024, (0, 512, 0, 1, 2), None)]),
+    "prec3_levels": ("lognormal_2layer_16to256", {"prec": 3},
+                     [(0, 65535, (1, 0, 0, 1, 2), None), (3, 1024, (0, 512, 0, 1, 2), None)]),
+    "mixed_large": ("lognormal_2layer_cgv_32to2048", {}, [(5, 8, (2, 512, 8, 1, 2), None)]),
+    "mixed_small": ("lognormal_2layer_cgv_16to512", {},
+                    [(0, 65535, (1, 0, 0, 1, 1), None), (1, 16384, (0, 128, 0, 1, 1), None)]),
+    "mixed_m256": ("lognormal_2layer_cgv_16to512", {}, [(4, 256, (0, 512, 0, 1, 2), (1, 1e-3))]),
+    "mixed_m512": ("lognormal_2layer_cgv_16to512", {}, [(5, 128, (2, 512, 4, 1, 2), None)]),
+    "mixed_1024": ("lognormal_2layer_cgv_32to2048", {}, [(5, 32, (2, 512, 8, 1, 2), None)]),
+    "fp64_m256": ("lognormal_2layer_16to256", {}, [(4, 512, (0, 512, 0, 1, 2), None)]),
+    "fields_m512": ("lognormal_2layer_cgv_16to512", {}, [(5, 64, None, None)]),
+    "mixed_3d": ("lognormal_3d_cgv_8to32", {},
+                 [(1, 4096, (0, 128, 0, 1, 2), None), (2, 512, (0, 256, 0, 1, 2), None)]),
+}
+
+
+def run_profile_case(case):
+    import torch
+    import paper_1506_04694_gb300 as pk
+    import workloads
+    name, over, levels = PROFILE_CASES[case]
+    with pk.Context(workloads.workload(name, **over)) as ctx:
+        for level, n, launch, solver in levels:
+            if launch is not None:
+                ctx.set_launch(level, *launch)
+            if solver is not None:
+                ctx.set_solver(level, *solver)
+            if launch is None:  # the field passes alone
+                g, _ = ctx.sample_fields(level, n, 0)
+                torch.cuda.synchronize()
+                print(case, "level", level, "fields of", n, "samples", tuple(g.shape), flush=True)
+                continue
+            s = ctx.level_batch(level, n, 0)
+            torch.cuda.synchronize()
+            print(case, "level", level, "m", ctx.m(level), "samples", s["n"], "iterations", s["iters_total"],
+                  flush=True)
+
+
+UNITS = {"ns": 1.0, "nsecond": 1.0, "us": 1e3, "usecond": 1e3, "ms": 1e6, "msecond": 1e6,
+         "s": 1e9, "second": 1e9}
+
+
+def ncu_summary(path, skip=0, start_at=None):
+    """Per kernel of an ncu launch list (--metrics gpu__time_duration.sum
+    --csv): launches, total device time and share.  skip leaves out the first
+    launches; start_at leaves out every launch before the first kernel whose
+    name contains that text."""
+    rows = list(csv.reader(open(path)))
+    start = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    hdr = rows[start]
+    ki, vi, ui = hdr.index("Kernel Name"), hdr.index("Metric Value"), hdr.index("Metric Unit")
+    idi = hdr.index("ID") if "ID" in hdr else None
+    agg = collections.OrderedDict()
+    seen = start_at is None
+    for n, r in enumerate(rows[start + 1:]):
+        if len(r) <= vi or not r[vi]:
+            continue
+        if (int(r[idi]) if idi is not None else n) < skip:
+            continue
+        if not seen:
+            if start_at not in r[ki]:
+                continue
+            seen = True
+        name = r[ki].split("(")[0].strip()
+        ns = float(r[vi].replace(",", "")) * UNITS[r[ui].strip()]
+        a = agg.setdefault(name, [0, 0.0])
+        a[0] += 1
+        a[1] += ns
+    tot = sum(a[1] for a in agg.values())
+    out = ["%-48s %8s %12s %7s" % ("kernel", "launches", "total ms", "share")]
+    for k, (n, ns) in sorted(agg.items(), key=lambda x: -x[1][1]):
+        out.append("%-48s %8d %12.3f %6.2f%%" % (k[:48], n, ns / 1e6, 100 * ns / tot))
+    out.append("%-48s %8d %12.3f" % ("total", sum(a[0] for a in agg.values()), tot / 1e6))
+    return "\n".join(out)
+
+
+# ------------------------------------------------------------------- main --
 def compare(args):
-    """Time-to-eps: the workload as configured (mixed precision + CGV) against
+    """--compare WORKLOAD: time-to-eps of its mixed-precision CGV form against
     plain FP64 batched MLMC without CGV at the same eps and levels; with
-    --bf16-arm also the mixed CGV form with BF16 multigrid faces (prec 2), with
-    --fp64cg-arm the CGV form with FP64 fields and CG around an FP32
-    multigrid preconditioner (prec 3)."""
+    --bf16-arm also BF16 multigrid faces (prec 2), with --fp64cg-arm the CGV
+    form with FP64 fields and CG around an FP32 multigrid (prec 3)."""
     import torch
     import paper_1506_04694_gb300 as pk
     import workloads
@@ -236,27 +494,17 @@ def compare(args):
            "steps": args.steps, "warmup": args.warmup}
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     for name, md in arms.items():
         ctx = pk.Context(md, stream=stream)
         ctx.autotune(seed=args.seed + 12345)
-        for _ in range(args.warmup):
-            ctx.estimate(md["eps"], args.seed, n_pilot=64, cost_model=0)
-        torch.cuda.synchronize()
-        ts, est = [], None
-        for _ in range(args.steps):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(ctx.stream)
-            est = ctx.estimate(md["eps"], args.seed, n_pilot=64, cost_model=0)
-            e1.record(ctx.stream)
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1) / 1e3)
-        out[name] = {"time_to_eps_s": sum(ts) / len(ts), "N": est["N"], "V": est["V"], "q_hat": est["q_hat"],
-                     "bias_estimate": est["bias"], "alpha": est["alpha"],
-                     "var_hat": est["var_hat"], "level_samples_per_s": sum(est["N"]) / (sum(ts) / len(ts)),
+        ms, est = timed_estimates(ctx, md, args.seed, args.steps, args.warmup, flush, stream)
+        t = sum(ms) / len(ms) / 1e3
+        out[name] = {"time_to_eps_s": t, "N": est["N"], "V": est["V"], "q_hat": est["q_hat"],
+                     "bias_estimate": est["bias"], "alpha": est["alpha"], "var_hat": est["var_hat"],
+                     "level_samples_per_s": sum(est["N"]) / t,
                      "iters_per_sample": [round(x["iters_total"] / max(x["n"], 1), 2) for x in est["sums"]],
-                     "prec": PREC_NAMES[md["prec"]],
-                     "cgv": md["cgv"]}
+                     "prec": PREC_NAMES[md["prec"]], "cgv": md["cgv"]}
         ctx.close()
         del ctx
         torch.cuda.empty_cache()
@@ -273,24 +521,35 @@ def compare(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--compare", default=None,
-                    help="workload name: time-to-eps of its mixed-precision CGV form against plain FP64 "
-                         "batched MLMC (no CGV) at the same eps and level set; prints one JSON line")
-    ap.add_argument("--bf16-arm", action="store_true",
-                    help="with --compare: add the mixed CGV arm with BF16 multigrid faces (prec 2)")
-    ap.add_argument("--fp64cg-arm", action="store_true",
-                    help="with --compare: add the CGV arm with FP64 CG around an FP32 multigrid (prec 3)")
-    ap.add_argument("--clocks-out", default=None,
-                    help="file for the raw nvidia-smi clock samples of the timed region (default: a temp file)")
     ap.add_argument("--prec", type=int, default=None, choices=[0, 1, 2, 3],
                     help="override the workload's solver precision mode")
+    ap.add_argument("--baseline-steps", type=int, default=3,
+                    help="timed estimates of the plain FP64 arm (after max(3, warmup) untimed ones)")
+    ap.add_argument("--no-baseline", action="store_true", help="skip the plain FP64 arm")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--clocks-out", default=None,
+                    help="file for the raw nvidia-smi clock samples of the timed region (default: a temp file)")
+    ap.add_argument("--compare", default=None,
+                    help="workload name: time-to-eps of its mixed CGV form against plain FP64 (one JSON line)")
+    ap.add_argument("--bf16-arm", action="store_true")
+    ap.add_argument("--fp64cg-arm", action="store_true")
+    ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES))
+    ap.add_argument("--ncu-summary", default=None, metavar="CSV")
+    ap.add_argument("--skip", type=int, default=0)
+    ap.add_argument("--from", dest="start_at", default=None)
     args = ap.parse_args()
+    if args.ncu_summary:
+        print(ncu_summary(args.ncu_summary, args.skip, args.start_at))
+        return
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+        return
     if args.compare:
         compare(args)
         return
@@ -299,6 +558,9 @@ def main():
     d = workloads.workload(args.workload)
     if args.prec is not None:
         d["prec"] = args.prec
+    base = None
+    if not args.no_baseline and (d["prec"] != 0 or d["cgv"] != 0):
+        base = dict(d, prec=0, cgv=0)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -307,6 +569,13 @@ def main():
         if rank == 0:
             print(json.dumps(run_reference(args, d)), flush=True)
         return
+
+    # the CPU baseline's process pool starts before the first GPU call
+    pool = None
+    cores = min(host_cores(), 16)
+    if rank == 0 and not args.no_cpu_baseline:
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(cores, initializer=_worker_init)
 
     import torch
     import torch.distributed as dist
@@ -319,9 +588,16 @@ def main():
     # a non-default stream: lets the library capture each estimate round in a CUDA graph
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
+    fp64_peak, _ = pk.fma_peak(local, fp64=True)
+    fp32_peak, _ = pk.fma_peak(local, fp64=False, iters=100000)
+    hbm, hbm_src = measured_hbm()
+    peaks = {"fp64": fp64_peak, "fp32": fp32_peak, "hbm": hbm, "hbm_src": hbm_src}
     ctx = pk.Context(d, device=local, stream=stream)
     tune = ctx.autotune(seed=args.seed + 12345)  # untimed set-up: launch plan per level
-    eps = d["eps"]
+    bctx = btune = None
+    if base is not None:
+        bctx = pk.Context(base, device=local, stream=stream)
+        btune = bctx.autotune(seed=args.seed + 12345)
     seed = args.seed + 7919 * rank
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
@@ -329,109 +605,105 @@ def main():
         if world > 1:
             dist.barrier()
 
-    for _ in range(args.warmup):
-        ctx.estimate(eps, seed, n_pilot=64, cost_model=0)
-    torch.cuda.synchronize(dev)
-
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     phys = vis.split(",")[local] if vis else str(local)
     clocks = ClockSampler(phys, args.clocks_out)
     clocks.start()
+    # ---- timed region: the mixed CGV arm (the line's value) ----
+    for _ in range(args.warmup):
+        ctx.estimate(d["eps"], seed, n_pilot=64, cost_model=0)
     barrier()
     torch.cuda.synchronize(dev)
-    ctx.profile(True)
-    step_ms, n_total, est = [], 0, None
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        est = ctx.estimate(eps, seed, n_pilot=64, cost_model=0)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        n_total += sum(est["N"])
+    step_ms, est = timed_estimates(ctx, d, seed, args.steps, 0, flush, stream)
     torch.cuda.synchronize(dev)
     barrier()
-    ctx.profile(False)
+    n_total = sum(est["N"]) * args.steps
+    # ---- the plain FP64 arm at the same eps and level set ----
+    base_out = None
+    if bctx is not None:
+        bms, best = timed_estimates(bctx, base, seed, args.baseline_steps, max(3, args.warmup), flush, stream)
+        base_out = {"time_to_eps_s": sum(bms) / len(bms) / 1e3, "steps": args.baseline_steps,
+                    "warmup": max(3, args.warmup), "N_per_level": best["N"], "q_hat": best["q_hat"],
+                    "var_hat": best["var_hat"], "level_samples_per_s": sum(best["N"]) / (sum(bms) / len(bms) / 1e3),
+                    "prec": PREC_NAMES[base["prec"]], "cgv": base["cgv"],
+                    "autotune": [{"m": base["m0"] << l, "threads": t["threads"], "warp": t["warp"],
+                                  "cluster": t["cluster"], "nu": t["nu"]} for l, t in enumerate(btune)]}
     clk = clocks.stop()
-    prof = ctx.profile_read()
     total_ms, n_all = reduce_over_ranks(sum(step_ms), n_total, dev)
-
-    # end to end through the host-buffer API: the estimate's per-level sample
-    # counts run with per-sample results copied back to host memory
-    e2e = None
-    if rank == 0:
-        N = est["N"]
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for lvl, n in enumerate(N):
-            ctx.level_batch_host(lvl, n, seed, first=0)
-        torch.cuda.synchronize(dev)
-        te = time.perf_counter() - t0
-        e2e = {"value": sum(N) / te, "unit": "level-samples/s", "h2d_bytes_per_step": 0,
-               "d2h_bytes_per_step": int(sum(N) * (3 * 8 + 4) + (d["L"] + 1) * 128),
-               "note": "inputs are (seed, model) passed by value; per-sample Q_f, Q_c, Q_cgv and "
-                       "iterations copied to host inside the timed region"}
-
     if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
         return
-    stage_ms = prof["ms"]
-    dom = max(stage_ms, key=lambda k: stage_ms[k])
-    if stage_ms[dom] <= 0:
-        raise RuntimeError("no stage timing collected in the timed region")
-    launches = int(sum(prof["launches"].values()))
-    prec = d["prec"]
-    fp64_src = "nominal FP64 vector rate (152 SMs x 2 DFMA/clk x 2.06 GHz)"
-    fp32_src = "nominal FP32 vector rate (152 SMs x 128 FFMA/clk x 2.07 GHz)"
-    if dom == "solve":
-        # algorithmic flops counted by the library per level from its cycle (V/W, sweeps); with
-        # prec 3 only the FP64 CG part (23 per cell-iteration) is set against the FP64 peak
-        if prec == 0:
-            flops, peak, src, what = prof["solve_flops"], FP64_PEAK_TFLOPS, fp64_src, "FP64 MG-PCG"
-        elif prec == 3:
-            flops, peak, src, what = 23.0 * prof["cell_iters"], FP64_PEAK_TFLOPS, fp64_src, "FP64 CG part"
-        else:
-            flops, peak, src, what = prof["solve_flops"], FP32_PEAK_TFLOPS, fp32_src, "FP32 MG-PCG"
-        ach = flops / (stage_ms["solve"] / 1e3) / 1e12
-        roof = {"kernel": "solve_kernel<%d, mode> (assembly + MG-PCG + QoI; %s)" % (prec, what), "bound": "alu",
-                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                "peak_source": src}
-    else:
-        # radix-2 FFT count, 5 log2(M) flops per point of each length-M transform, per level
-        f32 = prec in (1, 2)
-        peak = FP32_PEAK_TFLOPS if f32 else FP64_PEAK_TFLOPS
-        ach = prof["fft_flops"] / (stage_ms["fields"] / 1e3) / 1e12
-        roof = {"kernel": "ce_rows/ce_cols (Philox + Box-Muller + FFT, %s)" % ("FP32" if f32 else "FP64"),
-                "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "peak_source": fp32_src if f32 else fp64_src}
+
+    # ---- untimed: stage and per-level timing (CUDA events), roofline ----
+    tot, per = profiled_pass(ctx, d, est, seed, tune)
+    roof = roofline(d, per, peaks)
+    base_stages = None
+    if bctx is not None:
+        btot, bper = profiled_pass(bctx, base, best, seed, btune)
+        base_stages = {"stage_ms_per_step": btot["ms"],
+                       "per_level": [{k: r[k] for k in ("m", "N", "fields_ms", "solve_ms", "iters_per_sample",
+                                                        "solve_kernel")} for r in bper],
+                       "roofline": roofline(base, bper, peaks)}
+        base_out.update(base_stages)
+
+    # ---- end to end through the host-buffer entry point ----
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize(dev)
+        te, n_e2e, d2h = host_estimate_e2e(ctx, d, seed)
+        e2e = {"value": n_e2e / te, "unit": "level-samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
+               "seconds": te,
+               "note": "the same adaptive estimate driven from the host through mlmc_level_batch_host: per-sample "
+                       "Q_f, Q_c, Q_cgv and iterations of the pilot and every top-up copied to host arrays inside "
+                       "the timed region, sample sizes from those host values, levels one after another; the "
+                       "only inputs are (seed, model) passed by value"}
+
+    # kernel launches of one estimate (the same kernels run inside the graphs of
+    # the timed steps), times the timed steps
+    ctx.profile(True)
+    ctx.estimate(d["eps"], seed, n_pilot=64, cost_model=0)
+    launches = int(sum(ctx.profile_read()["launches"].values())) * args.steps
+    ctx.profile(False)
+    t_mix = total_ms / args.steps / 1e3
     out = {
-        "metric": metric_name(d, args), "value": n_all / (total_ms / 1e3), "unit": "level-samples/s",
+        "metric": metric_name(d), "value": n_all / (total_ms / 1e3), "unit": "level-samples/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if d["prec"] == 0 else "f64+f32-mg" if d["prec"] == 3 else "f32+f64", "data": "synthetic (Philox4x64-10 streams)",
-        "config": config_block(args, d), "roofline": roof, "e2e": e2e, "gpu_launches": launches // 1,
-        "clocks": clk, "time_to_eps_s": total_ms / args.steps / 1e3, "N_per_level": est["N"],
-        "q_hat": est["q_hat"], "var_hat": est["var_hat"], "alpha": est["alpha"], "bias_estimate": est["bias"],
-        "bias_flag": est["bias_flag"],
-        "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
-        "iters_per_cell_solve": prof["cell_iters"] / max(prof["cells"], 1.0),
-        "autotune": [{"m": d["m0"] << l, "threads": t["threads"], "warp": t["warp"], "cluster": t["cluster"],
-                      "cap_blocks_per_sm": t["cap_blocks_per_sm"], "gamma": t["gamma"], "nu": t["nu"]}
-                     for l, t in enumerate(tune)],
+        "dtype": "f64" if d["prec"] == 0 else "f64+f32-mg" if d["prec"] == 3 else "f32+f64",
+        "data": "synthetic (Philox4x64-10 streams)", "config": config_block(args, d, base),
+        "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        "time_to_eps_s": t_mix,
+        "time_to_eps": {"this_arm_s": t_mix, "plain_fp64_s": base_out["time_to_eps_s"] if base_out else None,
+                        "speedup_vs_plain_fp64": (base_out["time_to_eps_s"] / t_mix) if base_out else None},
+        "N_per_level": est["N"], "V_per_level": est["V"], "q_hat": est["q_hat"], "var_hat": est["var_hat"],
+        "alpha": est["alpha"], "bias_estimate": est["bias"], "bias_flag": est["bias_flag"],
+        "stage_ms_per_step_serial": tot["ms"],
+        "per_level": [dict({k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()
+                            if k not in ("cell_iters", "solve_flops", "fft_flops", "fft_bytes", "solve_bytes")},
+                           solve_alg_gbs=round(r["solve_bytes"] / max(r["solve_ms"], 1e-9) / 1e6, 1),
+                           solve_tflops=round(r["solve_flops"] / max(r["solve_ms"], 1e-9) / 1e9, 3),
+                           fields_alg_gbs=round(r["fft_bytes"] / max(r["fields_ms"], 1e-9) / 1e6, 1))
+                      for r in per],
+        "peaks": {"fp64_tflops": fp64_peak, "fp32_tflops": fp32_peak, "hbm_gbs": hbm},
+        "plain_fp64_arm": base_out,
     }
-    if not args.no_cpu_baseline:
-        cores = min(host_cores(), 16)
-        rates, _ = oracle_rates(args.workload, {}, list(range(d["L"] + 1)), args.seed, cores)
+    if pool is not None:
+        levels = list(range(d["L"] + 1))
+        rates, _, wall = oracle_rates(args.workload, {}, levels, args.seed, cores, pool)
+        pool.close()
+        pool.join()
         N = est["N"]
         t_cpu = sum(n / rates[lvl] for lvl, n in enumerate(N))
         out["cpu_baseline"] = {
             "value": sum(N) / t_cpu, "unit": "level-samples/s", "cores": cores, "kind": "oracle",
-            "sample": "oracle on %d spawned processes, %s samples of levels 0..%d timed; time-to-eps "
-                      "extrapolated with the GPU run's N_l (%.1f s)" % (
-                          cores, [CPU_SAMPLE.get(lv, 1) for lv in range(d["L"] + 1)], d["L"], t_cpu)}
+            "sample": "oracle on %d spawned processes, %s samples of levels 0..%d (wall %.1f s); time-to-eps "
+                      "extrapolated with the GPU run's N_l: %.1f s" % (
+                          cores, [CPU_SAMPLE.get(lv, 1) for lv in levels], d["L"], wall, t_cpu)}
     print(json.dumps(out), flush=True)
     ctx.close()
+    if bctx is not None:
+        bctx.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -115,6 +115,14 @@ typedef struct mlmc_model {
                                   the 8 offsets (ox, oy, oz) in the order ox fastest; needs
                                   m0 * 2^L <= 128, prec 0 or 1; problem 1 takes D* = [x0, x1] x
                                   [y0, y1] x [y0, y1] */
+  int32_t embed;               /* circulant embedding of k_kind 1 (Sec. 3.4 cites the method):
+                                  0: padding M = 2m, else (2-D, 2-norm, m >= 8) the cut-off
+                                     embedding at M = 3m, else 4m, 8m, 16m; the cut-off one
+                                     keeps the covariance of Eq. 2.3 up to the largest
+                                     distance between cell centres, sqrt(2)(m - 1)/m, then
+                                     tapers it to zero at M/(2m) with a C^1 cubic, so it
+                                     samples the same fields law on a smaller torus;
+                                  1: periodic embeddings with M = 2m, 4m, 8m, 16m only */
 } mlmc_model;
 
 /* Level sums over a range of samples (Eq. 3.6 and Eq. 4.2): Q_f is Q_l of the
@@ -159,9 +167,9 @@ typedef struct mlmc_ctx mlmc_ctx;
 
 /* Create a context on CUDA device `device` for `model`, issuing work on
  * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  Builds
- * the circulant-embedding tables of every level (padding M = p m with the
- * smallest p in {2, 4, 8, 16} whose embedding eigenvalues are all
- * >= -1e-13 max; the remaining negative ones are set to 0).
+ * the circulant-embedding tables of every level (the first embedding in the
+ * order of model.embed whose eigenvalues are all >= -1e-13 max; the
+ * remaining negative ones are set to 0).
  * Errors: MLMC_ERR_ARG (bad model), MLMC_ERR_NODEV, MLMC_ERR_EMBED, MLMC_ERR_NOMEM,
  * MLMC_ERR_CUDA.  On error *out is NULL. */
 MLMC_API int mlmc_create(int device, const mlmc_model* model, void* cuda_stream, mlmc_ctx** out);
@@ -207,7 +215,7 @@ MLMC_API int mlmc_estimate_ex(mlmc_ctx* ctx, double eps, uint64_t seed, int32_t 
 /* Write the estimator state of the last mlmc_estimate / _ex call to a text
  * file (host path).  Format (version 2), one key per line: "mlmc_checkpoint
  * 2"; "model" n_layers k_kind norm_r m0 L cgv prec max_it problem geometry
- * dim; "model_if" if_lo if_hi; "model_tol" tol; "model_mu", "model_sigma2",
+ * dim embed; "model_if" if_lo if_hi; "model_tol" tol; "model_mu", "model_sigma2",
  * "model_lam" (8 values each), "model_qoi_box", "model_line_lo",
  * "model_line_hi" (4 each); then seed, eps, cost_model, rounds, levels and
  * one "level" line of counts, sums and cost per level.  Doubles carry 17
@@ -218,7 +226,7 @@ MLMC_API int mlmc_checkpoint(mlmc_ctx* ctx, const char* path);
 /* Check, on the host alone (no context or GPU needed), that the checkpoint
  * at `path` was written for `model`: every field that changes a sample's Q
  * or its failure must be equal (per-layer mu, sigma2 and, for log-normal
- * fields, lam and norm_r below n_layers; the interface range with horizontal
+ * fields, lam, norm_r and embed below n_layers; the interface range with horizontal
  * layers; the box with Model Problem 1; the line ranges with the sloped
  * geometry; n_layers, k_kind, m0, L, cgv, prec, tol, max_it, problem,
  * geometry and dim always).  Merging level sums of another model into an
@@ -262,6 +270,8 @@ typedef struct mlmc_tune_report {
   int32_t candidates[MLMC_MAX_LEVELS];         /* plans timed */
   double ms_default[MLMC_MAX_LEVELS];          /* ms per sample, default plan */
   double ms_best[MLMC_MAX_LEVELS];             /* ms per sample, chosen plan */
+  int32_t smem[MLMC_MAX_LEVELS];               /* 1: the chosen plan keeps a system's workspace in
+                                                  shared memory (else global memory, streamed) */
 } mlmc_tune_report;
 
 /* Times the candidate launch plans of the solver (one warp, one block of
@@ -392,6 +402,12 @@ typedef struct mlmc_profile_stats {
                               grids; the cycle runs in FP32 with prec 1, 2, 3 */
   double fft_flops;        /* 5 log2(M) flops per complex point of every length-M transform of the
                               row and column passes (the radix-2 count), summed over levels */
+  double solve_bytes;      /* algorithmic bytes of the CG iterations: cells x iterations x the bytes
+                              one iteration moves when every pass reads its operands and writes its
+                              results once (CG vectors, faces and diagonal, every multigrid level;
+                              no reuse between passes) */
+  double fft_bytes;        /* algorithmic bytes of the field passes: every complex intermediate
+                              written once and read once, the fields written once */
 } mlmc_profile_stats;
 
 /* enable != 0: reset the counters and start collecting; 0: stop. */
@@ -399,6 +415,17 @@ MLMC_API int mlmc_profile(mlmc_ctx* ctx, int enable);
 
 /* Copy the counters collected so far (host pointer, required). */
 MLMC_API int mlmc_profile_read(mlmc_ctx* ctx, mlmc_profile_stats* out);
+
+/* Arithmetic peak of the GPU, measured (no paper counterpart: the roofline
+ * denominator of the ALU-bound kernels, whose bound the paper's CPU setting
+ * never needed).  Runs one kernel of independent fused multiply-add chains
+ * (FP64 if fp64 != 0, else FP32) on every SM of `device` for `iters` rounds
+ * of 32 FMAs per thread, timed with CUDA events after one warm-up launch, on
+ * a stream of its own; *tflops (host pointer, required) receives 2 flops per
+ * FMA / event time, *ms (host pointer or NULL) the event time.  Allocates
+ * one value of device memory for the duration of the call.
+ * Errors: MLMC_ERR_ARG, MLMC_ERR_NODEV, MLMC_ERR_NOMEM, MLMC_ERR_CUDA. */
+MLMC_API int mlmc_fma_peak(int device, int fp64, int32_t iters, double* tflops, double* ms);
 
 /* Human-readable text of an error code (static storage). */
 MLMC_API const char* mlmc_error_string(int code);

@@ -32,7 +32,7 @@ class Model(ctypes.Structure):
         ("tol", ctypes.c_double), ("max_it", ctypes.c_int32),
         ("problem", ctypes.c_int32), ("qoi_box", ctypes.c_double * 4),
         ("geometry", ctypes.c_int32), ("line_lo", ctypes.c_double * 4), ("line_hi", ctypes.c_double * 4),
-        ("dim", ctypes.c_int32),
+        ("dim", ctypes.c_int32), ("embed", ctypes.c_int32),
     ]
 
 
@@ -61,7 +61,8 @@ class ProfileStats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64 * 3), ("ms", ctypes.c_double * 3),
                 ("cell_iters", ctypes.c_double), ("cells", ctypes.c_double),
                 ("fft_row_points", ctypes.c_double), ("fft_col_points", ctypes.c_double),
-                ("samples", ctypes.c_double), ("solve_flops", ctypes.c_double), ("fft_flops", ctypes.c_double)]
+                ("samples", ctypes.c_double), ("solve_flops", ctypes.c_double), ("fft_flops", ctypes.c_double),
+                ("solve_bytes", ctypes.c_double), ("fft_bytes", ctypes.c_double)]
 
 
 STAGES = ("fields", "solve", "reduce")
@@ -74,7 +75,8 @@ class TuneReport(ctypes.Structure):
                 ("nu_coarse", ctypes.c_int32 * MAX_LEVELS),
                 ("inner_tol", ctypes.c_double * MAX_LEVELS), ("reliable", ctypes.c_int32 * MAX_LEVELS),
                 ("candidates", ctypes.c_int32 * MAX_LEVELS),
-                ("ms_default", ctypes.c_double * MAX_LEVELS), ("ms_best", ctypes.c_double * MAX_LEVELS)]
+                ("ms_default", ctypes.c_double * MAX_LEVELS), ("ms_best", ctypes.c_double * MAX_LEVELS),
+                ("smem", ctypes.c_int32 * MAX_LEVELS)]
 
 
 class MLMCError(RuntimeError):
@@ -123,6 +125,8 @@ EXPORTS = {
                                            ctypes.c_void_p]),
     "mlmc_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "mlmc_profile_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ProfileStats)]),
+    "mlmc_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]),
     "mlmc_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "mlmc_last_error": (ctypes.c_char_p, []),
 }
@@ -295,7 +299,7 @@ class Context:
                  "cluster": r.cluster[i], "gamma": r.gamma[i], "nu": r.nu[i], "nu_coarse": r.nu_coarse[i],
                  "inner_tol": r.inner_tol[i], "reliable": r.reliable[i],
                  "candidates": r.candidates[i], "ms_per_sample_default": r.ms_default[i],
-                 "ms_per_sample_best": r.ms_best[i]} for i in range(L)]
+                 "ms_per_sample_best": r.ms_best[i], "smem": r.smem[i]} for i in range(L)]
 
     def profile(self, enable=True):
         """mlmc_profile: reset and start (or stop) per-stage event timing."""
@@ -308,7 +312,7 @@ class Context:
         return {"launches": dict(zip(STAGES, p.launches)), "ms": dict(zip(STAGES, p.ms)),
                 "cell_iters": p.cell_iters, "cells": p.cells, "fft_row_points": p.fft_row_points,
                 "fft_col_points": p.fft_col_points, "samples": p.samples, "solve_flops": p.solve_flops,
-                "fft_flops": p.fft_flops}
+                "fft_flops": p.fft_flops, "solve_bytes": p.solve_bytes, "fft_bytes": p.fft_bytes}
 
     def set_launch(self, level, mode, threads=256, cluster=0, gamma=1, nu=1):
         """mlmc_set_launch: fix a level's solver launch (0 block, 1 warp, 2 cluster; <0 default),
@@ -411,6 +415,16 @@ def checkpoint_check(model, path):
     needs no GPU."""
     m = make_model(model)
     _check(lib().mlmc_checkpoint_check(ctypes.byref(m), os.fsencode(path)), allow_failed=False)
+
+
+def fma_peak(device=0, fp64=True, iters=20000):
+    """mlmc_fma_peak: measured FMA throughput of the GPU in TFLOP/s (and the
+    probe kernel's event time in ms)."""
+    t = ctypes.c_double()
+    ms = ctypes.c_double()
+    _check(lib().mlmc_fma_peak(device, 1 if fp64 else 0, iters, ctypes.byref(t), ctypes.byref(ms)),
+           allow_failed=False)
+    return t.value, ms.value
 
 
 def philox_words(seed, level, sample, stream_id, first_call, n_calls, device=0):

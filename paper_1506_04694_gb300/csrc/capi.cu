@@ -253,6 +253,7 @@ int check_model(const mlmc_model& md) {
   }
   if (md.geometry != 0 && md.geometry != 1) return fail(MLMC_ERR_ARG, "geometry must be 0 or 1");
   if (md.dim != 0 && md.dim != 2 && md.dim != 3) return fail(MLMC_ERR_ARG, "dim must be 0, 2 or 3");
+  if (md.embed != 0 && md.embed != 1) return fail(MLMC_ERR_ARG, "embed must be 0 or 1");
   if (md.dim == 3) {
     if ((int64_t)md.m0 << md.L > 128) return fail(MLMC_ERR_TOOBIG, "3-D: m0 * 2^L must be <= 128");
     if (md.prec != 0 && md.prec != 1) return fail(MLMC_ERR_ARG, "3-D: prec must be 0 or 1");
@@ -443,14 +444,18 @@ int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t see
   const SolvePlan* plan = c->tuned_ok[level] ? &c->tuned[level] : nullptr;
   CUDA_TRY(cudaMemsetAsync(itacc, 0, 2 * sizeof(int64_t), c->wst));
   const int m = md.m0 << level;
-  double sumM2 = 0, sumM = 0, fftf = 0;  // transformed points and FFT flops per sample over the draws
+  double sumM2 = 0, sumM = 0, fftf = 0, fftb = 0;  // transformed points, FFT flops and bytes per sample
   const bool d3 = dim_of(md) == 3;
+  const double sc = fields_f32(md) ? 8.0 : 16.0;     // bytes of a complex intermediate value
   for (const auto& T : c->lev[level].pair) {
     const double Md = T.M;
     sumM2 += d3 ? Md * Md * Md : Md * Md;              // points of the row pass
     sumM += d3 ? Md * Md + Md * m : Md;                // (3-D: middle and last passes) / m
     fftf += 5.0 * std::log2(Md) * (d3 ? Md * Md * Md + Md * Md * m + Md * m * m : Md * Md + Md * m);
+    // intermediates written once and read once (2-D: M x m; 3-D: M^2 m and M m^2)
+    fftb += 2.0 * sc * (d3 ? Md * Md * m + Md * m * m : Md * m);
   }
+  fftb += (double)md.n_layers * (double)cells_of(md, m) * (fields_f32(md) ? 4.0 : 8.0);  // fields written
   for (int64_t c0 = 0; c0 < n; c0 += chunk) {
     const int64_t cn = std::min<int64_t>(chunk, n - c0);
     SolveArgs a = base_args(c, level, seed, first + c0);
@@ -463,6 +468,7 @@ int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t see
         c->prof.fft_row_points += (double)cn * sumM2;
         c->prof.fft_col_points += (double)cn * sumM * m;
         c->prof.fft_flops += (double)cn * fftf;
+        c->prof.fft_bytes += (double)cn * fftb;
       }
     }
     {
@@ -513,6 +519,32 @@ double flops_per_cell_iter(int prec, int gamma, int nu, int nuc) {
   return (prec == 3 ? 23.0 : 21.0) + fine + coarse * (gamma >= 2 ? 1.0 : 1.0 / 3.0);
 }
 
+// Algorithmic bytes per cell and CG iteration: every pass of the iteration
+// reads each operand array once and writes each result once (no reuse
+// between passes), with s = bytes of a cell value and fs of a face (about
+// two faces per cell in 2-D, three in 3-D).  CG: operator apply (p, diag,
+// faces read, q written), x and r updates (4 reads, 2 writes), r.z (2
+// reads), p update (2 reads, 1 write): 14 s + 2 fs.  Multigrid, per cell of
+// a level: zero-guess red half sweep 1.5 s (f, invd, e of one colour), black
+// half sweep 2 s + 2 fs (plus the other colour's e and every face once),
+// each further half sweep the same, red-cell restriction 2.25 s + 2 fs,
+// prolongation 2.25 s: 6 s + 4 fs + (2 nu - 1)(4 s + 4 fs); coarser levels
+// add 1/3 (V) or 1 (W) of that with their own sweep count.  3-D: CG 14 s +
+// 3 fs; a level 5.75 s + 6 fs + (2 nu - 1)(4 s + 6 fs), coarser 1/7 (V) or
+// 1/3 (W).  prec 1, 2, 3: the cycle in FP32 (prec 2: BF16 faces); the CG in
+// FP32 for prec 1, 2, in FP64 for prec 0, 3.
+double bytes_per_cell_iter(int prec, int dim, int gamma, int nu, int nuc) {
+  const double s_cg = (prec == 1 || prec == 2) ? 4.0 : 8.0, fs_cg = s_cg;
+  const double s_mg = prec == 0 ? 8.0 : 4.0, fs_mg = prec == 0 ? 8.0 : prec == 2 ? 2.0 : 4.0;
+  const int nc = nuc > 0 ? nuc : nu;
+  if (dim == 3) {
+    auto lev = [&](int n) { return 5.75 * s_mg + 6.0 * fs_mg + (2.0 * n - 1.0) * (4.0 * s_mg + 6.0 * fs_mg); };
+    return 14.0 * s_cg + 3.0 * fs_cg + lev(nu) + lev(nc) * (gamma >= 2 ? 1.0 / 3.0 : 1.0 / 7.0);
+  }
+  auto lev = [&](int n) { return 6.0 * s_mg + 4.0 * fs_mg + (2.0 * n - 1.0) * (4.0 * s_mg + 4.0 * fs_mg); };
+  return 14.0 * s_cg + 2.0 * fs_cg + lev(nu) + lev(nc) * (gamma >= 2 ? 1.0 : 1.0 / 3.0);
+}
+
 // After the stream reached the copies of enqueue_level(): fill the sums.
 int finish_level(mlmc_ctx* c, int level, const HostLevel& h, mlmc_level_sums* sums) {
   const mlmc_model& md = c->model;
@@ -523,6 +555,7 @@ int finish_level(mlmc_ctx* c, int level, const HostLevel& h, mlmc_level_sums* su
     else if (plan_of(md, md.m0 << level, &P)) P.gamma = P.nu = 1;
     c->prof.solve_flops += (double)h.itc[1] * (dim_of(md) == 3 ? flops_per_cell_iter3(P.gamma, P.nu, P.nu_coarse)
                                                                : flops_per_cell_iter(md.prec, P.gamma, P.nu, P.nu_coarse));
+    c->prof.solve_bytes += (double)h.itc[1] * bytes_per_cell_iter(md.prec, dim_of(md), P.gamma, P.nu, P.nu_coarse);
   }
   sums->n = h.s.n;
   sums->n_failed = h.s.n_failed;
@@ -684,8 +717,8 @@ void add_sums(mlmc_level_sums& S, const mlmc_level_sums& add) {
 // The model block of a checkpoint: every field of mlmc_model that changes a
 // sample's Q (or which samples fail), doubles at 17 significant digits.
 void write_model_block(FILE* f, const mlmc_model& md) {
-  std::fprintf(f, "model %d %d %d %d %d %d %d %d %d %d %d\n", md.n_layers, md.k_kind, md.norm_r, md.m0, md.L,
-               md.cgv, md.prec, md.max_it, md.problem, md.geometry, dim_of(md));
+  std::fprintf(f, "model %d %d %d %d %d %d %d %d %d %d %d %d\n", md.n_layers, md.k_kind, md.norm_r, md.m0, md.L,
+               md.cgv, md.prec, md.max_it, md.problem, md.geometry, dim_of(md), md.embed);
   std::fprintf(f, "model_if %.17g %.17g\nmodel_tol %.17g\n", md.if_lo, md.if_hi, md.tol);
   auto arr = [&](const char* key, const double* v, int n) {
     std::fprintf(f, "%s", key);
@@ -701,8 +734,8 @@ void write_model_block(FILE* f, const mlmc_model& md) {
 }
 
 bool read_model_block(FILE* f, mlmc_model* md) {
-  if (std::fscanf(f, "model %d %d %d %d %d %d %d %d %d %d %d\n", &md->n_layers, &md->k_kind, &md->norm_r, &md->m0,
-                  &md->L, &md->cgv, &md->prec, &md->max_it, &md->problem, &md->geometry, &md->dim) != 11)
+  if (std::fscanf(f, "model %d %d %d %d %d %d %d %d %d %d %d %d\n", &md->n_layers, &md->k_kind, &md->norm_r, &md->m0,
+                  &md->L, &md->cgv, &md->prec, &md->max_it, &md->problem, &md->geometry, &md->dim, &md->embed) != 12)
     return false;
   if (std::fscanf(f, "model_if %lg %lg\nmodel_tol %lg\n", &md->if_lo, &md->if_hi, &md->tol) != 3) return false;
   auto arr = [&](const char* key, double* v, int n) {
@@ -740,6 +773,7 @@ const char* model_difference(const mlmc_model& a, const mlmc_model& b) {
     if (a.k_kind == 1 && a.lam[t] != b.lam[t]) return "lam";
   }
   if (a.k_kind == 1 && a.norm_r != b.norm_r) return "norm_r";
+  if (a.k_kind == 1 && a.embed != b.embed) return "embed";
   if (a.geometry == 0 && a.n_layers > 1 && (a.if_lo != b.if_lo || a.if_hi != b.if_hi)) return "if_lo/if_hi";
   if (a.problem == 1)
     for (int k = 0; k < 4; ++k)
@@ -821,7 +855,13 @@ int mlmc_create(int device, const mlmc_model* model, void* cuda_stream, mlmc_ctx
       PairTable& T = LT.pair[f];
       T.M = 0;
       const bool d3 = dim_of(*model) == 3;
-      for (int p = 2; p <= 16; p *= 2) {
+      // padding candidates in order: M = 2m, the cut-off embedding at 3m (2-D,
+      // 2-norm, m >= 8, unless embed = 1), then 4m, 8m, 16m
+      const int cand_p[5] = {2, 3, 4, 8, 16};
+      for (int ci = 0; ci < 5; ++ci) {
+        const int p = cand_p[ci];
+        const bool cut = p == 3;
+        if (cut && (d3 || model->norm_r != 2 || LT.m < 8 || model->embed != 0)) continue;
         const int M = p * LT.m;
         if (M > (d3 ? 256 : 16384)) {
           err = fail(MLMC_ERR_TOOBIG, d3 ? "3-D embedding size M above 256" : "embedding size M above 16384");
@@ -835,7 +875,8 @@ int mlmc_create(int device, const mlmc_model* model, void* cuda_stream, mlmc_ctx
         const int br = d3 ? ce_build_table3(LT.m, M, c->pair_sigma2[f], c->pair_lam[f], model->norm_r, scratch.p,
                                             T.s64.as<double>(), T.s32.as<float>(), mm.as<double>(), T.tw64.p,
                                             T.tw32.p, c->st)
-                          : ce_build_table(LT.m, M, c->pair_sigma2[f], c->pair_lam[f], model->norm_r, scratch.p,
+                          : ce_build_table(LT.m, M, c->pair_sigma2[f], c->pair_lam[f], model->norm_r, cut ? 1 : 0,
+                                           scratch.p,
                                            T.s64.as<double>(), T.s32.as<float>(), mm.as<double>(), T.tw64.p,
                                            T.tw32.p, c->st);
         if (br) {
@@ -1269,6 +1310,7 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
       rep->inner_tol[l] = cand[best_k].inner_tol;
       rep->reliable[l] = cand[best_k].reliable;
       rep->candidates[l] = nk;
+      rep->smem[l] = cand[best_k].use_smem;
       rep->ms_default[l] = def_ms / n;
       rep->ms_best[l] = best / n;
     }

@@ -13,7 +13,12 @@
 //   pass 2 (columns): y[b][a] = sum_q2 W[q2][a] exp(-2 pi i b q2/M), b < m,
 //                     written as g_t = mu_t + Re/Im y.
 // Each FFT of length M runs in shared memory: bit-reversed load, then log2 M
-// radix-2 decimation-in-time stages.
+// radix-2 decimation-in-time stages.  M = 3 N (N a power of two, the cut-off
+// embedding) splits the input by q mod 3 into three length-N sequences, each
+// loaded bit-reversed and transformed as above, and one radix-3 stage
+// combines them: X[k + jN] = F0[k] + W^(k+jN) F1[k] + W^(2(k+jN)) F2[k],
+// W = exp(-2 pi i/M), j = 0, 1, 2 (only j = 0 when the outputs kept are
+// fewer than N).
 #include <algorithm>
 
 #include "common.cuh"
@@ -40,9 +45,11 @@ __device__ __forceinline__ unsigned brev_n(unsigned v, int logn) {
 // k < nkeep of each row are needed (nkeep a power of two, 4 <= nkeep <= M):
 // stages whose half-span hs is >= nkeep compute, in each group, the nkeep
 // upper outputs u + w v only.
+// tws: the twiddle table holds exp(-2 pi i k/(tws M)), k < tws M (tws = 3: the
+// length-N sub-transforms of an M = 3N transform read every third entry).
 template <typename R>
 __device__ void block_fft_rows(Cplx<R>* s, int nrows, int M, int logM, const Cplx<R>* __restrict__ tw,
-                               int nkeep) {
+                               int nkeep, int tws = 1) {
   const int half = M >> 1;
   const int nb = nrows * half;
   // stages 0 and 1 together: their twiddles are 1 and -i (M >= 4)
@@ -61,7 +68,7 @@ __device__ void block_fft_rows(Cplx<R>* s, int nrows, int M, int logM, const Cpl
   int st = 2;
   for (; st + 1 < logM && (2 << st) < nkeep; st += 2) {  // radix-4: stages st, st + 1 (both full)
     const int h = 1 << st;
-    const int ts4 = M >> (st + 2);  // twiddle index step M / (4 h)
+    const int ts4 = (M >> (st + 2)) * tws;  // twiddle index step M / (4 h)
     for (int t = threadIdx.x; t < nq; t += blockDim.x) {
       const int row = t / (M >> 2);
       const int b = t - row * (M >> 2);
@@ -83,7 +90,7 @@ __device__ void block_fft_rows(Cplx<R>* s, int nrows, int M, int logM, const Cpl
   }
   for (; st < logM; ++st) {
     const int hs = 1 << st;
-    const int tstride = half >> st;  // twiddle index step M / (2 hs)
+    const int tstride = (half >> st) * tws;  // twiddle index step M / (2 hs)
     if (hs >= nkeep) {  // pruned stage: upper outputs of the first nkeep positions
       const int ngrp = M >> (st + 1);
       const int np = nrows * ngrp * nkeep;
@@ -122,6 +129,56 @@ __device__ void block_fft_rows(Cplx<R>* s, int nrows, int M, int logM, const Cpl
   }
 }
 
+// Position in shared memory of input q of a row of length M: bit reversal
+// for a power of two (r3 = 0, logn = log2 M); for M = 3N (r3 = 1, logn =
+// log2 N) the sub-sequence q mod 3 at offset (q mod 3) N, bit-reversed in q/3.
+__device__ __forceinline__ int fft_pos(int q, int logn, int r3) {
+  if (!r3) return (int)brev_n((unsigned)q, logn);
+  const int d = q / 3, r = q - 3 * d;
+  return (r << logn) + (int)brev_n((unsigned)d, logn);
+}
+
+// FFTs of `nrows` rows of length M = 3N in shared memory, inputs at fft_pos:
+// the three length-N sub-transforms of each row (all N outputs), then the
+// radix-3 stage.  nkeep <= N: outputs k < nkeep only, written in place of F0;
+// nkeep == M: all outputs, X[k + jN] in place of F_j[k].  tw: M entries.
+template <typename R>
+__device__ void block_fft_rows3(Cplx<R>* s, int nrows, int N, int logN, const Cplx<R>* __restrict__ tw, int nkeep) {
+  const int M = 3 * N;
+  block_fft_rows(s, 3 * nrows, N, logN, tw, N, 3);
+  const R c3 = R(0.8660254037844386467637);  // sin(2 pi / 3)
+  const bool full = nkeep > N;
+  const int nk = full ? N : nkeep;
+  for (int t = threadIdx.x; t < nrows * nk; t += blockDim.x) {
+    const int row = t / nk, k = t - row * nk;
+    Cplx<R>* x = s + row * M + k;
+    const Cplx<R> a = x[0], f1 = x[N], f2 = x[2 * N];
+    const Cplx<R> w1 = tw[k], w2 = tw[2 * k];
+    const Cplx<R> b{w1.x * f1.x - w1.y * f1.y, w1.x * f1.y + w1.y * f1.x};
+    const Cplx<R> c{w2.x * f2.x - w2.y * f2.y, w2.x * f2.y + w2.y * f2.x};
+    const Cplx<R> sm{b.x + c.x, b.y + c.y};
+    x[0] = Cplx<R>{a.x + sm.x, a.y + sm.y};
+    if (full) {
+      // W^N = exp(-2 pi i/3): X[k+N] = a - sm/2 - i c3 (b - c), X[k+2N] = a - sm/2 + i c3 (b - c)
+      const Cplx<R> h{a.x - R(0.5) * sm.x, a.y - R(0.5) * sm.y};
+      const Cplx<R> d{c3 * (b.x - c.x), c3 * (b.y - c.y)};
+      x[N] = Cplx<R>{h.x + d.y, h.y - d.x};
+      x[2 * N] = Cplx<R>{h.x - d.y, h.y + d.x};
+    }
+  }
+  __syncthreads();
+}
+
+// Row FFTs of either length kind (r3 = 0: M = 2^logn; r3 = 1: M = 3 2^logn).
+template <typename R>
+__device__ __forceinline__ void fft_rows_any(Cplx<R>* s, int nrows, int M, int logn, int r3,
+                                             const Cplx<R>* __restrict__ tw, int nkeep) {
+  if (r3)
+    block_fft_rows3(s, nrows, M / 3, logn, tw, nkeep);
+  else
+    block_fft_rows(s, nrows, M, logn, tw, nkeep);
+}
+
 // ------------------------------------------------------------ set-up -------
 template <typename R>
 __global__ void twiddle_kernel(Cplx<R>* tw, int M) {
@@ -135,25 +192,40 @@ __global__ void twiddle_kernel(Cplx<R>* tw, int M) {
 
 // Torus covariance c[b][a] = sigma2 exp(-||(d_a h, d_b h)||_r / lam),
 // d_a = min(a, M - a), h = 1/m (Eq. 2.3 at cell-centre offsets).
+// cutoff (2-norm): the cut-off embedding's radial function instead: Eq. 2.3
+// up to R0 = sqrt(2)(m - 1)/m (the largest centre distance), the C^1 cubic
+// from (R0, value and slope of Eq. 2.3) to (R1 = M/(2m), 0 and slope 0),
+// zero beyond R1.
 __global__ void covariance_kernel(Cplx<double>* c, int m, int M, double sigma2, double lam,
-                                  int norm_r) {
+                                  int norm_r, int cutoff) {
   const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= (int64_t)M * M) return;
   const int b = (int)(id / M), a = (int)(id - (int64_t)b * M);
   const double dx = (double)min(a, M - a) / (double)m;
   const double dy = (double)min(b, M - b) / (double)m;
   const double dist = norm_r == 1 ? fabs(dx) + fabs(dy) : sqrt(dx * dx + dy * dy);
-  c[id] = Cplx<double>{sigma2 * exp(-dist / lam), 0.0};
+  double v = sigma2 * exp(-dist / lam);
+  if (cutoff) {
+    const double R0 = sqrt(2.0) * (double)(m - 1) / (double)m, R1 = (double)M / (2.0 * (double)m);
+    if (dist >= R1) {
+      v = 0.0;
+    } else if (dist > R0) {
+      const double w = R1 - R0, t = (dist - R0) / w;
+      const double c0 = sigma2 * exp(-R0 / lam), d0 = -c0 / lam * w;
+      v = c0 * (2.0 * t * t * t - 3.0 * t * t + 1.0) + d0 * (t * t * t - 2.0 * t * t + t);
+    }
+  }
+  c[id] = Cplx<double>{v, 0.0};
 }
 
 // Full in-place FFT of each row of a rows x M array (global), one row per block.
-__global__ void fft_rows_full_kernel(Cplx<double>* data, int M, int logM, const Cplx<double>* tw) {
+__global__ void fft_rows_full_kernel(Cplx<double>* data, int M, int logn, int r3, const Cplx<double>* tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cplx<double>* s = reinterpret_cast<Cplx<double>*>(smem_raw);
   Cplx<double>* row = data + (int64_t)blockIdx.x * M;
-  for (int t = threadIdx.x; t < M; t += blockDim.x) s[brev_n(t, logM)] = row[t];
+  for (int t = threadIdx.x; t < M; t += blockDim.x) s[fft_pos(t, logn, r3)] = row[t];
   __syncthreads();
-  block_fft_rows(s, 1, M, logM, tw, M);
+  fft_rows_any(s, 1, M, logn, r3, tw, M);
   for (int t = threadIdx.x; t < M; t += blockDim.x) row[t] = s[t];
 }
 
@@ -255,7 +327,7 @@ __global__ void ce_rows_kernel(CeRowsArgs args, const R* __restrict__ scale,
                                const Cplx<R>* __restrict__ tw, Cplx<R>* __restrict__ W) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cplx<R>* s = reinterpret_cast<Cplx<R>*>(smem_raw);
-  const int M = args.M, logM = args.logM, m = args.m, rows = args.rows_per_block;
+  const int M = args.M, logM = args.logM, r3 = args.r3, m = args.m, rows = args.rows_per_block;
   const int rb = blockIdx.x, f = args.pair;
   const int64_t sidx = blockIdx.z + args.z_offset;
   const uint64_t sample = (uint64_t)(args.first + sidx);
@@ -273,11 +345,11 @@ __global__ void ce_rows_kernel(CeRowsArgs args, const R* __restrict__ scale,
     R re0, im0, re1, im1;
     box_muller_tab(w.w0, w.w1, tb, re0, im0, scale[(int64_t)q2 * M + q1]);
     box_muller_tab(w.w2, w.w3, tb, re1, im1, scale[(int64_t)q2 * M + q1 + 1]);
-    s[r * M + brev_n(q1, logM)] = Cplx<R>{re0, im0};
-    s[r * M + brev_n(q1 + 1, logM)] = Cplx<R>{re1, im1};
+    s[r * M + fft_pos(q1, logM, r3)] = Cplx<R>{re0, im0};
+    s[r * M + fft_pos(q1 + 1, logM, r3)] = Cplx<R>{re1, im1};
   }
   __syncthreads();
-  block_fft_rows(s, rows, M, logM, tw, m >= 4 ? m : M);
+  fft_rows_any(s, rows, M, logM, r3, tw, m >= 4 ? m : M);
   Cplx<R>* out = W + (sidx * (int64_t)args.n_rows + q2_0) * m;
   for (int t = threadIdx.x; t < rows * m; t += blockDim.x) {
     const int r = t / m, a = t - r * m;
@@ -296,7 +368,7 @@ __global__ void ce_cols_kernel(CeColsArgs args, const Cplx<R>* __restrict__ tw,
                                const Cplx<R>* __restrict__ W, G* __restrict__ g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cplx<R>* s = reinterpret_cast<Cplx<R>*>(smem_raw);
-  const int M = args.M, logM = args.logM, m = args.m, C = args.cols_per_block;
+  const int M = args.M, logM = args.logM, r3 = args.r3, m = args.m, C = args.cols_per_block;
   const int64_t nc = args.ncols;
   const int cb = blockIdx.x;
   const int64_t sidx = blockIdx.z + args.z_offset;
@@ -304,10 +376,10 @@ __global__ void ce_cols_kernel(CeColsArgs args, const Cplx<R>* __restrict__ tw,
   const Cplx<R>* in = W + (sidx * (int64_t)M) * nc + a0;
   for (int t = threadIdx.x; t < M * C; t += blockDim.x) {
     const int q2 = t / C, cc = t - q2 * C;
-    s[cc * M + brev_n(q2, logM)] = in[(int64_t)q2 * nc + cc];
+    s[cc * M + fft_pos(q2, logM, r3)] = in[(int64_t)q2 * nc + cc];
   }
   __syncthreads();
-  block_fft_rows(s, C, M, logM, tw, m >= 4 ? m : M);
+  fft_rows_any(s, C, M, logM, r3, tw, m >= 4 ? m : M);
   const bool has_im = args.t_im >= 0;
   G* g0 = g + (sidx * args.n_layers + args.t_re) * (int64_t)m * nc;
   G* g1 = g + (sidx * args.n_layers + (has_im ? args.t_im : args.t_re)) * (int64_t)m * nc;
@@ -346,10 +418,11 @@ __global__ void ce_mid_kernel(CeColsArgs args, const Cplx<R>* __restrict__ tw,
 }
 
 // ----------------------------------------------------------- host side ----
-int ce_build_table(int m, int M, double sigma2, double lam, int norm_r, void* scratch,
+int ce_build_table(int m, int M, double sigma2, double lam, int norm_r, int cutoff, void* scratch,
                    double* s64, float* s32, double* minmax_dev, void* tw64, void* tw32,
                    cudaStream_t st) {
-  const int logM = ilog2(M);
+  const int r3 = M % 3 == 0 ? 1 : 0;
+  const int logM = ilog2(r3 ? M / 3 : M);
   Cplx<double>* a = reinterpret_cast<Cplx<double>*>(scratch);
   Cplx<double>* b = a + (int64_t)M * M;
   const int64_t n = (int64_t)M * M;
@@ -357,12 +430,12 @@ int ce_build_table(int m, int M, double sigma2, double lam, int norm_r, void* sc
   const unsigned nblk = (unsigned)((n + nt - 1) / nt);
   twiddle_kernel<double><<<(M + nt - 1) / nt, nt, 0, st>>>((Cplx<double>*)tw64, M);
   twiddle_kernel<float><<<(M + nt - 1) / nt, nt, 0, st>>>((Cplx<float>*)tw32, M);
-  covariance_kernel<<<nblk, nt, 0, st>>>(a, m, M, sigma2, lam, norm_r);
+  covariance_kernel<<<nblk, nt, 0, st>>>(a, m, M, sigma2, lam, norm_r, cutoff);
   const size_t sm = (size_t)M * sizeof(Cplx<double>);
   cudaFuncSetAttribute(fft_rows_full_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  fft_rows_full_kernel<<<M, 256, sm, st>>>(a, M, logM, (const Cplx<double>*)tw64);
+  fft_rows_full_kernel<<<M, 256, sm, st>>>(a, M, logM, r3, (const Cplx<double>*)tw64);
   transpose_kernel<<<nblk, nt, 0, st>>>(a, b, M);
-  fft_rows_full_kernel<<<M, 256, sm, st>>>(b, M, logM, (const Cplx<double>*)tw64);
+  fft_rows_full_kernel<<<M, 256, sm, st>>>(b, M, logM, r3, (const Cplx<double>*)tw64);
   transpose_kernel<<<nblk, nt, 0, st>>>(b, a, M);
   minmax_kernel<<<1, 1024, 0, st>>>(a, n, minmax_dev);
   scale_kernel<<<nblk, nt, 0, st>>>(a, s64, s32, M);
@@ -403,10 +476,11 @@ static int ce_sample3_impl(const CeLaunch& L, const R* scale, const void* tw, vo
   CeRowsArgs ra;
   ra.bm_sc = L.bm_sc;
   ra.bm_lg = L.bm_lg;
-  ra.M = M; ra.logM = ilog2(M); ra.m = m; ra.rows_per_block = rows; ra.pair = L.pair;
+  ra.M = M; ra.logM = ilog2(M); ra.r3 = 0; ra.m = m; ra.rows_per_block = rows; ra.pair = L.pair;
   ra.level = L.level; ra.seed = L.seed; ra.first = L.first; ra.n_rows = M * M;
   CeColsArgs ma;
-  ma.M = M; ma.logM = ra.logM; ma.m = m; ma.cols_per_block = cmid; ma.n_layers = L.n_layers; ma.ncols = m;
+  ma.M = M; ma.logM = ra.logM; ma.r3 = 0; ma.m = m; ma.cols_per_block = cmid; ma.n_layers = L.n_layers;
+  ma.ncols = m;
   ma.t_re = L.t_re; ma.t_im = L.t_im; ma.mu_re = L.mu_re; ma.mu_im = L.mu_im;
   CeColsArgs ca = ma;
   ca.cols_per_block = c3;
@@ -430,21 +504,23 @@ static int ce_sample_impl(const CeLaunch& L, const R* scale, const void* tw, voi
                           cudaStream_t st) {
   if (L.dim == 3) return ce_sample3_impl<R, G>(L, scale, tw, W, g, st);
   const size_t esz = sizeof(Cplx<R>);
-  // rows / columns per block: at most 64 KB of FP64 (128 KB of FP32) per block
+  // rows / columns per block: at most 64 KB of FP64 (128 KB of FP32) per
+  // block, a power of two so that it divides M (= 2^k or 3 2^k) and m
   const int budget = (int)(65536 / sizeof(Cplx<double>)) * (int)(sizeof(Cplx<double>) / esz);
-  int rows = budget / L.M;
-  if (rows < 1) rows = 1;
-  if (rows > L.M) rows = L.M;
-  int cols = budget / L.M;
-  if (cols < 1) cols = 1;
+  const int r3 = L.M % 3 == 0 ? 1 : 0;
+  auto pow2_floor = [](int v) { int p = 1; while (2 * p <= v) p *= 2; return p; };
+  int rows = pow2_floor(std::max(1, budget / L.M));
+  while (L.M % rows) rows >>= 1;  // M = 3 2^k: at most 2^k rows per block
+  int cols = pow2_floor(std::max(1, budget / L.M));
   if (cols > L.m) cols = L.m;
   CeRowsArgs ra;
   ra.bm_sc = L.bm_sc;
   ra.bm_lg = L.bm_lg;
-  ra.M = L.M; ra.logM = ilog2(L.M); ra.m = L.m; ra.rows_per_block = rows; ra.pair = L.pair;
-  ra.level = L.level; ra.seed = L.seed; ra.first = L.first; ra.n_rows = L.M;
+  ra.M = L.M; ra.logM = ilog2(r3 ? L.M / 3 : L.M); ra.r3 = r3; ra.m = L.m; ra.rows_per_block = rows;
+  ra.pair = L.pair; ra.level = L.level; ra.seed = L.seed; ra.first = L.first; ra.n_rows = L.M;
   CeColsArgs ca;
-  ca.M = L.M; ca.logM = ra.logM; ca.m = L.m; ca.cols_per_block = cols; ca.n_layers = L.n_layers; ca.ncols = L.m;
+  ca.M = L.M; ca.logM = ra.logM; ca.r3 = r3; ca.m = L.m; ca.cols_per_block = cols; ca.n_layers = L.n_layers;
+  ca.ncols = L.m;
   ca.t_re = L.t_re; ca.t_im = L.t_im; ca.mu_re = L.mu_re; ca.mu_im = L.mu_im;
   const size_t sm_r = (size_t)rows * L.M * esz;
   const size_t sm_c = (size_t)cols * L.M * esz;

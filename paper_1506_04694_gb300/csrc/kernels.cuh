@@ -13,6 +13,7 @@ struct CeRowsArgs {
   const double2* bm_sc;  // Box-Muller tables (common.cuh, BmTables)
   const double* bm_lg;
   int M, logM, m, rows_per_block, pair, level;
+  int r3;            // 1: M = 3 2^logM (cut-off embedding), 0: M = 2^logM
   int n_rows;        // rows of M points per sample: M (2-D) or M^2 (3-D)
   uint64_t seed;
   int64_t first;     // sample index of chunk entry 0
@@ -21,6 +22,7 @@ struct CeRowsArgs {
 
 struct CeColsArgs {
   int M, logM, m, cols_per_block, n_layers;
+  int r3;          // as in CeRowsArgs
   int64_t ncols;   // columns of the M-row input: m (2-D), m (3-D middle pass) or m^2 (3-D last pass)
   int t_re, t_im;  // layers fed by Re and Im of this draw (t_im < 0: none)
   double mu_re, mu_im;
@@ -39,7 +41,8 @@ struct CeLaunch {
   int64_t first, n_samples;
 };
 
-int ce_build_table(int m, int M, double sigma2, double lam, int norm_r, void* scratch,
+// M = 2^k, or M = 3 2^k with the cut-off embedding (cutoff = 1, 2-norm).
+int ce_build_table(int m, int M, double sigma2, double lam, int norm_r, int cutoff, void* scratch,
                    double* s64, float* s32, double* minmax_dev, void* tw64, void* tw32,
                    cudaStream_t st);
 int ce_build_table3(int m, int M, double sigma2, double lam, int norm_r, void* scratch, double* s64,

@@ -92,9 +92,9 @@ def _checkpoint_text(d, levels):
     pad = lambda v, n: list(v) + [v[-1]] * (n - len(v))
     g = lambda x: "%.17g" % x
     lines = ["mlmc_checkpoint 2",
-             "model %d %d %d %d %d %d %d %d %d %d %d" % (
+             "model %d %d %d %d %d %d %d %d %d %d %d %d" % (
                  d["n_layers"], d["k_kind"], d["norm_r"], d["m0"], d["L"], d["cgv"], d["prec"], d["max_it"],
-                 d.get("problem", 0), d.get("geometry", 0), d.get("dim", 2)),
+                 d.get("problem", 0), d.get("geometry", 0), d.get("dim", 2), d.get("embed", 0)),
              "model_if %s %s" % (g(d["if_lo"]), g(d["if_hi"])), "model_tol %s" % g(d["tol"])]
     for key in ("mu", "sigma2", "lam"):
         lines.append("model_%s %s" % (key, " ".join(g(x) for x in pad(d[key], 8))))
@@ -116,7 +116,7 @@ def test_checkpoint_check_rejects_other_models(pk, tmp_path):
     pk.checkpoint_check(d, str(path))  # the same model is accepted
     for key, val in (("sigma2", [1.5, 1.5]), ("lam", [0.2, 0.2]), ("mu", [0.0, 0.1]), ("tol", 1e-12),
                      ("if_lo", 0.25), ("if_hi", 0.75), ("norm_r", 1), ("prec", 1), ("cgv", 1), ("m0", 8),
-                     ("max_it", 100)):
+                     ("max_it", 100), ("embed", 1)):
         with pytest.raises(pk.MLMCError, match="differs"):
             pk.checkpoint_check(dict(d, **{key: val}), str(path))
     # fields that do not change Q for this model are not compared: the box of

@@ -73,19 +73,25 @@ def test_const_fields():
         np.testing.assert_allclose(g[s], ref, rtol=1e-14, atol=1e-14)
 
 
-@pytest.mark.parametrize("name,levels", [("lognormal_2layer_16to256", (0, 1, 2)),
-                                         ("lognormal_4layer_cgv_16to1024", (0, 1))])
-def test_ce_fields_fp64(name, levels):
+# lambda = 0.3: m = 16 embeds periodically at M = 32, m = 32 ... 256 with the
+# cut-off embedding at M = 3m (radix-3 FFT stage); embed = 1 keeps the
+# powers-of-two padding (M = 4m); lambda = 0.1 embeds at M = 2m.
+@pytest.mark.parametrize("name,levels,embed", [("lognormal_2layer_16to256", (0, 1, 2, 4), 0),
+                                               ("lognormal_2layer_16to256", (1, 2), 1),
+                                               ("lognormal_4layer_cgv_16to1024", (0, 1), 0)])
+def test_ce_fields_fp64(name, levels, embed):
     torch, pk = need_gpu()
-    d = workloads.workload(name, prec=0)
+    d = workloads.workload(name, prec=0, embed=embed)
     model = darcy.Model.from_dict(d)
     cache = {}
     with pk.Context(d) as ctx:
         for level in levels:
             m = model.m(level)
             M, lo, hi = ctx.ce_info(level)
-            Mo, _ = darcy.ce_padding(m, model.sigma2[0], model.lam[0], model.norm_r)
-            assert M == Mo
+            Mo, _ = darcy.ce_padding(m, model.sigma2[0], model.lam[0], model.norm_r, model.embed)
+            assert M == Mo and lo >= -1e-13 * hi
+            if name == "lognormal_2layer_16to256" and m >= 32:
+                assert M == (3 * m if embed == 0 else 4 * m)
             n = 6
             g, _ = ctx.sample_fields(level, n, seed=3, first=11)
             g = g.cpu().numpy()
@@ -94,15 +100,21 @@ def test_ce_fields_fp64(name, levels):
                 np.testing.assert_allclose(g[s], ref, rtol=0, atol=1e-12)
 
 
-def test_ce_fields_fp32_error_bound():
+@pytest.mark.parametrize("level", [2, 5])
+def test_ce_fields_fp32_error_bound(level):
+    # the mixed workload's FP32 embedding: m = 64 (M = 192) and the finest
+    # level m = 512 (M = 1536, the cut-off embedding's radix-3 stage in FP32)
     torch, pk = need_gpu()
-    d = workloads.workload("lognormal_2layer_cgv_16to512", L=2)
+    d = workloads.workload("lognormal_2layer_cgv_16to512")
     model = darcy.Model.from_dict(d)
+    m = model.m(level)
     with pk.Context(d) as ctx:
-        g, _ = ctx.sample_fields(2, 4, seed=1)
+        assert ctx.ce_info(level)[0] == 3 * m
+        g, _ = ctx.sample_fields(level, 3, seed=1)
         g = g.cpu().numpy()
-    for s in range(4):
-        ref = darcy.layer_fields(model, 1, 2, s, 64)
+    cache = {}
+    for s in range(3):
+        ref = darcy.layer_fields(model, 1, level, s, m, cache)
         assert np.max(np.abs(g[s] - ref)) < 2e-5
 
 
