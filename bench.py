@@ -233,7 +233,7 @@ def timed_estimates(ctx, d, seed, steps, warmup, flush, stream):
 
 
 def solve_kernel_name(prec, t):
-    mode = 2 if t["cluster"] else 1 if t["warp"] else 0
+    mode = 2 if t["cluster"] else 3 if t["warp"] == 2 else 1 if t["warp"] else 0
     return "solve_kernel<%d, %d>" % (prec, mode)
 
 
@@ -404,7 +404,8 @@ PROFILE_CASES = {
                      [(0, 65535, (1, 0, 0, 1, 2), None), (3, 1024, (0, 512, 0, 1, 2), None)]),
     "mixed_large": ("lognormal_2layer_cgv_32to2048", {}, [(5, 8, (2, 512, 8, 1, 2), None)]),
     "mixed_small": ("lognormal_2layer_cgv_16to512", {},
-                    [(0, 65535, (1, 0, 0, 1, 1), None), (1, 16384, (0, 128, 0, 1, 1), None)]),
+                    [(0, 65535, (3, 0, 0, 1, 1), None), (1, 16384, (0, 128, 0, 1, 1), None)]),
+    "mixed_small_generic": ("lognormal_2layer_cgv_16to512", {}, [(0, 65535, (1, 0, 0, 1, 1), None)]),
     "mixed_m256": ("lognormal_2layer_cgv_16to512", {}, [(4, 256, (0, 512, 0, 1, 2), (1, 1e-3))]),
     "mixed_m512": ("lognormal_2layer_cgv_16to512", {}, [(5, 128, (2, 512, 4, 1, 2), None)]),
     "mixed_1024": ("lognormal_2layer_cgv_32to2048", {}, [(5, 32, (2, 512, 8, 1, 2), None)]),

@@ -259,7 +259,8 @@ MLMC_API int mlmc_multilevel_batch(mlmc_ctx* ctx, int32_t n_levels, const int64_
 /* Result of mlmc_autotune(), per level. */
 typedef struct mlmc_tune_report {
   int32_t threads[MLMC_MAX_LEVELS];            /* threads per block chosen */
-  int32_t warp[MLMC_MAX_LEVELS];               /* 1: one warp per system */
+  int32_t warp[MLMC_MAX_LEVELS];               /* 1: one warp per system; 2: the same with the
+                                                  finest grid in registers (m = 16, prec 1) */
   int32_t cap_blocks_per_sm[MLMC_MAX_LEVELS];  /* 0: occupancy limit */
   int32_t cluster[MLMC_MAX_LEVELS];            /* > 0: blocks of the cluster that solves one system */
   int32_t gamma[MLMC_MAX_LEVELS];              /* multigrid cycle: 1 V, 2 W */
@@ -291,7 +292,9 @@ MLMC_API int mlmc_autotune(mlmc_ctx* ctx, uint64_t seed, mlmc_tune_report* rep);
 /* Fix the solver's launch plan of one level by hand (overrides
  * mlmc_autotune): mode 0 = one block of `threads` (32..512, multiple of 32)
  * per system, 1 = one warp per system, 2 = one thread-block cluster of
- * `cluster` (2, 4, 8) blocks of 512 threads per system; gamma 1 = V-cycle,
+ * `cluster` (2, 4, 8) blocks of 512 threads per system, 3 = one warp per
+ * system with the finest grid in registers (m = 16, prec 1, 2-D; the
+ * default there); gamma 1 = V-cycle,
  * 2 = W-cycle preconditioner; nu = 1..4 red-black sweep pairs before and
  * after each coarse correction; mode < 0 restores the built-in default
  * (V-cycle, nu = 1).  Errors: MLMC_ERR_ARG. */

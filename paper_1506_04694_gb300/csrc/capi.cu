@@ -1341,9 +1341,11 @@ int mlmc_set_launch(mlmc_ctx* c, int level, int32_t mode, int32_t threads, int32
     c->tuned_ok[level] = false;
     return 0;
   }
-  if (mode > 2 || (mode == 0 && (threads < 32 || threads > 512 || threads % 32)) ||
+  if (mode > 3 || (mode == 0 && (threads < 32 || threads > 512 || threads % 32)) ||
       (mode == 2 && (cluster < 2 || cluster > 8 || (cluster & (cluster - 1)))))
     return fail(MLMC_ERR_ARG, "mode 0: threads 32..512 (multiple of 32); mode 2: cluster 2, 4 or 8");
+  if (mode == 3 && ((c->model.m0 << level) != 16 || c->model.prec != 1 || dim_of(c->model) == 3))
+    return fail(MLMC_ERR_ARG, "mode 3 (register path) needs m = 16, prec 1, 2-D");
   SolvePlan P;
   if (gamma < 1 || gamma > 2) return fail(MLMC_ERR_ARG, "gamma must be 1 (V-cycle) or 2 (W-cycle)");
   if (nu < 1 || nu > 4) return fail(MLMC_ERR_ARG, "nu must be 1..4");

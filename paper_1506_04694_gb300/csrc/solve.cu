@@ -533,12 +533,14 @@ __device__ __forceinline__ void coarse_solve(const G& g, const Level<T, F>& L) {
 // over an explicit per-level visit count (no recursion: the device stack
 // stays fixed).  With adjoint pre- and post-smoothing the cycle is a
 // symmetric positive definite preconditioner for any gamma.
+// zero_start = false starts level 0 from its current e (a repeated visit).
 template <typename T, typename F, typename G>
-__device__ void mg_cycle(const G& g, const Level<T, F>* lev, int nl, int gamma, int nu, int nuc) {
+__device__ void mg_cycle(const G& g, const Level<T, F>* lev, int nl, int gamma, int nu, int nuc,
+                         bool zero_start = true) {
   int done[kMaxLevels];   // visits of level l+1 finished in the current cycle on level l
   bool zero[kMaxLevels];  // level l starts from e_l = 0
   int l = 0;
-  zero[0] = true;
+  zero[0] = zero_start;
   while (true) {
     if (l < nl - 1) {  // descend: pre-smooth, restrict, enter the next level
       const int ns = l == 0 ? nu : nuc;
@@ -1235,18 +1237,27 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
   g.sync();
 }
 
+}  // namespace mlmc
+
+#include "tiny.cuh"
+
+namespace mlmc {
+
 // MODE 0: one block per system; 1: one warp per system (kWarpsPerBlock
-// systems per block); 2: one thread-block cluster per system.
+// systems per block); 2: one thread-block cluster per system; 3: one warp
+// per system with 16 x 16 systems on the register-resident path (prec 1;
+// other sizes of the launch take the generic warp path).
 template <int PREC, int MODE>
-__global__ void __launch_bounds__(MODE == 1 ? 32 * kWarpsPerBlock : kMaxThreads, MODE == 1 ? 5 : 2)
+__global__ void __launch_bounds__(MODE == 1 || MODE == 3 ? 32 * kWarpsPerBlock : kMaxThreads,
+                                  MODE == 1 ? 5 : MODE == 3 ? 3 : 2)
     solve_kernel(SolveArgs a) {
   using T = typename SolverTypes<PREC>::T;
   using F = typename SolverTypes<PREC>::F;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int kGroups = MODE == 1 ? kWarpsPerBlock : 1;
+  constexpr int kGroups = MODE == 1 || MODE == 3 ? kWarpsPerBlock : 1;
   __shared__ GroupState<T, F> gstate[kGroups];
-  __shared__ T red[MODE == 1 ? 1 : 132];
-  __shared__ double red64[MODE == 1 ? 1 : 132];
+  __shared__ T red[MODE == 1 || MODE == 3 ? 1 : 132];
+  __shared__ double red64[MODE == 1 || MODE == 3 ? 1 : 132];
   const int64_t n_sys = a.n_samples * (int64_t)(1 + a.n_coarse);
   int par = 0, m_prev = -1;
   if (MODE == 2) {
@@ -1261,13 +1272,20 @@ __global__ void __launch_bounds__(MODE == 1 ? 32 * kWarpsPerBlock : kMaxThreads,
     cl.sync();  // no block leaves while others may still read its shared memory
     return;
   }
-  const int gid = MODE == 1 ? (int)(threadIdx.x >> 5) : 0;
+  const int gid = MODE == 1 || MODE == 3 ? (int)(threadIdx.x >> 5) : 0;
   const size_t slot = (size_t)blockIdx.x * kGroups + gid;
   unsigned char* base = a.use_smem ? smem_raw + (size_t)gid * a.ws_stride : a.ws + slot * a.ws_stride;
   unsigned char* base64 = a.ws64_stride ? a.ws64 + slot * a.ws64_stride : nullptr;
   const int64_t stride = (int64_t)gridDim.x * kGroups;
   for (int64_t sys = (int64_t)blockIdx.x * kGroups + gid; sys < n_sys; sys += stride) {
-    if (MODE == 1)
+    if constexpr (MODE == 3 && PREC == 1) {
+      const int msys = sys < a.n_samples ? a.m : a.m >> 1;
+      if (msys == kTinyM) {
+        solve_one_tiny(WarpGroup(), a, sys, base, gstate[gid], m_prev);
+        continue;
+      }
+    }
+    if (MODE == 1 || MODE == 3)
       solve_one<PREC>(WarpGroup(), a, sys, base, gstate[gid], red, red64, par, m_prev, base64, nullptr);
     else
       solve_one<PREC>(BlockGroup(), a, sys, base, gstate[gid], red, red64, par, m_prev, base64, nullptr);
@@ -1280,21 +1298,27 @@ static const size_t kSmemCap = 110 * 1024;
 
 template <int PREC, int MODE>
 static int plan_fill(int m, int threads, int cluster, SolvePlan* P) {
-  const size_t ws = solve_ws_bytes(m, PREC);
+  if (MODE == 3 && !(PREC == 1 && m == kTinyM)) return -1;  // the register path: m = 16, prec 1
+  // MODE 3 solves its 16 x 16 systems with the register path (shared memory
+  // for the coarser levels only) and any 8 x 8 coarse systems generically
+  size_t ws = MODE == 3 ? std::max(tiny_ws_bytes(), solve_ws_bytes(m / 2, PREC)) : solve_ws_bytes(m, PREC);
   int nsm = 0, dev = 0;
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
-  P->warp = MODE == 1;
+  P->warp = MODE == 1 ? 1 : MODE == 3 ? 2 : 0;
   P->cluster = MODE == 2 ? cluster : 0;
-  P->threads = MODE == 1 ? 32 * kWarpsPerBlock : threads;
-  P->groups_per_block = MODE == 1 ? kWarpsPerBlock : 1;
+  P->threads = MODE == 1 || MODE == 3 ? 32 * kWarpsPerBlock : threads;
+  P->groups_per_block = MODE == 1 || MODE == 3 ? kWarpsPerBlock : 1;
   P->blocks_per_group = MODE == 2 ? cluster : 1;
   // prec 1, 2: the FP64 solution and residual of the refinement (touched once
   // per refinement sweep) stay in global memory when the rest of the
   // workspace fits on chip, so more systems fit per SM
-  const size_t v64 = (PREC == 1 || PREC == 2) ? 2 * align16((size_t)m * m * 8) : 0;
+  const int m64 = MODE == 3 ? m / 2 : m;  // the register path keeps them in registers
+  const size_t v64 = (PREC == 1 || PREC == 2) ? 2 * align16((size_t)m64 * m64 * 8) : 0;
+  if (MODE == 3) ws += v64;  // chip = ws - v64 below
   const size_t chip = ((ws - v64) + 255) & ~(size_t)255;
   P->use_smem = MODE != 2 && chip * P->groups_per_block <= kSmemCap;
+  if (MODE == 3 && !P->use_smem) return -1;
   P->ws_stride = P->use_smem ? chip : (ws + 255) & ~(size_t)255;
   P->ws64_stride = P->use_smem && v64 ? (v64 + 255) & ~(size_t)255 : 0;
   P->smem_bytes = P->use_smem ? P->ws_stride * P->groups_per_block : 0;
@@ -1345,6 +1369,10 @@ template <int PREC>
 static int plan_fill_mode(int m, int mode, int threads, int cluster, SolvePlan* P) {
   if (mode == 1) return plan_fill<PREC, 1>(m, threads, cluster, P);
   if (mode == 2) return plan_fill<PREC, 2>(m, threads, cluster, P);
+  if (mode == 3) {
+    if constexpr (PREC == 1) return plan_fill<1, 3>(m, threads, cluster, P);
+    return -1;
+  }
   return plan_fill<PREC, 0>(m, threads, cluster, P);
 }
 
@@ -1360,6 +1388,7 @@ static int plan_fill(int m, int prec, int mode, int threads, int cluster, SolveP
 // above (the system's working set then sits in L2 instead of streaming).
 int solve_plan(int m, int prec, SolvePlan* P) {
   if (m >= 512) return plan_fill(m, prec, 2, kMaxThreads, m >= 1024 ? 8 : 4, P);
+  if (m == kTinyM && prec == 1 && plan_fill(m, prec, 3, 0, 0, P) == 0) return 0;
   return plan_fill(m, prec, solve_warp_mode(m) ? 1 : 0, solve_threads(m), 0, P);
 }
 
@@ -1379,7 +1408,7 @@ int solve_plan_candidates(int m, int prec, SolvePlan* out, int max_out) {
     SolvePlan b;
     if (!plan_fill(m, prec, 0, kMaxThreads, 0, &b)) add(b);
   }
-  if (m <= 64 && !d.warp) {
+  if (m <= 64 && d.warp != 1) {  // the generic warp plan
     SolvePlan w;
     if (!plan_fill(m, prec, 1, 0, 0, &w)) add(w);
   }
@@ -1436,8 +1465,13 @@ int solve_launch(const SolveArgs& a, int prec, const SolvePlan& P, int n_blocks,
     cfg.attrs = attr;
     cfg.numAttrs = 1;
   }
-  const int mode = P.cluster ? 2 : P.warp ? 1 : 0;
+  const int mode = P.cluster ? 2 : P.warp == 2 ? 3 : P.warp ? 1 : 0;
   cudaError_t e = cudaErrorInvalidValue;
+  if (mode == 3) {
+    if (prec == 1) e = cudaLaunchKernelEx(&cfg, solve_kernel<1, 3>, b);
+    last_launch_error() = e;
+    return e == cudaSuccess ? 0 : -1;
+  }
   switch (prec * 3 + mode) {
     case 0: e = cudaLaunchKernelEx(&cfg, solve_kernel<0, 0>, b); break;
     case 1: e = cudaLaunchKernelEx(&cfg, solve_kernel<0, 1>, b); break;
