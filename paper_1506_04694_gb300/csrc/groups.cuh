@@ -14,6 +14,7 @@ namespace cg = cooperative_groups;
 struct BlockGroup {
   static constexpr int kU = 1;  // cells per thread per batch in the cell loops
   static constexpr bool kStaged = false;  // runs the shared-memory staged half sweeps
+  static constexpr bool kQuads = true;    // FP32 half sweeps over quads of 16-byte accesses
   __device__ __forceinline__ bool local_leader() const { return threadIdx.x == 0; }
   __device__ __forceinline__ int rank() const { return threadIdx.x; }
   __device__ __forceinline__ int size() const { return blockDim.x; }
@@ -33,6 +34,7 @@ struct BlockGroup {
 struct WarpGroup {
   static constexpr int kU = 1;
   static constexpr bool kStaged = false;
+  static constexpr bool kQuads = true;
   __device__ __forceinline__ bool local_leader() const { return (threadIdx.x & 31) == 0; }
   __device__ __forceinline__ int rank() const { return threadIdx.x & 31; }
   __device__ __forceinline__ int size() const { return 32; }
@@ -58,6 +60,7 @@ struct WarpGroup {
 struct ClusterGroup {
   static constexpr int kU = 1;
   static constexpr bool kStaged = true;
+  static constexpr bool kQuads = true;
   unsigned nblk, brank;
   double* part;  // two double slots in this block's shared memory
   __device__ __forceinline__ bool local_leader() const { return threadIdx.x == 0; }

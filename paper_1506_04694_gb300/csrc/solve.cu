@@ -121,6 +121,8 @@ struct Level {
   T* cbuf;  // coarsest level only: pivot row, pivot column (2 m^2 + 1)
   unsigned char* stage;  // shared-memory staging of the half sweeps (null: direct loads)
   int stage_rows;        // rows per staged chunk
+  int quads;             // FP32 half sweeps over quads of 16-byte accesses (global workspace,
+                         // at least one quad per thread of the group)
 };
 
 // Cell arrays (solution, right-hand side, diagonal, CG vectors) are stored
@@ -324,11 +326,97 @@ __device__ void rb_sweep_staged(const G& g, const Level<T, T>& L, int color, boo
   g.sync();
 }
 
+// Four consecutive FP32 values of a cell or face array, one 16-byte access
+// (the index a multiple of 4 from a 16-byte aligned array start).
+struct F4 {
+  float v[4];
+};
+__device__ __forceinline__ F4 ld4(const float* p) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  return F4{{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ void st4(float* p, const F4& a) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
+}
+
+// FP32 half sweep over quads of four consecutive cells of one colour in a
+// row (m >= 8, so a colour row holds a multiple of four cells): the own
+// colour's f, inverse diagonal and new e, the other colour's rows j - 1 and
+// j + 1 at the same four indices, the other colour's row j (indices k0 - 1 ..
+// k0 + 4) and the y-faces of rows j and j + 1 (columns 2 k0 .. 2 k0 + 7) move
+// as 16-byte accesses; the x-faces (row stride m + 1, not aligned) as single
+// values.  The arithmetic is rb_sweep's, term for term.
+template <typename G>
+__device__ __forceinline__ void rb_sweep_quads(const G& g, const Level<float, float>& L, int color, bool zero_guess) {
+  const int m = L.m;
+  const RbIndex R(m);
+  const int hm = R.hm;
+  const int nq = (m * hm) >> 2;
+  const int own0 = color * R.half, oth0 = (color ^ 1) * R.half;
+  for (int q = g.rank(); q < nq; q += g.size()) {
+    const int h0 = q << 2;
+    const int j = h0 >> R.lhm, k0 = h0 - (j << R.lhm);
+    const int sh = (j + color) & 1;
+    const int c0 = own0 + h0;
+    F4 s = ld4(L.f + c0);
+    const F4 id = ld4(L.invd + c0);
+    if (!zero_guess) {
+      const int ob = oth0 + j * hm + k0;
+      const F4 mid = ld4(L.e + ob);
+      float W[4], E[4];
+      if (sh) {
+        const float after = k0 + 4 < hm ? L.e[ob + 4] : 0.f;  // k0 + 4 (unused at the east boundary)
+        W[0] = mid.v[0]; W[1] = mid.v[1]; W[2] = mid.v[2]; W[3] = mid.v[3];
+        E[0] = mid.v[1]; E[1] = mid.v[2]; E[2] = mid.v[3]; E[3] = after;
+      } else {
+        const float before = k0 > 0 ? L.e[ob - 1] : 0.f;  // k0 - 1 (unused at the west boundary)
+        W[0] = before; W[1] = mid.v[0]; W[2] = mid.v[1]; W[3] = mid.v[2];
+        E[0] = mid.v[0]; E[1] = mid.v[1]; E[2] = mid.v[2]; E[3] = mid.v[3];
+      }
+      const int i0 = 2 * k0 + sh;
+      const float* tx = L.tx + j * (m + 1) + i0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + 2 * u;
+        if (i > 0) s.v[u] += tx[2 * u] * W[u];
+        if (i < m - 1) s.v[u] += tx[2 * u + 1] * E[u];
+      }
+      if (j > 0) {
+        const F4 es = ld4(L.e + ob - hm);
+        const F4 ta = ld4(L.ty + j * m + 2 * k0), tb = ld4(L.ty + j * m + 2 * k0 + 4);
+        const float ty[4] = {sh ? ta.v[1] : ta.v[0], sh ? ta.v[3] : ta.v[2], sh ? tb.v[1] : tb.v[0],
+                             sh ? tb.v[3] : tb.v[2]};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s.v[u] += ty[u] * es.v[u];
+      }
+      if (j < m - 1) {
+        const F4 en = ld4(L.e + ob + hm);
+        const F4 ta = ld4(L.ty + (j + 1) * m + 2 * k0), tb = ld4(L.ty + (j + 1) * m + 2 * k0 + 4);
+        const float ty[4] = {sh ? ta.v[1] : ta.v[0], sh ? ta.v[3] : ta.v[2], sh ? tb.v[1] : tb.v[0],
+                             sh ? tb.v[3] : tb.v[2]};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s.v[u] += ty[u] * en.v[u];
+      }
+    }
+    F4 out;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) out.v[u] = s.v[u] * id.v[u];
+    st4(L.e + c0, out);
+  }
+  g.sync();
+}
+
 template <typename T, typename F, typename G>
 __device__ __forceinline__ void rb_sweep(const G& g, const Level<T, F>& L, int color, bool zero_guess) {
   if constexpr (std::is_same<T, F>::value && G::kStaged) {
     if (L.stage) {
       rb_sweep_staged(g, L, color, zero_guess);
+      return;
+    }
+  }
+  if constexpr (std::is_same<T, float>::value && std::is_same<F, float>::value && G::kQuads) {
+    if (L.quads) {
+      rb_sweep_quads(g, L, color, zero_guess);
       return;
     }
   }
@@ -894,6 +982,10 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
         L.cinv = L.cbuf = nullptr;
         L.stage = nullptr;
         L.stage_rows = 0;
+        // measured on GB300: the quads pay where the level streams from global
+        // memory and every thread gets one; on shared-memory levels, or with
+        // idle threads, the single-cell loop is faster
+        L.quads = !a.use_smem && ml >= 8 && ml * (ml / 2) / 4 >= g.size();
         if (std::is_same<T, F>::value && stage && ml >= kStageMin &&
             stage_level_bytes<T>(ml, (int)blockDim.x) <= a.stage_bytes) {
           L.stage = stage;
@@ -1249,7 +1341,7 @@ namespace mlmc {
 // other sizes of the launch take the generic warp path).
 template <int PREC, int MODE>
 __global__ void __launch_bounds__(MODE == 1 || MODE == 3 ? 32 * kWarpsPerBlock : kMaxThreads,
-                                  MODE == 1 ? 5 : MODE == 3 ? 3 : 2)
+                                  MODE == 1 ? 5 : MODE == 3 ? 4 : 2)
     solve_kernel(SolveArgs a) {
   using T = typename SolverTypes<PREC>::T;
   using F = typename SolverTypes<PREC>::F;

@@ -114,8 +114,10 @@ __device__ __forceinline__ void tiny_half_sweep(const TinyOp& A, const float (&f
 }
 
 // Per-system state of the tiny path in shared memory: the hierarchy below the
-// finest grid (levels of side 8 and 4) in the generic layout.
-__host__ __device__ inline size_t tiny_ws_bytes() {
+// finest grid (levels of side 8 and 4) in the generic layout, then the FP64
+// refinement solution and residual of the finest grid, [slot][lane] (slots
+// 0..3 red, 4..7 black), touched once per refinement sweep.
+__host__ __device__ inline size_t tiny_lev_bytes() {
   size_t o = 0;
   auto take = [&](size_t bytes) { o += align16(bytes); };
   for (int ml = kTinyM / 2;; ml >>= 1) {
@@ -131,6 +133,15 @@ __host__ __device__ inline size_t tiny_ws_bytes() {
   }
   return o;
 }
+__host__ __device__ inline size_t tiny_ws_bytes() { return tiny_lev_bytes() + 2 * 8 * 32 * sizeof(double); }
+
+// One FP64 cell vector of the finest grid in shared memory, [slot][lane].
+struct TinyVec64 {
+  double* p;
+  int lane;
+  __device__ __forceinline__ double& r(int t) const { return p[t * 32 + lane]; }
+  __device__ __forceinline__ double& b(int t) const { return p[(4 + t) * 32 + lane]; }
+};
 
 // Symmetric multigrid cycle z = B r with the finest level in registers:
 // nu red-black sweep pairs, the residual of the red cells restricted to the
@@ -231,20 +242,24 @@ __device__ __forceinline__ double tiny_residual64_colour(const SolveArgs& a, con
   return s2;
 }
 
-// k at cell (i, j) of a 16 x 16 system, as the generic assembly computes it.
+// k at cell (i, j) of a 16 x 16 system, as the generic assembly computes it;
+// row_layer >= 0: the layer of every cell of row j (horizontal interfaces).
 __device__ __forceinline__ double tiny_k_of_cell(const SolveArgs& a, const GroupState<float, float>& gs,
                                                  int64_t sys, int64_t sidx, bool coarse, int ox, int oy, int i,
-                                                 int j) {
+                                                 int j, int row_layer) {
   const int m = kTinyM;
   if (a.ksrc == KSRC_ARRAY) return a.k[sys * (int64_t)(m * m) + j * m + i];
-  const int n_if = a.geometry == 1 ? 0 : a.n_layers - 1;
-  const double inv_m = 1.0 / (double)m, inv_mf = 1.0 / (double)a.m;
   const int jf = coarse ? 2 * j + oy : j;
   const int iff = coarse ? 2 * i + ox : i;
-  const bool own = coarse && !a.cgv_on_k;
-  const double yc = own ? ((double)j + 0.5) * inv_m : ((double)jf + 0.5) * inv_mf;
-  const double xc = own ? ((double)i + 0.5) * inv_m : ((double)iff + 0.5) * inv_mf;
-  const int t = layer_at_point(a.geometry, gs.eta, n_if, xc, yc);
+  int t = row_layer;
+  if (t < 0) {
+    const int n_if = a.geometry == 1 ? 0 : a.n_layers - 1;
+    const double inv_m = 1.0 / (double)m, inv_mf = 1.0 / (double)a.m;
+    const bool own = coarse && !a.cgv_on_k;
+    const double yc = own ? ((double)j + 0.5) * inv_m : ((double)jf + 0.5) * inv_mf;
+    const double xc = own ? ((double)i + 0.5) * inv_m : ((double)iff + 0.5) * inv_mf;
+    t = layer_at_point(a.geometry, gs.eta, n_if, xc, yc);
+  }
   if (a.ksrc == KSRC_CONST) return gs.kc[t];
   const float* gf = reinterpret_cast<const float*>(a.g);
   return (double)expf(gf[((sidx * a.n_layers + t) * (int64_t)a.m + jf) * a.m + iff]);
@@ -298,6 +313,7 @@ __device__ void solve_one_tiny(const G& g, const SolveArgs& a, int64_t sys, unsi
         L.cinv = L.cbuf = nullptr;
         L.stage = nullptr;
         L.stage_rows = 0;
+        L.quads = 0;
         if (ml <= kCoarseSide) {
           L.cinv = reinterpret_cast<T*>(take(nlv * nlv * 4));
           L.cbuf = reinterpret_cast<T*>(take((2 * nlv + 1) * 4));
@@ -318,11 +334,20 @@ __device__ void solve_one_tiny(const G& g, const SolveArgs& a, int64_t sys, unsi
     if (g.local_leader()) sample_layers(a, sample, gs.eta, gs.kc);
     g.sync();
   }
+  // horizontal interfaces: the layer depends on the row only (the same
+  // centre comparison as the generic per-cell one, evaluated once per lane)
+  int row_layer = -1;
+  if (a.ksrc != KSRC_ARRAY && a.geometry != 1) {
+    const bool own = coarse && !a.cgv_on_k;
+    const double yc = own ? ((double)ln.j + 0.5) * (1.0 / (double)m)
+                          : ((double)(coarse ? 2 * ln.j + oy : ln.j) + 0.5) * (1.0 / (double)a.m);
+    row_layer = layer_at(gs.eta, a.n_layers - 1, yc);
+  }
   TinyVec<float> k;
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
-    k.r[t] = (float)tiny_k_of_cell(a, gs, sys, sidx, coarse, ox, oy, ln.i_red(t), ln.j);
-    k.b[t] = (float)tiny_k_of_cell(a, gs, sys, sidx, coarse, ox, oy, ln.i_black(t), ln.j);
+    k.r[t] = (float)tiny_k_of_cell(a, gs, sys, sidx, coarse, ox, oy, ln.i_red(t), ln.j, row_layer);
+    k.b[t] = (float)tiny_k_of_cell(a, gs, sys, sidx, coarse, ox, oy, ln.i_black(t), ln.j, row_layer);
   }
   // ---- faces (Eq. 3.3: harmonic inside, 2k on Dirichlet faces, 0 on no-flow faces) ----
   TinyOp Ar, Ab;
@@ -378,28 +403,43 @@ __device__ void solve_one_tiny(const G& g, const SolveArgs& a, int64_t sys, unsi
   }
   build_coarse_inverse(g, gs.lev[nl - 1]);
   // ---- FP64 refinement around FP32 PCG (restarted, or reliable updates) ----
-  double xr64[4], xb64[4], rr64[4], rb64[4];
+  const TinyVec64 X64{reinterpret_cast<double*>(base + tiny_lev_bytes()), ln.lane};
+  const TinyVec64 R64{X64.p + 8 * 32, ln.lane};
   double bb = 0.0;
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
-    xr64[t] = xb64[t] = 0.0;
-    rr64[t] = tiny_rhs(a, Ar.w[t], ln.i_red(t));
-    rb64[t] = tiny_rhs(a, Ab.w[t], ln.i_black(t));
-    bb += rr64[t] * rr64[t];
+    const double br = tiny_rhs(a, Ar.w[t], ln.i_red(t)), bk = tiny_rhs(a, Ab.w[t], ln.i_black(t));
+    X64.r(t) = X64.b(t) = 0.0;
+    R64.r(t) = br;
+    R64.b(t) = bk;
+    bb += br * br;
   }
 #pragma unroll
-  for (int t = 0; t < 4; ++t) bb += rb64[t] * rb64[t];
+  for (int t = 0; t < 4; ++t) bb += R64.b(t) * R64.b(t);
   bb = warp_sum(bb);
   double rr = bb;
   const double thr = a.tol * a.tol * bb;
   auto residual64 = [&]() -> double {
-    double s2 = tiny_residual64_colour(a, Ar, xr64, xb64, ln, true, rr64);
-    s2 += tiny_residual64_colour(a, Ab, xb64, xr64, ln, false, rb64);
+    double xr[4], xk[4], rv[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      xr[t] = X64.r(t);
+      xk[t] = X64.b(t);
+    }
+    double s2 = tiny_residual64_colour(a, Ar, xr, xk, ln, true, rv);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) R64.r(t) = rv[t];
+    s2 += tiny_residual64_colour(a, Ab, xk, xr, ln, false, rv);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) R64.b(t) = rv[t];
     return warp_sum(s2);
   };
   const int gamma = a.mg_gamma, nu = a.mg_nu < 1 ? 1 : a.mg_nu, nuc = a.mg_nu_coarse;
   TinyVec<float> x, r, p, q, z;
   int status = 1, iters = 0, sweeps = 0;
+  // Each scheme calls the preconditioner from one place (at the top of its
+  // iteration), which keeps the unrolled code small; the operations and their
+  // order are the generic solver's.
   if (a.reliable) {
     // one FP32 CG on the correction with reliable updates (see the generic solver)
     if (rr <= thr) status = 0;
@@ -407,8 +447,8 @@ __device__ void solve_one_tiny(const G& g, const SolveArgs& a, int64_t sys, unsi
     float rr32 = 0.f;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      r.r[t] = (float)(rr64[t] / scl);
-      r.b[t] = (float)(rb64[t] / scl);
+      r.r[t] = (float)(R64.r(t) / scl);
+      r.b[t] = (float)(R64.b(t) / scl);
       x.r[t] = x.b[t] = 0.f;
       rr32 += r.r[t] * r.r[t] + r.b[t] * r.b[t];
     }
@@ -416,21 +456,25 @@ __device__ void solve_one_tiny(const G& g, const SolveArgs& a, int64_t sys, unsi
     float rr_ref = rr32;
     const float d2 = (float)(a.inner_tol * a.inner_tol);
     float rz = 0.f;
-    if (status != 0) {
-      tiny_precond(g, Ar, Ab, ln, lev, nl, gamma, nu, nuc, r, z);
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        p.r[t] = z.r[t];
-        p.b[t] = z.b[t];
-        rz += r.r[t] * z.r[t] + r.b[t] * z.b[t];
-      }
-      rz = warp_sum(rz);
-    }
+    bool first = true;
     int since = 0;
     while (status != 0 && iters < a.max_it) {
+      tiny_precond(g, Ar, Ab, ln, lev, nl, gamma, nu, nuc, r, z);
+      float rzn = 0.f;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) rzn += r.r[t] * z.r[t] + r.b[t] * z.b[t];
+      rzn = warp_sum(rzn);
+      const float beta = first ? 0.f : rzn / rz;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        p.r[t] = first ? z.r[t] : z.r[t] + beta * p.r[t];
+        p.b[t] = first ? z.b[t] : z.b[t] + beta * p.b[t];
+      }
+      rz = rzn;
+      first = false;
       ++iters;
       ++since;
-      float pq = warp_sum(tiny_matvec(Ar, Ab, ln, p, q));
+      const float pq = warp_sum(tiny_matvec(Ar, Ab, ln, p, q));
       if (!(pq > 0.f) || !isfinite(pq) || !isfinite(rz)) {
         status = 2;
         break;
@@ -449,8 +493,8 @@ __device__ void solve_one_tiny(const G& g, const SolveArgs& a, int64_t sys, unsi
       if ((double)rr32 * scl * scl <= thr || rr32 <= d2 * rr_ref || since >= 16) {  // reliable update
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-          xr64[t] += scl * (double)x.r[t];
-          xb64[t] += scl * (double)x.b[t];
+          X64.r(t) += scl * (double)x.r[t];
+          X64.b(t) += scl * (double)x.b[t];
         }
         rr = residual64();
         ++sweeps;
@@ -463,8 +507,8 @@ __device__ void solve_one_tiny(const G& g, const SolveArgs& a, int64_t sys, unsi
         rr32 = 0.f;
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-          r.r[t] = (float)(rr64[t] / scl_new);
-          r.b[t] = (float)(rb64[t] / scl_new);
+          r.r[t] = (float)(R64.r(t) / scl_new);
+          r.b[t] = (float)(R64.b(t) / scl_new);
           x.r[t] = x.b[t] = 0.f;
           p.r[t] *= ratio;
           p.b[t] *= ratio;
@@ -476,64 +520,68 @@ __device__ void solve_one_tiny(const G& g, const SolveArgs& a, int64_t sys, unsi
         rr_ref = rr32;
         since = 0;
       }
-      tiny_precond(g, Ar, Ab, ln, lev, nl, gamma, nu, nuc, r, z);
-      float rzn = 0.f;
-#pragma unroll
-      for (int t = 0; t < 4; ++t) rzn += r.r[t] * z.r[t] + r.b[t] * z.b[t];
-      rzn = warp_sum(rzn);
-      const float beta = rzn / rz;
-      rz = rzn;
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        p.r[t] = z.r[t] + beta * p.r[t];
-        p.b[t] = z.b[t] + beta * p.b[t];
-      }
     }
   } else {
+    // restarted refinement: FP32 PCG solves to ||r|| <= inner_tol ||r0|| on the
+    // scaled residual, each followed by x64 += scl x32 and the FP64 residual
+    float thr_in = 0.f, rz = 0.f;
+    double scl = 0.0;
+    int it = 0;         // iterations of the current inner solve
+    bool fresh = true;  // the next pass starts a refinement sweep
+    bool small0 = false;  // the scaled residual already meets the inner tolerance
     while (true) {
-      if (rr <= thr) {
-        status = 0;
-        break;
-      }
-      if (iters >= a.max_it || sweeps >= 40) {
-        status = 1;
-        break;
-      }
-      ++sweeps;
-      const double inv = 1.0 / sqrt(rr);
-      const double scl = sqrt(rr);
-      float r32 = 0.f;
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        r.r[t] = (float)(rr64[t] * inv);
-        r.b[t] = (float)(rb64[t] * inv);
-        r32 += r.r[t] * r.r[t] + r.b[t] * r.b[t];
-      }
-      r32 = warp_sum(r32);
-      // inner FP32 PCG from x = 0 to ||r|| <= inner_tol ||r0||
-      const float thr_in = (float)(a.inner_tol * a.inner_tol) * r32;
-      int it = 0, st_in = 1;
-#pragma unroll
-      for (int t = 0; t < 4; ++t) x.r[t] = x.b[t] = 0.f;
-      if (r32 <= thr_in) {
-        st_in = 0;
-      } else {
-        tiny_precond(g, Ar, Ab, ln, lev, nl, gamma, nu, nuc, r, z);
-        float rz = 0.f;
+      if (fresh) {
+        if (rr <= thr) {
+          status = 0;
+          break;
+        }
+        if (iters >= a.max_it || sweeps >= 40) {
+          status = 1;
+          break;
+        }
+        ++sweeps;
+        scl = sqrt(rr);
+        const double inv = 1.0 / scl;
+        float r32 = 0.f;
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-          p.r[t] = z.r[t];
-          p.b[t] = z.b[t];
-          rz += r.r[t] * z.r[t] + r.b[t] * z.b[t];
+          r.r[t] = (float)(R64.r(t) * inv);
+          r.b[t] = (float)(R64.b(t) * inv);
+          x.r[t] = x.b[t] = 0.f;
+          r32 += r.r[t] * r.r[t] + r.b[t] * r.b[t];
         }
-        rz = warp_sum(rz);
-        while (it < a.max_it - iters) {
-          ++it;
-          const float pq = warp_sum(tiny_matvec(Ar, Ab, ln, p, q));
-          if (!(pq > 0.f) || !isfinite(pq) || !isfinite(rz)) {
-            st_in = 2;
-            break;
-          }
+        r32 = warp_sum(r32);
+        thr_in = (float)(a.inner_tol * a.inner_tol) * r32;
+        small0 = r32 <= thr_in;
+        it = 0;
+        fresh = false;
+      }
+      int st_in = 1;  // 0 converged, 1 running / cap, 2 breakdown
+      bool end_inner = false;
+      if (it == 0 && small0) {
+        st_in = 0;
+        end_inner = true;
+      } else if (it >= a.max_it - iters) {
+        end_inner = true;  // cap (the generic pcg's loop condition)
+      } else {
+        tiny_precond(g, Ar, Ab, ln, lev, nl, gamma, nu, nuc, r, z);
+        float rzn = 0.f;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) rzn += r.r[t] * z.r[t] + r.b[t] * z.b[t];
+        rzn = warp_sum(rzn);
+        const float beta = it == 0 ? 0.f : rzn / rz;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          p.r[t] = it == 0 ? z.r[t] : z.r[t] + beta * p.r[t];
+          p.b[t] = it == 0 ? z.b[t] : z.b[t] + beta * p.b[t];
+        }
+        rz = rzn;
+        ++it;
+        const float pq = warp_sum(tiny_matvec(Ar, Ab, ln, p, q));
+        if (!(pq > 0.f) || !isfinite(pq) || !isfinite(rz)) {
+          st_in = 2;
+          end_inner = true;
+        } else {
           const float alpha = rz / pq;
           float rrs = 0.f;
 #pragma unroll
@@ -547,33 +595,24 @@ __device__ void solve_one_tiny(const G& g, const SolveArgs& a, int64_t sys, unsi
           rrs = warp_sum(rrs);
           if (rrs <= thr_in) {
             st_in = 0;
-            break;
-          }
-          tiny_precond(g, Ar, Ab, ln, lev, nl, gamma, nu, nuc, r, z);
-          float rzn = 0.f;
-#pragma unroll
-          for (int t = 0; t < 4; ++t) rzn += r.r[t] * z.r[t] + r.b[t] * z.b[t];
-          rzn = warp_sum(rzn);
-          const float beta = rzn / rz;
-          rz = rzn;
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            p.r[t] = z.r[t] + beta * p.r[t];
-            p.b[t] = z.b[t] + beta * p.b[t];
+            end_inner = true;
           }
         }
       }
+      if (!end_inner) continue;
+      // a breakdown counts its iteration only up to the failed step, as in pcg
       iters += it;
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        xr64[t] += scl * (double)x.r[t];
-        xb64[t] += scl * (double)x.b[t];
+        X64.r(t) += scl * (double)x.r[t];
+        X64.b(t) += scl * (double)x.b[t];
       }
       rr = residual64();
       if (it == 0 && st_in != 0) {  // inner solver made no progress
         status = 2;
         break;
       }
+      fresh = true;
     }
   }
   // ---- QoI and outputs ----
@@ -584,14 +623,14 @@ __device__ void solve_one_tiny(const G& g, const SolveArgs& a, int64_t sys, unsi
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int i = t < 4 ? ln.i_red(t) : ln.i_black(t - 4);
-      const double xv = t < 4 ? xr64[t] : xb64[t - 4];
+      const double xv = t < 4 ? X64.r(t) : X64.b(t - 4);
       const double bx = fmin((i + 1) * hh, a.box[1]) - fmax(i * hh, a.box[0]);
       const double by = fmin((ln.j + 1) * hh, a.box[3]) - fmax(ln.j * hh, a.box[2]);
       if (bx > 0.0 && by > 0.0) qsum += bx * by * inv_area * xv;
     }
   } else if (ln.h == 1) {
     // outflow through x1 = 1: column 15 is red slot 3 in odd rows, black slot 3 in even rows
-    qsum = ln.jp ? (double)Ar.e[3] * xr64[3] : (double)Ab.e[3] * xb64[3];
+    qsum = ln.jp ? (double)Ar.e[3] * X64.r(3) : (double)Ab.e[3] * X64.b(3);
   }
   qsum = warp_sum(qsum);
   if (ln.lane == 0) {
@@ -601,8 +640,8 @@ __device__ void solve_one_tiny(const G& g, const SolveArgs& a, int64_t sys, unsi
   if (a.p_out && !coarse) {
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      a.p_out[sidx * (int64_t)n + ln.j * m + ln.i_red(t)] = xr64[t];
-      a.p_out[sidx * (int64_t)n + ln.j * m + ln.i_black(t)] = xb64[t];
+      a.p_out[sidx * (int64_t)n + ln.j * m + ln.i_red(t)] = X64.r(t);
+      a.p_out[sidx * (int64_t)n + ln.j * m + ln.i_black(t)] = X64.b(t);
     }
   }
   g.sync();
