@@ -252,15 +252,20 @@ def profiled_pass(ctx, d, est, seed, tune):
         p = ctx.profile_read()
         ctx.profile(False)
         t = tune[lvl]
+        tc = t.get("coarse")
+        plan = lambda x: {"threads": x["threads"], "warp": x["warp"], "cluster": x["cluster"], "nu": x["nu"],
+                          "nu_coarse": x["nu_coarse"], "gamma": x["gamma"], "reliable": x["reliable"],
+                          "inner_tol": x["inner_tol"], "cap_blocks_per_sm": x["cap_blocks_per_sm"]}
         per.append({"level": lvl, "m": d["m0"] << lvl, "N": n, "fields_ms": p["ms"]["fields"],
-                    "solve_ms": p["ms"]["solve"], "reduce_ms": p["ms"]["reduce"],
+                    "solve_ms": p["ms"]["solve"] + p["ms"]["solve_coarse"], "reduce_ms": p["ms"]["reduce"],
+                    "solve_fine_ms": p["ms"]["solve"], "solve_coarse_ms": p["ms"]["solve_coarse"],
                     "iters_per_sample": s["iters_total"] / max(s["n"], 1),
                     "cell_iters": p["cell_iters"], "solve_bytes": p["solve_bytes"],
                     "solve_flops": p["solve_flops"], "fft_flops": p["fft_flops"], "fft_bytes": p["fft_bytes"],
-                    "solve_kernel": solve_kernel_name(d["prec"], t), "smem": t["smem"],
-                    "plan": {"threads": t["threads"], "warp": t["warp"], "cluster": t["cluster"], "nu": t["nu"],
-                             "nu_coarse": t["nu_coarse"], "gamma": t["gamma"], "reliable": t["reliable"],
-                             "inner_tol": t["inner_tol"], "cap_blocks_per_sm": t["cap_blocks_per_sm"]}})
+                    "solve_bytes_c": p["solve_bytes_c"], "solve_flops_c": p["solve_flops_c"],
+                    "solve_kernel": solve_kernel_name(d["prec"], t), "smem": t["smem"], "plan": plan(t),
+                    "coarse_kernel": solve_kernel_name(d["prec"], tc) if tc else None,
+                    "coarse_smem": tc["smem"] if tc else None, "coarse_plan": plan(tc) if tc else None})
     return tot, per
 
 
@@ -273,12 +278,26 @@ def roofline(d, per, peaks):
     of their precision with the algorithmic flops."""
     by = collections.OrderedDict()
     for r in per:
-        k = by.setdefault(r["solve_kernel"], {"ms": 0.0, "bytes": 0.0, "flops": 0.0, "levels": [], "stream": 0})
-        k["ms"] += r["solve_ms"]
-        k["bytes"] += r["solve_bytes"]
-        k["flops"] += r["solve_flops"]
-        k["levels"].append(r["m"])
-        k["stream"] += 0 if r["smem"] else r["solve_ms"]
+        # the fine systems' launch (all systems when the coarse ones share it) and the
+        # coarse systems' own launch, each under the kernel of its plan
+        split = r["coarse_kernel"] is not None and r["solve_coarse_ms"] > 0
+        parts = [(r["solve_kernel"], r["solve_fine_ms"],
+                  r["solve_bytes"] - (r["solve_bytes_c"] if split else 0.0),
+                  r["solve_flops"] - (r["solve_flops_c"] if split else 0.0), r["smem"], r["m"])]
+        if split:
+            parts.append((r["coarse_kernel"], r["solve_coarse_ms"], r["solve_bytes_c"], r["solve_flops_c"],
+                          r["coarse_smem"], r["m"] // 2))
+        for name_, ms, byt, fl, smem, msz in parts:
+            k = by.setdefault(name_, {"ms": 0.0, "bytes": 0.0, "flops": 0.0, "levels": [], "stream": 0,
+                                      "sbytes": 0.0, "sms": 0.0})
+            k["ms"] += ms
+            k["bytes"] += byt
+            k["flops"] += fl
+            k["levels"].append(msz)
+            if not smem:  # streamed launches: their bytes and time alone make the HBM figure
+                k["stream"] += ms
+                k["sbytes"] += byt
+                k["sms"] += ms
         f = by.setdefault("ce_rows+ce_cols", {"ms": 0.0, "bytes": 0.0, "flops": 0.0, "levels": [], "stream": 0})
         f["ms"] += r["fields_ms"]
         f["bytes"] += r["fft_bytes"]
@@ -290,8 +309,8 @@ def roofline(d, per, peaks):
     f32 = d["prec"] in (1, 2)
     shares = {n: round(v["ms"] / total, 4) for n, v in by.items()}
     if name.startswith("solve") and k["stream"] >= 0.5 * k["ms"]:
-        ach = k["bytes"] / (k["ms"] / 1e3) / 1e9
-        out = {"kernel": name, "levels_m": k["levels"], "bound": "hbm", "achieved": ach, "peak": peaks["hbm"],
+        ach = k["sbytes"] / (k["sms"] / 1e3) / 1e9
+        out = {"kernel": name, "systems_m": k["levels"], "bound": "hbm", "achieved": ach, "peak": peaks["hbm"],
                "unit": "GB/s", "frac": ach / peaks["hbm"], "traffic": None, "peak_source": peaks["hbm_src"],
                "note": "algorithmic bytes = cells x CG iterations x bytes per cell-iteration of the streaming "
                        "model (every pass reads its operands and writes its results once); traffic null: no "
@@ -303,7 +322,7 @@ def roofline(d, per, peaks):
         pk_t = peaks["fp32"] if use32 else peaks["fp64"]
         src = "measured by mlmc_fma_peak (independent FMA chains, %s) on this GPU" % ("FP32" if use32 else "FP64")
         ach = k["flops"] / (k["ms"] / 1e3) / 1e12
-        out = {"kernel": name, "levels_m": k["levels"], "bound": "alu", "achieved": ach, "peak": pk_t,
+        out = {"kernel": name, "systems_m": k["levels"], "bound": "alu", "achieved": ach, "peak": pk_t,
                "unit": "TFLOP/s", "frac": ach / pk_t, "traffic": None, "peak_source": src}
     out["time_share"] = shares
     return out
@@ -396,7 +415,9 @@ def run_reference(args, d):
 # program that exits 0 on its own (run it once without ncu first).  Launch
 # plans are fixed by hand to those the autotuner picks in the benchmark;
 # entries: (workload, overrides, [(level, samples, (mode, threads, cluster,
-# gamma, nu), solver)]) with solver None or (reliable, inner_tol).
+# gamma, nu), solver[, coarse launch])]) with solver None or (reliable,
+# inner_tol) and the optional coarse launch (mode, threads, cluster, gamma, nu)
+# giving the coarse systems a launch of their own.
 PROFILE_CASES = {
     "fp64_levels": ("lognormal_2layer_16to256", {},
                     [(0, 65535, (1, 0, 0, 1, 2), None), (3, 1024, (0, 512, 0, 1, 2), None)]),
@@ -407,6 +428,12 @@ PROFILE_CASES = {
                     [(0, 65535, (3, 0, 0, 1, 1), None), (1, 16384, (0, 128, 0, 1, 1), None)]),
     "mixed_small_generic": ("lognormal_2layer_cgv_16to512", {}, [(0, 65535, (1, 0, 0, 1, 1), None)]),
     "mixed_m256": ("lognormal_2layer_cgv_16to512", {}, [(4, 256, (0, 512, 0, 1, 2), (1, 1e-3))]),
+    # the headline's level 4 as the autotuner runs it: the 256 x 256 systems in
+    # one launch (blocks of 512, reliable updates), the 128 x 128 CGV coarse
+    # systems in a launch of their own; the first solve launch is the fine one
+    "mixed_m256_split": ("lognormal_2layer_cgv_16to512", {},
+                         [(4, 256, (0, 512, 0, 1, 2), (1, 1e-3), (0, 512, 0, 1, 2))]),
+    "fields_m16": ("lognormal_2layer_cgv_16to512", {}, [(0, 65536, None, None)]),
     "mixed_m512": ("lognormal_2layer_cgv_16to512", {}, [(5, 128, (2, 512, 4, 1, 2), None)]),
     "mixed_1024": ("lognormal_2layer_cgv_32to2048", {}, [(5, 32, (2, 512, 8, 1, 2), None)]),
     "fp64_m256": ("lognormal_2layer_16to256", {}, [(4, 512, (0, 512, 0, 1, 2), None)]),
@@ -422,9 +449,11 @@ def run_profile_case(case):
     import workloads
     name, over, levels = PROFILE_CASES[case]
     with pk.Context(workloads.workload(name, **over)) as ctx:
-        for level, n, launch, solver in levels:
+        for level, n, launch, solver, *coarse in levels:
             if launch is not None:
                 ctx.set_launch(level, *launch)
+            if coarse:
+                ctx.set_launch_coarse(level, *coarse[0])
             if solver is not None:
                 ctx.set_solver(level, *solver)
             if launch is None:  # the field passes alone
@@ -432,9 +461,13 @@ def run_profile_case(case):
                 torch.cuda.synchronize()
                 print(case, "level", level, "fields of", n, "samples", tuple(g.shape), flush=True)
                 continue
+            ctx.profile(True)
             s = ctx.level_batch(level, n, 0)
+            p = ctx.profile_read()
+            ctx.profile(False)
             torch.cuda.synchronize()
             print(case, "level", level, "m", ctx.m(level), "samples", s["n"], "iterations", s["iters_total"],
+                  "cell_iterations %.6g" % p["cell_iters"], "algorithmic_solve_bytes %.6g" % p["solve_bytes"],
                   flush=True)
 
 
@@ -681,7 +714,8 @@ def main():
         "alpha": est["alpha"], "bias_estimate": est["bias"], "bias_flag": est["bias_flag"],
         "stage_ms_per_step_serial": tot["ms"],
         "per_level": [dict({k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()
-                            if k not in ("cell_iters", "solve_flops", "fft_flops", "fft_bytes", "solve_bytes")},
+                            if k not in ("cell_iters", "solve_flops", "fft_flops", "fft_bytes", "solve_bytes",
+                                         "solve_bytes_c", "solve_flops_c")},
                            solve_alg_gbs=round(r["solve_bytes"] / max(r["solve_ms"], 1e-9) / 1e6, 1),
                            solve_tflops=round(r["solve_flops"] / max(r["solve_ms"], 1e-9) / 1e9, 3),
                            fields_alg_gbs=round(r["fft_bytes"] / max(r["fields_ms"], 1e-9) / 1e6, 1))

@@ -273,9 +273,21 @@ typedef struct mlmc_tune_report {
   double ms_best[MLMC_MAX_LEVELS];             /* ms per sample, chosen plan */
   int32_t smem[MLMC_MAX_LEVELS];               /* 1: the chosen plan keeps a system's workspace in
                                                   shared memory (else global memory, streamed) */
+  /* levels >= 1: the plan of the coarse systems (side m/2), tuned on them alone
+     and run as a launch of its own after the fine systems' launch when the two
+     launches beat one launch of all systems (c_threads = 0: one launch); the
+     fields above are the fine systems' plan */
+  int32_t c_threads[MLMC_MAX_LEVELS], c_warp[MLMC_MAX_LEVELS], c_cluster[MLMC_MAX_LEVELS];
+  int32_t c_cap_blocks_per_sm[MLMC_MAX_LEVELS], c_gamma[MLMC_MAX_LEVELS], c_nu[MLMC_MAX_LEVELS];
+  int32_t c_nu_coarse[MLMC_MAX_LEVELS];
+  double c_inner_tol[MLMC_MAX_LEVELS];
+  int32_t c_reliable[MLMC_MAX_LEVELS], c_smem[MLMC_MAX_LEVELS];
 } mlmc_tune_report;
 
-/* Times the candidate launch plans of the solver (one warp, one block of
+/* Times the candidate launch plans of the solver, for each level separately
+ * for its fine systems and (levels >= 1) its coarse systems, which then run as
+ * two launches with their own plans if that beats one launch of all systems
+ * on the fine plan (candidates: one warp, one block of
  * 64/128/256/512 threads, or, for m >= 128, one thread-block cluster of 2, 4
  * or 8 blocks per system; all resident blocks or one per SM; for the
  * fastest of those, W-cycles, two smoothing sweep pairs on every grid, two
@@ -290,7 +302,7 @@ typedef struct mlmc_tune_report {
 MLMC_API int mlmc_autotune(mlmc_ctx* ctx, uint64_t seed, mlmc_tune_report* rep);
 
 /* Fix the solver's launch plan of one level by hand (overrides
- * mlmc_autotune): mode 0 = one block of `threads` (32..512, multiple of 32)
+ * mlmc_autotune; all the level's systems in one launch): mode 0 = one block of `threads` (32..512, multiple of 32)
  * per system, 1 = one warp per system, 2 = one thread-block cluster of
  * `cluster` (2, 4, 8) blocks of 512 threads per system, 3 = one warp per
  * system with the finest grid in registers (m = 16, prec 1, 2-D; the
@@ -300,6 +312,15 @@ MLMC_API int mlmc_autotune(mlmc_ctx* ctx, uint64_t seed, mlmc_tune_report* rep);
  * (V-cycle, nu = 1).  Errors: MLMC_ERR_ARG. */
 MLMC_API int mlmc_set_launch(mlmc_ctx* ctx, int level, int32_t mode, int32_t threads, int32_t cluster,
                              int32_t gamma, int32_t nu);
+
+/* Fix the launch plan of the coarse systems (side m/2) of level `level` >= 1
+ * by hand: they then run as a launch of their own after the fine systems'
+ * (whose plan mlmc_set_launch() or the default sets); arguments as in
+ * mlmc_set_launch(), for the coarse size (mode 3 needs m/2 = 16, prec 1);
+ * mode < 0 returns to one launch for all the level's systems.
+ * Errors: MLMC_ERR_ARG. */
+MLMC_API int mlmc_set_launch_coarse(mlmc_ctx* ctx, int level, int32_t mode, int32_t threads, int32_t cluster,
+                                    int32_t gamma, int32_t nu);
 
 /* Mixed precision (prec 1, 2) of one level's solver, on top of its launch
  * plan (the autotuned or set one, else the default): reliable = 0 runs FP32
@@ -391,9 +412,11 @@ MLMC_API int mlmc_solve_k_static(int device, int32_t m, int64_t n, const double*
 /* Per-stage device timing of a context, collected with CUDA events on the
  * context's stream while enabled (used by the benchmark for the roofline). */
 typedef struct mlmc_profile_stats {
-  int64_t launches[3];     /* kernel launches: 0 field kernels (both FFT passes),
-                              1 fused assembly + solve + QoI, 2 gather + level reduction */
-  double ms[3];            /* summed event time of each stage */
+  int64_t launches[4];     /* kernel launches: 0 field kernels (both FFT passes),
+                              1 fused assembly + solve + QoI (all systems, or the fine ones when
+                              the coarse systems have a plan of their own), 2 gather + level
+                              reduction, 3 the coarse systems' solve launches */
+  double ms[4];            /* summed event time of each stage */
   double cell_iters;       /* sum over all solves of (cells x CG iterations) */
   double cells;            /* sum over all solves of cells */
   double fft_row_points;   /* sum of M*M complex points transformed by the row pass */
@@ -411,6 +434,9 @@ typedef struct mlmc_profile_stats {
                               no reuse between passes) */
   double fft_bytes;        /* algorithmic bytes of the field passes: every complex intermediate
                               written once and read once, the fields written once */
+  double cell_iters_c;     /* the part of cell_iters, solve_flops, solve_bytes due to the */
+  double solve_flops_c;    /* coarse systems (stage 3 when they run as a launch of their own) */
+  double solve_bytes_c;
 } mlmc_profile_stats;
 
 /* enable != 0: reset the counters and start collecting; 0: stop. */

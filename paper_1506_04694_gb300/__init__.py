@@ -58,14 +58,16 @@ class EstimateOut(ctypes.Structure):
 
 
 class ProfileStats(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64 * 3), ("ms", ctypes.c_double * 3),
+    _fields_ = [("launches", ctypes.c_int64 * 4), ("ms", ctypes.c_double * 4),
                 ("cell_iters", ctypes.c_double), ("cells", ctypes.c_double),
                 ("fft_row_points", ctypes.c_double), ("fft_col_points", ctypes.c_double),
                 ("samples", ctypes.c_double), ("solve_flops", ctypes.c_double), ("fft_flops", ctypes.c_double),
-                ("solve_bytes", ctypes.c_double), ("fft_bytes", ctypes.c_double)]
+                ("solve_bytes", ctypes.c_double), ("fft_bytes", ctypes.c_double),
+                ("cell_iters_c", ctypes.c_double), ("solve_flops_c", ctypes.c_double),
+                ("solve_bytes_c", ctypes.c_double)]
 
 
-STAGES = ("fields", "solve", "reduce")
+STAGES = ("fields", "solve", "reduce", "solve_coarse")
 
 
 class TuneReport(ctypes.Structure):
@@ -76,7 +78,12 @@ class TuneReport(ctypes.Structure):
                 ("inner_tol", ctypes.c_double * MAX_LEVELS), ("reliable", ctypes.c_int32 * MAX_LEVELS),
                 ("candidates", ctypes.c_int32 * MAX_LEVELS),
                 ("ms_default", ctypes.c_double * MAX_LEVELS), ("ms_best", ctypes.c_double * MAX_LEVELS),
-                ("smem", ctypes.c_int32 * MAX_LEVELS)]
+                ("smem", ctypes.c_int32 * MAX_LEVELS),
+                ("c_threads", ctypes.c_int32 * MAX_LEVELS), ("c_warp", ctypes.c_int32 * MAX_LEVELS),
+                ("c_cluster", ctypes.c_int32 * MAX_LEVELS), ("c_cap_blocks_per_sm", ctypes.c_int32 * MAX_LEVELS),
+                ("c_gamma", ctypes.c_int32 * MAX_LEVELS), ("c_nu", ctypes.c_int32 * MAX_LEVELS),
+                ("c_nu_coarse", ctypes.c_int32 * MAX_LEVELS), ("c_inner_tol", ctypes.c_double * MAX_LEVELS),
+                ("c_reliable", ctypes.c_int32 * MAX_LEVELS), ("c_smem", ctypes.c_int32 * MAX_LEVELS)]
 
 
 class MLMCError(RuntimeError):
@@ -107,6 +114,8 @@ EXPORTS = {
     "mlmc_checkpoint_check": (ctypes.c_int, [ctypes.POINTER(Model), ctypes.c_char_p]),
     "mlmc_set_launch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "mlmc_set_launch_coarse": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "mlmc_set_solver": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_double]),
     "mlmc_ce_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
@@ -299,7 +308,12 @@ class Context:
                  "cluster": r.cluster[i], "gamma": r.gamma[i], "nu": r.nu[i], "nu_coarse": r.nu_coarse[i],
                  "inner_tol": r.inner_tol[i], "reliable": r.reliable[i],
                  "candidates": r.candidates[i], "ms_per_sample_default": r.ms_default[i],
-                 "ms_per_sample_best": r.ms_best[i], "smem": r.smem[i]} for i in range(L)]
+                 "ms_per_sample_best": r.ms_best[i], "smem": r.smem[i],
+                 "coarse": None if i == 0 or r.c_threads[i] == 0 else {
+                     "threads": r.c_threads[i], "warp": r.c_warp[i], "cluster": r.c_cluster[i],
+                     "cap_blocks_per_sm": r.c_cap_blocks_per_sm[i], "gamma": r.c_gamma[i], "nu": r.c_nu[i],
+                     "nu_coarse": r.c_nu_coarse[i], "inner_tol": r.c_inner_tol[i], "reliable": r.c_reliable[i],
+                     "smem": r.c_smem[i]}} for i in range(L)]
 
     def profile(self, enable=True):
         """mlmc_profile: reset and start (or stop) per-stage event timing."""
@@ -312,12 +326,18 @@ class Context:
         return {"launches": dict(zip(STAGES, p.launches)), "ms": dict(zip(STAGES, p.ms)),
                 "cell_iters": p.cell_iters, "cells": p.cells, "fft_row_points": p.fft_row_points,
                 "fft_col_points": p.fft_col_points, "samples": p.samples, "solve_flops": p.solve_flops,
-                "fft_flops": p.fft_flops, "solve_bytes": p.solve_bytes, "fft_bytes": p.fft_bytes}
+                "fft_flops": p.fft_flops, "solve_bytes": p.solve_bytes, "fft_bytes": p.fft_bytes,
+                "cell_iters_c": p.cell_iters_c, "solve_flops_c": p.solve_flops_c, "solve_bytes_c": p.solve_bytes_c}
 
     def set_launch(self, level, mode, threads=256, cluster=0, gamma=1, nu=1):
         """mlmc_set_launch: fix a level's solver launch (0 block, 1 warp, 2 cluster; <0 default),
         its multigrid cycle (gamma 1 V, 2 W) and smoothing sweep pairs nu."""
         _check(lib().mlmc_set_launch(self._h, level, mode, threads, cluster, gamma, nu), allow_failed=False)
+
+    def set_launch_coarse(self, level, mode, threads=256, cluster=0, gamma=1, nu=1):
+        """mlmc_set_launch_coarse: a launch plan of its own for the coarse systems of a level >= 1
+        (mode < 0: one launch for all the level's systems again)."""
+        _check(lib().mlmc_set_launch_coarse(self._h, level, mode, threads, cluster, gamma, nu), allow_failed=False)
 
     def set_solver(self, level, reliable, inner_tol):
         """mlmc_set_solver: mixed-precision scheme of a level (reliable updates or restarted

@@ -108,7 +108,7 @@ struct StagePend {
 // Device results of one enqueued level range, copied to pinned host memory.
 struct HostLevel {
   LevelSumsDev s;
-  int64_t itc[2];
+  int64_t itc[3];  // iterations; cells x iterations of the fine and of the coarse systems
 };
 
 struct mlmc_ctx {
@@ -141,9 +141,13 @@ struct mlmc_ctx {
     WorkBufs wb;
   } slot[MLMC_MAX_LEVELS];
   HostLevel* host = nullptr;  // pinned, MLMC_MAX_LEVELS + 1 entries (last: single-level calls)
-  // launch plans chosen by mlmc_autotune(), per level
+  // launch plans chosen by mlmc_autotune() or set by hand, per level: for the
+  // fine systems (or all of them), and for the coarse systems in a launch of
+  // their own
   SolvePlan tuned[MLMC_MAX_LEVELS];
   bool tuned_ok[MLMC_MAX_LEVELS] = {};
+  SolvePlan tuned_c[MLMC_MAX_LEVELS];
+  bool tuned_c_ok[MLMC_MAX_LEVELS] = {};
   // estimator state: of the last estimate (for mlmc_checkpoint) and a loaded
   // one that the next estimate continues from (mlmc_resume)
   struct EstState {
@@ -363,9 +367,26 @@ int64_t chunk_samples(const mlmc_ctx* c, int level) {
 // resident blocks for very large grids).
 constexpr size_t kWsBudget = size_t(16) << 30;
 
-// Solve the systems of one chunk; results into the selected work buffers (qsys, itsys).
+// Workspace bytes and blocks of one solver launch over n_sys systems.
+struct LaunchSize {
+  size_t ws;
+  int64_t blocks;
+};
+LaunchSize launch_size(const mlmc_ctx* c, const SolvePlan& P, int64_t n_sys) {
+  const int64_t cap = P.use_smem ? 0 : (int64_t)(kWsBudget / P.ws_stride);
+  int64_t nb = 0;
+  const int64_t groups = solve_groups(P, n_sys, c->nsm, cap, &nb);
+  const size_t ws = !P.use_smem ? P.ws_stride * groups : P.ws64_stride * groups;
+  return {ws, nb};
+}
+
+// Solve the systems of one chunk; results into the selected work buffers
+// (qsys, itsys).  With a plan for the coarse systems (plan_c) the fine and the
+// coarse systems run as two launches, each with its own plan, one after the
+// other on the stream (sharing the workspace); which = 1 / 2 queues only the
+// fine / only the coarse launch (autotuning).
 int run_solves(mlmc_ctx* c, SolveArgs a, int64_t n_samples, int nc, int64_t max_rows,
-               const SolvePlan* plan = nullptr) {
+               const SolvePlan* plan = nullptr, const SolvePlan* plan_c = nullptr, int which = 0) {
   const int prec = c->model.prec;
   a.n_samples = n_samples;
   a.n_coarse = nc;
@@ -373,23 +394,41 @@ int run_solves(mlmc_ctx* c, SolveArgs a, int64_t n_samples, int nc, int64_t max_
   if (plan) P = *plan;
   else if (plan_of(c->model, a.m, &P)) return fail(MLMC_ERR_CUDA, "occupancy query failed");
   const int64_t n_sys = n_samples * (1 + nc);
-  const int64_t cap = P.use_smem ? 0 : (int64_t)(kWsBudget / P.ws_stride);
-  int64_t nb = 0;
-  const int64_t groups = solve_groups(P, n_sys, c->nsm, cap, &nb);
-  WorkBufs& B = *c->wb;
-  if (!P.use_smem) {
-    if (int e = B.ws.ensure(P.ws_stride * groups)) return e;
-    a.ws = B.ws.as<unsigned char>();
-  } else if (P.ws64_stride) {
-    if (int e = B.ws.ensure(P.ws64_stride * groups)) return e;
-    a.ws64 = B.ws.as<unsigned char>();
+  const bool split = plan_c && nc > 0;
+  struct Part {
+    const SolvePlan* P;
+    int64_t b, e;
+  } parts[2];
+  int np = 0;
+  if (!split) {
+    parts[np++] = {&P, 0, n_sys};
+  } else {
+    if (which != 2) parts[np++] = {&P, 0, n_samples};
+    if (which != 1) parts[np++] = {plan_c, n_samples, n_sys};
   }
+  WorkBufs& B = *c->wb;
+  size_t ws = 0;
+  for (int k = 0; k < np; ++k) ws = std::max(ws, launch_size(c, *parts[k].P, parts[k].e - parts[k].b).ws);
+  if (ws)
+    if (int e = B.ws.ensure(ws)) return e;
   if (int e = B.qsys.ensure((size_t)std::max<int64_t>(n_sys, max_rows) * 8)) return e;
   if (int e = B.itsys.ensure((size_t)std::max<int64_t>(n_sys, max_rows) * 4)) return e;
   a.q = B.qsys.as<double>();
   a.iters = B.itsys.as<int32_t>();
-  const int lr = dim_of(c->model) == 3 ? solve3_launch(a, prec, P, (int)nb, c->wst) : solve_launch(a, prec, P, (int)nb, c->wst);
-  if (lr) return fail(MLMC_ERR_CUDA, std::string("solve kernel launch: ") + cudaGetErrorString(last_launch_error()));
+  for (int k = 0; k < np; ++k) {
+    const SolvePlan& Q = *parts[k].P;
+    SolveArgs b = a;
+    b.sys_begin = parts[k].b;
+    b.sys_end = parts[k].e;
+    b.ws = nullptr;
+    b.ws64 = nullptr;
+    if (!Q.use_smem) b.ws = B.ws.as<unsigned char>();
+    else if (Q.ws64_stride) b.ws64 = B.ws.as<unsigned char>();
+    const int64_t nb = launch_size(c, Q, parts[k].e - parts[k].b).blocks;
+    const int lr = dim_of(c->model) == 3 ? solve3_launch(b, prec, Q, (int)nb, c->wst)
+                                         : solve_launch(b, prec, Q, (int)nb, c->wst);
+    if (lr) return fail(MLMC_ERR_CUDA, std::string("solve kernel launch: ") + cudaGetErrorString(last_launch_error()));
+  }
   return 0;
 }
 
@@ -442,7 +481,8 @@ int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t see
   const int nc = n_coarse(md, level);
   const int64_t chunk = chunk_samples(c, level);
   const SolvePlan* plan = c->tuned_ok[level] ? &c->tuned[level] : nullptr;
-  CUDA_TRY(cudaMemsetAsync(itacc, 0, 2 * sizeof(int64_t), c->wst));
+  const SolvePlan* plan_c = c->tuned_c_ok[level] ? &c->tuned_c[level] : nullptr;
+  CUDA_TRY(cudaMemsetAsync(itacc, 0, 3 * sizeof(int64_t), c->wst));
   const int m = md.m0 << level;
   double sumM2 = 0, sumM = 0, fftf = 0, fftb = 0;  // transformed points, FFT flops and bytes per sample
   const bool d3 = dim_of(md) == 3;
@@ -471,7 +511,16 @@ int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t see
         c->prof.fft_bytes += (double)cn * fftb;
       }
     }
-    {
+    if (plan_c && nc > 0) {  // the fine and the coarse systems, each timed as a stage of its own
+      {
+        StageTimer t(c, 1);
+        if (int e = run_solves(c, a, cn, nc, 0, plan, plan_c, 1)) return e;
+        t.stop(1);
+      }
+      StageTimer t(c, 3);
+      if (int e = run_solves(c, a, cn, nc, 0, plan, plan_c, 2)) return e;
+      t.stop(1);
+    } else {
       StageTimer t(c, 1);
       if (int e = run_solves(c, a, cn, nc, 0, plan)) return e;
       t.stop(1);
@@ -549,13 +598,25 @@ double bytes_per_cell_iter(int prec, int dim, int gamma, int nu, int nuc) {
 int finish_level(mlmc_ctx* c, int level, const HostLevel& h, mlmc_level_sums* sums) {
   const mlmc_model& md = c->model;
   if (c->prof_on) {
-    c->prof.cell_iters += (double)h.itc[1];
+    c->prof.cell_iters += (double)(h.itc[1] + h.itc[2]);
     SolvePlan P;
     if (c->tuned_ok[level]) P = c->tuned[level];
     else if (plan_of(md, md.m0 << level, &P)) P.gamma = P.nu = 1;
-    c->prof.solve_flops += (double)h.itc[1] * (dim_of(md) == 3 ? flops_per_cell_iter3(P.gamma, P.nu, P.nu_coarse)
-                                                               : flops_per_cell_iter(md.prec, P.gamma, P.nu, P.nu_coarse));
-    c->prof.solve_bytes += (double)h.itc[1] * bytes_per_cell_iter(md.prec, dim_of(md), P.gamma, P.nu, P.nu_coarse);
+    const SolvePlan& Pc = c->tuned_c_ok[level] ? c->tuned_c[level] : P;  // the coarse systems' plan
+    for (int part = 0; part < 2; ++part) {
+      const SolvePlan& Q = part ? Pc : P;
+      const double ci = (double)h.itc[1 + part];
+      const double fl = ci * (dim_of(md) == 3 ? flops_per_cell_iter3(Q.gamma, Q.nu, Q.nu_coarse)
+                                              : flops_per_cell_iter(md.prec, Q.gamma, Q.nu, Q.nu_coarse));
+      const double by = ci * bytes_per_cell_iter(md.prec, dim_of(md), Q.gamma, Q.nu, Q.nu_coarse);
+      c->prof.solve_flops += fl;
+      c->prof.solve_bytes += by;
+      if (part == 1) {
+        c->prof.cell_iters_c += ci;
+        c->prof.solve_flops_c += fl;
+        c->prof.solve_bytes_c += by;
+      }
+    }
   }
   sums->n = h.s.n;
   sums->n_failed = h.s.n_failed;
@@ -568,7 +629,7 @@ int finish_level(mlmc_ctx* c, int level, const HostLevel& h, mlmc_level_sums* su
 
 int level_batch_impl(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t seed, double* qf,
                      double* qc, double* qcg, int32_t* iters, mlmc_level_sums* sums) {
-  if (int e = c->itacc.ensure(2 * sizeof(int64_t))) return e;
+  if (int e = c->itacc.ensure(3 * sizeof(int64_t))) return e;
   if (int e = c->sums.ensure(256 + reduce_ws_bytes())) return e;  // sums at 0, partials at 256
   HostLevel* h = c->host + MLMC_MAX_LEVELS;
   if (int e = enqueue_level(c, level, first, n, seed, qf, qc, qcg, iters, c->sums.as<unsigned char>(),
@@ -596,12 +657,13 @@ int prepare_level(mlmc_ctx* c, int level, int64_t n) {
   if (c->tuned_ok[level]) P = c->tuned[level];
   else if (plan_of(md, m, &P)) return fail(MLMC_ERR_CUDA, "occupancy query failed");
   const int64_t n_sys = cn * (1 + nc);
-  if (!P.use_smem || P.ws64_stride) {
-    int64_t nb = 0;
-    const int64_t groups =
-        solve_groups(P, n_sys, c->nsm, P.use_smem ? 0 : (int64_t)(kWsBudget / P.ws_stride), &nb);
-    if (int e = B.ws.ensure((P.use_smem ? P.ws64_stride : P.ws_stride) * groups)) return e;
-  }
+  size_t ws = 0;
+  if (c->tuned_c_ok[level] && nc > 0)
+    ws = std::max(launch_size(c, P, cn).ws, launch_size(c, c->tuned_c[level], cn * nc).ws);
+  else
+    ws = launch_size(c, P, n_sys).ws;
+  if (ws)
+    if (int e = B.ws.ensure(ws)) return e;
   if (int e = B.qsys.ensure((size_t)n_sys * 8)) return e;
   if (int e = B.itsys.ensure((size_t)n_sys * 4)) return e;
   auto& S = c->slot[level];
@@ -609,7 +671,7 @@ int prepare_level(mlmc_ctx* c, int level, int64_t n) {
   if (int e = S.qc.ensure((size_t)n * 8)) return e;
   if (int e = S.qg.ensure((size_t)n * 8)) return e;
   if (int e = S.sums.ensure(256 + reduce_ws_bytes())) return e;
-  if (int e = S.itacc.ensure(2 * sizeof(int64_t))) return e;
+  if (int e = S.itacc.ensure(3 * sizeof(int64_t))) return e;
   return 0;
 }
 
@@ -661,6 +723,17 @@ int multilevel_impl(mlmc_ctx* c, int n_levels, const int64_t* first, const int64
       key.push_back(tol_bits);
       key.push_back(c->tuned_ok[l] ? c->tuned[l].nu_coarse : -1);
       key.push_back(c->tuned_ok[l] ? c->tuned[l].reliable : -1);
+      if (c->tuned_c_ok[l]) {
+        const SolvePlan& Q = c->tuned_c[l];
+        key.push_back(((int64_t)Q.nu << 28) + ((int64_t)Q.gamma << 24) + ((int64_t)Q.threads << 16) +
+                      (Q.cluster << 8) + (Q.warp << 4) + Q.cap_blocks_per_sm);
+        int64_t tb = 0;
+        std::memcpy(&tb, &Q.inner_tol, sizeof tb);
+        key.push_back(tb);
+        key.push_back(((int64_t)Q.nu_coarse << 8) + Q.reliable);
+      } else {
+        key.push_back(-2);
+      }
     }
     for (int l = 0; l < n_levels; ++l) {
       key.push_back(first[l]);
@@ -1203,6 +1276,7 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
   int err = 0;
   for (int l = 0; l <= md.L && !err; ++l) {
     c->tuned_ok[l] = false;
+    c->tuned_c_ok[l] = false;
     const int m = md.m0 << l;
     const int nc = n_coarse(md, l);
     // probe: enough systems to fill the GPU, few enough to stay short
@@ -1214,105 +1288,155 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
       if ((err = run_fields(c, l, a.first, n, seed))) break;
       a.g = c->wb->g.p;
     }
-    SolvePlan cand[28];
-    int nk = dim_of(md) == 3 ? solve3_plan_candidates(m, md.prec, cand, 16) : solve_plan_candidates(m, md.prec, cand, 16);
-    float best = 1e30f, def_ms = 0.f;
-    int best_k = -1;
-    auto time_plan = [&](const SolvePlan& P) -> float {
-      float ms = 1e30f;
+    // which = 0: all systems in one launch (level 0); 1: the fine systems;
+    // 2: the coarse systems (their own launch and plan); fine_plan is the
+    // fine launch's plan while the coarse one is tuned
+    SolvePlan fine_plan{};
+    auto tune = [&](int which, int msz, SolvePlan* best_out, float* def_out, float* best_ms_out,
+                    int* nk_out) -> int {
+      SolvePlan cand[28];
+      int nk = dim_of(md) == 3 ? solve3_plan_candidates(msz, md.prec, cand, 16)
+                               : solve_plan_candidates(msz, md.prec, cand, 16);
+      float best = 1e30f, def_ms = 0.f;
+      int best_k = -1;
+      auto time_plan = [&](const SolvePlan& P) -> float {
+        float ms = 1e30f;
+        for (int rep_i = 0; rep_i < 2 && !err; ++rep_i) {
+          cudaEventRecord(e0, c->st);
+          if (which == 0) err = run_solves(c, a, n, nc, 0, &P);
+          else if (which == 1) err = run_solves(c, a, n, nc, 0, &P, &P, 1);
+          else err = run_solves(c, a, n, nc, 0, &fine_plan, &P, 2);
+          cudaEventRecord(e1, c->st);
+          if (cudaEventSynchronize(e1) != cudaSuccess) err = fail(MLMC_ERR_CUDA, "autotune timing");
+          float t = 0.f;
+          cudaEventElapsedTime(&t, e0, e1);
+          ms = t;
+          if (rep_i == 0 && t > 3.f * best) break;  // clearly slower: one run is enough
+        }
+        return ms;
+      };
+      auto consider = [&](const SolvePlan& P) {
+        cand[nk] = P;
+        const float ms = time_plan(cand[nk]);
+        if (ms < best) {
+          best = ms;
+          best_k = nk;
+        }
+        ++nk;
+      };
+      for (int k = 0; k < nk && !err; ++k) {
+        const float ms = time_plan(cand[k]);
+        if (k == 0) def_ms = ms;
+        if (ms < best) {
+          best = ms;
+          best_k = k;
+        }
+      }
+      if (!err && best_k >= 0) {  // the fastest plan once more with W-cycles, and with two sweep pairs
+        const SolvePlan base = cand[best_k];
+        for (int v = 0; v < 2 && !err; ++v) {
+          SolvePlan q = base;
+          if (v == 0) q.gamma = 2;
+          else q.nu = 2;
+          consider(q);
+        }
+      }
+      if (!err && best_k >= 0) {  // stronger smoothing on the finest grid only: (nu, nuc) = (2, 1), (3, 1)
+        const SolvePlan base = cand[best_k];
+        for (int nu : {2, 3}) {
+          if (err) break;
+          SolvePlan q = base;
+          q.nu = nu;
+          q.nu_coarse = 1;
+          consider(q);
+        }
+      }
+      if (!err && best_k >= 0 && (md.prec == 1 || md.prec == 2)) {  // mixed: looser or tighter FP32 inner solves
+        const SolvePlan base = cand[best_k];
+        for (double it : {1e-4, 1e-6}) {
+          if (err) break;
+          SolvePlan q = base;
+          q.inner_tol = it;
+          consider(q);
+        }
+        // one FP32 CG with reliable updates instead of restarted refinement (2-D)
+        for (double it : {1e-2, 1e-3}) {
+          if (err || dim_of(md) == 3) break;
+          SolvePlan q = base;
+          q.reliable = 1;
+          q.inner_tol = it;
+          consider(q);
+        }
+      }
+      if (err) return err;
+      if (best_k < 0) return fail(MLMC_ERR_CUDA, "autotune: no launch plan ran");
+      *best_out = cand[best_k];
+      *def_out = def_ms;
+      *best_ms_out = best;
+      *nk_out = nk;
+      return 0;
+    };
+    SolvePlan best{}, best_c{};
+    float def_ms = 0.f, best_ms = 0.f, def_c = 0.f, best_c_ms = 0.f;
+    int nk = 0, nk_c = 0;
+    bool split = false;
+    if (nc == 0) {
+      if ((err = tune(0, m, &best, &def_ms, &best_ms, &nk))) break;
+    } else {
+      if ((err = tune(1, m, &best, &def_ms, &best_ms, &nk))) break;
+      fine_plan = best;
+      if ((err = tune(2, m / 2, &best_c, &def_c, &best_c_ms, &nk_c))) break;
+      // two launches run one after the other: keep them only if they beat one
+      // launch of all the level's systems on the fine systems' plan
+      float one = 1e30f;
       for (int rep_i = 0; rep_i < 2 && !err; ++rep_i) {
         cudaEventRecord(e0, c->st);
-        err = run_solves(c, a, n, nc, 0, &P);
+        err = run_solves(c, a, n, nc, 0, &best);
         cudaEventRecord(e1, c->st);
         if (cudaEventSynchronize(e1) != cudaSuccess) err = fail(MLMC_ERR_CUDA, "autotune timing");
         float t = 0.f;
         cudaEventElapsedTime(&t, e0, e1);
-        ms = t;
-        if (rep_i == 0 && t > 3.f * best) break;  // clearly slower: one run is enough
+        one = std::min(one, t);
       }
-      return ms;
-    };
-    for (int k = 0; k < nk && !err; ++k) {
-      const float ms = time_plan(cand[k]);
-      if (k == 0) def_ms = ms;
-      if (ms < best) {
-        best = ms;
-        best_k = k;
+      if (err) break;
+      split = best_ms + best_c_ms < one;
+      if (!split) {
+        best_ms = one;
+        best_c_ms = 0.f;
       }
     }
-    if (!err && best_k >= 0) {  // the fastest plan once more with W-cycles, and with two sweep pairs
-      const SolvePlan base = cand[best_k];
-      for (int v = 0; v < 2 && !err; ++v) {
-        cand[nk] = base;
-        if (v == 0) cand[nk].gamma = 2;
-        else cand[nk].nu = 2;
-        const float ms = time_plan(cand[nk]);
-        if (ms < best) {
-          best = ms;
-          best_k = nk;
-        }
-        ++nk;
-      }
-    }
-    if (!err && best_k >= 0) {  // stronger smoothing on the finest grid only: (nu, nuc) = (2, 1), (3, 1)
-      const SolvePlan base = cand[best_k];
-      for (int nu : {2, 3}) {
-        if (err) break;
-        cand[nk] = base;
-        cand[nk].nu = nu;
-        cand[nk].nu_coarse = 1;
-        const float ms = time_plan(cand[nk]);
-        if (ms < best) {
-          best = ms;
-          best_k = nk;
-        }
-        ++nk;
-      }
-    }
-    if (!err && best_k >= 0 && (md.prec == 1 || md.prec == 2)) {  // mixed: looser or tighter FP32 inner solves
-      const SolvePlan base = cand[best_k];
-      for (double it : {1e-4, 1e-6}) {
-        if (err) break;
-        cand[nk] = base;
-        cand[nk].inner_tol = it;
-        const float ms = time_plan(cand[nk]);
-        if (ms < best) {
-          best = ms;
-          best_k = nk;
-        }
-        ++nk;
-      }
-      // one FP32 CG with reliable updates instead of restarted refinement (2-D)
-      for (double it : {1e-2, 1e-3}) {
-        if (err || dim_of(md) == 3) break;
-        cand[nk] = base;
-        cand[nk].reliable = 1;
-        cand[nk].inner_tol = it;
-        const float ms = time_plan(cand[nk]);
-        if (ms < best) {
-          best = ms;
-          best_k = nk;
-        }
-        ++nk;
-      }
-    }
-    if (err || best_k < 0) break;
-    c->tuned[l] = cand[best_k];
+    c->tuned[l] = best;
     c->tuned_ok[l] = true;
+    if (split) {
+      c->tuned_c[l] = best_c;
+      c->tuned_c_ok[l] = true;
+    }
     if (rep) {
-      rep->threads[l] = cand[best_k].threads;
-      rep->warp[l] = cand[best_k].warp;
-      rep->cap_blocks_per_sm[l] = cand[best_k].cap_blocks_per_sm;
-      rep->cluster[l] = cand[best_k].cluster;
-      rep->gamma[l] = cand[best_k].gamma;
-      rep->nu[l] = cand[best_k].nu;
-      rep->nu_coarse[l] = cand[best_k].nu_coarse > 0 ? cand[best_k].nu_coarse : cand[best_k].nu;
-      rep->inner_tol[l] = cand[best_k].inner_tol;
-      rep->reliable[l] = cand[best_k].reliable;
-      rep->candidates[l] = nk;
-      rep->smem[l] = cand[best_k].use_smem;
-      rep->ms_default[l] = def_ms / n;
-      rep->ms_best[l] = best / n;
+      rep->threads[l] = best.threads;
+      rep->warp[l] = best.warp;
+      rep->cap_blocks_per_sm[l] = best.cap_blocks_per_sm;
+      rep->cluster[l] = best.cluster;
+      rep->gamma[l] = best.gamma;
+      rep->nu[l] = best.nu;
+      rep->nu_coarse[l] = best.nu_coarse > 0 ? best.nu_coarse : best.nu;
+      rep->inner_tol[l] = best.inner_tol;
+      rep->reliable[l] = best.reliable;
+      rep->candidates[l] = nk + nk_c;
+      rep->smem[l] = best.use_smem;
+      rep->ms_default[l] = (def_ms + def_c) / n;
+      rep->ms_best[l] = (best_ms + best_c_ms) / n;
+      if (split) {
+        rep->c_threads[l] = best_c.threads;
+        rep->c_warp[l] = best_c.warp;
+        rep->c_cluster[l] = best_c.cluster;
+        rep->c_cap_blocks_per_sm[l] = best_c.cap_blocks_per_sm;
+        rep->c_gamma[l] = best_c.gamma;
+        rep->c_nu[l] = best_c.nu;
+        rep->c_nu_coarse[l] = best_c.nu_coarse > 0 ? best_c.nu_coarse : best_c.nu;
+        rep->c_inner_tol[l] = best_c.inner_tol;
+        rep->c_reliable[l] = best_c.reliable;
+        rep->c_smem[l] = best_c.use_smem;
+      }
     }
   }
   cudaEventDestroy(e0);
@@ -1339,6 +1463,7 @@ int mlmc_set_launch(mlmc_ctx* c, int level, int32_t mode, int32_t threads, int32
   CUDA_TRY(cudaSetDevice(c->device));
   if (mode < 0) {
     c->tuned_ok[level] = false;
+    c->tuned_c_ok[level] = false;
     return 0;
   }
   if (mode > 3 || (mode == 0 && (threads < 32 || threads > 512 || threads % 32)) ||
@@ -1358,6 +1483,40 @@ int mlmc_set_launch(mlmc_ctx* c, int level, int32_t mode, int32_t threads, int32
   P.nu = nu;
   c->tuned[level] = P;
   c->tuned_ok[level] = true;
+  c->tuned_c_ok[level] = false;  // one launch for all the level's systems
+  return 0;
+}
+
+int mlmc_set_launch_coarse(mlmc_ctx* c, int level, int32_t mode, int32_t threads, int32_t cluster, int32_t gamma,
+                           int32_t nu) {
+  if (!c || level < 1 || level > c->model.L) return fail(MLMC_ERR_ARG, "bad context or level (>= 1)");
+  CUDA_TRY(cudaSetDevice(c->device));
+  if (mode < 0) {
+    c->tuned_c_ok[level] = false;
+    return 0;
+  }
+  if (mode > 3 || (mode == 0 && (threads < 32 || threads > 512 || threads % 32)) ||
+      (mode == 2 && (cluster < 2 || cluster > 8 || (cluster & (cluster - 1)))))
+    return fail(MLMC_ERR_ARG, "mode 0: threads 32..512 (multiple of 32); mode 2: cluster 2, 4 or 8");
+  const int mc = (c->model.m0 << level) / 2;
+  if (mode == 3 && (mc != 16 || c->model.prec != 1 || dim_of(c->model) == 3))
+    return fail(MLMC_ERR_ARG, "mode 3 (register path) needs coarse m = 16, prec 1, 2-D");
+  if (gamma < 1 || gamma > 2) return fail(MLMC_ERR_ARG, "gamma must be 1 (V-cycle) or 2 (W-cycle)");
+  if (nu < 1 || nu > 4) return fail(MLMC_ERR_ARG, "nu must be 1..4");
+  SolvePlan P;
+  const int mr = dim_of(c->model) == 3 ? solve3_plan_mode(mc, c->model.prec, mode, mode == 0 ? threads : 512, cluster, &P)
+                                       : solve_plan_mode(mc, c->model.prec, mode, mode == 0 ? threads : 512, cluster, &P);
+  if (mr) return fail(MLMC_ERR_CUDA, "launch plan query failed");
+  P.gamma = gamma;
+  P.nu = nu;
+  if (!c->tuned_ok[level]) {  // the fine systems keep the default plan
+    SolvePlan F;
+    if (plan_of(c->model, c->model.m0 << level, &F)) return fail(MLMC_ERR_CUDA, "launch plan query failed");
+    c->tuned[level] = F;
+    c->tuned_ok[level] = true;
+  }
+  c->tuned_c[level] = P;
+  c->tuned_c_ok[level] = true;
   return 0;
 }
 
@@ -1375,6 +1534,10 @@ int mlmc_set_solver(mlmc_ctx* c, int level, int32_t reliable, double inner_tol) 
   }
   c->tuned[level].reliable = reliable;
   c->tuned[level].inner_tol = inner_tol;
+  if (c->tuned_c_ok[level]) {
+    c->tuned_c[level].reliable = reliable;
+    c->tuned_c[level].inner_tol = inner_tol;
+  }
   return 0;
 }
 

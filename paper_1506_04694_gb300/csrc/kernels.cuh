@@ -64,8 +64,10 @@ enum KSource : int {
 };
 
 struct SolveArgs {
-  // systems: fine systems [0, n_samples), then n_coarse per sample
+  // systems: fine systems [0, n_samples), then n_coarse per sample; a launch
+  // solves systems [sys_begin, sys_end) (sys_end 0: all of them)
   int64_t n_samples;
+  int64_t sys_begin, sys_end;
   int n_coarse;        // 0, 1 (plain, offset (0,0)) or 4 (CGV offsets)
   int m;               // fine cells per side
   int ksrc;
@@ -150,7 +152,8 @@ struct LevelSumsDev {
 };
 
 // Gather system Q's of a chunk into the per-sample outputs.
-// it_acc[0] += iterations of all systems, it_acc[1] += cells x iterations.
+// it_acc[0] += iterations of all systems, it_acc[1] += cells x iterations of
+// the fine systems, it_acc[2] += the same of the coarse systems.
 // cells_f / cells_c: cells of a fine / coarse system; Q_cgv is the mean of the
 // n_coarse (4 or 8) coarse Q's, summed left to right.
 int gather_launch(const double* q_sys, const int32_t* it_sys, int64_t n_samples, int n_coarse,

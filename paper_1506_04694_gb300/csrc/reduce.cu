@@ -11,7 +11,7 @@ __global__ void gather_kernel(const double* q_sys, const int32_t* it_sys, int64_
                               int64_t cells_f, int64_t cells_c, double* qf, double* qc, double* qcg,
                               int32_t* iters, unsigned long long* it_acc) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  long long it = 0, itc = 0;
+  long long it = 0, itc = 0, itcc = 0;  // iterations; cells x iterations, fine and coarse
   if (s < n) {
     qf[s] = q_sys[s];
     it = it_sys[s];
@@ -26,7 +26,7 @@ __global__ void gather_kernel(const double* q_sys, const int32_t* it_sys, int64_
       double acc = qq[0];
       for (int o = 0; o < nc; ++o) {
         it += it_sys[n + s * nc + o];
-        itc += (long long)it_sys[n + s * nc + o] * cells_c;
+        itcc += (long long)it_sys[n + s * nc + o] * cells_c;
         if (o) acc += qq[o];
       }
       qcg[s] = nc >= 4 ? acc * (1.0 / nc) : nan("");
@@ -34,9 +34,11 @@ __global__ void gather_kernel(const double* q_sys, const int32_t* it_sys, int64_
   }
   it = warp_sum(it);
   itc = warp_sum(itc);
+  itcc = warp_sum(itcc);
   if ((threadIdx.x & 31) == 0 && it) {
     atomicAdd(it_acc, (unsigned long long)it);
     atomicAdd(it_acc + 1, (unsigned long long)itc);
+    if (itcc) atomicAdd(it_acc + 2, (unsigned long long)itcc);
   }
 }
 

@@ -1350,7 +1350,8 @@ __global__ void __launch_bounds__(MODE == 1 || MODE == 3 ? 32 * kWarpsPerBlock :
   __shared__ GroupState<T, F> gstate[kGroups];
   __shared__ T red[MODE == 1 || MODE == 3 ? 1 : 132];
   __shared__ double red64[MODE == 1 || MODE == 3 ? 1 : 132];
-  const int64_t n_sys = a.n_samples * (int64_t)(1 + a.n_coarse);
+  const int64_t n_all = a.n_samples * (int64_t)(1 + a.n_coarse);
+  const int64_t sys0 = a.sys_begin, n_sys = a.sys_end > 0 ? a.sys_end : n_all;
   int par = 0, m_prev = -1;
   if (MODE == 2) {
     __shared__ double cl_part[2];
@@ -1359,7 +1360,7 @@ __global__ void __launch_bounds__(MODE == 1 || MODE == 3 ? 32 * kWarpsPerBlock :
     const int64_t cid = blockIdx.x / g.nblk, ncl = gridDim.x / g.nblk;
     unsigned char* base = a.ws + (size_t)cid * a.ws_stride;
     unsigned char* stage = a.stage_bytes ? smem_raw : nullptr;
-    for (int64_t sys = cid; sys < n_sys; sys += ncl)
+    for (int64_t sys = sys0 + cid; sys < n_sys; sys += ncl)
       solve_one<PREC>(g, a, sys, base, gstate[0], red, red64, par, m_prev, nullptr, stage);
     cl.sync();  // no block leaves while others may still read its shared memory
     return;
@@ -1369,7 +1370,7 @@ __global__ void __launch_bounds__(MODE == 1 || MODE == 3 ? 32 * kWarpsPerBlock :
   unsigned char* base = a.use_smem ? smem_raw + (size_t)gid * a.ws_stride : a.ws + slot * a.ws_stride;
   unsigned char* base64 = a.ws64_stride ? a.ws64 + slot * a.ws64_stride : nullptr;
   const int64_t stride = (int64_t)gridDim.x * kGroups;
-  for (int64_t sys = (int64_t)blockIdx.x * kGroups + gid; sys < n_sys; sys += stride) {
+  for (int64_t sys = sys0 + (int64_t)blockIdx.x * kGroups + gid; sys < n_sys; sys += stride) {
     if constexpr (MODE == 3 && PREC == 1) {
       const int msys = sys < a.n_samples ? a.m : a.m >> 1;
       if (msys == kTinyM) {

@@ -611,7 +611,8 @@ __global__ void __launch_bounds__(MODE == 1 ? 32 * kWarpsPerBlock3 : kMaxThreads
   GroupState3<T>& gstate = gstates[0];
   __shared__ T red[MODE == 1 ? 1 : 132];
   __shared__ double red64[MODE == 1 ? 1 : 132];
-  const int64_t n_sys = a.n_samples * (int64_t)(1 + a.n_coarse);
+  const int64_t n_all = a.n_samples * (int64_t)(1 + a.n_coarse);
+  const int64_t sys0 = a.sys_begin, n_sys = a.sys_end > 0 ? a.sys_end : n_all;
   int par = 0, m_prev = -1;
   if (MODE == 2) {
     __shared__ double cl_part[2];
@@ -619,7 +620,7 @@ __global__ void __launch_bounds__(MODE == 1 ? 32 * kWarpsPerBlock3 : kMaxThreads
     const ClusterGroup g{cl.num_blocks(), cl.block_rank(), cl_part};
     const int64_t cid = blockIdx.x / g.nblk, ncl = gridDim.x / g.nblk;
     unsigned char* base = a.ws + (size_t)cid * a.ws_stride;
-    for (int64_t sys = cid; sys < n_sys; sys += ncl)
+    for (int64_t sys = sys0 + cid; sys < n_sys; sys += ncl)
       solve_one3<MIXED>(g, a, sys, base, gstate, red, red64, par, m_prev, nullptr);
     cl.sync();  // no block leaves while others may still read its shared memory
     return;
@@ -629,7 +630,7 @@ __global__ void __launch_bounds__(MODE == 1 ? 32 * kWarpsPerBlock3 : kMaxThreads
   unsigned char* base = a.use_smem ? smem_raw + (size_t)gid * a.ws_stride : a.ws + slot * a.ws_stride;
   unsigned char* base64 = a.ws64_stride ? a.ws64 + slot * a.ws64_stride : nullptr;
   const int64_t stride = (int64_t)gridDim.x * kGroups;
-  for (int64_t sys = (int64_t)blockIdx.x * kGroups + gid; sys < n_sys; sys += stride) {
+  for (int64_t sys = sys0 + (int64_t)blockIdx.x * kGroups + gid; sys < n_sys; sys += stride) {
     if (MODE == 1)
       solve_one3<MIXED>(WarpGroup(), a, sys, base, gstates[gid], red, red64, par, m_prev, base64);
     else

@@ -81,3 +81,33 @@ def test_register_path_solve_k_pressure():
         p_ref, q_ref = darcy.solve_k(k[s])
         assert abs(q[s] - q_ref) <= RTOL_MIX * abs(q_ref)
         assert np.max(np.abs(p[s] - p_ref)) < 5e-6
+
+
+@pytest.mark.parametrize("problem", [2, 1])
+def test_coarse_systems_in_a_launch_of_their_own(problem):
+    # level 1 (m = 32): the fine 32 x 32 systems in blocks of 128 threads, the
+    # four 16 x 16 CGV coarse systems of each sample on the register path in a
+    # launch of their own; the same Q as one launch for all systems, and the oracle's
+    torch, pk = need_gpu()
+    d = workloads.workload("lognormal_2layer_cgv_16to512", tol=1e-10, problem=problem)
+    model = darcy.Model.from_dict(d)
+    n, seed = 40, 5
+    with pk.Context(d) as ctx:
+        ctx.set_launch(1, 0, 128, 0, 1, 1)
+        one = level_q(pk, torch, ctx, 1, n, seed)
+        ctx.set_launch_coarse(1, 3, 0, 0, 1, 1)
+        two = level_q(pk, torch, ctx, 1, n, seed)
+        ctx.set_launch_coarse(1, 0, 64, 0, 1, 2)  # a block plan for the coarse launch
+        blk = level_q(pk, torch, ctx, 1, n, seed)
+        ctx.set_launch_coarse(1, -1)
+        back = level_q(pk, torch, ctx, 1, n, seed)
+    assert np.array_equal(back[0], one[0]) and np.array_equal(back[2], one[2])
+    for res in (two, blk):
+        np.testing.assert_array_equal(res[0], one[0])  # the fine systems' launch is unchanged
+        np.testing.assert_allclose(res[1], one[1], rtol=1e-8, atol=0)
+        np.testing.assert_allclose(res[2], one[2], rtol=1e-8, atol=0)
+    cache = {}
+    for i in (0, n - 1):
+        r = darcy.sample(model, seed, 1, i, cache)
+        assert abs(two[1][i] - r["qc"]) <= RTOL_MIX * abs(r["qc"])
+        assert abs(two[2][i] - r["qc_cgv"]) <= RTOL_MIX * abs(r["qc_cgv"])
