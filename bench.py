@@ -47,6 +47,15 @@ HBM_FALLBACK_GBS = 6800.0
 CPU_SAMPLE = {0: 256, 1: 64, 2: 32, 3: 16, 4: 16, 5: 16, 6: 2}
 PREC_NAMES = {0: "fp64", 1: "fp32-mg/fp64-refinement", 2: "fp32-mg-bf16-faces/fp64-refinement",
               3: "fp64-cg/fp32-mg-preconditioner"}
+# DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum) against the
+# library's algorithmic bytes of the same launches, from one-kernel captures of
+# the current kernel versions (profiles/); the line's traffic scales the ratio
+# to its kernel's average launch.
+TRAFFIC = {
+    "solve_kernel<1, 0>": (54.23e9, 72.30e9,
+                           "ncu of bench.py --profile-case mixed_m256_split: the two solve launches (m = 256 fine, "
+                           "m = 128 coarse systems, blocks of 512), profiles/solve_kernel_m256_hbm.txt"),
+}
 
 
 # ------------------------------------------------------------- oracle side --
@@ -259,6 +268,7 @@ def profiled_pass(ctx, d, est, seed, tune):
         per.append({"level": lvl, "m": d["m0"] << lvl, "N": n, "fields_ms": p["ms"]["fields"],
                     "solve_ms": p["ms"]["solve"] + p["ms"]["solve_coarse"], "reduce_ms": p["ms"]["reduce"],
                     "solve_fine_ms": p["ms"]["solve"], "solve_coarse_ms": p["ms"]["solve_coarse"],
+                    "solve_launches": p["launches"]["solve"], "solve_coarse_launches": p["launches"]["solve_coarse"],
                     "iters_per_sample": s["iters_total"] / max(s["n"], 1),
                     "cell_iters": p["cell_iters"], "solve_bytes": p["solve_bytes"],
                     "solve_flops": p["solve_flops"], "fft_flops": p["fft_flops"], "fft_bytes": p["fft_bytes"],
@@ -283,13 +293,14 @@ def roofline(d, per, peaks):
         split = r["coarse_kernel"] is not None and r["solve_coarse_ms"] > 0
         parts = [(r["solve_kernel"], r["solve_fine_ms"],
                   r["solve_bytes"] - (r["solve_bytes_c"] if split else 0.0),
-                  r["solve_flops"] - (r["solve_flops_c"] if split else 0.0), r["smem"], r["m"])]
+                  r["solve_flops"] - (r["solve_flops_c"] if split else 0.0), r["smem"], r["m"],
+                  r["solve_launches"])]
         if split:
             parts.append((r["coarse_kernel"], r["solve_coarse_ms"], r["solve_bytes_c"], r["solve_flops_c"],
-                          r["coarse_smem"], r["m"] // 2))
-        for name_, ms, byt, fl, smem, msz in parts:
+                          r["coarse_smem"], r["m"] // 2, r["solve_coarse_launches"]))
+        for name_, ms, byt, fl, smem, msz, nl in parts:
             k = by.setdefault(name_, {"ms": 0.0, "bytes": 0.0, "flops": 0.0, "levels": [], "stream": 0,
-                                      "sbytes": 0.0, "sms": 0.0})
+                                      "sbytes": 0.0, "sms": 0.0, "slaunch": 0})
             k["ms"] += ms
             k["bytes"] += byt
             k["flops"] += fl
@@ -298,6 +309,7 @@ def roofline(d, per, peaks):
                 k["stream"] += ms
                 k["sbytes"] += byt
                 k["sms"] += ms
+                k["slaunch"] += nl
         f = by.setdefault("ce_rows+ce_cols", {"ms": 0.0, "bytes": 0.0, "flops": 0.0, "levels": [], "stream": 0})
         f["ms"] += r["fields_ms"]
         f["bytes"] += r["fft_bytes"]
@@ -310,11 +322,18 @@ def roofline(d, per, peaks):
     shares = {n: round(v["ms"] / total, 4) for n, v in by.items()}
     if name.startswith("solve") and k["stream"] >= 0.5 * k["ms"]:
         ach = k["sbytes"] / (k["sms"] / 1e3) / 1e9
+        per_launch = k["sbytes"] / max(k["slaunch"], 1)
+        traffic, tsrc = None, "no counter capture of this kernel version"
+        if name in TRAFFIC:
+            dram, alg, tsrc = TRAFFIC[name]
+            traffic = dram / alg * per_launch
         out = {"kernel": name, "systems_m": k["levels"], "bound": "hbm", "achieved": ach, "peak": peaks["hbm"],
-               "unit": "GB/s", "frac": ach / peaks["hbm"], "traffic": None, "peak_source": peaks["hbm_src"],
-               "note": "algorithmic bytes = cells x CG iterations x bytes per cell-iteration of the streaming "
-                       "model (every pass reads its operands and writes its results once); traffic null: no "
-                       "counter capture of this kernel version"}
+               "unit": "GB/s", "frac": ach / peaks["hbm"], "traffic": traffic, "peak_source": peaks["hbm_src"],
+               "launches": k["slaunch"], "algorithmic_bytes_per_launch": per_launch,
+               "note": "achieved = algorithmic bytes of the kernel's streamed launches (cells x CG iterations x "
+                       "bytes per cell-iteration of the streaming model: every pass reads its operands and "
+                       "writes its results once) / their CUDA-event time; traffic = DRAM bytes per launch, the "
+                       "DRAM-to-algorithmic ratio of one ncu capture scaled to the average launch (" + tsrc + ")"}
     else:
         # the field passes compute in FP32 with prec 1, 2; a shared-memory solver plan's
         # multigrid (most of its flops) in FP32 with prec 1, 2, 3

@@ -20,6 +20,7 @@
 // W = exp(-2 pi i/M), j = 0, 1, 2 (only j = 0 when the outputs kept are
 // fewer than N).
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -383,11 +384,19 @@ __global__ void ce_cols_kernel(CeColsArgs args, const Cplx<R>* __restrict__ tw,
   const bool has_im = args.t_im >= 0;
   G* g0 = g + (sidx * args.n_layers + args.t_re) * (int64_t)m * nc;
   G* g1 = g + (sidx * args.n_layers + (has_im ? args.t_im : args.t_re)) * (int64_t)m * nc;
+  // FP32 fields add the mean in FP32 (an FP64 add and its two conversions
+  // would run on the FP64 pipe, 1/64 of the FP32 rate on this GPU)
+  const R mre = (R)args.mu_re, mim = (R)args.mu_im;
   for (int t = threadIdx.x; t < m * C; t += blockDim.x) {
     const int b = t / C, cc = t - b * C;
     const Cplx<R> v = s[cc * M + b];
-    g0[(int64_t)b * nc + a0 + cc] = (G)(args.mu_re + (double)v.x);
-    if (has_im) g1[(int64_t)b * nc + a0 + cc] = (G)(args.mu_im + (double)v.y);
+    if constexpr (std::is_same<G, float>::value) {
+      g0[(int64_t)b * nc + a0 + cc] = mre + v.x;
+      if (has_im) g1[(int64_t)b * nc + a0 + cc] = mim + v.y;
+    } else {
+      g0[(int64_t)b * nc + a0 + cc] = (G)(args.mu_re + (double)v.x);
+      if (has_im) g1[(int64_t)b * nc + a0 + cc] = (G)(args.mu_im + (double)v.y);
+    }
   }
 }
 
