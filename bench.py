@@ -52,6 +52,11 @@ PREC_NAMES = {0: "fp64", 1: "fp32-mg/fp64-refinement", 2: "fp32-mg-bf16-faces/fp
 # the current kernel versions (profiles/); the line's traffic scales the ratio
 # to its kernel's average launch.
 TRAFFIC = {
+    "solve_list_kernel<1, 0> [blocks of 512 threads, workspace in global memory]": (
+        51.003e9, 108.924e9,
+        "ncu of bench.py --profile-case sched_block512: the persistent launch of blocks of 512 over the "
+        "headline's levels 2 (fine), 3 and 4 at 2000 / 600 / 160 samples, "
+        "profiles/solve_list_kernel_block512_levels2to4.txt"),
     "solve_kernel<1, 0>": (54.23e9, 72.30e9,
                            "ncu of bench.py --profile-case mixed_m256_split: the two solve launches (m = 256 fine, "
                            "m = 128 coarse systems, blocks of 512), profiles/solve_kernel_m256_hbm.txt"),
@@ -192,7 +197,9 @@ def config_block(args, d, baseline):
          "dim": d.get("dim", 2), "norm_r": d["norm_r"], "cgv": d["cgv"], "prec": PREC_NAMES[d["prec"]],
          "solver_tol": d["tol"], "seed": args.seed, "cost_model": "deterministic m_l^d (1 + n_coarse/2^d)",
          "l2": "flushed between steps (256 MB device write)", "parallelism": "replicas%d" % args.gpus,
-         "graph": "levels of a round side by side under one CUDA graph"}
+         "graph": "each estimate round captured as one CUDA graph",
+         "schedule": ("work queue: per launch shape one persistent solver launch across the levels"
+                      if args.schedule else "per level: a launch chain per level, levels side by side")}
     if baseline is not None:
         c["baseline_arm"] = {"prec": PREC_NAMES[baseline["prec"]], "cgv": baseline["cgv"]}
     return c
@@ -347,6 +354,64 @@ def roofline(d, per, peaks):
     return out
 
 
+SHAPE_NAMES = {0: "blocks of %d threads", 1: "one warp per system (blocks of %d)", 2: "clusters of %d x %d threads",
+               3: "register path, one warp per system (blocks of %d)"}
+
+
+def shape_name(cl):
+    if cl["mode"] == 2:
+        return SHAPE_NAMES[2] % (cl["cluster"], cl["threads"])
+    return SHAPE_NAMES[cl["mode"]] % cl["threads"] + (", workspace in shared memory" if cl["smem"]
+                                                       else ", workspace in global memory")
+
+
+def roofline_classes(d, tot, peaks, m_of):
+    """Roofline of the dominant kernel of the profiled estimate under the
+    work-queue schedule: each launch shape's persistent solver launches (their
+    summed CUDA-event time, algorithmic bytes and flops) and the field passes;
+    the one with the largest time.  Streamed shapes (workspace in global
+    memory) against the copy bandwidth, shared-memory shapes and the field
+    passes against the measured FMA peak of their precision."""
+    cand = []
+    for cl in tot["classes"]:
+        cand.append({"kernel": "solve_list_kernel<%d, %d>" % (d["prec"], cl["mode"]), "shape": shape_name(cl),
+                     "ms": cl["ms"], "bytes": cl["bytes"], "flops": cl["flops"], "launches": cl["launches"],
+                     "smem": cl["smem"], "levels": cl["levels"]})
+    cand.append({"kernel": "ce_rows+ce_cols", "shape": "field passes", "ms": tot["ms"]["fields"],
+                 "bytes": tot["fft_bytes"], "flops": tot["fft_flops"], "launches": tot["launches"]["fields"],
+                 "smem": 1, "levels": []})
+    total = sum(c["ms"] for c in cand)
+    shares = {"%s [%s]" % (c["kernel"], c["shape"]): round(c["ms"] / total, 4) for c in cand}
+    k = max(cand, key=lambda c: c["ms"])
+    f32 = d["prec"] in (1, 2)
+    base = {"kernel": k["kernel"], "launch_shape": k["shape"], "levels": k["levels"],
+            "systems_m": sorted({m_of(l) for l in k["levels"]}, reverse=True), "launches": k["launches"]}
+    if k["kernel"].startswith("solve") and not k["smem"]:
+        ach = k["bytes"] / (k["ms"] / 1e3) / 1e9
+        per_launch = k["bytes"] / max(k["launches"], 1)
+        key = "%s [%s]" % (k["kernel"], k["shape"])
+        traffic, tsrc = None, "no counter capture of this kernel version and launch shape"
+        if key in TRAFFIC:
+            dram, alg, tsrc = TRAFFIC[key]
+            traffic = dram / alg * per_launch
+        out = dict(base, bound="hbm", achieved=ach, peak=peaks["hbm"], unit="GB/s", frac=ach / peaks["hbm"],
+                   traffic=traffic, peak_source=peaks["hbm_src"], algorithmic_bytes_per_launch=per_launch,
+                   note="achieved = algorithmic bytes of the launches (cells x CG iterations x bytes per "
+                        "cell-iteration of the streaming model: every pass reads its operands and writes its "
+                        "results once) / their CUDA-event time in the profiled estimate (launches in series); "
+                        "traffic = DRAM bytes per launch, the DRAM-to-algorithmic ratio of one ncu capture "
+                        "scaled to the average launch (" + tsrc + ")")
+    else:
+        use32 = f32 if k["kernel"].startswith("ce") else d["prec"] != 0
+        pk_t = peaks["fp32"] if use32 else peaks["fp64"]
+        src = "measured by mlmc_fma_peak (independent FMA chains, %s) on this GPU" % ("FP32" if use32 else "FP64")
+        ach = k["flops"] / (k["ms"] / 1e3) / 1e12
+        out = dict(base, bound="alu", achieved=ach, peak=pk_t, unit="TFLOP/s", frac=ach / pk_t, traffic=None,
+                   peak_source=src)
+    out["time_share"] = shares
+    return out
+
+
 def host_estimate_e2e(ctx, d, seed):
     """The same adaptive estimate driven from the host through the host-buffer
     entry point mlmc_level_batch_host: pilot and every top-up round copy the
@@ -461,11 +526,45 @@ PROFILE_CASES = {
                  [(1, 4096, (0, 128, 0, 1, 2), None), (2, 512, (0, 256, 0, 1, 2), None)]),
 }
 
+# Multilevel batches under the work-queue schedule: (workload, overrides,
+# per-level plans (level, launch, solver, coarse launch or None), samples per
+# level).  sched_block512: the headline's levels 2..4 with the autotuned plans
+# of the headline, so that one persistent launch of blocks of 512 (global
+# workspaces) solves level 2's fine systems and all of levels 3 and 4; the
+# first solve_list_kernel launch is that one.
+MULTI_CASES = {
+    "sched_block512": ("lognormal_2layer_cgv_16to512", {},
+                       [(2, (0, 512, 0, 1, 2), None, (0, 256, 0, 1, 1)), (3, (0, 512, 0, 1, 2), None, None),
+                        (4, (0, 512, 0, 1, 2), (1, 1e-3), None)],
+                       [0, 0, 2000, 600, 160, 0]),
+}
+
 
 def run_profile_case(case):
     import torch
     import paper_1506_04694_gb300 as pk
     import workloads
+    if case in MULTI_CASES:
+        name, over, plans, n = MULTI_CASES[case]
+        with pk.Context(workloads.workload(name, **over), stream=torch.cuda.Stream()) as ctx:
+            for level, launch, solver, coarse in plans:
+                ctx.set_launch(level, *launch)
+                if coarse is not None:
+                    ctx.set_launch_coarse(level, *coarse)
+                if solver is not None:
+                    ctx.set_solver(level, *solver)
+            ctx.set_schedule(1)
+            ctx.profile(True)
+            sums = ctx.multilevel_batch(n, 0, use_graph=False)
+            p = ctx.profile_read()
+            ctx.profile(False)
+            torch.cuda.synchronize()
+            print(case, "samples", [s["n"] for s in sums], "iterations", [s["iters_total"] for s in sums], flush=True)
+            for cl in p["classes"]:
+                print(case, "launch shape", shape_name(cl), "levels", cl["levels"], "launches", cl["launches"],
+                      "ms %.4f" % cl["ms"], "cell_iterations %.6g" % cl["cell_iters"],
+                      "algorithmic_solve_bytes %.6g" % cl["bytes"], flush=True)
+        return
     name, over, levels = PROFILE_CASES[case]
     with pk.Context(workloads.workload(name, **over)) as ctx:
         for level, n, launch, solver, *coarse in levels:
@@ -592,7 +691,9 @@ def main():
                     help="workload name: time-to-eps of its mixed CGV form against plain FP64 (one JSON line)")
     ap.add_argument("--bf16-arm", action="store_true")
     ap.add_argument("--fp64cg-arm", action="store_true")
-    ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES))
+    ap.add_argument("--schedule", type=int, default=1, choices=[0, 1],
+                    help="multilevel schedule (mlmc_set_schedule): 1 work queue per launch shape, 0 per level")
+    ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES) + sorted(MULTI_CASES))
     ap.add_argument("--ncu-summary", default=None, metavar="CSV")
     ap.add_argument("--skip", type=int, default=0)
     ap.add_argument("--from", dest="start_at", default=None)
@@ -647,10 +748,12 @@ def main():
     peaks = {"fp64": fp64_peak, "fp32": fp32_peak, "hbm": hbm, "hbm_src": hbm_src}
     ctx = pk.Context(d, device=local, stream=stream)
     tune = ctx.autotune(seed=args.seed + 12345)  # untimed set-up: launch plan per level
+    ctx.set_schedule(args.schedule)
     bctx = btune = None
     if base is not None:
         bctx = pk.Context(base, device=local, stream=stream)
         btune = bctx.autotune(seed=args.seed + 12345)
+        bctx.set_schedule(args.schedule)
     seed = args.seed + 7919 * rank
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
@@ -690,14 +793,16 @@ def main():
 
     # ---- untimed: stage and per-level timing (CUDA events), roofline ----
     tot, per = profiled_pass(ctx, d, est, seed, tune)
-    roof = roofline(d, per, peaks)
+    m_of = lambda l: d["m0"] << l
+    roof = roofline_classes(d, tot, peaks, m_of) if tot["classes"] else roofline(d, per, peaks)
     base_stages = None
     if bctx is not None:
         btot, bper = profiled_pass(bctx, base, best, seed, btune)
         base_stages = {"stage_ms_per_step": btot["ms"],
                        "per_level": [{k: r[k] for k in ("m", "N", "fields_ms", "solve_ms", "iters_per_sample",
                                                         "solve_kernel")} for r in bper],
-                       "roofline": roofline(base, bper, peaks)}
+                       "roofline": (roofline_classes(base, btot, peaks, m_of) if btot["classes"]
+                                    else roofline(base, bper, peaks))}
         base_out.update(base_stages)
 
     # ---- end to end through the host-buffer entry point ----
@@ -732,6 +837,12 @@ def main():
         "N_per_level": est["N"], "V_per_level": est["V"], "q_hat": est["q_hat"], "var_hat": est["var_hat"],
         "alpha": est["alpha"], "bias_estimate": est["bias"], "bias_flag": est["bias_flag"],
         "stage_ms_per_step_serial": tot["ms"],
+        "solve_launch_shapes": [{"kernel": "solve_list_kernel<%d, %d>" % (d["prec"], cl["mode"]),
+                                 "shape": shape_name(cl), "levels": cl["levels"], "launches": cl["launches"],
+                                 "ms_per_step": round(cl["ms"], 3),
+                                 "alg_gbs": round(cl["bytes"] / max(cl["ms"], 1e-9) / 1e6, 1),
+                                 "tflops": round(cl["flops"] / max(cl["ms"], 1e-9) / 1e9, 3)}
+                                for cl in tot["classes"]],
         "per_level": [dict({k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()
                             if k not in ("cell_iters", "solve_flops", "fft_flops", "fft_bytes", "solve_bytes",
                                          "solve_bytes_c", "solve_flops_c")},

@@ -252,7 +252,11 @@ MLMC_API int mlmc_resume(mlmc_ctx* ctx, const char* path);
  * created on a non-default stream and is skipped while profiling is on (stage
  * timing puts events between the launches).
  * Per-sample values are not returned (use mlmc_level_batch for those).
- * mlmc_estimate() runs its pilot and every top-up round through this call. */
+ * mlmc_estimate() runs its pilot and every top-up round through this call.
+ * With the work-queue schedule (mlmc_set_schedule, the default) a 2-D batch
+ * in precision 0 or 1 runs its solves as one persistent launch per launch
+ * shape across all levels instead of one per level (no effect on results).
+ */
 MLMC_API int mlmc_multilevel_batch(mlmc_ctx* ctx, int32_t n_levels, const int64_t* first, const int64_t* n,
                                    uint64_t seed, int32_t use_graph, mlmc_level_sums* sums);
 
@@ -321,6 +325,24 @@ MLMC_API int mlmc_set_launch(mlmc_ctx* ctx, int level, int32_t mode, int32_t thr
  * Errors: MLMC_ERR_ARG. */
 MLMC_API int mlmc_set_launch_coarse(mlmc_ctx* ctx, int level, int32_t mode, int32_t threads, int32_t cluster,
                                     int32_t gamma, int32_t nu);
+
+/* Schedule of mlmc_multilevel_batch() (and so of mlmc_estimate()).
+ * schedule 1 (the default): the work-queue schedule.  The fields of every
+ * level's whole range are sampled first (each level on its own stream); then
+ * the level ranges, split into fine and coarse systems where a level has a
+ * coarse plan of its own, are grouped by launch shape (kernel, block,
+ * cluster, shared memory, residency), and each group runs as ONE persistent
+ * solver launch over all its systems, largest systems first, whose thread
+ * groups take the next system from an atomic work counter (a group that drew
+ * long solves takes fewer; no group waits on another).  Each system keeps its
+ * own level's multigrid and refinement settings.  Then each level's gather
+ * and reduction.  It applies to 2-D contexts in precision 0 or 1 while stage
+ * profiling is off and the fields and per-system outputs of all levels'
+ * ranges fit in 24 GB; otherwise the batch takes schedule 0.
+ * schedule 0: one launch chain per level (fields, solves, gather chunk by
+ * chunk), the levels side by side on their streams.
+ * The two schedules give bit-identical results.  Errors: MLMC_ERR_ARG. */
+MLMC_API int mlmc_set_schedule(mlmc_ctx* ctx, int32_t schedule);
 
 /* Mixed precision (prec 1, 2) of one level's solver, on top of its launch
  * plan (the autotuned or set one, else the default): reliable = 0 runs FP32
@@ -411,6 +433,8 @@ MLMC_API int mlmc_solve_k_static(int device, int32_t m, int64_t n, const double*
 
 /* Per-stage device timing of a context, collected with CUDA events on the
  * context's stream while enabled (used by the benchmark for the roofline). */
+#define MLMC_PROFILE_CLASSES 8
+
 typedef struct mlmc_profile_stats {
   int64_t launches[4];     /* kernel launches: 0 field kernels (both FFT passes),
                               1 fused assembly + solve + QoI (all systems, or the fine ones when
@@ -437,6 +461,20 @@ typedef struct mlmc_profile_stats {
   double cell_iters_c;     /* the part of cell_iters, solve_flops, solve_bytes due to the */
   double solve_flops_c;    /* coarse systems (stage 3 when they run as a launch of their own) */
   double solve_bytes_c;
+  /* The work-queue launches of profiled multilevel batches (mlmc_set_schedule
+   * 1; their time is also in ms[1]), summed per launch shape, at most
+   * MLMC_PROFILE_CLASSES shapes (further ones are counted in ms[1] only). */
+  int32_t n_classes;
+  int32_t class_mode[MLMC_PROFILE_CLASSES];      /* 0 block, 1 warp, 2 cluster, 3 register path */
+  int32_t class_threads[MLMC_PROFILE_CLASSES];   /* threads per block */
+  int32_t class_cluster[MLMC_PROFILE_CLASSES];   /* blocks per cluster (0: none) */
+  int32_t class_smem[MLMC_PROFILE_CLASSES];      /* 1: workspace in shared memory */
+  int32_t class_levels[MLMC_PROFILE_CLASSES];    /* bit l: held systems of level l */
+  int32_t class_launches[MLMC_PROFILE_CLASSES];
+  double class_ms[MLMC_PROFILE_CLASSES];         /* summed event time of the launches */
+  double class_cell_iters[MLMC_PROFILE_CLASSES]; /* cells x CG iterations of their systems */
+  double class_flops[MLMC_PROFILE_CLASSES];      /* algorithmic flops, as solve_flops */
+  double class_bytes[MLMC_PROFILE_CLASSES];      /* algorithmic bytes, as solve_bytes */
 } mlmc_profile_stats;
 
 /* enable != 0: reset the counters and start collecting; 0: stop. */

@@ -57,6 +57,9 @@ class EstimateOut(ctypes.Structure):
     ]
 
 
+PROFILE_CLASSES = 8
+
+
 class ProfileStats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64 * 4), ("ms", ctypes.c_double * 4),
                 ("cell_iters", ctypes.c_double), ("cells", ctypes.c_double),
@@ -64,7 +67,12 @@ class ProfileStats(ctypes.Structure):
                 ("samples", ctypes.c_double), ("solve_flops", ctypes.c_double), ("fft_flops", ctypes.c_double),
                 ("solve_bytes", ctypes.c_double), ("fft_bytes", ctypes.c_double),
                 ("cell_iters_c", ctypes.c_double), ("solve_flops_c", ctypes.c_double),
-                ("solve_bytes_c", ctypes.c_double)]
+                ("solve_bytes_c", ctypes.c_double), ("n_classes", ctypes.c_int32)] + [
+                (name, ctypes.c_int32 * PROFILE_CLASSES) for name in
+                ("class_mode", "class_threads", "class_cluster", "class_smem", "class_levels",
+                 "class_launches")] + [
+                (name, ctypes.c_double * PROFILE_CLASSES) for name in
+                ("class_ms", "class_cell_iters", "class_flops", "class_bytes")]
 
 
 STAGES = ("fields", "solve", "reduce", "solve_coarse")
@@ -117,6 +125,7 @@ EXPORTS = {
     "mlmc_set_launch_coarse": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_int32,
                                               ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "mlmc_set_solver": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_double]),
+    "mlmc_set_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "mlmc_ce_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "mlmc_philox_words": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
@@ -327,7 +336,13 @@ class Context:
                 "cell_iters": p.cell_iters, "cells": p.cells, "fft_row_points": p.fft_row_points,
                 "fft_col_points": p.fft_col_points, "samples": p.samples, "solve_flops": p.solve_flops,
                 "fft_flops": p.fft_flops, "solve_bytes": p.solve_bytes, "fft_bytes": p.fft_bytes,
-                "cell_iters_c": p.cell_iters_c, "solve_flops_c": p.solve_flops_c, "solve_bytes_c": p.solve_bytes_c}
+                "cell_iters_c": p.cell_iters_c, "solve_flops_c": p.solve_flops_c, "solve_bytes_c": p.solve_bytes_c,
+                "classes": [{"mode": p.class_mode[k], "threads": p.class_threads[k],
+                             "cluster": p.class_cluster[k], "smem": p.class_smem[k],
+                             "levels": [l for l in range(MAX_LEVELS) if p.class_levels[k] >> l & 1],
+                             "launches": p.class_launches[k], "ms": p.class_ms[k],
+                             "cell_iters": p.class_cell_iters[k], "flops": p.class_flops[k],
+                             "bytes": p.class_bytes[k]} for k in range(p.n_classes)]}
 
     def set_launch(self, level, mode, threads=256, cluster=0, gamma=1, nu=1):
         """mlmc_set_launch: fix a level's solver launch (0 block, 1 warp, 2 cluster; <0 default),
@@ -343,6 +358,11 @@ class Context:
         """mlmc_set_solver: mixed-precision scheme of a level (reliable updates or restarted
         refinement) and its FP32 tolerance."""
         _check(lib().mlmc_set_solver(self._h, level, reliable, inner_tol), allow_failed=False)
+
+    def set_schedule(self, schedule):
+        """mlmc_set_schedule: 1 = one work-queue launch per launch shape across the levels of a
+        multilevel batch, 0 = one launch chain per level."""
+        _check(lib().mlmc_set_schedule(self._h, schedule), allow_failed=False)
 
     def ce_info(self, level):
         M = ctypes.c_int32()

@@ -103,6 +103,7 @@ int set_error(int code, const char* what) { return fail(code, what); }
 struct StagePend {
   int stage, launches;
   cudaEvent_t a, b;
+  int cls;  // >= 0: also the time of this profiled work-queue launch shape
 };
 
 // Device results of one enqueued level range, copied to pinned host memory.
@@ -161,6 +162,14 @@ struct mlmc_ctx {
   // last captured multilevel graph and the arguments it was captured with
   cudaGraphExec_t gexec = nullptr;
   std::vector<int64_t> gkey;
+  // work-queue schedule of the multilevel batch (mlmc_set_schedule): the
+  // solves of all levels in one launch per launch shape ("class"), each on a
+  // class stream of its own with its own workspace and work counter
+  static constexpr int kClasses = 2 * MLMC_MAX_LEVELS;
+  int sched = 1;
+  cudaStream_t cst[kClasses] = {};
+  cudaEvent_t class_done[kClasses] = {}, fields_done[MLMC_MAX_LEVELS] = {};
+  Buf sched_cnt, sched_ws[kClasses];
 };
 
 namespace {
@@ -313,14 +322,18 @@ SolveArgs base_args(const mlmc_ctx* c, int level, uint64_t seed, int64_t first) 
 // prec 1 and 2 sample the fields in FP32; prec 0 and 3 in FP64.
 static bool fields_f32(const mlmc_model& md) { return md.prec == 1 || md.prec == 2; }
 
-// Fields of chunk samples [first, first + n) of `level` into the selected work buffers (c->wb).
-int run_fields(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t seed) {
+// Fields of chunk samples [first, first + n) of `level` into the selected work
+// buffers (c->wb), or into g_out when given.
+int run_fields(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t seed, void* g_out = nullptr) {
   const mlmc_model& md = c->model;
   const LevelTable& LT = c->lev[level];
   const bool f32 = fields_f32(md);
   WorkBufs& B = *c->wb;
   if (int e = B.W.ensure(ce_w_bytes_per_sample(LT.m, max_M(c, level), f32, dim_of(md)) * n)) return e;
-  if (int e = B.g.ensure((size_t)n * md.n_layers * cells_of(md, LT.m) * (f32 ? 4 : 8))) return e;
+  if (!g_out) {
+    if (int e = B.g.ensure((size_t)n * md.n_layers * cells_of(md, LT.m) * (f32 ? 4 : 8))) return e;
+    g_out = B.g.p;
+  }
   for (int f = 0; f < c->n_draws; ++f) {  // one draw at a time, W reused
     const PairTable& T = LT.pair[f];
     CeLaunch L;
@@ -342,9 +355,9 @@ int run_fields(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t seed) 
     L.mu_im = L.t_im >= 0 ? md.mu[L.t_im] : 0.0;
     int r;
     if (f32)
-      r = ce_sample_fp32(L, T.s32.as<float>(), T.tw32.p, B.W.p, B.g.as<float>(), c->wst);
+      r = ce_sample_fp32(L, T.s32.as<float>(), T.tw32.p, B.W.p, static_cast<float*>(g_out), c->wst);
     else
-      r = ce_sample_fp64(L, T.s64.as<double>(), T.tw64.p, B.W.p, B.g.as<double>(), c->wst);
+      r = ce_sample_fp64(L, T.s64.as<double>(), T.tw64.p, B.W.p, static_cast<double*>(g_out), c->wst);
     if (r) return fail(MLMC_ERR_CUDA, std::string("field kernels: ") + cudaGetErrorString(cudaGetLastError()));
   }
   return 0;
@@ -443,10 +456,10 @@ struct StageTimer {
     cudaEventCreate(&e1);
     cudaEventRecord(e0, c->wst);
   }
-  void stop(int launches) {
+  void stop(int launches, int cls = -1) {
     if (!c->prof_on) return;
     cudaEventRecord(e1, c->wst);
-    pending().push_back({stage, launches, e0, e1});
+    pending().push_back({stage, launches, e0, e1, cls});
     e0 = e1 = nullptr;
   }
   static std::vector<StagePend>& pending() {
@@ -458,8 +471,12 @@ struct StageTimer {
   static void collect(mlmc_ctx* c) {
     for (auto& p : pending()) {
       float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) c->prof.ms[p.stage] += ms;
+      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+        c->prof.ms[p.stage] += ms;
+        if (p.cls >= 0) c->prof.class_ms[p.cls] += ms;
+      }
       c->prof.launches[p.stage] += p.launches;
+      if (p.cls >= 0) c->prof.class_launches[p.cls] += p.launches;
       cudaEventDestroy(p.a);
       cudaEventDestroy(p.b);
     }
@@ -469,6 +486,30 @@ struct StageTimer {
 
 double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Profiling counters of the field passes of n samples of `level`:
+// transformed points, FFT flops and the algorithmic bytes.
+void count_fields(mlmc_ctx* c, int level, int64_t n) {
+  if (!c->prof_on) return;
+  const mlmc_model& md = c->model;
+  const int m = md.m0 << level;
+  double sumM2 = 0, sumM = 0, fftf = 0, fftb = 0;  // transformed points, FFT flops and bytes per sample
+  const bool d3 = dim_of(md) == 3;
+  const double sc = fields_f32(md) ? 8.0 : 16.0;     // bytes of a complex intermediate value
+  for (const auto& T : c->lev[level].pair) {
+    const double Md = T.M;
+    sumM2 += d3 ? Md * Md * Md : Md * Md;              // points of the row pass
+    sumM += d3 ? Md * Md + Md * m : Md;                // (3-D: middle and last passes) / m
+    fftf += 5.0 * std::log2(Md) * (d3 ? Md * Md * Md + Md * Md * m + Md * m * m : Md * Md + Md * m);
+    // intermediates written once and read once (2-D: M x m; 3-D: M^2 m and M m^2)
+    fftb += 2.0 * sc * (d3 ? Md * Md * m + Md * m * m : Md * m);
+  }
+  fftb += (double)md.n_layers * (double)cells_of(md, m) * (fields_f32(md) ? 4.0 : 8.0);  // fields written
+  c->prof.fft_row_points += (double)n * sumM2;
+  c->prof.fft_col_points += (double)n * sumM * m;
+  c->prof.fft_flops += (double)n * fftf;
+  c->prof.fft_bytes += (double)n * fftb;
 }
 
 // Queue samples first .. first+n-1 of `level` on the context stream: fields,
@@ -484,18 +525,6 @@ int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t see
   const SolvePlan* plan_c = c->tuned_c_ok[level] ? &c->tuned_c[level] : nullptr;
   CUDA_TRY(cudaMemsetAsync(itacc, 0, 3 * sizeof(int64_t), c->wst));
   const int m = md.m0 << level;
-  double sumM2 = 0, sumM = 0, fftf = 0, fftb = 0;  // transformed points, FFT flops and bytes per sample
-  const bool d3 = dim_of(md) == 3;
-  const double sc = fields_f32(md) ? 8.0 : 16.0;     // bytes of a complex intermediate value
-  for (const auto& T : c->lev[level].pair) {
-    const double Md = T.M;
-    sumM2 += d3 ? Md * Md * Md : Md * Md;              // points of the row pass
-    sumM += d3 ? Md * Md + Md * m : Md;                // (3-D: middle and last passes) / m
-    fftf += 5.0 * std::log2(Md) * (d3 ? Md * Md * Md + Md * Md * m + Md * m * m : Md * Md + Md * m);
-    // intermediates written once and read once (2-D: M x m; 3-D: M^2 m and M m^2)
-    fftb += 2.0 * sc * (d3 ? Md * Md * m + Md * m * m : Md * m);
-  }
-  fftb += (double)md.n_layers * (double)cells_of(md, m) * (fields_f32(md) ? 4.0 : 8.0);  // fields written
   for (int64_t c0 = 0; c0 < n; c0 += chunk) {
     const int64_t cn = std::min<int64_t>(chunk, n - c0);
     SolveArgs a = base_args(c, level, seed, first + c0);
@@ -504,12 +533,7 @@ int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t see
       if (int e = run_fields(c, level, first + c0, cn, seed)) return e;
       t.stop(2 * c->n_draws * (int)((cn + 65534) / 65535));
       a.g = c->wb->g.p;
-      if (c->prof_on) {
-        c->prof.fft_row_points += (double)cn * sumM2;
-        c->prof.fft_col_points += (double)cn * sumM * m;
-        c->prof.fft_flops += (double)cn * fftf;
-        c->prof.fft_bytes += (double)cn * fftb;
-      }
+      count_fields(c, level, cn);
     }
     if (plan_c && nc > 0) {  // the fine and the coarse systems, each timed as a stage of its own
       {
@@ -675,20 +699,296 @@ int prepare_level(mlmc_ctx* c, int level, int64_t n) {
   return 0;
 }
 
+// ---- work-queue schedule: one solver launch per launch shape across levels ----
+
+// One range of a level's systems with the plan that solves it.
+struct SchedPart {
+  int level;
+  int64_t b, e;  // systems [b, e) of the level
+  int msys;      // cells per side of the range's first system
+  SolvePlan P;
+};
+
+// The parts that share a launch shape, largest systems first, and the plan
+// their launch takes (workspace strides of the largest part).
+struct SchedClass {
+  SolvePlan P;
+  std::vector<SchedPart> parts;
+  int64_t n_sys = 0;
+};
+
+// Plans that launch the same kernel with the same block, cluster, shared
+// memory and residency can share a launch.
+bool same_shape(const SolvePlan& a, const SolvePlan& b) {
+  return a.warp == b.warp && a.cluster == b.cluster && a.threads == b.threads && a.use_smem == b.use_smem &&
+         a.groups_per_block == b.groups_per_block && a.smem_bytes == b.smem_bytes &&
+         a.cap_blocks_per_sm == b.cap_blocks_per_sm;
+}
+
+// The classes of a multilevel batch of n[l] samples per level.
+int sched_classes(const mlmc_ctx* c, int n_levels, const int64_t* n, std::vector<SchedClass>& out) {
+  const mlmc_model& md = c->model;
+  out.clear();
+  for (int l = 0; l < n_levels; ++l) {
+    if (n[l] <= 0) continue;
+    const int m = md.m0 << l, nc = n_coarse(md, l);
+    SolvePlan P;
+    if (c->tuned_ok[l]) P = c->tuned[l];
+    else if (plan_of(md, m, &P)) return fail(MLMC_ERR_CUDA, "occupancy query failed");
+    SchedPart parts[2];
+    int np = 0;
+    if (c->tuned_c_ok[l] && nc > 0) {
+      parts[np++] = {l, 0, n[l], m, P};
+      parts[np++] = {l, n[l], n[l] * (1 + nc), m / 2, c->tuned_c[l]};
+    } else {
+      parts[np++] = {l, 0, n[l] * (1 + nc), m, P};
+    }
+    for (int k = 0; k < np; ++k) {
+      SchedClass* C = nullptr;
+      for (auto& x : out)
+        if (same_shape(x.P, parts[k].P)) C = &x;
+      if (!C) {
+        if ((int)out.size() == mlmc_ctx::kClasses) return fail(MLMC_ERR_ARG, "too many launch shapes");
+        out.emplace_back();
+        C = &out.back();
+        C->P = parts[k].P;
+      }
+      C->parts.push_back(parts[k]);
+      C->n_sys += parts[k].e - parts[k].b;
+      C->P.ws_stride = std::max(C->P.ws_stride, parts[k].P.ws_stride);
+      C->P.ws64_stride = std::max(C->P.ws64_stride, parts[k].P.ws64_stride);
+      C->P.stage_bytes = std::max(C->P.stage_bytes, parts[k].P.stage_bytes);
+    }
+  }
+  for (auto& C : out)
+    std::stable_sort(C.parts.begin(), C.parts.end(),
+                     [](const SchedPart& x, const SchedPart& y) { return x.msys > y.msys; });
+  return 0;
+}
+
+constexpr size_t kSchedBudget = size_t(24) << 30;  // bytes of whole-level fields and outputs
+
+// Whether this multilevel batch takes the work-queue schedule: 2-D, FP64 or
+// FP32-multigrid precision, and the fields of every level's whole range
+// within kSchedBudget.
+bool sched_usable(const mlmc_ctx* c, int n_levels, const int64_t* n) {
+  const mlmc_model& md = c->model;
+  if (!c->sched || dim_of(md) == 3 || (md.prec != 0 && md.prec != 1)) return false;
+  double bytes = 0;
+  for (int l = 0; l < n_levels; ++l) {
+    if (n[l] <= 0) continue;
+    const int m = md.m0 << l;
+    bytes += (double)n[l] * (1 + n_coarse(md, l)) * 12.0;
+    if (md.k_kind == 1) bytes += (double)n[l] * md.n_layers * cells_of(md, m) * (fields_f32(md) ? 4.0 : 8.0);
+  }
+  return bytes <= (double)kSchedBudget;
+}
+
+// Allocate, outside any stream capture, what the work-queue schedule of this
+// batch touches: per level one chunk of embedding intermediates, the fields
+// and the per-system outputs of the whole range, the level's results; per
+// class a workspace and a work counter, a stream and an event.
+int prepare_sched(mlmc_ctx* c, int n_levels, const int64_t* n, const std::vector<SchedClass>& cls) {
+  const mlmc_model& md = c->model;
+  const bool f32 = fields_f32(md);
+  for (int l = 0; l < n_levels; ++l) {
+    if (n[l] <= 0) continue;
+    const int m = md.m0 << l;
+    const int64_t n_sys = n[l] * (1 + n_coarse(md, l));
+    auto& S = c->slot[l];
+    WorkBufs& B = S.wb;
+    if (md.k_kind == 1) {
+      const int64_t cn = std::min<int64_t>(n[l], chunk_samples(c, l));
+      if (int e = B.W.ensure(ce_w_bytes_per_sample(m, max_M(c, l), f32, dim_of(md)) * cn)) return e;
+      if (int e = B.g.ensure((size_t)n[l] * md.n_layers * cells_of(md, m) * (f32 ? 4 : 8))) return e;
+    }
+    if (int e = B.qsys.ensure((size_t)n_sys * 8)) return e;
+    if (int e = B.itsys.ensure((size_t)n_sys * 4)) return e;
+    if (int e = S.qf.ensure((size_t)n[l] * 8)) return e;
+    if (int e = S.qc.ensure((size_t)n[l] * 8)) return e;
+    if (int e = S.qg.ensure((size_t)n[l] * 8)) return e;
+    if (int e = S.sums.ensure(256 + reduce_ws_bytes())) return e;
+    if (int e = S.itacc.ensure(3 * sizeof(int64_t))) return e;
+    if (!c->fields_done[l] && cudaEventCreateWithFlags(&c->fields_done[l], cudaEventDisableTiming) != cudaSuccess)
+      return fail(MLMC_ERR_CUDA, "event");
+  }
+  if (int e = c->sched_cnt.ensure(mlmc_ctx::kClasses * sizeof(unsigned long long))) return e;
+  if (solve_list_prepare())
+    return fail(MLMC_ERR_CUDA, std::string("list kernel attributes: ") + cudaGetErrorString(last_launch_error()));
+  for (size_t k = 0; k < cls.size(); ++k) {
+    const size_t ws = launch_size(c, cls[k].P, cls[k].n_sys).ws;
+    if (ws)
+      if (int e = c->sched_ws[k].ensure(ws)) return e;
+    if (!c->cst[k] && cudaStreamCreateWithFlags(&c->cst[k], cudaStreamNonBlocking) != cudaSuccess)
+      return fail(MLMC_ERR_CUDA, "class stream");
+    if (!c->class_done[k] && cudaEventCreateWithFlags(&c->class_done[k], cudaEventDisableTiming) != cudaSuccess)
+      return fail(MLMC_ERR_CUDA, "event");
+  }
+  return 0;
+}
+
+// Queue a multilevel batch in the work-queue schedule: (A) each level's
+// fields, chunk by chunk, on its level stream; (B) per class, after the
+// fields of its levels, one persistent solver launch over all its parts
+// (further launches only past kMaxSolveItems parts); (C) per level, after
+// its classes, the gather, the level reduction and the copy of its sums to
+// host memory, joined into the context stream.
+int enqueue_sched(mlmc_ctx* c, int n_levels, const int64_t* first, const int64_t* n, uint64_t seed,
+                  const std::vector<SchedClass>& cls, int* prof_cls) {
+  const mlmc_model& md = c->model;
+  const bool f32 = fields_f32(md);
+  // with stage profiling on, everything runs in order on the context stream
+  // (each launch's event time its own); events and waits then order nothing
+  const bool serial = c->prof_on;
+  if (cudaEventRecord(c->fork, c->st) != cudaSuccess) return fail(MLMC_ERR_CUDA, "fork event");
+  for (int l = 0; l < n_levels; ++l) {
+    if (n[l] <= 0) continue;
+    auto& S = c->slot[l];
+    const cudaStream_t ls = serial ? c->st : c->lst[l];
+    if (cudaStreamWaitEvent(ls, c->fork, 0) != cudaSuccess) return fail(MLMC_ERR_CUDA, "fork wait");
+    UseBufs use(c, &S.wb, ls);
+    CUDA_TRY(cudaMemsetAsync(S.itacc.p, 0, 3 * sizeof(int64_t), ls));
+    if (md.k_kind == 1) {
+      const int m = md.m0 << l;
+      const size_t gps = (size_t)md.n_layers * cells_of(md, m) * (f32 ? 4 : 8);
+      const int64_t chunk = chunk_samples(c, l);
+      for (int64_t c0 = 0; c0 < n[l]; c0 += chunk) {
+        const int64_t cn = std::min<int64_t>(chunk, n[l] - c0);
+        StageTimer t(c, 0);
+        if (int e = run_fields(c, l, first[l] + c0, cn, seed, S.wb.g.as<unsigned char>() + (size_t)c0 * gps))
+          return e;
+        t.stop(2 * c->n_draws * (int)((cn + 65534) / 65535));
+        count_fields(c, l, cn);
+      }
+    }
+    CUDA_TRY(cudaEventRecord(c->fields_done[l], ls));
+  }
+  unsigned long long* cnt = c->sched_cnt.as<unsigned long long>();
+  for (size_t k = 0; k < cls.size(); ++k) {
+    const SchedClass& C = cls[k];
+    const cudaStream_t cs = serial ? c->st : c->cst[k];
+    UseBufs use(c, c->wb, cs);
+    bool waited[MLMC_MAX_LEVELS] = {};
+    for (const auto& p : C.parts)
+      if (!waited[p.level]) {
+        CUDA_TRY(cudaStreamWaitEvent(cs, c->fields_done[p.level], 0));
+        waited[p.level] = true;
+      }
+    for (size_t p0 = 0; p0 < C.parts.size(); p0 += kMaxSolveItems) {
+      SolveList L;
+      std::memset(&L, 0, sizeof(L));
+      L.next = cnt + k;
+      int64_t total = 0;
+      for (size_t i = p0; i < C.parts.size() && L.n < kMaxSolveItems; ++i) {
+        const SchedPart& q = C.parts[i];
+        const auto& S = c->slot[q.level];
+        SolveArgs a = base_args(c, q.level, seed, first[q.level]);
+        a.n_samples = n[q.level];
+        a.n_coarse = n_coarse(md, q.level);
+        if (md.k_kind == 1) a.g = S.wb.g.p;
+        a.q = S.wb.qsys.as<double>();
+        a.iters = S.wb.itsys.as<int32_t>();
+        a.sys_begin = q.b;
+        a.sys_end = q.e;
+        solve_apply_plan(a, q.P);
+        a.ws_stride = C.P.ws_stride;
+        a.ws64_stride = C.P.ws64_stride;
+        a.ws = !C.P.use_smem ? c->sched_ws[k].as<unsigned char>() : nullptr;
+        a.ws64 = C.P.use_smem && C.P.ws64_stride ? c->sched_ws[k].as<unsigned char>() : nullptr;
+        L.start[L.n] = total;
+        L.a[L.n++] = a;
+        total += q.e - q.b;
+      }
+      L.start[L.n] = total;
+      CUDA_TRY(cudaMemsetAsync(cnt + k, 0, sizeof(unsigned long long), cs));
+      const int64_t nb = launch_size(c, C.P, total).blocks;
+      StageTimer t(c, 1);
+      if (solve_launch_list(L, md.prec, C.P, (int)nb, cs))
+        return fail(MLMC_ERR_CUDA, std::string("solve list launch: ") + cudaGetErrorString(last_launch_error()));
+      t.stop(1, prof_cls ? prof_cls[k] : -1);
+    }
+    CUDA_TRY(cudaEventRecord(c->class_done[k], cs));
+  }
+  for (int l = 0; l < n_levels; ++l) {
+    if (n[l] <= 0) continue;
+    auto& S = c->slot[l];
+    const cudaStream_t ls = serial ? c->st : c->lst[l];
+    UseBufs use(c, &S.wb, ls);
+    for (size_t k = 0; k < cls.size(); ++k) {
+      bool has = false;
+      for (const auto& p : cls[k].parts) has = has || p.level == l;
+      if (has) CUDA_TRY(cudaStreamWaitEvent(ls, c->class_done[k], 0));
+    }
+    const int m = md.m0 << l;
+    const int nc = n_coarse(md, l);
+    double* qf = S.qf.as<double>();
+    double* qc = S.qc.as<double>();
+    double* qg = S.qg.as<double>();
+    int64_t* itacc = S.itacc.as<int64_t>();
+    StageTimer t(c, 2);
+    if (gather_launch(S.wb.qsys.as<double>(), S.wb.itsys.as<int32_t>(), n[l], nc, md.cgv, cells_of(md, m),
+                      cells_of(md, m / 2), qf, qc, qg, nullptr, itacc, ls))
+      return fail(MLMC_ERR_CUDA, "gather kernel");
+    unsigned char* sums_dev = S.sums.as<unsigned char>();
+    if (reduce_launch(qf, qc, qg, n[l], md.cgv != 0, itacc, reinterpret_cast<LevelSumsDev*>(sums_dev),
+                      sums_dev + 256, ls))
+      return fail(MLMC_ERR_CUDA, "reduce kernel");
+    t.stop(3);
+    if (c->prof_on) {
+      c->prof.cells += (double)n[l] * ((double)cells_of(md, m) + nc * (double)cells_of(md, m / 2));
+      c->prof.samples += (double)n[l];
+    }
+    CUDA_TRY(cudaMemcpyAsync(&c->host[l].s, sums_dev, sizeof(LevelSumsDev), cudaMemcpyDeviceToHost, ls));
+    CUDA_TRY(cudaMemcpyAsync(c->host[l].itc, itacc, sizeof(c->host[l].itc), cudaMemcpyDeviceToHost, ls));
+    CUDA_TRY(cudaEventRecord(c->lev_done[l], ls));
+    CUDA_TRY(cudaStreamWaitEvent(c->st, c->lev_done[l], 0));
+  }
+  return 0;
+}
+
 // All levels' ranges queued back to back with one host synchronisation;
 // with use_graph the queue is captured once into a CUDA graph (kept for the
 // next call with the same arguments) and launched as one graph.
 int multilevel_impl(mlmc_ctx* c, int n_levels, const int64_t* first, const int64_t* n, uint64_t seed,
                     bool use_graph, mlmc_level_sums* sums) {
-  for (int l = 0; l < n_levels; ++l)
-    if (n[l] > 0)
-      if (int e = prepare_level(c, l, n[l])) return e;
+  std::vector<SchedClass> cls;
+  const bool sched = sched_usable(c, n_levels, n);
+  if (sched) {
+    if (int e = sched_classes(c, n_levels, n, cls)) return e;
+    if (int e = prepare_sched(c, n_levels, n, cls)) return e;
+  } else {
+    for (int l = 0; l < n_levels; ++l)
+      if (n[l] > 0)
+        if (int e = prepare_level(c, l, n[l])) return e;
+  }
   // the levels run side by side, each on its own stream with its own work
   // buffers, forked from and joined back into the context stream; with
   // stage profiling on they run one after another on the context stream, so
   // that every stage's CUDA-event time is its own
   const bool side_by_side = !c->prof_on;
+  // profiled work-queue launches: their launch shape's slot in the counters
+  int prof_cls[mlmc_ctx::kClasses];
+  for (size_t k = 0; k < cls.size(); ++k) {
+    prof_cls[k] = -1;
+    if (!c->prof_on) continue;
+    const SolvePlan& P = cls[k].P;
+    const int mode = P.cluster ? 2 : P.warp == 2 ? 3 : P.warp ? 1 : 0;
+    mlmc_profile_stats& S = c->prof;
+    for (int j = 0; j < S.n_classes; ++j)
+      if (S.class_mode[j] == mode && S.class_threads[j] == P.threads && S.class_cluster[j] == P.cluster &&
+          S.class_smem[j] == P.use_smem)
+        prof_cls[k] = j;
+    if (prof_cls[k] < 0 && S.n_classes < MLMC_PROFILE_CLASSES) {
+      const int j = S.n_classes++;
+      S.class_mode[j] = mode;
+      S.class_threads[j] = P.threads;
+      S.class_cluster[j] = P.cluster;
+      S.class_smem[j] = P.use_smem;
+      prof_cls[k] = j;
+    }
+  }
   auto enqueue_all = [&]() -> int {
+    if (sched) return enqueue_sched(c, n_levels, first, n, seed, cls, prof_cls);
     if (side_by_side && cudaEventRecord(c->fork, c->st) != cudaSuccess) return fail(MLMC_ERR_CUDA, "fork event");
     for (int l = 0; l < n_levels; ++l) {
       if (n[l] <= 0) continue;
@@ -711,7 +1011,8 @@ int multilevel_impl(mlmc_ctx* c, int n_levels, const int64_t* first, const int64
   // stage timing needs events between the launches, so profiling runs ungraphed
   const bool graph = use_graph && c->st != nullptr && !c->prof_on;
   if (graph) {
-    std::vector<int64_t> key = {(int64_t)n_levels, (int64_t)seed, (int64_t)g_alloc_generation.load()};
+    std::vector<int64_t> key = {(int64_t)n_levels, (int64_t)seed, (int64_t)g_alloc_generation.load(),
+                                (int64_t)sched};
     for (int l = 0; l < n_levels; ++l) {
       key.push_back(c->tuned_ok[l] ? ((int64_t)c->tuned[l].nu << 28) + ((int64_t)c->tuned[l].gamma << 24) +
                                          ((int64_t)c->tuned[l].threads << 16) +
@@ -768,6 +1069,19 @@ int multilevel_impl(mlmc_ctx* c, int n_levels, const int64_t* first, const int64
     CUDA_TRY(cudaStreamSynchronize(c->st));
     if (c->prof_on) StageTimer::collect(c);
   }
+  if (sched && c->prof_on)  // the work of each profiled work-queue launch shape
+    for (size_t k = 0; k < cls.size(); ++k) {
+      const int j = prof_cls[k];
+      if (j < 0) continue;
+      for (const SchedPart& q : cls[k].parts) {
+        const HostLevel& h = c->host[q.level];
+        const double ci = (double)(q.b == 0 ? h.itc[1] : 0) + (double)(q.e > n[q.level] ? h.itc[2] : 0);
+        c->prof.class_levels[j] |= 1 << q.level;
+        c->prof.class_cell_iters[j] += ci;
+        c->prof.class_flops[j] += ci * flops_per_cell_iter(c->model.prec, q.P.gamma, q.P.nu, q.P.nu_coarse);
+        c->prof.class_bytes[j] += ci * bytes_per_cell_iter(c->model.prec, 2, q.P.gamma, q.P.nu, q.P.nu_coarse);
+      }
+    }
   int rc = MLMC_OK;
   for (int l = 0; l < n_levels; ++l) {
     std::memset(&sums[l], 0, sizeof(sums[l]));
@@ -1003,6 +1317,14 @@ void mlmc_destroy(mlmc_ctx* c) {
     if (c->lst[l]) cudaStreamDestroy(c->lst[l]);
     if (c->lev_done[l]) cudaEventDestroy(c->lev_done[l]);
   }
+  for (int k = 0; k < mlmc_ctx::kClasses; ++k) {
+    if (c->cst[k]) cudaStreamDestroy(c->cst[k]);
+    if (c->class_done[k]) cudaEventDestroy(c->class_done[k]);
+    c->sched_ws[k].release();
+  }
+  for (int l = 0; l < MLMC_MAX_LEVELS; ++l)
+    if (c->fields_done[l]) cudaEventDestroy(c->fields_done[l]);
+  c->sched_cnt.release();
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->host) cudaFreeHost(c->host);
@@ -1517,6 +1839,13 @@ int mlmc_set_launch_coarse(mlmc_ctx* c, int level, int32_t mode, int32_t threads
   }
   c->tuned_c[level] = P;
   c->tuned_c_ok[level] = true;
+  return 0;
+}
+
+int mlmc_set_schedule(mlmc_ctx* c, int32_t schedule) {
+  if (!c) return fail(MLMC_ERR_ARG, "null context");
+  if (schedule != 0 && schedule != 1) return fail(MLMC_ERR_ARG, "schedule must be 0 or 1");
+  c->sched = schedule;
   return 0;
 }
 

@@ -127,6 +127,22 @@ struct SolvePlan {
   int reliable;          // mixed precision: reliable updates (inner_tol = residual drop between updates)
 };
 
+// The work of one solver launch: items (ranges of systems, each with its own
+// arguments: level, fields, outputs, multigrid and refinement settings) laid
+// end to end.  Work index w < start[n] is system a[k].sys_begin + (w -
+// start[k]) of the item k with start[k] <= w < start[k + 1]; the groups take
+// work indices from the counter *next (zero at launch).  All items of a
+// launch share its launch shape and workspace (ws, ws_stride, ws64,
+// ws64_stride, use_smem and stage_bytes of item 0, sized for the largest
+// item).  Passed by value as the kernel parameter (about 5.4 KB).
+constexpr int kMaxSolveItems = 12;
+struct SolveList {
+  int n;
+  unsigned long long* next;
+  int64_t start[kMaxSolveItems + 1];
+  SolveArgs a[kMaxSolveItems];
+};
+
 size_t solve_ws_bytes(int m, int prec);
 int solve_plan(int m, int prec, SolvePlan* plan);
 // An explicit plan: mode 0 block of `threads`, 1 warp, 2 cluster of `cluster` blocks.
@@ -138,6 +154,14 @@ int solve_plan_candidates(int m, int prec, SolvePlan* out, int max_out);
 // workspace (plan.use_smem == 0) must hold groups * ws_stride bytes.
 int64_t solve_groups(const SolvePlan& plan, int64_t n_sys, int nsm, int64_t max_groups_cap, int64_t* n_blocks);
 int solve_launch(const SolveArgs& a, int prec, const SolvePlan& plan, int n_blocks, cudaStream_t st);
+// Write a plan's launch settings (workspace layout, multigrid and refinement
+// settings) into an item's arguments.
+void solve_apply_plan(SolveArgs& a, const SolvePlan& plan);
+// One launch over the items of L with plan's shape (2-D, prec 0 or 1; the
+// caller has applied each item's own plan settings); -1 for other precisions.
+int solve_launch_list(const SolveList& L, int prec, const SolvePlan& plan, int n_blocks, cudaStream_t st);
+// Shared-memory limits of the list kernels (call before the first list launch, outside stream capture).
+int solve_list_prepare();
 // The same for the 3-D seven-point systems (solve3.cu; prec 0 or 1; modes 0 block, 2 cluster).
 size_t solve3_ws_bytes(int m, int prec);
 int solve3_plan(int m, int prec, SolvePlan* plan);

@@ -1385,6 +1385,99 @@ __global__ void __launch_bounds__(MODE == 1 || MODE == 3 ? 32 * kWarpsPerBlock :
   }
 }
 
+// The same solver over the items of a SolveList: one persistent launch of a
+// launch shape across the levels of an estimate round.  The systems form one
+// work queue; each group (warp, block or cluster) takes the next system from
+// the counter *L.next (a fetch-and-add: no group waits on another), so a group
+// that drew long solves takes fewer of them and the launch ends when the
+// queue is empty.  The caller lays the items out largest systems first, so the
+// last systems handed out are the short ones.  A group copies its current
+// item's arguments into shared memory when the item changes.
+template <int PREC, int MODE>
+__global__ void __launch_bounds__(MODE == 1 || MODE == 3 ? 32 * kWarpsPerBlock : kMaxThreads,
+                                  MODE == 1 ? 5 : MODE == 3 ? 4 : 2)
+    solve_list_kernel(const __grid_constant__ SolveList L) {
+  using T = typename SolverTypes<PREC>::T;
+  using F = typename SolverTypes<PREC>::F;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int kGroups = MODE == 1 || MODE == 3 ? kWarpsPerBlock : 1;
+  __shared__ GroupState<T, F> gstate[kGroups];
+  __shared__ T red[MODE == 1 || MODE == 3 ? 1 : 132];
+  __shared__ double red64[MODE == 1 || MODE == 3 ? 1 : 132];
+  __shared__ __align__(16) SolveArgs args[kGroups];
+  __shared__ long long wq[2];  // block and cluster groups: the taken work index (two slots, alternating)
+  const int64_t total = L.start[L.n];
+  const SolveArgs& a0 = L.a[0];  // the launch's workspace layout
+  int par = 0, m_prev = -1;
+  const int gid = MODE == 1 || MODE == 3 ? (int)(threadIdx.x >> 5) : 0;
+  int cur = -1;  // item whose arguments args[gid] hold
+  // the item of work index w and its system; refreshes the group's copy
+  auto take = [&](const auto& g, int64_t w, int64_t& sys) -> const SolveArgs& {
+    int k = 0;
+    while (k + 1 < L.n && w >= L.start[k + 1]) ++k;
+    if (k != cur) {
+      g.lsync();  // nobody still reads the previous copy
+      const unsigned* src = reinterpret_cast<const unsigned*>(&L.a[k]);
+      unsigned* dst = reinterpret_cast<unsigned*>(&args[gid]);
+      for (int t = g.lrank(); t < (int)(sizeof(SolveArgs) / 4); t += g.lsize()) dst[t] = src[t];
+      g.lsync();
+      cur = k;
+    }
+    sys = args[gid].sys_begin + (w - L.start[k]);
+    return args[gid];
+  };
+  if (MODE == 2) {
+    __shared__ double cl_part[2];
+    cg::cluster_group cl = cg::this_cluster();
+    const ClusterGroup g{cl.num_blocks(), cl.block_rank(), cl_part};
+    const int64_t cid = blockIdx.x / g.nblk;
+    unsigned char* base = a0.ws + (size_t)cid * a0.ws_stride;
+    unsigned char* stage = a0.stage_bytes ? smem_raw : nullptr;
+    for (int it = 0;; ++it) {
+      // block 0 of the cluster takes the index; the others read it from its
+      // shared memory after the cluster barrier (the slot it overwrites two
+      // turns later was read before the barrier of the turn in between)
+      if (g.brank == 0 && threadIdx.x == 0) wq[it & 1] = (long long)atomicAdd(L.next, 1ull);
+      cl.sync();
+      const int64_t w = *cl.map_shared_rank(&wq[it & 1], 0);
+      if (w >= total) break;
+      int64_t sys;
+      const SolveArgs& a = take(g, w, sys);
+      solve_one<PREC>(g, a, sys, base, gstate[0], red, red64, par, m_prev, nullptr, stage);
+    }
+    cl.sync();  // no block leaves while others may still read its shared memory
+    return;
+  }
+  const size_t slot = (size_t)blockIdx.x * kGroups + gid;
+  unsigned char* base = a0.use_smem ? smem_raw + (size_t)gid * a0.ws_stride : a0.ws + slot * a0.ws_stride;
+  unsigned char* base64 = a0.ws64_stride ? a0.ws64 + slot * a0.ws64_stride : nullptr;
+  for (int it = 0;; ++it) {
+    int64_t sys;
+    if (MODE == 1 || MODE == 3) {
+      long long w = 0;
+      if ((threadIdx.x & 31) == 0) w = (long long)atomicAdd(L.next, 1ull);
+      w = __shfl_sync(0xffffffffu, w, 0);
+      if (w >= total) break;
+      const SolveArgs& a = take(WarpGroup(), w, sys);
+      if constexpr (MODE == 3 && PREC == 1) {
+        const int msys = sys < a.n_samples ? a.m : a.m >> 1;
+        if (msys == kTinyM) {
+          solve_one_tiny(WarpGroup(), a, sys, base, gstate[gid], m_prev);
+          continue;
+        }
+      }
+      solve_one<PREC>(WarpGroup(), a, sys, base, gstate[gid], red, red64, par, m_prev, base64, nullptr);
+    } else {
+      if (threadIdx.x == 0) wq[it & 1] = (long long)atomicAdd(L.next, 1ull);
+      __syncthreads();
+      const int64_t w = wq[it & 1];
+      if (w >= total) break;
+      const SolveArgs& a = take(BlockGroup(), w, sys);
+      solve_one<PREC>(BlockGroup(), a, sys, base, gstate[gid], red, red64, par, m_prev, base64, nullptr);
+    }
+  }
+}
+
 size_t solve_ws_bytes(int m, int prec) { return ws_layout(m, prec); }
 
 static const size_t kSmemCap = 110 * 1024;
@@ -1530,8 +1623,8 @@ int solve_plan_candidates(int m, int prec, SolvePlan* out, int max_out) {
   return k;
 }
 
-int solve_launch(const SolveArgs& a, int prec, const SolvePlan& P, int n_blocks, cudaStream_t st) {
-  SolveArgs b = a;
+// The plan's launch settings written into an item's arguments.
+static void apply_plan(SolveArgs& b, const SolvePlan& P) {
   b.use_smem = P.use_smem;
   b.ws_stride = P.ws_stride;
   b.ws64_stride = P.ws64_stride;
@@ -1541,44 +1634,105 @@ int solve_launch(const SolveArgs& a, int prec, const SolvePlan& P, int n_blocks,
   b.mg_nu_coarse = P.nu_coarse;
   b.inner_tol = P.inner_tol;
   b.reliable = P.reliable;
+}
+
+// Launch configuration of a plan.
+struct LaunchCfg {
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[1];
+  int mode;
+  LaunchCfg(const SolvePlan& P, int n_blocks, cudaStream_t st) {
+    cfg = {};
+    cfg.gridDim = dim3(n_blocks);  // cluster plans: a multiple of the cluster size
+    cfg.blockDim = dim3(P.threads);
+    cfg.dynamicSmemBytes = P.smem_bytes;
+    cfg.stream = st;
+    if (P.cluster) {
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = P.cluster;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+    }
+    mode = P.cluster ? 2 : P.warp == 2 ? 3 : P.warp ? 1 : 0;
+  }
+};
+
+void solve_apply_plan(SolveArgs& a, const SolvePlan& P) { apply_plan(a, P); }
+
+int solve_launch(const SolveArgs& a, int prec, const SolvePlan& P, int n_blocks, cudaStream_t st) {
+  SolveArgs b = a;
+  apply_plan(b, P);
   // every plan goes through cudaLaunchKernelEx, whose return value is this
   // launch's own status (an error left pending by earlier work of the caller
   // is neither reported nor cleared here)
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  cfg.gridDim = dim3(n_blocks);  // cluster plans: a multiple of the cluster size
-  cfg.blockDim = dim3(P.threads);
-  cfg.dynamicSmemBytes = P.smem_bytes;
-  cfg.stream = st;
-  if (P.cluster) {
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = P.cluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-  }
-  const int mode = P.cluster ? 2 : P.warp == 2 ? 3 : P.warp ? 1 : 0;
+  LaunchCfg C(P, n_blocks, st);
+  cudaLaunchConfig_t* cfg = &C.cfg;
   cudaError_t e = cudaErrorInvalidValue;
-  if (mode == 3) {
-    if (prec == 1) e = cudaLaunchKernelEx(&cfg, solve_kernel<1, 3>, b);
+  if (C.mode == 3) {
+    if (prec == 1) e = cudaLaunchKernelEx(cfg, solve_kernel<1, 3>, b);
     last_launch_error() = e;
     return e == cudaSuccess ? 0 : -1;
   }
-  switch (prec * 3 + mode) {
-    case 0: e = cudaLaunchKernelEx(&cfg, solve_kernel<0, 0>, b); break;
-    case 1: e = cudaLaunchKernelEx(&cfg, solve_kernel<0, 1>, b); break;
-    case 2: e = cudaLaunchKernelEx(&cfg, solve_kernel<0, 2>, b); break;
-    case 3: e = cudaLaunchKernelEx(&cfg, solve_kernel<1, 0>, b); break;
-    case 4: e = cudaLaunchKernelEx(&cfg, solve_kernel<1, 1>, b); break;
-    case 5: e = cudaLaunchKernelEx(&cfg, solve_kernel<1, 2>, b); break;
-    case 6: e = cudaLaunchKernelEx(&cfg, solve_kernel<2, 0>, b); break;
-    case 7: e = cudaLaunchKernelEx(&cfg, solve_kernel<2, 1>, b); break;
-    case 8: e = cudaLaunchKernelEx(&cfg, solve_kernel<2, 2>, b); break;
-    case 9: e = cudaLaunchKernelEx(&cfg, solve_kernel<3, 0>, b); break;
-    case 10: e = cudaLaunchKernelEx(&cfg, solve_kernel<3, 1>, b); break;
-    case 11: e = cudaLaunchKernelEx(&cfg, solve_kernel<3, 2>, b); break;
+  switch (prec * 3 + C.mode) {
+    case 0: e = cudaLaunchKernelEx(cfg, solve_kernel<0, 0>, b); break;
+    case 1: e = cudaLaunchKernelEx(cfg, solve_kernel<0, 1>, b); break;
+    case 2: e = cudaLaunchKernelEx(cfg, solve_kernel<0, 2>, b); break;
+    case 3: e = cudaLaunchKernelEx(cfg, solve_kernel<1, 0>, b); break;
+    case 4: e = cudaLaunchKernelEx(cfg, solve_kernel<1, 1>, b); break;
+    case 5: e = cudaLaunchKernelEx(cfg, solve_kernel<1, 2>, b); break;
+    case 6: e = cudaLaunchKernelEx(cfg, solve_kernel<2, 0>, b); break;
+    case 7: e = cudaLaunchKernelEx(cfg, solve_kernel<2, 1>, b); break;
+    case 8: e = cudaLaunchKernelEx(cfg, solve_kernel<2, 2>, b); break;
+    case 9: e = cudaLaunchKernelEx(cfg, solve_kernel<3, 0>, b); break;
+    case 10: e = cudaLaunchKernelEx(cfg, solve_kernel<3, 1>, b); break;
+    case 11: e = cudaLaunchKernelEx(cfg, solve_kernel<3, 2>, b); break;
     default: break;
+  }
+  last_launch_error() = e;
+  return e == cudaSuccess ? 0 : -1;
+}
+
+// Let the list kernels take the plans' dynamic shared memory (outside any
+// stream capture; once per process and device is enough, repeating is harmless).
+int solve_list_prepare() {
+  const int cap = (int)kSmemCap;
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* f) {
+    const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    if (r != cudaSuccess) e = r;
+  };
+  set((const void*)solve_list_kernel<0, 0>);
+  set((const void*)solve_list_kernel<0, 1>);
+  set((const void*)solve_list_kernel<0, 2>);
+  set((const void*)solve_list_kernel<1, 0>);
+  set((const void*)solve_list_kernel<1, 1>);
+  set((const void*)solve_list_kernel<1, 2>);
+  set((const void*)solve_list_kernel<1, 3>);
+  last_launch_error() = e;
+  return e == cudaSuccess ? 0 : -1;
+}
+
+int solve_launch_list(const SolveList& L, int prec, const SolvePlan& P, int n_blocks, cudaStream_t st) {
+  LaunchCfg C(P, n_blocks, st);
+  cudaLaunchConfig_t* cfg = &C.cfg;
+  cudaError_t e = cudaErrorInvalidValue;
+  if (prec == 1) {
+    switch (C.mode) {
+      case 0: e = cudaLaunchKernelEx(cfg, solve_list_kernel<1, 0>, L); break;
+      case 1: e = cudaLaunchKernelEx(cfg, solve_list_kernel<1, 1>, L); break;
+      case 2: e = cudaLaunchKernelEx(cfg, solve_list_kernel<1, 2>, L); break;
+      case 3: e = cudaLaunchKernelEx(cfg, solve_list_kernel<1, 3>, L); break;
+      default: break;
+    }
+  } else if (prec == 0) {
+    switch (C.mode) {
+      case 0: e = cudaLaunchKernelEx(cfg, solve_list_kernel<0, 0>, L); break;
+      case 1: e = cudaLaunchKernelEx(cfg, solve_list_kernel<0, 1>, L); break;
+      case 2: e = cudaLaunchKernelEx(cfg, solve_list_kernel<0, 2>, L); break;
+      default: break;
+    }
   }
   last_launch_error() = e;
   return e == cudaSuccess ? 0 : -1;

@@ -1,0 +1,108 @@
+"""The work-queue schedule of the multilevel batch (one persistent solver
+launch per launch shape across the levels, systems taken from an atomic
+work counter) against the per-level schedule: the level sums of Eq. 3.6 and
+Eq. 4.2 are bit-identical, with and without the CUDA graph, when levels share
+a launch (warp, register and block plans, global and shared workspaces,
+fine and coarse systems of different levels in one launch) and when a level
+runs its own cluster launch."""
+import pytest
+
+import workloads
+from tests.gpu_util import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def both_schedules(pk, torch, d, n, seed, first, setup=None):
+    out = {}
+    stream = torch.cuda.Stream()
+    with pk.Context(d, stream=stream) as ctx:
+        if setup:
+            setup(ctx)
+        for sched in (0, 1):
+            ctx.set_schedule(sched)
+            out[sched] = [ctx.multilevel_batch(n, seed, first=first, use_graph=g) for g in (False, True, True)]
+        ref = [ctx.level_batch(l, n[l], seed, first=first[l]) for l in range(len(n)) if n[l] > 0]
+    return out, ref
+
+
+def assert_same(pk, out, ref, n):
+    keys = ("n", "n_failed", "iters_total") + pk.SUM_FIELDS
+    for sched in (0, 1):
+        for call in out[sched]:
+            for l in range(len(n)):
+                for key in keys:
+                    assert call[l][key] == out[0][0][l][key], (sched, l, key)
+    k = 0
+    for l in range(len(n)):
+        if n[l] == 0:
+            continue
+        for key in keys:
+            assert out[1][0][l][key] == ref[k][key], (l, key)
+        assert out[1][0][l]["n"] == n[l] and out[1][0][l]["n_failed"] == 0
+        k += 1
+
+
+def test_shared_launches_mixed_cgv():
+    # levels 0..3 (m = 16 .. 128) of the two-layer mixed CGV workload, with
+    # plans that put several levels into one launch: the 16 x 16 register
+    # path for level 0 and level 1's coarse systems, blocks of 256 with the
+    # workspace in shared memory for the 32 x 32 systems of levels 1 (fine)
+    # and 2 (coarse), blocks of 512 with global workspaces for level 2's fine
+    # and all of level 3's systems
+    torch, pk = need_gpu()
+    d = workloads.workload("lognormal_2layer_cgv_16to512", L=3)
+    n = [2500, 300, 60, 9]
+    first = [3, 0, 17, 4]
+
+    def setup(ctx):
+        ctx.set_launch(0, 3, 0, 0, 1, 2)
+        ctx.set_launch(1, 0, 256, 0, 1, 1)
+        ctx.set_launch_coarse(1, 3, 0, 0, 1, 2)
+        ctx.set_launch(2, 0, 512, 0, 1, 2)
+        ctx.set_launch_coarse(2, 0, 256, 0, 1, 1)
+        ctx.set_launch(3, 0, 512, 0, 1, 2)
+        ctx.set_solver(3, 1, 1e-3)
+
+    out, ref = both_schedules(pk, torch, d, n, 9, first, setup)
+    assert_same(pk, out, ref, n)
+
+
+def test_autotuned_plans_and_empty_level():
+    torch, pk = need_gpu()
+    d = workloads.workload("lognormal_2layer_cgv_16to512", L=4)
+    n = [1200, 0, 40, 12, 5]
+    first = [0, 0, 2, 0, 1]
+    out, ref = both_schedules(pk, torch, d, n, 5, first, lambda ctx: ctx.autotune(seed=1))
+    assert_same(pk, out, ref, n)
+
+
+def test_fp64_plain_warp_block_and_cluster():
+    # FP64 without CGV: warp plans at m = 16, 32 share a launch; level 3 runs
+    # a cluster of four blocks per system, level 2 blocks of 256
+    torch, pk = need_gpu()
+    d = workloads.workload("lognormal_2layer_16to256", L=3)
+    n = [700, 150, 30, 6]
+    first = [1, 2, 3, 4]
+
+    def setup(ctx):
+        ctx.set_launch(0, 1, 0, 0, 1, 1)
+        ctx.set_launch(1, 1, 0, 0, 1, 2)
+        ctx.set_launch(2, 0, 256, 0, 1, 1)
+        ctx.set_launch(3, 2, 512, 4, 1, 2)
+
+    out, ref = both_schedules(pk, torch, d, n, 13, first, setup)
+    assert_same(pk, out, ref, n)
+
+
+def test_estimate_same_under_both_schedules():
+    torch, pk = need_gpu()
+    d = workloads.workload("lognormal_2layer_cgv_16to512", L=2)
+    res = {}
+    for sched in (0, 1):
+        with pk.Context(d, stream=torch.cuda.Stream()) as ctx:
+            ctx.set_schedule(sched)
+            res[sched] = ctx.estimate(4e-3, seed=2, n_pilot=64, cost_model=0)
+    for key in ("q_hat", "var_hat", "alpha"):
+        assert res[0][key] == res[1][key], key
+    assert list(res[0]["N"]) == list(res[1]["N"])
