@@ -8,11 +8,14 @@
 // cells of one grid row and keeps their values, faces, diagonal and inverse
 // diagonal in registers; the four neighbours of a cell come from the lane's
 // own registers or from a warp shuffle (rows j -/+ 1 are lanes -/+ 2, the two
-// halves of a row are lanes 2j and 2j + 1).  The 8 x 8 and 4 x 4 levels of the
-// multigrid hierarchy stay in shared memory and run the generic code.  The
-// arithmetic is the generic solver's (Sec. 3.1 Eq. 3.3 with harmonic faces,
-// the same multigrid cycle, CG, refinement and stopping test), so results
-// agree with it to rounding order.
+// halves of a row are lanes 2j and 2j + 1).  The 8 x 8 level of the multigrid
+// hierarchy is held the same way, two cells per lane (its operator in shared
+// memory), and the 4 x 4 coarsest grid is solved with its dense inverse,
+// built per system by Gauss-Jordan elimination in registers.  The arithmetic
+// is the generic solver's (Sec. 3.1 Eq. 3.3 with harmonic faces, the same
+// multigrid cycle, CG, refinement and stopping test; the coarsest inverse in
+// natural instead of red-black cell order), so results agree with it to
+// rounding order.
 //
 // Lane layout: lane L holds row j = L >> 1 and the columns 8h .. 8h + 7
 // (h = L & 1).  Its red part (i + j even) is slot t = 0..3 at column
@@ -113,27 +116,117 @@ __device__ __forceinline__ void tiny_half_sweep(const TinyOp& A, const float (&f
   }
 }
 
-// Per-system state of the tiny path in shared memory: the hierarchy below the
-// finest grid (levels of side 8 and 4) in the generic layout, then the FP64
-// refinement solution and residual of the finest grid, [slot][lane] (slots
-// 0..3 red, 4..7 black), touched once per refinement sweep.
-__host__ __device__ inline size_t tiny_lev_bytes() {
-  size_t o = 0;
-  auto take = [&](size_t bytes) { o += align16(bytes); };
-  for (int ml = kTinyM / 2;; ml >>= 1) {
-    const size_t nl = (size_t)ml * ml, nf = (size_t)ml * (ml + 1);
-    take(nf * 4);
-    take(nf * 4);
-    for (int a = 0; a < 4; ++a) take(nl * 4);
-    if (ml <= kCoarseSide) {
-      take(nl * nl * 4);
-      take((2 * nl + 1) * 4);
-      break;
+// Per-system state of the tiny path in shared memory: the 8 x 8 level's
+// faces and inverse diagonal, [k][lane] (k = 0..4: west, east, south, north
+// face and inverse diagonal of the lane's red cell; 5..9 its black cell), the
+// dense inverse of the 4 x 4 grid's operator (16 x 16, natural cell order
+// c = 4 J + I), then the FP64 refinement solution and residual of the finest
+// grid, [slot][lane] (slots 0..3 red, 4..7 black), touched once per
+// refinement sweep.
+constexpr size_t kTinyOp8Bytes = 10 * 32 * sizeof(float);
+constexpr size_t kTinyCinvBytes = 16 * 16 * sizeof(float);
+__host__ __device__ inline size_t tiny_lev_bytes() { return kTinyOp8Bytes + kTinyCinvBytes; }
+__host__ __device__ inline size_t tiny_ws_bytes() { return tiny_lev_bytes() + 2 * 8 * 32 * sizeof(double); }
+
+// The lane's two cells of the 8 x 8 level: lane L holds row J = L >> 2 and
+// columns 2q, 2q + 1 (q = L & 3); its red cell is column 2q + (J & 1), its
+// black cell 2q + 1 - (J & 1).  Rows J -/+ 1 are lanes -/+ 4.
+struct TinyC8 {
+  int lane, J, q, jp;
+  __device__ __forceinline__ TinyC8() {
+    lane = threadIdx.x & 31;
+    J = lane >> 2;
+    q = lane & 3;
+    jp = J & 1;
+  }
+};
+
+// Neighbour values W, E, S, N of the lane's 8 x 8 cell of one colour, from
+// the other colour's value x (zero outside the grid).
+__device__ __forceinline__ void c8_nbrs(float x, const TinyC8& c, bool red, float& W, float& E, float& S,
+                                        float& N) {
+  const unsigned full = 0xffffffffu;
+  const float from_left = __shfl_up_sync(full, x, 1);    // lane - 1's right cell: column 2q - 1
+  const float from_right = __shfl_down_sync(full, x, 1);  // lane + 1's left cell: column 2q + 2
+  const float s = __shfl_up_sync(full, x, 4);
+  const float n = __shfl_down_sync(full, x, 4);
+  // `right`: the cell is the lane's right one (column 2q + 1), its west
+  // neighbour the lane's other cell
+  const bool right = red ? (c.jp == 1) : (c.jp == 0);
+  W = right ? x : (c.q > 0 ? from_left : 0.f);
+  E = right ? (c.q < 3 ? from_right : 0.f) : x;
+  S = c.J > 0 ? s : 0.f;
+  N = c.J < 7 ? n : 0.f;
+}
+
+// Gauss-Seidel half sweep of one colour on the 8 x 8 level (op8: the faces
+// and inverse diagonal, [k][lane]).
+__device__ __forceinline__ void c8_half_sweep(const float* op8, const TinyC8& c, bool red, float f, float& e_own,
+                                              float e_oth, bool zero_guess) {
+  const int o = red ? 0 : 5;
+  const float id = op8[(o + 4) * 32 + c.lane];
+  if (zero_guess) {
+    e_own = f * id;
+    return;
+  }
+  float W, E, S, N;
+  c8_nbrs(e_oth, c, red, W, E, S, N);
+  float s = f;
+  s += op8[o * 32 + c.lane] * W;
+  s += op8[(o + 1) * 32 + c.lane] * E;
+  s += op8[(o + 2) * 32 + c.lane] * S;
+  s += op8[(o + 3) * 32 + c.lane] * N;
+  e_own = s * id;
+}
+
+// One visit of the 8 x 8 level (Sec. 3.5 multigrid preconditioner, the
+// generic cycle's steps on a two-level hierarchy): nuc red-black sweep pairs
+// (from e = 0 when zero_start), the red cells' residual summed over each 2 x 2
+// aggregate onto the 4 x 4 grid, its exact solve with the dense inverse,
+// prolongation, nuc black-red sweep pairs.
+__device__ __forceinline__ void c8_cycle(const float* op8, const float* cinv, const TinyC8& c, float fr, float fb,
+                                         float& er, float& eb, int nuc, bool zero_start) {
+  const unsigned full = 0xffffffffu;
+  for (int s = 0; s < nuc; ++s) {
+    c8_half_sweep(op8, c, true, fr, er, eb, zero_start && s == 0);
+    c8_half_sweep(op8, c, false, fb, eb, er, false);
+  }
+  // residual at the red cell (zero at the black one after a black sweep):
+  // f - (diag e - the faces times the neighbours), the generic order
+  float W, E, S, N;
+  c8_nbrs(eb, c, true, W, E, S, N);
+  const float tw = op8[c.lane], te = op8[32 + c.lane], ts = op8[64 + c.lane], tn = op8[96 + c.lane];
+  float ax = ((tw + te) + (ts + tn)) * er;
+  ax -= tw * W;
+  ax -= te * E;
+  ax -= ts * S;
+  ax -= tn * N;
+  const float res = fr - ax;
+  // coarse cell (I', J') = red cells (2I', 2J') [lane 8J' + I'] and
+  // (2I' + 1, 2J' + 1) [lane 8J' + I' + 4]
+  const float f4 = res + __shfl_down_sync(full, res, 4);
+  // e4 = Cinv f4 at the lanes with even J (the others compute a value nobody uses)
+  const int c4 = 4 * (c.J >> 1) + c.q;
+  const float4* row = reinterpret_cast<const float4*>(cinv + c4 * 16);
+  float e4 = 0.f;
+#pragma unroll
+  for (int k4 = 0; k4 < 4; ++k4) {
+    const float4 w = row[k4];
+    const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int cc = 4 * k4 + u;
+      e4 += wv[u] * __shfl_sync(full, f4, 8 * (cc >> 2) + (cc & 3));
     }
   }
-  return o;
+  const float ec = __shfl_sync(full, e4, 8 * (c.J >> 1) + c.q);
+  er += ec;
+  eb += ec;
+  for (int s = 0; s < nuc; ++s) {
+    c8_half_sweep(op8, c, false, fb, eb, er, false);
+    c8_half_sweep(op8, c, true, fr, er, eb, false);
+  }
 }
-__host__ __device__ inline size_t tiny_ws_bytes() { return tiny_lev_bytes() + 2 * 8 * 32 * sizeof(double); }
 
 // One FP64 cell vector of the finest grid in shared memory, [slot][lane].
 struct TinyVec64 {
@@ -145,55 +238,158 @@ struct TinyVec64 {
 
 // Symmetric multigrid cycle z = B r with the finest level in registers:
 // nu red-black sweep pairs, the residual of the red cells restricted to the
-// 8 x 8 grid, gamma visits of the shared-memory hierarchy (the generic
-// cycle), prolongation, nu black-red sweep pairs.
-template <typename G>
-__device__ __forceinline__ void tiny_precond(const G& g, const TinyOp& Ar, const TinyOp& Ab, const TinyLane& ln,
-                                             const Level<float>* lev, int nl, int gamma, int nu, int nuc,
-                                             const TinyVec<float>& r, TinyVec<float>& z) {
+// 8 x 8 grid, gamma visits of the 8 x 8 level (c8_cycle), prolongation, nu
+// black-red sweep pairs.
+__device__ __forceinline__ void tiny_precond(const TinyOp& Ar, const TinyOp& Ab, const TinyLane& ln,
+                                             const TinyC8& c8, const float* op8, const float* cinv, int gamma,
+                                             int nu, int nuc, const TinyVec<float>& r, TinyVec<float>& z) {
+  const unsigned full = 0xffffffffu;
   for (int s = 0; s < nu; ++s) {
     tiny_half_sweep(Ar, r.r, z.r, z.b, ln, true, s == 0);
     tiny_half_sweep(Ab, r.b, z.b, z.r, ln, false, false);
   }
   // residual at the red cells (zero at the black ones after a black sweep);
-  // coarse cell (I, J) = red slot t of rows 2J and 2J + 1, I = 4h + t
+  // coarse cell (I, J) = red slot t of rows 2J and 2J + 1, I = 4h + t, summed
+  // in the lanes of row 2J
+  float rs[4];
   {
     float W[4], E[4], S[4], N[4], az[4];
     tiny_nbrs(z.b, ln, true, W, E, S, N);
     tiny_apply(Ar, z.r, W, E, S, N, az);
-    const Level<float>& C = lev[1];
-    const RbIndex Rc(kTinyM / 2);
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       const float res = r.r[t] - az[t];
-      const float up = __shfl_down_sync(0xffffffffu, res, 2);  // row 2J + 1
-      if (ln.jp == 0) C.f[Rc.at(4 * ln.h + t, ln.j >> 1)] = res + up;
+      rs[t] = res + __shfl_down_sync(full, res, 2);  // row 2J + 1
     }
   }
-  g.sync();
-  const int nuc1 = nuc < 1 ? nu : nuc;
-  const int visits = nl - 1 == 1 ? 1 : gamma;  // the next level is the coarsest: solved once
-  for (int v = 0; v < visits; ++v) {
-    if (gamma <= 1 && nuc1 <= 1 && v == 0)
-      vcycle(g, lev + 1, nl - 1);
-    else
-      mg_cycle(g, lev + 1, nl - 1, gamma < 1 ? 1 : gamma, nuc1, nuc1, v == 0);
-  }
+  // to the 8 x 8 layout: cell I = 2q + u of row J is slot t = 2 (q & 1) + u of lane 4J + (q >> 1)
+  float fr, fb;
   {
-    const Level<float>& C = lev[1];
-    const RbIndex Rc(kTinyM / 2);
+    float v[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) v[t] = __shfl_sync(full, rs[t], 4 * c8.J + (c8.q >> 1));
+    const float u0 = (c8.q & 1) ? v[2] : v[0], u1 = (c8.q & 1) ? v[3] : v[1];
+    fr = c8.jp ? u1 : u0;
+    fb = c8.jp ? u0 : u1;
+  }
+  const int nuc1 = nuc < 1 ? nu : nuc;
+  float er = 0.f, eb = 0.f;
+  for (int v = 0; v < (gamma < 1 ? 1 : gamma); ++v) c8_cycle(op8, cinv, c8, fr, fb, er, eb, nuc1, v == 0);
+  // prolongation: fine slot t of lane (j, h) takes coarse cell (4h + t, j >> 1),
+  // cell u = t & 1 of 8 x 8 lane 4 (j >> 1) + 2h + (t >> 1), red there when u == (j >> 1) & 1
+  {
+    const int Jc = ln.j >> 1, s0 = 4 * Jc + 2 * ln.h;
+    const float ar = __shfl_sync(full, er, s0), ab = __shfl_sync(full, eb, s0);
+    const float br = __shfl_sync(full, er, s0 + 1), bb = __shfl_sync(full, eb, s0 + 1);
+    const bool odd = Jc & 1;
+    const float ec[4] = {odd ? ab : ar, odd ? ar : ab, odd ? bb : br, odd ? br : bb};
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      const float ec = C.e[Rc.at(4 * ln.h + t, ln.j >> 1)];
-      z.r[t] += ec;
-      z.b[t] += ec;
+      z.r[t] += ec[t];
+      z.b[t] += ec[t];
     }
   }
-  g.sync();  // every lane has read the coarse correction before the next cycle writes it
   for (int s = 0; s < nu; ++s) {
     tiny_half_sweep(Ab, r.b, z.b, z.r, ln, false, false);
     tiny_half_sweep(Ar, r.r, z.r, z.b, ln, true, false);
   }
+}
+
+// The 8 x 8 level's operator (faces: means of the two fine faces forming each
+// coarse face; inverse diagonal) into op8, and the dense inverse of the 4 x 4
+// grid's operator (faces from the 8 x 8 ones by the same rule) into cinv, by
+// Gauss-Jordan elimination without pivoting (the operator is SPD) with lane L
+// holding columns 8 (L & 1) .. + 7 of row L >> 1.
+__device__ __forceinline__ void tiny_build_coarse(const TinyOp& Ar, const TinyOp& Ab, const TinyLane& ln,
+                                                  const TinyC8& c8, float* op8, float* cinv) {
+  const unsigned full = 0xffffffffu;
+  // fine layout, lanes of even rows 2J: the coarse faces of cells (4h + t, J)
+  float cw[4], ce[4], cs[4], cn[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    cw[t] = 0.5f * (Ar.w[t] + __shfl_down_sync(full, Ab.w[t], 2));
+    ce[t] = 0.5f * (Ab.e[t] + __shfl_down_sync(full, Ar.e[t], 2));
+    cs[t] = 0.5f * (Ar.s[t] + Ab.s[t]);
+    cn[t] = 0.5f * (__shfl_down_sync(full, Ab.n[t], 2) + __shfl_down_sync(full, Ar.n[t], 2));
+  }
+  // 8 x 8 layout: faces of the lane's cells u = 0 (column 2q) and u = 1
+  float w8[2], e8[2], s8[2], n8[2];
+  {
+    const int src = 4 * c8.J + (c8.q >> 1);
+    const int t0 = 2 * (c8.q & 1);
+    float v[4];
+#define TINY_MOVE(X, Y)                                                   \
+  for (int t = 0; t < 4; ++t) v[t] = __shfl_sync(full, X[t], src);        \
+  Y[0] = t0 ? v[2] : v[0];                                                \
+  Y[1] = t0 ? v[3] : v[1];
+#pragma unroll
+    TINY_MOVE(cw, w8)
+#pragma unroll
+    TINY_MOVE(ce, e8)
+#pragma unroll
+    TINY_MOVE(cs, s8)
+#pragma unroll
+    TINY_MOVE(cn, n8)
+#undef TINY_MOVE
+  }
+#pragma unroll
+  for (int col = 0; col < 2; ++col) {  // 0 red (u = jp), 1 black
+    const int u = col == 0 ? c8.jp : 1 - c8.jp;
+    const float w = u ? w8[1] : w8[0], e = u ? e8[1] : e8[0], s = u ? s8[1] : s8[0], n = u ? n8[1] : n8[0];
+    float* o = op8 + col * 5 * 32 + c8.lane;
+    o[0] = w;
+    o[32] = e;
+    o[64] = s;
+    o[96] = n;
+    o[128] = 1.0f / ((w + e) + (s + n));
+  }
+  // 4 x 4 faces at lanes 8J' + I' (rows 2J' and 2J' + 1 of the 8 x 8 level are lanes L and L + 4)
+  const float w4 = 0.5f * (w8[0] + __shfl_down_sync(full, w8[0], 4));
+  const float e4 = 0.5f * (e8[1] + __shfl_down_sync(full, e8[1], 4));
+  const float s4 = 0.5f * (s8[0] + s8[1]);
+  const float n4 = 0.5f * (__shfl_down_sync(full, n8[0], 4) + __shfl_down_sync(full, n8[1], 4));
+  // row r = L >> 1 of the 4 x 4 operator, columns 8 hh .. 8 hh + 7
+  const int r = ln.lane >> 1, hh = ln.lane & 1;
+  const int src4 = 8 * (r >> 2) + (r & 3);
+  const float rw = __shfl_sync(full, w4, src4), re = __shfl_sync(full, e4, src4);
+  const float rsv = __shfl_sync(full, s4, src4), rn = __shfl_sync(full, n4, src4);
+  float B[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int cc = 8 * hh + k;
+    float v = 0.f;
+    if (cc == r) v = (rw + re) + (rsv + rn);
+    else if (cc == r - 1 && (r & 3) != 0) v = -rw;
+    else if (cc == r + 1 && (r & 3) != 3) v = -re;
+    else if (cc == r - 4) v = -rsv;
+    else if (cc == r + 4) v = -rn;
+    B[k] = v;
+  }
+  // Gauss-Jordan: at step k with pivot p = B[k][k], scaled pivot row B[k][j] / p and
+  // column c_i = B[i][k]: B[k][k] <- 1/p, B[k][j] <- B[k][j] / p, B[i][k] <- -c_i / p,
+  // B[i][j] <- B[i][j] - c_i (B[k][j] / p); after 16 steps B = A^-1
+#pragma unroll
+  for (int kk = 0; kk < 16; ++kk) {
+    const float p = __shfl_sync(full, B[kk & 7], 2 * kk + (kk >> 3));
+    const float ip = 1.0f / p;
+    const float ci = __shfl_sync(full, B[kk & 7], (ln.lane & ~1) + (kk >> 3));
+    float rj[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) rj[k] = __shfl_sync(full, B[k], 2 * kk + hh) * ip;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int jc = 8 * hh + k;
+      float v;
+      if (r == kk) v = jc == kk ? ip : rj[k];
+      else if (jc == kk) v = -ci * ip;
+      else v = fmaf(-ci, rj[k], B[k]);
+      B[k] = v;
+    }
+  }
+  float4* dst = reinterpret_cast<float4*>(cinv + r * 16 + 8 * hh);
+  dst[0] = make_float4(B[0], B[1], B[2], B[3]);
+  dst[1] = make_float4(B[4], B[5], B[6], B[7]);
+  __syncwarp();
 }
 
 // q = A p on both colours; returns the lane's part of p.q.
@@ -290,44 +486,10 @@ __device__ void solve_one_tiny(const G& g, const SolveArgs& a, int64_t sys, unsi
     oy = o >> 1;
   }
   const uint64_t sample = (uint64_t)(a.first + sidx);
-  if (m_prev != -kTinyM) {  // level table of the shared-memory levels (8 x 8, 4 x 4)
-    g.sync();
-    if (g.local_leader()) {
-      size_t o = 0;
-      auto take = [&](size_t bytes) {
-        unsigned char* p = base + o;
-        o += align16(bytes);
-        return p;
-      };
-      int l = 1;
-      for (int ml = m / 2;; ml >>= 1, ++l) {
-        const size_t nlv = (size_t)ml * ml, nf = (size_t)ml * (ml + 1);
-        Level<T, T>& L = gs.lev[l];
-        L.m = ml;
-        L.tx = reinterpret_cast<T*>(take(nf * 4));
-        L.ty = reinterpret_cast<T*>(take(nf * 4));
-        L.diag = reinterpret_cast<T*>(take(nlv * 4));
-        L.invd = reinterpret_cast<T*>(take(nlv * 4));
-        L.e = reinterpret_cast<T*>(take(nlv * 4));
-        L.f = reinterpret_cast<T*>(take(nlv * 4));
-        L.cinv = L.cbuf = nullptr;
-        L.stage = nullptr;
-        L.stage_rows = 0;
-        L.quads = 0;
-        if (ml <= kCoarseSide) {
-          L.cinv = reinterpret_cast<T*>(take(nlv * nlv * 4));
-          L.cbuf = reinterpret_cast<T*>(take((2 * nlv + 1) * 4));
-          break;
-        }
-      }
-      gs.nl = l + 1;
-      gs.lev[0].m = m;
-    }
+  if (m_prev != -kTinyM) {  // the workspace held another size's levels
     g.sync();
     m_prev = -kTinyM;
   }
-  const int nl = gs.nl;
-  const Level<T>* lev = gs.lev;
   const TinyLane ln;
   // ---- layers, cell permeabilities (FP32, as the generic assembly rounds them) ----
   if (a.ksrc != KSRC_ARRAY) {
@@ -370,38 +532,11 @@ __device__ void solve_one_tiny(const G& g, const SolveArgs& a, int64_t sys, unsi
       }
     }
   }
-  // ---- the 8 x 8 level's faces: means of the two fine faces forming each coarse face ----
-  {
-    const Level<T>& C = gs.lev[1];
-    const int mc = m / 2;
-    // tx: coarse face I' = 4h + t of coarse row J is fine face 2I' (the west
-    // face of column 2I') of rows 2J, 2J + 1; I' = 8 is the east face of column 15
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const float fw = ln.jp ? Ab.w[t] : Ar.w[t];  // column 8h + 2t is black in odd rows
-      const float up = __shfl_down_sync(0xffffffffu, fw, 2);
-      if (ln.jp == 0) C.tx[(ln.j >> 1) * (mc + 1) + 4 * ln.h + t] = 0.5f * (fw + up);
-    }
-    {
-      const float fe = ln.jp ? Ar.e[3] : Ab.e[3];  // column 15: red in odd rows
-      const float up = __shfl_down_sync(0xffffffffu, fe, 2);
-      if (ln.jp == 0 && ln.h == 1) C.tx[(ln.j >> 1) * (mc + 1) + mc] = 0.5f * (fe + up);
-    }
-    // ty: coarse face J' of coarse column I = 4h + t is fine face 2J' of
-    // columns 2I, 2I + 1 (south faces of row 2J'); J' = 8: north faces of row 15
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      if (ln.jp == 0) C.ty[(ln.j >> 1) * mc + 4 * ln.h + t] = 0.5f * (Ar.s[t] + Ab.s[t]);
-      if (ln.j == m - 1) C.ty[mc * mc + 4 * ln.h + t] = 0.5f * (Ab.n[t] + Ar.n[t]);
-    }
-  }
-  g.sync();
-  build_diag<true>(g, gs.lev[1]);
-  for (int l = 2; l < nl; ++l) {
-    build_coarse(g, gs.lev[l - 1], gs.lev[l]);
-    build_diag<true>(g, gs.lev[l]);
-  }
-  build_coarse_inverse(g, gs.lev[nl - 1]);
+  // ---- the 8 x 8 level's operator and the 4 x 4 grid's inverse ----
+  const TinyC8 c8;
+  float* op8 = reinterpret_cast<float*>(base);
+  float* cinv = reinterpret_cast<float*>(base + kTinyOp8Bytes);
+  tiny_build_coarse(Ar, Ab, ln, c8, op8, cinv);
   // ---- FP64 refinement around FP32 PCG (restarted, or reliable updates) ----
   const TinyVec64 X64{reinterpret_cast<double*>(base + tiny_lev_bytes()), ln.lane};
   const TinyVec64 R64{X64.p + 8 * 32, ln.lane};
@@ -459,7 +594,7 @@ __device__ void solve_one_tiny(const G& g, const SolveArgs& a, int64_t sys, unsi
     bool first = true;
     int since = 0;
     while (status != 0 && iters < a.max_it) {
-      tiny_precond(g, Ar, Ab, ln, lev, nl, gamma, nu, nuc, r, z);
+      tiny_precond(Ar, Ab, ln, c8, op8, cinv, gamma, nu, nuc, r, z);
       float rzn = 0.f;
 #pragma unroll
       for (int t = 0; t < 4; ++t) rzn += r.r[t] * z.r[t] + r.b[t] * z.b[t];
@@ -564,7 +699,7 @@ __device__ void solve_one_tiny(const G& g, const SolveArgs& a, int64_t sys, unsi
       } else if (it >= a.max_it - iters) {
         end_inner = true;  // cap (the generic pcg's loop condition)
       } else {
-        tiny_precond(g, Ar, Ab, ln, lev, nl, gamma, nu, nuc, r, z);
+        tiny_precond(Ar, Ab, ln, c8, op8, cinv, gamma, nu, nuc, r, z);
         float rzn = 0.f;
 #pragma unroll
         for (int t = 0; t < 4; ++t) rzn += r.r[t] * z.r[t] + r.b[t] * z.b[t];
