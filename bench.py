@@ -747,13 +747,23 @@ def main():
     hbm, hbm_src = measured_hbm()
     peaks = {"fp64": fp64_peak, "fp32": fp32_peak, "hbm": hbm, "hbm_src": hbm_src}
     ctx = pk.Context(d, device=local, stream=stream)
-    tune = ctx.autotune(seed=args.seed + 12345)  # untimed set-up: launch plan per level
+    # untimed set-up: launch plan per level, then (work-queue schedule) the launch
+    # shapes of the large levels re-timed on whole estimates
+    tune = ctx.autotune(seed=args.seed + 12345)
     ctx.set_schedule(args.schedule)
+    sched_tune = None
+    if args.schedule:
+        before, after, tune = ctx.autotune_schedule(d["eps"], seed=args.seed + 4242, n_pilot=64, cost_model=0)
+        sched_tune = {"estimate_ms_before": before, "estimate_ms_after": after}
     bctx = btune = None
     if base is not None:
         bctx = pk.Context(base, device=local, stream=stream)
         btune = bctx.autotune(seed=args.seed + 12345)
         bctx.set_schedule(args.schedule)
+        if args.schedule:
+            bb, ba, btune = bctx.autotune_schedule(base["eps"], seed=args.seed + 4242, n_pilot=64, cost_model=0,
+                                                   reps=1)
+            sched_tune["plain_fp64_arm"] = {"estimate_ms_before": bb, "estimate_ms_after": ba}
     seed = args.seed + 7919 * rank
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 
@@ -837,6 +847,7 @@ def main():
         "N_per_level": est["N"], "V_per_level": est["V"], "q_hat": est["q_hat"], "var_hat": est["var_hat"],
         "alpha": est["alpha"], "bias_estimate": est["bias"], "bias_flag": est["bias_flag"],
         "stage_ms_per_step_serial": tot["ms"],
+        "schedule_tuning": sched_tune,
         "solve_launch_shapes": [{"kernel": "solve_list_kernel<%d, %d>" % (d["prec"], cl["mode"]),
                                  "shape": shape_name(cl), "levels": cl["levels"], "launches": cl["launches"],
                                  "ms_per_step": round(cl["ms"], 3),

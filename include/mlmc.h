@@ -305,6 +305,29 @@ typedef struct mlmc_tune_report {
  * the solver tolerance.  rep: host pointer or NULL. */
 MLMC_API int mlmc_autotune(mlmc_ctx* ctx, uint64_t seed, mlmc_tune_report* rep);
 
+/* Launch shapes for the work-queue schedule (no paper counterpart: a
+ * throughput setting of this implementation).  mlmc_autotune() times each
+ * level alone, where a level with few large systems pays for the tail of its
+ * launch; in the work-queue schedule the systems of all levels that share a
+ * launch shape fill each other's tails.  This pass, run after
+ * mlmc_autotune() (or on the default plans), re-times whole adaptive
+ * estimates (mlmc_estimate(ctx, eps, seed, n_pilot, cost_model): one
+ * untimed, then the fastest of `reps` timed with CUDA events on the context
+ * stream) while it changes the launch shape of each part with systems of
+ * side >= 256 (the fine systems of a level, and its coarse systems as a
+ * launch of their own), finest level first: a cluster plan tries one block
+ * of 512 threads and the other cluster size (4 or 8), a block plan a cluster
+ * of 4; each part keeps its cycle, smoothing and mixed-precision settings, and
+ * a change stays only if the estimate gets faster by more than 0.5 %.
+ * Only for 2-D contexts in precision 0 or 1 with schedule 1 (otherwise it
+ * does nothing).  The estimates' state is not kept (the last estimate and a
+ * pending resume are restored).  ms: host array of 2 or NULL, receives the
+ * estimate's time before and after.  rep: host pointer or NULL, receives the
+ * final plans (plan fields only).  Errors: MLMC_ERR_ARG, and those of
+ * mlmc_estimate(). */
+MLMC_API int mlmc_autotune_schedule(mlmc_ctx* ctx, double eps, uint64_t seed, int32_t n_pilot,
+                                    int32_t cost_model, int32_t reps, double* ms, mlmc_tune_report* rep);
+
 /* Fix the solver's launch plan of one level by hand (overrides
  * mlmc_autotune; all the level's systems in one launch): mode 0 = one block of `threads` (32..512, multiple of 32)
  * per system, 1 = one warp per system, 2 = one thread-block cluster of

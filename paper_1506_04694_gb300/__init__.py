@@ -126,6 +126,9 @@ EXPORTS = {
                                               ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "mlmc_set_solver": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_double]),
     "mlmc_set_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "mlmc_autotune_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_uint64, ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(TuneReport)]),
     "mlmc_ce_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
     "mlmc_philox_words": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
@@ -312,6 +315,18 @@ class Context:
         """mlmc_autotune: time the solver's launch plans per level, keep the fastest."""
         r = TuneReport()
         _check(lib().mlmc_autotune(self._h, seed, ctypes.byref(r)), allow_failed=False)
+        return self._plans(r)
+
+    def autotune_schedule(self, eps, seed=0, n_pilot=64, cost_model=0, reps=2):
+        """mlmc_autotune_schedule: launch shapes of the large levels re-timed on whole estimates under
+        the work-queue schedule; returns (ms before, ms after, plans)."""
+        r = TuneReport()
+        ms = (ctypes.c_double * 2)()
+        _check(lib().mlmc_autotune_schedule(self._h, eps, seed, n_pilot, cost_model, reps, ms, ctypes.byref(r)),
+               allow_failed=False)
+        return ms[0], ms[1], self._plans(r)
+
+    def _plans(self, r):
         L = self.model.L + 1
         return [{"threads": r.threads[i], "warp": r.warp[i], "cap_blocks_per_sm": r.cap_blocks_per_sm[i],
                  "cluster": r.cluster[i], "gamma": r.gamma[i], "nu": r.nu[i], "nu_coarse": r.nu_coarse[i],

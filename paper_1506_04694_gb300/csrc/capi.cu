@@ -1766,6 +1766,146 @@ int mlmc_autotune(mlmc_ctx* c, uint64_t seed, mlmc_tune_report* rep) {
   return err;
 }
 
+// Plan fields of a tune report from the context's current plans.
+static void report_plans(const mlmc_ctx* c, mlmc_tune_report* rep) {
+  std::memset(rep, 0, sizeof(*rep));
+  const mlmc_model& md = c->model;
+  for (int l = 0; l <= md.L; ++l) {
+    SolvePlan P;
+    if (c->tuned_ok[l]) P = c->tuned[l];
+    else if (plan_of(md, md.m0 << l, &P)) continue;
+    rep->threads[l] = P.threads;
+    rep->warp[l] = P.warp;
+    rep->cap_blocks_per_sm[l] = P.cap_blocks_per_sm;
+    rep->cluster[l] = P.cluster;
+    rep->gamma[l] = P.gamma;
+    rep->nu[l] = P.nu;
+    rep->nu_coarse[l] = P.nu_coarse > 0 ? P.nu_coarse : P.nu;
+    rep->inner_tol[l] = P.inner_tol;
+    rep->reliable[l] = P.reliable;
+    rep->smem[l] = P.use_smem;
+    if (c->tuned_c_ok[l]) {
+      const SolvePlan& Q = c->tuned_c[l];
+      rep->c_threads[l] = Q.threads;
+      rep->c_warp[l] = Q.warp;
+      rep->c_cluster[l] = Q.cluster;
+      rep->c_cap_blocks_per_sm[l] = Q.cap_blocks_per_sm;
+      rep->c_gamma[l] = Q.gamma;
+      rep->c_nu[l] = Q.nu;
+      rep->c_nu_coarse[l] = Q.nu_coarse > 0 ? Q.nu_coarse : Q.nu;
+      rep->c_inner_tol[l] = Q.inner_tol;
+      rep->c_reliable[l] = Q.reliable;
+      rep->c_smem[l] = Q.use_smem;
+    }
+  }
+}
+
+int mlmc_autotune_schedule(mlmc_ctx* c, double eps, uint64_t seed, int32_t n_pilot, int32_t cost_model,
+                           int32_t reps, double* ms, mlmc_tune_report* rep) {
+  if (!c) return fail(MLMC_ERR_ARG, "null context");
+  if (!(eps > 0) || n_pilot < 2 || reps < 1 || (cost_model != 0 && cost_model != 1))
+    return fail(MLMC_ERR_ARG, "eps > 0, n_pilot >= 2, reps >= 1, cost_model 0 or 1");
+  CUDA_TRY(cudaSetDevice(c->device));
+  const mlmc_model& md = c->model;
+  if (ms) ms[0] = ms[1] = 0.0;
+  if (!c->sched || dim_of(md) == 3 || (md.prec != 0 && md.prec != 1)) {
+    if (rep) report_plans(c, rep);
+    return 0;
+  }
+  for (int l = 0; l <= md.L; ++l)  // explicit plans for every level, to vary
+    if (!c->tuned_ok[l]) {
+      if (plan_of(md, md.m0 << l, &c->tuned[l])) return fail(MLMC_ERR_CUDA, "occupancy query failed");
+      c->tuned_ok[l] = true;
+    }
+  const auto saved_last = c->last_est, saved_resume = c->resume_est;
+  c->resume_est.valid = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  int err = 0;
+  auto time_estimate = [&](double* out) -> int {
+    mlmc_estimate_out o;
+    int e = mlmc_estimate(c, eps, seed, n_pilot, cost_model, &o);  // untimed: captures the round graphs
+    if (e < 0) return e;
+    double best = 1e300;
+    for (int r = 0; r < reps; ++r) {
+      if (cudaEventRecord(e0, c->st) != cudaSuccess) return fail(MLMC_ERR_CUDA, "event");
+      e = mlmc_estimate(c, eps, seed, n_pilot, cost_model, &o);
+      if (e < 0) return e;
+      if (cudaEventRecord(e1, c->st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+        return fail(MLMC_ERR_CUDA, "event");
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      best = std::min(best, (double)t);
+    }
+    *out = best;
+    return 0;
+  };
+  double best = 0.0;
+  err = time_estimate(&best);
+  if (ms) ms[0] = best;
+  for (int l = md.L; l >= 0 && !err; --l) {
+    const int m = md.m0 << l;
+    const int nc = n_coarse(md, l);
+    for (int part = 0; part < 2 && !err; ++part) {
+      if (part == 1 && nc == 0) break;
+      const int msz = part == 0 ? m : m / 2;
+      if (msz < 256) continue;
+      const bool split = c->tuned_c_ok[l];
+      const SolvePlan cur = part == 0 ? c->tuned[l] : (split ? c->tuned_c[l] : c->tuned[l]);
+      // candidate shapes (mode, cluster)
+      int shapes[2][2], ns = 0;
+      if (part == 1 && !split) {  // the coarse systems share the fine launch: try a launch of their own
+        shapes[ns][0] = 0, shapes[ns][1] = 0, ++ns;
+        shapes[ns][0] = 2, shapes[ns][1] = 4, ++ns;
+      } else if (cur.cluster) {
+        shapes[ns][0] = 0, shapes[ns][1] = 0, ++ns;
+        shapes[ns][0] = 2, shapes[ns][1] = cur.cluster == 4 ? 8 : 4, ++ns;
+      } else {
+        shapes[ns][0] = 2, shapes[ns][1] = 4, ++ns;
+      }
+      for (int k = 0; k < ns && !err; ++k) {
+        SolvePlan P;
+        const int mode = shapes[k][0], cl = shapes[k][1];
+        if (solve_plan_mode(msz, md.prec, mode, 512, cl, &P)) continue;
+        if (part == 1 && split == false && mode == 0 && !cur.cluster && cur.threads == 512 && !cur.warp)
+          continue;  // the shared launch already is a block of 512
+        P.gamma = cur.gamma;
+        P.nu = cur.nu;
+        P.nu_coarse = cur.nu_coarse;
+        P.reliable = cur.reliable;
+        P.inner_tol = cur.inner_tol;
+        P.cap_blocks_per_sm = 0;
+        const SolvePlan keep = part == 0 ? c->tuned[l] : c->tuned_c[l];
+        const bool keep_ok = part == 0 ? true : c->tuned_c_ok[l];
+        if (part == 0) c->tuned[l] = P;
+        else {
+          c->tuned_c[l] = P;
+          c->tuned_c_ok[l] = true;
+        }
+        double t = 0.0;
+        if ((err = time_estimate(&t))) break;
+        if (t < 0.995 * best) {
+          best = t;
+        } else if (part == 0) {
+          c->tuned[l] = keep;
+        } else {
+          c->tuned_c[l] = keep;
+          c->tuned_c_ok[l] = keep_ok;
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->last_est = saved_last;
+  c->resume_est = saved_resume;
+  if (err) return err;
+  if (ms) ms[1] = best;
+  if (rep) report_plans(c, rep);
+  return 0;
+}
+
 int mlmc_profile(mlmc_ctx* c, int enable) {
   if (!c) return fail(MLMC_ERR_ARG, "null context");
   if (enable) std::memset(&c->prof, 0, sizeof(c->prof));

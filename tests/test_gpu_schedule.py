@@ -106,3 +106,23 @@ def test_estimate_same_under_both_schedules():
     for key in ("q_hat", "var_hat", "alpha"):
         assert res[0][key] == res[1][key], key
     assert list(res[0]["N"]) == list(res[1]["N"])
+
+
+def test_schedule_autotune_keeps_results():
+    # the schedule-aware pass only changes launch shapes of the large levels:
+    # an estimate after it agrees with one on the per-level plans to the solver
+    # tolerance (same sample sizes under the deterministic cost model)
+    torch, pk = need_gpu()
+    d = workloads.workload("lognormal_2layer_cgv_16to512")
+    res = {}
+    with pk.Context(d, stream=torch.cuda.Stream()) as ctx:
+        ctx.autotune(seed=3)
+        res[0] = ctx.estimate(2e-3, seed=2, n_pilot=32, cost_model=0)
+        before, after, plans = ctx.autotune_schedule(2e-3, seed=5, n_pilot=32, cost_model=0, reps=1)
+        assert 0 < after <= before
+        for p in plans:
+            assert p["cluster"] in (0, 2, 4, 8) and p["threads"] > 0
+            assert p["coarse"] is None or p["coarse"]["cluster"] in (0, 2, 4, 8)
+        res[1] = ctx.estimate(2e-3, seed=2, n_pilot=32, cost_model=0)
+    assert list(res[0]["N"]) == list(res[1]["N"])
+    assert abs(res[1]["q_hat"] - res[0]["q_hat"]) <= 1e-7 * abs(res[0]["q_hat"])
