@@ -593,11 +593,12 @@ UNITS = {"ns": 1.0, "nsecond": 1.0, "us": 1e3, "usecond": 1e3, "ms": 1e6, "mseco
          "s": 1e9, "second": 1e9}
 
 
-def ncu_summary(path, skip=0, start_at=None):
+def ncu_summary(path, skip=0, start_at=None, limit=0):
     """Per kernel of an ncu launch list (--metrics gpu__time_duration.sum
     --csv): launches, total device time and share.  skip leaves out the first
     launches; start_at leaves out every launch before the first kernel whose
-    name contains that text."""
+    name contains that text; limit > 0 keeps only that many launches from
+    there on."""
     rows = list(csv.reader(open(path)))
     start = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
     hdr = rows[start]
@@ -614,6 +615,8 @@ def ncu_summary(path, skip=0, start_at=None):
             if start_at not in r[ki]:
                 continue
             seen = True
+        if limit and sum(a[0] for a in agg.values()) >= limit:
+            break
         name = r[ki].split("(")[0].strip()
         ns = float(r[vi].replace(",", "")) * UNITS[r[ui].strip()]
         a = agg.setdefault(name, [0, 0.0])
@@ -691,15 +694,18 @@ def main():
                     help="workload name: time-to-eps of its mixed CGV form against plain FP64 (one JSON line)")
     ap.add_argument("--bf16-arm", action="store_true")
     ap.add_argument("--fp64cg-arm", action="store_true")
+    ap.add_argument("--plans", default=None, metavar="FILE",
+                    help="launch plans: replayed from FILE if it exists, else tuned and written there")
     ap.add_argument("--schedule", type=int, default=1, choices=[0, 1],
                     help="multilevel schedule (mlmc_set_schedule): 1 work queue per launch shape, 0 per level")
     ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES) + sorted(MULTI_CASES))
     ap.add_argument("--ncu-summary", default=None, metavar="CSV")
     ap.add_argument("--skip", type=int, default=0)
+    ap.add_argument("--limit", type=int, default=0)
     ap.add_argument("--from", dest="start_at", default=None)
     args = ap.parse_args()
     if args.ncu_summary:
-        print(ncu_summary(args.ncu_summary, args.skip, args.start_at))
+        print(ncu_summary(args.ncu_summary, args.skip, args.start_at, args.limit))
         return
     if args.profile_case:
         run_profile_case(args.profile_case)
@@ -749,21 +755,37 @@ def main():
     ctx = pk.Context(d, device=local, stream=stream)
     # untimed set-up: launch plan per level, then (work-queue schedule) the launch
     # shapes of the large levels re-timed on whole estimates
-    tune = ctx.autotune(seed=args.seed + 12345)
+    # (--plans FILE: replay the plans a previous run of the same command wrote there)
+    replay = None
+    if args.plans and os.path.exists(args.plans):
+        replay = json.load(open(args.plans))
     ctx.set_schedule(args.schedule)
     sched_tune = None
-    if args.schedule:
-        before, after, tune = ctx.autotune_schedule(d["eps"], seed=args.seed + 4242, n_pilot=64, cost_model=0)
-        sched_tune = {"estimate_ms_before": before, "estimate_ms_after": after}
+    if replay:
+        ctx.set_plans(replay["mixed"])
+        tune = replay["mixed"]
+        sched_tune = {"replayed_plans": args.plans}
+    else:
+        tune = ctx.autotune(seed=args.seed + 12345)
+        if args.schedule:
+            before, after, tune = ctx.autotune_schedule(d["eps"], seed=args.seed + 4242, n_pilot=64, cost_model=0)
+            sched_tune = {"estimate_ms_before": before, "estimate_ms_after": after}
     bctx = btune = None
     if base is not None:
         bctx = pk.Context(base, device=local, stream=stream)
-        btune = bctx.autotune(seed=args.seed + 12345)
         bctx.set_schedule(args.schedule)
-        if args.schedule:
-            bb, ba, btune = bctx.autotune_schedule(base["eps"], seed=args.seed + 4242, n_pilot=64, cost_model=0,
-                                                   reps=1)
-            sched_tune["plain_fp64_arm"] = {"estimate_ms_before": bb, "estimate_ms_after": ba}
+        if replay and replay.get("plain"):
+            bctx.set_plans(replay["plain"])
+            btune = replay["plain"]
+        else:
+            btune = bctx.autotune(seed=args.seed + 12345)
+            if args.schedule:
+                bb, ba, btune = bctx.autotune_schedule(base["eps"], seed=args.seed + 4242, n_pilot=64,
+                                                       cost_model=0, reps=1)
+                sched_tune = dict(sched_tune or {}, plain_fp64_arm={"estimate_ms_before": bb,
+                                                                    "estimate_ms_after": ba})
+    if args.plans and not replay and rank == 0:
+        json.dump({"mixed": tune, "plain": btune}, open(args.plans, "w"))
     seed = args.seed + 7919 * rank
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 

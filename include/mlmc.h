@@ -367,6 +367,20 @@ MLMC_API int mlmc_set_launch_coarse(mlmc_ctx* ctx, int level, int32_t mode, int3
  * The two schedules give bit-identical results.  Errors: MLMC_ERR_ARG. */
 MLMC_API int mlmc_set_schedule(mlmc_ctx* ctx, int32_t schedule);
 
+/* A complete launch plan set by hand, as mlmc_autotune() or
+ * mlmc_autotune_schedule() report it (so that a tuning result can be
+ * replayed in another process): part 0 = the fine systems of `level` (or all
+ * of them while the level has no coarse plan), part 1 = its coarse systems
+ * (level >= 1) as a launch of their own.  mode, threads, cluster, gamma, nu
+ * as in mlmc_set_launch() (mode 3 needs systems of side 16 and prec 1; no
+ * mode < 0 here); nu_coarse 0..4 (0: nu) the sweep pairs on the coarser
+ * grids; cap_blocks_per_sm >= 0 (0: the occupancy limit); reliable 0 / 1 and
+ * inner_tol in (0, 0.5] as in mlmc_set_solver() (used with prec 1, 2).
+ * Errors: MLMC_ERR_ARG. */
+MLMC_API int mlmc_set_launch_ex(mlmc_ctx* ctx, int level, int32_t part, int32_t mode, int32_t threads,
+                                int32_t cluster, int32_t gamma, int32_t nu, int32_t nu_coarse,
+                                int32_t cap_blocks_per_sm, int32_t reliable, double inner_tol);
+
 /* Mixed precision (prec 1, 2) of one level's solver, on top of its launch
  * plan (the autotuned or set one, else the default): reliable = 0 runs FP32
  * multigrid-preconditioned CG solves to the relative tolerance inner_tol

@@ -126,6 +126,9 @@ EXPORTS = {
                                               ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "mlmc_set_solver": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_double]),
     "mlmc_set_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "mlmc_set_launch_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_double]),
     "mlmc_autotune_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_uint64, ctypes.c_int32,
                                               ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(TuneReport)]),
@@ -368,6 +371,21 @@ class Context:
         """mlmc_set_launch_coarse: a launch plan of its own for the coarse systems of a level >= 1
         (mode < 0: one launch for all the level's systems again)."""
         _check(lib().mlmc_set_launch_coarse(self._h, level, mode, threads, cluster, gamma, nu), allow_failed=False)
+
+    def set_plan(self, level, plan, part=0):
+        """mlmc_set_launch_ex: replay one plan dict as autotune() / autotune_schedule() report it
+        (part 0 the fine systems, 1 the coarse ones)."""
+        mode = 2 if plan["cluster"] else 3 if plan["warp"] == 2 else 1 if plan["warp"] else 0
+        _check(lib().mlmc_set_launch_ex(self._h, level, part, mode, plan["threads"], plan["cluster"], plan["gamma"],
+                                        plan["nu"], plan["nu_coarse"], plan["cap_blocks_per_sm"], plan["reliable"],
+                                        plan["inner_tol"]), allow_failed=False)
+
+    def set_plans(self, plans):
+        """Replay a whole list of per-level plans (fine, and coarse where the level has its own)."""
+        for level, p in enumerate(plans):
+            self.set_plan(level, p, 0)
+            if p.get("coarse"):
+                self.set_plan(level, p["coarse"], 1)
 
     def set_solver(self, level, reliable, inner_tol):
         """mlmc_set_solver: mixed-precision scheme of a level (reliable updates or restarted

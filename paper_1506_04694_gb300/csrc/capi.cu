@@ -1989,6 +1989,53 @@ int mlmc_set_schedule(mlmc_ctx* c, int32_t schedule) {
   return 0;
 }
 
+int mlmc_set_launch_ex(mlmc_ctx* c, int level, int32_t part, int32_t mode, int32_t threads, int32_t cluster,
+                       int32_t gamma, int32_t nu, int32_t nu_coarse, int32_t cap_blocks_per_sm, int32_t reliable,
+                       double inner_tol) {
+  if (!c || level < 0 || level > c->model.L) return fail(MLMC_ERR_ARG, "bad context or level");
+  if (part != 0 && part != 1) return fail(MLMC_ERR_ARG, "part must be 0 (fine) or 1 (coarse)");
+  if (part == 1 && (level < 1 || n_coarse(c->model, level) == 0))
+    return fail(MLMC_ERR_ARG, "part 1 needs a level >= 1 with coarse systems");
+  if (mode < 0 || mode > 3 || (mode == 0 && (threads < 32 || threads > 512 || threads % 32)) ||
+      (mode == 2 && (cluster < 2 || cluster > 8 || (cluster & (cluster - 1)))))
+    return fail(MLMC_ERR_ARG, "mode 0..3; mode 0: threads 32..512 (multiple of 32); mode 2: cluster 2, 4 or 8");
+  const int msz = part == 0 ? c->model.m0 << level : (c->model.m0 << level) / 2;
+  if (mode == 3 && (msz != 16 || c->model.prec != 1 || dim_of(c->model) == 3))
+    return fail(MLMC_ERR_ARG, "mode 3 (register path) needs systems of side 16, prec 1, 2-D");
+  if (gamma < 1 || gamma > 2) return fail(MLMC_ERR_ARG, "gamma must be 1 (V-cycle) or 2 (W-cycle)");
+  if (nu < 1 || nu > 4 || nu_coarse < 0 || nu_coarse > 4) return fail(MLMC_ERR_ARG, "nu 1..4, nu_coarse 0..4");
+  if (cap_blocks_per_sm < 0) return fail(MLMC_ERR_ARG, "cap_blocks_per_sm >= 0");
+  if ((reliable != 0 && reliable != 1) || !(inner_tol > 0 && inner_tol <= 0.5))
+    return fail(MLMC_ERR_ARG, "reliable must be 0 or 1 and inner_tol in (0, 0.5]");
+  if (reliable && dim_of(c->model) == 3) return fail(MLMC_ERR_ARG, "reliable updates are 2-D only");
+  CUDA_TRY(cudaSetDevice(c->device));
+  SolvePlan P;
+  const int t = mode == 0 ? threads : 512;
+  const int mr = dim_of(c->model) == 3 ? solve3_plan_mode(msz, c->model.prec, mode, t, cluster, &P)
+                                       : solve_plan_mode(msz, c->model.prec, mode, t, cluster, &P);
+  if (mr) return fail(MLMC_ERR_CUDA, "launch plan query failed");
+  P.gamma = gamma;
+  P.nu = nu;
+  P.nu_coarse = nu_coarse;
+  P.cap_blocks_per_sm = cap_blocks_per_sm;
+  P.reliable = reliable;
+  P.inner_tol = inner_tol;
+  if (part == 0) {
+    c->tuned[level] = P;
+    c->tuned_ok[level] = true;
+  } else {
+    if (!c->tuned_ok[level]) {  // the fine systems keep the default plan
+      SolvePlan F;
+      if (plan_of(c->model, c->model.m0 << level, &F)) return fail(MLMC_ERR_CUDA, "launch plan query failed");
+      c->tuned[level] = F;
+      c->tuned_ok[level] = true;
+    }
+    c->tuned_c[level] = P;
+    c->tuned_c_ok[level] = true;
+  }
+  return 0;
+}
+
 int mlmc_set_solver(mlmc_ctx* c, int level, int32_t reliable, double inner_tol) {
   if (!c || level < 0 || level > c->model.L) return fail(MLMC_ERR_ARG, "bad context or level");
   if ((reliable != 0 && reliable != 1) || !(inner_tol > 0 && inner_tol <= 0.5))

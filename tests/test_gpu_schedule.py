@@ -126,3 +126,20 @@ def test_schedule_autotune_keeps_results():
         res[1] = ctx.estimate(2e-3, seed=2, n_pilot=32, cost_model=0)
     assert list(res[0]["N"]) == list(res[1]["N"])
     assert abs(res[1]["q_hat"] - res[0]["q_hat"]) <= 1e-7 * abs(res[0]["q_hat"])
+
+
+def test_plans_replay_in_another_context():
+    # mlmc_set_launch_ex replays a tuned plan set exactly: a second context
+    # given the first one's plans gives bit-identical level sums
+    torch, pk = need_gpu()
+    d = workloads.workload("lognormal_2layer_cgv_16to512", L=4)
+    n = [1500, 200, 40, 12, 6]
+    with pk.Context(d, stream=torch.cuda.Stream()) as a:
+        plans = a.autotune(seed=8)
+        ra = a.multilevel_batch(n, 3)
+    with pk.Context(d, stream=torch.cuda.Stream()) as b:
+        b.set_plans(plans)
+        rb = b.multilevel_batch(n, 3)
+    for l in range(len(n)):
+        for key in ("n", "n_failed", "iters_total") + pk.SUM_FIELDS:
+            assert ra[l][key] == rb[l][key], (l, key)
