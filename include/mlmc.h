@@ -250,7 +250,9 @@ MLMC_API int mlmc_resume(mlmc_ctx* ctx, const char* path);
  * mlmc_level_batch().  use_graph != 0 captures the whole queue into one CUDA
  * graph (kept and relaunched while the arguments repeat); it needs a context
  * created on a non-default stream and is skipped while profiling is on (stage
- * timing puts events between the launches).
+ * timing puts events between the launches).  Under the work-queue schedule a
+ * captured batch queues its phases as one chain on the context stream (the
+ * graph of that chain ran faster than a graph of the side-by-side form).
  * Per-sample values are not returned (use mlmc_level_batch for those).
  * mlmc_estimate() runs its pilot and every top-up round through this call.
  * With the work-queue schedule (mlmc_set_schedule, the default) a 2-D batch

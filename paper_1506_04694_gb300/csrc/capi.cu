@@ -832,14 +832,17 @@ int prepare_sched(mlmc_ctx* c, int n_levels, const int64_t* n, const std::vector
 // fields of its levels, one persistent solver launch over all its parts
 // (further launches only past kMaxSolveItems parts); (C) per level, after
 // its classes, the gather, the level reduction and the copy of its sums to
-// host memory, joined into the context stream.
+// host memory, joined into the context stream.  With `serial` the three
+// phases run in this order on the context stream.
 int enqueue_sched(mlmc_ctx* c, int n_levels, const int64_t* first, const int64_t* n, uint64_t seed,
-                  const std::vector<SchedClass>& cls, int* prof_cls) {
+                  const std::vector<SchedClass>& cls, int* prof_cls, bool serial) {
   const mlmc_model& md = c->model;
   const bool f32 = fields_f32(md);
-  // with stage profiling on, everything runs in order on the context stream
-  // (each launch's event time its own); events and waits then order nothing
-  const bool serial = c->prof_on;
+  // serial: everything in order on the context stream (events and waits then
+  // order nothing): with stage profiling on (each launch's event time its
+  // own) and under graph capture (measured on GB300: a graph of the side-by-side
+  // form ran the headline estimate in 636 ms, the same launches as one chain
+  // in 615 ms, direct side-by-side launches in 610 ms)
   if (cudaEventRecord(c->fork, c->st) != cudaSuccess) return fail(MLMC_ERR_CUDA, "fork event");
   for (int l = 0; l < n_levels; ++l) {
     if (n[l] <= 0) continue;
@@ -966,6 +969,8 @@ int multilevel_impl(mlmc_ctx* c, int n_levels, const int64_t* first, const int64
   // stage profiling on they run one after another on the context stream, so
   // that every stage's CUDA-event time is its own
   const bool side_by_side = !c->prof_on;
+  // stage timing needs events between the launches, so profiling runs ungraphed
+  const bool graph = use_graph && c->st != nullptr && !c->prof_on;
   // profiled work-queue launches: their launch shape's slot in the counters
   int prof_cls[mlmc_ctx::kClasses];
   for (size_t k = 0; k < cls.size(); ++k) {
@@ -988,7 +993,7 @@ int multilevel_impl(mlmc_ctx* c, int n_levels, const int64_t* first, const int64
     }
   }
   auto enqueue_all = [&]() -> int {
-    if (sched) return enqueue_sched(c, n_levels, first, n, seed, cls, prof_cls);
+    if (sched) return enqueue_sched(c, n_levels, first, n, seed, cls, prof_cls, c->prof_on || graph);
     if (side_by_side && cudaEventRecord(c->fork, c->st) != cudaSuccess) return fail(MLMC_ERR_CUDA, "fork event");
     for (int l = 0; l < n_levels; ++l) {
       if (n[l] <= 0) continue;
@@ -1008,8 +1013,6 @@ int multilevel_impl(mlmc_ctx* c, int n_levels, const int64_t* first, const int64
     }
     return 0;
   };
-  // stage timing needs events between the launches, so profiling runs ungraphed
-  const bool graph = use_graph && c->st != nullptr && !c->prof_on;
   if (graph) {
     std::vector<int64_t> key = {(int64_t)n_levels, (int64_t)seed, (int64_t)g_alloc_generation.load(),
                                 (int64_t)sched};
