@@ -406,6 +406,120 @@ __device__ __forceinline__ void rb_sweep_quads(const G& g, const Level<float, fl
   g.sync();
 }
 
+// ---- FP32 CG passes over quads (streamed finest grids) ----
+// The CG iteration's passes on 16-byte accesses, for the same grids as the
+// quad half sweeps: q = A p over quads of one colour (apply_at's terms in its
+// order, the neighbours as in rb_sweep_quads), and the pointwise updates over
+// quads of the whole cell array (n = m^2 a multiple of 4).  Each returns the
+// calling thread's part of its dot product.
+template <typename G>
+__device__ __forceinline__ float cg_matvec_quads(const G& g, const Level<float, float>& A,
+                                                 const float* __restrict__ p, float* __restrict__ q) {
+  const int m = A.m;
+  const RbIndex R(m);
+  const int hm = R.hm;
+  const int nq = (m * hm) >> 2;  // quads of one colour
+  float pq = 0.f;
+  for (int t = g.rank(); t < 2 * nq; t += g.size()) {
+    const int color = t >= nq ? 1 : 0;
+    const int h0 = (t - color * nq) << 2;
+    const int j = h0 >> R.lhm, k0 = h0 - (j << R.lhm);
+    const int sh = (j + color) & 1;
+    const int c0 = color * R.half + h0;
+    const int ob = (color ^ 1) * R.half + j * hm + k0;
+    const F4 v = ld4(p + c0), d = ld4(A.diag + c0), mid = ld4(p + ob);
+    float W[4], E[4];
+    if (sh) {
+      const float after = k0 + 4 < hm ? p[ob + 4] : 0.f;
+      W[0] = mid.v[0]; W[1] = mid.v[1]; W[2] = mid.v[2]; W[3] = mid.v[3];
+      E[0] = mid.v[1]; E[1] = mid.v[2]; E[2] = mid.v[3]; E[3] = after;
+    } else {
+      const float before = k0 > 0 ? p[ob - 1] : 0.f;
+      W[0] = before; W[1] = mid.v[0]; W[2] = mid.v[1]; W[3] = mid.v[2];
+      E[0] = mid.v[0]; E[1] = mid.v[1]; E[2] = mid.v[2]; E[3] = mid.v[3];
+    }
+    F4 s;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s.v[u] = d.v[u] * v.v[u];
+    const int i0 = 2 * k0 + sh;
+    const float* tx = A.tx + j * (m + 1) + i0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + 2 * u;
+      if (i > 0) s.v[u] -= tx[2 * u] * W[u];
+      if (i < m - 1) s.v[u] -= tx[2 * u + 1] * E[u];
+    }
+    if (j > 0) {
+      const F4 es = ld4(p + ob - hm);
+      const F4 ta = ld4(A.ty + j * m + 2 * k0), tb = ld4(A.ty + j * m + 2 * k0 + 4);
+      const float ty[4] = {sh ? ta.v[1] : ta.v[0], sh ? ta.v[3] : ta.v[2], sh ? tb.v[1] : tb.v[0],
+                           sh ? tb.v[3] : tb.v[2]};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s.v[u] -= ty[u] * es.v[u];
+    }
+    if (j < m - 1) {
+      const F4 en = ld4(p + ob + hm);
+      const F4 ta = ld4(A.ty + (j + 1) * m + 2 * k0), tb = ld4(A.ty + (j + 1) * m + 2 * k0 + 4);
+      const float ty[4] = {sh ? ta.v[1] : ta.v[0], sh ? ta.v[3] : ta.v[2], sh ? tb.v[1] : tb.v[0],
+                           sh ? tb.v[3] : tb.v[2]};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s.v[u] -= ty[u] * en.v[u];
+    }
+    st4(q + c0, s);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) pq += v.v[u] * s.v[u];
+  }
+  return pq;
+}
+
+// x += alpha p, r -= alpha q; returns the part of r.r
+template <typename G>
+__device__ __forceinline__ float cg_update_quads(const G& g, int n, float alpha, float* __restrict__ x,
+                                                 const float* __restrict__ p, float* __restrict__ r,
+                                                 const float* __restrict__ q) {
+  float rr = 0.f;
+  for (int t = g.rank(); t < (n >> 2); t += g.size()) {
+    const int c = t << 2;
+    F4 xv = ld4(x + c), rv = ld4(r + c);
+    const F4 pv = ld4(p + c), qv = ld4(q + c);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      xv.v[u] += alpha * pv.v[u];
+      rv.v[u] = rv.v[u] - alpha * qv.v[u];
+      rr += rv.v[u] * rv.v[u];
+    }
+    st4(x + c, xv);
+    st4(r + c, rv);
+  }
+  return rr;
+}
+
+// part of a.b
+template <typename G>
+__device__ __forceinline__ float cg_dot_quads(const G& g, int n, const float* __restrict__ a,
+                                              const float* __restrict__ b) {
+  float s = 0.f;
+  for (int t = g.rank(); t < (n >> 2); t += g.size()) {
+    const F4 av = ld4(a + 4 * t), bv = ld4(b + 4 * t);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s += av.v[u] * bv.v[u];
+  }
+  return s;
+}
+
+// p = z + beta p
+template <typename G>
+__device__ __forceinline__ void cg_xpay_quads(const G& g, int n, float beta, const float* __restrict__ z,
+                                              float* __restrict__ p) {
+  for (int t = g.rank(); t < (n >> 2); t += g.size()) {
+    const F4 zv = ld4(z + 4 * t);
+    F4 pv = ld4(p + 4 * t);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) pv.v[u] = zv.v[u] + beta * pv.v[u];
+    st4(p + 4 * t, pv);
+  }
+}
+
 template <typename T, typename F, typename G>
 __device__ __forceinline__ void rb_sweep(const G& g, const Level<T, F>& L, int color, bool zero_guess) {
   if constexpr (std::is_same<T, F>::value && G::kStaged) {
@@ -723,9 +837,16 @@ __device__ int pcg(const G& g, const Level<T>& A, const Level<T, F>* lev, int nl
   }
   rz = g.sum(rz, red, par);
   int it = 0;
+  // FP32 on a streamed finest grid: the passes on 16-byte quads
+  bool vq = false;
+  if constexpr (std::is_same<T, float>::value && G::kQuads) vq = L0.quads != 0;
   while (it < max_it) {
     ++it;
     T pq = T(0);
+    if constexpr (std::is_same<T, float>::value && G::kQuads) {
+      if (vq) pq = cg_matvec_quads(g, A, p, q);
+    }
+    if (!vq)
     for (int c0 = g.rank(); c0 < n; c0 += G::kU * step) {
       T val[G::kU];
 #pragma unroll
@@ -750,12 +871,16 @@ __device__ int pcg(const G& g, const Level<T>& A, const Level<T, F>* lev, int nl
     }
     const T alpha = rz / pq;
     rr = T(0);
-    for (int c = g.rank(); c < n; c += step) {
-      x[c] += alpha * p[c];
-      const T rv = r[c] - alpha * q[c];
-      r[c] = rv;
-      rr += rv * rv;
+    if constexpr (std::is_same<T, float>::value && G::kQuads) {
+      if (vq) rr = cg_update_quads(g, n, alpha, x, p, r, q);
     }
+    if (!vq)
+      for (int c = g.rank(); c < n; c += step) {
+        x[c] += alpha * p[c];
+        const T rv = r[c] - alpha * q[c];
+        r[c] = rv;
+        rr += rv * rv;
+      }
     rr = g.sum(rr, red, par);
     if (rr <= thr) {
       status = 0;
@@ -763,11 +888,19 @@ __device__ int pcg(const G& g, const Level<T>& A, const Level<T, F>* lev, int nl
     }
     precond(g, lev, nl, gamma, nu, nuc);
     T rzn = T(0);
-    for (int c = g.rank(); c < n; c += step) rzn += r[c] * z[c];
+    if constexpr (std::is_same<T, float>::value && G::kQuads) {
+      if (vq) rzn = cg_dot_quads(g, n, r, z);
+    }
+    if (!vq)
+      for (int c = g.rank(); c < n; c += step) rzn += r[c] * z[c];
     rzn = g.sum(rzn, red, par);
     const T beta = rzn / rz;
     rz = rzn;
-    for (int c = g.rank(); c < n; c += step) p[c] = z[c] + beta * p[c];
+    if constexpr (std::is_same<T, float>::value && G::kQuads) {
+      if (vq) cg_xpay_quads(g, n, beta, z, p);
+    }
+    if (!vq)
+      for (int c = g.rank(); c < n; c += step) p[c] = z[c] + beta * p[c];
     g.sync();
   }
   return it;
@@ -1199,17 +1332,24 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
         rz = g.sum(rz, red, par);
       }
       int since = 0;
+      // FP32 on a streamed finest grid: the CG passes on 16-byte quads
+      bool vq = false;
+      if constexpr (std::is_same<T, float>::value && G::kQuads) vq = L0.quads != 0;
       while (status != 0 && iters < a.max_it) {
         ++iters;
         ++since;
         T pq = T(0);
-        for (int c = g.rank(); c < n; c += g.size()) {
-          int i, j;
-          R.cell(c, i, j);
-          const T v = apply_at(A, pv, R, c, i, j);
-          qv[c] = v;
-          pq += pv[c] * v;
+        if constexpr (std::is_same<T, float>::value && G::kQuads) {
+          if (vq) pq = cg_matvec_quads(g, A, pv, qv);
         }
+        if (!vq)
+          for (int c = g.rank(); c < n; c += g.size()) {
+            int i, j;
+            R.cell(c, i, j);
+            const T v = apply_at(A, pv, R, c, i, j);
+            qv[c] = v;
+            pq += pv[c] * v;
+          }
         pq = g.sum(pq, red, par);
         if (!(pq > T(0)) || !isfinite(pq) || !isfinite(rz)) {
           status = 2;
@@ -1217,12 +1357,16 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
         }
         const T alpha = rz / pq;
         rr32 = T(0);
-        for (int c = g.rank(); c < n; c += g.size()) {
-          xv[c] += alpha * pv[c];
-          const T rv = L0.f[c] - alpha * qv[c];
-          L0.f[c] = rv;
-          rr32 += rv * rv;
+        if constexpr (std::is_same<T, float>::value && G::kQuads) {
+          if (vq) rr32 = cg_update_quads(g, n, alpha, xv, pv, L0.f, qv);
         }
+        if (!vq)
+          for (int c = g.rank(); c < n; c += g.size()) {
+            xv[c] += alpha * pv[c];
+            const T rv = L0.f[c] - alpha * qv[c];
+            L0.f[c] = rv;
+            rr32 += rv * rv;
+          }
         rr32 = g.sum(rr32, red, par);
         if ((double)rr32 * scl * scl <= thr || rr32 <= d2 * rr_ref || since >= 16) {  // reliable update
           for (int c = g.rank(); c < n; c += g.size()) x64[c] += scl * (double)xv[c];
@@ -1252,11 +1396,19 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
         }
         precond(g, lev, nl, a.mg_gamma, a.mg_nu, nuc);
         T rzn = T(0);
-        for (int c = g.rank(); c < n; c += g.size()) rzn += L0.f[c] * L0.e[c];
+        if constexpr (std::is_same<T, float>::value && G::kQuads) {
+          if (vq) rzn = cg_dot_quads(g, n, L0.f, L0.e);
+        }
+        if (!vq)
+          for (int c = g.rank(); c < n; c += g.size()) rzn += L0.f[c] * L0.e[c];
         rzn = g.sum(rzn, red, par);
         const T beta = rzn / rz;
         rz = rzn;
-        for (int c = g.rank(); c < n; c += g.size()) pv[c] = L0.e[c] + beta * pv[c];
+        if constexpr (std::is_same<T, float>::value && G::kQuads) {
+          if (vq) cg_xpay_quads(g, n, beta, L0.e, pv);
+        }
+        if (!vq)
+          for (int c = g.rank(); c < n; c += g.size()) pv[c] = L0.e[c] + beta * pv[c];
         g.sync();
       }
     }
