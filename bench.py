@@ -53,7 +53,7 @@ PREC_NAMES = {0: "fp64", 1: "fp32-mg/fp64-refinement", 2: "fp32-mg-bf16-faces/fp
 # to its kernel's average launch.
 TRAFFIC = {
     "solve_list_kernel<1, 0> [blocks of 512 threads, workspace in global memory]": (
-        51.003e9, 108.924e9,
+        50.329e9, 108.927e9,
         "ncu of bench.py --profile-case sched_block512: the persistent launch of blocks of 512 over the "
         "headline's levels 2 (fine), 3 and 4 at 2000 / 600 / 160 samples, "
         "profiles/solve_list_kernel_block512_levels2to4.txt"),
