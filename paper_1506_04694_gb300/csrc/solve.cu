@@ -520,6 +520,121 @@ __device__ __forceinline__ void cg_xpay_quads(const G& g, int n, float beta, con
   }
 }
 
+// ---- FP64 refinement passes over quads (the same grids) ----
+// Four consecutive FP64 values, two 16-byte accesses.
+struct D4 {
+  double v[4];
+};
+__device__ __forceinline__ D4 ld4d(const double* p) {
+  const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+  return D4{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4d(double* p, const D4& a) {
+  *reinterpret_cast<double2*>(p) = make_double2(a.v[0], a.v[1]);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(a.v[2], a.v[3]);
+}
+
+// r64 = b - A64 x64 with A64 = the FP32 faces widened (the refinement
+// residual's terms in its order, the diagonal the FP64 sum of the four
+// faces); returns the part of r64.r64.
+template <typename G>
+__device__ __forceinline__ double ref_residual_quads(const G& g, const Level<float, float>& A,
+                                                     const double* __restrict__ x64, double* __restrict__ r64,
+                                                     int problem, double fmid) {
+  const int m = A.m;
+  const RbIndex R(m);
+  const int hm = R.hm;
+  const int nq = (m * hm) >> 2;
+  double s2 = 0.0;
+  for (int t = g.rank(); t < 2 * nq; t += g.size()) {
+    const int color = t >= nq ? 1 : 0;
+    const int h0 = (t - color * nq) << 2;
+    const int j = h0 >> R.lhm, k0 = h0 - (j << R.lhm);
+    const int sh = (j + color) & 1;
+    const int c0 = color * R.half + h0;
+    const int ob = (color ^ 1) * R.half + j * hm + k0;
+    const D4 xc = ld4d(x64 + c0), mid = ld4d(x64 + ob);
+    double W[4], E[4];
+    if (sh) {
+      const double after = k0 + 4 < hm ? x64[ob + 4] : 0.0;
+      W[0] = mid.v[0]; W[1] = mid.v[1]; W[2] = mid.v[2]; W[3] = mid.v[3];
+      E[0] = mid.v[1]; E[1] = mid.v[2]; E[2] = mid.v[3]; E[3] = after;
+    } else {
+      const double before = k0 > 0 ? x64[ob - 1] : 0.0;
+      W[0] = before; W[1] = mid.v[0]; W[2] = mid.v[1]; W[3] = mid.v[2];
+      E[0] = mid.v[0]; E[1] = mid.v[1]; E[2] = mid.v[2]; E[3] = mid.v[3];
+    }
+    D4 S{{0.0, 0.0, 0.0, 0.0}}, N{{0.0, 0.0, 0.0, 0.0}};
+    if (j > 0) S = ld4d(x64 + ob - hm);
+    if (j < m - 1) N = ld4d(x64 + ob + hm);
+    const F4 sa = ld4(A.ty + j * m + 2 * k0), sb = ld4(A.ty + j * m + 2 * k0 + 4);
+    const F4 na = ld4(A.ty + (j + 1) * m + 2 * k0), nb = ld4(A.ty + (j + 1) * m + 2 * k0 + 4);
+    const float tys[4] = {sh ? sa.v[1] : sa.v[0], sh ? sa.v[3] : sa.v[2], sh ? sb.v[1] : sb.v[0],
+                          sh ? sb.v[3] : sb.v[2]};
+    const float tyn[4] = {sh ? na.v[1] : na.v[0], sh ? na.v[3] : na.v[2], sh ? nb.v[1] : nb.v[0],
+                          sh ? nb.v[3] : nb.v[2]};
+    const int i0 = 2 * k0 + sh;
+    const float* tx = A.tx + j * (m + 1) + i0;
+    D4 out;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + 2 * u;
+      const double tw = (double)tx[2 * u], te = (double)tx[2 * u + 1];
+      const double ts = (double)tys[u], tn = (double)tyn[u];
+      double ax = ((tw + te) + (ts + tn)) * xc.v[u];
+      if (i > 0) ax -= tw * W[u];
+      if (i < m - 1) ax -= te * E[u];
+      if (j > 0) ax -= ts * S.v[u];
+      if (j < m - 1) ax -= tn * N.v[u];
+      const double bv = problem == 1 ? fmid : (i == 0 ? tw : 0.0);
+      out.v[u] = bv - ax;
+      s2 += out.v[u] * out.v[u];
+    }
+    st4d(r64 + c0, out);
+  }
+  return s2;
+}
+
+// x64 += scl xv
+template <typename G>
+__device__ __forceinline__ void ref_update_quads(const G& g, int n, double scl, double* __restrict__ x64,
+                                                 const float* __restrict__ xv) {
+  for (int t = g.rank(); t < (n >> 2); t += g.size()) {
+    D4 x = ld4d(x64 + 4 * t);
+    const F4 d = ld4(xv + 4 * t);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x.v[u] += scl * (double)d.v[u];
+    st4d(x64 + 4 * t, x);
+  }
+}
+
+// f = (float)(r64 inv), optionally xv = 0 and pv *= ratio; returns the part of f.f
+template <typename G>
+__device__ __forceinline__ float ref_rescale_quads(const G& g, int n, double inv, const double* __restrict__ r64,
+                                                   float* __restrict__ f, float* __restrict__ xv,
+                                                   float* __restrict__ pv, float ratio) {
+  float s = 0.f;
+  const F4 zero{{0.f, 0.f, 0.f, 0.f}};
+  for (int t = g.rank(); t < (n >> 2); t += g.size()) {
+    const D4 r = ld4d(r64 + 4 * t);
+    F4 v;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      v.v[u] = (float)(r.v[u] * inv);
+      s += v.v[u] * v.v[u];
+    }
+    st4(f + 4 * t, v);
+    if (xv) st4(xv + 4 * t, zero);
+    if (pv) {
+      F4 pp = ld4(pv + 4 * t);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pp.v[u] *= ratio;
+      st4(pv + 4 * t, pp);
+    }
+  }
+  return s;
+}
+
 template <typename T, typename F, typename G>
 __device__ __forceinline__ void rb_sweep(const G& g, const Level<T, F>& L, int color, bool zero_guess) {
   if constexpr (std::is_same<T, F>::value && G::kStaged) {
@@ -1153,7 +1268,7 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
   const Level<T>& A = cg_operator<PREC>(gs);
   const RbIndex R(m);  // cell-array layout (colour by colour)
 
-  // ---- layers and per-cell permeability (into r64 as scratch) ----
+  // ---- layers and per-cell permeability (into r64, or x with prec 1, 2, as scratch) ----
   if (a.ksrc != KSRC_ARRAY) {
     if (g.local_leader()) sample_layers(a, sample, gs.eta, gs.kc);
     g.sync();
@@ -1162,6 +1277,22 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
   // m and a.m are powers of two: scaling by the reciprocal is exact, so the
   // centre (j + 1/2) / m is the same double as the quotient
   const double inv_m = 1.0 / (double)m, inv_mf = 1.0 / (double)a.m;
+  // horizontal interfaces: the layer of each row, once per row (the same
+  // centre and comparisons as per cell), in the finest level's e as scratch
+  int* row_t = reinterpret_cast<int*>(L0.e);
+  const bool by_row = a.ksrc != KSRC_ARRAY && a.geometry != 1;
+  if (by_row) {
+    const bool own = coarse && !a.cgv_on_k;
+    for (int j = g.rank(); j < m; j += g.size()) {
+      const int jf = coarse ? 2 * j + oy : j;
+      const double yc = own ? ((double)j + 0.5) * inv_m : ((double)jf + 0.5) * inv_mf;
+      row_t[j] = layer_at(gs.eta, n_if, yc);
+    }
+    g.sync();
+  }
+  // the cell permeabilities: FP32 for the FP32 operators (prec 1, 2; in the CG
+  // x vector as scratch), else FP64 (in r64)
+  float* k32 = reinterpret_cast<float*>(xv);
   for (int c = g.rank(); c < n; c += g.size()) {
     int i, j;
     R.cell(c, i, j);
@@ -1173,9 +1304,14 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
       const int jf = coarse ? 2 * j + oy : j;
       const int iff = coarse ? 2 * i + ox : i;
       const bool own = coarse && !a.cgv_on_k;  // layer at the coarse centre
-      const double yc = own ? ((double)j + 0.5) * inv_m : ((double)jf + 0.5) * inv_mf;
-      const double xc = own ? ((double)i + 0.5) * inv_m : ((double)iff + 0.5) * inv_mf;
-      const int t = layer_at_point(a.geometry, gs.eta, n_if, xc, yc);
+      int t;
+      if (by_row) {
+        t = row_t[j];
+      } else {
+        const double yc = own ? ((double)j + 0.5) * inv_m : ((double)jf + 0.5) * inv_mf;
+        const double xc = own ? ((double)i + 0.5) * inv_m : ((double)iff + 0.5) * inv_mf;
+        t = layer_at_point(a.geometry, gs.eta, n_if, xc, yc);
+      }
       if (a.ksrc == KSRC_CONST) {
         kk = gs.kc[t];
       } else if (REFINE) {
@@ -1186,20 +1322,22 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
         kk = exp(gd[((sidx * a.n_layers + t) * (int64_t)a.m + jf) * a.m + iff]);
       }
     }
-    r64[c] = kk;
+    if (REFINE) k32[c] = (float)kk;
+    else r64[c] = kk;
   }
   g.sync();
   // ---- faces (Eq. 3.3, harmonic averages; Dirichlet 2k; no-flow 0) ----
   {
+    auto kc = [&](int c) -> TF { return REFINE ? (TF)k32[c] : (TF)r64[c]; };
     const int nfx = m * (m + 1);
     for (int t = g.rank(); t < 2 * nfx; t += g.size()) {
       if (t < nfx) {
         const int j = t / (m + 1), ip = t - j * (m + 1);
         TF v;
-        if (ip == 0) v = TF(2) * (TF)r64[R.at(0, j)];
-        else if (ip == m) v = TF(2) * (TF)r64[R.at(m - 1, j)];
+        if (ip == 0) v = TF(2) * kc(R.at(0, j));
+        else if (ip == m) v = TF(2) * kc(R.at(m - 1, j));
         else {
-          const TF ka = (TF)r64[R.at(ip - 1, j)], kb = (TF)r64[R.at(ip, j)];
+          const TF ka = kc(R.at(ip - 1, j)), kb = kc(R.at(ip, j));
           v = TF(2) * ka * kb / (ka + kb);
         }
         A.tx[t] = (T)v;
@@ -1210,10 +1348,10 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
         const int jp = u / m, i = u - jp * m;
         TF v = TF(0);
         if (jp > 0 && jp < m) {
-          const TF ka = (TF)r64[R.at(i, jp - 1)], kb = (TF)r64[R.at(i, jp)];
+          const TF ka = kc(R.at(i, jp - 1)), kb = kc(R.at(i, jp));
           v = TF(2) * ka * kb / (ka + kb);
         } else if (a.problem == 1) {  // Dirichlet p = 0 half a cell away
-          v = TF(2) * (TF)r64[R.at(i, jp == 0 ? 0 : m - 1)];
+          v = TF(2) * kc(R.at(i, jp == 0 ? 0 : m - 1));
         }
         A.ty[u] = (T)v;
         if (PREC == 2) L0.ty[u] = face_st<F>((T)v);
@@ -1276,9 +1414,15 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
     bb = g.sum(bb, red64, par);
     double rr = bb;
     const double thr = a.tol * a.tol * bb;
+    // FP32 on a streamed finest grid: the passes on 16-byte quads
+    bool vq = false;
+    if constexpr (std::is_same<T, float>::value && G::kQuads) vq = L0.quads != 0;
     // r64 = b - A64 x64 and its squared norm
     auto residual64 = [&]() -> double {
       double s2 = 0.0;
+      if constexpr (std::is_same<T, float>::value && G::kQuads) {
+        if (vq) return g.sum(ref_residual_quads(g, A, x64, r64, a.problem, fmid), red64, par);
+      }
       for (int c = g.rank(); c < n; c += g.size()) {
         int i, j;
         R.cell(c, i, j);
@@ -1311,12 +1455,19 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
       if (rr <= thr) status = 0;
       double scl = sqrt(rr);
       T rr32 = T(0);
-      for (int c = g.rank(); c < n; c += g.size()) {
-        const T v = (T)(r64[c] / scl);
-        L0.f[c] = v;
-        xv[c] = T(0);
-        rr32 += v * v;
+      // the scaled residual, by multiplication with the reciprocal (FP64 division
+      // is a long instruction sequence at GB300's FP64 rate)
+      const double inv0 = status == 0 ? 0.0 : 1.0 / scl;
+      if constexpr (std::is_same<T, float>::value && G::kQuads) {
+        if (vq) rr32 = ref_rescale_quads(g, n, inv0, r64, L0.f, xv, nullptr, 1.f);
       }
+      if (!vq)
+        for (int c = g.rank(); c < n; c += g.size()) {
+          const T v = (T)(r64[c] * inv0);
+          L0.f[c] = v;
+          xv[c] = T(0);
+          rr32 += v * v;
+        }
       rr32 = g.sum(rr32, red, par);
       g.sync();
       T rr_ref = rr32;
@@ -1332,9 +1483,6 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
         rz = g.sum(rz, red, par);
       }
       int since = 0;
-      // FP32 on a streamed finest grid: the CG passes on 16-byte quads
-      bool vq = false;
-      if constexpr (std::is_same<T, float>::value && G::kQuads) vq = L0.quads != 0;
       while (status != 0 && iters < a.max_it) {
         ++iters;
         ++since;
@@ -1369,7 +1517,11 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
           }
         rr32 = g.sum(rr32, red, par);
         if ((double)rr32 * scl * scl <= thr || rr32 <= d2 * rr_ref || since >= 16) {  // reliable update
-          for (int c = g.rank(); c < n; c += g.size()) x64[c] += scl * (double)xv[c];
+          if constexpr (std::is_same<T, float>::value && G::kQuads) {
+            if (vq) ref_update_quads(g, n, scl, x64, xv);
+          }
+          if (!vq)
+            for (int c = g.rank(); c < n; c += g.size()) x64[c] += scl * (double)xv[c];
           g.sync();
           rr = residual64();
           ++sweeps;
@@ -1379,14 +1531,19 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
           }
           const double scl_new = sqrt(rr);
           const T ratio = (T)(scl / scl_new);
+          const double inv = 1.0 / scl_new;
           rr32 = T(0);
-          for (int c = g.rank(); c < n; c += g.size()) {
-            const T v = (T)(r64[c] / scl_new);
-            L0.f[c] = v;
-            xv[c] = T(0);
-            pv[c] *= ratio;
-            rr32 += v * v;
+          if constexpr (std::is_same<T, float>::value && G::kQuads) {
+            if (vq) rr32 = ref_rescale_quads(g, n, inv, r64, L0.f, xv, pv, ratio);
           }
+          if (!vq)
+            for (int c = g.rank(); c < n; c += g.size()) {
+              const T v = (T)(r64[c] * inv);
+              L0.f[c] = v;
+              xv[c] = T(0);
+              pv[c] *= ratio;
+              rr32 += v * v;
+            }
           rr32 = g.sum(rr32, red, par);
           g.sync();
           rz *= ratio * ratio;
@@ -1425,11 +1582,15 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
       const double scl = sqrt(rr);
       const double inv = 1.0 / scl;
       T r32 = T(0);
-      for (int c = g.rank(); c < n; c += g.size()) {
-        const T v = (T)(r64[c] * inv);
-        L0.f[c] = v;
-        r32 += v * v;
+      if constexpr (std::is_same<T, float>::value && G::kQuads) {
+        if (vq) r32 = ref_rescale_quads(g, n, inv, r64, L0.f, nullptr, nullptr, 1.f);
       }
+      if (!vq)
+        for (int c = g.rank(); c < n; c += g.size()) {
+          const T v = (T)(r64[c] * inv);
+          L0.f[c] = v;
+          r32 += v * v;
+        }
       r32 = g.sum(r32, red, par);
       int st_in = 1;
       const T thr_in = (T)(a.inner_tol * a.inner_tol) * r32;
@@ -1438,7 +1599,11 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
               st_in);
       iters += it;
       // x64 += scl * d, then r64 = b - A64 x64 (FP64)
-      for (int c = g.rank(); c < n; c += g.size()) x64[c] += scl * (double)xv[c];
+      if constexpr (std::is_same<T, float>::value && G::kQuads) {
+        if (vq) ref_update_quads(g, n, scl, x64, xv);
+      }
+      if (!vq)
+        for (int c = g.rank(); c < n; c += g.size()) x64[c] += scl * (double)xv[c];
       g.sync();
       rr = residual64();
       if (it == 0 && st_in != 0) {  // inner solver made no progress
