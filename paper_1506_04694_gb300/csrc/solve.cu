@@ -688,12 +688,126 @@ __device__ __forceinline__ void rb_sweep(const G& g, const Level<T, F>& L, int c
   g.sync();
 }
 
+// (A e) at a quad of four consecutive cells of colour `color` in row j
+// (own-colour indices k0 .. k0 + 3): apply_at's terms in its order, with the
+// neighbours read as in rb_sweep_quads.
+template <typename G>
+__device__ __forceinline__ F4 apply_quad(const Level<float, float>& L, const float* __restrict__ e, int color, int j,
+                                         int k0) {
+  const int m = L.m;
+  const RbIndex R(m);
+  const int hm = R.hm;
+  const int sh = (j + color) & 1;
+  const int c0 = color * R.half + j * hm + k0;
+  const int ob = (color ^ 1) * R.half + j * hm + k0;
+  const F4 v = ld4(e + c0), d = ld4(L.diag + c0), mid = ld4(e + ob);
+  float W[4], E[4];
+  if (sh) {
+    const float after = k0 + 4 < hm ? e[ob + 4] : 0.f;
+    W[0] = mid.v[0]; W[1] = mid.v[1]; W[2] = mid.v[2]; W[3] = mid.v[3];
+    E[0] = mid.v[1]; E[1] = mid.v[2]; E[2] = mid.v[3]; E[3] = after;
+  } else {
+    const float before = k0 > 0 ? e[ob - 1] : 0.f;
+    W[0] = before; W[1] = mid.v[0]; W[2] = mid.v[1]; W[3] = mid.v[2];
+    E[0] = mid.v[0]; E[1] = mid.v[1]; E[2] = mid.v[2]; E[3] = mid.v[3];
+  }
+  F4 s;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) s.v[u] = d.v[u] * v.v[u];
+  const int i0 = 2 * k0 + sh;
+  const float* tx = L.tx + j * (m + 1) + i0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i0 + 2 * u;
+    if (i > 0) s.v[u] -= tx[2 * u] * W[u];
+    if (i < m - 1) s.v[u] -= tx[2 * u + 1] * E[u];
+  }
+  if (j > 0) {
+    const F4 es = ld4(e + ob - hm);
+    const F4 ta = ld4(L.ty + j * m + 2 * k0), tb = ld4(L.ty + j * m + 2 * k0 + 4);
+    const float ty[4] = {sh ? ta.v[1] : ta.v[0], sh ? ta.v[3] : ta.v[2], sh ? tb.v[1] : tb.v[0],
+                         sh ? tb.v[3] : tb.v[2]};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s.v[u] -= ty[u] * es.v[u];
+  }
+  if (j < m - 1) {
+    const F4 en = ld4(e + ob + hm);
+    const F4 ta = ld4(L.ty + (j + 1) * m + 2 * k0), tb = ld4(L.ty + (j + 1) * m + 2 * k0 + 4);
+    const float ty[4] = {sh ? ta.v[1] : ta.v[0], sh ? ta.v[3] : ta.v[2], sh ? tb.v[1] : tb.v[0],
+                         sh ? tb.v[3] : tb.v[2]};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) s.v[u] -= ty[u] * en.v[u];
+  }
+  return s;
+}
+
+// restrict_residual over quads (FP32, the fine level m >= 8 streamed): four
+// consecutive coarse cells I0 .. I0 + 3 of coarse row J take the red quads
+// k = I0 .. I0 + 3 of fine rows 2J and 2J + 1; in the coarse colour-by-colour
+// layout they are two pairs (columns I0, I0 + 2 of one colour and I0 + 1,
+// I0 + 3 of the other), stored as 8-byte accesses.
+template <typename G>
+__device__ __forceinline__ void restrict_residual_quads(const G& g, const Level<float, float>& F,
+                                                        const Level<float, float>& C) {
+  const int mc = C.m, m = F.m;
+  const RbIndex Rf(m), Rc(mc);
+  const int qpr = mc >> 2;  // coarse quads per row
+  const int nqc = mc * qpr;
+  for (int t = g.rank(); t < nqc; t += g.size()) {
+    const int J = t / qpr, I0 = (t - J * qpr) << 2;
+    const F4 a0 = apply_quad<G>(F, F.e, 0, 2 * J, I0), a1 = apply_quad<G>(F, F.e, 0, 2 * J + 1, I0);
+    const F4 f0 = ld4(F.f + 2 * J * Rf.hm + I0), f1 = ld4(F.f + (2 * J + 1) * Rf.hm + I0);
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = (f0.v[u] - a0.v[u]) + (f1.v[u] - a1.v[u]);
+    const int ca = J & 1;  // colour of coarse columns I0, I0 + 2
+    const int base_a = ca * Rc.half + J * Rc.hm + (I0 >> 1), base_b = (ca ^ 1) * Rc.half + J * Rc.hm + (I0 >> 1);
+    *reinterpret_cast<float2*>(C.f + base_a) = make_float2(v[0], v[2]);
+    *reinterpret_cast<float2*>(C.f + base_b) = make_float2(v[1], v[3]);
+  }
+  g.sync();
+}
+
+// prolong_add over quads: the fine quad k0 .. k0 + 3 of row j (either
+// colour) takes coarse columns k0 .. k0 + 3 of coarse row j >> 1, two pairs
+// of the coarse layout.
+template <typename G>
+__device__ __forceinline__ void prolong_add_quads(const G& g, const Level<float, float>& C,
+                                                  const Level<float, float>& F) {
+  const int m = F.m;
+  const RbIndex Rf(m), Rc(C.m);
+  const int nq = (m * Rf.hm) >> 2;  // quads of one colour
+  for (int t = g.rank(); t < 2 * nq; t += g.size()) {
+    const int color = t >= nq ? 1 : 0;
+    const int h0 = (t - color * nq) << 2;
+    const int j = h0 >> Rf.lhm, k0 = h0 - (j << Rf.lhm);
+    const int J = j >> 1;
+    const int ca = J & 1;
+    const float2 pa = *reinterpret_cast<const float2*>(C.e + ca * Rc.half + J * Rc.hm + (k0 >> 1));
+    const float2 pb = *reinterpret_cast<const float2*>(C.e + (ca ^ 1) * Rc.half + J * Rc.hm + (k0 >> 1));
+    const int c0 = color * Rf.half + h0;
+    F4 e = ld4(F.e + c0);
+    e.v[0] += pa.x;
+    e.v[1] += pb.x;
+    e.v[2] += pa.y;
+    e.v[3] += pb.y;
+    st4(F.e + c0, e);
+  }
+  g.sync();
+}
+
 // Coarse f = sum of the fine residuals f - A e over each 2x2 aggregate.
 // Called right after a black half sweep, which leaves the residual at the
 // black cells zero, so only the two red cells (2I, 2J), (2I+1, 2J+1) of the
 // aggregate contribute.
 template <typename T, typename FT, typename G>
 __device__ __forceinline__ void restrict_residual(const G& g, const Level<T, FT>& F, const Level<T, FT>& C) {
+  if constexpr (std::is_same<T, float>::value && std::is_same<FT, float>::value && G::kQuads) {
+    if (F.quads) {
+      restrict_residual_quads(g, F, C);
+      return;
+    }
+  }
   const int mc = C.m, m = F.m;
   const RbIndex Rf(m), Rc(mc);
   const int lmc = log2_pow2(mc);
@@ -724,6 +838,12 @@ __device__ __forceinline__ void restrict_residual(const G& g, const Level<T, FT>
 
 template <typename T, typename FT, typename G>
 __device__ __forceinline__ void prolong_add(const G& g, const Level<T, FT>& C, const Level<T, FT>& F) {
+  if constexpr (std::is_same<T, float>::value && std::is_same<FT, float>::value && G::kQuads) {
+    if (F.quads) {
+      prolong_add_quads(g, C, F);
+      return;
+    }
+  }
   const int m = F.m, mc = C.m;
   const RbIndex Rf(m), Rc(mc);
   const int n = m * m, step = g.size();
@@ -1649,6 +1769,7 @@ __device__ void solve_one(const G& g, const SolveArgs& a, int64_t sys, unsigned 
 }  // namespace mlmc
 
 #include "tiny.cuh"
+
 
 namespace mlmc {
 
