@@ -53,10 +53,9 @@ PREC_NAMES = {0: "fp64", 1: "fp32-mg/fp64-refinement", 2: "fp32-mg-bf16-faces/fp
 # to its kernel's average launch.
 TRAFFIC = {
     "solve_list_kernel<1, 0> [blocks of 512 threads, workspace in global memory]": (
-        50.329e9, 108.927e9,
-        "ncu of bench.py --profile-case sched_block512: the persistent launch of blocks of 512 over the "
-        "headline's levels 2 (fine), 3 and 4 at 2000 / 600 / 160 samples, "
-        "profiles/solve_list_kernel_block512_levels2to4.txt"),
+        292.80e9, 309.10e9,
+        "ncu of bench.py --profile-case sched_block512_headline: the persistent launch of blocks of 512 as the "
+        "headline estimate composes it (level 3 fine, level 4, level 5), profiles/solve_list_kernel_block512_dram.txt"),
     "solve_kernel<1, 0>": (54.23e9, 72.30e9,
                            "ncu of bench.py --profile-case mixed_m256_split: the two solve launches (m = 256 fine, "
                            "m = 128 coarse systems, blocks of 512), profiles/solve_kernel_m256_hbm.txt"),
@@ -526,9 +525,13 @@ PROFILE_CASES = {
                  [(1, 4096, (0, 128, 0, 1, 2), None), (2, 512, (0, 256, 0, 1, 2), None)]),
 }
 
+_P512 = {"threads": 512, "warp": 0, "cluster": 0, "cap_blocks_per_sm": 0, "gamma": 1, "nu": 2, "nu_coarse": 2,
+         "inner_tol": 1e-3, "reliable": 1}
+
 # Multilevel batches under the work-queue schedule: (workload, overrides,
-# per-level plans (level, launch, solver, coarse launch or None), samples per
-# level).  sched_block512: the headline's levels 2..4 with the autotuned plans
+# per-level plans, samples per level); a plan is (level, launch, solver,
+# coarse launch or None) in the arguments of set_launch / set_solver /
+# set_launch_coarse, or (level, plan dict) in the replay form of set_plan.  sched_block512: the headline's levels 2..4 with the autotuned plans
 # of the headline, so that one persistent launch of blocks of 512 (global
 # workspaces) solves level 2's fine systems and all of levels 3 and 4; the
 # first solve_list_kernel launch is that one.
@@ -537,6 +540,20 @@ MULTI_CASES = {
                        [(2, (0, 512, 0, 1, 2), None, (0, 256, 0, 1, 1)), (3, (0, 512, 0, 1, 2), None, None),
                         (4, (0, 512, 0, 1, 2), (1, 1e-3), None)],
                        [0, 0, 2000, 600, 160, 0]),
+    # the headline's level 5 alone in blocks of 512 (512 x 512 fine and 256 x 256
+    # coarse systems, reliable updates): working sets far beyond L2, so DRAM
+    # traffic follows the streaming model
+    "sched_m512": ("lognormal_2layer_cgv_16to512", {},
+                   [(5, (0, 512, 0, 1, 2), (1, 1e-3), (0, 512, 0, 1, 2))],
+                   [0, 0, 0, 0, 0, 96]),
+    # the blocks-of-512 launch of the headline estimate as one autotuned run
+    # composed it (level 3's fine systems, all of level 4, level 5's fine and
+    # coarse systems; full plans), at about a third of the final round's samples
+    "sched_block512_headline": ("lognormal_2layer_cgv_16to512", {},
+                                [(3, dict(_P512, coarse=dict(_P512, threads=256))),
+                                 (4, dict(_P512, coarse=None)),
+                                 (5, dict(_P512, nu=1, nu_coarse=1, coarse=dict(_P512, gamma=2, nu=1, nu_coarse=1)))],
+                                [0, 0, 0, 1600, 390, 117]),
 }
 
 
@@ -547,7 +564,13 @@ def run_profile_case(case):
     if case in MULTI_CASES:
         name, over, plans, n = MULTI_CASES[case]
         with pk.Context(workloads.workload(name, **over), stream=torch.cuda.Stream()) as ctx:
-            for level, launch, solver, coarse in plans:
+            for item in plans:
+                if isinstance(item[1], dict):  # a full plan (replay form)
+                    ctx.set_plan(item[0], item[1], 0)
+                    if item[1].get("coarse"):
+                        ctx.set_plan(item[0], item[1]["coarse"], 1)
+                    continue
+                level, launch, solver, coarse = item
                 ctx.set_launch(level, *launch)
                 if coarse is not None:
                     ctx.set_launch_coarse(level, *coarse)
