@@ -51,6 +51,11 @@ PREC_NAMES = {0: "fp64", 1: "fp32-mg/fp64-refinement", 2: "fp32-mg-bf16-faces/fp
 # library's algorithmic bytes of the same launches, from one-kernel captures of
 # the current kernel versions (profiles/); the line's traffic scales the ratio
 # to its kernel's average launch.
+# Estimator cost model of every estimate (mlmc_estimate's cost_model): 2 = the
+# per-sample GPU cost of each level measured by mlmc_calibrate_costs after the
+# tuning (set from --cost-model in main).
+COST_MODEL = 2
+
 TRAFFIC = {
     "solve_list_kernel<1, 0> [blocks of 512 threads, workspace in global memory]": (
         292.80e9, 309.10e9,
@@ -194,7 +199,11 @@ def config_block(args, d, baseline):
     c = {"workload": args.workload, "m_levels": [d["m0"] << l for l in range(d["L"] + 1)],
          "eps": d["eps"], "sigma2": d["sigma2"][0], "lambda": d["lam"][0], "layers": d["n_layers"],
          "dim": d.get("dim", 2), "norm_r": d["norm_r"], "cgv": d["cgv"], "prec": PREC_NAMES[d["prec"]],
-         "solver_tol": d["tol"], "seed": args.seed, "cost_model": "deterministic m_l^d (1 + n_coarse/2^d)",
+         "solver_tol": d["tol"], "seed": args.seed,
+         "cost_model": ({0: "deterministic m_l^d (1 + n_coarse/2^d)", 1: "measured 64-sample pilot",
+                         2: "measured per-sample GPU time of each level (mlmc_calibrate_costs, fixed for the run)"}
+                        [args.cost_model] if args.impl != "reference" else
+                        "measured per-sample time of each level of the oracle itself"),
          "l2": "flushed between steps (256 MB device write)", "parallelism": "replicas%d" % args.gpus,
          "graph": "each estimate round captured as one CUDA graph",
          "schedule": ("work queue: per launch shape one persistent solver launch across the levels"
@@ -232,7 +241,7 @@ def timed_estimates(ctx, d, seed, steps, warmup, flush, stream):
     context's stream, L2 flushed before each); returns (ms list, last estimate)."""
     import torch
     for _ in range(warmup):
-        ctx.estimate(d["eps"], seed, n_pilot=64, cost_model=0)
+        ctx.estimate(d["eps"], seed, n_pilot=64, cost_model=COST_MODEL)
     torch.cuda.synchronize()
     ms, est = [], None
     for _ in range(steps):
@@ -240,7 +249,7 @@ def timed_estimates(ctx, d, seed, steps, warmup, flush, stream):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        est = ctx.estimate(d["eps"], seed, n_pilot=64, cost_model=0)
+        est = ctx.estimate(d["eps"], seed, n_pilot=64, cost_model=COST_MODEL)
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
@@ -257,7 +266,7 @@ def profiled_pass(ctx, d, est, seed, tune):
     level alone at the estimate's N_l with stage events.  Returns the stage
     totals per step and the per-level records."""
     ctx.profile(True)
-    ctx.estimate(d["eps"], seed, n_pilot=64, cost_model=0)
+    ctx.estimate(d["eps"], seed, n_pilot=64, cost_model=COST_MODEL)
     tot = ctx.profile_read()
     ctx.profile(False)
     per = []
@@ -411,7 +420,7 @@ def roofline_classes(d, tot, peaks, m_of):
     return out
 
 
-def host_estimate_e2e(ctx, d, seed):
+def host_estimate_e2e(ctx, d, seed, costs=None):
     """The same adaptive estimate driven from the host through the host-buffer
     entry point mlmc_level_batch_host: pilot and every top-up round copy the
     per-sample Q_f, Q_c, Q_cgv and iteration counts to host arrays, and the
@@ -421,8 +430,8 @@ def host_estimate_e2e(ctx, d, seed):
     L = d["L"]
     eps = d["eps"]
     dim = d.get("dim", 2)
-    C = []
-    for l in range(L + 1):
+    C = list(costs) if costs else []  # the estimate's costs (calibrated), else the m^d model
+    for l in range(len(C), L + 1):
         nc = 0 if l == 0 else (2 ** dim if d["cgv"] else 1)
         C.append(float((d["m0"] << l) ** dim) * (1.0 + nc / 2.0 ** dim))
     ys = [np.empty(0) for _ in range(L + 1)]
@@ -454,15 +463,14 @@ def run_reference(args, d):
     """The CPU oracle on the host cores, bounded sample per step; same metric
     and unit.  ms_per_step is the measured wall time of one bounded sample;
     the level-samples/s value uses the measured per-level rates with the
-    sample sizes N_l of the oracle's own pilot variances, and the time-to-eps
-    they extrapolate to is reported under its own key."""
+    sample sizes N_l of the oracle's own pilot variances and own per-sample
+    costs, and the time-to-eps they extrapolate to is reported under its own
+    key."""
     import multiprocessing as mp
     import numpy as np
-    from oracle import darcy, mlmc
+    from oracle import mlmc
     cores = min(host_cores(), 16)
     levels = list(range(d["L"] + 1))
-    model = darcy.Model.from_dict(d)
-    C = [mlmc.parity_cost(model, lvl) for lvl in levels]
     walls, values, t_eps = [], [], []
     with mp.get_context("spawn").Pool(cores, initializer=_worker_init) as pool:
         for step in range(args.warmup + args.steps):
@@ -472,6 +480,8 @@ def run_reference(args, d):
                 arr = np.array(results[lvl])
                 y = arr[:, 0] - (arr[:, 2] if (d["cgv"] and lvl) else arr[:, 1])
                 V.append(float(np.var(y, ddof=1)) if len(y) > 1 else float(np.var(arr[:, 0])))
+            # the oracle's own per-sample cost of each level (as the GPU arm uses its own)
+            C = [1.0 / rates[lvl] for lvl in levels]
             N = mlmc.optimal_samples(d["eps"], V, C)
             te = sum(n / rates[lvl] for lvl, n in zip(levels, N))
             if step >= args.warmup:
@@ -719,6 +729,8 @@ def main():
     ap.add_argument("--fp64cg-arm", action="store_true")
     ap.add_argument("--plans", default=None, metavar="FILE",
                     help="launch plans: replayed from FILE if it exists, else tuned and written there")
+    ap.add_argument("--cost-model", type=int, default=2, choices=[0, 1, 2],
+                    help="estimator costs: 2 calibrated per-level GPU time (default), 0 the m^d model")
     ap.add_argument("--schedule", type=int, default=1, choices=[0, 1],
                     help="multilevel schedule (mlmc_set_schedule): 1 work queue per launch shape, 0 per level")
     ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES) + sorted(MULTI_CASES))
@@ -727,6 +739,8 @@ def main():
     ap.add_argument("--limit", type=int, default=0)
     ap.add_argument("--from", dest="start_at", default=None)
     args = ap.parse_args()
+    global COST_MODEL
+    COST_MODEL = args.cost_model
     if args.ncu_summary:
         print(ncu_summary(args.ncu_summary, args.skip, args.start_at, args.limit))
         return
@@ -784,6 +798,7 @@ def main():
         replay = json.load(open(args.plans))
     ctx.set_schedule(args.schedule)
     sched_tune = None
+    calib = lambda c: c.calibrate_costs(seed=args.seed + 777) if COST_MODEL == 2 else None
     if replay:
         ctx.set_plans(replay["mixed"])
         tune = replay["mixed"]
@@ -791,8 +806,11 @@ def main():
     else:
         tune = ctx.autotune(seed=args.seed + 12345)
         if args.schedule:
-            before, after, tune = ctx.autotune_schedule(d["eps"], seed=args.seed + 4242, n_pilot=64, cost_model=0)
+            calib(ctx)
+            before, after, tune = ctx.autotune_schedule(d["eps"], seed=args.seed + 4242, n_pilot=64,
+                                                        cost_model=COST_MODEL)
             sched_tune = {"estimate_ms_before": before, "estimate_ms_after": after}
+    costs = calib(ctx)  # the per-sample costs of the final plans
     bctx = btune = None
     if base is not None:
         bctx = pk.Context(base, device=local, stream=stream)
@@ -803,10 +821,12 @@ def main():
         else:
             btune = bctx.autotune(seed=args.seed + 12345)
             if args.schedule:
+                calib(bctx)
                 bb, ba, btune = bctx.autotune_schedule(base["eps"], seed=args.seed + 4242, n_pilot=64,
-                                                       cost_model=0, reps=1)
+                                                       cost_model=COST_MODEL, reps=1)
                 sched_tune = dict(sched_tune or {}, plain_fp64_arm={"estimate_ms_before": bb,
                                                                     "estimate_ms_after": ba})
+    bcosts = calib(bctx) if bctx is not None else None
     if args.plans and not replay and rank == 0:
         json.dump({"mixed": tune, "plain": btune}, open(args.plans, "w"))
     seed = args.seed + 7919 * rank
@@ -822,7 +842,7 @@ def main():
     clocks.start()
     # ---- timed region: the mixed CGV arm (the line's value) ----
     for _ in range(args.warmup):
-        ctx.estimate(d["eps"], seed, n_pilot=64, cost_model=0)
+        ctx.estimate(d["eps"], seed, n_pilot=64, cost_model=COST_MODEL)
     barrier()
     torch.cuda.synchronize(dev)
     step_ms, est = timed_estimates(ctx, d, seed, args.steps, 0, flush, stream)
@@ -836,7 +856,7 @@ def main():
         base_out = {"time_to_eps_s": sum(bms) / len(bms) / 1e3, "steps": args.baseline_steps,
                     "warmup": max(3, args.warmup), "N_per_level": best["N"], "q_hat": best["q_hat"],
                     "var_hat": best["var_hat"], "level_samples_per_s": sum(best["N"]) / (sum(bms) / len(bms) / 1e3),
-                    "prec": PREC_NAMES[base["prec"]], "cgv": base["cgv"],
+                    "prec": PREC_NAMES[base["prec"]], "cgv": base["cgv"], "level_costs_s": bcosts,
                     "autotune": [{"m": base["m0"] << l, "threads": t["threads"], "warp": t["warp"],
                                   "cluster": t["cluster"], "nu": t["nu"]} for l, t in enumerate(btune)]}
     clk = clocks.stop()
@@ -864,7 +884,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         torch.cuda.synchronize(dev)
-        te, n_e2e, d2h = host_estimate_e2e(ctx, d, seed)
+        te, n_e2e, d2h = host_estimate_e2e(ctx, d, seed, costs)
         e2e = {"value": n_e2e / te, "unit": "level-samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
                "seconds": te,
                "note": "the same adaptive estimate driven from the host through mlmc_level_batch_host: per-sample "
@@ -875,7 +895,7 @@ def main():
     # kernel launches of one estimate (the same kernels run inside the graphs of
     # the timed steps), times the timed steps
     ctx.profile(True)
-    ctx.estimate(d["eps"], seed, n_pilot=64, cost_model=0)
+    ctx.estimate(d["eps"], seed, n_pilot=64, cost_model=COST_MODEL)
     launches = int(sum(ctx.profile_read()["launches"].values())) * args.steps
     ctx.profile(False)
     t_mix = total_ms / args.steps / 1e3
@@ -908,6 +928,7 @@ def main():
                       for r in per],
         "peaks": {"fp64_tflops": fp64_peak, "fp32_tflops": fp32_peak, "hbm_gbs": hbm},
         "plain_fp64_arm": base_out,
+        "level_costs_s": costs,
     }
     if pool is not None:
         levels = list(range(d["L"] + 1))

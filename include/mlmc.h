@@ -199,9 +199,23 @@ MLMC_API int mlmc_level_batch_host(mlmc_ctx* ctx, int level, int64_t first, int6
  * to N_l = ceil(2 eps^-2 sqrt(V_l/C_l) sum_k sqrt(V_k C_k)) until no level
  * needs more (at most 10 rounds).  cost_model 0: C_l = m_l^d (1 + n_coarse/2^d)
  * with n_coarse = 0 at level 0, 1 plain, 2^d CGV (deterministic); 1: C_l =
- * measured seconds per sample of the pilot.  out: host pointer, required. */
+ * measured seconds per sample of the pilot (64-sample batches: latency more
+ * than throughput); 2: C_l = the per-sample GPU time of each level measured
+ * by mlmc_calibrate_costs() (deterministic while those costs are kept).
+ * out: host pointer, required. */
 MLMC_API int mlmc_estimate(mlmc_ctx* ctx, double eps, uint64_t seed, int32_t n_pilot,
                   int32_t cost_model, mlmc_estimate_out* out);
+
+/* Measure the cost C_l of one sample of each level for the estimator's
+ * sample sizes (Eq. 3.7's N_l depend on the costs; cost_model 2 of
+ * mlmc_estimate): the per-sample GPU time (CUDA events on the context stream:
+ * fields, fine and coarse solves, reductions) of a batch of each level alone,
+ * large enough to fill the GPU (2^26 cells, 64 to 65536 samples, from sample
+ * index 2^40 on, so that no sample of real use is consumed), the faster of
+ * two after one untimed batch, with the context's current launch plans (run
+ * it after tuning).  The context keeps the costs; C (host array of L+1, or
+ * NULL) receives them in seconds.  Errors: those of mlmc_level_batch(). */
+MLMC_API int mlmc_calibrate_costs(mlmc_ctx* ctx, uint64_t seed, double* C);
 
 /* mlmc_estimate() with a cap on the number of top-up rounds (0 = pilot only);
  * mlmc_estimate() is this call with max_rounds = 10.  After a call the
@@ -313,8 +327,8 @@ MLMC_API int mlmc_autotune(mlmc_ctx* ctx, uint64_t seed, mlmc_tune_report* rep);
  * launch; in the work-queue schedule the systems of all levels that share a
  * launch shape fill each other's tails.  This pass, run after
  * mlmc_autotune() (or on the default plans), re-times whole adaptive
- * estimates (mlmc_estimate(ctx, eps, seed, n_pilot, cost_model): one
- * untimed, then the fastest of `reps` timed with CUDA events on the context
+ * estimates (mlmc_estimate(ctx, eps, seed, n_pilot, cost_model), cost_model
+ * 0, 1 or 2: one untimed, then the fastest of `reps` timed with CUDA events on the context
  * stream) while it changes the launch shape of each part with systems of
  * side >= 256 (the fine systems of a level, and its coarse systems as a
  * launch of their own), finest level first: a cluster plan tries one block

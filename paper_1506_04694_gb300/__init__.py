@@ -126,6 +126,7 @@ EXPORTS = {
                                               ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "mlmc_set_solver": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_double]),
     "mlmc_set_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "mlmc_calibrate_costs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
     "mlmc_set_launch_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_double]),
@@ -391,6 +392,14 @@ class Context:
         """mlmc_set_solver: mixed-precision scheme of a level (reliable updates or restarted
         refinement) and its FP32 tolerance."""
         _check(lib().mlmc_set_solver(self._h, level, reliable, inner_tol), allow_failed=False)
+
+    def calibrate_costs(self, seed=0):
+        """mlmc_calibrate_costs: per-sample GPU seconds of each level at GPU-filling batch sizes,
+        kept for estimates with cost_model=2; returns the list."""
+        L = self.model.L + 1
+        C = (ctypes.c_double * L)()
+        _check(lib().mlmc_calibrate_costs(self._h, seed, C), allow_failed=False)
+        return list(C)
 
     def set_schedule(self, schedule):
         """mlmc_set_schedule: 1 = one work-queue launch per launch shape across the levels of a

@@ -167,6 +167,9 @@ struct mlmc_ctx {
   // class stream of its own with its own workspace and work counter
   static constexpr int kClasses = 2 * MLMC_MAX_LEVELS;
   int sched = 1;
+  // per-sample GPU cost of each level measured by mlmc_calibrate_costs (seconds)
+  double cal_C[MLMC_MAX_LEVELS] = {};
+  bool cal_ok = false;
   cudaStream_t cst[kClasses] = {};
   cudaEvent_t class_done[kClasses] = {}, fields_done[MLMC_MAX_LEVELS] = {};
   Buf sched_cnt, sched_ws[kClasses];
@@ -1399,6 +1402,12 @@ int mlmc_estimate_ex(mlmc_ctx* c, double eps, uint64_t seed, int32_t n_pilot, in
     C = c->resume_est.C;
     rounds = c->resume_est.rounds;
     c->resume_est.valid = false;
+  } else if (cost_model == 2) {
+    if (!c->cal_ok) return fail(MLMC_ERR_ARG, "cost_model 2 needs mlmc_calibrate_costs first");
+    int r = multilevel_impl(c, NL, first.data(), cnt.data(), seed, true, S.data());
+    if (r < 0) return r;
+    rc_any |= r;
+    for (int l = 0; l < NL; ++l) C[l] = c->cal_C[l];
   } else if (cost_model == 1) {
     // measured cost: the pilot runs level by level so that each is timed
     for (int l = 0; l < NL; ++l) {
@@ -1806,8 +1815,8 @@ static void report_plans(const mlmc_ctx* c, mlmc_tune_report* rep) {
 int mlmc_autotune_schedule(mlmc_ctx* c, double eps, uint64_t seed, int32_t n_pilot, int32_t cost_model,
                            int32_t reps, double* ms, mlmc_tune_report* rep) {
   if (!c) return fail(MLMC_ERR_ARG, "null context");
-  if (!(eps > 0) || n_pilot < 2 || reps < 1 || (cost_model != 0 && cost_model != 1))
-    return fail(MLMC_ERR_ARG, "eps > 0, n_pilot >= 2, reps >= 1, cost_model 0 or 1");
+  if (!(eps > 0) || n_pilot < 2 || reps < 1 || cost_model < 0 || cost_model > 2)
+    return fail(MLMC_ERR_ARG, "eps > 0, n_pilot >= 2, reps >= 1, cost_model 0, 1 or 2");
   CUDA_TRY(cudaSetDevice(c->device));
   const mlmc_model& md = c->model;
   if (ms) ms[0] = ms[1] = 0.0;
@@ -1906,6 +1915,48 @@ int mlmc_autotune_schedule(mlmc_ctx* c, double eps, uint64_t seed, int32_t n_pil
   if (err) return err;
   if (ms) ms[1] = best;
   if (rep) report_plans(c, rep);
+  return 0;
+}
+
+int mlmc_calibrate_costs(mlmc_ctx* c, uint64_t seed, double* C_out) {
+  if (!c) return fail(MLMC_ERR_ARG, "null context");
+  CUDA_TRY(cudaSetDevice(c->device));
+  const mlmc_model& md = c->model;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  int err = 0;
+  for (int l = 0; l <= md.L && !err; ++l) {
+    // enough samples to fill the GPU at every level (2^26 cells, 64 .. 65536
+    // samples), from sample index 2^40 on so that no sample of real use is
+    // consumed; one untimed batch (allocations, caches), then the faster of two
+    const int64_t n = std::max<int64_t>(64, std::min<int64_t>(65536, ((int64_t)1 << 26) / cells_of(md, md.m0 << l)));
+    mlmc_level_sums s;
+    double best = 1e300;
+    for (int r = 0; r < 3 && !err; ++r) {
+      if (r > 0 && cudaEventRecord(e0, c->st) != cudaSuccess) err = fail(MLMC_ERR_CUDA, "event");
+      if (!err) {
+        const int rc = mlmc_level_batch(c, l, (int64_t)1 << 40, n, seed, nullptr, nullptr, nullptr, nullptr, &s);
+        if (rc < 0) err = rc;
+      }
+      if (!err && r > 0) {
+        if (cudaEventRecord(e1, c->st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+          err = fail(MLMC_ERR_CUDA, "event");
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        best = std::min(best, (double)ms);
+      }
+    }
+    if (!err) c->cal_C[l] = best * 1e-3 / (double)n;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err) return err;
+  c->cal_ok = true;
+  if (C_out)
+    for (int l = 0; l <= md.L; ++l) C_out[l] = c->cal_C[l];
   return 0;
 }
 

@@ -143,3 +143,22 @@ def test_plans_replay_in_another_context():
     for l in range(len(n)):
         for key in ("n", "n_failed", "iters_total") + pk.SUM_FIELDS:
             assert ra[l][key] == rb[l][key], (l, key)
+
+
+def test_calibrated_costs_estimate():
+    # mlmc_calibrate_costs: positive per-sample costs, growing with the grid
+    # from level 1 on; an estimate on them meets the sampling-error target of
+    # Eq. 3.7 and is deterministic while the costs are kept
+    torch, pk = need_gpu()
+    d = workloads.workload("lognormal_2layer_cgv_16to512", L=3)
+    with pk.Context(d, stream=torch.cuda.Stream()) as ctx:
+        with pytest.raises(pk.MLMCError):
+            ctx.estimate(4e-3, seed=2, n_pilot=32, cost_model=2)
+        C = ctx.calibrate_costs(seed=1)
+        assert len(C) == 4 and all(c > 0 for c in C)
+        assert C[3] > C[2] > C[1]
+        e1 = ctx.estimate(4e-3, seed=2, n_pilot=32, cost_model=2)
+        e2 = ctx.estimate(4e-3, seed=2, n_pilot=32, cost_model=2)
+    assert list(e1["N"]) == list(e2["N"]) and e1["q_hat"] == e2["q_hat"]
+    assert list(e1["C"]) == C
+    assert sum(v / n for v, n in zip(e1["V"], e1["N"])) <= 0.5 * 4e-3 ** 2 * (1 + 1e-12)
