@@ -422,9 +422,10 @@ def roofline_classes(d, tot, peaks, m_of):
 
 def host_estimate_e2e(ctx, d, seed, costs=None):
     """The same adaptive estimate driven from the host through the host-buffer
-    entry point mlmc_level_batch_host: pilot and every top-up round copy the
-    per-sample Q_f, Q_c, Q_cgv and iteration counts to host arrays, and the
-    sample sizes come from those host values (same rule as mlmc_estimate).
+    entry point mlmc_multilevel_batch_host: pilot and every top-up round copy
+    the per-sample Q_f, Q_c, Q_cgv and iteration counts of all levels to host
+    arrays, and the sample sizes come from those host values (same rule as
+    mlmc_estimate).
     Returns (seconds, sum N_l, d2h bytes)."""
     import numpy as np
     L = d["L"]
@@ -440,13 +441,16 @@ def host_estimate_e2e(ctx, d, seed, costs=None):
     t0 = time.perf_counter()
     want = [64] * (L + 1)
     for _ in range(11):  # the pilot and at most ten top-up rounds
+        n = [max(0, want[l] - len(ys[l])) for l in range(L + 1)]
+        # all levels of the round in one call (work-queue schedule, captured graph),
+        # per-sample values copied to host arrays
+        res = ctx.multilevel_batch_host(n, seed, first=list(tried))
         for l in range(L + 1):
-            n = want[l] - len(ys[l])
-            if n <= 0:
+            if n[l] <= 0:
                 continue
-            s, qf, qc, qg, it = ctx.level_batch_host(l, n, seed, first=tried[l])
-            tried[l] += n
-            d2h += n * (3 * 8 + 4)
+            s, qf, qc, qg, it = res[l]
+            tried[l] += n[l]
+            d2h += n[l] * (3 * 8 + 4)
             y = qf - (qg if (d["cgv"] and l > 0) else qc)
             ys[l] = np.concatenate([ys[l], y[np.isfinite(y)]])
         V = [float(np.var(y, ddof=1)) for y in ys]
@@ -887,10 +891,10 @@ def main():
         te, n_e2e, d2h = host_estimate_e2e(ctx, d, seed, costs)
         e2e = {"value": n_e2e / te, "unit": "level-samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
                "seconds": te,
-               "note": "the same adaptive estimate driven from the host through mlmc_level_batch_host: per-sample "
-                       "Q_f, Q_c, Q_cgv and iterations of the pilot and every top-up copied to host arrays inside "
-                       "the timed region, sample sizes from those host values, levels one after another; the "
-                       "only inputs are (seed, model) passed by value"}
+               "note": "the same adaptive estimate driven from the host through mlmc_multilevel_batch_host: "
+                       "per-sample Q_f, Q_c, Q_cgv and iterations of the pilot and every top-up (all levels of a "
+                       "round in one call) copied to host arrays inside the timed region, sample sizes from those "
+                       "host values; the only inputs are (seed, model) passed by value"}
 
     # kernel launches of one estimate (the same kernels run inside the graphs of
     # the timed steps), times the timed steps

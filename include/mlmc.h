@@ -276,6 +276,18 @@ MLMC_API int mlmc_resume(mlmc_ctx* ctx, const char* path);
 MLMC_API int mlmc_multilevel_batch(mlmc_ctx* ctx, int32_t n_levels, const int64_t* first, const int64_t* n,
                                    uint64_t seed, int32_t use_graph, mlmc_level_sums* sums);
 
+/* mlmc_multilevel_batch() with the per-sample results of every level copied
+ * to host memory before returning (the multilevel form of
+ * mlmc_level_batch_host(): the levels of a round run together, in the same
+ * schedule and graph).  qf, qc, qc_cgv, iters: host arrays of n_levels
+ * pointers (or NULL), each entry a host array of n[l] values (or NULL: not
+ * copied); the values are those of mlmc_level_batch() (Q_f, Q_c, the CGV
+ * average of Eq. 4.1, CG iterations).  Ownership stays with the caller.
+ * Errors: as mlmc_multilevel_batch(). */
+MLMC_API int mlmc_multilevel_batch_host(mlmc_ctx* ctx, int32_t n_levels, const int64_t* first, const int64_t* n,
+                                        uint64_t seed, int32_t use_graph, double* const* qf, double* const* qc,
+                                        double* const* qc_cgv, int32_t* const* iters, mlmc_level_sums* sums);
+
 /* Result of mlmc_autotune(), per level. */
 typedef struct mlmc_tune_report {
   int32_t threads[MLMC_MAX_LEVELS];            /* threads per block chosen */

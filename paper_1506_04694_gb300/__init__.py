@@ -114,6 +114,10 @@ EXPORTS = {
     "mlmc_multilevel_batch": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
                                              ctypes.POINTER(ctypes.c_int64), ctypes.c_uint64, ctypes.c_int32,
                                              ctypes.POINTER(LevelSums)]),
+    "mlmc_multilevel_batch_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                                  ctypes.POINTER(ctypes.c_int64), ctypes.c_uint64, ctypes.c_int32,
+                                                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                  ctypes.POINTER(LevelSums)]),
     "mlmc_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(TuneReport)]),
     "mlmc_estimate_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_uint64, ctypes.c_int32,
                                         ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(EstimateOut)]),
@@ -313,6 +317,26 @@ class Context:
         out = [S[i].as_dict() for i in range(k)]
         for o in out:
             o["rc"] = rc
+        return out
+
+    def multilevel_batch_host(self, n, seed, first=None, use_graph=True):
+        """mlmc_multilevel_batch_host: levels 0..len(n)-1 in one call, per-sample outputs copied to
+        host numpy arrays; list of (level-sum dict, qf, qc, qc_cgv, iters) per level."""
+        import numpy as np
+        k = len(n)
+        first = first or [0] * k
+        arrs = [(np.empty(n[l]), np.empty(n[l]), np.empty(n[l]), np.empty(n[l], dtype=np.int32)) for l in range(k)]
+        ptrs = [(ctypes.c_void_p * k)(*[arrs[l][j].ctypes.data if n[l] > 0 else None for l in range(k)])
+                for j in range(4)]
+        S = (LevelSums * k)()
+        rc = _check(lib().mlmc_multilevel_batch_host(self._h, k, (ctypes.c_int64 * k)(*first),
+                                                     (ctypes.c_int64 * k)(*n), seed, 1 if use_graph else 0,
+                                                     ptrs[0], ptrs[1], ptrs[2], ptrs[3], S))
+        out = []
+        for l in range(k):
+            d = S[l].as_dict()
+            d["rc"] = rc
+            out.append((d,) + arrs[l])
         return out
 
     def autotune(self, seed=0):

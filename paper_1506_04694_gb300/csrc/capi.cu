@@ -138,7 +138,7 @@ struct mlmc_ctx {
   mlmc_profile_stats prof{};
   // per-level slots of the multilevel batch (outputs, sums, iteration counters)
   struct Slot {
-    Buf qf, qc, qg, sums, itacc;
+    Buf qf, qc, qg, it, sums, itacc;
     WorkBufs wb;
   } slot[MLMC_MAX_LEVELS];
   HostLevel* host = nullptr;  // pinned, MLMC_MAX_LEVELS + 1 entries (last: single-level calls)
@@ -669,7 +669,7 @@ int level_batch_impl(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t 
 
 // Allocate, outside any stream capture, every buffer a range of n samples of
 // `level` will touch.
-int prepare_level(mlmc_ctx* c, int level, int64_t n) {
+int prepare_level(mlmc_ctx* c, int level, int64_t n, bool want_iters = false) {
   const mlmc_model& md = c->model;
   const int m = md.m0 << level;
   const bool f32 = fields_f32(md);
@@ -697,6 +697,8 @@ int prepare_level(mlmc_ctx* c, int level, int64_t n) {
   if (int e = S.qf.ensure((size_t)n * 8)) return e;
   if (int e = S.qc.ensure((size_t)n * 8)) return e;
   if (int e = S.qg.ensure((size_t)n * 8)) return e;
+  if (want_iters)
+    if (int e = S.it.ensure((size_t)n * 4)) return e;
   if (int e = S.sums.ensure(256 + reduce_ws_bytes())) return e;
   if (int e = S.itacc.ensure(3 * sizeof(int64_t))) return e;
   return 0;
@@ -791,7 +793,8 @@ bool sched_usable(const mlmc_ctx* c, int n_levels, const int64_t* n) {
 // batch touches: per level one chunk of embedding intermediates, the fields
 // and the per-system outputs of the whole range, the level's results; per
 // class a workspace and a work counter, a stream and an event.
-int prepare_sched(mlmc_ctx* c, int n_levels, const int64_t* n, const std::vector<SchedClass>& cls) {
+int prepare_sched(mlmc_ctx* c, int n_levels, const int64_t* n, const std::vector<SchedClass>& cls,
+                  bool want_iters) {
   const mlmc_model& md = c->model;
   const bool f32 = fields_f32(md);
   for (int l = 0; l < n_levels; ++l) {
@@ -810,6 +813,8 @@ int prepare_sched(mlmc_ctx* c, int n_levels, const int64_t* n, const std::vector
     if (int e = S.qf.ensure((size_t)n[l] * 8)) return e;
     if (int e = S.qc.ensure((size_t)n[l] * 8)) return e;
     if (int e = S.qg.ensure((size_t)n[l] * 8)) return e;
+    if (want_iters)
+      if (int e = S.it.ensure((size_t)n[l] * 4)) return e;
     if (int e = S.sums.ensure(256 + reduce_ws_bytes())) return e;
     if (int e = S.itacc.ensure(3 * sizeof(int64_t))) return e;
     if (!c->fields_done[l] && cudaEventCreateWithFlags(&c->fields_done[l], cudaEventDisableTiming) != cudaSuccess)
@@ -838,7 +843,7 @@ int prepare_sched(mlmc_ctx* c, int n_levels, const int64_t* n, const std::vector
 // host memory, joined into the context stream.  With `serial` the three
 // phases run in this order on the context stream.
 int enqueue_sched(mlmc_ctx* c, int n_levels, const int64_t* first, const int64_t* n, uint64_t seed,
-                  const std::vector<SchedClass>& cls, int* prof_cls, bool serial) {
+                  const std::vector<SchedClass>& cls, int* prof_cls, bool serial, bool want_iters) {
   const mlmc_model& md = c->model;
   const bool f32 = fields_f32(md);
   // serial: everything in order on the context stream (events and waits then
@@ -933,7 +938,7 @@ int enqueue_sched(mlmc_ctx* c, int n_levels, const int64_t* first, const int64_t
     int64_t* itacc = S.itacc.as<int64_t>();
     StageTimer t(c, 2);
     if (gather_launch(S.wb.qsys.as<double>(), S.wb.itsys.as<int32_t>(), n[l], nc, md.cgv, cells_of(md, m),
-                      cells_of(md, m / 2), qf, qc, qg, nullptr, itacc, ls))
+                      cells_of(md, m / 2), qf, qc, qg, want_iters ? S.it.as<int32_t>() : nullptr, itacc, ls))
       return fail(MLMC_ERR_CUDA, "gather kernel");
     unsigned char* sums_dev = S.sums.as<unsigned char>();
     if (reduce_launch(qf, qc, qg, n[l], md.cgv != 0, itacc, reinterpret_cast<LevelSumsDev*>(sums_dev),
@@ -956,16 +961,16 @@ int enqueue_sched(mlmc_ctx* c, int n_levels, const int64_t* first, const int64_t
 // with use_graph the queue is captured once into a CUDA graph (kept for the
 // next call with the same arguments) and launched as one graph.
 int multilevel_impl(mlmc_ctx* c, int n_levels, const int64_t* first, const int64_t* n, uint64_t seed,
-                    bool use_graph, mlmc_level_sums* sums) {
+                    bool use_graph, mlmc_level_sums* sums, bool want_iters = false) {
   std::vector<SchedClass> cls;
   const bool sched = sched_usable(c, n_levels, n);
   if (sched) {
     if (int e = sched_classes(c, n_levels, n, cls)) return e;
-    if (int e = prepare_sched(c, n_levels, n, cls)) return e;
+    if (int e = prepare_sched(c, n_levels, n, cls, want_iters)) return e;
   } else {
     for (int l = 0; l < n_levels; ++l)
       if (n[l] > 0)
-        if (int e = prepare_level(c, l, n[l])) return e;
+        if (int e = prepare_level(c, l, n[l], want_iters)) return e;
   }
   // the levels run side by side, each on its own stream with its own work
   // buffers, forked from and joined back into the context stream; with
@@ -996,7 +1001,7 @@ int multilevel_impl(mlmc_ctx* c, int n_levels, const int64_t* first, const int64
     }
   }
   auto enqueue_all = [&]() -> int {
-    if (sched) return enqueue_sched(c, n_levels, first, n, seed, cls, prof_cls, c->prof_on || graph);
+    if (sched) return enqueue_sched(c, n_levels, first, n, seed, cls, prof_cls, c->prof_on || graph, want_iters);
     if (side_by_side && cudaEventRecord(c->fork, c->st) != cudaSuccess) return fail(MLMC_ERR_CUDA, "fork event");
     for (int l = 0; l < n_levels; ++l) {
       if (n[l] <= 0) continue;
@@ -1006,8 +1011,8 @@ int multilevel_impl(mlmc_ctx* c, int n_levels, const int64_t* first, const int64
       {
         UseBufs use(c, &S.wb, ls);
         if (int e = enqueue_level(c, l, first[l], n[l], seed, S.qf.as<double>(), S.qc.as<double>(),
-                                  S.qg.as<double>(), nullptr, S.sums.as<unsigned char>(), S.itacc.as<int64_t>(),
-                                  c->host + l))
+                                  S.qg.as<double>(), want_iters ? S.it.as<int32_t>() : nullptr,
+                                  S.sums.as<unsigned char>(), S.itacc.as<int64_t>(), c->host + l))
           return e;
       }
       if (side_by_side && (cudaEventRecord(c->lev_done[l], ls) != cudaSuccess ||
@@ -1018,7 +1023,7 @@ int multilevel_impl(mlmc_ctx* c, int n_levels, const int64_t* first, const int64
   };
   if (graph) {
     std::vector<int64_t> key = {(int64_t)n_levels, (int64_t)seed, (int64_t)g_alloc_generation.load(),
-                                (int64_t)sched};
+                                (int64_t)sched, (int64_t)want_iters};
     for (int l = 0; l < n_levels; ++l) {
       key.push_back(c->tuned_ok[l] ? ((int64_t)c->tuned[l].nu << 28) + ((int64_t)c->tuned[l].gamma << 24) +
                                          ((int64_t)c->tuned[l].threads << 16) +
@@ -1316,7 +1321,7 @@ void mlmc_destroy(mlmc_ctx* c) {
   for (Buf* b : {&c->oqf, &c->oqc, &c->oqg, &c->oit, &c->sums, &c->itacc, &c->g64, &c->bm}) b->release();
   c->misc.release();
   for (auto& S : c->slot) {
-    for (Buf* b : {&S.qf, &S.qc, &S.qg, &S.sums, &S.itacc}) b->release();
+    for (Buf* b : {&S.qf, &S.qc, &S.qg, &S.it, &S.sums, &S.itacc}) b->release();
     S.wb.release();
   }
   for (int l = 0; l < MLMC_MAX_LEVELS; ++l) {
@@ -1592,6 +1597,34 @@ int mlmc_multilevel_batch(mlmc_ctx* c, int32_t n_levels, const int64_t* first, c
   CUDA_TRY(cudaSetDevice(c->device));
   const double t0 = now_s();
   const int r = multilevel_impl(c, n_levels, first, n, seed, use_graph != 0, sums);
+  const double dt = now_s() - t0;
+  for (int l = 0; l < n_levels; ++l) sums[l].seconds = dt;
+  return r;
+}
+
+int mlmc_multilevel_batch_host(mlmc_ctx* c, int32_t n_levels, const int64_t* first, const int64_t* n,
+                               uint64_t seed, int32_t use_graph, double* const* qf, double* const* qc,
+                               double* const* qc_cgv, int32_t* const* iters, mlmc_level_sums* sums) {
+  if (!c || !first || !n || !sums) return fail(MLMC_ERR_ARG, "null argument");
+  if (n_levels < 1 || n_levels > c->model.L + 1) return fail(MLMC_ERR_ARG, "n_levels out of range");
+  for (int l = 0; l < n_levels; ++l)
+    if (n[l] < 0 || first[l] < 0) return fail(MLMC_ERR_ARG, "negative sample range");
+  CUDA_TRY(cudaSetDevice(c->device));
+  bool want_iters = false;
+  for (int l = 0; l < n_levels && iters; ++l) want_iters = want_iters || (iters[l] && n[l] > 0);
+  const double t0 = now_s();
+  const int r = multilevel_impl(c, n_levels, first, n, seed, use_graph != 0, sums, want_iters);
+  if (r < 0) return r;
+  for (int l = 0; l < n_levels; ++l) {
+    if (n[l] <= 0) continue;
+    const auto& S = c->slot[l];
+    const size_t nb = (size_t)n[l];
+    if (qf && qf[l]) CUDA_TRY(cudaMemcpyAsync(qf[l], S.qf.p, nb * 8, cudaMemcpyDeviceToHost, c->st));
+    if (qc && qc[l]) CUDA_TRY(cudaMemcpyAsync(qc[l], S.qc.p, nb * 8, cudaMemcpyDeviceToHost, c->st));
+    if (qc_cgv && qc_cgv[l]) CUDA_TRY(cudaMemcpyAsync(qc_cgv[l], S.qg.p, nb * 8, cudaMemcpyDeviceToHost, c->st));
+    if (iters && iters[l]) CUDA_TRY(cudaMemcpyAsync(iters[l], S.it.p, nb * 4, cudaMemcpyDeviceToHost, c->st));
+  }
+  CUDA_TRY(cudaStreamSynchronize(c->st));
   const double dt = now_s() - t0;
   for (int l = 0; l < n_levels; ++l) sums[l].seconds = dt;
   return r;

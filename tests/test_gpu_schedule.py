@@ -162,3 +162,26 @@ def test_calibrated_costs_estimate():
     assert list(e1["N"]) == list(e2["N"]) and e1["q_hat"] == e2["q_hat"]
     assert list(e1["C"]) == C
     assert sum(v / n for v, n in zip(e1["V"], e1["N"])) <= 0.5 * 4e-3 ** 2 * (1 + 1e-12)
+
+
+def test_multilevel_host_outputs_match_level_batches():
+    # mlmc_multilevel_batch_host: the per-sample values of every level equal
+    # those of mlmc_level_batch_host, with and without the work-queue schedule
+    torch, pk = need_gpu()
+    import numpy as np
+    d = workloads.workload("lognormal_2layer_cgv_16to512", L=3)
+    n = [500, 0, 30, 7]
+    first = [4, 0, 9, 1]
+    with pk.Context(d, stream=torch.cuda.Stream()) as ctx:
+        ref = [ctx.level_batch_host(l, n[l], 6, first=first[l]) if n[l] else None for l in range(4)]
+        for sched in (1, 0):
+            ctx.set_schedule(sched)
+            for use_graph in (False, True):
+                got = ctx.multilevel_batch_host(n, 6, first=first, use_graph=use_graph)
+                for l in range(4):
+                    if not n[l]:
+                        continue
+                    for j in range(1, 5):
+                        np.testing.assert_array_equal(got[l][j], ref[l][j])
+                    for key in ("n", "n_failed", "iters_total") + pk.SUM_FIELDS:
+                        assert got[l][0][key] == ref[l][0][key], (sched, use_graph, l, key)
