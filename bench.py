@@ -390,33 +390,48 @@ def roofline_classes(d, tot, peaks, m_of):
                  "smem": 1, "levels": []})
     total = sum(c["ms"] for c in cand)
     shares = {"%s [%s]" % (c["kernel"], c["shape"]): round(c["ms"] / total, 4) for c in cand}
-    k = max(cand, key=lambda c: c["ms"])
     f32 = d["prec"] in (1, 2)
-    base = {"kernel": k["kernel"], "launch_shape": k["shape"], "levels": k["levels"],
-            "systems_m": sorted({m_of(l) for l in k["levels"]}, reverse=True), "launches": k["launches"]}
-    if k["kernel"].startswith("solve") and not k["smem"]:
-        ach = k["bytes"] / (k["ms"] / 1e3) / 1e9
-        per_launch = k["bytes"] / max(k["launches"], 1)
-        key = "%s [%s]" % (k["kernel"], k["shape"])
-        traffic, tsrc = None, "no counter capture of this kernel version and launch shape"
-        if key in TRAFFIC:
-            dram, alg, tsrc = TRAFFIC[key]
-            traffic = dram / alg * per_launch
-        out = dict(base, bound="hbm", achieved=ach, peak=peaks["hbm"], unit="GB/s", frac=ach / peaks["hbm"],
-                   traffic=traffic, peak_source=peaks["hbm_src"], algorithmic_bytes_per_launch=per_launch,
-                   note="achieved = algorithmic bytes of the launches (cells x CG iterations x bytes per "
-                        "cell-iteration of the streaming model: every pass reads its operands and writes its "
-                        "results once) / their CUDA-event time in the profiled estimate (launches in series); "
-                        "traffic = DRAM bytes per launch, the DRAM-to-algorithmic ratio of one ncu capture "
-                        "scaled to the average launch (" + tsrc + ")")
-    else:
+
+    def line(k):
+        base = {"kernel": k["kernel"], "launch_shape": k["shape"], "levels": k["levels"], "launches": k["launches"]}
+        if k["kernel"].startswith("solve") and not k["smem"]:
+            ach = k["bytes"] / (k["ms"] / 1e3) / 1e9
+            per_launch = k["bytes"] / max(k["launches"], 1)
+            key = "%s [%s]" % (k["kernel"], k["shape"])
+            traffic, tsrc = None, "no counter capture of this kernel version and launch shape"
+            if key in TRAFFIC:
+                dram, alg, tsrc = TRAFFIC[key]
+                traffic = dram / alg * per_launch
+            return dict(base, bound="hbm", achieved=ach, peak=peaks["hbm"], unit="GB/s", frac=ach / peaks["hbm"],
+                        traffic=traffic, peak_source=peaks["hbm_src"], algorithmic_bytes_per_launch=per_launch,
+                        note="achieved = algorithmic bytes of the launches (cells x CG iterations x bytes per "
+                             "cell-iteration of the streaming model: every pass reads its operands and writes its "
+                             "results once) / their CUDA-event time in the profiled estimate (launches in series); "
+                             "traffic = DRAM bytes per launch, the DRAM-to-algorithmic ratio of one ncu capture "
+                             "scaled to the average launch (" + tsrc + ")")
         use32 = f32 if k["kernel"].startswith("ce") else d["prec"] != 0
         pk_t = peaks["fp32"] if use32 else peaks["fp64"]
         src = "measured by mlmc_fma_peak (independent FMA chains, %s) on this GPU" % ("FP32" if use32 else "FP64")
         ach = k["flops"] / (k["ms"] / 1e3) / 1e12
         out = dict(base, bound="alu", achieved=ach, peak=pk_t, unit="TFLOP/s", frac=ach / pk_t, traffic=None,
-                   peak_source=src)
+                   peak_source=src,
+                   note="achieved = algorithmic flops (the library's per cell-iteration count) / CUDA-event time")
+        if k["kernel"].endswith(", 3>"):
+            out["note"] += ("; the register path is bound by instruction issue and latency, not by FMA "
+                            "throughput: per ncu it issues on about a third of the cycles (0.97e9 warp "
+                            "instructions in 2.33 ms on 65535 systems) with the FP64 pipe 58.5 % busy "
+                            "from the refinement and shuffle / shared-memory waits leading "
+                            "(profiles/solve_kernel_register_path_m16.txt)")
+        elif k["kernel"].startswith("ce"):
+            out["note"] += ("; the FP32 field passes are bound by the integer multiplies of Philox4x64 "
+                            "(the normals are generated inside the row pass)")
+        return out
+
+    out = line(max(cand, key=lambda c: c["ms"]))
     out["time_share"] = shares
+    out["all_shapes"] = [{key: v for key, v in line(c).items() if key in (
+        "kernel", "launch_shape", "levels", "bound", "achieved", "peak", "unit", "frac", "traffic")}
+        for c in sorted(cand, key=lambda c: -c["ms"])]
     return out
 
 
