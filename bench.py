@@ -747,7 +747,8 @@ def main():
     ap.add_argument("--bf16-arm", action="store_true")
     ap.add_argument("--fp64cg-arm", action="store_true")
     ap.add_argument("--plans", default=None, metavar="FILE",
-                    help="launch plans: replayed from FILE if it exists, else tuned and written there")
+                    help="launch plans and estimator costs: replayed from FILE if it exists, else tuned and "
+                         "written there")
     ap.add_argument("--cost-model", type=int, default=2, choices=[0, 1, 2],
                     help="estimator costs: 2 calibrated per-level GPU time (default), 0 the m^d model")
     ap.add_argument("--schedule", type=int, default=1, choices=[0, 1],
@@ -829,7 +830,11 @@ def main():
             before, after, tune = ctx.autotune_schedule(d["eps"], seed=args.seed + 4242, n_pilot=64,
                                                         cost_model=COST_MODEL)
             sched_tune = {"estimate_ms_before": before, "estimate_ms_after": after}
-    costs = calib(ctx)  # the per-sample costs of the final plans
+    if replay and replay.get("costs"):  # the costs the tuning run measured
+        ctx.set_costs(replay["costs"])
+        costs = replay["costs"]
+    else:
+        costs = calib(ctx)  # the per-sample costs of the final plans
     bctx = btune = None
     if base is not None:
         bctx = pk.Context(base, device=local, stream=stream)
@@ -845,9 +850,15 @@ def main():
                                                        cost_model=COST_MODEL, reps=1)
                 sched_tune = dict(sched_tune or {}, plain_fp64_arm={"estimate_ms_before": bb,
                                                                     "estimate_ms_after": ba})
-    bcosts = calib(bctx) if bctx is not None else None
+    bcosts = None
+    if bctx is not None:
+        if replay and replay.get("plain_costs"):
+            bctx.set_costs(replay["plain_costs"])
+            bcosts = replay["plain_costs"]
+        else:
+            bcosts = calib(bctx)
     if args.plans and not replay and rank == 0:
-        json.dump({"mixed": tune, "plain": btune}, open(args.plans, "w"))
+        json.dump({"mixed": tune, "plain": btune, "costs": costs, "plain_costs": bcosts}, open(args.plans, "w"))
     seed = args.seed + 7919 * rank
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
 

@@ -217,6 +217,12 @@ MLMC_API int mlmc_estimate(mlmc_ctx* ctx, double eps, uint64_t seed, int32_t n_p
  * NULL) receives them in seconds.  Errors: those of mlmc_level_batch(). */
 MLMC_API int mlmc_calibrate_costs(mlmc_ctx* ctx, uint64_t seed, double* C);
 
+/* Set the per-sample costs of cost_model 2 by hand (C: host array of L+1
+ * positive values, seconds or any common unit), e.g. those an earlier
+ * mlmc_calibrate_costs() returned, so that estimates in another process use
+ * the same sample-size rule.  Errors: MLMC_ERR_ARG. */
+MLMC_API int mlmc_set_costs(mlmc_ctx* ctx, const double* C);
+
 /* mlmc_estimate() with a cap on the number of top-up rounds (0 = pilot only);
  * mlmc_estimate() is this call with max_rounds = 10.  After a call the
  * context keeps the estimator state (per-level sums, costs, rounds, seed,

@@ -131,6 +131,7 @@ EXPORTS = {
     "mlmc_set_solver": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_double]),
     "mlmc_set_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "mlmc_calibrate_costs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]),
+    "mlmc_set_costs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "mlmc_set_launch_ex": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_double]),
@@ -424,6 +425,12 @@ class Context:
         C = (ctypes.c_double * L)()
         _check(lib().mlmc_calibrate_costs(self._h, seed, C), allow_failed=False)
         return list(C)
+
+    def set_costs(self, costs):
+        """mlmc_set_costs: fix the per-sample costs used by estimates with cost_model=2."""
+        L = self.model.L + 1
+        C = (ctypes.c_double * L)(*costs[:L])
+        _check(lib().mlmc_set_costs(self._h, C), allow_failed=False)
 
     def set_schedule(self, schedule):
         """mlmc_set_schedule: 1 = one work-queue launch per launch shape across the levels of a

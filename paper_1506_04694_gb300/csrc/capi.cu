@@ -1993,6 +1993,15 @@ int mlmc_calibrate_costs(mlmc_ctx* c, uint64_t seed, double* C_out) {
   return 0;
 }
 
+int mlmc_set_costs(mlmc_ctx* c, const double* C) {
+  if (!c || !C) return fail(MLMC_ERR_ARG, "null argument");
+  for (int l = 0; l <= c->model.L; ++l)
+    if (!(C[l] > 0) || !std::isfinite(C[l])) return fail(MLMC_ERR_ARG, "costs must be positive and finite");
+  for (int l = 0; l <= c->model.L; ++l) c->cal_C[l] = C[l];
+  c->cal_ok = true;
+  return 0;
+}
+
 int mlmc_profile(mlmc_ctx* c, int enable) {
   if (!c) return fail(MLMC_ERR_ARG, "null context");
   if (enable) std::memset(&c->prof, 0, sizeof(c->prof));

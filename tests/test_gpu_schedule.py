@@ -185,3 +185,19 @@ def test_multilevel_host_outputs_match_level_batches():
                         np.testing.assert_array_equal(got[l][j], ref[l][j])
                     for key in ("n", "n_failed", "iters_total") + pk.SUM_FIELDS:
                         assert got[l][0][key] == ref[l][0][key], (sched, use_graph, l, key)
+
+
+def test_set_costs_replays_calibration():
+    # mlmc_set_costs: a second context given the first one's calibrated costs
+    # draws the same sample sizes
+    torch, pk = need_gpu()
+    d = workloads.workload("lognormal_2layer_cgv_16to512", L=2)
+    with pk.Context(d, stream=torch.cuda.Stream()) as a:
+        C = a.calibrate_costs(seed=4)
+        ea = a.estimate(4e-3, seed=2, n_pilot=32, cost_model=2)
+    with pk.Context(d, stream=torch.cuda.Stream()) as b:
+        with pytest.raises(pk.MLMCError):
+            b.set_costs([1.0, -1.0, 1.0])
+        b.set_costs(C)
+        eb = b.estimate(4e-3, seed=2, n_pilot=32, cost_model=2)
+    assert list(ea["N"]) == list(eb["N"]) and ea["q_hat"] == eb["q_hat"]
