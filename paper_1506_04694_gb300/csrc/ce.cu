@@ -508,10 +508,108 @@ static int ce_sample3_impl(const CeLaunch& L, const R* scale, const void* tw, vo
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// ------------------------------------------- fused passes at M = 32 (FP32) -----
+// The 16 x 16 grids of the standard embedding (M = 2m = 32): one block per
+// sample does both passes.  The block draws the sample's 32 x 32 complex
+// normals into shared memory (the same Philox calls and scaling as
+// ce_rows_kernel), then each warp transforms whole rows with one point per
+// lane: a 32-point decimation-in-frequency FFT whose butterflies exchange
+// values between lanes by shuffles (stage of half-span h: the lane with bit
+// h clear keeps u + v, the other (u - v) W^((lane mod h) 32 / (2h))), which
+// leaves X[brev(lane)] in each lane; the even lanes hold the kept outputs a
+// < 16 and store them transposed, and the columns go through the same FFT,
+// the even lanes writing g[b][a] = mu + Re / Im for b < 16.  Same sums as the
+// two-pass form up to rounding order.
+constexpr int kFusedM = 32;
+
+__device__ __forceinline__ void fft32_dif_warp(float& xr, float& xi, const float2 (&w)[5], int lane) {
+  const unsigned full = 0xffffffffu;
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int h = 16 >> st;
+    const float pr = __shfl_xor_sync(full, xr, h), pi = __shfl_xor_sync(full, xi, h);
+    if ((lane & h) == 0) {
+      xr = xr + pr;
+      xi = xi + pi;
+    } else {
+      const float dr = pr - xr, di = pi - xi;  // (u - v), v = this lane's value
+      xr = dr * w[st].x - di * w[st].y;
+      xi = dr * w[st].y + di * w[st].x;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) ce_fused32_kernel(CeRowsArgs args, CeColsArgs cargs,
+                                                         const float* __restrict__ scale,
+                                                         const Cplx<float>* __restrict__ tw,
+                                                         float* __restrict__ g) {
+  __shared__ Cplx<float> s[kFusedM * kFusedM];           // the draw, [q2][q1]
+  __shared__ Cplx<float> wt[(kFusedM / 2) * kFusedM];    // row-pass output, [a][q2]
+  constexpr int M = kFusedM, m = kFusedM / 2;
+  const int64_t sidx = blockIdx.x + args.z_offset;
+  const uint64_t sample = (uint64_t)(args.first + sidx);
+  const BmTables tb{args.bm_sc, args.bm_lg};
+  for (int c = threadIdx.x; c < M * M / 2; c += blockDim.x) {  // one Philox call per two points
+    const int q = 2 * c, q2 = q / M, q1 = q - q2 * M;
+    const Words4 w = philox4x64_10((uint64_t)c, sample, (uint64_t)args.level, kStreamField0 + args.pair, args.seed);
+    float re0, im0, re1, im1;
+    box_muller_tab(w.w0, w.w1, tb, re0, im0, scale[q]);
+    box_muller_tab(w.w2, w.w3, tb, re1, im1, scale[q + 1]);
+    s[q2 * M + q1] = Cplx<float>{re0, im0};
+    s[q2 * M + q1 + 1] = Cplx<float>{re1, im1};
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  float2 w5[5];
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int h = 16 >> st;
+    const Cplx<float> t = tw[(lane & (h - 1)) * (16 / h)];
+    w5[st] = make_float2(t.x, t.y);
+  }
+  const int a_out = (int)(__brev((unsigned)lane) >> 27);  // this lane's output index
+  __syncthreads();
+  for (int q2 = warp; q2 < M; q2 += nwarp) {  // rows: W[q2][a], a < m
+    Cplx<float> x = s[q2 * M + lane];
+    fft32_dif_warp(x.x, x.y, w5, lane);
+    if (a_out < m) wt[a_out * M + q2] = x;
+  }
+  __syncthreads();
+  const bool has_im = cargs.t_im >= 0;
+  float* g0 = g + (sidx * cargs.n_layers + cargs.t_re) * (int64_t)(m * m);
+  float* g1 = g + (sidx * cargs.n_layers + (has_im ? cargs.t_im : cargs.t_re)) * (int64_t)(m * m);
+  const float mre = (float)cargs.mu_re, mim = (float)cargs.mu_im;
+  for (int a = warp; a < m; a += nwarp) {  // columns: y[b][a], b < m
+    Cplx<float> x = wt[a * M + lane];
+    fft32_dif_warp(x.x, x.y, w5, lane);
+    if (a_out < m) {
+      g0[a_out * m + a] = mre + x.x;
+      if (has_im) g1[a_out * m + a] = mim + x.y;
+    }
+  }
+}
+
 template <typename R, typename G>
 static int ce_sample_impl(const CeLaunch& L, const R* scale, const void* tw, void* W, G* g,
                           cudaStream_t st) {
   if (L.dim == 3) return ce_sample3_impl<R, G>(L, scale, tw, W, g, st);
+  if constexpr (std::is_same<R, float>::value && std::is_same<G, float>::value) {
+    if (L.M == kFusedM && L.m == kFusedM / 2) {  // both passes in one kernel, W unused
+      CeRowsArgs ra{};
+      ra.bm_sc = L.bm_sc;
+      ra.bm_lg = L.bm_lg;
+      ra.M = L.M; ra.logM = ilog2(L.M); ra.r3 = 0; ra.m = L.m; ra.rows_per_block = L.M;
+      ra.pair = L.pair; ra.level = L.level; ra.seed = L.seed; ra.first = L.first; ra.n_rows = L.M;
+      CeColsArgs ca{};
+      ca.M = L.M; ca.logM = ra.logM; ca.r3 = 0; ca.m = L.m; ca.cols_per_block = L.m; ca.n_layers = L.n_layers;
+      ca.ncols = L.m; ca.t_re = L.t_re; ca.t_im = L.t_im; ca.mu_re = L.mu_re; ca.mu_im = L.mu_im;
+      for (int64_t z0 = 0; z0 < L.n_samples; z0 += (int64_t)1 << 30) {
+        const int64_t nz = std::min<int64_t>(L.n_samples - z0, (int64_t)1 << 30);
+        ra.z_offset = z0;
+        ce_fused32_kernel<<<(unsigned)nz, 256, 0, st>>>(ra, ca, scale, (const Cplx<float>*)tw, g);
+      }
+      return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    }
+  }
   const size_t esz = sizeof(Cplx<R>);
   // rows / columns per block: at most 64 KB of FP64 (128 KB of FP32) per
   // block, a power of two so that it divides M (= 2^k or 3 2^k) and m

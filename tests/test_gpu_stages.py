@@ -100,21 +100,22 @@ def test_ce_fields_fp64(name, levels, embed):
                 np.testing.assert_allclose(g[s], ref, rtol=0, atol=1e-12)
 
 
-@pytest.mark.parametrize("level", [2, 5])
-def test_ce_fields_fp32_error_bound(level):
-    # the mixed workload's FP32 embedding: m = 64 (M = 192) and the finest
-    # level m = 512 (M = 1536, the cut-off embedding's radix-3 stage in FP32)
+@pytest.mark.parametrize("level,pad,n", [(0, 2, 40), (2, 3, 3), (5, 3, 3)])
+def test_ce_fields_fp32_error_bound(level, pad, n):
+    # the mixed workload's FP32 embedding: m = 16 (M = 32: both passes fused in
+    # one kernel, warp-shuffle FFTs), m = 64 (M = 192) and the finest level
+    # m = 512 (M = 1536, the cut-off embedding's radix-3 stage in FP32)
     torch, pk = need_gpu()
     d = workloads.workload("lognormal_2layer_cgv_16to512")
     model = darcy.Model.from_dict(d)
     m = model.m(level)
     with pk.Context(d) as ctx:
-        assert ctx.ce_info(level)[0] == 3 * m
-        g, _ = ctx.sample_fields(level, 3, seed=1)
+        assert ctx.ce_info(level)[0] == pad * m
+        g, _ = ctx.sample_fields(level, n, seed=1, first=5)
         g = g.cpu().numpy()
     cache = {}
-    for s in range(3):
-        ref = darcy.layer_fields(model, 1, level, s, m, cache)
+    for s in range(n):
+        ref = darcy.layer_fields(model, 1, level, 5 + s, m, cache)
         assert np.max(np.abs(g[s] - ref)) < 2e-5
 
 
