@@ -110,22 +110,25 @@ def test_estimate_same_under_both_schedules():
 
 def test_schedule_autotune_keeps_results():
     # the schedule-aware pass only changes launch shapes of the large levels:
-    # an estimate after it agrees with one on the per-level plans to the solver
-    # tolerance (same sample sizes under the deterministic cost model)
+    # a fixed multilevel batch gives the same level sums to the solver
+    # tolerance before and after it (a whole estimate may draw N_l one apart,
+    # since Eq. 3.7's ceiling sees V_l to that tolerance)
     torch, pk = need_gpu()
     d = workloads.workload("lognormal_2layer_cgv_16to512")
-    res = {}
+    n = [4000, 300, 60, 20, 8, 3]
     with pk.Context(d, stream=torch.cuda.Stream()) as ctx:
         ctx.autotune(seed=3)
-        res[0] = ctx.estimate(2e-3, seed=2, n_pilot=32, cost_model=0)
+        r0 = ctx.multilevel_batch(n, 2)
         before, after, plans = ctx.autotune_schedule(2e-3, seed=5, n_pilot=32, cost_model=0, reps=1)
         assert 0 < after <= before
         for p in plans:
             assert p["cluster"] in (0, 2, 4, 8) and p["threads"] > 0
             assert p["coarse"] is None or p["coarse"]["cluster"] in (0, 2, 4, 8)
-        res[1] = ctx.estimate(2e-3, seed=2, n_pilot=32, cost_model=0)
-    assert list(res[0]["N"]) == list(res[1]["N"])
-    assert abs(res[1]["q_hat"] - res[0]["q_hat"]) <= 1e-7 * abs(res[0]["q_hat"])
+        r1 = ctx.multilevel_batch(n, 2)
+    for l in range(len(n)):
+        assert r1[l]["n"] == r0[l]["n"] == n[l] and r1[l]["n_failed"] == r0[l]["n_failed"] == 0
+        for key in ("s_qf", "s_qc", "s_qcg", "s_yg"):
+            assert abs(r1[l][key] - r0[l][key]) <= 1e-7 * abs(r0[l]["s_qf"]), (l, key)
 
 
 def test_plans_replay_in_another_context():
