@@ -327,7 +327,8 @@ static bool fields_f32(const mlmc_model& md) { return md.prec == 1 || md.prec ==
 
 // Fields of chunk samples [first, first + n) of `level` into the selected work
 // buffers (c->wb), or into g_out when given.
-int run_fields(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t seed, void* g_out = nullptr) {
+int run_fields(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t seed, void* g_out = nullptr,
+               int* launches = nullptr) {
   const mlmc_model& md = c->model;
   const LevelTable& LT = c->lev[level];
   const bool f32 = fields_f32(md);
@@ -363,6 +364,8 @@ int run_fields(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t seed, 
       r = ce_sample_fp64(L, T.s64.as<double>(), T.tw64.p, B.W.p, static_cast<double*>(g_out), c->wst);
     if (r) return fail(MLMC_ERR_CUDA, std::string("field kernels: ") + cudaGetErrorString(cudaGetLastError()));
   }
+  const int nl = ce_launches_take();
+  if (launches) *launches += nl;
   return 0;
 }
 
@@ -533,8 +536,9 @@ int enqueue_level(mlmc_ctx* c, int level, int64_t first, int64_t n, uint64_t see
     SolveArgs a = base_args(c, level, seed, first + c0);
     if (md.k_kind == 1) {
       StageTimer t(c, 0);
-      if (int e = run_fields(c, level, first + c0, cn, seed)) return e;
-      t.stop(2 * c->n_draws * (int)((cn + 65534) / 65535));
+      int nlaunch = 0;
+      if (int e = run_fields(c, level, first + c0, cn, seed, nullptr, &nlaunch)) return e;
+      t.stop(nlaunch);
       a.g = c->wb->g.p;
       count_fields(c, level, cn);
     }
@@ -866,9 +870,11 @@ int enqueue_sched(mlmc_ctx* c, int n_levels, const int64_t* first, const int64_t
       for (int64_t c0 = 0; c0 < n[l]; c0 += chunk) {
         const int64_t cn = std::min<int64_t>(chunk, n[l] - c0);
         StageTimer t(c, 0);
-        if (int e = run_fields(c, l, first[l] + c0, cn, seed, S.wb.g.as<unsigned char>() + (size_t)c0 * gps))
+        int nlaunch = 0;
+        if (int e = run_fields(c, l, first[l] + c0, cn, seed, S.wb.g.as<unsigned char>() + (size_t)c0 * gps,
+                               &nlaunch))
           return e;
-        t.stop(2 * c->n_draws * (int)((cn + 65534) / 65535));
+        t.stop(nlaunch);
         count_fields(c, l, cn);
       }
     }

@@ -32,6 +32,15 @@ struct Cplx {
   R x, y;
 };
 
+// Kernel launches queued by the samplers since the last ce_launches_take()
+// (the host thread's own count, for the profiling counters).
+static thread_local int g_ce_launches = 0;
+int ce_launches_take() {
+  const int n = g_ce_launches;
+  g_ce_launches = 0;
+  return n;
+}
+
 __device__ __forceinline__ unsigned brev_n(unsigned v, int logn) {
   return logn ? (__brev(v) >> (32 - logn)) : 0u;
 }
@@ -504,6 +513,7 @@ static int ce_sample3_impl(const CeLaunch& L, const R* scale, const void* tw, vo
     ce_rows_kernel<R><<<dim3((unsigned)(M * M / rows), 1u, nz), 256, sm_r, st>>>(ra, scale, (const Cplx<R>*)tw, W1);
     ce_mid_kernel<R><<<dim3((unsigned)(m / cmid), (unsigned)M, nz), 256, sm_m, st>>>(ma, (const Cplx<R>*)tw, W1, W2);
     ce_cols_kernel<R, G><<<dim3((unsigned)(ncol3 / c3), 1u, nz), 256, sm_c, st>>>(ca, (const Cplx<R>*)tw, W2, g);
+    g_ce_launches += 3;
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -521,6 +531,7 @@ static int ce_sample3_impl(const CeLaunch& L, const R* scale, const void* tw, vo
 // the even lanes writing g[b][a] = mu + Re / Im for b < 16.  Same sums as the
 // two-pass form up to rounding order.
 constexpr int kFusedM = 32;
+
 
 __device__ __forceinline__ void fft32_dif_warp(float& xr, float& xi, const float2 (&w)[5], int lane) {
   const unsigned full = 0xffffffffu;
@@ -606,6 +617,7 @@ static int ce_sample_impl(const CeLaunch& L, const R* scale, const void* tw, voi
         const int64_t nz = std::min<int64_t>(L.n_samples - z0, (int64_t)1 << 30);
         ra.z_offset = z0;
         ce_fused32_kernel<<<(unsigned)nz, 256, 0, st>>>(ra, ca, scale, (const Cplx<float>*)tw, g);
+        g_ce_launches += 1;
       }
       return cudaGetLastError() == cudaSuccess ? 0 : -1;
     }
@@ -642,6 +654,7 @@ static int ce_sample_impl(const CeLaunch& L, const R* scale, const void* tw, voi
     ce_rows_kernel<R><<<gr, 256, sm_r, st>>>(ra, scale, (const Cplx<R>*)tw, (Cplx<R>*)W);
     dim3 gc((unsigned)(L.m / cols), 1u, nz);
     ce_cols_kernel<R, G><<<gc, 256, sm_c, st>>>(ca, (const Cplx<R>*)tw, (const Cplx<R>*)W, g);
+    g_ce_launches += 2;
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -51,6 +51,8 @@ int ce_sample_fp64(const CeLaunch& L, const double* scale, const void* tw, void*
                    cudaStream_t st);
 int ce_sample_fp32(const CeLaunch& L, const float* scale, const void* tw, void* W, float* g,
                    cudaStream_t st);
+// Kernel launches the samplers queued on this host thread since the last call (and reset).
+int ce_launches_take();
 size_t ce_w_bytes_per_sample(int m, int M, bool fp32, int dim);
 // Box-Muller tables: sc 1024 double2, lg 3*128 doubles.
 int bm_tables_build(double2* sc, double* lg, cudaStream_t st);
