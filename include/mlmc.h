@@ -201,8 +201,9 @@ MLMC_API int mlmc_level_batch_host(mlmc_ctx* ctx, int level, int64_t first, int6
  * with n_coarse = 0 at level 0, 1 plain, 2^d CGV (deterministic); 1: C_l =
  * measured seconds per sample of the pilot (64-sample batches: latency more
  * than throughput); 2: C_l = the per-sample GPU time of each level measured
- * by mlmc_calibrate_costs() (deterministic while those costs are kept).
- * out: host pointer, required. */
+ * by mlmc_calibrate_costs() or set by mlmc_set_costs() (deterministic while
+ * those costs are kept).  out: host pointer, required.  Errors: MLMC_ERR_ARG
+ * (eps <= 0, n_pilot < 2, cost_model not 0..2, cost_model 2 without costs). */
 MLMC_API int mlmc_estimate(mlmc_ctx* ctx, double eps, uint64_t seed, int32_t n_pilot,
                   int32_t cost_model, mlmc_estimate_out* out);
 

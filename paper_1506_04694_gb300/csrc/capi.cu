@@ -1393,6 +1393,7 @@ int mlmc_estimate_ex(mlmc_ctx* c, double eps, uint64_t seed, int32_t n_pilot, in
                      int32_t max_rounds, mlmc_estimate_out* out) {
   if (!c || !out) return fail(MLMC_ERR_ARG, "null argument");
   if (!(eps > 0) || n_pilot < 2 || max_rounds < 0) return fail(MLMC_ERR_ARG, "eps > 0, n_pilot >= 2, max_rounds >= 0");
+  if (cost_model < 0 || cost_model > 2) return fail(MLMC_ERR_ARG, "cost_model must be 0, 1 or 2");
   std::memset(out, 0, sizeof(*out));
   CUDA_TRY(cudaSetDevice(c->device));
   const double t0 = now_s();
