@@ -141,3 +141,21 @@ def test_solve_wrappers_check_shapes_on_host(pk):
         pk.solve_k_static(torch.ones((8, 8), dtype=torch.float64), q)
     with pytest.raises(pk.MLMCError, match="CUDA"):
         pk.solve_k_static(torch.ones((2, 8, 8), dtype=torch.float64), q)
+
+
+def test_null_context_is_an_argument_error(pk):
+    # the scheduling, tuning and cost entry points check their context and
+    # host arguments before any CUDA call: MLMC_ERR_ARG with a message
+    import ctypes
+    L = pk.lib()
+    ERR_ARG = -1
+    nul = ctypes.c_void_p(None)
+    C = (ctypes.c_double * 4)(1.0, 2.0, 3.0, 4.0)
+    i64 = (ctypes.c_int64 * 2)(0, 0)
+    assert L.mlmc_set_schedule(nul, 1) == ERR_ARG
+    assert L.mlmc_calibrate_costs(nul, 0, C) == ERR_ARG
+    assert L.mlmc_set_costs(nul, C) == ERR_ARG
+    assert L.mlmc_set_launch_ex(nul, 0, 0, 0, 256, 0, 1, 1, 0, 0, 0, 1e-5) == ERR_ARG
+    assert L.mlmc_autotune_schedule(nul, 1e-3, 0, 64, 0, 1, None, None) == ERR_ARG
+    assert L.mlmc_multilevel_batch_host(nul, 2, i64, i64, 0, 0, None, None, None, None, None) == ERR_ARG
+    assert b"null" in L.mlmc_last_error()
