@@ -703,8 +703,19 @@ def compare(args):
     torch.cuda.set_stream(stream)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     for name, md in arms.items():
+        # the default line's untimed set-up: plans per level, then (work-queue
+        # schedule) launch shapes re-timed on whole estimates, then the
+        # per-level costs of the final plans when the estimator uses them
         ctx = pk.Context(md, stream=stream)
+        ctx.set_schedule(args.schedule)
         ctx.autotune(seed=args.seed + 12345)
+        if COST_MODEL == 2:
+            ctx.calibrate_costs(seed=args.seed + 777)
+        if args.schedule:
+            ctx.autotune_schedule(md["eps"], seed=args.seed + 4242, n_pilot=64, cost_model=COST_MODEL,
+                                  reps=1 if md["prec"] == 0 else 2)
+            if COST_MODEL == 2:
+                ctx.calibrate_costs(seed=args.seed + 777)
         ms, est = timed_estimates(ctx, md, args.seed, args.steps, args.warmup, flush, stream)
         t = sum(ms) / len(ms) / 1e3
         out[name] = {"time_to_eps_s": t, "N": est["N"], "V": est["V"], "q_hat": est["q_hat"],
@@ -712,6 +723,7 @@ def compare(args):
                      "level_samples_per_s": sum(est["N"]) / t,
                      "iters_per_sample": [round(x["iters_total"] / max(x["n"], 1), 2) for x in est["sums"]],
                      "prec": PREC_NAMES[md["prec"]], "cgv": md["cgv"]}
+        print("%s: %s" % (name, json.dumps(out[name])), file=sys.stderr, flush=True)  # progress
         ctx.close()
         del ctx
         torch.cuda.empty_cache()
