@@ -58,3 +58,94 @@ def test_ncu_summary(tmp_path):
     line = [ln for ln in out if "solve_kernel<1," in ln][0]
     assert line.split()[-3] == "2" and float(line.split()[-2]) == pytest.approx(4.0)
     assert out[-1].split()[1] == "4" and float(out[-1].split()[2]) == pytest.approx(4.501)
+
+
+class _FakeEvent:
+    def __init__(self, enable_timing=False):
+        pass
+
+    def record(self, stream=None):
+        pass
+
+    def synchronize(self):
+        pass
+
+    def elapsed_time(self, other):
+        return 250.0
+
+
+def _fake_library(calls):
+    import types
+
+    class Context:
+        def __init__(self, model, stream=None, device=0):
+            self.model = model
+            self.log = []
+            calls.append((model["prec"], model["cgv"], self.log))
+
+        def set_schedule(self, s):
+            self.log.append(("set_schedule", s))
+
+        def autotune(self, seed=0):
+            self.log.append(("autotune",))
+            return []
+
+        def calibrate_costs(self, seed=0):
+            self.log.append(("calibrate_costs",))
+            return [1.0] * (self.model["L"] + 1)
+
+        def autotune_schedule(self, eps, seed=0, n_pilot=64, cost_model=0, reps=2):
+            self.log.append(("autotune_schedule", cost_model, reps))
+            return 1.0, 1.0, []
+
+        def estimate(self, eps, seed, n_pilot=64, cost_model=0):
+            self.log.append(("estimate", cost_model))
+            L = self.model["L"] + 1
+            return {"N": [4] * L, "V": [1.0] * L, "q_hat": 1.0, "bias": 0.0, "alpha": 1.0, "var_hat": 0.0,
+                    "sums": [{"iters_total": 8, "n": 4}] * L}
+
+        def close(self):
+            self.log.append(("close",))
+
+    return types.SimpleNamespace(Context=Context)
+
+
+@pytest.mark.parametrize("cost_model,schedule", [(2, 1), (0, 1), (2, 0)])
+def test_compare_sets_up_each_arm_like_the_default_line(monkeypatch, capsys, cost_model, schedule):
+    """--compare: every arm is tuned as the default line is (plans per level,
+    calibrated costs when cost model 2 is used, launch shapes re-timed on
+    whole estimates under the work-queue schedule) before its timed
+    estimates; run here against a fake library and fake CUDA events."""
+    import argparse
+    import json
+    import sys
+    import torch
+    calls = []
+    monkeypatch.setitem(sys.modules, "paper_1506_04694_gb300", _fake_library(calls))
+    monkeypatch.setattr(torch.cuda, "Stream", lambda *a, **k: None)
+    monkeypatch.setattr(torch.cuda, "set_stream", lambda s: None)
+    monkeypatch.setattr(torch.cuda, "Event", _FakeEvent)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "empty_cache", lambda: None)
+    real_empty = torch.empty
+    monkeypatch.setattr(torch, "empty", lambda *a, **k: real_empty(4, dtype=k.get("dtype")))
+    monkeypatch.setattr(bench, "COST_MODEL", cost_model)
+    args = argparse.Namespace(compare="lognormal_2layer_cgv_16to512", bf16_arm=False, fp64cg_arm=False,
+                              seed=0, steps=2, warmup=1, schedule=schedule)
+    bench.compare(args)
+    out = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert [(p, g) for p, g, _ in calls] == [(1, 1), (0, 0)]
+    for prec, _, log in calls:
+        setup = [e for e in log if e[0] != "estimate"][:-1]
+        want = [("set_schedule", schedule), ("autotune",)]
+        cal = [("calibrate_costs",)] if cost_model == 2 else []
+        want += cal
+        if schedule:
+            want += [("autotune_schedule", cost_model, 1 if prec == 0 else 2)] + cal
+        assert setup == want
+        # the timed estimates come after the whole set-up, with the same cost model
+        first = next(i for i, e in enumerate(log) if e[0] == "estimate")
+        assert first == len(want) and log[-1] == ("close",)
+        assert log[first:-1] == [("estimate", cost_model)] * 3
+    assert out["mixed_cgv"]["time_to_eps_s"] == pytest.approx(0.25)
+    assert out["speedup_mixed_cgv_vs_plain_fp64"] == pytest.approx(1.0)
