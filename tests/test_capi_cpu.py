@@ -159,3 +159,27 @@ def test_null_context_is_an_argument_error(pk):
     assert L.mlmc_autotune_schedule(nul, 1e-3, 0, 64, 0, 1, None, None) == ERR_ARG
     assert L.mlmc_multilevel_batch_host(nul, 2, i64, i64, 0, 0, None, None, None, None, None) == ERR_ARG
     assert b"null" in L.mlmc_last_error()
+
+
+def test_every_struct_field_matches_c(pk, tmp_path):
+    """Each ctypes structure of the binding against its C struct in the
+    header: the size and the offset of every member, by name."""
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    pairs = [(pk.Model, "mlmc_model"), (pk.LevelSums, "mlmc_level_sums"), (pk.EstimateOut, "mlmc_estimate_out"),
+             (pk.ProfileStats, "mlmc_profile_stats"), (pk.TuneReport, "mlmc_tune_report")]
+    lines, want = [], []
+    for cls, cname in pairs:
+        lines.append('  printf("%%zu\\n", sizeof(%s));' % cname)
+        want.append(ctypes.sizeof(cls))
+        for name, _ in cls._fields_:
+            lines.append('  printf("%%zu\\n", offsetof(%s, %s));' % (cname, name))
+            want.append(getattr(cls, name).offset)
+    prog = tmp_path / "fields.c"
+    prog.write_text("#include <stdio.h>\n#include <stddef.h>\n#include \"mlmc.h\"\nint main(void) {\n"
+                    + "\n".join(lines) + "\n  return 0;\n}\n")
+    exe = tmp_path / "fields"
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                           str(prog), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    assert got == want
