@@ -183,3 +183,75 @@ def test_every_struct_field_matches_c(pk, tmp_path):
                            str(prog), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     assert got == want
+
+
+def _prototypes():
+    """name -> (return type, [parameter types]) of every MLMC_API declaration
+    in the header, comments removed, whitespace normalised ("double* const*")."""
+    src = re.sub(r"/\*.*?\*/", " ", open(HEADER).read(), flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    norm = lambda t: re.sub(r"\s*\*", "*", " ".join(t.split())).strip()
+    out = {}
+    for ret, name, params in re.findall(r"MLMC_API\s+([^;(]*?)\b(mlmc_\w+)\s*\(([^;]*?)\)\s*;", src, flags=re.S):
+        ps = [] if params.strip() in ("", "void") else [norm(re.sub(r"\w+\s*$", "", p)) for p in params.split(",")]
+        out[name] = (norm(ret), ps)
+    return out
+
+
+_SCALARS = {"int": (4, "i"), "int32_t": (4, "i"), "int64_t": (8, "i"), "uint64_t": (8, "u"), "double": (8, "f")}
+
+
+def _ctypes_scalar(t):
+    code = getattr(t, "_type_", None)
+    if not isinstance(code, str) or code not in "bBhHiIlLqQfd":
+        return None
+    return ctypes.sizeof(t), "f" if code in "fd" else ("u" if code.isupper() else "i")
+
+
+def _matches(pk, ctype, t):
+    structs = {pk.Model: "mlmc_model", pk.LevelSums: "mlmc_level_sums", pk.EstimateOut: "mlmc_estimate_out",
+               pk.ProfileStats: "mlmc_profile_stats", pk.TuneReport: "mlmc_tune_report"}
+    if t == "void":
+        return ctype is None
+    if not t.endswith("*"):
+        return t in _SCALARS and _ctypes_scalar(ctype) == _SCALARS[t]
+    pointee = re.sub(r"^const ", "", t[:-1].strip())
+    pointee = re.sub(r" const$", "", pointee)
+    if ctype is ctypes.c_void_p:  # an untyped address: any data pointer
+        return True
+    if ctype is ctypes.c_char_p:
+        return pointee == "char"
+    target = getattr(ctype, "_type_", None)
+    if not isinstance(target, type):
+        return False
+    if target in structs:
+        return pointee == structs[target]
+    if target is ctypes.c_void_p:
+        return pointee.endswith("*")
+    return pointee in _SCALARS and _ctypes_scalar(target) == _SCALARS[pointee]
+
+
+def test_binding_signatures_match_prototypes(pk):
+    """The argument and return types the binding declares to ctypes agree
+    with the header's prototypes: same count, scalars of the same size and
+    kind, pointers where the header has pointers (typed ones to the same
+    struct or scalar)."""
+    protos = _prototypes()
+    assert set(protos) == set(pk.EXPORTS)
+    for name, (ret, params) in protos.items():
+        cret, cargs = pk.EXPORTS[name]
+        assert _matches(pk, cret, ret), (name, "return", ret, cret)
+        assert len(cargs) == len(params), (name, params, cargs)
+        for i, (ca, p) in enumerate(zip(cargs, params)):
+            assert _matches(pk, ca, p), (name, i, p, ca)
+
+
+def test_signature_check_catches_a_wrong_type(pk):
+    # the check above is not vacuous: a 32-bit integer where the header has
+    # int64_t, a scalar where it has a pointer, or the wrong struct all fail
+    assert not _matches(pk, ctypes.c_int32, "int64_t")
+    assert not _matches(pk, ctypes.c_uint64, "int64_t")
+    assert not _matches(pk, ctypes.c_double, "double*")
+    assert not _matches(pk, ctypes.POINTER(pk.LevelSums), "mlmc_estimate_out*")
+    assert not _matches(pk, ctypes.POINTER(ctypes.c_int32), "int64_t*")
+    assert _matches(pk, ctypes.POINTER(ctypes.c_void_p), "mlmc_ctx**")
