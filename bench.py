@@ -189,8 +189,9 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- helpers --
 def metric_name(d):
-    return ("level solves/s and time-to-RMSE eps=%g: %d-layer piecewise log-normal%s, m=%d..%d, %s%s"
-            % (d["eps"], d["n_layers"], ", 3-D" if d.get("dim", 2) == 3 else "", d["m0"], d["m0"] << d["L"],
+    return ("level solves/s and time-to-RMSE eps=%g: %d-layer piecewise %s%s, m=%d..%d, %s%s"
+            % (d["eps"], d["n_layers"], "log-normal" if d["k_kind"] == 1 else "constant (k = exp(Z) per layer)",
+               ", 3-D" if d.get("dim", 2) == 3 else "", d["m0"], d["m0"] << d["L"],
                {0: "plain FP64", 1: "mixed FP32-MG/FP64", 2: "mixed FP32-MG (BF16 faces)/FP64",
                 3: "FP64 CG with FP32-MG preconditioner"}[d["prec"]], " + CGV" if d["cgv"] else ""))
 
@@ -692,6 +693,8 @@ def compare(args):
     import paper_1506_04694_gb300 as pk
     import workloads
     d = workloads.workload(args.compare)
+    if "eps" not in d:
+        raise SystemExit("workload %s has a fixed sample count per level and no RMSE target" % args.compare)
     arms = {"mixed_cgv": dict(d), "plain_fp64": dict(d, prec=0, cgv=0)}
     if args.bf16_arm:
         arms["mixed_cgv_bf16_faces"] = dict(d, prec=2)
@@ -785,6 +788,9 @@ def main():
 
     import workloads
     d = workloads.workload(args.workload)
+    if "eps" not in d:
+        ap.error("workload %s has a fixed sample count per level and no RMSE target; the benchmark times "
+                 "time-to-eps" % args.workload)
     if args.prec is not None:
         d["prec"] = args.prec
     base = None

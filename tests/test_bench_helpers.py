@@ -149,3 +149,41 @@ def test_compare_sets_up_each_arm_like_the_default_line(monkeypatch, capsys, cos
         assert log[first:-1] == [("estimate", cost_model)] * 3
     assert out["mixed_cgv"]["time_to_eps_s"] == pytest.approx(0.25)
     assert out["speedup_mixed_cgv_vs_plain_fp64"] == pytest.approx(1.0)
+
+
+def _run_bench(*args):
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    return subprocess.run([sys.executable, os.path.join(root, "bench.py"), *args], capture_output=True, text=True,
+                          timeout=600, cwd=root)
+
+
+def test_reference_arm_line():
+    """--impl reference: the oracle timed on the host cores prints one JSON
+    line with the keys the benchmark contract names (run here on the small
+    three-layer workload; the default workload takes about 15 s a step)."""
+    import json
+    r = _run_bench("--impl", "reference", "--workload", "paper_3layer_const_16to128", "--steps", "2",
+                   "--warmup", "1")
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 1
+    assert line["unit"] == "level-samples/s" and line["higher_is_better"] is True and line["value"] > 0
+    assert line["ms_per_step"] > 0 and line["time_to_eps_extrapolated_s"] > 0
+    assert line["config"]["workload"] == "paper_3layer_const_16to128"
+    assert "piecewise constant" in line["metric"] and "eps=0.002" in line["metric"]
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
+def test_fixed_count_workload_rejected():
+    # the constant two-layer workload has a fixed N per level and no RMSE
+    # target: the time-to-eps benchmark refuses it with a message
+    r = _run_bench("--impl", "reference", "--workload", "const_2layer_8to32")
+    assert r.returncode == 2 and "no RMSE target" in r.stderr
+    r = _run_bench("--compare", "const_2layer_8to32")
+    assert r.returncode != 0 and "no RMSE target" in r.stderr
