@@ -151,13 +151,13 @@ def test_compare_sets_up_each_arm_like_the_default_line(monkeypatch, capsys, cos
     assert out["speedup_mixed_cgv_vs_plain_fp64"] == pytest.approx(1.0)
 
 
-def _run_bench(*args):
+def _run_bench(*args, env=None):
     import os
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     return subprocess.run([sys.executable, os.path.join(root, "bench.py"), *args], capture_output=True, text=True,
-                          timeout=600, cwd=root)
+                          timeout=600, cwd=root, env=dict(os.environ, **(env or {})))
 
 
 def test_reference_arm_line():
@@ -187,3 +187,10 @@ def test_fixed_count_workload_rejected():
     assert r.returncode == 2 and "no RMSE target" in r.stderr
     r = _run_bench("--compare", "const_2layer_8to32")
     assert r.returncode != 0 and "no RMSE target" in r.stderr
+
+
+def test_reference_arm_other_ranks_do_no_work():
+    # under torchrun only rank 0 times the oracle and prints; the others exit 0
+    r = _run_bench("--impl", "reference", "--workload", "paper_3layer_const_16to128", "--steps", "1",
+                   "--warmup", "0", env={"RANK": "1", "LOCAL_RANK": "1", "WORLD_SIZE": "2"})
+    assert r.returncode == 0 and r.stdout.strip() == ""
