@@ -115,6 +115,31 @@ def test_optimal_samples_rule():
         assert sum(x * c for x, c in zip(pert, C)) >= base * (1 - 1e-12)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_cgv_cost_bound(dim):
+    # Sec. 4.1: with CGV a level difference costs at most one fine solve more
+    # than in standard MLMC (2^d coarse solves of (m/2)^d cells instead of one),
+    # so less than twice its cost (paper value cgv_cost_factor_bound)
+    bound = json.load(open(os.path.join(GOLD, "paper_values.json")))["cgv_cost_factor_bound"]["value"]
+    name = "lognormal_3d_cgv_8to32" if dim == 3 else "lognormal_2layer_cgv_16to512"
+    cgv = darcy.Model.from_dict(workloads.workload(name))
+    plain = darcy.Model.from_dict(workloads.workload(name, cgv=0))
+    assert mlmc.parity_cost(cgv, 0) == mlmc.parity_cost(plain, 0) == cgv.m(0) ** dim
+    for lvl in range(1, cgv.L + 1):
+        c, p, fine = mlmc.parity_cost(cgv, lvl), mlmc.parity_cost(plain, lvl), cgv.m(lvl) ** dim
+        assert p == fine + (cgv.m(lvl) // 2) ** dim  # one coarse solve
+        assert c == 2 * fine  # 2^d coarse solves of 2^-d the cells
+        assert c - p <= fine and c < bound * p
+
+
+def test_paper_solver_tolerance_in_timed_workloads():
+    # Sec. 3.5: the outer PCG stops at ||r_m|| / ||r_0|| < 1e-10; the workloads
+    # the benchmark times with a target eps use that tolerance
+    tol = json.load(open(os.path.join(GOLD, "paper_values.json")))["pcg_relative_residual_tol"]["value"]
+    timed = [n for n, d in workloads.WORKLOADS.items() if "eps" in d and d["k_kind"] == 1]
+    assert timed and all(workloads.WORKLOADS[n]["tol"] == tol for n in timed)
+
+
 def test_estimate_const_model():
     model = const_model(L=1)
     est = mlmc.estimate(model, eps=0.15, seed=3, n_pilot=32)
