@@ -186,7 +186,9 @@ def test_cgv_variance_reduction():
     for lvl in (1, 2, 3):
         b = mlmc.level_batch(model, lvl, 0, 300, 1)
         ratios.append(np.var(b["qf"] - b["qc"], ddof=1) / np.var(b["qf"] - b["qc_cgv"], ddof=1))
-    assert ratios[0] > 10 and ratios[1] > 30 and ratios[2] > 100
+    # at h = 1/32 the reduction reaches the two orders of magnitude of Sec. 5
+    orders = json.load(open(os.path.join(GOLD, "paper_values.json")))["cgv_overall_reduction_orders"]["value"]
+    assert ratios[0] > 10 and ratios[1] > 30 and ratios[2] > 10 ** orders
     assert ratios[0] < ratios[1] < ratios[2]
 
 
