@@ -255,3 +255,16 @@ def test_signature_check_catches_a_wrong_type(pk):
     assert not _matches(pk, ctypes.POINTER(pk.LevelSums), "mlmc_estimate_out*")
     assert not _matches(pk, ctypes.POINTER(ctypes.c_int32), "int64_t*")
     assert _matches(pk, ctypes.POINTER(ctypes.c_void_p), "mlmc_ctx**")
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no fallback: without libmlmc.so every entry of the binding raises
+    import paper_1506_04694_gb300 as pk
+    import workloads
+    monkeypatch.setattr(pk, "_lib", None)
+    monkeypatch.setattr(pk, "LIB_PATH", str(tmp_path / "libmlmc.so"))
+    with pytest.raises(pk.MLMCError, match="not built"):
+        pk.lib()
+    # (without a GPU the context refuses first, with its own message)
+    with pytest.raises(pk.MLMCError, match="not built|no CUDA device"):
+        pk.Context(workloads.workload("lognormal_2layer_16to256"))
